@@ -1,0 +1,331 @@
+"""Benchmark: LM bundle-adjustment iterations/s on the 1M-observation scene.
+
+Workload: 200 cameras, 100k points, ~1M observations (track length 3-20,
+truncated geometric, mean 10), FP32 hot path with FP64 dot products, cost and
+gain ratio; 2% outliers, depth priors on 50% of observations.  A step is one
+full LM iteration (extraction, residuals/Jacobians, normal equations and
+Schur terms, PCG + back-substitution, candidate evaluation and accept/reject).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With N > 1 (torchrun) every rank solves its own replica
+on its own GPU ("replicas only": the solve does not shard across GPUs) and the
+time is the maximum over ranks.  --impl reference times the CPU oracle on the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_13310_b300 import scenes  # noqa: E402
+
+METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 GPU"
+WORKLOAD = "medium"
+LM_ITERS = 30
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_scene():
+    return scenes.make_scene(WORKLOAD)
+
+
+def oracle_cpu_baseline(scene, max_seconds=20.0, max_iters=30):
+    """The FP64 CPU oracle (test infrastructure) on a bounded sample: LM iterations
+    of the same scene until max_seconds of work or max_iters."""
+    import oracle
+    ob = oracle.OracleBA.from_scene(scene)
+    cams, pts = scene.cams0.copy(), scene.pts0.copy()
+    done, t_tot = 0, 0.0
+    alive = np.ones(scene.n_obs, np.uint8)
+    # one iteration per call keeps the loop bounded; the state carries over
+    lam_state = None
+    while done < max_iters and t_tot < max_seconds:
+        t0 = time.perf_counter()
+        cams, pts, rows = ob.lm(cams, pts, 1, alive=alive)
+        t_tot += time.perf_counter() - t0
+        done += 1
+        lam_state = rows[-1]["lam"] if rows else lam_state
+    return {"value": done / t_tot, "unit": "LM iters/s", "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": f"{done} LM iteration(s) of the 1M-observation scene (FP64, dense Cholesky "
+                      f"of the Schur system), {t_tot:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    scene = build_scene()
+    import oracle
+    ob = oracle.OracleBA.from_scene(scene)
+    cams, pts = scene.cams0.copy(), scene.pts0.copy()
+    alive = np.ones(scene.n_obs, np.uint8)
+    # W warm-up iterations, then K timed iterations, one oracle LM iteration per step
+    for _ in range(args.warmup):
+        cams, pts, _ = ob.lm(cams, pts, 1, alive=alive)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cams, pts, _ = ob.lm(cams, pts, 1, alive=alive)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "LM iters/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "1M-observation scene: 200 cams, 100k pts, %d obs" % scene.n_obs,
+                       "n_cams": scene.spec.n_cams, "n_pts": scene.spec.n_pts,
+                       "n_obs": scene.n_obs},
+            "cpu_baseline": {"value": value, "unit": "LM iters/s", "cores": oracle.get_threads(),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} timed LM iterations of the full scene after "
+                                       f"{args.warmup} warm-up iterations"},
+            "e2e": {"value": value, "unit": "LM iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=27)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-RMSE comparison")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2510_13310_b300 import ba
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    scene = build_scene()
+    N = scene.n_obs
+    opts = ba.Options(precision=ba.BA_FP32)
+    prob = ba.Problem.from_scene(scene, opts, stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    infos = []
+    for _ in range(args.warmup):
+        prob.lm_step()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = prob.kernel_launches
+    step_ms = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            infos.append(prob.lm_step())
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+    torch.cuda.synchronize(dev)
+    launches = prob.kernel_launches - launches0
+    tot_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps / (tot_ms / 1e3)
+
+    # Jacobian+Schur throughput: observations through steps (a)+(b) per second
+    lin = [i for i in infos if i["ms"][1] > 0]
+    ab_ms = statistics.median([i["ms"][1] + i["ms"][2] for i in lin]) if lin else None
+    schur_ms = statistics.median([i["ms"][2] for i in infos])
+    gobs = N / (ab_ms * 1e-3) / 1e9 if ab_ms else None
+
+    # roofline of the dominant kernel: the persistent PCG solve
+    hbm, peak_kind = _peaks()
+    pcg_ms = [i["ms"][3] for i in infos if i["pcg_iters"] > 0]
+    pcg_it = [i["pcg_iters"] for i in infos if i["pcg_iters"] > 0]
+    P = scene.spec.n_pts
+    bytes_per_matvec = N * (27 * 4 + 4) + P * (6 * 4 + 4)
+    if pcg_ms:
+        achieved = (sum(pcg_it) * bytes_per_matvec) / (sum(pcg_ms) * 1e-3) / 1e9
+    else:
+        achieved = 0.0
+    roofline = {"kernel": "k_pcg (persistent block-Jacobi PCG, implicit Schur matvec)",
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": peak_kind, "traffic": None,
+                "bytes_per_matvec": bytes_per_matvec,
+                "mean_pcg_iters": statistics.mean(pcg_it) if pcg_it else 0,
+                "pcg_ms_median": statistics.median(pcg_ms) if pcg_ms else None}
+
+    # end to end through the public API from pinned host buffers, one full solve
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_in = [pin(scene.cams0), pin(scene.pts0), pin(scene.obs_cam), pin(scene.obs_pt),
+            pin(scene.obs_uv), pin(scene.depth)]
+    h_cams = torch.empty((scene.spec.n_cams, 9), dtype=torch.float64).pin_memory()
+    h_pts = torch.empty((P, 3), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    p2 = ba.Problem(*h_in, options=opts, stream=stream.cuda_stream)
+    p2.solve(LM_ITERS)
+    p2.get_params(h_cams, h_pts)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    p2.close()
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    d2h = (h_cams.numel() + h_pts.numel()) * 8
+    e2e = {"value": LM_ITERS / e2e_s, "unit": "LM iters/s",
+           "h2d_bytes_per_step": h2d / LM_ITERS, "d2h_bytes_per_step": d2h / LM_ITERS,
+           "what": f"ba_create from pinned host arrays + {LM_ITERS} LM iterations + "
+                   "parameters back to pinned host memory, wall clock"}
+
+    # time to the FP64 GPU path's final RMSE
+    ttr = None
+    if not args.no_ttr:
+        def trajectory(prec):
+            p = ba.Problem.from_scene(scene, ba.Options(precision=prec), stream=stream.cuda_stream)
+            rows, t = [], 0.0
+            for _ in range(LM_ITERS):
+                ev0.record(stream)
+                r = p.lm_step()
+                ev1.record(stream)
+                ev1.synchronize()
+                t += ev0.elapsed_time(ev1) / 1e3
+                rows.append((t, r))
+            F, rm = p.eval_cost()
+            p.close()
+            return rows, F, rm
+        rows64, F64, rmse64 = trajectory(ba.BA_FP64)
+        rows32, F32, rmse32 = trajectory(ba.BA_FP32)
+
+        def reach(rows, target_rmse):
+            # the end time of the first iteration whose accepted result is within
+            # 1e-5 (relative) of the target RMSE, or None
+            for i, (t, r) in enumerate(rows):
+                nxt = rows[i + 1][1]["rmse_px"] if i + 1 < len(rows) else None
+                if nxt is not None and abs(nxt - target_rmse) <= 1e-5 * target_rmse:
+                    return t
+            return None
+        t64 = reach(rows64, rmse64)
+        t32 = reach(rows32, rmse64)
+        ttr = {"target_rmse_px": rmse64, "fp64_final_cost": F64, "fp32_final_rmse_px": rmse32,
+               "fp32_final_cost": F32, "fp64_s": t64, "fp32_s": t32,
+               "speedup": (t64 / t32) if (t64 and t32) else None,
+               "fp64_total_s": rows64[-1][0], "fp32_total_s": rows32[-1][0],
+               "rule": "first iteration whose result RMSE is within 1e-5 of the FP64 final RMSE"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_cpu_baseline(scene)
+
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": "LM iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "1M-observation scene: 200 cams, 100k pts, %d obs, FP32 with "
+                                   "FP64 dots/cost/gain" % N,
+                       "n_cams": scene.spec.n_cams, "n_pts": P, "n_obs": N,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "flushed between steps (256 MB write)"},
+            "jacobian_schur_gobs_s": gobs, "jacobian_schur_ms": ab_ms, "schur_terms_ms": schur_ms,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_rmse": ttr,
+            "gpu_launches": launches, "clocks": clk.summary(),
+            "lm_trace": [{"cost": i["cost"], "rmse_px": i["rmse_px"], "accepted": i["accepted"],
+                          "pcg_iters": i["pcg_iters"], "ms": [round(m, 3) for m in i["ms"][:7]]}
+                         for i in infos[:5]]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/* ba_b300.h -- C ABI of the B300 (sm_103a) Levenberg-Marquardt bundle adjuster
+ * with metric depth priors and dynamic parameter extraction
+ * (InstantSfM, arXiv 2510.13310: Sec. 3.2 BA objective, Sec. 3.3 LM,
+ *  Sec. 4.1 depth-constrained Jacobian, Sec. 4.2 dynamic parameter extraction).
+ *
+ * One LM iteration runs five steps, all as CUDA kernels on one GPU:
+ *  (a) per-observation reprojection + depth residuals and Jacobian blocks
+ *      (Eq. BA objective with depth, Sec. 4.1),
+ *  (b) normal-equation blocks U (camera), V (point), W (camera-point), the
+ *      Schur right-hand side and the block-Jacobi preconditioner (Eq. LM),
+ *  (c) dynamic active-set extraction: validity (z > min_depth, in image),
+ *      optional sticky residual drop, threshold peeling, ascending ranks
+ *      (Sec. 4.2 steps 1-2, Eqs. O_valid, C_active, P_active, rank),
+ *  (d) block-Jacobi PCG on the reduced camera system, point back-substitution
+ *      and scatter of the compact update (Sec. 4.2 step 3),
+ *  (e) Marquardt damping and the gain-ratio accept/reject (Sec. 3.3).
+ *
+ * Camera parameters (9 doubles, row-major [C][9]): axis-angle w (world-to-camera
+ * rotation), translation t, focal f, radial k1, k2.  A point X projects as
+ * P = Exp(w) X + t (+z forward), (x, y) = (P_x, P_y) / P_z, rr = x^2 + y^2,
+ * pixel = f (1 + k1 rr + k2 rr^2) (x, y) + (cx, cy).  Rotation updates are
+ * left-multiplicative: w <- Log(Exp(dw) Exp(w)).
+ *
+ * Pointers.  Every array argument may be a host pointer (pageable or pinned)
+ * or a device pointer of the problem's device; copies use unified addressing
+ * (cudaMemcpyDefault).  The library copies inputs into buffers it owns; the
+ * caller keeps ownership of everything it passes.  Outputs are written to
+ * caller-owned memory.  Calls are ordered on the stream given to ba_create and
+ * return once their results are in the destination.  Errors are returned as a
+ * ba_status, never thrown or trapped; ba_last_error() gives a message.
+ * A problem handle must not be used from two threads at once.
+ */
+#ifndef BA_B300_H
+#define BA_B300_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BA_OK = 0,
+  BA_ERR_INVALID_ARG = 1,   /* bad size, index, option or non-finite input */
+  BA_ERR_CUDA = 2,          /* a CUDA call failed; see ba_last_error() */
+  BA_ERR_OOM = 3,           /* device allocation failed */
+  BA_ERR_NOT_CONVERGED = 4, /* PCG hit its iteration cap; the step is still usable */
+  BA_ERR_NONFINITE = 5,     /* non-finite cost or step: the step was rejected */
+  BA_ERR_STATE = 6,         /* call out of order (e.g. backward before a solve) */
+  BA_ERR_TIMEOUT = 7        /* an in-kernel grid barrier gave up waiting */
+} ba_status;
+
+typedef enum { BA_FP64 = 0, BA_FP32 = 1 } ba_precision;
+
+typedef struct {
+  ba_precision precision;      /* BA_FP64: every step in FP64.  BA_FP32: (a),(b),(d) in FP32
+                                  with FP64 PCG dot products; cost, gain ratio and the
+                                  extraction predicate always in FP64 */
+  int img_w, img_h;            /* image size for the in-frustum test (640, 480) */
+  double cx, cy;               /* principal point, held fixed (320, 240) */
+  double huber_delta;          /* Huber threshold on |r| in px (1.0); <= 0: squared loss */
+  double depth_weight;         /* lambda_d: weight of the squared inverse-depth residual (1.0) */
+  double invalid_depth_weight; /* weight of the zero-target depth residual of observations
+                                  without a prior (Sec. 4.1 sentinel); default 0 */
+  double min_depth;            /* validity: camera-frame z > min_depth (0.1) */
+  int extract_every;           /* residual drop at iterations e, 2e, ...; 0 = never */
+  double drop_residual_px;     /* drop observations with |r_uv| > this; <= 0 disables */
+  int min_cam_obs, min_pt_obs; /* extraction thresholds (1, 1) */
+  double lambda0;              /* initial damping (1e-4) */
+  double pcg_rel_tol;          /* PCG stop: |r| <= tol |b| (1e-6) */
+  int pcg_max_iters;           /* PCG cap (500) */
+  const int32_t* fixed_cams;   /* host array of gauge cameras held constant ({0}) */
+  int n_fixed;
+} ba_options;
+
+typedef struct {
+  double cost;        /* F(x) = 1/2 sum rho(|r_k|^2) over the iteration's active set */
+  double rmse_px;     /* reprojection RMSE over the active set */
+  double lambda;      /* damping used by this iteration's solve */
+  double gain;        /* (F(x) - F(x + dx)) / predicted decrease */
+  double pred_decrease;
+  double cand_cost;   /* F(x + dx) over the same active set */
+  int accepted;
+  int pcg_iters;
+  double pcg_rel_res;
+  int64_t n_cam_act, n_pt_act, n_obs_act;
+  float ms[8];        /* per-phase device time: extract, linearize, schur, pcg, backsub,
+                         evaluate, total, host */
+} ba_iter_info;
+
+typedef struct ba_problem ba_problem;
+
+/* Fill *o with the defaults listed above (FP32, camera 0 fixed). */
+void ba_default_options(ba_options* o);
+
+/* Create a problem: cams [C][9], pts [P][3], obs_cam/obs_pt [N] (int32 indices),
+ * obs_uv [N][2] pixels, depth [N] metric depth prior (<= 0 or NaN: none).
+ * Checks index ranges, finiteness and duplicate (camera, point) pairs on the
+ * host (BA_ERR_INVALID_ARG).  Limits: N < 2^31, at most 256 observations per
+ * point.  stream: a cudaStream_t (NULL = legacy default stream).  The problem
+ * lives on the device current at the call. */
+ba_status ba_create(const ba_options* opts, void* stream, int64_t n_cams, const double* cams,
+                    int64_t n_pts, const double* pts, int64_t n_obs, const int32_t* obs_cam,
+                    const int32_t* obs_pt, const double* obs_uv, const double* depth,
+                    ba_problem** out);
+
+/* One LM iteration, steps (c) -> (a) -> (b) -> (d) -> (e).  info may be NULL.
+ * Returns BA_ERR_NOT_CONVERGED when PCG hit its cap (the iteration still ran). */
+ba_status ba_lm_step(ba_problem* pb, ba_iter_info* info);
+
+/* Up to max_iters LM iterations; log has max_iters entries or is NULL. */
+ba_status ba_solve(ba_problem* pb, int max_iters, ba_iter_info* log, int* n_done);
+
+/* Current parameters, cams [C][9] and pts [P][3]. */
+ba_status ba_get_params(ba_problem* pb, double* cams, double* pts);
+
+/* Replace the current parameters; the next step re-extracts and re-linearises. */
+ba_status ba_set_params(ba_problem* pb, const double* cams, const double* pts);
+
+/* Active sets of the latest extraction (Sec. 4.2 step 2).  Masks are 0/1 bytes;
+ * obs_mask is in the input observation order; cam_rank is the position among
+ * active non-gauge cameras, pt_rank among active points, -1 otherwise.
+ * Any output may be NULL. */
+ba_status ba_get_active(ba_problem* pb, uint8_t* cam_mask, uint8_t* pt_mask, uint8_t* obs_mask,
+                        int32_t* cam_rank, int32_t* pt_rank);
+
+/* Run step (c) now on the current parameters (validity, optional residual drop
+ * when drop != 0, peeling, ranks).  n_rounds (nullable) gets the peel rounds. */
+ba_status ba_extract(ba_problem* pb, int drop, int* n_rounds);
+
+/* Run steps (a)-(b) at the current parameters and active set and copy out FP64
+ * blocks in full indexing: U [C][81], V [P][9], gc [C][9], gp [P][3] (rows of
+ * inactive entries are zero) and W [N][27] (9x3 row-major, input order; zero
+ * for inactive observations).  Any output may be NULL. */
+ba_status ba_linearize(ba_problem* pb, double* U, double* V, double* W, double* gc, double* gp);
+
+/* Step (d) for damping lambda at the current linearisation: the step in full
+ * indexing, dc [C][9] and dp [P][3] (zero for inactive and gauge entries).
+ * info (nullable) receives pcg_iters, pcg_rel_res and pred_decrease. */
+ba_status ba_solve_damped(ba_problem* pb, double lambda, double* dc, double* dp,
+                          ba_iter_info* info);
+
+/* FP64 cost 1/2 sum rho and RMSE of the given parameters over the current
+ * active set (NULL cams/pts: the current parameters). */
+ba_status ba_eval_cost(ba_problem* pb, const double* cams, const double* pts, double* cost,
+                       double* rmse_px);
+
+/* Implicit-adjoint gradients at the current state: with the active set and the
+ * IRLS weights frozen, solve H mu = (dL/dcams, dL/dpts) with the undamped
+ * Gauss-Newton matrix through the Schur complement, then
+ * dL/du_k = rho'_k (J_k mu)_0, dL/dv_k = rho'_k (J_k mu)_1,
+ * dL/dd_k = -rho'_k sqrt(w_k) m_k / d_k^2 (J_k mu)_2.
+ * dL_dcams [C][9], dL_dpts [P][3] in; dL_duv [N][2], dL_ddepth [N] out (input order). */
+ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_dpts,
+                      double* dL_duv, double* dL_ddepth);
+
+/* Number of this library's kernels launched since creation (counts launches). */
+int64_t ba_kernel_launches(const ba_problem* pb);
+
+void ba_destroy(ba_problem* pb);
+const char* ba_status_string(ba_status s);
+const char* ba_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,292 @@
+"""Python binding of the C ABI in include/ba_b300.h (libba_b300.so).
+
+Argument marshalling only: every step of the LM iteration runs in the
+library's CUDA kernels.  Arrays may be NumPy arrays (host memory) or torch
+tensors (host or CUDA); the library copies through unified addressing.
+Importing this module never falls back to a CPU implementation: if the
+shared library is missing or cannot be loaded, it raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libba_b300.so")
+
+BA_OK, BA_ERR_INVALID_ARG, BA_ERR_CUDA, BA_ERR_OOM = 0, 1, 2, 3
+BA_ERR_NOT_CONVERGED, BA_ERR_NONFINITE, BA_ERR_STATE, BA_ERR_TIMEOUT = 4, 5, 6, 7
+BA_FP64, BA_FP32 = 0, 1
+
+# every symbol include/ba_b300.h declares
+EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
+           "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
+           "ba_eval_cost", "ba_backward", "ba_kernel_launches", "ba_destroy", "ba_status_string",
+           "ba_last_error")
+
+
+class _Options(ct.Structure):
+    _fields_ = [("precision", ct.c_int), ("img_w", ct.c_int), ("img_h", ct.c_int),
+                ("cx", ct.c_double), ("cy", ct.c_double), ("huber_delta", ct.c_double),
+                ("depth_weight", ct.c_double), ("invalid_depth_weight", ct.c_double),
+                ("min_depth", ct.c_double), ("extract_every", ct.c_int),
+                ("drop_residual_px", ct.c_double), ("min_cam_obs", ct.c_int),
+                ("min_pt_obs", ct.c_int), ("lambda0", ct.c_double), ("pcg_rel_tol", ct.c_double),
+                ("pcg_max_iters", ct.c_int), ("fixed_cams", ct.POINTER(ct.c_int32)),
+                ("n_fixed", ct.c_int)]
+
+
+class _IterInfo(ct.Structure):
+    _fields_ = [("cost", ct.c_double), ("rmse_px", ct.c_double), ("lambda_", ct.c_double),
+                ("gain", ct.c_double), ("pred_decrease", ct.c_double), ("cand_cost", ct.c_double),
+                ("accepted", ct.c_int), ("pcg_iters", ct.c_int), ("pcg_rel_res", ct.c_double),
+                ("n_cam_act", ct.c_int64), ("n_pt_act", ct.c_int64), ("n_obs_act", ct.c_int64),
+                ("ms", ct.c_float * 8)]
+
+    def as_dict(self):
+        return dict(cost=self.cost, rmse_px=self.rmse_px, lam=self.lambda_, gain=self.gain,
+                    pred_decrease=self.pred_decrease, cand_cost=self.cand_cost,
+                    accepted=bool(self.accepted), pcg_iters=self.pcg_iters,
+                    pcg_rel_res=self.pcg_rel_res, n_cam_act=self.n_cam_act,
+                    n_pt_act=self.n_pt_act, n_obs_act=self.n_obs_act, ms=list(self.ms))
+
+
+_lib = None
+
+
+def lib():
+    """Load libba_b300.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2510_13310_b300.build` (no CPU fallback exists)")
+        try:  # torch first, so the CUDA runtime it loads is the one shared with the library
+            import torch  # noqa: F401
+        except ImportError:
+            pass
+        L = ct.CDLL(LIB_PATH)
+        vp = ct.c_void_p
+        L.ba_default_options.argtypes = [ct.POINTER(_Options)]
+        L.ba_create.argtypes = [ct.POINTER(_Options), vp, ct.c_int64, vp, ct.c_int64, vp, ct.c_int64,
+                                vp, vp, vp, vp, ct.POINTER(vp)]
+        L.ba_lm_step.argtypes = [vp, ct.POINTER(_IterInfo)]
+        L.ba_solve.argtypes = [vp, ct.c_int, ct.POINTER(_IterInfo), ct.POINTER(ct.c_int)]
+        L.ba_get_params.argtypes = [vp, vp, vp]
+        L.ba_set_params.argtypes = [vp, vp, vp]
+        L.ba_get_active.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.ba_extract.argtypes = [vp, ct.c_int, ct.POINTER(ct.c_int)]
+        L.ba_linearize.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.ba_solve_damped.argtypes = [vp, ct.c_double, vp, vp, ct.POINTER(_IterInfo)]
+        L.ba_eval_cost.argtypes = [vp, vp, vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+        L.ba_backward.argtypes = [vp, vp, vp, vp, vp]
+        L.ba_kernel_launches.argtypes = [vp]
+        L.ba_kernel_launches.restype = ct.c_int64
+        L.ba_destroy.argtypes = [vp]
+        L.ba_status_string.argtypes = [ct.c_int]
+        L.ba_status_string.restype = ct.c_char_p
+        L.ba_last_error.restype = ct.c_char_p
+        for f in ("ba_create", "ba_lm_step", "ba_solve", "ba_get_params", "ba_set_params",
+                  "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped", "ba_eval_cost",
+                  "ba_backward"):
+            getattr(L, f).restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+class BAError(RuntimeError):
+    def __init__(self, status, where):
+        L = lib()
+        msg = L.ba_status_string(status).decode()
+        detail = L.ba_last_error().decode()
+        super().__init__(f"{where}: {msg} ({detail})")
+        self.status = status
+
+
+def _check(status, where, allow=(BA_OK,)):
+    if status not in allow:
+        raise BAError(status, where)
+    return status
+
+
+@dataclasses.dataclass
+class Options:
+    precision: int = BA_FP32
+    img_w: int = 640
+    img_h: int = 480
+    cx: float = 320.0
+    cy: float = 240.0
+    huber_delta: float = 1.0
+    depth_weight: float = 1.0
+    invalid_depth_weight: float = 0.0
+    min_depth: float = 0.1
+    extract_every: int = 0
+    drop_residual_px: float = 0.0
+    min_cam_obs: int = 1
+    min_pt_obs: int = 1
+    lambda0: float = 1e-4
+    pcg_rel_tol: float = 1e-6
+    pcg_max_iters: int = 500
+    fixed_cams: tuple = (0,)
+
+
+class _Arr:
+    """Keeps a host/device buffer alive and exposes its address."""
+
+    def __init__(self, a, dtype):
+        self.obj = a
+        if hasattr(a, "data_ptr"):  # torch tensor
+            import torch
+            tdt = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8,
+                   np.float32: torch.float32}[dtype]
+            t = a.contiguous()
+            if t.dtype != tdt:
+                t = t.to(tdt)
+            self.obj = t
+            self.ptr = t.data_ptr()
+        else:
+            arr = np.ascontiguousarray(a, dtype=dtype)
+            self.obj = arr
+            self.ptr = arr.ctypes.data
+
+    @property
+    def p(self):
+        return ct.c_void_p(self.ptr)
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return ct.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ct.c_void_p(0)
+
+
+class Problem:
+    """One bundle-adjustment problem living on the current CUDA device."""
+
+    def __init__(self, cams, pts, obs_cam, obs_pt, obs_uv, depth, options: Options | None = None,
+                 stream=None):
+        self.L = lib()
+        self.options = options or Options()
+        o = self.options
+        self._fixed = np.ascontiguousarray(np.asarray(o.fixed_cams, dtype=np.int32))
+        copt = _Options(o.precision, o.img_w, o.img_h, o.cx, o.cy, o.huber_delta, o.depth_weight,
+                        o.invalid_depth_weight, o.min_depth, o.extract_every, o.drop_residual_px,
+                        o.min_cam_obs, o.min_pt_obs, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
+                        self._fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(self._fixed))
+        arrs = [_Arr(cams, np.float64), _Arr(pts, np.float64), _Arr(obs_cam, np.int32),
+                _Arr(obs_pt, np.int32), _Arr(obs_uv, np.float64), _Arr(depth, np.float64)]
+        self.n_cams = int(np.prod(arrs[0].obj.shape)) // 9
+        self.n_pts = int(np.prod(arrs[1].obj.shape)) // 3
+        self.n_obs = int(np.prod(arrs[2].obj.shape))
+        h = ct.c_void_p()
+        st = self.L.ba_create(ct.byref(copt), _stream_handle(stream), self.n_cams, arrs[0].p,
+                              self.n_pts, arrs[1].p, self.n_obs, arrs[2].p, arrs[3].p, arrs[4].p,
+                              arrs[5].p, ct.byref(h))
+        _check(st, "ba_create")
+        self.h = h
+
+    @classmethod
+    def from_scene(cls, scene, options: Options | None = None, stream=None):
+        opts = options or Options()
+        if tuple(opts.fixed_cams) != tuple(int(c) for c in scene.fixed_cams):
+            opts = dataclasses.replace(opts, fixed_cams=tuple(int(c) for c in scene.fixed_cams))
+        return cls(scene.cams0, scene.pts0, scene.obs_cam, scene.obs_pt, scene.obs_uv, scene.depth,
+                   opts, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ba_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lm_step(self):
+        info = _IterInfo()
+        _check(self.L.ba_lm_step(self.h, ct.byref(info)), "ba_lm_step",
+               allow=(BA_OK, BA_ERR_NOT_CONVERGED, BA_ERR_NONFINITE))
+        return info.as_dict()
+
+    def solve(self, max_iters):
+        log = (_IterInfo * max(1, max_iters))()
+        n = ct.c_int(0)
+        _check(self.L.ba_solve(self.h, int(max_iters), log, ct.byref(n)), "ba_solve",
+               allow=(BA_OK, BA_ERR_NOT_CONVERGED))
+        return [log[i].as_dict() for i in range(n.value)]
+
+    def get_params(self, cams=None, pts=None):
+        """Copies into the given buffers (NumPy or torch); allocates NumPy arrays if omitted."""
+        c = cams if cams is not None else np.zeros((self.n_cams, 9))
+        p = pts if pts is not None else np.zeros((self.n_pts, 3))
+        ca, pa = _Arr(c, np.float64), _Arr(p, np.float64)
+        _check(self.L.ba_get_params(self.h, ca.p, pa.p), "ba_get_params")
+        return ca.obj, pa.obj
+
+    def set_params(self, cams, pts):
+        ca, pa = _Arr(cams, np.float64), _Arr(pts, np.float64)
+        _check(self.L.ba_set_params(self.h, ca.p, pa.p), "ba_set_params")
+
+    def extract(self, drop=False):
+        n = ct.c_int(0)
+        _check(self.L.ba_extract(self.h, 1 if drop else 0, ct.byref(n)), "ba_extract")
+        return n.value
+
+    def get_active(self):
+        cm = np.zeros(self.n_cams, np.uint8)
+        pm = np.zeros(self.n_pts, np.uint8)
+        om = np.zeros(self.n_obs, np.uint8)
+        cr = np.zeros(self.n_cams, np.int32)
+        pr = np.zeros(self.n_pts, np.int32)
+        _check(self.L.ba_get_active(self.h, cm.ctypes.data, pm.ctypes.data, om.ctypes.data,
+                                    cr.ctypes.data, pr.ctypes.data), "ba_get_active")
+        return dict(cam_mask=cm, pt_mask=pm, obs_mask=om, cam_rank=cr, pt_rank=pr)
+
+    def linearize(self, want_W=True):
+        U = np.zeros((self.n_cams, 9, 9)); V = np.zeros((self.n_pts, 3, 3))
+        gc = np.zeros((self.n_cams, 9)); gp = np.zeros((self.n_pts, 3))
+        W = np.zeros((self.n_obs, 9, 3)) if want_W else None
+        _check(self.L.ba_linearize(self.h, U.ctypes.data, V.ctypes.data,
+                                   W.ctypes.data if want_W else None, gc.ctypes.data, gp.ctypes.data),
+               "ba_linearize")
+        return dict(U=U, V=V, W=W, gc=gc, gp=gp)
+
+    def solve_damped(self, lam):
+        dc = np.zeros((self.n_cams, 9)); dp = np.zeros((self.n_pts, 3))
+        info = _IterInfo()
+        _check(self.L.ba_solve_damped(self.h, float(lam), dc.ctypes.data, dp.ctypes.data,
+                                      ct.byref(info)), "ba_solve_damped")
+        d = info.as_dict()
+        d.update(dc=dc, dp=dp)
+        return d
+
+    def eval_cost(self, cams=None, pts=None):
+        F, r = ct.c_double(0), ct.c_double(0)
+        ca = _Arr(cams, np.float64) if cams is not None else None
+        pa = _Arr(pts, np.float64) if pts is not None else None
+        _check(self.L.ba_eval_cost(self.h, ca.p if ca else None, pa.p if pa else None,
+                                   ct.byref(F), ct.byref(r)), "ba_eval_cost")
+        return F.value, r.value
+
+    def backward(self, dL_dcams, dL_dpts, dL_duv=None, dL_ddepth=None):
+        duv = dL_duv if dL_duv is not None else np.zeros((self.n_obs, 2))
+        dd = dL_ddepth if dL_ddepth is not None else np.zeros(self.n_obs)
+        a, b = _Arr(dL_dcams, np.float64), _Arr(dL_dpts, np.float64)
+        ua, da = _Arr(duv, np.float64), _Arr(dd, np.float64)
+        _check(self.L.ba_backward(self.h, a.p, b.p, ua.p, da.p), "ba_backward")
+        return ua.obj, da.obj
+
+    @property
+    def kernel_launches(self):
+        return int(self.L.ba_kernel_launches(self.h))

@@ -1,0 +1,1116 @@
+// ba_abi.cu -- host side of the C ABI: problem set-up, the LM loop and inspection calls.
+//
+// The host only orders kernels on the problem's stream, reads back a handful
+// of scalars per iteration and keeps the scalar LM bookkeeping (damping and
+// the accept decision of Sec. 3.3).  Every array operation of steps (a)-(e)
+// runs in the kernels of kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ba_b300.h"
+#include "internal.h"
+
+using namespace bab;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+#define CU(expr)                                                                     \
+  do {                                                                               \
+    cudaError_t _e = (expr);                                                         \
+    if (_e != cudaSuccess) {                                                         \
+      set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
+      return _e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA;             \
+    }                                                                                \
+  } while (0)
+
+#define ST(expr)                      \
+  do {                                \
+    ba_status _s = (expr);            \
+    if (_s != BA_OK) return _s;       \
+  } while (0)
+
+}  // namespace
+
+struct ba_problem {
+  ba_options opt{};
+  std::vector<int32_t> fixed_list;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  int C = 0, P = 0, N = 0;
+  bool fp64 = false;
+  Layout L{};
+  ModelParams mp{};
+  std::vector<void*> allocs;
+  int64_t launches = 0;
+
+  // layout arrays (device)
+  int *po_cam = nullptr, *po_pt = nullptr, *po_orig = nullptr, *pt_off = nullptr;
+  double *po_uv64 = nullptr, *po_tau64 = nullptr;
+  void *po_uvw = nullptr, *po_tauw = nullptr, *co_uvw = nullptr, *co_tauw = nullptr;
+  int *co_pt = nullptr, *co_po = nullptr, *po_wrow = nullptr;
+  int *chunk_obs = nullptr, *chunk_cam = nullptr, *cam_chunk = nullptr;
+  TileDesc* descs = nullptr;
+  unsigned char* meta = nullptr;
+  int w_rows = 0;
+  uint8_t* cam_fixed = nullptr;
+  int n_tiles = 0, n_chunks = 0;
+
+  // state, two slots (current / candidate)
+  double* cams64[2] = {nullptr, nullptr};
+  double* pts64[2] = {nullptr, nullptr};
+  double* camw64[2] = {nullptr, nullptr};
+  void* camw[2] = {nullptr, nullptr};
+  void* ptsw[2] = {nullptr, nullptr};
+  uint8_t* bits[2] = {nullptr, nullptr};
+  int cur = 0;
+
+  // extraction
+  uint8_t *alive = nullptr, *valid = nullptr, *obs_act = nullptr, *obs_act_co = nullptr;
+  uint8_t *cam_act = nullptr, *pt_act = nullptr, *cam_flags = nullptr;
+  int *cam_cnt = nullptr, *crank = nullptr, *cam_map = nullptr, *pt_rank = nullptr, *pt_map = nullptr;
+  int *rank_tmp = nullptr, *counts = nullptr;
+  int n_rank_tmp = 0;
+
+  // normal equations and solver
+  void *W = nullptr, *V = nullptr, *gp = nullptr, *Vinv = nullptr, *z0 = nullptr;
+  void *Ug = nullptr, *Sg = nullptr, *cam_part = nullptr, *Ud = nullptr, *Dinv = nullptr;
+  void *bvec = nullptr, *dampc = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
+  void *p0 = nullptr, *p1 = nullptr, *partials = nullptr, *dp = nullptr;
+  double *dots = nullptr, *pred_parts = nullptr, *eval_parts = nullptr;
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  Scalars* sc = nullptr;
+  Scalars* h_sc = nullptr;  // pinned
+  int pcg_grid = 0, eval_grid = 0, pcg_stages = 2;
+  size_t pcg_smem = 0;
+
+  // LM bookkeeping
+  int iter = 0;
+  double lambda = 1e-4, nu = 2.0;
+  bool extracted = false, state_changed = true, linearized = false;
+  bool bits_valid[2] = {false, false};
+  bool cost_valid[2] = {false, false};
+  int n_cam_free = 0, n_pt_act = 0, n_obs_act = 0, n_cam_act = 0;
+  bool solved = false;
+
+  cudaEvent_t ev[8] = {};
+};
+
+namespace {
+
+template <typename X>
+ba_status dalloc(ba_problem* pb, X** p, size_t count) {
+  void* q = nullptr;
+  size_t bytes = std::max<size_t>(sizeof(X) * count, 16);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return BA_ERR_OOM;
+  }
+  pb->allocs.push_back(q);
+  *p = reinterpret_cast<X*>(q);
+  return BA_OK;
+}
+
+ba_status dalloc_bytes(ba_problem* pb, void** p, size_t bytes) {
+  char* q = nullptr;
+  ST(dalloc(pb, &q, bytes));
+  *p = q;
+  return BA_OK;
+}
+
+size_t rsz(const ba_problem* pb) { return pb->fp64 ? sizeof(double) : sizeof(float); }
+
+// Stable counting sort of idx by key (keys in [0, nkeys)).
+void counting_sort(const std::vector<int>& idx_in, const int32_t* key, int nkeys,
+                   std::vector<int>& idx_out) {
+  std::vector<int64_t> cnt((size_t)nkeys + 1, 0);
+  for (int k : idx_in) cnt[key[k] + 1]++;
+  for (int i = 0; i < nkeys; ++i) cnt[i + 1] += cnt[i];
+  idx_out.resize(idx_in.size());
+  for (int k : idx_in) idx_out[cnt[key[k]]++] = k;
+}
+
+bool finite_opts(const ba_options* o) {
+  return std::isfinite(o->cx) && std::isfinite(o->cy) && std::isfinite(o->huber_delta) &&
+         std::isfinite(o->depth_weight) && o->depth_weight >= 0 &&
+         std::isfinite(o->invalid_depth_weight) && o->invalid_depth_weight >= 0 &&
+         std::isfinite(o->min_depth) && std::isfinite(o->lambda0) && o->lambda0 > 0 &&
+         std::isfinite(o->pcg_rel_tol) && o->pcg_rel_tol > 0 && o->pcg_max_iters > 0 &&
+         o->img_w > 0 && o->img_h > 0 && o->min_cam_obs >= 0 && o->min_pt_obs >= 0 &&
+         o->extract_every >= 0 && (o->precision == BA_FP64 || o->precision == BA_FP32);
+}
+
+template <typename T>
+ba_status upload_converted(ba_problem* pb, void** dst, const std::vector<double>& src) {
+  std::vector<T> tmp(src.begin(), src.end());
+  ST(dalloc_bytes(pb, dst, sizeof(T) * tmp.size()));
+  if (!tmp.empty()) CU(cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice));
+  return BA_OK;
+}
+
+ba_status sync(ba_problem* pb) {
+  CU(cudaStreamSynchronize(pb->stream));
+  return BA_OK;
+}
+
+#define LAUNCH(n, expr)      \
+  do {                       \
+    pb->launches += (n);     \
+    CU(expr);                \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// evaluation and extraction
+// ---------------------------------------------------------------------------
+
+// FP64 pass over a state slot: validity bits (if bits != null) and the cost over
+// the current active set (if with_cost) into sc->cost[slot].
+ba_status eval_state(ba_problem* pb, int slot, bool want_bits, bool with_cost) {
+  LAUNCH(1, launch_eval64(pb->L, pb->mp, pb->camw64[slot], pb->pts64[slot],
+                          with_cost ? pb->obs_act : nullptr, want_bits ? pb->bits[slot] : nullptr,
+                          with_cost ? pb->eval_parts : nullptr, pb->eval_grid, pb->stream));
+  if (with_cost) LAUNCH(1, launch_reduce_eval(pb->eval_parts, pb->eval_grid, pb->sc, slot, pb->stream));
+  if (want_bits) pb->bits_valid[slot] = true;
+  if (with_cost) pb->cost_valid[slot] = true;
+  return BA_OK;
+}
+
+ba_status run_extraction(ba_problem* pb, bool drop, int* rounds_out) {
+  ba_problem* p = pb;
+  int slot = p->cur;
+  if (!p->bits_valid[slot]) ST(eval_state(p, slot, true, false));
+  LAUNCH(1, launch_extract_begin(p->L, p->alive, p->bits[slot], p->valid, drop ? 1 : 0, p->stream));
+  LAUNCH(1, launch_fill_u8(p->cam_act, 1, p->C, p->stream));
+  LAUNCH(1, launch_fill_u8(p->pt_act, 1, p->P, p->stream));
+  CU(cudaMemsetAsync(p->cam_cnt, 0, sizeof(int) * std::max(1, p->C), p->stream));
+  int rounds = 0;
+  const int max_rounds = p->C + p->P + 2;
+  for (;;) {
+    ++rounds;
+    CU(cudaMemsetAsync(&p->sc->changed, 0, sizeof(int), p->stream));
+    LAUNCH(1, launch_peel_points(p->L, p->valid, p->cam_act, p->pt_act, p->cam_cnt, p->opt.min_pt_obs,
+                                 p->sc, p->stream));
+    LAUNCH(1, launch_peel_cams(p->L, p->cam_act, p->cam_cnt, p->opt.min_cam_obs, p->sc, p->stream));
+    CU(cudaMemcpyAsync(&p->h_sc->changed, &p->sc->changed, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    ST(sync(p));
+    if (!p->h_sc->changed || rounds >= max_rounds) break;
+  }
+  CU(cudaMemsetAsync(&p->sc->mask_changed, 0, sizeof(int), p->stream));
+  CU(cudaMemsetAsync(&p->sc->n_obs_act, 0, sizeof(int), p->stream));
+  LAUNCH(2, launch_finalize_obs(p->L, p->valid, p->cam_act, p->pt_act, p->obs_act, p->obs_act_co,
+                                p->sc, p->stream));
+  LAUNCH(1, launch_cam_flags(p->L, p->cam_act, p->cam_flags, p->stream));
+  LAUNCH(3, launch_rank(p->cam_flags, p->C, p->crank, p->cam_map, &p->sc->n_cam_free, p->rank_tmp,
+                        p->n_rank_tmp, p->stream));
+  LAUNCH(3, launch_rank(p->pt_act, p->P, p->pt_rank, p->pt_map, &p->sc->n_pt_act, p->rank_tmp,
+                        p->n_rank_tmp, p->stream));
+  CU(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->stream));
+  ST(sync(p));
+  p->n_cam_free = p->h_sc->n_cam_free;
+  p->n_pt_act = p->h_sc->n_pt_act;
+  p->n_obs_act = p->h_sc->n_obs_act;
+  {
+    std::vector<uint8_t> ca((size_t)p->C);
+    if (p->C) CU(cudaMemcpy(ca.data(), p->cam_act, (size_t)p->C, cudaMemcpyDeviceToHost));
+    int n = 0;
+    for (uint8_t v : ca) n += v;
+    p->n_cam_act = n;
+  }
+  if (p->h_sc->mask_changed) {
+    p->cost_valid[0] = p->cost_valid[1] = false;
+    p->linearized = false;
+  }
+  p->extracted = true;
+  if (rounds_out) *rounds_out = rounds;
+  return BA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// steps (a)-(d)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+ba_status linearize_t(ba_problem* pb) {
+  int s = pb->cur;
+  LAUNCH(1, launch_pt_lin<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
+                             (T*)pb->W, (T*)pb->V, (T*)pb->gp, pb->stream));
+  LAUNCH(1, launch_cam_accum<T>(pb->L, pb->mp, 0, (const T*)pb->camw[s], (const T*)pb->ptsw[s],
+                                pb->obs_act_co, pb->cam_act, pb->crank, nullptr, nullptr,
+                                (T*)pb->cam_part, pb->stream));
+  LAUNCH(1, launch_cam_reduce<T>(pb->L, (const T*)pb->cam_part, (T*)pb->Ug, pb->stream));
+  pb->linearized = true;
+  return BA_OK;
+}
+
+template <typename T>
+ba_status schur_t(ba_problem* pb, double lambda) {
+  int s = pb->cur;
+  LAUNCH(1, launch_damp_pts<T>(pb->P, (const T*)pb->V, (const T*)pb->gp, pb->pt_act, lambda, (T*)pb->Vinv,
+                               (T*)pb->z0, pb->err, pb->stream));
+  LAUNCH(1, launch_cam_accum<T>(pb->L, pb->mp, 1, (const T*)pb->camw[s], (const T*)pb->ptsw[s],
+                                pb->obs_act_co, pb->cam_act, pb->crank, (const T*)pb->Vinv,
+                                (const T*)pb->z0, (T*)pb->cam_part, pb->stream));
+  LAUNCH(1, launch_cam_reduce<T>(pb->L, (const T*)pb->cam_part, (T*)pb->Sg, pb->stream));
+  LAUNCH(1, launch_schur_diag<T>(pb->n_cam_free, pb->cam_map, (const T*)pb->Ug, (const T*)pb->Sg, lambda,
+                                 (T*)pb->Ud, (T*)pb->Dinv, (T*)pb->bvec, (T*)pb->dampc, pb->err,
+                                 pb->stream));
+  return BA_OK;
+}
+
+// (d): PCG on the reduced camera system, point back-substitution and the
+// predicted decrease, for the Schur terms prepared at damping lambda.
+template <typename T>
+ba_status pcg_t(ba_problem* pb, double lambda) {
+  int Cf = pb->n_cam_free;
+  PcgArgs<T> a{};
+  a.W = (const T*)pb->W;
+  a.descs = pb->descs;
+  a.meta = pb->meta;
+  a.n_tiles = pb->n_tiles;
+  a.stages = pb->pcg_stages;
+  a.Vinv = (const T*)pb->Vinv;
+  a.crank = pb->crank;
+  a.C = pb->C;
+  a.Ud = (const T*)pb->Ud;
+  a.Dinv = (const T*)pb->Dinv;
+  a.b = (const T*)pb->bvec;
+  a.Cf = Cf;
+  a.n = 9 * Cf;
+  a.x = (T*)pb->x;
+  a.r = (T*)pb->r;
+  a.z = (T*)pb->z;
+  a.p0 = (T*)pb->p0;
+  a.p1 = (T*)pb->p1;
+  a.partials = (T*)pb->partials;
+  a.dots = pb->dots;
+  a.bar = pb->bar;
+  a.err = pb->err;
+  a.sc = pb->sc;
+  a.tol = pb->opt.pcg_rel_tol;
+  a.max_iters = pb->opt.pcg_max_iters;
+  a.timeout_ns = 2000000000LL;
+  a.gp = (const T*)pb->gp;
+  a.V = (const T*)pb->V;
+  a.lambda = lambda;
+  a.dp = (T*)pb->dp;
+  a.pred_parts = pb->pred_parts;
+  size_t smem = pcg_smem_bytes<T>(a.n, pb->C, pb->pcg_stages);
+  CU(cudaMemsetAsync(pb->bar, 0, sizeof(unsigned), pb->stream));
+  LAUNCH(1, launch_pcg<T>(a, pb->pcg_grid, smem, pb->stream));
+  LAUNCH(1, launch_pred_cams<T>(Cf, pb->cam_map, (const T*)pb->x, (const T*)pb->Ug, (const T*)pb->dampc,
+                                lambda, pb->pred_parts, pb->pcg_grid, pb->stream));
+  LAUNCH(1, launch_reduce_pred(pb->pred_parts, pb->pcg_grid + 1, pb->sc, pb->stream));
+  return BA_OK;
+}
+
+template <typename T>
+ba_status candidate_t(ba_problem* pb) {
+  int s = pb->cur, d = 1 - pb->cur;
+  LAUNCH(2, launch_candidate<T>(pb->C, pb->P, pb->crank, (const T*)pb->x, (const T*)pb->dp, pb->cams64[s],
+                                pb->pts64[s], pb->cams64[d], pb->pts64[d], pb->camw64[d],
+                                pb->fp64 ? nullptr : (T*)pb->camw[d], (T*)pb->ptsw[d], pb->stream));
+  pb->bits_valid[d] = false;
+  pb->cost_valid[d] = false;
+  return BA_OK;
+}
+
+ba_status ensure_extracted(ba_problem* pb) {
+  if (!pb->extracted || pb->state_changed) {
+    ST(run_extraction(pb, false, nullptr));
+    pb->state_changed = false;
+  }
+  return BA_OK;
+}
+
+ba_status ensure_linearized(ba_problem* pb) {
+  ST(ensure_extracted(pb));
+  if (!pb->linearized) {
+    if (pb->fp64) ST(linearize_t<double>(pb));
+    else ST(linearize_t<float>(pb));
+  }
+  return BA_OK;
+}
+
+// Damped solve at the current linearisation: (b) Schur terms, (d) PCG + back-substitution.
+ba_status solve_damped(ba_problem* pb, double lambda) {
+  if (pb->fp64) {
+    ST(schur_t<double>(pb, lambda));
+    ST(pcg_t<double>(pb, lambda));
+  } else {
+    ST(schur_t<float>(pb, lambda));
+    ST(pcg_t<float>(pb, lambda));
+  }
+  return BA_OK;
+}
+
+ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
+  const ba_options& o = pb->opt;
+  int k = pb->iter;
+  bool drop = o.extract_every > 0 && o.drop_residual_px > 0 && k > 0 && k % o.extract_every == 0;
+  CU(cudaEventRecord(pb->ev[0], pb->stream));
+  if (!pb->extracted || pb->state_changed || drop) {
+    ST(run_extraction(pb, drop, nullptr));
+    pb->state_changed = false;
+  }
+  if (!pb->cost_valid[pb->cur]) ST(eval_state(pb, pb->cur, false, true));
+  CU(cudaEventRecord(pb->ev[1], pb->stream));
+  if (!pb->linearized) {
+    if (pb->fp64) ST(linearize_t<double>(pb));
+    else ST(linearize_t<float>(pb));
+  }
+  CU(cudaEventRecord(pb->ev[2], pb->stream));
+  double lambda = pb->lambda;
+  CU(cudaMemsetAsync(pb->err, 0, sizeof(int), pb->stream));
+  if (pb->fp64) ST(schur_t<double>(pb, lambda));
+  else ST(schur_t<float>(pb, lambda));
+  CU(cudaEventRecord(pb->ev[3], pb->stream));
+  if (pb->fp64) ST(pcg_t<double>(pb, lambda));
+  else ST(pcg_t<float>(pb, lambda));
+  CU(cudaEventRecord(pb->ev[4], pb->stream));
+  CU(cudaEventRecord(pb->ev[5], pb->stream));
+  if (pb->fp64) ST(candidate_t<double>(pb));
+  else ST(candidate_t<float>(pb));
+  int nxt = 1 - pb->cur;
+  ST(eval_state(pb, nxt, true, true));
+  CU(cudaEventRecord(pb->ev[6], pb->stream));
+  CU(cudaMemcpyAsync(pb->h_sc, pb->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, pb->stream));
+  int h_err = 0;
+  CU(cudaMemcpyAsync(&h_err, pb->err, sizeof(int), cudaMemcpyDeviceToHost, pb->stream));
+  ST(sync(pb));
+  const Scalars& s = *pb->h_sc;
+  double F = s.cost[pb->cur], Fc = s.cost[nxt], pred = s.pred;
+  double gain = (F - Fc) / pred;
+  bool timeout = (h_err & 1) != 0;
+  bool ok = std::isfinite(Fc) && std::isfinite(gain) && pred > 0.0 && !timeout;
+  bool accept = ok && gain > 1e-3;
+  double n_act = s.n_act[pb->cur];
+  if (info) {
+    memset(info, 0, sizeof *info);
+    info->cost = F;
+    info->rmse_px = n_act > 0 ? std::sqrt(s.rmse_sum[pb->cur] / n_act) : 0.0;
+    info->lambda = lambda;
+    info->gain = gain;
+    info->pred_decrease = pred;
+    info->cand_cost = Fc;
+    info->accepted = accept ? 1 : 0;
+    info->pcg_iters = s.pcg_iters;
+    info->pcg_rel_res = s.pcg_rel_res;
+    info->n_cam_act = pb->n_cam_act;
+    info->n_pt_act = pb->n_pt_act;
+    info->n_obs_act = pb->n_obs_act;
+    for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&info->ms[i], pb->ev[i], pb->ev[i + 1]);
+    cudaEventElapsedTime(&info->ms[6], pb->ev[0], pb->ev[6]);
+  }
+  if (accept) {
+    pb->cur = nxt;
+    pb->state_changed = true;
+    pb->linearized = false;
+    double t = 2.0 * gain - 1.0;
+    pb->lambda = lambda * std::max(1.0 / 3.0, 1.0 - t * t * t);
+    pb->nu = 2.0;
+  } else {
+    pb->lambda = lambda * pb->nu;
+    pb->nu *= 2.0;
+  }
+  pb->iter++;
+  pb->solved = true;
+  if (timeout) {
+    set_error("PCG grid barrier timed out");
+    return BA_ERR_TIMEOUT;
+  }
+  if (!ok) return BA_ERR_NONFINITE;
+  if (s.pcg_iters >= o.pcg_max_iters && s.pcg_rel_res > o.pcg_rel_tol) return BA_ERR_NOT_CONVERGED;
+  return BA_OK;
+}
+
+ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, const double* cams,
+                      int64_t n_pts, const double* pts, int64_t n_obs, const int32_t* obs_cam,
+                      const int32_t* obs_pt, const double* obs_uv, const double* depth,
+                      ba_problem* pb) {
+  if (!opts || !finite_opts(opts)) {
+    set_error("invalid options");
+    return BA_ERR_INVALID_ARG;
+  }
+  if (n_cams < 0 || n_pts < 0 || n_obs < 0 || n_cams >= (1LL << 24) || n_pts >= (1LL << 30) ||
+      n_obs >= (1LL << 31) - 1024) {
+    set_error("sizes out of range");
+    return BA_ERR_INVALID_ARG;
+  }
+  if ((n_cams && !cams) || (n_pts && !pts) || (n_obs && (!obs_cam || !obs_pt || !obs_uv || !depth))) {
+    set_error("null input array");
+    return BA_ERR_INVALID_ARG;
+  }
+  pb->opt = *opts;
+  pb->fixed_list.assign(opts->fixed_cams, opts->fixed_cams + (opts->fixed_cams ? opts->n_fixed : 0));
+  pb->opt.fixed_cams = nullptr;
+  pb->stream = (cudaStream_t)stream;
+  pb->fp64 = opts->precision == BA_FP64;
+  pb->lambda = opts->lambda0;
+  const int C = (int)n_cams, P = (int)n_pts, N = (int)n_obs;
+  pb->C = C;
+  pb->P = P;
+  pb->N = N;
+  CU(cudaGetDevice(&pb->device));
+  CU(cudaDeviceGetAttribute(&pb->num_sms, cudaDevAttrMultiProcessorCount, pb->device));
+
+  // ---- host copies of the inputs (host or device pointers)
+  std::vector<double> h_cams((size_t)C * 9), h_pts((size_t)P * 3), h_uv((size_t)N * 2), h_depth(N);
+  std::vector<int32_t> h_oc(N), h_op(N);
+  if (C) CU(cudaMemcpy(h_cams.data(), cams, sizeof(double) * h_cams.size(), cudaMemcpyDefault));
+  if (P) CU(cudaMemcpy(h_pts.data(), pts, sizeof(double) * h_pts.size(), cudaMemcpyDefault));
+  if (N) {
+    CU(cudaMemcpy(h_oc.data(), obs_cam, sizeof(int32_t) * N, cudaMemcpyDefault));
+    CU(cudaMemcpy(h_op.data(), obs_pt, sizeof(int32_t) * N, cudaMemcpyDefault));
+    CU(cudaMemcpy(h_uv.data(), obs_uv, sizeof(double) * 2 * (size_t)N, cudaMemcpyDefault));
+    CU(cudaMemcpy(h_depth.data(), depth, sizeof(double) * N, cudaMemcpyDefault));
+  }
+  // ---- validation
+  for (double v : h_cams)
+    if (!std::isfinite(v)) { set_error("non-finite camera parameter"); return BA_ERR_INVALID_ARG; }
+  for (double v : h_pts)
+    if (!std::isfinite(v)) { set_error("non-finite point"); return BA_ERR_INVALID_ARG; }
+  for (double v : h_uv)
+    if (!std::isfinite(v)) { set_error("non-finite observation"); return BA_ERR_INVALID_ARG; }
+  for (int k = 0; k < N; ++k) {
+    if (h_oc[k] < 0 || h_oc[k] >= C || h_op[k] < 0 || h_op[k] >= P) {
+      set_error("observation %d has an index out of range", k);
+      return BA_ERR_INVALID_ARG;
+    }
+  }
+  std::vector<uint8_t> h_fixed((size_t)C, 0);
+  for (int32_t f : pb->fixed_list) {
+    if (f < 0 || f >= C) { set_error("fixed camera %d out of range", f); return BA_ERR_INVALID_ARG; }
+    h_fixed[f] = 1;
+  }
+  // ---- point order (by point, then camera) and camera order (by camera, then point)
+  std::vector<int> ident(N), tmp, po, co;
+  for (int k = 0; k < N; ++k) ident[k] = k;
+  counting_sort(ident, h_oc.data(), C, tmp);
+  counting_sort(tmp, h_op.data(), P, po);
+  counting_sort(ident, h_op.data(), P, tmp);
+  counting_sort(tmp, h_oc.data(), C, co);
+  for (int i = 1; i < N; ++i)
+    if (h_op[po[i]] == h_op[po[i - 1]] && h_oc[po[i]] == h_oc[po[i - 1]]) {
+      set_error("duplicate observation of point %d in camera %d", h_op[po[i]], h_oc[po[i]]);
+      return BA_ERR_INVALID_ARG;
+    }
+  std::vector<int> pos_in_po(N);
+  for (int i = 0; i < N; ++i) pos_in_po[po[i]] = i;
+  std::vector<int> pt_off((size_t)P + 1, 0), cam_off((size_t)C + 1, 0);
+  for (int k = 0; k < N; ++k) {
+    pt_off[h_op[k] + 1]++;
+    cam_off[h_oc[k] + 1]++;
+  }
+  for (int i = 0; i < P; ++i) pt_off[i + 1] += pt_off[i];
+  for (int i = 0; i < C; ++i) cam_off[i + 1] += cam_off[i];
+  for (int p = 0; p < P; ++p)
+    if (pt_off[p + 1] - pt_off[p] > kTileObs) {
+      set_error("point %d has %d observations (limit %d)", p, pt_off[p + 1] - pt_off[p], kTileObs);
+      return BA_ERR_INVALID_ARG;
+    }
+  // tiles: whole points, at most kTileObs observations and kTileObs points
+  std::vector<int> tile_obs{0}, tile_pt{0};
+  {
+    int tobs = 0, tpts = 0;
+    for (int p = 0; p < P; ++p) {
+      int len = pt_off[p + 1] - pt_off[p];
+      if (tobs + len > kTileObs || tpts + 1 > kTileObs) {
+        tile_obs.push_back(pt_off[p]);
+        tile_pt.push_back(p);
+        tobs = 0;
+        tpts = 0;
+      }
+      tobs += len;
+      tpts += 1;
+    }
+    if (P > 0) {
+      tile_obs.push_back(N);
+      tile_pt.push_back(P);
+    }
+  }
+  pb->n_tiles = (int)tile_obs.size() - 1;
+  // Per tile: W rows padded to a multiple of 4 (16-byte aligned copies) and a
+  // metadata record: camera of each observation, point offsets, the runs of
+  // equal cameras once the tile's observations are sorted by camera
+  // ((camera << 8) | start), and the tile-local positions in that order.
+  std::vector<TileDesc> descs((size_t)pb->n_tiles);
+  std::vector<unsigned char> meta;
+  std::vector<int> po_wrow((size_t)N);
+  {
+    int wrow = 0;
+    for (int t = 0; t < pb->n_tiles; ++t) {
+      int ob = tile_obs[t], oe = tile_obs[t + 1], pbeg = tile_pt[t], pend = tile_pt[t + 1];
+      int nobs = oe - ob, npts = pend - pbeg;
+      std::vector<int> cams_t(nobs), loc(nobs), poff(npts + 1);
+      for (int i = 0; i < nobs; ++i) {
+        cams_t[i] = h_oc[po[ob + i]];
+        loc[i] = i;
+        po_wrow[ob + i] = wrow + i;
+      }
+      for (int j = 0; j <= npts; ++j) poff[j] = pt_off[pbeg + j] - ob;
+      std::stable_sort(loc.begin(), loc.end(), [&](int x, int y) { return cams_t[x] < cams_t[y]; });
+      std::vector<unsigned> runs;
+      std::vector<uint8_t> cperm(nobs);
+      for (int j = 0; j < nobs; ++j) {
+        cperm[j] = (uint8_t)loc[j];
+        if (j == 0 || cams_t[loc[j]] != cams_t[loc[j - 1]])
+          runs.push_back(((unsigned)cams_t[loc[j]] << 8) | (unsigned)j);
+      }
+      TileDesc d{};
+      d.w_row = wrow;
+      d.n_obs = nobs;
+      d.pt_begin = pbeg;
+      d.n_pts = npts;
+      d.meta_off = (int)meta.size();
+      d.n_runs = (int)runs.size();
+      d.obs_begin = ob;
+      descs[t] = d;
+      size_t mb = (size_t)meta_bytes_of(nobs, npts, d.n_runs);
+      meta.resize(meta.size() + mb);
+      build_tile_meta(nobs, npts, d.n_runs, cams_t.data(), poff.data(), runs.data(), cperm.data(),
+                      meta.data() + d.meta_off);
+      wrow += (nobs + 3) & ~3;
+    }
+    pb->w_rows = wrow;
+  }
+  // chunks: pieces of one camera's observations
+  std::vector<int> chunk_obs{0}, chunk_cam, cam_chunk((size_t)C + 1, 0);
+  for (int c = 0; c < C; ++c) {
+    for (int b = cam_off[c]; b < cam_off[c + 1]; b += kChunkObs) {
+      chunk_cam.push_back(c);
+      chunk_obs.push_back(std::min(b + kChunkObs, cam_off[c + 1]));
+    }
+    cam_chunk[c + 1] = (int)chunk_cam.size();
+  }
+  pb->n_chunks = (int)chunk_cam.size();
+
+  // ---- per-observation arrays in both orders
+  std::vector<int> h_po_cam(N), h_po_pt(N), h_co_pt(N), h_co_po(N);
+  std::vector<double> h_po_uv((size_t)2 * N), h_po_tau(N), h_co_uv((size_t)2 * N), h_co_tau(N);
+  auto tau_of = [&](int k) {
+    double d = h_depth[k];
+    return (d > 0.0 && std::isfinite(d)) ? 1.0 / d : 0.0;
+  };
+  for (int i = 0; i < N; ++i) {
+    int k = po[i];
+    h_po_cam[i] = h_oc[k];
+    h_po_pt[i] = h_op[k];
+    h_po_uv[2 * i] = h_uv[2 * (size_t)k];
+    h_po_uv[2 * i + 1] = h_uv[2 * (size_t)k + 1];
+    h_po_tau[i] = tau_of(k);
+    int kc = co[i];
+    h_co_pt[i] = h_op[kc];
+    h_co_po[i] = pos_in_po[kc];
+    h_co_uv[2 * i] = h_uv[2 * (size_t)kc];
+    h_co_uv[2 * i + 1] = h_uv[2 * (size_t)kc + 1];
+    h_co_tau[i] = tau_of(kc);
+  }
+
+  // ---- device buffers
+  auto up_int = [&](int** d, const std::vector<int>& h) -> ba_status {
+    ST(dalloc(pb, d, h.size()));
+    if (!h.empty()) CU(cudaMemcpy(*d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice));
+    return BA_OK;
+  };
+  auto up_dbl = [&](double** d, const std::vector<double>& h) -> ba_status {
+    ST(dalloc(pb, d, h.size()));
+    if (!h.empty()) CU(cudaMemcpy(*d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+    return BA_OK;
+  };
+  ST(up_int(&pb->po_cam, h_po_cam));
+  ST(up_int(&pb->po_pt, h_po_pt));
+  ST(up_int(&pb->po_orig, po));
+  ST(up_int(&pb->pt_off, pt_off));
+  ST(up_int(&pb->co_pt, h_co_pt));
+  ST(up_int(&pb->co_po, h_co_po));
+  ST(up_int(&pb->chunk_obs, chunk_obs));
+  ST(up_int(&pb->chunk_cam, chunk_cam));
+  ST(up_int(&pb->cam_chunk, cam_chunk));
+  ST(up_int(&pb->po_wrow, po_wrow));
+  ST(dalloc(pb, &pb->descs, descs.size()));
+  if (!descs.empty())
+    CU(cudaMemcpy(pb->descs, descs.data(), sizeof(TileDesc) * descs.size(), cudaMemcpyHostToDevice));
+  ST(dalloc(pb, &pb->meta, meta.size()));
+  if (!meta.empty()) CU(cudaMemcpy(pb->meta, meta.data(), meta.size(), cudaMemcpyHostToDevice));
+  ST(up_dbl(&pb->po_uv64, h_po_uv));
+  ST(up_dbl(&pb->po_tau64, h_po_tau));
+  if (pb->fp64) {
+    pb->po_uvw = pb->po_uv64;
+    pb->po_tauw = pb->po_tau64;
+    double *cu = nullptr, *ct = nullptr;
+    ST(up_dbl(&cu, h_co_uv));
+    ST(up_dbl(&ct, h_co_tau));
+    pb->co_uvw = cu;
+    pb->co_tauw = ct;
+  } else {
+    ST(upload_converted<float>(pb, &pb->po_uvw, h_po_uv));
+    ST(upload_converted<float>(pb, &pb->po_tauw, h_po_tau));
+    ST(upload_converted<float>(pb, &pb->co_uvw, h_co_uv));
+    ST(upload_converted<float>(pb, &pb->co_tauw, h_co_tau));
+  }
+  ST(dalloc(pb, &pb->cam_fixed, (size_t)C));
+  if (C) CU(cudaMemcpy(pb->cam_fixed, h_fixed.data(), (size_t)C, cudaMemcpyHostToDevice));
+
+  Layout& L = pb->L;
+  L.C = C;
+  L.P = P;
+  L.N = N;
+  L.n_tiles = pb->n_tiles;
+  L.n_chunks = pb->n_chunks;
+  L.po_cam = pb->po_cam;
+  L.po_pt = pb->po_pt;
+  L.po_orig = pb->po_orig;
+  L.po_uv64 = pb->po_uv64;
+  L.po_tau64 = pb->po_tau64;
+  L.po_uvw = pb->po_uvw;
+  L.po_tauw = pb->po_tauw;
+  L.pt_off = pb->pt_off;
+  L.co_pt = pb->co_pt;
+  L.co_po = pb->co_po;
+  L.co_uvw = pb->co_uvw;
+  L.co_tauw = pb->co_tauw;
+  L.descs = pb->descs;
+  L.po_wrow = pb->po_wrow;
+  L.chunk_obs = pb->chunk_obs;
+  L.chunk_cam = pb->chunk_cam;
+  L.cam_chunk = pb->cam_chunk;
+  L.cam_fixed = pb->cam_fixed;
+
+  ModelParams& mp = pb->mp;
+  mp.cx = opts->cx;
+  mp.cy = opts->cy;
+  mp.huber = opts->huber_delta;
+  mp.sw_valid = std::sqrt(opts->depth_weight);
+  mp.sw_invalid = std::sqrt(opts->invalid_depth_weight);
+  mp.min_depth = opts->min_depth;
+  mp.drop_px = opts->drop_residual_px;
+  mp.img_w = opts->img_w;
+  mp.img_h = opts->img_h;
+
+  const size_t R = rsz(pb);
+  for (int s = 0; s < 2; ++s) {
+    ST(dalloc(pb, &pb->cams64[s], (size_t)C * 9));
+    ST(dalloc(pb, &pb->pts64[s], (size_t)P * 3));
+    ST(dalloc(pb, &pb->camw64[s], (size_t)C * kCamStride));
+    if (pb->fp64) pb->camw[s] = pb->camw64[s];
+    else ST(dalloc_bytes(pb, &pb->camw[s], R * (size_t)C * kCamStride));
+    ST(dalloc_bytes(pb, &pb->ptsw[s], R * (size_t)P * 4));
+    ST(dalloc(pb, &pb->bits[s], (size_t)N));
+  }
+  if (C) CU(cudaMemcpy(pb->cams64[0], h_cams.data(), sizeof(double) * h_cams.size(), cudaMemcpyHostToDevice));
+  if (P) CU(cudaMemcpy(pb->pts64[0], h_pts.data(), sizeof(double) * h_pts.size(), cudaMemcpyHostToDevice));
+  ST(dalloc(pb, &pb->alive, (size_t)N));
+  ST(dalloc(pb, &pb->valid, (size_t)N));
+  ST(dalloc(pb, &pb->obs_act, (size_t)N));
+  ST(dalloc(pb, &pb->obs_act_co, (size_t)N));
+  ST(dalloc(pb, &pb->cam_act, (size_t)C));
+  ST(dalloc(pb, &pb->pt_act, (size_t)P));
+  ST(dalloc(pb, &pb->cam_flags, (size_t)C));
+  ST(dalloc(pb, &pb->cam_cnt, (size_t)C));
+  ST(dalloc(pb, &pb->crank, (size_t)C));
+  ST(dalloc(pb, &pb->cam_map, (size_t)C));
+  ST(dalloc(pb, &pb->pt_rank, (size_t)P));
+  ST(dalloc(pb, &pb->pt_map, (size_t)P));
+  pb->n_rank_tmp = rank_blocks(std::max(C, P)) + 1;
+  ST(dalloc(pb, &pb->rank_tmp, (size_t)pb->n_rank_tmp));
+  ST(dalloc(pb, &pb->counts, 8));
+  if (N) CU(cudaMemset(pb->alive, 1, (size_t)N));
+  if (N) CU(cudaMemset(pb->obs_act, 0, (size_t)N));
+
+  ST(dalloc_bytes(pb, &pb->W, R * 27 * ((size_t)pb->w_rows + 4)));
+  CU(cudaMemset(pb->W, 0, R * 27 * ((size_t)pb->w_rows + 4)));
+  ST(dalloc_bytes(pb, &pb->V, R * 6 * (size_t)P));
+  ST(dalloc_bytes(pb, &pb->gp, R * 3 * (size_t)P));
+  ST(dalloc_bytes(pb, &pb->Vinv, R * 6 * ((size_t)P + 2)));
+  CU(cudaMemset(pb->Vinv, 0, R * 6 * ((size_t)P + 2)));
+  ST(dalloc_bytes(pb, &pb->z0, R * 3 * (size_t)P));
+  ST(dalloc_bytes(pb, &pb->dp, R * 3 * (size_t)P));
+  ST(dalloc_bytes(pb, &pb->Ug, R * 54 * (size_t)C));
+  ST(dalloc_bytes(pb, &pb->Sg, R * 54 * (size_t)C));
+  ST(dalloc_bytes(pb, &pb->cam_part, R * 54 * (size_t)std::max(1, pb->n_chunks)));
+  ST(dalloc_bytes(pb, &pb->Ud, R * 45 * (size_t)C));
+  ST(dalloc_bytes(pb, &pb->Dinv, R * 81 * (size_t)C));
+  ST(dalloc_bytes(pb, &pb->dampc, R * 9 * (size_t)C));
+  for (void** v : {&pb->bvec, &pb->x, &pb->r, &pb->z, &pb->p0, &pb->p1})
+    ST(dalloc_bytes(pb, v, R * 9 * (size_t)C));
+
+  // persistent PCG grid: every block resident (cooperative launch); double-buffered
+  // tile copies when the shared memory allows, else a single buffer
+  int n_max = 9 * C;
+  int dev_smem_optin = 0;
+  CU(cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pb->device));
+  pb->pcg_stages = 2;
+  for (;;) {
+    pb->pcg_smem = pb->fp64 ? pcg_smem_bytes<double>(n_max, C, pb->pcg_stages)
+                            : pcg_smem_bytes<float>(n_max, C, pb->pcg_stages);
+    if (pb->pcg_smem <= (size_t)dev_smem_optin || pb->pcg_stages == 1) break;
+    pb->pcg_stages = 1;
+  }
+  if (pb->pcg_smem > (size_t)dev_smem_optin) {
+    set_error("camera system of %d cameras needs %zu B of shared memory per block (limit %d)", C,
+              pb->pcg_smem, dev_smem_optin);
+    return BA_ERR_INVALID_ARG;
+  }
+  const void* kfn = pb->fp64 ? pcg_kernel_ptr<double>() : pcg_kernel_ptr<float>();
+  CU(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb->pcg_smem));
+  int per_sm = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, pcg_threads(), pb->pcg_smem));
+  if (per_sm < 1) {
+    set_error("PCG kernel cannot be resident");
+    return BA_ERR_INVALID_ARG;
+  }
+  // at most two blocks per SM: fewer blocks means fewer partial vectors to reduce
+  pb->pcg_grid = std::max(1, std::min(std::min(per_sm, 2) * pb->num_sms, std::max(1, pb->n_tiles)));
+  ST(dalloc_bytes(pb, &pb->partials, R * (size_t)pb->pcg_grid * std::max(1, n_max)));
+  ST(dalloc(pb, &pb->dots, (size_t)2 * 4 * pb->pcg_grid));
+  ST(dalloc(pb, &pb->bar, 1));
+  ST(dalloc(pb, &pb->err, 1));
+  ST(dalloc(pb, &pb->pred_parts, (size_t)pb->pcg_grid + 1));
+  pb->eval_grid = std::max(1, std::min(pb->num_sms * 8, (N + kBlock - 1) / kBlock));
+  ST(dalloc(pb, &pb->eval_parts, (size_t)3 * pb->eval_grid));
+  ST(dalloc(pb, &pb->sc, 1));
+  CU(cudaMemset(pb->sc, 0, sizeof(Scalars)));
+  CU(cudaMallocHost(&pb->h_sc, sizeof(Scalars)));
+  memset(pb->h_sc, 0, sizeof(Scalars));
+  for (auto& e : pb->ev) CU(cudaEventCreate(&e));
+
+  // working copies of the initial state
+  if (pb->fp64) {
+    LAUNCH(1, launch_prep_cams<double>(pb->cams64[0], (double*)pb->camw[0], nullptr, C, pb->stream));
+    LAUNCH(1, launch_prep_pts<double>(pb->pts64[0], (double*)pb->ptsw[0], P, pb->stream));
+  } else {
+    LAUNCH(1, launch_prep_cams<float>(pb->cams64[0], (float*)pb->camw[0], pb->camw64[0], C, pb->stream));
+    LAUNCH(1, launch_prep_pts<float>(pb->pts64[0], (float*)pb->ptsw[0], P, pb->stream));
+  }
+  ST(sync(pb));
+  return BA_OK;
+}
+
+void free_problem(ba_problem* pb) {
+  if (!pb) return;
+  if (pb->stream) cudaStreamSynchronize(pb->stream);
+  for (void* p : pb->allocs) cudaFree(p);
+  if (pb->h_sc) cudaFreeHost(pb->h_sc);
+  for (auto& e : pb->ev)
+    if (e) cudaEventDestroy(e);
+  delete pb;
+}
+
+template <typename T>
+ba_status copy_out_linearization(ba_problem* pb, double* U, double* V, double* W, double* gc,
+                                 double* gp) {
+  const int C = pb->C, P = pb->P, N = pb->N;
+  // camera blocks and point blocks are small: bring them to the host and unpack
+  if (U || gc) {
+    std::vector<T> ug((size_t)C * 54);
+    if (C) CU(cudaMemcpy(ug.data(), pb->Ug, sizeof(T) * ug.size(), cudaMemcpyDeviceToHost));
+    std::vector<double> hU((size_t)C * 81, 0.0), hg((size_t)C * 9, 0.0);
+    for (int c = 0; c < C; ++c)
+      for (int i = 0; i < 9; ++i) {
+        for (int j = 0; j < 9; ++j) hU[81 * (size_t)c + 9 * i + j] = ug[54 * (size_t)c + sym9(i, j)];
+        hg[9 * (size_t)c + i] = ug[54 * (size_t)c + 45 + i];
+      }
+    if (U && C) CU(cudaMemcpy(U, hU.data(), sizeof(double) * hU.size(), cudaMemcpyDefault));
+    if (gc && C) CU(cudaMemcpy(gc, hg.data(), sizeof(double) * hg.size(), cudaMemcpyDefault));
+  }
+  if (V || gp) {
+    std::vector<T> hv((size_t)P * 6), hgp((size_t)P * 3);
+    if (P) {
+      CU(cudaMemcpy(hv.data(), pb->V, sizeof(T) * hv.size(), cudaMemcpyDeviceToHost));
+      CU(cudaMemcpy(hgp.data(), pb->gp, sizeof(T) * hgp.size(), cudaMemcpyDeviceToHost));
+    }
+    std::vector<double> oV((size_t)P * 9), og((size_t)P * 3);
+    for (int p = 0; p < P; ++p) {
+      for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) oV[9 * (size_t)p + 3 * i + j] = hv[6 * (size_t)p + sym3(i, j)];
+        og[3 * (size_t)p + i] = hgp[3 * (size_t)p + i];
+      }
+    }
+    if (V && P) CU(cudaMemcpy(V, oV.data(), sizeof(double) * oV.size(), cudaMemcpyDefault));
+    if (gp && P) CU(cudaMemcpy(gp, og.data(), sizeof(double) * og.size(), cudaMemcpyDefault));
+  }
+  if (W && N) {
+    double* tmp = nullptr;
+    CU(cudaMalloc(&tmp, sizeof(double) * 27 * (size_t)N));
+    pb->launches += 1;
+    cudaError_t e = launch_permute_rows<T>(pb->po_orig, pb->po_wrow, (const T*)pb->W, tmp, N, 27, pb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pb->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(W, tmp, sizeof(double) * 27 * (size_t)N, cudaMemcpyDefault);
+    cudaFree(tmp);
+    CU(e);
+  }
+  return BA_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+void ba_default_options(ba_options* o) {
+  static const int32_t kGauge[1] = {0};
+  memset(o, 0, sizeof *o);
+  o->precision = BA_FP32;
+  o->img_w = 640;
+  o->img_h = 480;
+  o->cx = 320.0;
+  o->cy = 240.0;
+  o->huber_delta = 1.0;
+  o->depth_weight = 1.0;
+  o->invalid_depth_weight = 0.0;
+  o->min_depth = 0.1;
+  o->extract_every = 0;
+  o->drop_residual_px = 0.0;
+  o->min_cam_obs = 1;
+  o->min_pt_obs = 1;
+  o->lambda0 = 1e-4;
+  o->pcg_rel_tol = 1e-6;
+  o->pcg_max_iters = 500;
+  o->fixed_cams = kGauge;
+  o->n_fixed = 1;
+}
+
+ba_status ba_create(const ba_options* opts, void* stream, int64_t n_cams, const double* cams,
+                    int64_t n_pts, const double* pts, int64_t n_obs, const int32_t* obs_cam,
+                    const int32_t* obs_pt, const double* obs_uv, const double* depth,
+                    ba_problem** out) {
+  if (!out) {
+    set_error("null output handle");
+    return BA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  ba_problem* pb = new ba_problem();
+  ba_status s = create_impl(opts, stream, n_cams, cams, n_pts, pts, n_obs, obs_cam, obs_pt, obs_uv,
+                            depth, pb);
+  if (s != BA_OK) {
+    free_problem(pb);
+    return s;
+  }
+  *out = pb;
+  return BA_OK;
+}
+
+ba_status ba_lm_step(ba_problem* pb, ba_iter_info* info) {
+  if (!pb) return BA_ERR_INVALID_ARG;
+  return lm_step(pb, info);
+}
+
+ba_status ba_solve(ba_problem* pb, int max_iters, ba_iter_info* log, int* n_done) {
+  if (!pb || max_iters < 0) return BA_ERR_INVALID_ARG;
+  ba_status worst = BA_OK;
+  int i = 0;
+  for (; i < max_iters; ++i) {
+    ba_status s = lm_step(pb, log ? log + i : nullptr);
+    if (s == BA_ERR_NOT_CONVERGED || s == BA_ERR_NONFINITE) {
+      worst = s;
+      continue;
+    }
+    if (s != BA_OK) {
+      if (n_done) *n_done = i;
+      return s;
+    }
+  }
+  if (n_done) *n_done = i;
+  return worst == BA_ERR_NONFINITE ? BA_OK : worst;
+}
+
+ba_status ba_get_params(ba_problem* pb, double* cams, double* pts) {
+  if (!pb) return BA_ERR_INVALID_ARG;
+  ST(sync(pb));
+  if (cams && pb->C) CU(cudaMemcpy(cams, pb->cams64[pb->cur], sizeof(double) * 9 * (size_t)pb->C, cudaMemcpyDefault));
+  if (pts && pb->P) CU(cudaMemcpy(pts, pb->pts64[pb->cur], sizeof(double) * 3 * (size_t)pb->P, cudaMemcpyDefault));
+  return BA_OK;
+}
+
+ba_status ba_set_params(ba_problem* pb, const double* cams, const double* pts) {
+  if (!pb || (!cams && pb->C) || (!pts && pb->P)) return BA_ERR_INVALID_ARG;
+  ST(sync(pb));
+  std::vector<double> hc((size_t)pb->C * 9), hp((size_t)pb->P * 3);
+  if (pb->C) CU(cudaMemcpy(hc.data(), cams, sizeof(double) * hc.size(), cudaMemcpyDefault));
+  if (pb->P) CU(cudaMemcpy(hp.data(), pts, sizeof(double) * hp.size(), cudaMemcpyDefault));
+  for (double v : hc)
+    if (!std::isfinite(v)) return BA_ERR_INVALID_ARG;
+  for (double v : hp)
+    if (!std::isfinite(v)) return BA_ERR_INVALID_ARG;
+  int s = pb->cur;
+  if (pb->C) CU(cudaMemcpy(pb->cams64[s], hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice));
+  if (pb->P) CU(cudaMemcpy(pb->pts64[s], hp.data(), sizeof(double) * hp.size(), cudaMemcpyHostToDevice));
+  if (pb->fp64) {
+    LAUNCH(1, launch_prep_cams<double>(pb->cams64[s], (double*)pb->camw[s], nullptr, pb->C, pb->stream));
+    LAUNCH(1, launch_prep_pts<double>(pb->pts64[s], (double*)pb->ptsw[s], pb->P, pb->stream));
+  } else {
+    LAUNCH(1, launch_prep_cams<float>(pb->cams64[s], (float*)pb->camw[s], pb->camw64[s], pb->C, pb->stream));
+    LAUNCH(1, launch_prep_pts<float>(pb->pts64[s], (float*)pb->ptsw[s], pb->P, pb->stream));
+  }
+  pb->bits_valid[s] = pb->cost_valid[s] = false;
+  pb->state_changed = true;
+  pb->linearized = false;
+  ST(sync(pb));
+  return BA_OK;
+}
+
+ba_status ba_get_active(ba_problem* pb, uint8_t* cam_mask, uint8_t* pt_mask, uint8_t* obs_mask,
+                        int32_t* cam_rank, int32_t* pt_rank) {
+  if (!pb) return BA_ERR_INVALID_ARG;
+  if (!pb->extracted) {
+    set_error("no extraction has run yet");
+    return BA_ERR_STATE;
+  }
+  ST(sync(pb));
+  if (cam_mask && pb->C) CU(cudaMemcpy(cam_mask, pb->cam_act, (size_t)pb->C, cudaMemcpyDefault));
+  if (pt_mask && pb->P) CU(cudaMemcpy(pt_mask, pb->pt_act, (size_t)pb->P, cudaMemcpyDefault));
+  if (cam_rank && pb->C) CU(cudaMemcpy(cam_rank, pb->crank, sizeof(int) * (size_t)pb->C, cudaMemcpyDefault));
+  if (pt_rank && pb->P) CU(cudaMemcpy(pt_rank, pb->pt_rank, sizeof(int) * (size_t)pb->P, cudaMemcpyDefault));
+  if (obs_mask && pb->N) {
+    uint8_t* tmp = nullptr;
+    CU(cudaMalloc(&tmp, (size_t)pb->N));
+    pb->launches += 1;
+    cudaError_t e = launch_permute_u8(pb->po_orig, pb->obs_act, tmp, pb->N, pb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pb->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(obs_mask, tmp, (size_t)pb->N, cudaMemcpyDefault);
+    cudaFree(tmp);
+    CU(e);
+  }
+  return BA_OK;
+}
+
+ba_status ba_extract(ba_problem* pb, int drop, int* n_rounds) {
+  if (!pb) return BA_ERR_INVALID_ARG;
+  ST(run_extraction(pb, drop != 0, n_rounds));
+  pb->state_changed = false;
+  return BA_OK;
+}
+
+ba_status ba_linearize(ba_problem* pb, double* U, double* V, double* W, double* gc, double* gp) {
+  if (!pb) return BA_ERR_INVALID_ARG;
+  ST(ensure_linearized(pb));
+  ST(sync(pb));
+  if (pb->fp64) return copy_out_linearization<double>(pb, U, V, W, gc, gp);
+  return copy_out_linearization<float>(pb, U, V, W, gc, gp);
+}
+
+ba_status ba_solve_damped(ba_problem* pb, double lambda, double* dc, double* dp,
+                          ba_iter_info* info) {
+  if (!pb || !(lambda >= 0.0) || !std::isfinite(lambda)) return BA_ERR_INVALID_ARG;
+  ST(ensure_linearized(pb));
+  CU(cudaMemsetAsync(pb->err, 0, sizeof(int), pb->stream));
+  ST(solve_damped(pb, lambda));
+  CU(cudaMemcpyAsync(pb->h_sc, pb->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, pb->stream));
+  int h_err = 0;
+  CU(cudaMemcpyAsync(&h_err, pb->err, sizeof(int), cudaMemcpyDeviceToHost, pb->stream));
+  ST(sync(pb));
+  if (dc && pb->C) {
+    double* tmp = nullptr;
+    CU(cudaMalloc(&tmp, sizeof(double) * 9 * (size_t)pb->C));
+    pb->launches += 1;
+    cudaError_t e = pb->fp64 ? launch_scatter_cams<double>(pb->C, pb->crank, (const double*)pb->x, tmp, pb->stream)
+                             : launch_scatter_cams<float>(pb->C, pb->crank, (const float*)pb->x, tmp, pb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pb->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, tmp, sizeof(double) * 9 * (size_t)pb->C, cudaMemcpyDefault);
+    cudaFree(tmp);
+    CU(e);
+  }
+  if (dp && pb->P) {
+    double* tmp = nullptr;
+    CU(cudaMalloc(&tmp, sizeof(double) * 3 * (size_t)pb->P));
+    pb->launches += 1;
+    cudaError_t e = pb->fp64 ? launch_to_double<double>((const double*)pb->dp, tmp, 3LL * pb->P, pb->stream)
+                             : launch_to_double<float>((const float*)pb->dp, tmp, 3LL * pb->P, pb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pb->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(dp, tmp, sizeof(double) * 3 * (size_t)pb->P, cudaMemcpyDefault);
+    cudaFree(tmp);
+    CU(e);
+  }
+  if (info) {
+    memset(info, 0, sizeof *info);
+    info->lambda = lambda;
+    info->pcg_iters = pb->h_sc->pcg_iters;
+    info->pcg_rel_res = pb->h_sc->pcg_rel_res;
+    info->pred_decrease = pb->h_sc->pred;
+    info->n_cam_act = pb->n_cam_act;
+    info->n_pt_act = pb->n_pt_act;
+    info->n_obs_act = pb->n_obs_act;
+  }
+  if (h_err & 1) {
+    set_error("PCG grid barrier timed out");
+    return BA_ERR_TIMEOUT;
+  }
+  return BA_OK;
+}
+
+ba_status ba_eval_cost(ba_problem* pb, const double* cams, const double* pts, double* cost,
+                       double* rmse_px) {
+  if (!pb) return BA_ERR_INVALID_ARG;
+  ST(ensure_extracted(pb));
+  int slot = pb->cur;
+  if (cams || pts) {
+    // evaluate in the spare slot without disturbing the solver state
+    slot = 1 - pb->cur;
+    if (cams && pb->C) CU(cudaMemcpyAsync(pb->cams64[slot], cams, sizeof(double) * 9 * (size_t)pb->C, cudaMemcpyDefault, pb->stream));
+    else if (pb->C) CU(cudaMemcpyAsync(pb->cams64[slot], pb->cams64[pb->cur], sizeof(double) * 9 * (size_t)pb->C, cudaMemcpyDeviceToDevice, pb->stream));
+    if (pts && pb->P) CU(cudaMemcpyAsync(pb->pts64[slot], pts, sizeof(double) * 3 * (size_t)pb->P, cudaMemcpyDefault, pb->stream));
+    else if (pb->P) CU(cudaMemcpyAsync(pb->pts64[slot], pb->pts64[pb->cur], sizeof(double) * 3 * (size_t)pb->P, cudaMemcpyDeviceToDevice, pb->stream));
+    LAUNCH(1, launch_prep_cams<double>(pb->cams64[slot], pb->camw64[slot], nullptr, pb->C, pb->stream));
+    pb->bits_valid[slot] = false;
+  }
+  ST(eval_state(pb, slot, false, true));
+  if (slot != pb->cur) pb->cost_valid[slot] = false;
+  CU(cudaMemcpyAsync(pb->h_sc, pb->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, pb->stream));
+  ST(sync(pb));
+  if (cost) *cost = pb->h_sc->cost[slot];
+  if (rmse_px) *rmse_px = pb->h_sc->n_act[slot] > 0 ? std::sqrt(pb->h_sc->rmse_sum[slot] / pb->h_sc->n_act[slot]) : 0.0;
+  return BA_OK;
+}
+
+ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_dpts,
+                      double* dL_duv, double* dL_ddepth) {
+  (void)dL_dcams;
+  (void)dL_dpts;
+  (void)dL_duv;
+  (void)dL_ddepth;
+  if (!pb) return BA_ERR_INVALID_ARG;
+  set_error("ba_backward: not available in this build");
+  return BA_ERR_STATE;
+}
+
+int64_t ba_kernel_launches(const ba_problem* pb) { return pb ? pb->launches : 0; }
+
+void ba_destroy(ba_problem* pb) { free_problem(pb); }
+
+const char* ba_status_string(ba_status s) {
+  switch (s) {
+    case BA_OK: return "ok";
+    case BA_ERR_INVALID_ARG: return "invalid argument";
+    case BA_ERR_CUDA: return "CUDA error";
+    case BA_ERR_OOM: return "out of device memory";
+    case BA_ERR_NOT_CONVERGED: return "PCG did not converge";
+    case BA_ERR_NONFINITE: return "non-finite cost or step";
+    case BA_ERR_STATE: return "call out of order";
+    case BA_ERR_TIMEOUT: return "grid barrier timeout";
+  }
+  return "unknown status";
+}
+
+const char* ba_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

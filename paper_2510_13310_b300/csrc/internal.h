@@ -1,0 +1,155 @@
+// internal.h -- device views and kernel launchers shared by the library's host code.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace bab {
+
+// One tile of whole points in point order.  W rows of the tile start at w_row
+// (a multiple of 4, so every tile starts on a 16-byte boundary); its static
+// metadata (camera of each observation, point offsets, camera runs, positions in
+// camera order) is a 16-byte aligned record at meta_off.
+struct TileDesc {
+  int w_row, n_obs, pt_begin, n_pts;
+  int meta_off, n_runs, obs_begin, pad;
+};
+
+// Immutable observation layout built by ba_create.  "po" = point order (sorted by
+// point, then camera), "co" = camera order (sorted by camera, then point).
+struct Layout {
+  int C, P, N;
+  int n_tiles, n_chunks;
+  const int* po_cam;       // [N]
+  const int* po_pt;        // [N]
+  const int* po_orig;      // [N] input index
+  const double* po_uv64;   // [N][2]
+  const double* po_tau64;  // [N] inverse-depth target m/d (0 without prior)
+  const void* po_uvw;      // [N][2] working precision
+  const void* po_tauw;     // [N]
+  const int* pt_off;       // [P+1]
+  const int* co_pt;        // [N]
+  const int* co_po;        // [N] point-order index of each camera-order observation
+  const void* co_uvw;      // [N][2]
+  const void* co_tauw;     // [N]
+  const TileDesc* descs;   // [n_tiles]
+  const int* po_wrow;      // [N] W row of each point-order observation
+  const int* chunk_obs;    // [n_chunks+1]
+  const int* chunk_cam;    // [n_chunks]
+  const int* cam_chunk;    // [C+1] chunk range of each camera
+  const uint8_t* cam_fixed;  // [C]
+};
+
+struct ModelParams {
+  double cx, cy, huber, sw_valid, sw_invalid, min_depth, drop_px;
+  int img_w, img_h;
+};
+
+template <typename T>
+struct PcgArgs {
+  const T* W;                   // tiled W rows
+  const TileDesc* descs;
+  const unsigned char* meta;    // tile metadata records
+  int n_tiles;
+  int stages;                   // 2: double-buffered tile copies, 1: single buffer
+  const T* Vinv;                // [P+2][6]
+  const int* crank;
+  int C;
+  const T* Ud;
+  const T* Dinv;
+  const T* b;
+  int Cf, n;
+  T *x, *r, *z, *p0, *p1;
+  T* partials;
+  double* dots;                 // [2][G][4]
+  unsigned* bar;
+  int* err;
+  Scalars* sc;
+  double tol;
+  int max_iters;
+  long long timeout_ns;
+  // back-substitution
+  const T* gp;
+  const T* V;
+  double lambda;
+  T* dp;
+  double* pred_parts;           // [G] (+1 slot for the camera part)
+};
+
+// ---- launchers (return cudaGetLastError of the launch) ----
+template <typename T>
+cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prep_pts(const double* pts64, T* ptsw, int P, cudaStream_t s);
+
+cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* camw64,
+                          const double* pts64, const uint8_t* act, uint8_t* bits,
+                          double* partials, int grid, cudaStream_t s);
+cudaError_t launch_reduce_eval(const double* partials, int nparts, Scalars* sc, int slot,
+                               cudaStream_t s);
+
+cudaError_t launch_extract_begin(const Layout& L, uint8_t* alive, const uint8_t* bits,
+                                 uint8_t* valid, int drop, cudaStream_t s);
+cudaError_t launch_fill_u8(uint8_t* p, uint8_t v, int n, cudaStream_t s);
+cudaError_t launch_peel_points(const Layout& L, const uint8_t* valid, const uint8_t* cam_act,
+                               uint8_t* pt_act, int* cam_cnt, int min_pt, Scalars* sc,
+                               cudaStream_t s);
+cudaError_t launch_peel_cams(const Layout& L, uint8_t* cam_act, int* cam_cnt, int min_cam,
+                             Scalars* sc, cudaStream_t s);
+cudaError_t launch_finalize_obs(const Layout& L, const uint8_t* valid, const uint8_t* cam_act,
+                                const uint8_t* pt_act, uint8_t* obs_act, uint8_t* obs_act_co,
+                                Scalars* sc, cudaStream_t s);
+cudaError_t launch_cam_flags(const Layout& L, const uint8_t* cam_act, uint8_t* flags,
+                             cudaStream_t s);
+// ranks of nonzero flags: rank[i] (-1 if zero), map[rank] = i, *count
+cudaError_t launch_rank(const uint8_t* flags, int n, int* rank, int* map, int* count,
+                        int* block_tmp, int n_block_tmp, cudaStream_t s);
+int rank_blocks(int n);
+
+template <typename T>
+cudaError_t launch_pt_lin(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
+                          const uint8_t* obs_act, T* W, T* V, T* gp, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cam_accum(const Layout& L, const ModelParams& mp, int mode, const T* camw,
+                             const T* ptsw, const uint8_t* act_co, const uint8_t* cam_act,
+                             const int* crank, const T* Vinv, const T* z0, T* partials,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_cam_reduce(const Layout& L, const T* partials, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_act, double lambda,
+                            T* Vinv, T* z0, int* err, cudaStream_t s);
+template <typename T>
+cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
+                              T* Ud, T* Dinv, T* b, T* dampc, int* err, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pcg(const PcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
+template <typename T>
+size_t pcg_smem_bytes(int n, int C, int stages);
+template <typename T>
+const void* pcg_kernel_ptr();
+int pcg_threads();
+int meta_bytes_of(int n_obs, int n_pts, int n_runs);
+void build_tile_meta(int n_obs, int n_pts, int n_runs, const int* cams, const int* poff,
+                     const unsigned* runs, const uint8_t* cperm, unsigned char* out);
+template <typename T>
+cudaError_t launch_pred_cams(int Cf, const int* cam_map, const T* x, const T* Ug, const T* dampc,
+                             double lambda, double* pred_parts, int offset, cudaStream_t s);
+cudaError_t launch_reduce_pred(const double* parts, int n, Scalars* sc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_candidate(int C, int P, const int* crank, const T* x, const T* dp,
+                             const double* cams_src, const double* pts_src, double* cams_dst,
+                             double* pts_dst, double* camw64_dst, T* camw_dst, T* ptsw_dst,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter_cams(int C, const int* crank, const T* x, double* dc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t s);
+cudaError_t launch_permute_u8(const int* orig, const uint8_t* src, uint8_t* dst, int N,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, double* dst, int N,
+                                int width, cudaStream_t s);
+
+}  // namespace bab

@@ -1,0 +1,938 @@
+// kernels.cu -- sm_103a kernels of one LM bundle-adjustment iteration.
+//
+// Observation streams are kept in two sorted layouts built once at creation:
+// point order (tiles of whole points) for everything reduced per point and for
+// the Schur matvec, camera order (chunks inside one camera) for everything
+// reduced per camera.  No kernel uses global floating-point atomics: camera
+// sums go through fixed-order chunk partials, point sums through per-tile
+// shared memory.
+#include "internal.h"
+#include "model.cuh"
+
+namespace bab {
+
+// ---------------------------------------------------------------------------
+// working copies of the state
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_prep_cams(const double* __restrict__ cams64, T* __restrict__ camw,
+                            double* __restrict__ camw64, int C) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const double* cp = cams64 + 9 * (size_t)c;
+  double R[9];
+  double w[3] = {cp[0], cp[1], cp[2]};
+  rotvec_matrix(w, R);
+  double rec[kCamStride];
+  for (int i = 0; i < 9; ++i) rec[i] = R[i];
+  for (int i = 0; i < 6; ++i) rec[9 + i] = cp[3 + i];
+  rec[15] = 0.0;
+  for (int i = 0; i < kCamStride; ++i) camw[kCamStride * (size_t)c + i] = (T)rec[i];
+  if (camw64)
+    for (int i = 0; i < kCamStride; ++i) camw64[kCamStride * (size_t)c + i] = rec[i];
+}
+
+template <typename T>
+cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s) {
+  if (C > 0) k_prep_cams<T><<<(C + 127) / 128, 128, 0, s>>>(cams64, camw, camw64, C);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_prep_pts(const double* __restrict__ pts64, T* __restrict__ ptsw, int P) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  using V4 = typename Vec4<T>::type;
+  V4 v;
+  v.x = (T)pts64[3 * (size_t)p];
+  v.y = (T)pts64[3 * (size_t)p + 1];
+  v.z = (T)pts64[3 * (size_t)p + 2];
+  v.w = T(0);
+  reinterpret_cast<V4*>(ptsw)[p] = v;
+}
+
+template <typename T>
+cudaError_t launch_prep_pts(const double* pts64, T* ptsw, int P, cudaStream_t s) {
+  if (P > 0) k_prep_pts<T><<<(P + 255) / 256, 256, 0, s>>>(pts64, ptsw, P);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 evaluation: cost over the active set and validity bits of a state
+// (Eq. BA objective with depth; Sec. 4.2 step 1 validity)
+// ---------------------------------------------------------------------------
+
+// bits: 1 = geometrically valid (z > min_depth, pixel inside the image),
+//       2 = valid and |r_uv| above the residual-drop threshold.
+__global__ void k_eval64(Layout L, ModelParams mp, const double* __restrict__ camw64,
+                         const double* __restrict__ pts64, const uint8_t* __restrict__ act,
+                         uint8_t* __restrict__ bits, double* __restrict__ partials) {
+  __shared__ double red[32];
+  double acc_cost = 0.0, acc_e2 = 0.0, acc_n = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += gridDim.x * blockDim.x) {
+    int c = L.po_cam[k], p = L.po_pt[k];
+    const double* X = pts64 + 3 * (size_t)p;
+    double tau = L.po_tau64[k];
+    double sw = tau > 0.0 ? mp.sw_valid : mp.sw_invalid;
+    Eval64 e = eval_obs64(camw64 + kCamStride * (size_t)c, X[0], X[1], X[2], L.po_uv64[2 * (size_t)k],
+                          L.po_uv64[2 * (size_t)k + 1], tau, sw, mp.cx, mp.cy);
+    double e2 = e.r0 * e.r0 + e.r1 * e.r1;
+    if (bits) {
+      int ok = e.z > mp.min_depth && e.uh >= 0.0 && e.uh < (double)mp.img_w && e.vh >= 0.0 &&
+               e.vh < (double)mp.img_h;
+      int b = ok ? 1 : 0;
+      if (ok && mp.drop_px > 0.0 && sqrt(e2) > mp.drop_px) b |= 2;
+      bits[k] = (uint8_t)b;
+    }
+    if (act && act[k]) {
+      acc_cost += huber_loss(e2 + e.r2 * e.r2, mp.huber);
+      acc_e2 += e2;
+      acc_n += 1.0;
+    }
+  }
+  if (!partials) return;
+  double s0 = block_sum(acc_cost, red);
+  double s1 = block_sum(acc_e2, red);
+  double s2 = block_sum(acc_n, red);
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x] = s0;
+    partials[3 * blockIdx.x + 1] = s1;
+    partials[3 * blockIdx.x + 2] = s2;
+  }
+}
+
+cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* camw64,
+                          const double* pts64, const uint8_t* act, uint8_t* bits,
+                          double* partials, int grid, cudaStream_t s) {
+  k_eval64<<<grid, kBlock, 0, s>>>(L, mp, camw64, pts64, act, bits, partials);
+  return cudaGetLastError();
+}
+
+__global__ void k_reduce_eval(const double* __restrict__ partials, int n, Scalars* sc, int slot) {
+  __shared__ double red[32];
+  double a = 0, b = 0, c = 0;
+  // fixed assignment of partials to threads and a fixed tree: deterministic
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a += partials[3 * i];
+    b += partials[3 * i + 1];
+    c += partials[3 * i + 2];
+  }
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  c = block_sum(c, red);
+  if (threadIdx.x == 0) {
+    sc->cost[slot] = 0.5 * a;
+    sc->rmse_sum[slot] = b;
+    sc->n_act[slot] = c;
+  }
+}
+
+cudaError_t launch_reduce_eval(const double* partials, int nparts, Scalars* sc, int slot,
+                               cudaStream_t s) {
+  k_reduce_eval<<<1, 256, 0, s>>>(partials, nparts, sc, slot);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// dynamic parameter extraction (Sec. 4.2 steps 1-2)
+// ---------------------------------------------------------------------------
+
+__global__ void k_extract_begin(int N, uint8_t* __restrict__ alive, const uint8_t* __restrict__ bits,
+                                uint8_t* __restrict__ valid, int drop) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    uint8_t b = bits[k];
+    uint8_t a = alive[k];
+    if (drop && (b & 3) == 3) a = 0;  // sticky residual drop of a valid observation
+    alive[k] = a;
+    valid[k] = (uint8_t)(a && (b & 1));
+  }
+}
+
+cudaError_t launch_extract_begin(const Layout& L, uint8_t* alive, const uint8_t* bits,
+                                 uint8_t* valid, int drop, cudaStream_t s) {
+  if (L.N > 0) k_extract_begin<<<(L.N + 255) / 256, 256, 0, s>>>(L.N, alive, bits, valid, drop);
+  return cudaGetLastError();
+}
+
+__global__ void k_fill_u8(uint8_t* p, uint8_t v, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+cudaError_t launch_fill_u8(uint8_t* p, uint8_t v, int n, cudaStream_t s) {
+  if (n > 0) k_fill_u8<<<(n + 255) / 256, 256, 0, s>>>(p, v, n);
+  return cudaGetLastError();
+}
+
+// One peeling round over points: a point stays active while it keeps >= min_pt
+// valid observations in active cameras; the surviving observations are counted
+// per camera for the camera round.
+__global__ void k_peel_points(Layout L, const uint8_t* __restrict__ valid,
+                              const uint8_t* __restrict__ cam_act, uint8_t* __restrict__ pt_act,
+                              int* __restrict__ cam_cnt, int min_pt, Scalars* sc) {
+  extern __shared__ int s_cnt[];
+  bool use_smem = L.C <= 8192;
+  if (use_smem) {
+    for (int c = threadIdx.x; c < L.C; c += blockDim.x) s_cnt[c] = 0;
+    __syncthreads();
+  }
+  int changed = 0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < L.P; p += gridDim.x * blockDim.x) {
+    int k0 = L.pt_off[p], k1 = L.pt_off[p + 1];
+    int cnt = 0;
+    for (int k = k0; k < k1; ++k) cnt += (valid[k] && cam_act[L.po_cam[k]]) ? 1 : 0;
+    uint8_t old = pt_act[p];
+    uint8_t now = (uint8_t)(old && cnt >= min_pt);
+    if (now != old) {
+      pt_act[p] = now;
+      changed = 1;
+    }
+    if (now)
+      for (int k = k0; k < k1; ++k)
+        if (valid[k] && cam_act[L.po_cam[k]]) {
+          if (use_smem) atomicAdd(&s_cnt[L.po_cam[k]], 1);
+          else atomicAdd(&cam_cnt[L.po_cam[k]], 1);
+        }
+  }
+  if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&sc->changed, 1);
+  if (use_smem) {
+    for (int c = threadIdx.x; c < L.C; c += blockDim.x)
+      if (s_cnt[c]) atomicAdd(&cam_cnt[c], s_cnt[c]);
+  }
+}
+
+cudaError_t launch_peel_points(const Layout& L, const uint8_t* valid, const uint8_t* cam_act,
+                               uint8_t* pt_act, int* cam_cnt, int min_pt, Scalars* sc,
+                               cudaStream_t s) {
+  if (L.P == 0) return cudaSuccess;
+  size_t smem = L.C <= 8192 ? sizeof(int) * (size_t)L.C : 0;
+  int grid = (L.P + 255) / 256;
+  if (grid > 2048) grid = 2048;
+  k_peel_points<<<grid, 256, smem, s>>>(L, valid, cam_act, pt_act, cam_cnt, min_pt, sc);
+  return cudaGetLastError();
+}
+
+__global__ void k_peel_cams(int C, const uint8_t* __restrict__ fixed, uint8_t* __restrict__ cam_act,
+                            int* __restrict__ cam_cnt, int min_cam, Scalars* sc) {
+  int changed = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    uint8_t old = cam_act[c];
+    uint8_t now = (uint8_t)(fixed[c] || (old && cam_cnt[c] >= min_cam));
+    if (now != old) {
+      cam_act[c] = now;
+      changed = 1;
+    }
+    cam_cnt[c] = 0;
+  }
+  if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&sc->changed, 1);
+}
+
+cudaError_t launch_peel_cams(const Layout& L, uint8_t* cam_act, int* cam_cnt, int min_cam,
+                             Scalars* sc, cudaStream_t s) {
+  if (L.C > 0) k_peel_cams<<<(L.C + 255) / 256, 256, 0, s>>>(L.C, L.cam_fixed, cam_act, cam_cnt, min_cam, sc);
+  return cudaGetLastError();
+}
+
+__global__ void k_finalize_obs(Layout L, const uint8_t* __restrict__ valid,
+                               const uint8_t* __restrict__ cam_act, const uint8_t* __restrict__ pt_act,
+                               uint8_t* __restrict__ obs_act, Scalars* sc) {
+  int cnt = 0, changed = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += gridDim.x * blockDim.x) {
+    uint8_t a = (uint8_t)(valid[k] && cam_act[L.po_cam[k]] && pt_act[L.po_pt[k]]);
+    if (a != obs_act[k]) changed = 1;
+    obs_act[k] = a;
+    cnt += a;
+  }
+  __shared__ int red[32];
+  int tot = block_sum(cnt, red);
+  if (threadIdx.x == 0 && tot) atomicAdd(&sc->n_obs_act, tot);
+  if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&sc->mask_changed, 1);
+}
+
+__global__ void k_gather_co(int N, const int* __restrict__ co_po, const uint8_t* __restrict__ obs_act,
+                            uint8_t* __restrict__ obs_act_co) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x)
+    obs_act_co[j] = obs_act[co_po[j]];
+}
+
+cudaError_t launch_finalize_obs(const Layout& L, const uint8_t* valid, const uint8_t* cam_act,
+                                const uint8_t* pt_act, uint8_t* obs_act, uint8_t* obs_act_co,
+                                Scalars* sc, cudaStream_t s) {
+  if (L.N == 0) return cudaSuccess;
+  int grid = (L.N + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  k_finalize_obs<<<grid, 256, 0, s>>>(L, valid, cam_act, pt_act, obs_act, sc);
+  k_gather_co<<<grid, 256, 0, s>>>(L.N, L.co_po, obs_act, obs_act_co);
+  return cudaGetLastError();
+}
+
+__global__ void k_cam_flags(int C, const uint8_t* __restrict__ fixed, const uint8_t* __restrict__ cam_act,
+                            uint8_t* __restrict__ flags) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < C) flags[c] = (uint8_t)(cam_act[c] && !fixed[c]);
+}
+
+cudaError_t launch_cam_flags(const Layout& L, const uint8_t* cam_act, uint8_t* flags, cudaStream_t s) {
+  if (L.C > 0) k_cam_flags<<<(L.C + 255) / 256, 256, 0, s>>>(L.C, L.cam_fixed, cam_act, flags);
+  return cudaGetLastError();
+}
+
+// Exclusive scan of 0/1 flags into ascending ranks (Eq. rank): three passes,
+// block counts -> scan of block counts -> local scan plus block offset.
+constexpr int kScanItems = 8;
+constexpr int kScanThreads = 256;
+constexpr int kScanTile = kScanItems * kScanThreads;
+
+int rank_blocks(int n) { return (n + kScanTile - 1) / kScanTile; }
+
+__device__ int block_excl_scan(int v, int* sh /* >= 33 */, int* total) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    int w = lane < nw ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) sh[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  int base = wid > 0 ? sh[wid - 1] : 0;
+  if (total) *total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+__global__ void k_scan_count(const uint8_t* __restrict__ flags, int n, int* __restrict__ bsum) {
+  __shared__ int red[32];
+  int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int c = 0;
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) c += flags[base + i] ? 1 : 0;
+  int t = block_sum(c, red);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+}
+
+__global__ void k_scan_blocks(int* __restrict__ bsum, int nb, int* __restrict__ count) {
+  __shared__ int sh[33];
+  int per = (nb + blockDim.x - 1) / blockDim.x;
+  int beg = threadIdx.x * per;
+  int s = 0;
+  for (int i = 0; i < per; ++i)
+    if (beg + i < nb) s += bsum[beg + i];
+  int total;
+  int off = block_excl_scan(s, sh, &total);
+  for (int i = 0; i < per; ++i)
+    if (beg + i < nb) {
+      int v = bsum[beg + i];
+      bsum[beg + i] = off;
+      off += v;
+    }
+  if (threadIdx.x == 0) *count = total;
+}
+
+__global__ void k_scan_apply(const uint8_t* __restrict__ flags, int n, const int* __restrict__ boff,
+                             int* __restrict__ rank, int* __restrict__ map) {
+  __shared__ int sh[33];
+  int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int c = 0;
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) c += flags[base + i] ? 1 : 0;
+  int off = block_excl_scan(c, sh, nullptr) + boff[blockIdx.x];
+  for (int i = 0; i < kScanItems; ++i) {
+    int j = base + i;
+    if (j >= n) break;
+    if (flags[j]) {
+      rank[j] = off;
+      if (map) map[off] = j;
+      ++off;
+    } else {
+      rank[j] = -1;
+    }
+  }
+}
+
+cudaError_t launch_rank(const uint8_t* flags, int n, int* rank, int* map, int* count,
+                        int* block_tmp, int n_block_tmp, cudaStream_t s) {
+  int nb = rank_blocks(n);
+  if (nb > n_block_tmp) return cudaErrorInvalidValue;
+  if (n == 0) return cudaMemsetAsync(count, 0, sizeof(int), s);
+  k_scan_count<<<nb, kScanThreads, 0, s>>>(flags, n, block_tmp);
+  k_scan_blocks<<<1, 1024, 0, s>>>(block_tmp, nb, count);
+  k_scan_apply<<<nb, kScanThreads, 0, s>>>(flags, n, block_tmp, rank, map);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// steps (a)+(b), point side: W_k, V_p, g_p over tiles of whole points
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void load_cam(const T* __restrict__ camw, int c, T cw[kCamStride]) {
+  using V4 = typename Vec4<T>::type;
+  const V4* src = reinterpret_cast<const V4*>(camw + kCamStride * (size_t)c);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    V4 v = src[i];
+    cw[4 * i] = v.x;
+    cw[4 * i + 1] = v.y;
+    cw[4 * i + 2] = v.z;
+    cw[4 * i + 3] = v.w;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_pt(const T* __restrict__ ptsw, int p, T& x, T& y, T& z) {
+  using V4 = typename Vec4<T>::type;
+  V4 v = reinterpret_cast<const V4*>(ptsw)[p];
+  x = v.x;
+  y = v.y;
+  z = v.z;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, const T* __restrict__ camw,
+                                                   const T* __restrict__ ptsw,
+                                                   const uint8_t* __restrict__ obs_act, T* __restrict__ W,
+                                                   T* __restrict__ V, T* __restrict__ gp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ws = reinterpret_cast<T*>(smem_raw);  // [kTileObs][27]
+  T* Vs = Ws + kTileObs * 27;              // [kTileObs][9]
+  const TileDesc d = L.descs[blockIdx.x];
+  int ob = d.obs_begin, n = d.n_obs;
+  int pb = d.pt_begin, pe = d.pt_begin + d.n_pts;
+  const T* uvw = reinterpret_cast<const T*>(L.po_uvw);
+  const T* tauw = reinterpret_cast<const T*>(L.po_tauw);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int k = ob + i;
+    T* wrow = Ws + 27 * i;
+    T* vrow = Vs + 9 * i;
+    if (!obs_act[k]) {
+#pragma unroll
+      for (int j = 0; j < 27; ++j) wrow[j] = T(0);
+#pragma unroll
+      for (int j = 0; j < 9; ++j) vrow[j] = T(0);
+      continue;
+    }
+    T cw[kCamStride];
+    load_cam(camw, L.po_cam[k], cw);
+    T X0, X1, X2;
+    load_pt(ptsw, L.po_pt[k], X0, X1, X2);
+    T tau = tauw[k];
+    T sw = tau > T(0) ? (T)mp.sw_valid : (T)mp.sw_invalid;
+    ObsLin<T> o;
+    linearize_obs<T>(cw, X0, X1, X2, uvw[2 * (size_t)k], uvw[2 * (size_t)k + 1], tau, sw, (T)mp.cx,
+                     (T)mp.cy, (T)mp.huber, o);
+    T w = o.wrob;
+#pragma unroll
+    for (int a = 0; a < 9; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        wrow[3 * a + b] = w * (o.Jc[0][a] * o.Jp[0][b] + o.Jc[1][a] * o.Jp[1][b] + o.Jc[2][a] * o.Jp[2][b]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int b = a; b < 3; ++b)
+        vrow[sym3(a, b)] = w * (o.Jp[0][a] * o.Jp[0][b] + o.Jp[1][a] * o.Jp[1][b] + o.Jp[2][a] * o.Jp[2][b]);
+      vrow[6 + a] = w * (o.Jp[0][a] * o.r[0] + o.Jp[1][a] * o.r[1] + o.Jp[2][a] * o.r[2]);
+    }
+  }
+  __syncthreads();
+  T* Wdst = W + 27 * (size_t)d.w_row;
+  for (int j = threadIdx.x; j < 27 * n; j += blockDim.x) Wdst[j] = Ws[j];
+  for (int p = pb + threadIdx.x; p < pe; p += blockDim.x) {
+    T acc[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) acc[j] = T(0);
+    for (int k = L.pt_off[p]; k < L.pt_off[p + 1]; ++k)
+#pragma unroll
+      for (int j = 0; j < 9; ++j) acc[j] += Vs[9 * (k - ob) + j];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) V[6 * (size_t)p + j] = acc[j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gp[3 * (size_t)p + j] = acc[6 + j];
+  }
+}
+
+template <typename T>
+cudaError_t launch_pt_lin(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
+                          const uint8_t* obs_act, T* W, T* V, T* gp, cudaStream_t s) {
+  if (L.n_tiles == 0) return cudaSuccess;
+  size_t smem = sizeof(T) * kTileObs * 36;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_pt_lin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_pt_lin<T><<<L.n_tiles, kBlock, smem, s>>>(L, mp, camw, ptsw, obs_act, W, V, gp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// steps (a)+(b), camera side: per-chunk sums over one camera's observations.
+// mode 0: U_i (45 packed) and g_c (9).
+// mode 1: Schur terms sum_k W_k V*^-1 W_k^T (45) and sum_k W_k V*^-1 g_p (9), using
+//         W_k V^-1 W_k^T = w^2 Jc^T (Jp V^-1 Jp^T) Jc.
+// ---------------------------------------------------------------------------
+
+constexpr int kCamThreads = 128;
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kCamThreads) k_cam_accum(
+    Layout L, ModelParams mp, const T* __restrict__ camw, const T* __restrict__ ptsw,
+    const uint8_t* __restrict__ act_co, const uint8_t* __restrict__ cam_act,
+    const int* __restrict__ crank, const T* __restrict__ Vinv, const T* __restrict__ z0,
+    T* __restrict__ partials) {
+  __shared__ T red[kCamThreads / 32][54];
+  __shared__ T s_cw[kCamStride];
+  int q = blockIdx.x;
+  int c = L.chunk_cam[q];
+  int kb = L.chunk_obs[q], ke = L.chunk_obs[q + 1];
+  bool live = MODE == 0 ? (cam_act[c] != 0) : (crank[c] >= 0);
+  T* out = partials + 54 * (size_t)q;
+  if (!live) {
+    for (int j = threadIdx.x; j < 54; j += blockDim.x) out[j] = T(0);
+    return;
+  }
+  if (threadIdx.x < kCamStride) s_cw[threadIdx.x] = camw[kCamStride * (size_t)c + threadIdx.x];
+  __syncthreads();
+  T cw[kCamStride];
+#pragma unroll
+  for (int i = 0; i < kCamStride; ++i) cw[i] = s_cw[i];
+  const T* uvw = reinterpret_cast<const T*>(L.co_uvw);
+  const T* tauw = reinterpret_cast<const T*>(L.co_tauw);
+  T acc[54];
+#pragma unroll
+  for (int j = 0; j < 54; ++j) acc[j] = T(0);
+  for (int k = kb + threadIdx.x; k < ke; k += blockDim.x) {
+    if (!act_co[k]) continue;
+    int p = L.co_pt[k];
+    T X0, X1, X2;
+    load_pt(ptsw, p, X0, X1, X2);
+    T tau = tauw[k];
+    T sw = tau > T(0) ? (T)mp.sw_valid : (T)mp.sw_invalid;
+    ObsLin<T> o;
+    linearize_obs<T>(cw, X0, X1, X2, uvw[2 * (size_t)k], uvw[2 * (size_t)k + 1], tau, sw, (T)mp.cx,
+                     (T)mp.cy, (T)mp.huber, o);
+    T w = o.wrob;
+    if (MODE == 0) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+#pragma unroll
+        for (int b = a; b < 9; ++b)
+          acc[sym9(a, b)] += w * (o.Jc[0][a] * o.Jc[0][b] + o.Jc[1][a] * o.Jc[1][b] + o.Jc[2][a] * o.Jc[2][b]);
+        acc[45 + a] += w * (o.Jc[0][a] * o.r[0] + o.Jc[1][a] * o.r[1] + o.Jc[2][a] * o.r[2]);
+      }
+    } else {
+      const T* vi = Vinv + 6 * (size_t)p;
+      T Vi[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Vi[a][b] = vi[sym3(a, b)];
+      // A = Jp V^-1 (3x3), Q = A Jp^T (3x3 symmetric)
+      T A[3][3], Q[3][3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          A[m][b] = o.Jp[m][0] * Vi[0][b] + o.Jp[m][1] * Vi[1][b] + o.Jp[m][2] * Vi[2][b];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+          Q[m][l] = w * w * (A[m][0] * o.Jp[l][0] + A[m][1] * o.Jp[l][1] + A[m][2] * o.Jp[l][2]);
+      // M = Q Jc (3x9); acc += Jc^T M
+      T M[3][9];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int b = 0; b < 9; ++b) M[m][b] = Q[m][0] * o.Jc[0][b] + Q[m][1] * o.Jc[1][b] + Q[m][2] * o.Jc[2][b];
+#pragma unroll
+      for (int a = 0; a < 9; ++a)
+#pragma unroll
+        for (int b = a; b < 9; ++b)
+          acc[sym9(a, b)] += o.Jc[0][a] * M[0][b] + o.Jc[1][a] * M[1][b] + o.Jc[2][a] * M[2][b];
+      // W z0 = w Jc^T (Jp z0)
+      const T* zp = z0 + 3 * (size_t)p;
+      T jz[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) jz[m] = w * (o.Jp[m][0] * zp[0] + o.Jp[m][1] * zp[1] + o.Jp[m][2] * zp[2]);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) acc[45 + a] += o.Jc[0][a] * jz[0] + o.Jc[1][a] * jz[1] + o.Jc[2][a] * jz[2];
+    }
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 54; ++j) {
+    T v = warp_sum(acc[j]);
+    if (lane == 0) red[wid][j] = v;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < 54; j += blockDim.x) {
+    T s = T(0);
+    for (int w = 0; w < kCamThreads / 32; ++w) s += red[w][j];
+    out[j] = s;
+  }
+}
+
+template <typename T>
+cudaError_t launch_cam_accum(const Layout& L, const ModelParams& mp, int mode, const T* camw,
+                             const T* ptsw, const uint8_t* act_co, const uint8_t* cam_act,
+                             const int* crank, const T* Vinv, const T* z0, T* partials,
+                             cudaStream_t s) {
+  if (L.n_chunks == 0) return cudaSuccess;
+  if (mode == 0)
+    k_cam_accum<T, 0><<<L.n_chunks, kCamThreads, 0, s>>>(L, mp, camw, ptsw, act_co, cam_act, crank,
+                                                         Vinv, z0, partials);
+  else
+    k_cam_accum<T, 1><<<L.n_chunks, kCamThreads, 0, s>>>(L, mp, camw, ptsw, act_co, cam_act, crank,
+                                                         Vinv, z0, partials);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_cam_reduce(int C, const int* __restrict__ cam_chunk, const T* __restrict__ partials,
+                             T* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C * 54) return;
+  int c = i / 54, j = i - 54 * c;
+  double s = 0.0;
+  for (int q = cam_chunk[c]; q < cam_chunk[c + 1]; ++q) s += (double)partials[54 * (size_t)q + j];
+  out[i] = (T)s;
+}
+
+template <typename T>
+cudaError_t launch_cam_reduce(const Layout& L, const T* partials, T* out, cudaStream_t s) {
+  int n = L.C * 54;
+  if (n > 0) k_cam_reduce<T><<<(n + 255) / 256, 256, 0, s>>>(L.C, L.cam_chunk, partials, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// damping (Eq. LM, Marquardt scaling with the clamped diagonal)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double clamp_diag(double a) { return fmin(fmax(a, 1e-6), 1e32); }
+
+template <typename T>
+__global__ void k_damp_pts(int P, const T* __restrict__ V, const T* __restrict__ gp,
+                           const uint8_t* __restrict__ pt_act, double lambda, T* __restrict__ Vinv,
+                           T* __restrict__ z0, int* err) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  T* vo = Vinv + 6 * (size_t)p;
+  T* zo = z0 + 3 * (size_t)p;
+  if (!pt_act[p]) {
+    for (int j = 0; j < 6; ++j) vo[j] = T(0);
+    for (int j = 0; j < 3; ++j) zo[j] = T(0);
+    return;
+  }
+  const T* v = V + 6 * (size_t)p;
+  double a = v[0], b = v[1], c = v[2], d = v[3], e = v[4], f = v[5];  // [[a b c][b d e][c e f]]
+  a += lambda * clamp_diag(a);
+  d += lambda * clamp_diag(d);
+  f += lambda * clamp_diag(f);
+  // adjugate of the symmetric matrix
+  double A = d * f - e * e, B = c * e - b * f, Cc = b * e - c * d;
+  double det = a * A + b * B + c * Cc;
+  if (!(det > 0.0) || !isfinite(det)) {
+    atomicOr(err, 4);
+    for (int j = 0; j < 6; ++j) vo[j] = T(0);
+    for (int j = 0; j < 3; ++j) zo[j] = T(0);
+    return;
+  }
+  double id = 1.0 / det;
+  double i00 = A * id, i01 = B * id, i02 = Cc * id;
+  double i11 = (a * f - c * c) * id, i12 = (b * c - a * e) * id, i22 = (a * d - b * b) * id;
+  vo[0] = (T)i00; vo[1] = (T)i01; vo[2] = (T)i02; vo[3] = (T)i11; vo[4] = (T)i12; vo[5] = (T)i22;
+  double g0 = gp[3 * (size_t)p], g1 = gp[3 * (size_t)p + 1], g2 = gp[3 * (size_t)p + 2];
+  zo[0] = (T)(i00 * g0 + i01 * g1 + i02 * g2);
+  zo[1] = (T)(i01 * g0 + i11 * g1 + i12 * g2);
+  zo[2] = (T)(i02 * g0 + i12 * g1 + i22 * g2);
+}
+
+template <typename T>
+cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_act, double lambda,
+                            T* Vinv, T* z0, int* err, cudaStream_t s) {
+  if (P > 0) k_damp_pts<T><<<(P + 255) / 256, 256, 0, s>>>(P, V, gp, pt_act, lambda, Vinv, z0, err);
+  return cudaGetLastError();
+}
+
+// Per free camera f: damped U block, block-Jacobi inverse of the Schur diagonal
+// D_f = U*_f - sum W V*^-1 W^T (FP64 Cholesky), Schur RHS b_f = -g_c + sum W V*^-1 g_p.
+template <typename T>
+__global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* __restrict__ Ug,
+                             const T* __restrict__ Sg, double lambda, T* __restrict__ Ud,
+                             T* __restrict__ Dinv, T* __restrict__ b, T* __restrict__ dampc, int* err) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= Cf) return;
+  int c = cam_map[f];
+  const T* u = Ug + 54 * (size_t)c;
+  const T* sch = Sg + 54 * (size_t)c;
+  double D[9][9];
+  for (int i = 0; i < 9; ++i) {
+    for (int j = i; j < 9; ++j) {
+      double uij = u[sym9(i, j)];
+      if (i == j) {
+        double dc = clamp_diag(uij);
+        dampc[9 * (size_t)f + i] = (T)dc;
+        uij += lambda * dc;
+      }
+      Ud[45 * (size_t)f + sym9(i, j)] = (T)uij;
+      double v = uij - (double)sch[sym9(i, j)];
+      D[i][j] = v;
+      D[j][i] = v;
+    }
+    b[9 * (size_t)f + i] = (T)(-(double)u[45 + i] + (double)sch[45 + i]);
+  }
+  // Cholesky D = L L^T in place (lower)
+  bool ok = true;
+  for (int j = 0; j < 9 && ok; ++j) {
+    double s = D[j][j];
+    for (int l = 0; l < j; ++l) s -= D[j][l] * D[j][l];
+    if (!(s > 0.0)) {
+      ok = false;
+      break;
+    }
+    double dj = sqrt(s);
+    D[j][j] = dj;
+    for (int i = j + 1; i < 9; ++i) {
+      double t = D[i][j];
+      for (int l = 0; l < j; ++l) t -= D[i][l] * D[j][l];
+      D[i][j] = t / dj;
+    }
+  }
+  T* out = Dinv + 81 * (size_t)f;
+  if (!ok) {
+    // fall back to the Jacobi diagonal of the damped U block
+    atomicOr(err, 8);
+    for (int i = 0; i < 9; ++i)
+      for (int j = 0; j < 9; ++j) out[9 * i + j] = i == j ? (T)(1.0 / (double)Ud[45 * (size_t)f + sym9(i, i)]) : T(0);
+    return;
+  }
+  // inverse column by column: solve L L^T x = e_j
+  for (int j = 0; j < 9; ++j) {
+    double x[9];
+    for (int i = 0; i < 9; ++i) {
+      double s = i == j ? 1.0 : 0.0;
+      for (int l = 0; l < i; ++l) s -= D[i][l] * x[l];
+      x[i] = s / D[i][i];
+    }
+    for (int i = 8; i >= 0; --i) {
+      double s = x[i];
+      for (int l = i + 1; l < 9; ++l) s -= D[l][i] * x[l];
+      x[i] = s / D[i][i];
+    }
+    for (int i = 0; i < 9; ++i) out[9 * i + j] = (T)x[i];
+  }
+}
+
+template <typename T>
+cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
+                              T* Ud, T* Dinv, T* b, T* dampc, int* err, cudaStream_t s) {
+  if (Cf > 0) k_schur_diag<T><<<(Cf + 63) / 64, 64, 0, s>>>(Cf, cam_map, Ug, Sg, lambda, Ud, Dinv, b, dampc, err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_pred_cams(int Cf, const int* __restrict__ cam_map, const T* __restrict__ x,
+                            const T* __restrict__ Ug, const T* __restrict__ dampc, double lambda,
+                            double* __restrict__ pred_parts) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 9 * Cf; e += gridDim.x * blockDim.x) {
+    int f = e / 9, i = e - 9 * f;
+    int c = cam_map[f];
+    double d = (double)x[e];
+    acc += d * (lambda * (double)dampc[e] * d - (double)Ug[54 * (size_t)c + 45 + i]);
+  }
+  double s = block_sum(acc, red);
+  if (threadIdx.x == 0) pred_parts[blockIdx.x] = s;
+}
+
+template <typename T>
+cudaError_t launch_pred_cams(int Cf, const int* cam_map, const T* x, const T* Ug, const T* dampc,
+                             double lambda, double* pred_parts, int offset, cudaStream_t s) {
+  k_pred_cams<T><<<1, 256, 0, s>>>(Cf, cam_map, x, Ug, dampc, lambda, pred_parts + offset);
+  return cudaGetLastError();
+}
+
+__global__ void k_reduce_pred(const double* __restrict__ parts, int n, Scalars* sc) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += parts[i];
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) sc->pred = 0.5 * a;
+}
+
+cudaError_t launch_reduce_pred(const double* parts, int n, Scalars* sc, cudaStream_t s) {
+  k_reduce_pred<<<1, 256, 0, s>>>(parts, n, sc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// step (e) candidate x (+) dx and scatter of the compact camera step (Sec. 4.2 step 3)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_candidate_cams(int C, const int* __restrict__ crank, const T* __restrict__ x,
+                                 const double* __restrict__ src, double* __restrict__ dst,
+                                 double* __restrict__ camw64, T* __restrict__ camw) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const double* s = src + 9 * (size_t)c;
+  double o[9];
+  int r = crank[c];
+  if (r >= 0) {
+    const T* d = x + 9 * (size_t)r;
+    double dw[3] = {(double)d[0], (double)d[1], (double)d[2]};
+    double w[3] = {s[0], s[1], s[2]};
+    rotvec_left_compose(dw, w, o);
+    for (int i = 3; i < 9; ++i) o[i] = s[i] + (double)d[i];
+  } else {
+    for (int i = 0; i < 9; ++i) o[i] = s[i];
+  }
+  for (int i = 0; i < 9; ++i) dst[9 * (size_t)c + i] = o[i];
+  double R[9];
+  rotvec_matrix(o, R);
+  double rec[kCamStride];
+  for (int i = 0; i < 9; ++i) rec[i] = R[i];
+  for (int i = 0; i < 6; ++i) rec[9 + i] = o[3 + i];
+  rec[15] = 0.0;
+  for (int i = 0; i < kCamStride; ++i) camw64[kCamStride * (size_t)c + i] = rec[i];
+  if (camw)
+    for (int i = 0; i < kCamStride; ++i) camw[kCamStride * (size_t)c + i] = (T)rec[i];
+}
+
+template <typename T>
+__global__ void k_candidate_pts(int P, const T* __restrict__ dp, const double* __restrict__ src,
+                                double* __restrict__ dst, T* __restrict__ ptsw) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double v[3];
+  for (int i = 0; i < 3; ++i) {
+    v[i] = src[3 * (size_t)p + i] + (double)dp[3 * (size_t)p + i];
+    dst[3 * (size_t)p + i] = v[i];
+  }
+  using V4 = typename Vec4<T>::type;
+  V4 q;
+  q.x = (T)v[0];
+  q.y = (T)v[1];
+  q.z = (T)v[2];
+  q.w = T(0);
+  reinterpret_cast<V4*>(ptsw)[p] = q;
+}
+
+template <typename T>
+cudaError_t launch_candidate(int C, int P, const int* crank, const T* x, const T* dp,
+                             const double* cams_src, const double* pts_src, double* cams_dst,
+                             double* pts_dst, double* camw64_dst, T* camw_dst, T* ptsw_dst,
+                             cudaStream_t s) {
+  if (C > 0) k_candidate_cams<T><<<(C + 127) / 128, 128, 0, s>>>(C, crank, x, cams_src, cams_dst, camw64_dst, camw_dst);
+  if (P > 0) k_candidate_pts<T><<<(P + 255) / 256, 256, 0, s>>>(P, dp, pts_src, pts_dst, ptsw_dst);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_scatter_cams(int C, const int* __restrict__ crank, const T* __restrict__ x,
+                               double* __restrict__ dc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 9 * C) return;
+  int c = i / 9, j = i - 9 * c;
+  int r = crank[c];
+  dc[i] = r >= 0 ? (double)x[9 * (size_t)r + j] : 0.0;
+}
+
+template <typename T>
+cudaError_t launch_scatter_cams(int C, const int* crank, const T* x, double* dc, cudaStream_t s) {
+  if (C > 0) k_scatter_cams<T><<<(9 * C + 255) / 256, 256, 0, s>>>(C, crank, x, dc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+template <typename T>
+cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t s) {
+  if (n > 0) {
+    long long g = (n + 255) / 256;
+    k_to_double<T><<<(int)(g > 65535 ? 65535 : g), 256, 0, s>>>(src, dst, n);
+  }
+  return cudaGetLastError();
+}
+
+__global__ void k_permute_u8(const int* __restrict__ orig, const uint8_t* __restrict__ src,
+                             uint8_t* __restrict__ dst, int N) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) dst[orig[k]] = src[k];
+}
+
+cudaError_t launch_permute_u8(const int* orig, const uint8_t* src, uint8_t* dst, int N, cudaStream_t s) {
+  if (N > 0) k_permute_u8<<<(N + 255) / 256, 256, 0, s>>>(orig, src, dst, N);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_permute_rows(const int* __restrict__ orig, const int* __restrict__ row,
+                               const T* __restrict__ src, double* __restrict__ dst, int N, int width) {
+  long long tot = (long long)N * width;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    int k = (int)(i / width), j = (int)(i - (long long)k * width);
+    size_t r = row ? (size_t)row[k] : (size_t)k;
+    dst[(size_t)orig[k] * width + j] = (double)src[r * width + j];
+  }
+}
+
+template <typename T>
+cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, double* dst, int N,
+                                int width, cudaStream_t s) {
+  long long tot = (long long)N * width;
+  if (tot > 0) {
+    long long g = (tot + 255) / 256;
+    k_permute_rows<T><<<(int)(g > 65535 ? 65535 : g), 256, 0, s>>>(orig, row, src, dst, N, width);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------
+#define BAB_INST(T)                                                                                \
+  template cudaError_t launch_prep_cams<T>(const double*, T*, double*, int, cudaStream_t);          \
+  template cudaError_t launch_prep_pts<T>(const double*, T*, int, cudaStream_t);                    \
+  template cudaError_t launch_pt_lin<T>(const Layout&, const ModelParams&, const T*, const T*,      \
+                                        const uint8_t*, T*, T*, T*, cudaStream_t);                  \
+  template cudaError_t launch_cam_accum<T>(const Layout&, const ModelParams&, int, const T*,        \
+                                           const T*, const uint8_t*, const uint8_t*, const int*,    \
+                                           const T*, const T*, T*, cudaStream_t);                   \
+  template cudaError_t launch_cam_reduce<T>(const Layout&, const T*, T*, cudaStream_t);             \
+  template cudaError_t launch_damp_pts<T>(int, const T*, const T*, const uint8_t*, double, T*, T*,  \
+                                          int*, cudaStream_t);                                      \
+  template cudaError_t launch_schur_diag<T>(int, const int*, const T*, const T*, double, T*, T*,    \
+                                            T*, T*, int*, cudaStream_t);                            \
+  template cudaError_t launch_pred_cams<T>(int, const int*, const T*, const T*, const T*, double,   \
+                                           double*, int, cudaStream_t);                             \
+  template cudaError_t launch_candidate<T>(int, int, const int*, const T*, const T*, const double*, \
+                                           const double*, double*, double*, double*, T*, T*,        \
+                                           cudaStream_t);                                           \
+  template cudaError_t launch_scatter_cams<T>(int, const int*, const T*, double*, cudaStream_t);    \
+  template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);              \
+  template cudaError_t launch_permute_rows<T>(const int*, const int*, const T*, double*, int, int,    \
+                                              cudaStream_t);
+
+BAB_INST(float)
+BAB_INST(double)
+
+}  // namespace bab

@@ -1,0 +1,285 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Each test runs both sides on the same seeded inputs and compares element by
+element: step (a)+(b) blocks at an identical state, step (c) masks and ranks
+bit for bit, step (d) damped steps, step (e) whole LM trajectories."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_13310_b300 import ba, scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+
+def tiny(n_cams=8, n_pts=300, track=4, seed=5, **kw):
+    spec = dataclasses.replace(scenes.SPECS["small"], n_cams=n_cams, n_pts=n_pts, track_min=track,
+                               track_max=track, track_mean=track, seed=seed)
+    return scenes.make_scene(spec, **kw)
+
+
+def geometric(n_cams, n_pts, lo, hi, mean, seed, **kw):
+    spec = dataclasses.replace(scenes.SPECS["medium"], n_cams=n_cams, n_pts=n_pts, track_min=lo,
+                               track_max=hi, track_mean=mean, seed=seed)
+    return scenes.make_scene(spec, **kw)
+
+
+def pair(scene, precision, **opt):
+    o = ba.Options(precision=precision, **opt)
+    gpu = ba.Problem.from_scene(scene, o)
+    oo = oracle.OracleOptions(**{k: v for k, v in opt.items() if k in oracle.OracleOptions.__dataclass_fields__})
+    orc = oracle.OracleBA.from_scene(scene, oo)
+    return gpu, orc
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# (a)+(b): normal-equation blocks at an identical state
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-11), (ba.BA_FP32, 2e-4)])
+def test_linearization_blocks_match_oracle(precision, tol):
+    sc = geometric(12, 3000, 2, 12, 5.0, seed=31)   # several tiles, ragged last tile
+    gpu, orc = pair(sc, precision, invalid_depth_weight=1e-3)
+    lin = gpu.linearize()
+    act = gpu.get_active()
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    np.testing.assert_array_equal(act["obs_mask"], ext["obs_mask"])
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    live = ext["cam_mask"].astype(bool)
+    assert rel_err(lin["U"][live], ne["U"][live]) < tol
+    assert rel_err(lin["gc"][live], ne["gc"][live]) < tol
+    assert rel_err(lin["V"], ne["V"]) < tol
+    assert rel_err(lin["gp"], ne["gp"]) < tol
+    assert rel_err(lin["W"], ne["W"]) < tol
+
+
+def test_cost_fp64_matches_oracle_at_same_state():
+    sc = geometric(10, 2000, 2, 10, 5.0, seed=3)
+    for prec in (ba.BA_FP64, ba.BA_FP32):
+        gpu, orc = pair(sc, prec)
+        F, rmse = gpu.eval_cost()
+        m = gpu.get_active()["obs_mask"]
+        Fo, rmse_o = orc.cost(sc.cams0, sc.pts0, m)
+        assert F == pytest.approx(Fo, rel=1e-12)
+        assert rmse == pytest.approx(rmse_o, rel=1e-12)
+        # another state, passed in
+        c2, p2 = sc.cams_gt, sc.pts_gt
+        F2, _ = gpu.eval_cost(c2, p2)
+        Fo2, _ = orc.cost(c2, p2, m)
+        assert F2 == pytest.approx(Fo2, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# (c): extraction masks and ranks, bit for bit
+# ---------------------------------------------------------------------------
+
+def _perturb_visibility(sc, rng, n_far=40, n_behind=20):
+    """Move some points out of every image and some behind one camera."""
+    pts = sc.pts0.copy()
+    far = rng.choice(sc.spec.n_pts, n_far, replace=False)
+    pts[far] = np.array([0.0, 0.0, 30.0]) + rng.normal(size=(n_far, 3))
+    from scipy.spatial.transform import Rotation
+    ks = rng.choice(sc.n_obs, n_behind, replace=False)
+    for k in ks:
+        c = sc.obs_cam[k]
+        centre = -Rotation.from_rotvec(sc.cams0[c, :3]).inv().apply(sc.cams0[c, 3:6])
+        pts[sc.obs_pt[k]] = 1.02 * centre
+    return pts
+
+
+@pytest.mark.parametrize("thresholds", [(1, 1), (15, 2), (40, 3)])
+def test_extraction_bit_exact(thresholds):
+    rng = np.random.default_rng(11)
+    sc = geometric(30, 4000, 2, 12, 4.0, seed=17)
+    pts = _perturb_visibility(sc, rng)
+    tc, tp = thresholds
+    gpu, orc = pair(sc, ba.BA_FP32, min_cam_obs=tc, min_pt_obs=tp)
+    gpu.set_params(sc.cams0, pts)
+    gpu.extract()
+    g = gpu.get_active()
+    geom, _ = orc.predicate(sc.cams0, pts)
+    e = orc.extract(geom)
+    for key in ("cam_mask", "pt_mask", "obs_mask", "cam_rank", "pt_rank"):
+        np.testing.assert_array_equal(g[key], e[key], err_msg=key)
+    if thresholds == (1, 1):
+        v = geom.astype(bool)
+        np.testing.assert_array_equal(np.flatnonzero(g["pt_mask"]), np.unique(sc.obs_pt[v]))
+
+
+def test_extraction_residual_drop_and_order_invariance():
+    sc = geometric(20, 3000, 2, 10, 5.0, seed=23)
+    opt = dict(min_cam_obs=15, min_pt_obs=2, drop_residual_px=4.0, extract_every=5)
+    gpu, orc = pair(sc, ba.BA_FP32, **opt)
+    gpu.extract(drop=True)
+    g = gpu.get_active()
+    geom, res = orc.predicate(sc.cams0, sc.pts0)
+    alive = ~((geom == 1) & (res > 4.0))
+    e = orc.extract((geom.astype(bool) & alive).astype(np.uint8))
+    for key in ("cam_mask", "pt_mask", "obs_mask", "cam_rank", "pt_rank"):
+        np.testing.assert_array_equal(g[key], e[key], err_msg=key)
+    # a shuffled observation order gives the same sets
+    perm = np.random.default_rng(2).permutation(sc.n_obs)
+    sc2 = dataclasses.replace(sc, obs_cam=sc.obs_cam[perm], obs_pt=sc.obs_pt[perm],
+                              obs_uv=sc.obs_uv[perm], depth=sc.depth[perm])
+    gpu2 = ba.Problem.from_scene(sc2, ba.Options(**opt))
+    gpu2.extract(drop=True)
+    g2 = gpu2.get_active()
+    np.testing.assert_array_equal(g2["pt_mask"], g["pt_mask"])
+    np.testing.assert_array_equal(g2["cam_rank"], g["cam_rank"])
+    np.testing.assert_array_equal(g2["obs_mask"], g["obs_mask"][perm])
+
+
+# ---------------------------------------------------------------------------
+# (d): damped step (Schur + PCG + back-substitution) vs the oracle's solve
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-7), (ba.BA_FP32, 2e-2)])
+def test_damped_step_matches_oracle(precision, tol):
+    sc = geometric(12, 3000, 2, 12, 5.0, seed=41)
+    gpu, orc = pair(sc, precision, pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6)
+    lam = 1e-3
+    g = gpu.solve_damped(lam)
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    o = orc.solve_step(ne, ext, lam)   # dense Cholesky of the Schur system
+    assert rel_err(g["dc"], o["dc"]) < tol
+    assert rel_err(g["dp"], o["dp"]) < tol
+    assert g["pred_decrease"] == pytest.approx(o["pred_decrease"], rel=tol)
+    assert g["pcg_rel_res"] <= (1e-10 if precision == ba.BA_FP64 else 1e-6)
+    assert not g["dc"][sc.fixed_cams].any()
+
+
+# ---------------------------------------------------------------------------
+# (e): LM trajectories
+# ---------------------------------------------------------------------------
+
+def test_small_scene_fp64_trajectory_matches_oracle():
+    """The FP64 small workload: 20 cameras, 2k points, ~20k observations, 10 iterations."""
+    sc = scenes.make_scene("small")
+    gpu, orc = pair(sc, ba.BA_FP64)
+    log_g = gpu.solve(10)
+    orc.opts.solver = 1
+    c_o, p_o, log_o = orc.lm(sc.cams0, sc.pts0, 10)
+    for i, (a, b) in enumerate(zip(log_g, log_o)):
+        assert a["cost"] == pytest.approx(b["cost"], rel=1e-5), i
+        assert a["accepted"] == b["accepted"], i
+        assert a["n_obs_act"] == b["n_obs_act"]
+    c_g, p_g = gpu.get_params()
+    assert np.abs(p_g - p_o).max() < 1e-5
+    assert np.abs(c_g - c_o).max() < 1e-4
+
+
+def test_fp32_trajectory_close_to_oracle():
+    sc = geometric(40, 20000, 3, 20, 10.0, seed=1001)
+    gpu, orc = pair(sc, ba.BA_FP32)
+    log_g = gpu.solve(8)
+    orc.opts.solver = 1
+    _, _, log_o = orc.lm(sc.cams0, sc.pts0, 8)
+    for i, (a, b) in enumerate(zip(log_g, log_o)):
+        assert a["cost"] == pytest.approx(b["cost"], rel=1e-5), i
+
+
+def test_inactive_parameters_unchanged_by_a_step():
+    rng = np.random.default_rng(4)
+    sc = geometric(12, 1500, 2, 8, 4.0, seed=8)
+    pts = _perturb_visibility(sc, rng, n_far=30, n_behind=0)
+    gpu = ba.Problem.from_scene(sc, ba.Options(precision=ba.BA_FP64))
+    gpu.set_params(sc.cams0, pts)
+    gpu.lm_step()
+    act = gpu.get_active()
+    _, p1 = gpu.get_params()
+    off = act["pt_mask"] == 0
+    assert off.sum() >= 30
+    np.testing.assert_array_equal(p1[off], pts[off])
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_invalid_inputs_rejected():
+    sc = tiny()
+    bad = sc.obs_cam.copy()
+    bad[3] = 99
+    with pytest.raises(ba.BAError, match="invalid argument"):
+        ba.Problem(sc.cams0, sc.pts0, bad, sc.obs_pt, sc.obs_uv, sc.depth)
+    dup_c = np.concatenate([sc.obs_cam, sc.obs_cam[:1]])
+    dup_p = np.concatenate([sc.obs_pt, sc.obs_pt[:1]])
+    with pytest.raises(ba.BAError, match="invalid argument"):
+        ba.Problem(sc.cams0, sc.pts0, dup_c, dup_p, np.concatenate([sc.obs_uv, sc.obs_uv[:1]]),
+                   np.concatenate([sc.depth, sc.depth[:1]]))
+    uv = sc.obs_uv.copy()
+    uv[0, 0] = np.nan
+    with pytest.raises(ba.BAError, match="invalid argument"):
+        ba.Problem(sc.cams0, sc.pts0, sc.obs_cam, sc.obs_pt, uv, sc.depth)
+
+
+def test_track_length_limit():
+    # a point seen by 256 cameras is accepted, 257 is refused
+    C = 257
+    cams = np.tile(np.array([0, 0, 0, 0, 0, 3.0, 500, 0, 0]), (C, 1))
+    cams[:, 0] = np.linspace(-0.1, 0.1, C)
+    for n in (256, 257):
+        oc = np.arange(n, dtype=np.int32)
+        op = np.zeros(n, np.int32)
+        uv = np.full((n, 2), 320.0)
+        if n == 256:
+            p = ba.Problem(cams, np.zeros((1, 3)), oc, op, uv, np.zeros(n))
+            p.lm_step()
+        else:
+            with pytest.raises(ba.BAError, match="invalid argument"):
+                ba.Problem(cams, np.zeros((1, 3)), oc, op, uv, np.zeros(n))
+
+
+def test_degenerate_problems():
+    # only the gauge camera: nothing to solve for cameras, points still move
+    sc = tiny(n_cams=4, n_pts=50, track=3, seed=2)
+    keep = sc.obs_cam == 0
+    p = ba.Problem(sc.cams0[:1], sc.pts0, sc.obs_cam[keep], sc.obs_pt[keep], sc.obs_uv[keep],
+                   sc.depth[keep], ba.Options(precision=ba.BA_FP64))
+    info = p.lm_step()
+    assert info["pcg_iters"] == 0
+    # points and cameras without any observation
+    C, P = sc.spec.n_cams + 2, sc.spec.n_pts + 5
+    cams = np.concatenate([sc.cams0, sc.cams0[:2]])
+    pts = np.concatenate([sc.pts0, np.zeros((5, 3))])
+    p = ba.Problem(cams, pts, sc.obs_cam, sc.obs_pt, sc.obs_uv, sc.depth)
+    p.lm_step()
+    act = p.get_active()
+    assert not act["cam_mask"][-2:].any() and not act["pt_mask"][-5:].any()
+    assert (act["pt_rank"][-5:] == -1).all()
+    # no observations at all
+    p = ba.Problem(sc.cams0, sc.pts0, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                   np.zeros((0, 2)), np.zeros(0))
+    info = p.lm_step()
+    assert info["n_obs_act"] == 0
+
+
+def test_device_and_host_buffers_agree():
+    sc = tiny()
+    dev = lambda a: torch.as_tensor(a).cuda()
+    p1 = ba.Problem.from_scene(sc)
+    p2 = ba.Problem(dev(sc.cams0), dev(sc.pts0), dev(sc.obs_cam), dev(sc.obs_pt), dev(sc.obs_uv),
+                    dev(sc.depth))
+    l1 = p1.solve(3)
+    l2 = p2.solve(3)
+    # every reduction runs in a fixed order: the same inputs give bit-identical runs
+    assert [a["cost"] for a in l1] == [b["cost"] for b in l2]
+    c_dev = torch.zeros((sc.spec.n_cams, 9), dtype=torch.float64, device="cuda")
+    p_dev = torch.zeros((sc.spec.n_pts, 3), dtype=torch.float64, device="cuda")
+    p2.get_params(c_dev, p_dev)
+    c_h, p_h = p1.get_params()
+    np.testing.assert_array_equal(c_dev.cpu().numpy(), c_h)
+    np.testing.assert_array_equal(p_dev.cpu().numpy(), p_h)
