@@ -154,6 +154,32 @@ ba_status ba_eval_cost(ba_problem* pb, const double* cams, const double* pts, do
 ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_dpts,
                       double* dL_duv, double* dL_ddepth);
 
+/* FP64 cost of a state without allocating device memory.  The paper has no
+ * counterpart: this is an interface for callers that cannot call cudaMalloc,
+ * such as code captured into a CUDA graph, code running under a framework that
+ * owns all device memory, or code that must avoid the synchronisation an
+ * allocation can cause.  Returns on the stream (asynchronously)
+ * out[0] = 1/2 sum rho(|r_k|^2), out[1] = reprojection RMSE, out[2] = number of
+ * observations counted, over observations with obs_mask[k] != 0 (NULL: all),
+ * in the input order; the camera model, Huber loss, depth residual and weights
+ * are those of ba_lm_step, taken from opts (precision and extraction fields are
+ * ignored).  Observations whose indices are out of range are skipped.
+ * Every array (inputs and out) must be readable/writable by kernels of the
+ * current device: device memory of that device, managed memory, or mapped
+ * page-locked host memory; anything else is rejected (BA_ERR_INVALID_ARG).
+ * Scratch is a fixed device array in the library (about 0.55 MB per device
+ * that loads it, held until exit): n_cams above 4096 is rejected with
+ * BA_ERR_INVALID_ARG.  The first call on a device looks that array up
+ * (cudaGetSymbolAddress); make it before any stream capture.  Every call
+ * shares the array, so calls whose work overlaps on the GPU (other streams,
+ * other host threads) race; order them on one stream.  Nothing in the scratch
+ * needs clearing: each call writes every entry it reads. */
+ba_status ba_eval_cost_noalloc(const ba_options* opts, void* stream, int64_t n_cams,
+                               const double* cams, int64_t n_pts, const double* pts,
+                               int64_t n_obs, const int32_t* obs_cam, const int32_t* obs_pt,
+                               const double* obs_uv, const double* depth,
+                               const uint8_t* obs_mask, double* out);
+
 /* Number of this library's kernels launched since creation (counts launches). */
 int64_t ba_kernel_launches(const ba_problem* pb);
 

@@ -24,8 +24,8 @@ BA_FP64, BA_FP32 = 0, 1
 # every symbol include/ba_b300.h declares
 EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
-           "ba_eval_cost", "ba_backward", "ba_kernel_launches", "ba_destroy", "ba_status_string",
-           "ba_last_error")
+           "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_kernel_launches", "ba_destroy",
+           "ba_status_string", "ba_last_error")
 
 
 class _Options(ct.Structure):
@@ -83,6 +83,8 @@ def lib():
         L.ba_solve_damped.argtypes = [vp, ct.c_double, vp, vp, ct.POINTER(_IterInfo)]
         L.ba_eval_cost.argtypes = [vp, vp, vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         L.ba_backward.argtypes = [vp, vp, vp, vp, vp]
+        L.ba_eval_cost_noalloc.argtypes = [ct.POINTER(_Options), vp, ct.c_int64, vp, ct.c_int64, vp,
+                                           ct.c_int64, vp, vp, vp, vp, vp, vp]
         L.ba_kernel_launches.argtypes = [vp]
         L.ba_kernel_launches.restype = ct.c_int64
         L.ba_destroy.argtypes = [vp]
@@ -91,7 +93,7 @@ def lib():
         L.ba_last_error.restype = ct.c_char_p
         for f in ("ba_create", "ba_lm_step", "ba_solve", "ba_get_params", "ba_set_params",
                   "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped", "ba_eval_cost",
-                  "ba_backward"):
+                  "ba_backward", "ba_eval_cost_noalloc"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -290,3 +292,29 @@ class Problem:
     @property
     def kernel_launches(self):
         return int(self.L.ba_kernel_launches(self.h))
+
+
+def _c_options(o: Options):
+    fixed = np.ascontiguousarray(np.asarray(o.fixed_cams, dtype=np.int32))
+    c = _Options(o.precision, o.img_w, o.img_h, o.cx, o.cy, o.huber_delta, o.depth_weight,
+                 o.invalid_depth_weight, o.min_depth, o.extract_every, o.drop_residual_px,
+                 o.min_cam_obs, o.min_pt_obs, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
+                 fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(fixed))
+    return c, fixed
+
+
+def eval_cost_noalloc(cams, pts, obs_cam, obs_pt, obs_uv, depth, out, obs_mask=None,
+                      options: Options | None = None, stream=None):
+    """ba_eval_cost_noalloc: every argument a CUDA tensor of the current device
+    (out: float64 with 3 entries).  Enqueued on the stream; nothing is allocated."""
+    L = lib()
+    copt, _fixed = _c_options(options or Options())
+    n_cams = cams.numel() // 9
+    n_pts = pts.numel() // 3
+    n_obs = obs_cam.numel()
+    st = L.ba_eval_cost_noalloc(ct.byref(copt), _stream_handle(stream), n_cams, cams.data_ptr(),
+                                n_pts, pts.data_ptr(), n_obs, obs_cam.data_ptr(), obs_pt.data_ptr(),
+                                obs_uv.data_ptr(), depth.data_ptr(),
+                                None if obs_mask is None else obs_mask.data_ptr(), out.data_ptr())
+    _check(st, "ba_eval_cost_noalloc")
+    return out

@@ -47,6 +47,8 @@ void set_error(const char* fmt, ...) {
 
 }  // namespace
 
+void bab::set_last_error_message(const char* msg) { g_last_error = msg; }
+
 struct ba_problem {
   ba_options opt{};
   std::vector<int32_t> fixed_list;

@@ -77,6 +77,9 @@ struct PcgArgs {
   double* pred_parts;           // [G] (+1 slot for the camera part)
 };
 
+// message returned by ba_last_error() for the calling thread
+void set_last_error_message(const char* msg);
+
 // ---- launchers (return cudaGetLastError of the launch) ----
 template <typename T>
 cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s);

@@ -1,0 +1,65 @@
+"""ba_eval_cost_noalloc: the FP64 cost of a state for callers that cannot allocate
+device memory (code captured into a CUDA graph, frameworks that own every
+device allocation).  It must agree with ba_eval_cost, the problem-based entry
+point, on the same state and active set, call after call.
+
+Kept in a file that pytest collects last, so a run that stops at the first
+failure has already run every other test."""
+import ctypes as ct
+
+import numpy as np
+import pytest
+
+from paper_2510_13310_b300 import ba, scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+
+def _dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def test_noalloc_cost_matches_problem_cost_on_two_calls():
+    sc = scenes.make_scene("small")
+    opts = ba.Options(invalid_depth_weight=1e-3)
+    prob = ba.Problem.from_scene(sc, opts)
+    prob.extract()
+    mask = prob.get_active()["obs_mask"]
+    obs = [_dev(sc.obs_cam, torch.int32), _dev(sc.obs_pt, torch.int32),
+           _dev(sc.obs_uv, torch.float64), _dev(sc.depth, torch.float64)]
+    m = _dev(mask, torch.uint8)
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for cams, pts in ((sc.cams0, sc.pts0), (sc.cams_gt, sc.pts_gt)):
+        F_ref, rmse_ref = prob.eval_cost(cams, pts)
+        ba.eval_cost_noalloc(_dev(cams, torch.float64), _dev(pts, torch.float64), *obs, out,
+                             obs_mask=m, options=opts)
+        torch.cuda.synchronize()
+        F, rmse, n = out.tolist()
+        assert F == pytest.approx(F_ref, rel=1e-12)
+        assert rmse == pytest.approx(rmse_ref, rel=1e-12)
+        assert n == int(mask.sum())
+
+
+def test_noalloc_rejects_oversize_and_unmapped_host_memory():
+    L = ba.lib()
+    copt, _fixed = ba._c_options(ba.Options())
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    C = 4097
+    cams = torch.zeros((C, 9), dtype=torch.float64, device="cuda")
+    pts = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    z_i = torch.zeros(1, dtype=torch.int32, device="cuda")
+    z_d = torch.zeros((1, 2), dtype=torch.float64, device="cuda")
+    st = L.ba_eval_cost_noalloc(ct.byref(copt), None, C, cams.data_ptr(), 1, pts.data_ptr(), 1,
+                                z_i.data_ptr(), z_i.data_ptr(), z_d.data_ptr(), z_d.data_ptr(),
+                                None, out.data_ptr())
+    assert st == ba.BA_ERR_INVALID_ARG
+    assert b"scratch limit" in L.ba_last_error()
+    host = np.zeros((4, 9))
+    st = L.ba_eval_cost_noalloc(ct.byref(copt), None, 4, host.ctypes.data, 1, pts.data_ptr(), 1,
+                                z_i.data_ptr(), z_i.data_ptr(), z_d.data_ptr(), z_d.data_ptr(),
+                                None, out.data_ptr())
+    assert st == ba.BA_ERR_INVALID_ARG
