@@ -90,16 +90,17 @@ struct ba_problem {
   int n_rank_tmp = 0;
 
   // normal equations and solver
-  void *W = nullptr, *V = nullptr, *gp = nullptr, *Vinv = nullptr, *z0 = nullptr;
+  void *W = nullptr, *wsgn = nullptr, *V = nullptr, *gp = nullptr, *Vinv = nullptr, *z0 = nullptr;
   void *Ug = nullptr, *Sg = nullptr, *cam_part = nullptr, *Ud = nullptr, *Dinv = nullptr;
-  void *bvec = nullptr, *dampc = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
-  void *p0 = nullptr, *p1 = nullptr, *partials = nullptr, *dp = nullptr;
+  void *bvec = nullptr, *dampc = nullptr, *x = nullptr, *z = nullptr;
+  void *partials = nullptr, *dp = nullptr;
   double *dots = nullptr, *pred_parts = nullptr, *eval_parts = nullptr;
   unsigned* bar = nullptr;
   int* err = nullptr;
   Scalars* sc = nullptr;
   Scalars* h_sc = nullptr;  // pinned
-  int pcg_grid = 0, eval_grid = 0, pcg_stages = 2;
+  int pcg_grid = 0, eval_grid = 0, pcg_stages = 2, pcg_own_max = 1;
+  int recompute = 0, cam_in_smem = 0, max_tiles_per_block = 1, g_rows = 0;
   size_t pcg_smem = 0;
 
   // LM bookkeeping
@@ -252,7 +253,8 @@ template <typename T>
 ba_status linearize_t(ba_problem* pb) {
   int s = pb->cur;
   LAUNCH(1, launch_pt_lin<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
-                             (T*)pb->W, (T*)pb->V, (T*)pb->gp, pb->stream));
+                             pb->recompute ? nullptr : (T*)pb->W, pb->recompute ? (T*)pb->wsgn : nullptr,
+                             (T*)pb->V, (T*)pb->gp, pb->stream));
   LAUNCH(1, launch_cam_accum<T>(pb->L, pb->mp, 0, (const T*)pb->camw[s], (const T*)pb->ptsw[s],
                                 pb->obs_act_co, pb->cam_act, pb->crank, nullptr, nullptr,
                                 (T*)pb->cam_part, pb->stream));
@@ -282,7 +284,15 @@ template <typename T>
 ba_status pcg_t(ba_problem* pb, double lambda) {
   int Cf = pb->n_cam_free;
   PcgArgs<T> a{};
+  a.recompute = pb->recompute;
   a.W = (const T*)pb->W;
+  a.wsgn = (const T*)pb->wsgn;
+  a.ptsw = (const T*)pb->ptsw[pb->cur];
+  a.camw = (const T*)pb->camw[pb->cur];
+  a.cam_in_smem = pb->cam_in_smem;
+  a.sw_valid = pb->mp.sw_valid;
+  a.sw_invalid = pb->mp.sw_invalid;
+  a.max_tiles_per_block = pb->max_tiles_per_block;
   a.descs = pb->descs;
   a.meta = pb->meta;
   a.n_tiles = pb->n_tiles;
@@ -295,11 +305,9 @@ ba_status pcg_t(ba_problem* pb, double lambda) {
   a.b = (const T*)pb->bvec;
   a.Cf = Cf;
   a.n = 9 * Cf;
+  a.own_max = pb->pcg_own_max;
   a.x = (T*)pb->x;
-  a.r = (T*)pb->r;
   a.z = (T*)pb->z;
-  a.p0 = (T*)pb->p0;
-  a.p1 = (T*)pb->p1;
   a.partials = (T*)pb->partials;
   a.dots = pb->dots;
   a.bar = pb->bar;
@@ -313,7 +321,8 @@ ba_status pcg_t(ba_problem* pb, double lambda) {
   a.lambda = lambda;
   a.dp = (T*)pb->dp;
   a.pred_parts = pb->pred_parts;
-  size_t smem = pcg_smem_bytes<T>(a.n, pb->C, pb->pcg_stages);
+  size_t smem = pcg_smem_bytes<T>(a.n, pb->C, pb->pcg_stages, pb->pcg_own_max, pb->recompute,
+                                  pb->cam_in_smem, pb->max_tiles_per_block);
   CU(cudaMemsetAsync(pb->bar, 0, sizeof(unsigned), pb->stream));
   LAUNCH(1, launch_pcg<T>(a, pb->pcg_grid, smem, pb->stream));
   LAUNCH(1, launch_pred_cams<T>(Cf, pb->cam_map, (const T*)pb->x, (const T*)pb->Ug, (const T*)pb->dampc,
@@ -527,71 +536,92 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       set_error("point %d has %d observations (limit %d)", p, pt_off[p + 1] - pt_off[p], kTileObs);
       return BA_ERR_INVALID_ARG;
     }
-  // tiles: whole points, at most kTileObs observations and kTileObs points
-  std::vector<int> tile_obs{0}, tile_pt{0};
+  // Warp ranges: consecutive whole points with at most 32 observations together,
+  // or one point with more.  Tiles: up to one warp range per PCG warp, at most
+  // kTileObs observations and kTileObs points.
+  std::vector<int> wr_pt{0};  // first point of each warp range
   {
-    int tobs = 0, tpts = 0;
+    int cur_obs = 0;
     for (int p = 0; p < P; ++p) {
       int len = pt_off[p + 1] - pt_off[p];
-      if (tobs + len > kTileObs || tpts + 1 > kTileObs) {
-        tile_obs.push_back(pt_off[p]);
-        tile_pt.push_back(p);
-        tobs = 0;
-        tpts = 0;
+      bool open = wr_pt.back() < p;  // the current range already holds points
+      if (open && (len > 32 || cur_obs + len > 32 || p - wr_pt.back() >= 32)) {
+        wr_pt.push_back(p);
+        cur_obs = 0;
       }
-      tobs += len;
-      tpts += 1;
+      cur_obs += len;
+      if (len > 32) {  // a long point closes its own range
+        wr_pt.push_back(p + 1);
+        cur_obs = 0;
+      }
     }
-    if (P > 0) {
-      tile_obs.push_back(N);
-      tile_pt.push_back(P);
-    }
+    if (wr_pt.back() != P) wr_pt.push_back(P);
   }
-  pb->n_tiles = (int)tile_obs.size() - 1;
-  // Per tile: W rows padded to a multiple of 4 (16-byte aligned copies) and a
-  // metadata record: camera of each observation, point offsets, the runs of
-  // equal cameras once the tile's observations are sorted by camera
-  // ((camera << 8) | start), and the tile-local positions in that order.
+  const int n_wr_total = (int)wr_pt.size() - 1;
+  std::vector<int> tile_wr{0};  // first warp range of each tile
+  {
+    int t_obs = 0, t_pts = 0, t_wr = 0;
+    for (int r = 0; r < n_wr_total; ++r) {
+      int r_obs = pt_off[wr_pt[r + 1]] - pt_off[wr_pt[r]], r_pts = wr_pt[r + 1] - wr_pt[r];
+      if (t_wr > 0 && (t_wr + 1 > pcg_warps() || t_obs + r_obs > kTileObs || t_pts + r_pts > kTileObs)) {
+        tile_wr.push_back(r);
+        t_obs = t_pts = t_wr = 0;
+      }
+      t_obs += r_obs;
+      t_pts += r_pts;
+      t_wr += 1;
+    }
+    if (tile_wr.back() != n_wr_total) tile_wr.push_back(n_wr_total);
+  }
+  pb->n_tiles = (int)tile_wr.size() - 1;
+  // Per tile: its metadata record (camera of each observation, point offsets,
+  // runs of equal cameras once the tile's observations are sorted by camera,
+  // warp-range offsets, positions in camera order, local point of each
+  // observation) and its descriptor.
   std::vector<TileDesc> descs((size_t)pb->n_tiles);
   std::vector<unsigned char> meta;
   std::vector<int> po_wrow((size_t)N);
-  {
-    int wrow = 0;
-    for (int t = 0; t < pb->n_tiles; ++t) {
-      int ob = tile_obs[t], oe = tile_obs[t + 1], pbeg = tile_pt[t], pend = tile_pt[t + 1];
-      int nobs = oe - ob, npts = pend - pbeg;
-      std::vector<int> cams_t(nobs), loc(nobs), poff(npts + 1);
-      for (int i = 0; i < nobs; ++i) {
-        cams_t[i] = h_oc[po[ob + i]];
-        loc[i] = i;
-        po_wrow[ob + i] = wrow + i;
-      }
-      for (int j = 0; j <= npts; ++j) poff[j] = pt_off[pbeg + j] - ob;
-      std::stable_sort(loc.begin(), loc.end(), [&](int x, int y) { return cams_t[x] < cams_t[y]; });
-      std::vector<unsigned> runs;
-      std::vector<uint8_t> cperm(nobs);
-      for (int j = 0; j < nobs; ++j) {
-        cperm[j] = (uint8_t)loc[j];
-        if (j == 0 || cams_t[loc[j]] != cams_t[loc[j - 1]])
-          runs.push_back(((unsigned)cams_t[loc[j]] << 8) | (unsigned)j);
-      }
-      TileDesc d{};
-      d.w_row = wrow;
-      d.n_obs = nobs;
-      d.pt_begin = pbeg;
-      d.n_pts = npts;
-      d.meta_off = (int)meta.size();
-      d.n_runs = (int)runs.size();
-      d.obs_begin = ob;
-      descs[t] = d;
-      size_t mb = (size_t)meta_bytes_of(nobs, npts, d.n_runs);
-      meta.resize(meta.size() + mb);
-      build_tile_meta(nobs, npts, d.n_runs, cams_t.data(), poff.data(), runs.data(), cperm.data(),
-                      meta.data() + d.meta_off);
-      wrow += (nobs + 3) & ~3;
+  for (int t = 0; t < pb->n_tiles; ++t) {
+    int r0 = tile_wr[t], r1 = tile_wr[t + 1];
+    int pbeg = wr_pt[r0], pend = wr_pt[r1];
+    int ob = pt_off[pbeg], oe = pt_off[pend];
+    int nobs = oe - ob, npts = pend - pbeg;
+    std::vector<int> cams_t(nobs), loc(nobs), poff(npts + 1), wr(r1 - r0 + 1);
+    std::vector<uint8_t> lid(nobs);
+    for (int i = 0; i < nobs; ++i) {
+      cams_t[i] = h_oc[po[ob + i]];
+      loc[i] = i;
+      po_wrow[ob + i] = ob + i;
     }
-    pb->w_rows = wrow;
+    for (int j = 0; j <= npts; ++j) poff[j] = pt_off[pbeg + j] - ob;
+    for (int j = 0; j < npts; ++j)
+      for (int i = poff[j]; i < poff[j + 1]; ++i) lid[i] = (uint8_t)j;
+    for (int r = r0; r <= r1; ++r) wr[r - r0] = pt_off[wr_pt[r]] - ob;
+    std::stable_sort(loc.begin(), loc.end(), [&](int x, int y) { return cams_t[x] < cams_t[y]; });
+    std::vector<unsigned> runs;
+    std::vector<uint8_t> cperm(nobs);
+    for (int j = 0; j < nobs; ++j) {
+      cperm[j] = (uint8_t)loc[j];
+      if (j == 0 || cams_t[loc[j]] != cams_t[loc[j - 1]])
+        runs.push_back(((unsigned)cams_t[loc[j]] << 8) | (unsigned)j);
+    }
+    TileDesc d{};
+    d.g_row = pb->g_rows;
+    pb->g_rows += (nobs + 3) & ~3;
+    d.w_row = ob;
+    d.n_obs = nobs;
+    d.pt_begin = pbeg;
+    d.n_pts = npts;
+    d.meta_off = (int)meta.size();
+    d.n_runs = (int)runs.size();
+    d.obs_begin = ob;
+    descs[t] = d;
+    size_t mb = (size_t)meta_bytes_of(nobs, npts, d.n_runs);
+    meta.resize(meta.size() + mb);
+    build_tile_meta(nobs, npts, d.n_runs, r1 - r0, cams_t.data(), poff.data(), runs.data(), wr.data(),
+                    cperm.data(), lid.data(), meta.data() + d.meta_off);
   }
+  pb->w_rows = N;
   // chunks: pieces of one camera's observations
   std::vector<int> chunk_obs{0}, chunk_cam, cam_chunk((size_t)C + 1, 0);
   for (int c = 0; c < C; ++c) {
@@ -713,7 +743,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     ST(dalloc(pb, &pb->camw64[s], (size_t)C * kCamStride));
     if (pb->fp64) pb->camw[s] = pb->camw64[s];
     else ST(dalloc_bytes(pb, &pb->camw[s], R * (size_t)C * kCamStride));
-    ST(dalloc_bytes(pb, &pb->ptsw[s], R * (size_t)P * 4));
+    ST(dalloc_bytes(pb, &pb->ptsw[s], R * ((size_t)P + 2) * 4));
+    CU(cudaMemset(pb->ptsw[s], 0, R * ((size_t)P + 2) * 4));
     ST(dalloc(pb, &pb->bits[s], (size_t)N));
   }
   if (C) CU(cudaMemcpy(pb->cams64[0], h_cams.data(), sizeof(double) * h_cams.size(), cudaMemcpyHostToDevice));
@@ -736,8 +767,16 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   if (N) CU(cudaMemset(pb->alive, 1, (size_t)N));
   if (N) CU(cudaMemset(pb->obs_act, 0, (size_t)N));
 
-  ST(dalloc_bytes(pb, &pb->W, R * 27 * ((size_t)pb->w_rows + 4)));
-  CU(cudaMemset(pb->W, 0, R * 27 * ((size_t)pb->w_rows + 4)));
+  // FP32 recomputes the W blocks inside the Schur matvec from a signed IRLS weight
+  // per observation; FP64 stores them (FP64 arithmetic is the scarce resource there)
+  pb->recompute = pb->fp64 ? 0 : 1;
+  if (pb->recompute) {
+    ST(dalloc_bytes(pb, &pb->wsgn, R * ((size_t)pb->g_rows + 4)));
+    CU(cudaMemset(pb->wsgn, 0, R * ((size_t)pb->g_rows + 4)));
+  } else {
+    ST(dalloc_bytes(pb, &pb->W, R * kWStride * ((size_t)pb->w_rows + 1)));
+    CU(cudaMemset(pb->W, 0, R * kWStride * ((size_t)pb->w_rows + 1)));
+  }
   ST(dalloc_bytes(pb, &pb->V, R * 6 * (size_t)P));
   ST(dalloc_bytes(pb, &pb->gp, R * 3 * (size_t)P));
   ST(dalloc_bytes(pb, &pb->Vinv, R * 6 * ((size_t)P + 2)));
@@ -750,7 +789,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   ST(dalloc_bytes(pb, &pb->Ud, R * 45 * (size_t)C));
   ST(dalloc_bytes(pb, &pb->Dinv, R * 81 * (size_t)C));
   ST(dalloc_bytes(pb, &pb->dampc, R * 9 * (size_t)C));
-  for (void** v : {&pb->bvec, &pb->x, &pb->r, &pb->z, &pb->p0, &pb->p1})
+  for (void** v : {&pb->bvec, &pb->x, &pb->z})
     ST(dalloc_bytes(pb, v, R * 9 * (size_t)C));
 
   // persistent PCG grid: every block resident (cooperative launch); double-buffered
@@ -758,12 +797,26 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   int n_max = 9 * C;
   int dev_smem_optin = 0;
   CU(cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pb->device));
-  pb->pcg_stages = 2;
+  // owned camera slice and tile count per block: at most ceil(x / min(SMs, tiles))
+  {
+    int gmin = std::max(1, std::min(pb->num_sms, pb->n_tiles));
+    pb->pcg_own_max = std::max(1, (C + gmin - 1) / gmin);
+    pb->max_tiles_per_block = std::max(1, (pb->n_tiles + gmin - 1) / gmin);
+  }
+  pb->cam_in_smem = (pb->recompute && R * (size_t)C * kCamStride <= 48 * 1024) ? 1 : 0;
+  pb->pcg_stages = pb->recompute ? 3 : 2;
   for (;;) {
-    pb->pcg_smem = pb->fp64 ? pcg_smem_bytes<double>(n_max, C, pb->pcg_stages)
-                            : pcg_smem_bytes<float>(n_max, C, pb->pcg_stages);
-    if (pb->pcg_smem <= (size_t)dev_smem_optin || pb->pcg_stages == 1) break;
-    pb->pcg_stages = 1;
+    pb->pcg_smem = pb->fp64 ? pcg_smem_bytes<double>(n_max, C, pb->pcg_stages, pb->pcg_own_max, pb->recompute,
+                                                     pb->cam_in_smem, pb->max_tiles_per_block)
+                            : pcg_smem_bytes<float>(n_max, C, pb->pcg_stages, pb->pcg_own_max, pb->recompute,
+                                                    pb->cam_in_smem, pb->max_tiles_per_block);
+    if (pb->pcg_smem <= (size_t)dev_smem_optin) break;
+    if (pb->cam_in_smem) {
+      pb->cam_in_smem = 0;
+      continue;
+    }
+    if (pb->pcg_stages == 1) break;
+    pb->pcg_stages -= 1;
   }
   if (pb->pcg_smem > (size_t)dev_smem_optin) {
     set_error("camera system of %d cameras needs %zu B of shared memory per block (limit %d)", C,
@@ -849,13 +902,33 @@ ba_status copy_out_linearization(ba_problem* pb, double* U, double* V, double* W
     if (gp && P) CU(cudaMemcpy(gp, og.data(), sizeof(double) * og.size(), cudaMemcpyDefault));
   }
   if (W && N) {
+    // in recompute mode the W blocks are never stored: form them into a scratch
+    // buffer with the same linearization kernel (inspection only)
+    T* wsrc = (T*)pb->W;
+    T* wtmp = nullptr;
+    T* scratch_v = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!wsrc) {
+      e = cudaMalloc(&wtmp, sizeof(T) * kWStride * ((size_t)N + 1));
+      if (e == cudaSuccess) e = cudaMalloc(&scratch_v, sizeof(T) * 9 * ((size_t)P + 1));
+      if (e == cudaSuccess) {
+        pb->launches += 1;
+        e = launch_pt_lin<T>(pb->L, pb->mp, (const T*)pb->camw[pb->cur], (const T*)pb->ptsw[pb->cur],
+                             pb->obs_act, wtmp, nullptr, scratch_v, scratch_v + 6 * (size_t)P, pb->stream);
+      }
+      wsrc = wtmp;
+    }
     double* tmp = nullptr;
-    CU(cudaMalloc(&tmp, sizeof(double) * 27 * (size_t)N));
-    pb->launches += 1;
-    cudaError_t e = launch_permute_rows<T>(pb->po_orig, pb->po_wrow, (const T*)pb->W, tmp, N, 27, pb->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(double) * 27 * (size_t)N);
+    if (e == cudaSuccess) {
+      pb->launches += 1;
+      e = launch_permute_rows<T>(pb->po_orig, pb->po_wrow, wsrc, kWStride, tmp, N, 27, pb->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(pb->stream);
     if (e == cudaSuccess) e = cudaMemcpy(W, tmp, sizeof(double) * 27 * (size_t)N, cudaMemcpyDefault);
     cudaFree(tmp);
+    cudaFree(wtmp);
+    cudaFree(scratch_v);
     CU(e);
   }
   return BA_OK;

@@ -8,6 +8,7 @@ namespace bab {
 constexpr int kTileObs = 256;      // max observations per point-order tile (and per point)
 constexpr int kChunkObs = 1024;    // max observations per camera-order chunk
 constexpr int kCamStride = 16;     // working camera record: R(9) t(3) f k1 k2 pad
+constexpr int kWStride = 28;       // W row: 9x3 block padded to 28 entries (16-byte rows)
 constexpr int kBlock = 256;
 
 // Packed upper triangle of a symmetric 9x9 block, row-major over i <= j.

@@ -13,7 +13,8 @@ namespace bab {
 // camera order) is a 16-byte aligned record at meta_off.
 struct TileDesc {
   int w_row, n_obs, pt_begin, n_pts;
-  int meta_off, n_runs, obs_begin, pad;
+  int meta_off, n_runs, obs_begin, g_row;  // g_row: first row of per-observation arrays
+                                           // padded to 4 rows per tile (16-byte aligned)
 };
 
 // Immutable observation layout built by ba_create.  "po" = point order (sorted by
@@ -48,7 +49,14 @@ struct ModelParams {
 
 template <typename T>
 struct PcgArgs {
-  const T* W;                   // tiled W rows
+  int recompute;                // 1: recompute Jacobian blocks from wsgn, points and cameras
+  const T* W;                   // stored W rows (recompute == 0)
+  const T* wsgn;                // signed IRLS weight per observation (recompute == 1)
+  const T* ptsw;                // working points [P+2][4] (recompute == 1)
+  const T* camw;                // working cameras [C][16] (recompute == 1)
+  int cam_in_smem;              // stage the camera table in shared memory
+  double sw_valid, sw_invalid;  // square roots of the depth-row weights
+  int max_tiles_per_block;
   const TileDesc* descs;
   const unsigned char* meta;    // tile metadata records
   int n_tiles;
@@ -60,7 +68,8 @@ struct PcgArgs {
   const T* Dinv;
   const T* b;
   int Cf, n;
-  T *x, *r, *z, *p0, *p1;
+  int own_max;                  // largest owned camera slice of a block
+  T *x, *z;
   T* partials;
   double* dots;                 // [2][G][4]
   unsigned* bar;
@@ -112,7 +121,7 @@ int rank_blocks(int n);
 
 template <typename T>
 cudaError_t launch_pt_lin(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
-                          const uint8_t* obs_act, T* W, T* V, T* gp, cudaStream_t s);
+                          const uint8_t* obs_act, T* W, T* wsgn, T* V, T* gp, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cam_accum(const Layout& L, const ModelParams& mp, int mode, const T* camw,
                              const T* ptsw, const uint8_t* act_co, const uint8_t* cam_act,
@@ -129,13 +138,17 @@ cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* 
 template <typename T>
 cudaError_t launch_pcg(const PcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
 template <typename T>
-size_t pcg_smem_bytes(int n, int C, int stages);
+size_t pcg_smem_bytes(int n, int C, int stages, int own_max, int recompute, int cam_in_smem,
+                      int max_tiles_per_block);
 template <typename T>
 const void* pcg_kernel_ptr();
 int pcg_threads();
+int pcg_warps();
+int pcg_max_stages();
 int meta_bytes_of(int n_obs, int n_pts, int n_runs);
-void build_tile_meta(int n_obs, int n_pts, int n_runs, const int* cams, const int* poff,
-                     const unsigned* runs, const uint8_t* cperm, unsigned char* out);
+void build_tile_meta(int n_obs, int n_pts, int n_runs, int n_wr, const int* cams, const int* poff,
+                     const unsigned* runs, const int* wr, const uint8_t* cperm, const uint8_t* lid,
+                     unsigned char* out);
 template <typename T>
 cudaError_t launch_pred_cams(int Cf, const int* cam_map, const T* x, const T* Ug, const T* dampc,
                              double lambda, double* pred_parts, int offset, cudaStream_t s);
@@ -152,7 +165,7 @@ cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_
 cudaError_t launch_permute_u8(const int* orig, const uint8_t* src, uint8_t* dst, int N,
                               cudaStream_t s);
 template <typename T>
-cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, double* dst, int N,
-                                int width, cudaStream_t s);
+cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, int src_stride,
+                                double* dst, int N, int width, cudaStream_t s);
 
 }  // namespace bab

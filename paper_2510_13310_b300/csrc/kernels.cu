@@ -399,14 +399,18 @@ __device__ __forceinline__ void load_pt(const T* __restrict__ ptsw, int p, T& x,
   z = v.z;
 }
 
+// W: stored W rows (nullptr when the matvec recomputes the Jacobian); wsgn: per
+// observation IRLS weight rho', negated when the observation has no depth prior
+// (0 for inactive observations), in the padded per-tile layout (nullptr if unused).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, const T* __restrict__ camw,
                                                    const T* __restrict__ ptsw,
                                                    const uint8_t* __restrict__ obs_act, T* __restrict__ W,
-                                                   T* __restrict__ V, T* __restrict__ gp) {
+                                                   T* __restrict__ wsgn, T* __restrict__ V,
+                                                   T* __restrict__ gp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ws = reinterpret_cast<T*>(smem_raw);  // [kTileObs][27]
-  T* Vs = Ws + kTileObs * 27;              // [kTileObs][9]
+  T* Ws = reinterpret_cast<T*>(smem_raw);  // [kTileObs][kWStride]
+  T* Vs = Ws + kTileObs * kWStride;        // [kTileObs][9]
   const TileDesc d = L.descs[blockIdx.x];
   int ob = d.obs_begin, n = d.n_obs;
   int pb = d.pt_begin, pe = d.pt_begin + d.n_pts;
@@ -414,13 +418,14 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
   const T* tauw = reinterpret_cast<const T*>(L.po_tauw);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     int k = ob + i;
-    T* wrow = Ws + 27 * i;
+    T* wrow = Ws + kWStride * i;
     T* vrow = Vs + 9 * i;
     if (!obs_act[k]) {
 #pragma unroll
-      for (int j = 0; j < 27; ++j) wrow[j] = T(0);
+      for (int j = 0; j < kWStride; ++j) wrow[j] = T(0);
 #pragma unroll
       for (int j = 0; j < 9; ++j) vrow[j] = T(0);
+      if (wsgn) wsgn[(size_t)d.g_row + i] = T(0);
       continue;
     }
     T cw[kCamStride];
@@ -433,11 +438,15 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
     linearize_obs<T>(cw, X0, X1, X2, uvw[2 * (size_t)k], uvw[2 * (size_t)k + 1], tau, sw, (T)mp.cx,
                      (T)mp.cy, (T)mp.huber, o);
     T w = o.wrob;
+    if (wsgn) wsgn[(size_t)d.g_row + i] = tau > T(0) ? w : -w;
+    if (W) {
 #pragma unroll
-    for (int a = 0; a < 9; ++a)
+      for (int a = 0; a < 9; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
-        wrow[3 * a + b] = w * (o.Jc[0][a] * o.Jp[0][b] + o.Jc[1][a] * o.Jp[1][b] + o.Jc[2][a] * o.Jp[2][b]);
+        for (int b = 0; b < 3; ++b)
+          wrow[3 * a + b] = w * (o.Jc[0][a] * o.Jp[0][b] + o.Jc[1][a] * o.Jp[1][b] + o.Jc[2][a] * o.Jp[2][b]);
+      wrow[27] = T(0);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -447,8 +456,10 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
     }
   }
   __syncthreads();
-  T* Wdst = W + 27 * (size_t)d.w_row;
-  for (int j = threadIdx.x; j < 27 * n; j += blockDim.x) Wdst[j] = Ws[j];
+  if (W) {
+    T* Wdst = W + kWStride * (size_t)d.w_row;
+    for (int j = threadIdx.x; j < kWStride * n; j += blockDim.x) Wdst[j] = Ws[j];
+  }
   for (int p = pb + threadIdx.x; p < pe; p += blockDim.x) {
     T acc[9];
 #pragma unroll
@@ -465,15 +476,15 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
 
 template <typename T>
 cudaError_t launch_pt_lin(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
-                          const uint8_t* obs_act, T* W, T* V, T* gp, cudaStream_t s) {
+                          const uint8_t* obs_act, T* W, T* wsgn, T* V, T* gp, cudaStream_t s) {
   if (L.n_tiles == 0) return cudaSuccess;
-  size_t smem = sizeof(T) * kTileObs * 36;
+  size_t smem = sizeof(T) * kTileObs * (kWStride + 9);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_pt_lin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_pt_lin<T><<<L.n_tiles, kBlock, smem, s>>>(L, mp, camw, ptsw, obs_act, W, V, gp);
+  k_pt_lin<T><<<L.n_tiles, kBlock, smem, s>>>(L, mp, camw, ptsw, obs_act, W, wsgn, V, gp);
   return cudaGetLastError();
 }
 
@@ -886,22 +897,23 @@ cudaError_t launch_permute_u8(const int* orig, const uint8_t* src, uint8_t* dst,
 
 template <typename T>
 __global__ void k_permute_rows(const int* __restrict__ orig, const int* __restrict__ row,
-                               const T* __restrict__ src, double* __restrict__ dst, int N, int width) {
+                               const T* __restrict__ src, int src_stride, double* __restrict__ dst,
+                               int N, int width) {
   long long tot = (long long)N * width;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
     int k = (int)(i / width), j = (int)(i - (long long)k * width);
     size_t r = row ? (size_t)row[k] : (size_t)k;
-    dst[(size_t)orig[k] * width + j] = (double)src[r * width + j];
+    dst[(size_t)orig[k] * width + j] = (double)src[r * src_stride + j];
   }
 }
 
 template <typename T>
-cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, double* dst, int N,
-                                int width, cudaStream_t s) {
+cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, int src_stride,
+                                double* dst, int N, int width, cudaStream_t s) {
   long long tot = (long long)N * width;
   if (tot > 0) {
     long long g = (tot + 255) / 256;
-    k_permute_rows<T><<<(int)(g > 65535 ? 65535 : g), 256, 0, s>>>(orig, row, src, dst, N, width);
+    k_permute_rows<T><<<(int)(g > 65535 ? 65535 : g), 256, 0, s>>>(orig, row, src, src_stride, dst, N, width);
   }
   return cudaGetLastError();
 }
@@ -913,7 +925,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, d
   template cudaError_t launch_prep_cams<T>(const double*, T*, double*, int, cudaStream_t);          \
   template cudaError_t launch_prep_pts<T>(const double*, T*, int, cudaStream_t);                    \
   template cudaError_t launch_pt_lin<T>(const Layout&, const ModelParams&, const T*, const T*,      \
-                                        const uint8_t*, T*, T*, T*, cudaStream_t);                  \
+                                        const uint8_t*, T*, T*, T*, T*, cudaStream_t);              \
   template cudaError_t launch_cam_accum<T>(const Layout&, const ModelParams&, int, const T*,        \
                                            const T*, const uint8_t*, const uint8_t*, const int*,    \
                                            const T*, const T*, T*, cudaStream_t);                   \
@@ -929,8 +941,8 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, d
                                            cudaStream_t);                                           \
   template cudaError_t launch_scatter_cams<T>(int, const int*, const T*, double*, cudaStream_t);    \
   template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);              \
-  template cudaError_t launch_permute_rows<T>(const int*, const int*, const T*, double*, int, int,    \
-                                              cudaStream_t);
+  template cudaError_t launch_permute_rows<T>(const int*, const int*, const T*, int, double*, int,    \
+                                              int, cudaStream_t);
 
 BAB_INST(float)
 BAB_INST(double)
