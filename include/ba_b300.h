@@ -71,7 +71,13 @@ typedef struct {
   int pcg_max_iters;           /* PCG cap (500) */
   const int32_t* fixed_cams;   /* host array of gauge cameras held constant ({0}) */
   int n_fixed;
+  int solver;                  /* reduced camera system: BA_SOLVER_AUTO (explicit when
+                                  9 x cameras <= 4608), BA_SOLVER_IMPLICIT (matrix-free
+                                  Schur matvec), BA_SOLVER_EXPLICIT (dense S formed per
+                                  damping value, PCG on it) */
 } ba_options;
+
+enum { BA_SOLVER_AUTO = 0, BA_SOLVER_IMPLICIT = 1, BA_SOLVER_EXPLICIT = 2 };
 
 typedef struct {
   double cost;        /* F(x) = 1/2 sum rho(|r_k|^2) over the iteration's active set */

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libba_b300.so")
 BA_OK, BA_ERR_INVALID_ARG, BA_ERR_CUDA, BA_ERR_OOM = 0, 1, 2, 3
 BA_ERR_NOT_CONVERGED, BA_ERR_NONFINITE, BA_ERR_STATE, BA_ERR_TIMEOUT = 4, 5, 6, 7
 BA_FP64, BA_FP32 = 0, 1
+BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT = 0, 1, 2
 
 # every symbol include/ba_b300.h declares
 EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
@@ -36,7 +37,7 @@ class _Options(ct.Structure):
                 ("drop_residual_px", ct.c_double), ("min_cam_obs", ct.c_int),
                 ("min_pt_obs", ct.c_int), ("lambda0", ct.c_double), ("pcg_rel_tol", ct.c_double),
                 ("pcg_max_iters", ct.c_int), ("fixed_cams", ct.POINTER(ct.c_int32)),
-                ("n_fixed", ct.c_int)]
+                ("n_fixed", ct.c_int), ("solver", ct.c_int)]
 
 
 class _IterInfo(ct.Structure):
@@ -133,6 +134,7 @@ class Options:
     pcg_rel_tol: float = 1e-6
     pcg_max_iters: int = 500
     fixed_cams: tuple = (0,)
+    solver: int = BA_SOLVER_AUTO
 
 
 class _Arr:
@@ -183,7 +185,7 @@ class Problem:
         copt = _Options(o.precision, o.img_w, o.img_h, o.cx, o.cy, o.huber_delta, o.depth_weight,
                         o.invalid_depth_weight, o.min_depth, o.extract_every, o.drop_residual_px,
                         o.min_cam_obs, o.min_pt_obs, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
-                        self._fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(self._fixed))
+                        self._fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(self._fixed), o.solver)
         arrs = [_Arr(cams, np.float64), _Arr(pts, np.float64), _Arr(obs_cam, np.int32),
                 _Arr(obs_pt, np.int32), _Arr(obs_uv, np.float64), _Arr(depth, np.float64)]
         self.n_cams = int(np.prod(arrs[0].obj.shape)) // 9
@@ -299,7 +301,7 @@ def _c_options(o: Options):
     c = _Options(o.precision, o.img_w, o.img_h, o.cx, o.cy, o.huber_delta, o.depth_weight,
                  o.invalid_depth_weight, o.min_depth, o.extract_every, o.drop_residual_px,
                  o.min_cam_obs, o.min_pt_obs, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
-                 fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(fixed))
+                 fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(fixed), o.solver)
     return c, fixed
 
 

@@ -101,6 +101,12 @@ struct ba_problem {
   Scalars* h_sc = nullptr;  // pinned
   int pcg_grid = 0, eval_grid = 0, pcg_stages = 2, pcg_own_max = 1;
   int recompute = 0, cam_in_smem = 0, max_tiles_per_block = 1, g_rows = 0;
+  // explicit reduced camera system
+  bool explicit_S = false;
+  void *Shat = nullptr, *Dblk = nullptr, *Sacc = nullptr;
+  double* dscale = nullptr;
+  int spcg_grid = 0, spcg_own_max = 1, spcg_rows_in_smem = 0, bs_grid = 1;
+  size_t spcg_smem = 0;
   size_t pcg_smem = 0;
 
   // LM bookkeeping
@@ -252,9 +258,10 @@ ba_status run_extraction(ba_problem* pb, bool drop, int* rounds_out) {
 template <typename T>
 ba_status linearize_t(ba_problem* pb) {
   int s = pb->cur;
+  // W rows are stored when the matvec streams them or the explicit system is formed
   LAUNCH(1, launch_pt_lin<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
-                             pb->recompute ? nullptr : (T*)pb->W, pb->recompute ? (T*)pb->wsgn : nullptr,
-                             (T*)pb->V, (T*)pb->gp, pb->stream));
+                             (pb->recompute && !pb->explicit_S) ? nullptr : (T*)pb->W,
+                             pb->recompute ? (T*)pb->wsgn : nullptr, (T*)pb->V, (T*)pb->gp, pb->stream));
   LAUNCH(1, launch_cam_accum<T>(pb->L, pb->mp, 0, (const T*)pb->camw[s], (const T*)pb->ptsw[s],
                                 pb->obs_act_co, pb->cam_act, pb->crank, nullptr, nullptr,
                                 (T*)pb->cam_part, pb->stream));
@@ -273,8 +280,52 @@ ba_status schur_t(ba_problem* pb, double lambda) {
                                 (const T*)pb->z0, (T*)pb->cam_part, pb->stream));
   LAUNCH(1, launch_cam_reduce<T>(pb->L, (const T*)pb->cam_part, (T*)pb->Sg, pb->stream));
   LAUNCH(1, launch_schur_diag<T>(pb->n_cam_free, pb->cam_map, (const T*)pb->Ug, (const T*)pb->Sg, lambda,
-                                 (T*)pb->Ud, (T*)pb->Dinv, (T*)pb->bvec, (T*)pb->dampc, pb->err,
-                                 pb->stream));
+                                 (T*)pb->Ud, (T*)pb->Dinv, (T*)pb->bvec, (T*)pb->dampc,
+                                 pb->explicit_S ? (T*)pb->Dblk : nullptr, pb->err, pb->stream));
+  return BA_OK;
+}
+
+// (d) with an explicit reduced camera system: form S^ (scaled), PCG on it, then
+// the point back-substitution and the predicted decrease.
+template <typename T>
+ba_status spcg_t(ba_problem* pb, double lambda) {
+  int Cf = pb->n_cam_free, s = pb->cur;
+  CU(cudaMemsetAsync(&pb->sc->pcg_iters, 0, sizeof(int), pb->stream));
+  CU(cudaMemsetAsync(&pb->sc->pcg_rel_res, 0, sizeof(double), pb->stream));
+  if (Cf > 0) {
+    LAUNCH(5, launch_form_S<T>(pb->L, (const T*)pb->W, pb->obs_act_co, pb->obs_act, pb->crank, pb->cam_map,
+                               (const T*)pb->Vinv, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale, Cf,
+                               pb->Sacc, (T*)pb->Shat, pb->num_sms, pb->stream));
+    SpcgArgs<T> a{};
+    a.Shat = (const T*)pb->Shat;
+    a.Dinv = (const T*)pb->Dinv;
+    a.dscale = pb->dscale;
+    a.b = (const T*)pb->bvec;
+    a.Cf = Cf;
+    a.n = 9 * Cf;
+    a.own_max = pb->spcg_own_max;
+    a.rows_in_smem = pb->spcg_rows_in_smem;
+    a.x = (T*)pb->x;
+    a.z = (T*)pb->z;
+    a.dots = pb->dots;
+    a.bar = pb->bar;
+    a.err = pb->err;
+    a.sc = pb->sc;
+    a.tol = pb->opt.pcg_rel_tol;
+    a.max_iters = pb->opt.pcg_max_iters;
+    a.timeout_ns = 2000000000LL;
+    size_t smem = spcg_smem_bytes<T>(a.n, a.own_max, a.rows_in_smem);
+    int grid = std::min(pb->spcg_grid, Cf);
+    CU(cudaMemsetAsync(pb->bar, 0, sizeof(unsigned), pb->stream));
+    LAUNCH(1, launch_spcg<T>(a, grid, smem, pb->stream));
+  }
+  LAUNCH(1, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
+                                  pb->pt_act, pb->crank, (const T*)pb->x, (const T*)pb->Vinv, (const T*)pb->V,
+                                  (const T*)pb->gp, lambda, (T*)pb->dp, pb->pred_parts, pb->bs_grid,
+                                  pb->stream));
+  LAUNCH(1, launch_pred_cams<T>(Cf, pb->cam_map, (const T*)pb->x, (const T*)pb->Ug, (const T*)pb->dampc,
+                                lambda, pb->pred_parts, pb->bs_grid, pb->stream));
+  LAUNCH(1, launch_reduce_pred(pb->pred_parts, pb->bs_grid + 1, pb->sc, pb->stream));
   return BA_OK;
 }
 
@@ -282,6 +333,7 @@ ba_status schur_t(ba_problem* pb, double lambda) {
 // predicted decrease, for the Schur terms prepared at damping lambda.
 template <typename T>
 ba_status pcg_t(ba_problem* pb, double lambda) {
+  if (pb->explicit_S) return spcg_t<T>(pb, lambda);
   int Cf = pb->n_cam_free;
   PcgArgs<T> a{};
   a.recompute = pb->recompute;
@@ -770,10 +822,23 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   // FP32 recomputes the W blocks inside the Schur matvec from a signed IRLS weight
   // per observation; FP64 stores them (FP64 arithmetic is the scarce resource there)
   pb->recompute = pb->fp64 ? 0 : 1;
+  {
+    int so = opts->solver;
+    if (so != BA_SOLVER_AUTO && so != BA_SOLVER_IMPLICIT && so != BA_SOLVER_EXPLICIT) {
+      set_error("unknown solver %d", so);
+      return BA_ERR_INVALID_ARG;
+    }
+    pb->explicit_S = so == BA_SOLVER_EXPLICIT || (so == BA_SOLVER_AUTO && 9 * C <= 4608);
+    if (pb->explicit_S && (size_t)81 * C * C * (R + 8) > ((size_t)8 << 30)) {
+      set_error("explicit reduced camera system of order %d is too large", 9 * C);
+      return BA_ERR_INVALID_ARG;
+    }
+  }
   if (pb->recompute) {
     ST(dalloc_bytes(pb, &pb->wsgn, R * ((size_t)pb->g_rows + 4)));
     CU(cudaMemset(pb->wsgn, 0, R * ((size_t)pb->g_rows + 4)));
-  } else {
+  }
+  if (!pb->recompute || pb->explicit_S) {
     ST(dalloc_bytes(pb, &pb->W, R * kWStride * ((size_t)pb->w_rows + 1)));
     CU(cudaMemset(pb->W, 0, R * kWStride * ((size_t)pb->w_rows + 1)));
   }
@@ -837,7 +902,32 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   ST(dalloc(pb, &pb->dots, (size_t)2 * 4 * pb->pcg_grid));
   ST(dalloc(pb, &pb->bar, 1));
   ST(dalloc(pb, &pb->err, 1));
-  ST(dalloc(pb, &pb->pred_parts, (size_t)pb->pcg_grid + 1));
+  // explicit reduced camera system (solver option; automatic for up to 512 cameras)
+  if (pb->explicit_S && n_max > 0) {
+    ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * n_max));
+    ST(dalloc_bytes(pb, &pb->Sacc, (size_t)form_acc_bytes(pb->fp64) * n_max * n_max));
+    ST(dalloc(pb, &pb->dscale, (size_t)2 * n_max));  // D, then 1/D in the working precision
+    ST(dalloc_bytes(pb, &pb->Dblk, R * 45 * (size_t)C));
+    pb->spcg_grid = std::max(1, std::min(pb->num_sms, C));
+    pb->spcg_own_max = std::max(1, (C + pb->spcg_grid - 1) / pb->spcg_grid);
+    pb->spcg_rows_in_smem = 1;
+    for (;;) {
+      pb->spcg_smem = pb->fp64 ? spcg_smem_bytes<double>(n_max, pb->spcg_own_max, pb->spcg_rows_in_smem)
+                               : spcg_smem_bytes<float>(n_max, pb->spcg_own_max, pb->spcg_rows_in_smem);
+      if (pb->spcg_smem <= (size_t)dev_smem_optin || !pb->spcg_rows_in_smem) break;
+      pb->spcg_rows_in_smem = 0;
+    }
+    const void* sfn = pb->fp64 ? spcg_kernel_ptr<double>() : spcg_kernel_ptr<float>();
+    CU(cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb->spcg_smem));
+    int sper = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, sfn, spcg_threads(), pb->spcg_smem));
+    if (sper < 1 || pb->spcg_grid > sper * pb->num_sms) {
+      set_error("explicit PCG kernel cannot be resident");
+      return BA_ERR_INVALID_ARG;
+    }
+  }
+  pb->bs_grid = std::max(1, std::min(pb->num_sms * 8, (P + 255) / 256));
+  ST(dalloc(pb, &pb->pred_parts, (size_t)std::max(pb->pcg_grid, pb->bs_grid) + 1));
   pb->eval_grid = std::max(1, std::min(pb->num_sms * 8, (N + kBlock - 1) / kBlock));
   ST(dalloc(pb, &pb->eval_parts, (size_t)3 * pb->eval_grid));
   ST(dalloc(pb, &pb->sc, 1));
@@ -963,6 +1053,7 @@ void ba_default_options(ba_options* o) {
   o->pcg_max_iters = 500;
   o->fixed_cams = kGauge;
   o->n_fixed = 1;
+  o->solver = BA_SOLVER_AUTO;
 }
 
 ba_status ba_create(const ba_options* opts, void* stream, int64_t n_cams, const double* cams,

@@ -71,6 +71,64 @@ __device__ T block_sum(T v, T* red /* >= 32 entries */) {
   return s;
 }
 
+// FP64 is scarce on B300 (a small fraction of the FP32 rate), so FP64 sums run
+// in one warp only.  warp0_sum2: sum of per-thread values a, b held by threads
+// [0, count) (others ignored); every thread gets both results.
+// buf: >= 2 * count doubles of shared scratch; out: 2 doubles of shared scratch.
+__device__ __forceinline__ void warp0_sum2(double a, double b, int count, double* buf, double* out,
+                                           double& ra, double& rb) {
+  if ((int)threadIdx.x < count) {
+    buf[threadIdx.x] = a;
+    buf[count + threadIdx.x] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double sa = 0.0, sb = 0.0;
+    for (int i = threadIdx.x; i < count; i += 32) {
+      sa += buf[i];
+      sb += buf[count + i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if (threadIdx.x == 0) {
+      out[0] = sa;
+      out[1] = sb;
+    }
+  }
+  __syncthreads();
+  ra = out[0];
+  rb = out[1];
+}
+
+// Sum of slots s0, s1 of the G per-block records (4 doubles each), by warp 0,
+// broadcast to the block.  Fixed order: every block gets identical results.
+__device__ __forceinline__ void warp0_sum_slots(const double* region, int G, int s0, int s1,
+                                                double* out, double& r0, double& r1) {
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0;
+    for (int g = threadIdx.x; g < G; g += 32) {
+      a += region[4 * g + s0];
+      b += region[4 * g + s1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+      out[0] = a;
+      out[1] = b;
+    }
+  }
+  __syncthreads();
+  r0 = out[0];
+  r1 = out[1];
+  __syncthreads();
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -86,6 +86,23 @@ struct PcgArgs {
   double* pred_parts;           // [G] (+1 slot for the camera part)
 };
 
+template <typename T>
+struct SpcgArgs {
+  const T* Shat;                // scaled reduced camera system [n][n]
+  const T* Dinv;                // unscaled block-Jacobi inverses [Cf][81]
+  const double* dscale;         // D = sqrt(diag U*) [n]
+  const T* b;                   // Schur right-hand side [n]
+  int Cf, n, own_max, rows_in_smem;
+  T *x, *z;
+  double* dots;                 // [2][G][4]
+  unsigned* bar;
+  int* err;
+  Scalars* sc;
+  double tol;
+  int max_iters;
+  long long timeout_ns;
+};
+
 // message returned by ba_last_error() for the calling thread
 void set_last_error_message(const char* msg);
 
@@ -134,7 +151,24 @@ cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_ac
                             T* Vinv, T* z0, int* err, cudaStream_t s);
 template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
-                              T* Ud, T* Dinv, T* b, T* dampc, int* err, cudaStream_t s);
+                              T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, int* err, cudaStream_t s);
+template <typename T>
+cudaError_t launch_form_S(const Layout& L, const T* W, const uint8_t* act_co, const uint8_t* act_po,
+                          const int* crank, const int* cam_map, const T* Vinv, const T* Ud, const T* Dblk,
+                          double* dscale, int Cf, void* Sacc, T* Shat, int num_sms, cudaStream_t s);
+int form_acc_bytes(int fp64);
+template <typename T>
+size_t spcg_smem_bytes(int n, int own_max, int rows_in_smem);
+template <typename T>
+const void* spcg_kernel_ptr();
+template <typename T>
+cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
+int spcg_threads();
+template <typename T>
+cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
+                               const uint8_t* act_po, const uint8_t* pt_act, const int* crank, const T* x,
+                               const T* Vinv, const T* V, const T* gp, double lambda, T* dp,
+                               double* pred_parts, int grid, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pcg(const PcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
 template <typename T>

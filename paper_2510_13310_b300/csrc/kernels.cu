@@ -684,7 +684,8 @@ cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_ac
 template <typename T>
 __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* __restrict__ Ug,
                              const T* __restrict__ Sg, double lambda, T* __restrict__ Ud,
-                             T* __restrict__ Dinv, T* __restrict__ b, T* __restrict__ dampc, int* err) {
+                             T* __restrict__ Dinv, T* __restrict__ b, T* __restrict__ dampc,
+                             T* __restrict__ Dblk, int* err) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= Cf) return;
   int c = cam_map[f];
@@ -703,6 +704,7 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
       double v = uij - (double)sch[sym9(i, j)];
       D[i][j] = v;
       D[j][i] = v;
+      if (Dblk) Dblk[45 * (size_t)f + sym9(i, j)] = (T)v;
     }
     b[9 * (size_t)f + i] = (T)(-(double)u[45 + i] + (double)sch[45 + i]);
   }
@@ -750,8 +752,8 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
 
 template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
-                              T* Ud, T* Dinv, T* b, T* dampc, int* err, cudaStream_t s) {
-  if (Cf > 0) k_schur_diag<T><<<(Cf + 63) / 64, 64, 0, s>>>(Cf, cam_map, Ug, Sg, lambda, Ud, Dinv, b, dampc, err);
+                              T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, int* err, cudaStream_t s) {
+  if (Cf > 0) k_schur_diag<T><<<(Cf + 63) / 64, 64, 0, s>>>(Cf, cam_map, Ug, Sg, lambda, Ud, Dinv, b, dampc, Dblk, err);
   return cudaGetLastError();
 }
 
@@ -933,7 +935,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
   template cudaError_t launch_damp_pts<T>(int, const T*, const T*, const uint8_t*, double, T*, T*,  \
                                           int*, cudaStream_t);                                      \
   template cudaError_t launch_schur_diag<T>(int, const int*, const T*, const T*, double, T*, T*,    \
-                                            T*, T*, int*, cudaStream_t);                            \
+                                            T*, T*, T*, int*, cudaStream_t);                        \
   template cudaError_t launch_pred_cams<T>(int, const int*, const T*, const T*, const T*, double,   \
                                            double*, int, cudaStream_t);                             \
   template cudaError_t launch_candidate<T>(int, int, const int*, const T*, const T*, const double*, \

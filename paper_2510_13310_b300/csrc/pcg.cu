@@ -123,7 +123,7 @@ size_t pcg_smem_bytes(int n, int C, int stages, int own_max, int recompute, int 
   size_t b = (size_t)stages * L.bytes;
   b += kMaxStages * sizeof(uint64_t);
   b += sizeof(TileDesc) * (size_t)max_tiles_per_block;
-  b += sizeof(double) * 32;
+  b += sizeof(double) * (2 * kPcgThreads + 8);
   b += sizeof(T) * kTileObs * 9;                          // vb
   b += sizeof(T) * kPcgThreads;                           // osum
   b += sizeof(T) * (size_t)n * 2;                         // xs, ys
@@ -145,7 +145,7 @@ __device__ PcgSmem<T> carve(unsigned char* base, const PcgArgs<T>& a) {
   s.dtab = reinterpret_cast<TileDesc*>(p);
   p += sizeof(TileDesc) * (size_t)a.max_tiles_per_block;
   s.dred = reinterpret_cast<double*>(p);
-  p += sizeof(double) * 32;
+  p += sizeof(double) * (2 * kPcgThreads + 8);
   s.vb = reinterpret_cast<T*>(p);
   p += sizeof(T) * kTileObs * 9;
   s.osum = reinterpret_cast<T*>(p);
@@ -566,6 +566,8 @@ __global__ void __launch_bounds__(kPcgThreads, REC ? 2 : 1) k_pcg(PcgArgs<T> a) 
   const int n = a.n;
   const int f0 = (int)(((long long)a.Cf * bid) / G), f1 = (int)(((long long)a.Cf * (bid + 1)) / G);
   const int e0 = 9 * f0, ne = 9 * (f1 - f0);
+  const int cnt = min(ne, (int)blockDim.x);
+  double* dout = sm.dred + 2 * kPcgThreads;
   unsigned epoch = 0;
   Pipe pp{0, 0};
   double unused = 0.0;
@@ -606,16 +608,16 @@ __global__ void __launch_bounds__(kPcgThreads, REC ? 2 : 1) k_pcg(PcgArgs<T> a) 
   int dph = 0;
   auto dregion = [&](int ph) { return a.dots + (size_t)(ph & 1) * 4 * G; };
   {
-    double s0 = block_sum(loc_rz, sm.dred);
-    double s1 = block_sum(loc_bb, sm.dred);
+    double s0, s1;
+    warp0_sum2(loc_rz, loc_bb, cnt, sm.dred, dout, s0, s1);
     if (tid == 0) {
       dregion(dph)[4 * bid + 0] = s0;
       dregion(dph)[4 * bid + 1] = s1;
     }
   }
   if (!grid_barrier(a.bar, (++epoch) * G, a.err, a.timeout_ns)) return;
-  double rz = sum_dots(dregion(dph), 0, G, sm.dred);
-  double bb = sum_dots(dregion(dph), 1, G, sm.dred);
+  double rz, bb;
+  warp0_sum_slots(dregion(dph), G, 0, 1, dout + 4, rz, bb);
   ++dph;
   double bnorm = sqrt(bb);
   int it = 0;
@@ -624,11 +626,24 @@ __global__ void __launch_bounds__(kPcgThreads, REC ? 2 : 1) k_pcg(PcgArgs<T> a) 
   bool first = true;
   while (bnorm > 0.0 && it < a.max_iters) {
     walk_prologue<T, REC>(a, sm, pp);
-    // ---- p = z (first) or z + beta p, in every block's own copy; clear the partial
-    for (int e = tid; e < n; e += blockDim.x) {
-      T zv = a.z[e];
-      sm.xs[e] = first ? zv : (T)((double)zv + beta * (double)sm.xs[e]);
-      sm.ys[e] = T(0);
+    // ---- p = z (first) or z + beta p, in every block's own copy; clear the partial.
+    // Every load of z is issued before any use.
+    for (int base = 0; base < n; base += 4 * (int)blockDim.x) {
+      T zv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int e = base + u * blockDim.x + tid;
+        zv[u] = e < n ? a.z[e] : T(0);
+      }
+      const T bt = (T)beta;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int e = base + u * blockDim.x + tid;
+        if (e < n) {
+          sm.xs[e] = first ? zv[u] : zv[u] + bt * sm.xs[e];
+          sm.ys[e] = T(0);
+        }
+      }
     }
     first = false;
     __syncthreads();
@@ -673,11 +688,13 @@ __global__ void __launch_bounds__(kPcgThreads, REC ? 2 : 1) k_pcg(PcgArgs<T> a) 
       __syncthreads();
     }
     {
-      double s0 = block_sum(loc_pq, sm.dred);
+      double s0, s1;
+      warp0_sum2(loc_pq, 0.0, cnt, sm.dred, dout, s0, s1);
       if (tid == 0) dregion(dph)[4 * bid + 2] = s0;
     }
     if (!grid_barrier(a.bar, (++epoch) * G, a.err, a.timeout_ns)) return;
-    double pq = sum_dots(dregion(dph), 2, G, sm.dred);
+    double pq, unused_pq;
+    warp0_sum_slots(dregion(dph), G, 2, 2, dout + 4, pq, unused_pq);
     ++dph;
     if (!(pq > 0.0) || !isfinite(pq)) {
       if (bid == 0 && tid == 0) atomicOr(a.err, 2);
@@ -703,16 +720,16 @@ __global__ void __launch_bounds__(kPcgThreads, REC ? 2 : 1) k_pcg(PcgArgs<T> a) 
       loc_rz2 += rv * (double)zz;
     }
     {
-      double s0 = block_sum(loc_rr, sm.dred);
-      double s1 = block_sum(loc_rz2, sm.dred);
+      double s0, s1;
+      warp0_sum2(loc_rr, loc_rz2, cnt, sm.dred, dout, s0, s1);
       if (tid == 0) {
         dregion(dph)[4 * bid + 0] = s0;
         dregion(dph)[4 * bid + 1] = s1;
       }
     }
     if (!grid_barrier(a.bar, (++epoch) * G, a.err, a.timeout_ns)) return;
-    double rr = sum_dots(dregion(dph), 0, G, sm.dred);
-    double rz2 = sum_dots(dregion(dph), 1, G, sm.dred);
+    double rr, rz2;
+    warp0_sum_slots(dregion(dph), G, 0, 1, dout + 4, rr, rz2);
     ++dph;
     ++it;
     rr_last = rr;
@@ -734,7 +751,8 @@ __global__ void __launch_bounds__(kPcgThreads, REC ? 2 : 1) k_pcg(PcgArgs<T> a) 
   __syncthreads();
   double pred = 0.0;
   if (!walk_tiles<T, 1, REC>(a, sm, pp, pred)) return;
-  double ps = block_sum(pred, sm.dred);
+  double ps, unused_ps;
+  warp0_sum2(pred, 0.0, blockDim.x, sm.dred, dout, ps, unused_ps);
   if (tid == 0) a.pred_parts[bid] = ps;
 }
 

@@ -144,10 +144,15 @@ def test_extraction_residual_drop_and_order_invariance():
 # (d): damped step (Schur + PCG + back-substitution) vs the oracle's solve
 # ---------------------------------------------------------------------------
 
+SOLVERS = [ba.BA_SOLVER_IMPLICIT, ba.BA_SOLVER_EXPLICIT]
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-7), (ba.BA_FP32, 2e-2)])
-def test_damped_step_matches_oracle(precision, tol):
+def test_damped_step_matches_oracle(precision, tol, solver):
     sc = geometric(12, 3000, 2, 12, 5.0, seed=41)
-    gpu, orc = pair(sc, precision, pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6)
+    gpu, orc = pair(sc, precision, pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6,
+                    solver=solver)
     lam = 1e-3
     g = gpu.solve_damped(lam)
     geom, _ = orc.predicate(sc.cams0, sc.pts0)
@@ -165,10 +170,11 @@ def test_damped_step_matches_oracle(precision, tol):
 # (e): LM trajectories
 # ---------------------------------------------------------------------------
 
-def test_small_scene_fp64_trajectory_matches_oracle():
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_small_scene_fp64_trajectory_matches_oracle(solver):
     """The FP64 small workload: 20 cameras, 2k points, ~20k observations, 10 iterations."""
     sc = scenes.make_scene("small")
-    gpu, orc = pair(sc, ba.BA_FP64)
+    gpu, orc = pair(sc, ba.BA_FP64, solver=solver)
     log_g = gpu.solve(10)
     orc.opts.solver = 1
     c_o, p_o, log_o = orc.lm(sc.cams0, sc.pts0, 10)
@@ -181,9 +187,10 @@ def test_small_scene_fp64_trajectory_matches_oracle():
     assert np.abs(c_g - c_o).max() < 1e-4
 
 
-def test_fp32_trajectory_close_to_oracle():
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_fp32_trajectory_close_to_oracle(solver):
     sc = geometric(40, 20000, 3, 20, 10.0, seed=1001)
-    gpu, orc = pair(sc, ba.BA_FP32)
+    gpu, orc = pair(sc, ba.BA_FP32, solver=solver)
     log_g = gpu.solve(8)
     orc.opts.solver = 1
     _, _, log_o = orc.lm(sc.cams0, sc.pts0, 8)
