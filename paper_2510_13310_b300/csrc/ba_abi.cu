@@ -103,7 +103,11 @@ struct ba_problem {
   int recompute = 0, cam_in_smem = 0, max_tiles_per_block = 1, g_rows = 0;
   // explicit reduced camera system
   bool explicit_S = false;
-  void *Shat = nullptr, *Dblk = nullptr, *Sacc = nullptr;
+  void *Shat = nullptr, *Dblk = nullptr;
+  void* Yhat = nullptr;         // [N][kWStride] D^-1 W M per damping value (explicit system)
+  int4* covis_runs = nullptr;   // (camera i, camera j, first pair, count), i < j
+  int2* covis_pairs = nullptr;  // point-order observations (k in i, k2 in j) of shared points
+  int n_covis_runs = 0;
   double* dscale = nullptr;
   int spcg_grid = 0, spcg_own_max = 1, spcg_rows_in_smem = 0, bs_grid = 1;
   size_t spcg_smem = 0;
@@ -293,9 +297,9 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   CU(cudaMemsetAsync(&pb->sc->pcg_iters, 0, sizeof(int), pb->stream));
   CU(cudaMemsetAsync(&pb->sc->pcg_rel_res, 0, sizeof(double), pb->stream));
   if (Cf > 0) {
-    LAUNCH(5, launch_form_S<T>(pb->L, (const T*)pb->W, pb->obs_act_co, pb->obs_act, pb->crank, pb->cam_map,
-                               (const T*)pb->Vinv, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale, Cf,
-                               pb->Sacc, (T*)pb->Shat, pb->num_sms, pb->stream));
+    LAUNCH(5, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
+                               (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
+                               Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->num_sms, pb->stream));
     SpcgArgs<T> a{};
     a.Shat = (const T*)pb->Shat;
     a.Dinv = (const T*)pb->Dinv;
@@ -905,7 +909,38 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   // explicit reduced camera system (solver option; automatic for up to 512 cameras)
   if (pb->explicit_S && n_max > 0) {
     ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * n_max));
-    ST(dalloc_bytes(pb, &pb->Sacc, (size_t)form_acc_bytes(pb->fp64) * n_max * n_max));
+    ST(dalloc_bytes(pb, &pb->Yhat, R * (size_t)kWStride * ((size_t)N + 1)));
+    // co-visibility runs: every pair of observations of one point in cameras i < j,
+    // grouped by (i, j), ascending in point within a run
+    {
+      std::vector<long long> cnt((size_t)C * C + 1, 0);
+      for (int p = 0; p < P; ++p)
+        for (int k = pt_off[p]; k < pt_off[p + 1]; ++k)
+          for (int k2 = k + 1; k2 < pt_off[p + 1]; ++k2) cnt[(size_t)h_po_cam[k] * C + h_po_cam[k2] + 1]++;
+      for (size_t q = 0; q < (size_t)C * C; ++q) cnt[q + 1] += cnt[q];
+      const size_t npairs = (size_t)cnt[(size_t)C * C];
+      if (npairs >= (1ull << 31)) {
+        set_error("too many co-visible observation pairs (%zu) for the explicit system", npairs);
+        return BA_ERR_INVALID_ARG;
+      }
+      std::vector<int2> hp(npairs);
+      std::vector<long long> fill(cnt.begin(), cnt.end() - 1);
+      for (int p = 0; p < P; ++p)
+        for (int k = pt_off[p]; k < pt_off[p + 1]; ++k)
+          for (int k2 = k + 1; k2 < pt_off[p + 1]; ++k2)
+            hp[fill[(size_t)h_po_cam[k] * C + h_po_cam[k2]]++] = make_int2(k, k2);
+      std::vector<int4> hr;
+      for (int i = 0; i < C; ++i)
+        for (int j = i + 1; j < C; ++j) {
+          size_t q = (size_t)i * C + j;
+          if (cnt[q + 1] > cnt[q]) hr.push_back(make_int4(i, j, (int)cnt[q], (int)(cnt[q + 1] - cnt[q])));
+        }
+      pb->n_covis_runs = (int)hr.size();
+      ST(dalloc(pb, &pb->covis_pairs, npairs));
+      if (npairs) CU(cudaMemcpy(pb->covis_pairs, hp.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice));
+      ST(dalloc(pb, &pb->covis_runs, hr.size()));
+      if (!hr.empty()) CU(cudaMemcpy(pb->covis_runs, hr.data(), sizeof(int4) * hr.size(), cudaMemcpyHostToDevice));
+    }
     ST(dalloc(pb, &pb->dscale, (size_t)2 * n_max));  // D, then 1/D in the working precision
     ST(dalloc_bytes(pb, &pb->Dblk, R * 45 * (size_t)C));
     pb->spcg_grid = std::max(1, std::min(pb->num_sms, C));

@@ -153,10 +153,9 @@ template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
                               T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, int* err, cudaStream_t s);
 template <typename T>
-cudaError_t launch_form_S(const Layout& L, const T* W, const uint8_t* act_co, const uint8_t* act_po,
-                          const int* crank, const int* cam_map, const T* Vinv, const T* Ud, const T* Dblk,
-                          double* dscale, int Cf, void* Sacc, T* Shat, int num_sms, cudaStream_t s);
-int form_acc_bytes(int fp64);
+cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
+                          const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
+                          int Cf, T* Y, T* Shat, int num_sms, cudaStream_t s);
 template <typename T>
 size_t spcg_smem_bytes(int n, int own_max, int rows_in_smem);
 template <typename T>

@@ -679,73 +679,92 @@ cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_ac
   return cudaGetLastError();
 }
 
-// Per free camera f: damped U block, block-Jacobi inverse of the Schur diagonal
-// D_f = U*_f - sum W V*^-1 W^T (FP64 Cholesky), Schur RHS b_f = -g_c + sum W V*^-1 g_p.
+// Per free camera f (one warp each): damped U block, block-Jacobi inverse of the
+// Schur diagonal D_f = U*_f - sum W V*^-1 W^T (FP64 Cholesky in shared memory,
+// the 9 inverse columns solved by 9 lanes), Schur RHS b_f = -g_c + sum W V*^-1 g_p.
+constexpr int kDiagWarps = 4;
+
 template <typename T>
 __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* __restrict__ Ug,
                              const T* __restrict__ Sg, double lambda, T* __restrict__ Ud,
                              T* __restrict__ Dinv, T* __restrict__ b, T* __restrict__ dampc,
                              T* __restrict__ Dblk, int* err) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double Ds[kDiagWarps][81];
+  __shared__ int okS[kDiagWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int f = blockIdx.x * kDiagWarps + w;
   if (f >= Cf) return;
-  int c = cam_map[f];
+  const int c = cam_map[f];
   const T* u = Ug + 54 * (size_t)c;
   const T* sch = Sg + 54 * (size_t)c;
-  double D[9][9];
-  for (int i = 0; i < 9; ++i) {
-    for (int j = i; j < 9; ++j) {
-      double uij = u[sym9(i, j)];
-      if (i == j) {
-        double dc = clamp_diag(uij);
-        dampc[9 * (size_t)f + i] = (T)dc;
-        uij += lambda * dc;
-      }
+  double* D = Ds[w];
+  for (int q = lane; q < 81; q += 32) {
+    int i = q / 9, j = q - 9 * i;
+    double uij = u[sym9(i, j)];
+    if (i == j) {
+      double dc = clamp_diag(uij);
+      dampc[9 * (size_t)f + i] = (T)dc;
+      uij += lambda * dc;
+    }
+    double v = uij - (double)sch[sym9(i, j)];
+    D[q] = v;
+    if (j >= i) {
       Ud[45 * (size_t)f + sym9(i, j)] = (T)uij;
-      double v = uij - (double)sch[sym9(i, j)];
-      D[i][j] = v;
-      D[j][i] = v;
       if (Dblk) Dblk[45 * (size_t)f + sym9(i, j)] = (T)v;
     }
-    b[9 * (size_t)f + i] = (T)(-(double)u[45 + i] + (double)sch[45 + i]);
   }
-  // Cholesky D = L L^T in place (lower)
-  bool ok = true;
-  for (int j = 0; j < 9 && ok; ++j) {
-    double s = D[j][j];
-    for (int l = 0; l < j; ++l) s -= D[j][l] * D[j][l];
-    if (!(s > 0.0)) {
-      ok = false;
-      break;
+  if (lane < 9) b[9 * (size_t)f + lane] = (T)(-(double)u[45 + lane] + (double)sch[45 + lane]);
+  __syncwarp();
+  if (lane == 0) {
+    // Cholesky D = L L^T in place (lower)
+    int ok = 1;
+    for (int j = 0; j < 9 && ok; ++j) {
+      double s = D[9 * j + j];
+      for (int l = 0; l < j; ++l) s -= D[9 * j + l] * D[9 * j + l];
+      if (!(s > 0.0)) {
+        ok = 0;
+        break;
+      }
+      double dj = sqrt(s), inv = 1.0 / dj;
+      D[9 * j + j] = dj;
+      for (int i = j + 1; i < 9; ++i) {
+        double t = D[9 * i + j];
+        for (int l = 0; l < j; ++l) t -= D[9 * i + l] * D[9 * j + l];
+        D[9 * i + j] = t * inv;
+      }
     }
-    double dj = sqrt(s);
-    D[j][j] = dj;
-    for (int i = j + 1; i < 9; ++i) {
-      double t = D[i][j];
-      for (int l = 0; l < j; ++l) t -= D[i][l] * D[j][l];
-      D[i][j] = t / dj;
-    }
+    okS[w] = ok;
   }
+  __syncwarp();
   T* out = Dinv + 81 * (size_t)f;
-  if (!ok) {
+  if (!okS[w]) {
     // fall back to the Jacobi diagonal of the damped U block
-    atomicOr(err, 8);
-    for (int i = 0; i < 9; ++i)
-      for (int j = 0; j < 9; ++j) out[9 * i + j] = i == j ? (T)(1.0 / (double)Ud[45 * (size_t)f + sym9(i, i)]) : T(0);
+    if (lane == 0) atomicOr(err, 8);
+    for (int q = lane; q < 81; q += 32) {
+      int i = q / 9, j = q - 9 * i;
+      out[q] = i == j ? (T)(1.0 / (double)Ud[45 * (size_t)f + sym9(i, i)]) : T(0);
+    }
     return;
   }
-  // inverse column by column: solve L L^T x = e_j
-  for (int j = 0; j < 9; ++j) {
+  if (lane < 9) {
+    // column `lane` of the inverse: solve L L^T x = e_lane
+    const int j = lane;
     double x[9];
+#pragma unroll
     for (int i = 0; i < 9; ++i) {
       double s = i == j ? 1.0 : 0.0;
-      for (int l = 0; l < i; ++l) s -= D[i][l] * x[l];
-      x[i] = s / D[i][i];
+#pragma unroll
+      for (int l = 0; l < i; ++l) s -= D[9 * i + l] * x[l];
+      x[i] = s / D[9 * i + i];
     }
+#pragma unroll
     for (int i = 8; i >= 0; --i) {
       double s = x[i];
-      for (int l = i + 1; l < 9; ++l) s -= D[l][i] * x[l];
-      x[i] = s / D[i][i];
+#pragma unroll
+      for (int l = i + 1; l < 9; ++l) s -= D[9 * l + i] * x[l];
+      x[i] = s / D[9 * i + i];
     }
+#pragma unroll
     for (int i = 0; i < 9; ++i) out[9 * i + j] = (T)x[i];
   }
 }
@@ -753,10 +772,13 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
 template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
                               T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, int* err, cudaStream_t s) {
-  if (Cf > 0) k_schur_diag<T><<<(Cf + 63) / 64, 64, 0, s>>>(Cf, cam_map, Ug, Sg, lambda, Ud, Dinv, b, dampc, Dblk, err);
+  if (Cf > 0)
+    k_schur_diag<T><<<(Cf + kDiagWarps - 1) / kDiagWarps, 32 * kDiagWarps, 0, s>>>(Cf, cam_map, Ug, Sg, lambda, Ud,
+                                                                                    Dinv, b, dampc, Dblk, err);
   return cudaGetLastError();
 }
 
+// predicted decrease, camera part: 1/2 dx^T (lambda D dx - g) over the free cameras
 template <typename T>
 __global__ void k_pred_cams(int Cf, const int* __restrict__ cam_map, const T* __restrict__ x,
                             const T* __restrict__ Ug, const T* __restrict__ dampc, double lambda,

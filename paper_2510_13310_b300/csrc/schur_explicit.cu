@@ -7,44 +7,17 @@
 // a dense row-block product with no cross-block partial sums.
 //
 // S is formed Jacobi-scaled, S^ = D^-1 S D^-1 with D = sqrt(diag U*), so every
-// entry is of order one.  Off-diagonal blocks are accumulated by their row
-// camera: a block owns one free camera i (and a range of columns) and, for each
-// of its observations k of point p and each observation k' of p in a camera
-// ranked after i, adds W_k V*_p^-1 W_k'^T into a shared-memory row block held
-// as 64-bit fixed point (2^-48 units).  Integer addition is associative, so the
-// result does not depend on the order in which threads add: S^ is
-// bit-reproducible.  The diagonal blocks come from the block-Jacobi pass
-// (U* - sum W V*^-1 W^T) and the lower triangle is mirrored from the upper.
+// entry is of order one.  Off-diagonal blocks S_ij (i < j) are sums over the
+// points both cameras see; those pairs of observations are listed once at set-up
+// (the co-visibility runs), so each block is summed by one warp in registers in
+// a fixed order: no atomics, bit-reproducible.  The diagonal blocks come from the
+// block-Jacobi pass (U* - sum W V*^-1 W^T) and the lower triangle is mirrored.
 #include <cuda/atomic>
 
 #include "internal.h"
 #include "model.cuh"
 
 namespace bab {
-
-// Fixed-point accumulators.  Every partial sum of W_k V*^-1 W_k'^T scaled by
-// D^-1 (.) D^-1 is bounded by 1 in magnitude (it is a block of a PSD matrix no
-// larger than D^-1 U* D^-1, whose diagonal is 1), so FP32 accumulates in 32-bit
-// integers of 2^-30 units (range +-2, finer than FP32 rounding of the terms),
-// FP64 in 64-bit integers of 2^-48 units.
-template <typename T> struct FixAcc;
-template <> struct FixAcc<float> {
-  using type = int;
-  static constexpr double scale = 1073741824.0;  // 2^30
-  __device__ static __forceinline__ int conv(float v) { return __float2int_rn(v); }
-  __device__ static __forceinline__ void add(int* p, int v) { atomicAdd(p, v); }
-  __device__ static __forceinline__ void gadd(int* p, int v) { atomicAdd(p, v); }
-};
-template <> struct FixAcc<double> {
-  using type = long long;
-  static constexpr double scale = 281474976710656.0;  // 2^48
-  __device__ static __forceinline__ long long conv(double v) { return __double2ll_rn(v); }
-  __device__ static __forceinline__ void add(long long* p, long long v) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
-  }
-  __device__ static __forceinline__ void gadd(long long* p, long long v) { add(p, v); }
-};
-constexpr int kFormThreads = 256;
 
 template <typename T>
 __device__ __forceinline__ void load_cam_rec(const T* __restrict__ camw, int c, T cw[kCamStride]) {
@@ -66,98 +39,116 @@ __device__ __forceinline__ void obs_W(const T* cw, const T* X, T u, T v, T tau, 
       W[3 * a + b] = o.wrob * (o.Jc[0][a] * o.Jp[0][b] + o.Jc[1][a] * o.Jp[1][b] + o.Jc[2][a] * o.Jp[2][b]);
 }
 
-// grid (Cf, n_col_chunks, n_obs_parts): row camera a = blockIdx.x, columns
-// [9 (a+1) + blockIdx.y * chunk, ... + chunk) of the strictly upper part, and
-// part blockIdx.z of camera a's observations.  W rows (point order, stride
-// kWStride) are read, not recomputed.  The block's shared-memory row block is
-// flushed into the global integer accumulator Sacc with integer atomics.
+// Per point-order observation k (camera a, point p): Y^_k = D_a^-1 W_k M_p with
+// M_p M_p^T = V*_p^-1 (3x3 Cholesky), so that W_k V*_p^-1 W_k'^T scaled by the
+// Jacobi factors is the plain product Y^_k Y^_k'^T.  Rows of observations of
+// cameras that are not free are not written (their blocks are never formed);
+// an inactive observation has W = 0 and gets Y^ = 0.
 template <typename T>
-__global__ void __launch_bounds__(kFormThreads) k_form_S(Layout L, const T* __restrict__ W,
-                                                         const uint8_t* __restrict__ act_co,
-                                                         const uint8_t* __restrict__ act_po,
-                                                         const int* __restrict__ crank,
-                                                         const int* __restrict__ cam_map,
-                                                         const T* __restrict__ Vinv,
-                                                         const double* __restrict__ dscale, int Cf,
-                                                         int chunk,
-                                                         typename FixAcc<T>::type* __restrict__ Sacc) {
-  using Acc = typename FixAcc<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Acc* acc = reinterpret_cast<Acc*>(smem_raw);  // [9][chunk]
-  const int a = blockIdx.x;
-  const int n = 9 * Cf;
-  const int start = 9 * (a + 1) + blockIdx.y * chunk;
-  if (start >= n) return;
-  const int width = min(chunk, n - start);
-  const int ci = cam_map[a];
-  const int kb0 = L.chunk_obs[L.cam_chunk[ci]], ke0 = L.chunk_obs[L.cam_chunk[ci + 1]];
-  const int per = (ke0 - kb0 + gridDim.z - 1) / gridDim.z;
-  const int kb = kb0 + blockIdx.z * per, ke = min(ke0, kb + per);
-  if (kb >= ke) return;
-  for (int q = threadIdx.x; q < 9 * chunk; q += blockDim.x) acc[q] = 0;
-  __syncthreads();
-  // row scale with the fixed-point unit folded in; each term is rounded once,
-  // deterministically, before the integer (order-free) sums
-  T dsa[9];
-#pragma unroll
-  for (int r = 0; r < 9; ++r) dsa[r] = (T)(FixAcc<T>::scale / dscale[9 * a + r]);
-  const T* dinv = reinterpret_cast<const T*>(dscale + n);
-  for (int k = kb + threadIdx.x; k < ke; k += blockDim.x) {
-    if (!act_co[k]) continue;
-    const int p = L.co_pt[k];
-    const T* Wk = W + kWStride * (size_t)L.co_po[k];
-    const T* vi = Vinv + 6 * (size_t)p;
-    T v00 = vi[0], v01 = vi[1], v02 = vi[2], v11 = vi[3], v12 = vi[4], v22 = vi[5];
-    T Y[27];  // diag(dsa) W V*^-1
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      T w0 = Wk[3 * r], w1 = Wk[3 * r + 1], w2 = Wk[3 * r + 2];
-      Y[3 * r] = dsa[r] * (w0 * v00 + w1 * v01 + w2 * v02);
-      Y[3 * r + 1] = dsa[r] * (w0 * v01 + w1 * v11 + w2 * v12);
-      Y[3 * r + 2] = dsa[r] * (w0 * v02 + w1 * v12 + w2 * v22);
+__global__ void k_form_Y(int N, const int* __restrict__ po_cam, const int* __restrict__ po_pt,
+                         const T* __restrict__ W, const T* __restrict__ Vinv, const int* __restrict__ crank,
+                         const double* __restrict__ dscale, int Cf, T* __restrict__ Y) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int a = crank[po_cam[k]];
+  if (a < 0) return;
+  const T* dinv = reinterpret_cast<const T*>(dscale + 9 * Cf) + 9 * a;
+  const T* vi = Vinv + 6 * (size_t)po_pt[k];
+  const T v00 = vi[0], v01 = vi[1], v02 = vi[2], v11 = vi[3], v12 = vi[4], v22 = vi[5];
+  T l00 = T(0), l10 = T(0), l20 = T(0), l11 = T(0), l21 = T(0), l22 = T(0);
+  if (v00 > T(0)) {
+    l00 = sqrt(v00);
+    const T r0 = T(1) / l00;
+    l10 = v01 * r0;
+    l20 = v02 * r0;
+    const T d1 = v11 - l10 * l10;
+    if (d1 > T(0)) {
+      l11 = sqrt(d1);
+      l21 = (v12 - l20 * l10) / l11;
     }
-    for (int k2 = L.pt_off[p]; k2 < L.pt_off[p + 1]; ++k2) {
-      const int b = crank[L.po_cam[k2]];
-      if (b <= a || !act_po[k2]) continue;
-      const int col0 = 9 * b - start;
-      if (col0 < 0 || col0 >= width) continue;
-      const T* W2 = W + kWStride * (size_t)k2;
-      T Z[27];  // W2 scaled by its column scales
-#pragma unroll
-      for (int s2 = 0; s2 < 9; ++s2) {
-        T ds = dinv[9 * b + s2];
-        Z[3 * s2] = ds * W2[3 * s2];
-        Z[3 * s2 + 1] = ds * W2[3 * s2 + 1];
-        Z[3 * s2 + 2] = ds * W2[3 * s2 + 2];
-      }
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        Acc* row = acc + r * chunk + col0;
-#pragma unroll
-        for (int s2 = 0; s2 < 9; ++s2) {
-          T cv = Y[3 * r] * Z[3 * s2] + Y[3 * r + 1] * Z[3 * s2 + 1] + Y[3 * r + 2] * Z[3 * s2 + 2];
-          FixAcc<T>::add(row + s2, FixAcc<T>::conv(cv));
-        }
-      }
-    }
+    const T d2 = v22 - l20 * l20 - l21 * l21;
+    l22 = d2 > T(0) ? sqrt(d2) : T(0);
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < 9 * width; q += blockDim.x) {
-    int r = q / width, c = q - r * width;
-    Acc v = acc[r * chunk + c];
-    if (v != 0) FixAcc<T>::gadd(Sacc + (size_t)(9 * a + r) * n + start + c, v);
+  const T* w = W + kWStride * (size_t)k;
+  T* y = Y + kWStride * (size_t)k;
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    const T w0 = w[3 * r], w1 = w[3 * r + 1], w2 = w[3 * r + 2], sc = dinv[r];
+    y[3 * r] = sc * (w0 * l00 + w1 * l10 + w2 * l20);
+    y[3 * r + 1] = sc * (w1 * l11 + w2 * l21);
+    y[3 * r + 2] = sc * (w2 * l22);
   }
 }
 
-// Upper off-diagonal entries of S^ from the integer accumulator (S^ = -sum / scale).
 template <typename T>
-__global__ void k_S_convert(int Cf, const typename FixAcc<T>::type* __restrict__ Sacc, T* __restrict__ Shat) {
+__device__ __forceinline__ void load_row27(const T* __restrict__ p, T v[27]);
+template <>
+__device__ __forceinline__ void load_row27<float>(const float* __restrict__ p, float v[27]) {
+  const float4* q = reinterpret_cast<const float4*>(p);  // rows are 112-byte aligned
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float4 t = q[i];
+    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+  }
+  const float4 t = q[6];
+  v[24] = t.x; v[25] = t.y; v[26] = t.z;
+}
+template <>
+__device__ __forceinline__ void load_row27<double>(const double* __restrict__ p, double v[27]) {
+  const double2* q = reinterpret_cast<const double2*>(p);  // rows are 224-byte aligned
+#pragma unroll
+  for (int i = 0; i < 13; ++i) {
+    const double2 t = q[i];
+    v[2 * i] = t.x; v[2 * i + 1] = t.y;
+  }
+  v[26] = p[26];
+}
+
+// Off-diagonal blocks from the static co-visibility runs: run = every point seen
+// by both cameras i < j, as pairs (k, k2) of point-order observations, ascending
+// in point.  One warp per run: each lane sums Y^_k Y^_k2^T over its subset of the
+// run in registers, then the lanes are reduced in a fixed order
+// (deterministic).  Inactive observations have Y^ = 0 and add nothing; runs whose
+// cameras are not both free are skipped.
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
+    k_form_S_runs(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
+                  const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int n = 9 * Cf;
-  const T unit = (T)(-1.0 / FixAcc<T>::scale);
-  for (int r = blockIdx.x; r < n; r += gridDim.x) {
-    const size_t row = (size_t)r * n;
-    for (int c = 9 * (r / 9 + 1) + threadIdx.x; c < n; c += blockDim.x)
-      Shat[row + c] = (T)Sacc[row + c] * unit;
+  for (int ri = gw; ri < n_runs; ri += nw) {
+    const int4 rn = runs[ri];  // (camera i, camera j, first pair, pair count)
+    const int a = crank[rn.x], b = crank[rn.y];
+    if (a < 0 || b < 0) continue;
+    T acc[81];
+#pragma unroll
+    for (int q = 0; q < 81; ++q) acc[q] = T(0);
+    const int qe = rn.z + rn.w;
+    int q = rn.z + lane;
+    int2 nxt = q < qe ? pairs[q] : make_int2(0, 0);
+    for (; q < qe; q += 32) {
+      const int2 pr = nxt;
+      if (q + 32 < qe) nxt = pairs[q + 32];  // next pair's indices in flight during this one
+      T y1[27], y2[27];
+      load_row27<T>(Y + kWStride * (size_t)pr.x, y1);
+      load_row27<T>(Y + kWStride * (size_t)pr.y, y2);
+#pragma unroll
+      for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int s2 = 0; s2 < 9; ++s2)
+          acc[9 * r + s2] += y1[3 * r] * y2[3 * s2] + y1[3 * r + 1] * y2[3 * s2 + 1] + y1[3 * r + 2] * y2[3 * s2 + 2];
+    }
+#pragma unroll
+    for (int t = 0; t < 81; ++t) acc[t] = warp_sum(acc[t]);
+    for (int t = lane; t < 81; t += 32) {
+      T v = acc[0];
+#pragma unroll
+      for (int u = 1; u < 81; ++u)
+        if (u == t) v = acc[u];
+      const int r = t / 9, s2 = t - 9 * r;
+      Shat[(size_t)(9 * a + r) * n + 9 * b + s2] = -v;
+    }
   }
 }
 
@@ -222,42 +213,26 @@ __global__ void k_dscale(int Cf, const T* __restrict__ Ud, double* __restrict__ 
 }
 
 template <typename T>
-cudaError_t launch_form_S(const Layout& L, const T* W, const uint8_t* act_co, const uint8_t* act_po,
-                          const int* crank, const int* cam_map, const T* Vinv, const T* Ud, const T* Dblk,
-                          double* dscale, int Cf, void* Sacc, T* Shat, int num_sms, cudaStream_t s) {
+cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
+                          const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
+                          int Cf, T* Y, T* Shat, int num_sms, cudaStream_t s) {
   if (Cf <= 0) return cudaSuccess;
-  using Acc = typename FixAcc<T>::type;
   const int n = 9 * Cf;
   k_dscale<T><<<(n + 255) / 256, 256, 0, s>>>(Cf, Ud, dscale);
-  cudaError_t e = cudaMemsetAsync(Sacc, 0, sizeof(Acc) * (size_t)n * n, s);
+  if (L.N > 0) k_form_Y<T><<<(L.N + 255) / 256, 256, 0, s>>>(L.N, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
+  cudaError_t e = cudaMemsetAsync(Shat, 0, sizeof(T) * (size_t)n * n, s);
   if (e != cudaSuccess) return e;
-  // column chunk: as many 9-column camera blocks as fit in ~96 KB of accumulator rows
-  const int asz = (int)sizeof(Acc);
-  int chunk = (96 * 1024) / (9 * asz);
-  chunk = (chunk / 9) * 9;
-  if (n - 9 < chunk) chunk = n - 9 > 9 ? n - 9 : 9;
-  int nch = (n - 9 + chunk - 1) / chunk;
-  if (nch < 1) nch = 1;
-  // split every camera's observations so that about 4 blocks per SM run
-  int nz = (4 * num_sms + Cf * nch - 1) / (Cf * nch);
-  nz = nz < 1 ? 1 : (nz > 16 ? 16 : nz);
-  size_t smem = (size_t)9 * chunk * asz;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_form_S<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
+  if (n_runs > 0) {
+    const int wpb = 4;  // warps per 128-thread block
+    int grid = (n_runs + wpb - 1) / wpb;
+    if (grid > 32 * num_sms) grid = 32 * num_sms;
+    k_form_S_runs<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
   }
-  if (n > 9)
-    k_form_S<T><<<dim3(Cf, nch, nz), kFormThreads, smem, s>>>(L, W, act_co, act_po, crank, cam_map, Vinv,
-                                                               dscale, Cf, chunk, reinterpret_cast<Acc*>(Sacc));
-  k_S_convert<T><<<n < 8 * num_sms ? n : 8 * num_sms, 256, 0, s>>>(Cf, reinterpret_cast<const Acc*>(Sacc), Shat);
   int nt = (n + 31) / 32;
   k_S_finalize<T><<<dim3(nt, nt), dim3(32, 8), 0, s>>>(Cf, Dblk, dscale, Shat);
   k_S_diag_upper<T><<<Cf, 128, 0, s>>>(Cf, Dblk, dscale, Shat);
   return cudaGetLastError();
 }
-
-int form_acc_bytes(int fp64) { return fp64 ? 8 : 4; }
 
 // ---------------------------------------------------------------------------
 // PCG on the scaled explicit system S^ x^ = b^ (b^ = D^-1 b, x = D^-1 x^) with the
@@ -543,9 +518,9 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
 }
 
 #define BAB_SINST(T)                                                                                   \
-  template cudaError_t launch_form_S<T>(const Layout&, const T*, const uint8_t*, const uint8_t*,      \
-                                        const int*, const int*, const T*, const T*, const T*, double*, \
-                                        int, void*, T*, int, cudaStream_t);                            \
+  template cudaError_t launch_form_S<T>(const Layout&, int, const int4*, const int2*, const T*,        \
+                                        const T*, const int*, const T*, const T*, double*, int, T*, T*, \
+                                        int, cudaStream_t);                                            \
   template size_t spcg_smem_bytes<T>(int, int, int);                                                   \
   template const void* spcg_kernel_ptr<T>();                                                           \
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \
