@@ -90,8 +90,9 @@ typedef struct {
   int pcg_iters;
   double pcg_rel_res;
   int64_t n_cam_act, n_pt_act, n_obs_act;
-  float ms[8];        /* per-phase device time: extract, linearize, schur, pcg, backsub,
-                         evaluate, total, host */
+  float ms[8];        /* device time per phase: [0] extract, [1] linearize, [2] Schur terms,
+                         [3] solve (d) in full, [4] the PCG kernel launch alone (inside [3]),
+                         [5] candidate + evaluation, [6] total; [7] unused */
 } ba_iter_info;
 
 typedef struct ba_problem ba_problem;
@@ -151,12 +152,21 @@ ba_status ba_solve_damped(ba_problem* pb, double lambda, double* dc, double* dp,
 ba_status ba_eval_cost(ba_problem* pb, const double* cams, const double* pts, double* cost,
                        double* rmse_px);
 
-/* Implicit-adjoint gradients at the current state: with the active set and the
- * IRLS weights frozen, solve H mu = (dL/dcams, dL/dpts) with the undamped
- * Gauss-Newton matrix through the Schur complement, then
- * dL/du_k = rho'_k (J_k mu)_0, dL/dv_k = rho'_k (J_k mu)_1,
- * dL/dd_k = -rho'_k sqrt(w_k) m_k / d_k^2 (J_k mu)_2.
- * dL_dcams [C][9], dL_dpts [P][3] in; dL_duv [N][2], dL_ddepth [N] out (input order). */
+/* Implicit-adjoint gradients at the current state (implicit function theorem on
+ * the stationarity of Sec. 3.3's normal equations): with the active set of the
+ * latest extraction and the IRLS weights frozen, solve H mu = a with the
+ * undamped Gauss-Newton matrix H through the Schur complement (the LM step's
+ * solver at lambda = 0, PCG to pcg_rel_tol), then per active observation
+ *   dL/du_k = rho'_k (J_k mu)_0,  dL/dv_k = rho'_k (J_k mu)_1,
+ *   dL/dd_k = -rho'_k sqrt(w_k) (J_k mu)_2 / d_k^2  (zero without a prior).
+ * dL_dcams [C][9] and dL_dpts [P][3] are the loss gradient in the stored
+ * parameters; a is that gradient in the LM update's coordinates: the rotation
+ * block is Jl(w)^-T dL/dw (inverse left Jacobian of SO(3)), gauge and inactive
+ * entries are dropped.  Outputs: dL_duv [N][2], dL_ddepth [N] in the input
+ * order, zero for inactive observations.  Gradients with respect to the initial
+ * parameters are zero (not returned).  The next LM step re-linearises.
+ * Errors: BA_ERR_NONFINITE if the undamped system is singular, BA_ERR_NOT_CONVERGED
+ * if PCG hit pcg_max_iters (outputs still written). */
 ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_dpts,
                       double* dL_duv, double* dL_ddepth);
 
@@ -188,6 +198,10 @@ ba_status ba_eval_cost_noalloc(const ba_options* opts, void* stream, int64_t n_c
 
 /* Number of this library's kernels launched since creation (counts launches). */
 int64_t ba_kernel_launches(const ba_problem* pb);
+
+/* The reduced-camera-system solver the problem resolved to at creation:
+ * BA_SOLVER_IMPLICIT or BA_SOLVER_EXPLICIT (0 for a NULL handle). */
+int ba_solver_kind(const ba_problem* pb);
 
 void ba_destroy(ba_problem* pb);
 const char* ba_status_string(ba_status s);

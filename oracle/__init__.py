@@ -52,6 +52,7 @@ def lib():
         L.oracle_default_opts.argtypes = [ct.POINTER(Opts)]
         L.oracle_rotvec_to_matrix.argtypes = [P_f64, P_f64]
         L.oracle_rotvec_compose.argtypes = [P_f64, P_f64, P_f64]
+        L.oracle_so3_left_jacobian_inv.argtypes = [P_f64, P_f64]
         L.oracle_observe.argtypes = [P_f64, P_f64, P_f64, ct.c_double, ct.c_double, ct.c_double,
                                      ct.c_double, P_f64, P_f64, P_f64, P_f64, P_f64]
         L.oracle_eval_obs.argtypes = [ct.POINTER(Problem), ct.POINTER(Opts), P_f64, P_f64, P_f64,
@@ -254,6 +255,12 @@ def rotvec_to_matrix(w):
     R = np.zeros(9)
     lib().oracle_rotvec_to_matrix(_p(_f64(w), P_f64), _p(R, P_f64))
     return R.reshape(3, 3)
+
+
+def so3_left_jacobian_inv(w):
+    J = np.zeros(9)
+    lib().oracle_so3_left_jacobian_inv(_p(_f64(w), P_f64), _p(J, P_f64))
+    return J.reshape(3, 3)
 
 
 def rotvec_compose(a, b):

@@ -1024,6 +1024,23 @@ int oracle_lm(const oracle_problem* pb, const oracle_opts* o, int max_iters, dou
  * dr/du_k = -e_0, dr/dv_k = -e_1, dr/dd_k = sqrt(w) m / d^2 e_2, hence
  * dL/du_k = rho'_k (J_k mu)_0, dL/dv_k = rho'_k (J_k mu)_1,
  * dL/dd_k = -rho'_k sqrt(w) m / d^2 (J_k mu)_2. */
+/* Inverse left Jacobian of SO(3) at w: the LM update w <- Log(Exp(dw) Exp(w))
+ * has d w / d dw = Jl(w)^-1 at dw = 0, with
+ *   Jl^-1 = I - W/2 + (1/th^2 - (1 + cos th) / (2 th sin th)) W^2,  W = [w]x,
+ * and the series 1/12 + th^2/720 of the last coefficient near th = 0. */
+void oracle_so3_left_jacobian_inv(const double w[3], double J[9]) {
+  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double th = sqrt(th2);
+  double c2 = th < 1e-4 ? 1.0 / 12.0 + th2 / 720.0 : 1.0 / th2 - (1.0 + cos(th)) / (2.0 * th * sin(th));
+  double Wm[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double w2 = 0.0;
+      for (int k = 0; k < 3; ++k) w2 += Wm[3 * i + k] * Wm[3 * k + j];
+      J[3 * i + j] = (i == j ? 1.0 : 0.0) - 0.5 * Wm[3 * i + j] + c2 * w2;
+    }
+}
+
 int oracle_backward(const oracle_problem* pb, const oracle_opts* o, const double* cams,
                     const double* pts, const uint8_t* obs_mask, const int32_t* cam_rank,
                     const int32_t* pt_rank, int64_t n_cam_free, const double* dL_dcams,
@@ -1042,7 +1059,18 @@ int oracle_backward(const oracle_problem* pb, const oracle_opts* o, const double
    * routine as the LM step with lambda = 0 and g := -a. */
   double* ac = (double*)malloc(sizeof(double) * 9 * ((size_t)C + 1));
   double* ap = (double*)malloc(sizeof(double) * 3 * ((size_t)P + 1));
-  for (int64_t i = 0; i < 9 * C; ++i) ac[i] = -dL_dcams[i];
+  /* dL_dcams is the gradient in the stored parameters; the solve runs in the
+   * update's coordinates, where the rotation block is Jl(w)^-T dL/dw. */
+  for (int64_t c = 0; c < C; ++c) {
+    double J[9];
+    oracle_so3_left_jacobian_inv(cams + 9 * c, J);
+    for (int i = 0; i < 3; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < 3; ++j) acc += J[3 * j + i] * dL_dcams[9 * c + j];
+      ac[9 * c + i] = -acc;
+    }
+    for (int i = 3; i < 9; ++i) ac[9 * c + i] = -dL_dcams[9 * c + i];
+  }
   for (int64_t i = 0; i < 3 * P; ++i) ap[i] = -dL_dpts[i];
   oracle_opts od = *o;
   od.solver = 0;

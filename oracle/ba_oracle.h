@@ -129,6 +129,9 @@ int oracle_lm(const oracle_problem* pb, const oracle_opts* o, int max_iters, dou
 /* Implicit adjoint at a converged state: solves H mu = (dL/dcams, dL/dpts) with the
  * undamped Gauss-Newton matrix of the active set (IRLS weights frozen) and returns
  * dL/duv [N][2] and dL/ddepth [N]. */
+/* Inverse left Jacobian of SO(3) (row-major 3x3). */
+void oracle_so3_left_jacobian_inv(const double w[3], double J[9]);
+
 int oracle_backward(const oracle_problem* pb, const oracle_opts* o, const double* cams,
                     const double* pts, const uint8_t* obs_mask, const int32_t* cam_rank,
                     const int32_t* pt_rank, int64_t n_cam_free, const double* dL_dcams,

@@ -25,7 +25,8 @@ BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT = 0, 1, 2
 # every symbol include/ba_b300.h declares
 EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
-           "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_kernel_launches", "ba_destroy",
+           "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_kernel_launches", "ba_solver_kind",
+           "ba_destroy",
            "ba_status_string", "ba_last_error")
 
 
@@ -88,6 +89,8 @@ def lib():
                                            ct.c_int64, vp, vp, vp, vp, vp, vp]
         L.ba_kernel_launches.argtypes = [vp]
         L.ba_kernel_launches.restype = ct.c_int64
+        L.ba_solver_kind.argtypes = [vp]
+        L.ba_solver_kind.restype = ct.c_int
         L.ba_destroy.argtypes = [vp]
         L.ba_status_string.argtypes = [ct.c_int]
         L.ba_status_string.restype = ct.c_char_p
@@ -288,12 +291,18 @@ class Problem:
         dd = dL_ddepth if dL_ddepth is not None else np.zeros(self.n_obs)
         a, b = _Arr(dL_dcams, np.float64), _Arr(dL_dpts, np.float64)
         ua, da = _Arr(duv, np.float64), _Arr(dd, np.float64)
-        _check(self.L.ba_backward(self.h, a.p, b.p, ua.p, da.p), "ba_backward")
+        _check(self.L.ba_backward(self.h, a.p, b.p, ua.p, da.p), "ba_backward",
+               allow=(BA_OK, BA_ERR_NOT_CONVERGED))
         return ua.obj, da.obj
 
     @property
     def kernel_launches(self):
         return int(self.L.ba_kernel_launches(self.h))
+
+    @property
+    def explicit_solver(self) -> bool:
+        """True when the reduced camera system is formed explicitly (BA_SOLVER_EXPLICIT)."""
+        return int(self.L.ba_solver_kind(self.h)) == BA_SOLVER_EXPLICIT
 
 
 def _c_options(o: Options):
@@ -320,3 +329,58 @@ def eval_cost_noalloc(cams, pts, obs_cam, obs_pt, obs_uv, depth, out, obs_mask=N
                                 None if obs_mask is None else obs_mask.data_ptr(), out.data_ptr())
     _check(st, "ba_eval_cost_noalloc")
     return out
+
+
+def _make_ba_function():
+    import torch
+
+    class BAFunction(torch.autograd.Function):
+        """Differentiable bundle adjustment.
+
+        forward(cams0 [C,9], pts0 [P,3], obs_uv [N,2], depth [N], obs_cam [N], obs_pt [N],
+        options, iters) runs `iters` LM iterations (ba_solve) and returns the
+        solution (cams [C,9], pts [P,3]) as float64 tensors on the inputs' device.
+        backward gives dL/dobs_uv and dL/ddepth by the implicit adjoint at the
+        solution (ba_backward); the gradients with respect to the initial
+        parameters are zero, and the index arrays have none."""
+
+        @staticmethod
+        def forward(ctx, cams0, pts0, obs_uv, depth, obs_cam, obs_pt, options, iters):
+            dev = obs_uv.device
+            prob = Problem(cams0.detach(), pts0.detach(), obs_cam, obs_pt, obs_uv.detach(), depth.detach(),
+                           options=options,
+                           stream=torch.cuda.current_stream(dev).cuda_stream if dev.type == "cuda" else None)
+            prob.solve(int(iters))
+            cams = torch.empty((prob.n_cams, 9), dtype=torch.float64, device=dev)
+            pts = torch.empty((prob.n_pts, 3), dtype=torch.float64, device=dev)
+            prob.get_params(cams, pts)
+            ctx.prob = prob
+            ctx.uv_dtype, ctx.depth_dtype = obs_uv.dtype, depth.dtype
+            return cams, pts
+
+        @staticmethod
+        def backward(ctx, g_cams, g_pts):
+            prob = ctx.prob
+            dev = g_cams.device
+            duv = torch.empty((prob.n_obs, 2), dtype=torch.float64, device=dev)
+            dd = torch.empty((prob.n_obs,), dtype=torch.float64, device=dev)
+            prob.backward(g_cams.to(torch.float64).contiguous(), g_pts.to(torch.float64).contiguous(), duv, dd)
+            prob.close()
+            ctx.prob = None
+            zc = torch.zeros_like(g_cams) if ctx.needs_input_grad[0] else None
+            zp = torch.zeros_like(g_pts) if ctx.needs_input_grad[1] else None
+            return (zc, zp, duv.to(ctx.uv_dtype), dd.to(ctx.depth_dtype), None, None, None, None)
+
+    return BAFunction
+
+
+_BAFunction = None
+
+
+def bundle_adjust(cams0, pts0, obs_uv, depth, obs_cam, obs_pt, options: Options | None = None,
+                  iters: int = 30):
+    """LM bundle adjustment as a differentiable torch op (see BAFunction)."""
+    global _BAFunction
+    if _BAFunction is None:
+        _BAFunction = _make_ba_function()
+    return _BAFunction.apply(cams0, pts0, obs_uv, depth, obs_cam, obs_pt, options or Options(), iters)

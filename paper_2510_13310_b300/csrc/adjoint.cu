@@ -1,0 +1,143 @@
+// adjoint.cu -- implicit differentiation of the converged bundle adjustment.
+//
+// At a stationary point of F the normal-equation gradient g(theta, y) = 0, with
+// y the observations (pixels u, v and depth priors d).  With the active set and
+// the IRLS weights rho' frozen and the Gauss-Newton matrix H = J^T W rho' J in
+// place of the Hessian, the implicit function theorem gives
+//   dL/dy = -(dg/dy)^T mu,   H mu = dL/dtheta.
+// mu is found with the same Schur-complement solve as an LM step, undamped
+// (lambda = 0) and with the gradient replaced by -dL/dtheta; then per
+// observation, since dr_k/du_k = -e_0, dr_k/dv_k = -e_1 and
+// dr_k/dd_k = sqrt(w) / d_k^2 e_2 (residual sqrt(w)(1/z - 1/d)):
+//   dL/du_k = rho'_k (J_k mu)_0,  dL/dv_k = rho'_k (J_k mu)_1,
+//   dL/dd_k = -rho'_k sqrt(w_k) tau_k^2 (J_k mu)_2   (tau_k = 1/d_k).
+// The Jacobian blocks are recomputed, not stored.  dL/dtheta is the gradient
+// in the stored camera parameters (axis-angle, t, f, k1, k2) and point
+// coordinates.
+#include "internal.h"
+#include "model.cuh"
+
+namespace bab {
+
+// The solve runs in the coordinates of the LM update, w <- Log(Exp(dw) Exp(w)),
+// in which d w / d dw = Jl(w)^-1 (inverse left Jacobian of SO(3)):
+//   Jl^-1 = I - [w]x / 2 + c2 [w]x^2,  c2 = 1/th^2 - (1 + cos th) / (2 th sin th),
+// with c2 = 1/12 + th^2/720 near th = 0.  So the rotation block of the adjoint
+// right-hand side is Jl(w)^-T dL/dw; translation and intrinsics pass through.
+__device__ __forceinline__ void so3_jl_inv_T_apply(const double* w, const double* g, double* out) {
+  const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  const double th = sqrt(th2);
+  const double c2 = th < 1e-4 ? 1.0 / 12.0 + th2 / 720.0 : 1.0 / th2 - (1.0 + cos(th)) / (2.0 * th * sin(th));
+  // out = (I - K/2 + c2 K^2)^T g = g + (K g)/2 + c2 K^2 g, with K = [w]x (K^T = -K, (K^2)^T = K^2)
+  const double kg0 = w[1] * g[2] - w[2] * g[1];
+  const double kg1 = w[2] * g[0] - w[0] * g[2];
+  const double kg2 = w[0] * g[1] - w[1] * g[0];
+  const double kkg0 = w[1] * kg2 - w[2] * kg1;
+  const double kkg1 = w[2] * kg0 - w[0] * kg2;
+  const double kkg2 = w[0] * kg1 - w[1] * kg0;
+  out[0] = g[0] + 0.5 * kg0 + c2 * kkg0;
+  out[1] = g[1] + 0.5 * kg1 + c2 * kkg1;
+  out[2] = g[2] + 0.5 * kg2 + c2 * kkg2;
+}
+
+// g_c := -(Jl^-T dL/dw, dL/dt, dL/df, dL/dk) for free cameras (the gradient slot
+// of the packed camera record), g_p := -dL/dpts for active points, zero elsewhere.
+template <typename T>
+__global__ void k_adjoint_rhs(int C, int P, const double* __restrict__ cams64, const int* __restrict__ crank,
+                              const uint8_t* __restrict__ pt_act, const double* __restrict__ dL_dc,
+                              const double* __restrict__ dL_dp, T* __restrict__ Ug, T* __restrict__ gp) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < C) {
+    const int c = (int)i;
+    T* g = Ug + 54 * (size_t)c + 45;
+    if (crank[c] < 0) {
+#pragma unroll
+      for (int j = 0; j < 9; ++j) g[j] = T(0);
+    } else {
+      const double* d = dL_dc + 9 * (size_t)c;
+      double rw[3];
+      so3_jl_inv_T_apply(cams64 + 9 * (size_t)c, d, rw);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) g[j] = (T)(-rw[j]);
+#pragma unroll
+      for (int j = 3; j < 9; ++j) g[j] = (T)(-d[j]);
+    }
+  }
+  if (i < 3LL * P) {
+    const int p = (int)(i / 3);
+    gp[i] = pt_act[p] ? (T)(-dL_dp[i]) : T(0);
+  }
+}
+
+template <typename T>
+cudaError_t launch_adjoint_rhs(int C, int P, const double* cams64, const int* crank, const uint8_t* pt_act,
+                               const double* dL_dc, const double* dL_dp, T* Ug, T* gp, cudaStream_t s) {
+  const long long n = std::max((long long)C, 3LL * P);
+  if (n > 0)
+    k_adjoint_rhs<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C, P, cams64, crank, pt_act, dL_dc, dL_dp, Ug, gp);
+  return cudaGetLastError();
+}
+
+// One thread per point-order observation; outputs in the input order.
+template <typename T>
+__global__ void k_adjoint_obs(Layout L, ModelParams mp, const T* __restrict__ camw, const T* __restrict__ ptsw,
+                              const uint8_t* __restrict__ act_po, const int* __restrict__ crank,
+                              const T* __restrict__ x, const T* __restrict__ dp, double* __restrict__ duv,
+                              double* __restrict__ ddepth) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= L.N) return;
+  const int o = L.po_orig[k];
+  if (!act_po[k]) {
+    duv[2 * (size_t)o] = 0.0;
+    duv[2 * (size_t)o + 1] = 0.0;
+    ddepth[o] = 0.0;
+    return;
+  }
+  const T* po_uv = reinterpret_cast<const T*>(L.po_uvw);
+  const T* po_tau = reinterpret_cast<const T*>(L.po_tauw);
+  const int c = L.po_cam[k], p = L.po_pt[k];
+  T cw[kCamStride];
+#pragma unroll
+  for (int q = 0; q < kCamStride; ++q) cw[q] = camw[kCamStride * (size_t)c + q];
+  const T* X = ptsw + 4 * (size_t)p;
+  const T tau = po_tau[k];
+  const T sw = tau > T(0) ? (T)mp.sw_valid : (T)mp.sw_invalid;
+  ObsLin<T> ol;
+  linearize_obs<T>(cw, X[0], X[1], X[2], po_uv[2 * (size_t)k], po_uv[2 * (size_t)k + 1], tau, sw, (T)mp.cx,
+                   (T)mp.cy, (T)mp.huber, ol);
+  T mc[9];
+  const int cr = crank[c];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) mc[i] = cr >= 0 ? x[9 * (size_t)cr + i] : T(0);
+  const T m0 = dp[3 * (size_t)p], m1 = dp[3 * (size_t)p + 1], m2 = dp[3 * (size_t)p + 2];
+  T Jm[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    T acc = ol.Jp[r][0] * m0 + ol.Jp[r][1] * m1 + ol.Jp[r][2] * m2;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) acc += ol.Jc[r][i] * mc[i];
+    Jm[r] = acc;
+  }
+  duv[2 * (size_t)o] = (double)(ol.wrob * Jm[0]);
+  duv[2 * (size_t)o + 1] = (double)(ol.wrob * Jm[1]);
+  ddepth[o] = tau > T(0) ? (double)(-ol.wrob * sw * tau * tau * Jm[2]) : 0.0;
+}
+
+template <typename T>
+cudaError_t launch_adjoint_obs(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
+                               const uint8_t* act_po, const int* crank, const T* x, const T* dp, double* duv,
+                               double* ddepth, cudaStream_t s) {
+  if (L.N > 0) k_adjoint_obs<T><<<(L.N + 255) / 256, 256, 0, s>>>(L, mp, camw, ptsw, act_po, crank, x, dp, duv, ddepth);
+  return cudaGetLastError();
+}
+
+#define BAB_INST_ADJ(T)                                                                                   \
+  template cudaError_t launch_adjoint_rhs<T>(int, int, const double*, const int*, const uint8_t*,      \
+                                             const double*, const double*, T*, T*, cudaStream_t);        \
+  template cudaError_t launch_adjoint_obs<T>(const Layout&, const ModelParams&, const T*, const T*,     \
+                                             const uint8_t*, const int*, const T*, const T*, double*,    \
+                                             double*, cudaStream_t);
+BAB_INST_ADJ(float)
+BAB_INST_ADJ(double)
+
+}  // namespace bab

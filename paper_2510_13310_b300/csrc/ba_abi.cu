@@ -123,6 +123,8 @@ struct ba_problem {
   bool solved = false;
 
   cudaEvent_t ev[8] = {};
+  cudaEvent_t evk[2] = {};  // around the PCG kernel launch of the latest solve
+  bool evk_valid = false;
 };
 
 namespace {
@@ -321,7 +323,10 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     size_t smem = spcg_smem_bytes<T>(a.n, a.own_max, a.rows_in_smem);
     int grid = std::min(pb->spcg_grid, Cf);
     CU(cudaMemsetAsync(pb->bar, 0, sizeof(unsigned), pb->stream));
+    CU(cudaEventRecord(pb->evk[0], pb->stream));
     LAUNCH(1, launch_spcg<T>(a, grid, smem, pb->stream));
+    CU(cudaEventRecord(pb->evk[1], pb->stream));
+    pb->evk_valid = true;
   }
   LAUNCH(1, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                                   pb->pt_act, pb->crank, (const T*)pb->x, (const T*)pb->Vinv, (const T*)pb->V,
@@ -380,7 +385,10 @@ ba_status pcg_t(ba_problem* pb, double lambda) {
   size_t smem = pcg_smem_bytes<T>(a.n, pb->C, pb->pcg_stages, pb->pcg_own_max, pb->recompute,
                                   pb->cam_in_smem, pb->max_tiles_per_block);
   CU(cudaMemsetAsync(pb->bar, 0, sizeof(unsigned), pb->stream));
+  CU(cudaEventRecord(pb->evk[0], pb->stream));
   LAUNCH(1, launch_pcg<T>(a, pb->pcg_grid, smem, pb->stream));
+  CU(cudaEventRecord(pb->evk[1], pb->stream));
+  pb->evk_valid = true;
   LAUNCH(1, launch_pred_cams<T>(Cf, pb->cam_map, (const T*)pb->x, (const T*)pb->Ug, (const T*)pb->dampc,
                                 lambda, pb->pred_parts, pb->pcg_grid, pb->stream));
   LAUNCH(1, launch_reduce_pred(pb->pred_parts, pb->pcg_grid + 1, pb->sc, pb->stream));
@@ -427,6 +435,21 @@ ba_status solve_damped(ba_problem* pb, double lambda) {
   return BA_OK;
 }
 
+// Implicit adjoint: undamped Schur solve of H mu = dL/dtheta (gradient slot
+// replaced by -dL/dtheta), then rho'_k (J_k mu) per observation.
+template <typename T>
+ba_status backward_t(ba_problem* pb, const double* dc, const double* dpts, double* duv, double* dd) {
+  LAUNCH(1, launch_adjoint_rhs<T>(pb->C, pb->P, pb->cams64[pb->cur], pb->crank, pb->pt_act, dc, dpts,
+                                  (T*)pb->Ug, (T*)pb->gp, pb->stream));
+  pb->linearized = false;  // the gradient slots now hold the adjoint right-hand side
+  ST(schur_t<T>(pb, 0.0));
+  ST(pcg_t<T>(pb, 0.0));
+  int s = pb->cur;
+  LAUNCH(1, launch_adjoint_obs<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
+                                  pb->crank, (const T*)pb->x, (const T*)pb->dp, duv, dd, pb->stream));
+  return BA_OK;
+}
+
 ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   const ba_options& o = pb->opt;
   int k = pb->iter;
@@ -448,6 +471,7 @@ ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   if (pb->fp64) ST(schur_t<double>(pb, lambda));
   else ST(schur_t<float>(pb, lambda));
   CU(cudaEventRecord(pb->ev[3], pb->stream));
+  pb->evk_valid = false;
   if (pb->fp64) ST(pcg_t<double>(pb, lambda));
   else ST(pcg_t<float>(pb, lambda));
   CU(cudaEventRecord(pb->ev[4], pb->stream));
@@ -484,6 +508,8 @@ ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
     info->n_obs_act = pb->n_obs_act;
     for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&info->ms[i], pb->ev[i], pb->ev[i + 1]);
     cudaEventElapsedTime(&info->ms[6], pb->ev[0], pb->ev[6]);
+    info->ms[4] = 0.f;
+    if (pb->evk_valid) cudaEventElapsedTime(&info->ms[4], pb->evk[0], pb->evk[1]);
   }
   if (accept) {
     pb->cur = nxt;
@@ -970,6 +996,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   CU(cudaMallocHost(&pb->h_sc, sizeof(Scalars)));
   memset(pb->h_sc, 0, sizeof(Scalars));
   for (auto& e : pb->ev) CU(cudaEventCreate(&e));
+  for (auto& e : pb->evk) CU(cudaEventCreate(&e));
 
   // working copies of the initial state
   if (pb->fp64) {
@@ -989,6 +1016,8 @@ void free_problem(ba_problem* pb) {
   for (void* p : pb->allocs) cudaFree(p);
   if (pb->h_sc) cudaFreeHost(pb->h_sc);
   for (auto& e : pb->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : pb->evk)
     if (e) cudaEventDestroy(e);
   delete pb;
 }
@@ -1285,16 +1314,63 @@ ba_status ba_eval_cost(ba_problem* pb, const double* cams, const double* pts, do
 
 ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_dpts,
                       double* dL_duv, double* dL_ddepth) {
-  (void)dL_dcams;
-  (void)dL_dpts;
-  (void)dL_duv;
-  (void)dL_ddepth;
-  if (!pb) return BA_ERR_INVALID_ARG;
-  set_error("ba_backward: not available in this build");
-  return BA_ERR_STATE;
+  if (!pb || !dL_dcams || !dL_dpts || !dL_duv || !dL_ddepth) {
+    set_error("ba_backward: NULL argument");
+    return BA_ERR_INVALID_ARG;
+  }
+  ST(ensure_linearized(pb));
+  const size_t C = (size_t)pb->C, P = (size_t)pb->P, N = (size_t)pb->N;
+  // device staging: dL/dcams, dL/dpts in; dL/duv, dL/ddepth out
+  double* buf = nullptr;
+  const size_t nb = 9 * C + 3 * P + 3 * N + 1;
+  CU(cudaMallocAsync(&buf, sizeof(double) * nb, pb->stream));
+  double *dc = buf, *dpv = buf + 9 * C, *duv = dpv + 3 * P, *dd = duv + 2 * N;
+  cudaError_t e = cudaSuccess;
+  if (C) e = cudaMemcpyAsync(dc, dL_dcams, sizeof(double) * 9 * C, cudaMemcpyDefault, pb->stream);
+  if (e == cudaSuccess && P) e = cudaMemcpyAsync(dpv, dL_dpts, sizeof(double) * 3 * P, cudaMemcpyDefault, pb->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pb->err, 0, sizeof(int), pb->stream);
+  ba_status st = BA_OK;
+  if (e != cudaSuccess) {
+    set_error("ba_backward: %s", cudaGetErrorString(e));
+    st = BA_ERR_CUDA;
+  } else {
+    st = pb->fp64 ? backward_t<double>(pb, dc, dpv, duv, dd) : backward_t<float>(pb, dc, dpv, duv, dd);
+  }
+  int h_err = 0;
+  if (st == BA_OK) {
+    e = cudaMemcpyAsync(pb->h_sc, pb->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, pb->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, pb->err, sizeof(int), cudaMemcpyDeviceToHost, pb->stream);
+    if (e == cudaSuccess && N) e = cudaMemcpyAsync(dL_duv, duv, sizeof(double) * 2 * N, cudaMemcpyDefault, pb->stream);
+    if (e == cudaSuccess && N) e = cudaMemcpyAsync(dL_ddepth, dd, sizeof(double) * N, cudaMemcpyDefault, pb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pb->stream);
+    if (e != cudaSuccess) {
+      set_error("ba_backward: %s", cudaGetErrorString(e));
+      st = BA_ERR_CUDA;
+    }
+  }
+  cudaFreeAsync(buf, pb->stream);
+  if (st != BA_OK) return st;
+  if (h_err & 1) {
+    set_error("ba_backward: PCG grid barrier timed out");
+    return BA_ERR_TIMEOUT;
+  }
+  if (h_err & 14) {
+    set_error("ba_backward: the undamped system is singular (flags %d)", h_err);
+    return BA_ERR_NONFINITE;
+  }
+  if (pb->h_sc->pcg_iters >= pb->opt.pcg_max_iters) {
+    set_error("ba_backward: PCG reached its iteration cap (relative residual %g)", pb->h_sc->pcg_rel_res);
+    return BA_ERR_NOT_CONVERGED;
+  }
+  return BA_OK;
 }
 
 int64_t ba_kernel_launches(const ba_problem* pb) { return pb ? pb->launches : 0; }
+
+int ba_solver_kind(const ba_problem* pb) {
+  if (!pb) return 0;
+  return pb->explicit_S ? BA_SOLVER_EXPLICIT : BA_SOLVER_IMPLICIT;
+}
 
 void ba_destroy(ba_problem* pb) { free_problem(pb); }
 

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace bab {
@@ -193,6 +195,13 @@ cudaError_t launch_candidate(int C, int P, const int* crank, const T* x, const T
                              cudaStream_t s);
 template <typename T>
 cudaError_t launch_scatter_cams(int C, const int* crank, const T* x, double* dc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint_rhs(int C, int P, const double* cams64, const int* crank, const uint8_t* pt_act,
+                               const double* dL_dc, const double* dL_dp, T* Ug, T* gp, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint_obs(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
+                               const uint8_t* act_po, const int* crank, const T* x, const T* dp, double* duv,
+                               double* ddepth, cudaStream_t s);
 template <typename T>
 cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t s);
 cudaError_t launch_permute_u8(const int* orig, const uint8_t* src, uint8_t* dst, int N,

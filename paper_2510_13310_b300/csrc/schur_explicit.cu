@@ -41,43 +41,65 @@ __device__ __forceinline__ void obs_W(const T* cw, const T* X, T u, T v, T tau, 
 
 // Per point-order observation k (camera a, point p): Y^_k = D_a^-1 W_k M_p with
 // M_p M_p^T = V*_p^-1 (3x3 Cholesky), so that W_k V*_p^-1 W_k'^T scaled by the
-// Jacobi factors is the plain product Y^_k Y^_k'^T.  Rows of observations of
-// cameras that are not free are not written (their blocks are never formed);
-// an inactive observation has W = 0 and gets Y^ = 0.
+// Jacobi factors is the plain product Y^_k Y^_k'^T.  A block takes 128
+// consecutive rows: W rows are brought into shared memory with 16-byte
+// coalesced loads, transformed in place one row per thread, and stored back the
+// same way.  Rows of observations of cameras that are not free are zero (their
+// blocks are never formed); an inactive observation has W = 0 and gets Y^ = 0.
+constexpr int kYRows = 128;
+
 template <typename T>
-__global__ void k_form_Y(int N, const int* __restrict__ po_cam, const int* __restrict__ po_pt,
-                         const T* __restrict__ W, const T* __restrict__ Vinv, const int* __restrict__ crank,
-                         const double* __restrict__ dscale, int Cf, T* __restrict__ Y) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  const int a = crank[po_cam[k]];
-  if (a < 0) return;
-  const T* dinv = reinterpret_cast<const T*>(dscale + 9 * Cf) + 9 * a;
-  const T* vi = Vinv + 6 * (size_t)po_pt[k];
-  const T v00 = vi[0], v01 = vi[1], v02 = vi[2], v11 = vi[3], v12 = vi[4], v22 = vi[5];
-  T l00 = T(0), l10 = T(0), l20 = T(0), l11 = T(0), l21 = T(0), l22 = T(0);
-  if (v00 > T(0)) {
-    l00 = sqrt(v00);
-    const T r0 = T(1) / l00;
-    l10 = v01 * r0;
-    l20 = v02 * r0;
-    const T d1 = v11 - l10 * l10;
-    if (d1 > T(0)) {
-      l11 = sqrt(d1);
-      l21 = (v12 - l20 * l10) / l11;
-    }
-    const T d2 = v22 - l20 * l20 - l21 * l21;
-    l22 = d2 > T(0) ? sqrt(d2) : T(0);
-  }
-  const T* w = W + kWStride * (size_t)k;
-  T* y = Y + kWStride * (size_t)k;
+__global__ void __launch_bounds__(kYRows) k_form_Y(int N, const int* __restrict__ po_cam,
+                                                  const int* __restrict__ po_pt, const T* __restrict__ W,
+                                                  const T* __restrict__ Vinv, const int* __restrict__ crank,
+                                                  const double* __restrict__ dscale, int Cf,
+                                                  T* __restrict__ Y) {
+  __shared__ __align__(16) T buf[kYRows * kWStride];
+  constexpr int kVec = (int)(kWStride * sizeof(T) / 16);  // 16-byte words per row
+  const int k0 = blockIdx.x * kYRows;
+  const int rows = min(kYRows, N - k0);
+  const uint4* src = reinterpret_cast<const uint4*>(W + kWStride * (size_t)k0);
+  uint4* sb = reinterpret_cast<uint4*>(buf);
+  for (int i = threadIdx.x; i < rows * kVec; i += kYRows) sb[i] = src[i];
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < rows) {
+    const int k = k0 + t;
+    T* y = buf + kWStride * t;
+    const int a = crank[po_cam[k]];
+    if (a < 0) {
 #pragma unroll
-  for (int r = 0; r < 9; ++r) {
-    const T w0 = w[3 * r], w1 = w[3 * r + 1], w2 = w[3 * r + 2], sc = dinv[r];
-    y[3 * r] = sc * (w0 * l00 + w1 * l10 + w2 * l20);
-    y[3 * r + 1] = sc * (w1 * l11 + w2 * l21);
-    y[3 * r + 2] = sc * (w2 * l22);
+      for (int q = 0; q < 27; ++q) y[q] = T(0);
+    } else {
+      const T* dinv = reinterpret_cast<const T*>(dscale + 9 * Cf) + 9 * a;
+      const T* vi = Vinv + 6 * (size_t)po_pt[k];
+      const T v00 = vi[0], v01 = vi[1], v02 = vi[2], v11 = vi[3], v12 = vi[4], v22 = vi[5];
+      T l00 = T(0), l10 = T(0), l20 = T(0), l11 = T(0), l21 = T(0), l22 = T(0);
+      if (v00 > T(0)) {
+        l00 = sqrt(v00);
+        const T r0 = T(1) / l00;
+        l10 = v01 * r0;
+        l20 = v02 * r0;
+        const T d1 = v11 - l10 * l10;
+        if (d1 > T(0)) {
+          l11 = sqrt(d1);
+          l21 = (v12 - l20 * l10) / l11;
+        }
+        const T d2 = v22 - l20 * l20 - l21 * l21;
+        l22 = d2 > T(0) ? sqrt(d2) : T(0);
+      }
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        const T w0 = y[3 * r], w1 = y[3 * r + 1], w2 = y[3 * r + 2], sc = dinv[r];
+        y[3 * r] = sc * (w0 * l00 + w1 * l10 + w2 * l20);
+        y[3 * r + 1] = sc * (w1 * l11 + w2 * l21);
+        y[3 * r + 2] = sc * (w2 * l22);
+      }
+    }
   }
+  __syncthreads();
+  uint4* dst = reinterpret_cast<uint4*>(Y + kWStride * (size_t)k0);
+  for (int i = threadIdx.x; i < rows * kVec; i += kYRows) dst[i] = sb[i];
 }
 
 template <typename T>
@@ -219,7 +241,7 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
   if (Cf <= 0) return cudaSuccess;
   const int n = 9 * Cf;
   k_dscale<T><<<(n + 255) / 256, 256, 0, s>>>(Cf, Ud, dscale);
-  if (L.N > 0) k_form_Y<T><<<(L.N + 255) / 256, 256, 0, s>>>(L.N, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
+  if (L.N > 0) k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
   cudaError_t e = cudaMemsetAsync(Shat, 0, sizeof(T) * (size_t)n * n, s);
   if (e != cudaSuccess) return e;
   if (n_runs > 0) {

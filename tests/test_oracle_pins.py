@@ -406,3 +406,78 @@ def test_residual_drop_is_sticky_and_thresholds_apply():
     assert dropped[sc.is_outlier].mean() > 0.9
     assert dropped[~sc.is_outlier].mean() < 0.01
     assert rows[-1]["n_obs_act"] <= sc.n_obs - dropped.sum()
+
+
+# --------------------------------------------------------------------------
+# implicit adjoint (Sec. 3.3 normal equations at the optimum)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("w", [[0.0, 0.0, 0.0], [2e-5, -1e-5, 3e-5], [0.3, -0.7, 0.2],
+                               [1.2, 2.1, -0.4], [0.0, 3.0, 0.1]])
+def test_so3_left_jacobian_inverse_is_update_derivative(w):
+    """d Log(Exp(dw) Exp(w)) / d dw at dw = 0, by central differences through SciPy."""
+    w = np.asarray(w, dtype=np.float64)
+    J = oracle.so3_left_jacobian_inv(w)
+    h = 1e-6
+    fd = np.zeros((3, 3))
+    R = Rotation.from_rotvec(w)
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        wp = (Rotation.from_rotvec(e) * R).as_rotvec()
+        wm = (Rotation.from_rotvec(-e) * R).as_rotvec()
+        fd[:, j] = (wp - wm) / (2 * h)
+    np.testing.assert_allclose(J, fd, atol=2e-8)
+
+
+def _converge(ob, cams, pts, iters=40):
+    c, p, _ = ob.lm(cams, pts, iters)
+    return c, p
+
+
+def test_adjoint_matches_finite_differences_of_reconverged_oracle():
+    """Low-noise scene (0.01 px, depth-prior noise 1e-4, no outliers): Gauss-Newton
+    is the exact Hessian up to O(residual), so the implicit gradient of L = |cams - gt|^2/2 + |pts - gt|^2/2
+    with respect to pixels and depth priors matches central differences of the
+    fully re-converged FP64 LM."""
+    spec = dataclasses.replace(scenes.SPECS["small"], n_cams=6, n_pts=50, track_min=4,
+                               track_max=4, track_mean=4, pixel_sigma=0.01, depth_sigma=1e-4,
+                               seed=21)
+    sc = scenes.make_scene(spec, outliers=False)
+    ob = oracle.OracleBA(sc.cams0.shape[0], sc.pts0.shape[0], sc.obs_cam, sc.obs_pt,
+                         sc.obs_uv.copy(), sc.depth.copy(), sc.fixed_cams)
+    c, p = _converge(ob, sc.cams0, sc.pts0, 60)
+    valid, _ = ob.predicate(c, p)
+    ext = ob.extract(valid)
+    assert ext["obs_mask"].all()
+
+    def loss(cc, pp):
+        return 0.5 * np.sum((cc - sc.cams_gt) ** 2) + 0.5 * np.sum((pp - sc.pts_gt) ** 2)
+
+    duv, dd = ob.backward(c, p, ext, c - sc.cams_gt, p - sc.pts_gt)
+    rng = np.random.default_rng(3)
+    ks = rng.choice(sc.n_obs, 8, replace=False)
+    kd = rng.choice(np.flatnonzero(sc.depth > 0), 4, replace=False)
+    scale = max(np.abs(duv).max(), 1e-12)
+    for k in ks:
+        for j in range(2):
+            h = 1e-4
+            ob.obs_uv[k, j] += h
+            Lp = loss(*_converge(ob, c, p))
+            ob.obs_uv[k, j] -= 2 * h
+            Lm = loss(*_converge(ob, c, p))
+            ob.obs_uv[k, j] += h
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - duv[k, j]) <= 2e-3 * scale, (k, j, fd, duv[k, j])
+    dscale = max(np.abs(dd).max(), 1e-12)
+    for k in kd:
+        h = 1e-3 * ob.depth[k]  # smaller steps move the cost by less than LM resolves
+        ob.depth[k] += h
+        Lp = loss(*_converge(ob, c, p))
+        ob.depth[k] -= 2 * h
+        Lm = loss(*_converge(ob, c, p))
+        ob.depth[k] += h
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - dd[k]) <= 2e-3 * dscale, (k, fd, dd[k])
+    # observations without a prior have no depth gradient
+    assert np.all(dd[~(sc.depth > 0)] == 0.0)
