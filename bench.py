@@ -32,6 +32,11 @@ sys.path.insert(0, ROOT)
 from paper_2510_13310_b300 import scenes  # noqa: E402
 
 METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 GPU"
+
+# DRAM bytes (read + write) of one launch of the roofline kernel, from an ncu
+# capture of this workload (profiles/k_spcg_medium_1M_obs.md); None once the
+# kernel has changed since the counters were taken.
+NCU_TRAFFIC = {"k_spcg": 12992256 + 512, "k_pcg": None}
 WORKLOAD = "medium"
 LM_ITERS = 30
 
@@ -251,7 +256,8 @@ def main():
     achieved = per_launch / (kern_ms * 1e-3) / 1e9 if kern_ms else 0.0
     roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_kind + " (burst copy)",
-                "traffic": None, "algorithmic_bytes_per_launch": per_launch,
+                "traffic": NCU_TRAFFIC["k_spcg" if prob.explicit_solver else "k_pcg"],
+                "algorithmic_bytes_per_launch": per_launch,
                 "bytes_formula": unit_txt, "launch_ms_mean": kern_ms,
                 "mean_pcg_iters": mean_it, "us_per_pcg_iter": (kern_ms * 1e3 / mean_it) if mean_it else None,
                 "solver": "explicit" if prob.explicit_solver else "implicit"}
