@@ -196,6 +196,25 @@ ba_status ba_eval_cost_noalloc(const ba_options* opts, void* stream, int64_t n_c
                                const double* obs_uv, const double* depth,
                                const uint8_t* obs_mask, double* out);
 
+/* C = alpha A B^T + beta C on the tensor cores (tcgen05.mma kind::tf32: FP32
+ * operands enter as TF32, FP32 accumulation).  The dense-system factorisation's
+ * building block, exposed on its own.  A [M][lda], B [N][ldb], C [M][ldc]
+ * row-major device pointers of the current device; lda, ldb multiples of 4 and
+ * A, B 16-byte aligned (tensor-map rules); M, N, K < 2^31.  Ordered on stream;
+ * returns after completion. */
+ba_status ba_tc_gemm_nt(void* stream, int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
+
+/* Blocked Cholesky A = L L^T of an n x n symmetric positive definite FP32 matrix
+ * (lower triangle of A read; host or device pointers, row-major) on the tensor
+ * cores: 128 x 128 tiles, diagonal tiles factored and inverted in FP32, the
+ * off-diagonal solves and the trailing updates as TF32 products (so L carries
+ * TF32-level error, ~1e-3 relative; it is meant as a preconditioner or for
+ * refinement).  L [n][ldl] receives the lower factor with zeros above.  flags
+ * (nullable): bit 32 = a pivot was not positive (BA_ERR_NONFINITE). n <= 65536. */
+ba_status ba_dense_cholesky(void* stream, int64_t n, const float* A, int64_t lda, float* L, int64_t ldl,
+                            int* flags);
+
 /* Number of this library's kernels launched since creation (counts launches). */
 int64_t ba_kernel_launches(const ba_problem* pb);
 

@@ -25,8 +25,8 @@ BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT = 0, 1, 2
 # every symbol include/ba_b300.h declares
 EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
-           "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_kernel_launches", "ba_solver_kind",
-           "ba_destroy",
+           "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
+           "ba_kernel_launches", "ba_solver_kind", "ba_destroy",
            "ba_status_string", "ba_last_error")
 
 
@@ -91,13 +91,16 @@ def lib():
         L.ba_kernel_launches.restype = ct.c_int64
         L.ba_solver_kind.argtypes = [vp]
         L.ba_solver_kind.restype = ct.c_int
+        L.ba_tc_gemm_nt.argtypes = [vp, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_float, vp, ct.c_int64, vp,
+                                    ct.c_int64, ct.c_float, vp, ct.c_int64]
+        L.ba_dense_cholesky.argtypes = [vp, ct.c_int64, vp, ct.c_int64, vp, ct.c_int64, ct.POINTER(ct.c_int)]
         L.ba_destroy.argtypes = [vp]
         L.ba_status_string.argtypes = [ct.c_int]
         L.ba_status_string.restype = ct.c_char_p
         L.ba_last_error.restype = ct.c_char_p
         for f in ("ba_create", "ba_lm_step", "ba_solve", "ba_get_params", "ba_set_params",
                   "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped", "ba_eval_cost",
-                  "ba_backward", "ba_eval_cost_noalloc"):
+                  "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -384,3 +387,41 @@ def bundle_adjust(cams0, pts0, obs_uv, depth, obs_cam, obs_pt, options: Options 
     if _BAFunction is None:
         _BAFunction = _make_ba_function()
     return _BAFunction.apply(cams0, pts0, obs_uv, depth, obs_cam, obs_pt, options or Options(), iters)
+
+
+def tc_gemm_nt(A, B, C=None, alpha=1.0, beta=0.0, stream=None):
+    """ba_tc_gemm_nt: C = alpha A B^T + beta C on the tensor cores (TF32 inputs, FP32
+    accumulation).  A [M,K], B [N,K], C [M,N]: contiguous float32 CUDA tensors."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float32, device=A.device)
+    for t in (A, B, C):
+        if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError("tc_gemm_nt: contiguous float32 CUDA tensors")
+    L = lib()
+    _check(L.ba_tc_gemm_nt(_stream_handle(stream), M, N, K, float(alpha), ct.c_void_p(A.data_ptr()), A.stride(0),
+                           ct.c_void_p(B.data_ptr()), B.stride(0), float(beta), ct.c_void_p(C.data_ptr()),
+                           C.stride(0)), "ba_tc_gemm_nt")
+    return C
+
+
+def dense_cholesky(A, stream=None):
+    """ba_dense_cholesky: lower factor L of an SPD float32 matrix (NumPy or torch,
+    host or device); returns L like A (NumPy in, NumPy out) and the flags."""
+    n = A.shape[0]
+    is_torch = hasattr(A, "data_ptr")
+    if is_torch:
+        import torch
+        A = A.contiguous().to(torch.float32)
+        Lo = torch.empty_like(A)
+        pa, pl = A.data_ptr(), Lo.data_ptr()
+    else:
+        A = np.ascontiguousarray(A, dtype=np.float32)
+        Lo = np.empty_like(A)
+        pa, pl = A.ctypes.data, Lo.ctypes.data
+    flags = ct.c_int(0)
+    _check(lib().ba_dense_cholesky(_stream_handle(stream), n, ct.c_void_p(pa), n, ct.c_void_p(pl), n,
+                                   ct.byref(flags)), "ba_dense_cholesky", allow=(BA_OK, BA_ERR_NONFINITE))
+    return Lo, flags.value

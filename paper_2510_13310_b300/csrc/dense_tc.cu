@@ -1,0 +1,570 @@
+// dense_tc.cu -- dense symmetric positive definite factorisation of the reduced
+// camera system on the 5th-generation tensor cores (tcgen05, kind::tf32).
+//
+// When many cameras see the same points the Schur complement S (Eq. LM, Schur
+// form) is dense, and a direct factorisation replaces hundreds of PCG
+// iterations.  S^ = L L^T is computed by a blocked right-looking Cholesky:
+// 128 x 128 tiles, panels of kPanelTiles tile columns.  Per tile column j the
+// diagonal tile is factored and inverted on CUDA cores in FP32 (k_potrf_tile);
+// the tiles below it become L_ij = A_ij L_jj^-T, a product with the explicit
+// inverse; the remaining tile columns of the panel are updated with K = 128.
+// After each panel the trailing matrix takes one rank-(128 kPanelTiles) update
+// A_il -= L_i,P L_l,P^T, the bulk of the n^3/3 flops.  All three products run
+// in k_tc_gemm_nt: operands streamed by TMA (128-byte swizzle) through a
+// 4-stage mbarrier ring, tcgen05.mma issued by one thread, FP32 accumulators in
+// tensor memory, read back with tcgen05.ld for the epilogue.  Operands are FP32
+// in memory and enter the tensor cores as TF32 (10-bit mantissa); the factor is
+// used as a preconditioner, so the solution is recovered to FP32 accuracy by
+// the conjugate-gradient refinement in dense_solve.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "../../include/ba_b300.h"
+#include "internal.h"
+#include "tma.cuh"
+
+namespace bab {
+
+constexpr int kTcBM = 128;      // output tile rows (UMMA M)
+constexpr int kTcBN = 256;      // output tile columns (UMMA N)
+constexpr int kTcBK = 32;       // K per pipeline stage: 32 FP32 = one 128-byte swizzle row
+constexpr int kTcStages = 4;
+constexpr int kTcThreads = 128;
+constexpr int kTcStageBytes = (kTcBM + kTcBN) * kTcBK * 4;  // 48 KB
+constexpr int kTcSmem = kTcStages * kTcStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr long long kTcTimeoutNs = 1000000000LL;
+
+cudaError_t tc_gemm_nt(const float* A, long long lda, const float* B, long long ldb, float* C, long long ldc,
+                       int M, int N, int K, float alpha, float beta, bool lower_only, int* err, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// tcgen05 / TMA inline PTX
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand in the 128-byte swizzled
+// layout TMA writes: rows of 128 B, 8-row groups 1024 B apart (SBO), leading
+// offset unused for this layout, descriptor version 1, swizzle mode 128B.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: D F32, A and B TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// mbarrier arrives once every tcgen05.mma issued so far by this thread has completed.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 TMEM lanes x 32 consecutive 32-bit columns: thread i of the warp gets lane
+// (lane base + i), columns [col, col + 32).
+__device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// C = alpha A B^T + beta C over a grid of 128 x 256 output tiles.
+// A: M x K, B: N x K, both row-major FP32 (K contiguous), seen through tensor
+// maps with boxes {32, 128} and {32, 256}; rows and columns past M, N, K read
+// as zero.  C row-major, ldc.  lower_only: tiles wholly above the diagonal
+// (first row > last column... i.e. row tile end <= column tile start) are
+// skipped; used for symmetric updates of the lower triangle.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm_nt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* C,
+                 long long ldc, int M, int N, int K, float alpha, float beta, int tiles_n, int lower_only,
+                 int vec_ok, int* err) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  const int tm = blockIdx.x / tiles_n, tn = blockIdx.x - (blockIdx.x / tiles_n) * tiles_n;
+  const int row0 = tm * kTcBM, col0 = tn * kTcBN;
+  if (lower_only && row0 + kTcBM <= col0) return;
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + kTcStages * kTcStageBytes);
+  uint64_t* empty = full + kTcStages;
+  uint64_t* done = empty + kTcStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, kTcBN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int nk = (K + kTcBK - 1) / kTcBK;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kTcStages;
+      if (kb >= kTcStages && !mbar_wait(&empty[s], ((kb / kTcStages) & 1) ^ 1, kTcTimeoutNs)) {
+        ok = false;
+        break;
+      }
+      unsigned char* sa = base + s * kTcStageBytes;
+      unsigned char* sb = sa + kTcBM * kTcBK * 4;
+      mbar_arrive_expect_tx(&full[s], kTcStageBytes);
+      tma_load_2d(sa, &tmA, kb * kTcBK, row0, &full[s]);
+      tma_load_2d(sb, &tmB, kb * kTcBK, col0, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: 4 x (128 x 256 x 8) per stage
+    constexpr uint32_t idesc = umma_idesc_tf32(kTcBM, kTcBN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kTcStages;
+      if (!mbar_wait(&full[s], (kb / kTcStages) & 1, kTcTimeoutNs)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = smem_u32(base + s * kTcStageBytes);
+      const uint32_t sb = sa + kTcBM * kTcBK * 4;
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 8; ++kk)
+        umma_tf32(tmem, umma_desc_sw128(sa + kk * 32), umma_desc_sw128(sb + kk * 32), idesc,
+                  (kb > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(&empty[s]);
+    }
+    umma_commit(done);
+  }
+  __syncwarp();
+  // epilogue: warp w reads TMEM lanes [32w, 32w + 32) = tile rows
+  if (!mbar_wait(done, 0, kTcTimeoutNs)) ok = false;
+  tc_fence_after();
+  const int r = row0 + warp * 32 + lane;
+  for (int c = 0; c < kTcBN / 32; ++c) {
+    float v[32];
+    tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+    const int cc = col0 + c * 32;
+    if (!ok || r >= M || cc >= N) continue;
+    float* crow = C + (size_t)r * ldc + cc;
+    if (cc + 32 <= N && vec_ok) {
+      float4* c4 = reinterpret_cast<float4*>(crow);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (beta != 0.f) o = c4[q];
+        o.x = alpha * v[4 * q] + beta * o.x;
+        o.y = alpha * v[4 * q + 1] + beta * o.y;
+        o.z = alpha * v[4 * q + 2] + beta * o.z;
+        o.w = alpha * v[4 * q + 3] + beta * o.w;
+        c4[q] = o;
+      }
+    } else {
+      for (int q = 0; q < 32 && cc + q < N; ++q) crow[q] = alpha * v[q] + (beta != 0.f ? beta * crow[q] : 0.f);
+    }
+  }
+  if (!ok && lane == 0) atomicOr(err, 16);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTcBN);
+}
+
+// ---------------------------------------------------------------------------
+// One 128 x 128 diagonal tile: L = chol(A) in place (lower triangle; the upper
+// triangle is left as it was) and its inverse L^-1 (lower, zeros above) into a
+// separate 128 x 128 buffer.  FP32, one block of 512 threads, left-looking over
+// four 32-column blocks: update the block column with the columns before it,
+// factor its 32 x 32 diagonal block in one warp (row per lane, registers and
+// shuffles), solve the rows below it.  The inverse: inverses of the four
+// diagonal blocks (one warp each, forward substitution per column), then the
+// off-diagonal blocks by distance, X_ij = -X_ii sum_k L_ik X_kj.
+// A pivot <= 0 (not positive definite in FP32) sets err bit 32 and is replaced
+// by a tiny positive value so that the outputs stay finite.
+// ---------------------------------------------------------------------------
+constexpr int kPt = 128;
+constexpr int kPtLd = kPt + 1;
+constexpr int kPtThreads = 512;
+constexpr int kPtSmem = (2 * kPt * kPtLd + 3 * 32 * 33) * 4;
+
+__global__ void __launch_bounds__(kPtThreads) k_potrf_tile(float* __restrict__ A, long long lda,
+                                                          float* __restrict__ Linv, int* err) {
+  extern __shared__ float pt_smem[];
+  float* T = pt_smem;               // [128][129]
+  float* X = T + kPt * kPtLd;       // [128][129]
+  float* Sc = X + kPt * kPtLd;      // [3][32][33]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int q = tid; q < kPt * kPt; q += kPtThreads) {
+    const int r = q >> 7, c = q & 127;
+    T[r * kPtLd + c] = c <= r ? A[(size_t)r * lda + c] : 0.f;
+    X[r * kPtLd + c] = 0.f;
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int b = 0; b < 4; ++b) {
+    const int c0 = 32 * b;
+    if (b > 0) {
+      for (int q = tid; q < (kPt - c0) * 32; q += kPtThreads) {
+        const int r = c0 + (q >> 5), c = c0 + (q & 31);
+        if (r < c) continue;
+        float acc = T[r * kPtLd + c];
+        for (int l = 0; l < c0; ++l) acc -= T[r * kPtLd + l] * T[c * kPtLd + l];
+        T[r * kPtLd + c] = acc;
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      float R[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) R[j] = j <= lane ? T[(c0 + lane) * kPtLd + c0 + j] : 0.f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        float dkk = __shfl_sync(0xffffffffu, R[k], k);
+        if (!(dkk > 0.f)) {
+          bad = true;
+          dkk = 1e-30f;
+        }
+        const float piv = sqrtf(dkk), ip = 1.f / piv;
+        if (lane == k) R[k] = piv;
+        else if (lane > k) R[k] *= ip;
+#pragma unroll
+        for (int j = k + 1; j < 32; ++j) {
+          const float ljk = __shfl_sync(0xffffffffu, R[k], j);
+          if (lane >= j) R[j] -= R[k] * ljk;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j <= lane) T[(c0 + lane) * kPtLd + c0 + j] = R[j];
+    }
+    __syncthreads();
+    // rows below the diagonal block: x L_bb^T = a
+    for (int r = c0 + 32 + tid; r < kPt; r += kPtThreads) {
+      float* row = T + r * kPtLd + c0;
+      for (int j = 0; j < 32; ++j) {
+        float acc = row[j];
+        for (int l = 0; l < j; ++l) acc -= row[l] * T[(c0 + j) * kPtLd + c0 + l];
+        row[j] = acc / T[(c0 + j) * kPtLd + c0 + j];
+      }
+    }
+    __syncthreads();
+  }
+  // inverse of the diagonal blocks: warp b, lane c computes column c of inv(L_bb)
+  if (warp < 4) {
+    const int c0 = 32 * warp, c = lane;
+    for (int i = 0; i < 32; ++i) {
+      if (i < c) continue;
+      const float lii = T[(c0 + i) * kPtLd + c0 + i];
+      if (i == c) {
+        X[(c0 + i) * kPtLd + c0 + c] = 1.f / lii;
+      } else {
+        float acc = 0.f;
+        for (int l = c; l < i; ++l) acc += T[(c0 + i) * kPtLd + c0 + l] * X[(c0 + l) * kPtLd + c0 + c];
+        X[(c0 + i) * kPtLd + c0 + c] = -acc / lii;
+      }
+    }
+  }
+  __syncthreads();
+  for (int d = 1; d < 4; ++d) {
+    const int nb = 4 - d;  // blocks (bi, bj = bi - d), bi = d .. 3
+    for (int q = tid; q < nb * 1024; q += kPtThreads) {
+      const int blk = q >> 10, e = q & 1023, r = e >> 5, c = e & 31;
+      const int bi = d + blk, bj = bi - d;
+      float acc = 0.f;
+      for (int k = bj; k < bi; ++k)
+        for (int l = 0; l < 32; ++l)
+          acc += T[(32 * bi + r) * kPtLd + 32 * k + l] * X[(32 * k + l) * kPtLd + 32 * bj + c];
+      Sc[blk * 32 * 33 + r * 33 + c] = acc;
+    }
+    __syncthreads();
+    for (int q = tid; q < nb * 1024; q += kPtThreads) {
+      const int blk = q >> 10, e = q & 1023, r = e >> 5, c = e & 31;
+      const int bi = d + blk, bj = bi - d;
+      float acc = 0.f;
+      for (int l = 0; l <= r; ++l) acc += X[(32 * bi + r) * kPtLd + 32 * bi + l] * Sc[blk * 32 * 33 + l * 33 + c];
+      X[(32 * bi + r) * kPtLd + 32 * bj + c] = -acc;
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < kPt * kPt; q += kPtThreads) {
+    const int r = q >> 7, c = q & 127;
+    if (c <= r) A[(size_t)r * lda + c] = T[r * kPtLd + c];
+    Linv[q] = c <= r ? X[r * kPtLd + c] : 0.f;
+  }
+  if (bad) atomicOr(err, 32);
+}
+
+constexpr int kPanelTiles = 8;  // 1024-column panels: trailing updates with K = 1024
+
+// Blocked Cholesky of the lower triangle of A (np x np, np a multiple of 128,
+// lda a multiple of 4, 16-byte aligned), in place; Linv receives the inverses of
+// the np/128 diagonal tiles.  Rows/columns past the problem size must hold the
+// identity.  Returns the number of kernels launched in *launches.
+cudaError_t dense_cholesky_tc(float* A, long long lda, int np, float* Linv, int* err, cudaStream_t s,
+                              long long* launches) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_potrf_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int T = np / kPt;
+  long long nl = 0;
+  cudaError_t e = cudaSuccess;
+  for (int p0 = 0; p0 < T && e == cudaSuccess; p0 += kPanelTiles) {
+    const int p1 = min(T, p0 + kPanelTiles);
+    for (int j = p0; j < p1 && e == cudaSuccess; ++j) {
+      float* Ajj = A + (size_t)j * kPt * lda + (size_t)j * kPt;
+      float* Lj = Linv + (size_t)j * kPt * kPt;
+      k_potrf_tile<<<1, kPtThreads, kPtSmem, s>>>(Ajj, lda, Lj, err);
+      ++nl;
+      e = cudaGetLastError();
+      const int below = T - j - 1;
+      if (e != cudaSuccess || below <= 0) continue;
+      float* Aij = Ajj + (size_t)kPt * lda;
+      // L_ij = A_ij L_jj^-T (each block reads all of its rows before writing them)
+      e = tc_gemm_nt(Aij, lda, Lj, kPt, Aij, lda, below * kPt, kPt, kPt, 1.f, 0.f, false, err, s);
+      ++nl;
+      const int wcols = p1 - j - 1;
+      if (e == cudaSuccess && wcols > 0) {
+        e = tc_gemm_nt(Aij, lda, Aij, lda, Aij + kPt, lda, below * kPt, wcols * kPt, kPt, -1.f, 1.f, true, err, s);
+        ++nl;
+      }
+    }
+    const int rest = T - p1;
+    if (e == cudaSuccess && rest > 0) {
+      const float* Lp = A + (size_t)p1 * kPt * lda + (size_t)p0 * kPt;
+      float* Cq = A + (size_t)p1 * kPt * lda + (size_t)p1 * kPt;
+      e = tc_gemm_nt(Lp, lda, Lp, lda, Cq, lda, rest * kPt, rest * kPt, (p1 - p0) * kPt, -1.f, 1.f, true, err, s);
+      ++nl;
+    }
+  }
+  if (launches) *launches += nl;
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// host: tensor maps and launches
+// ---------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// rows x cols FP32, row stride ld (elements, multiple of 4; base 16-byte aligned), box {32, box_rows}
+static cudaError_t make_map(CUtensorMap* m, const float* ptr, long long rows, long long cols, long long ld,
+                            int box_rows) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  if ((ld & 3) || (reinterpret_cast<uintptr_t>(ptr) & 15)) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t tc_gemm_nt(const float* A, long long lda, const float* B, long long ldb, float* C, long long ldc,
+                       int M, int N, int K, float alpha, float beta, bool lower_only, int* err, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  CUtensorMap ma, mb;
+  cudaError_t e = make_map(&ma, A, M, K, lda, kTcBM);
+  if (e == cudaSuccess) e = make_map(&mb, B, N, K, ldb, kTcBN);
+  if (e != cudaSuccess) return e;
+  const int tiles_m = (M + kTcBM - 1) / kTcBM, tiles_n = (N + kTcBN - 1) / kTcBN;
+  const int vec_ok = (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+  k_tc_gemm_nt<<<tiles_m * tiles_n, kTcThreads, kTcSmem, s>>>(ma, mb, C, ldc, M, N, K, alpha, beta, tiles_n,
+                                                             lower_only ? 1 : 0, vec_ok, err);
+  return cudaGetLastError();
+}
+
+}  // namespace bab
+
+// ---------------------------------------------------------------------------
+// C ABI: the dense kernels on their own
+// ---------------------------------------------------------------------------
+namespace {
+
+void dense_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  bab::set_last_error_message(buf);
+}
+
+__global__ void k_pad_identity(float* A, long long ld, int n, int np) {
+  // rows and columns n..np of the padded matrix: identity
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long tot = (long long)np * (np - n);
+  if (q >= tot) return;
+  const int r = (int)(q / (np - n)), c = n + (int)(q % (np - n));
+  A[(size_t)r * ld + c] = r == c ? 1.f : 0.f;       // columns n..np of every row
+  A[(size_t)c * ld + r] = r == c ? 1.f : 0.f;       // rows n..np of every column
+}
+
+__global__ void k_zero_upper(float* A, long long ld, int n) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= (long long)n * n) return;
+  const int r = (int)(q / n), c = (int)(q % n);
+  if (c > r) A[(size_t)r * ld + c] = 0.f;
+}
+
+}  // namespace
+
+extern "C" {
+
+ba_status ba_tc_gemm_nt(void* stream, int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float beta, float* C, int64_t ldc) {
+  if (M < 0 || N < 0 || K < 0 || M >= (1LL << 31) || N >= (1LL << 31) || K >= (1LL << 31) || !A || !B || !C ||
+      lda < K || ldb < K || ldc < N || (lda & 3) || (ldb & 3) ||
+      (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) {
+    dense_error("ba_tc_gemm_nt: invalid sizes, strides or pointers (lda, ldb multiples of 4, A, B 16-byte aligned)");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int* err = nullptr;
+  cudaError_t e = cudaMallocAsync(&err, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = bab::tc_gemm_nt(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, alpha, beta, false, err, s);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (err) cudaFreeAsync(err, s);
+  if (e != cudaSuccess) {
+    dense_error("ba_tc_gemm_nt: %s", cudaGetErrorString(e));
+    return BA_ERR_CUDA;
+  }
+  if (h & 16) {
+    dense_error("ba_tc_gemm_nt: pipeline wait timed out");
+    return BA_ERR_TIMEOUT;
+  }
+  return BA_OK;
+}
+
+ba_status ba_dense_cholesky(void* stream, int64_t n, const float* A, int64_t lda, float* L, int64_t ldl,
+                            int* flags) {
+  if (n < 0 || n > 65536 || !A || !L || lda < n || ldl < n) {
+    dense_error("ba_dense_cholesky: invalid size or pointers");
+    return BA_ERR_INVALID_ARG;
+  }
+  if (flags) *flags = 0;
+  if (n == 0) return BA_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int np = (int)((n + 127) / 128 * 128);
+  float *Ap = nullptr, *Li = nullptr;
+  int* err = nullptr;
+  cudaError_t e = cudaMallocAsync(&Ap, sizeof(float) * (size_t)np * np, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&Li, sizeof(float) * (size_t)np * 128, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&err, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(Ap, sizeof(float) * np, A, sizeof(float) * lda, sizeof(float) * n, n, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && np > n) {
+    const long long tot = (long long)np * (np - n);
+    k_pad_identity<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Ap, np, (int)n, np);
+    e = cudaGetLastError();
+  }
+  long long nl = 0;
+  if (e == cudaSuccess) e = bab::dense_cholesky_tc(Ap, np, np, Li, err, s, &nl);
+  if (e == cudaSuccess) {
+    const long long tot = (long long)n * n;
+    k_zero_upper<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Ap, np, (int)n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(L, sizeof(float) * ldl, Ap, sizeof(float) * np, sizeof(float) * n, n, cudaMemcpyDefault, s);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (Ap) cudaFreeAsync(Ap, s);
+  if (Li) cudaFreeAsync(Li, s);
+  if (err) cudaFreeAsync(err, s);
+  if (e != cudaSuccess) {
+    dense_error("ba_dense_cholesky: %s", cudaGetErrorString(e));
+    return BA_ERR_CUDA;
+  }
+  if (flags) *flags = h;
+  if (h & 16) {
+    dense_error("ba_dense_cholesky: pipeline wait timed out");
+    return BA_ERR_TIMEOUT;
+  }
+  if (h & 32) {
+    dense_error("ba_dense_cholesky: not positive definite in FP32/TF32");
+    return BA_ERR_NONFINITE;
+  }
+  return BA_OK;
+}
+
+}  // extern "C"

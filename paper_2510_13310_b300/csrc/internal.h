@@ -107,6 +107,10 @@ struct SpcgArgs {
 
 // message returned by ba_last_error() for the calling thread
 void set_last_error_message(const char* msg);
+cudaError_t tc_gemm_nt(const float* A, long long lda, const float* B, long long ldb, float* C, long long ldc,
+                       int M, int N, int K, float alpha, float beta, bool lower_only, int* err, cudaStream_t s);
+cudaError_t dense_cholesky_tc(float* A, long long lda, int np, float* Linv, int* err, cudaStream_t s,
+                              long long* launches);
 
 // ---- launchers (return cudaGetLastError of the launch) ----
 template <typename T>
