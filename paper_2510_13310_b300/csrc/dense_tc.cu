@@ -213,7 +213,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         c4[q] = o;
       }
     } else {
-      for (int q = 0; q < 32 && cc + q < N; ++q) crow[q] = alpha * v[q] + (beta != 0.f ? beta * crow[q] : 0.f);
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (cc + q < N) crow[q] = alpha * v[q] + (beta != 0.f ? beta * crow[q] : 0.f);
     }
   }
   if (!ok && lane == 0) atomicOr(err, 16);
@@ -225,123 +227,228 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---------------------------------------------------------------------------
 // One 128 x 128 diagonal tile: L = chol(A) in place (lower triangle; the upper
 // triangle is left as it was) and its inverse L^-1 (lower, zeros above) into a
-// separate 128 x 128 buffer.  FP32, one block of 512 threads, left-looking over
-// four 32-column blocks: update the block column with the columns before it,
-// factor its 32 x 32 diagonal block in one warp (row per lane, registers and
-// shuffles), solve the rows below it.  The inverse: inverses of the four
-// diagonal blocks (one warp each, forward substitution per column), then the
-// off-diagonal blocks by distance, X_ij = -X_ii sum_k L_ik X_kj.
-// A pivot <= 0 (not positive definite in FP32) sets err bit 32 and is replaced
-// by a tiny positive value so that the outputs stay finite.
+// separate 128 x 128 buffer.  FP32, one block of 256 threads, right-looking over
+// four 32-column blocks: one warp factors the 32 x 32 diagonal block and
+// inverts it in registers (row per lane for the factor, column per lane for the
+// inverse; pivots through rsqrt, so no divisions); the rows below become
+// T_b = A_b L_bb^-T, a product with that inverse; the trailing part takes the
+// rank-32 update.  The off-diagonal blocks of L^-1 follow by distance:
+// X_ij = -X_ii sum_k L_ik X_kj.  The products use 4-wide and 4 x 4 register
+// tiles (independent FMA chains).  A pivot <= 0 (not positive definite in FP32)
+// sets err bit 32 and is replaced by a tiny positive value, keeping outputs finite.
 // ---------------------------------------------------------------------------
 constexpr int kPt = 128;
 constexpr int kPtLd = kPt + 1;
-constexpr int kPtThreads = 512;
-constexpr int kPtSmem = (2 * kPt * kPtLd + 3 * 32 * 33) * 4;
+constexpr int kPtThreads = 256;  // the warp-0 register work needs > 128 registers
+constexpr int kPtSmem = (2 * kPt * kPtLd + 3 * 32 * 33 + kPt) * 4;
+
+// One pivot step of the 32 x 32 register factorisation (lane = row): pivot K,
+// scale column K, rank-1 update of the columns after K.  Template recursion keeps
+// every register index static.  dinv[K] receives 1 / L_KK.
+template <int K>
+__device__ __forceinline__ void chol32_step(float (&R)[32], int lane, bool& bad, float* dinv) {
+  float dkk = __shfl_sync(0xffffffffu, R[K], K);
+  if (!(dkk > 0.f)) {
+    bad = true;
+    dkk = 1e-30f;
+  }
+  const float rs = rsqrtf(dkk);
+  const float lik = lane == K ? dkk * rs : (lane > K ? R[K] * rs : 0.f);
+  if (lane == 0) dinv[K] = rs;
+  R[K] = lik;
+#pragma unroll
+  for (int j = K + 1; j < 32; ++j) {
+    const float ljk = __shfl_sync(0xffffffffu, lik, j);
+    if (lane >= j) R[j] -= lik * ljk;
+  }
+  if constexpr (K + 1 < 32) chol32_step<K + 1>(R, lane, bad, dinv);
+}
+
+// Row I of column `lane` of L^-1 (forward substitution), L read from shared
+// memory (every lane reads the same entries: broadcasts).
+template <int I>
+__device__ __forceinline__ void inv32_step(float (&Xc)[32], int lane, const float* Lb, const float* dinv) {
+  float acc = I == lane ? 1.f : 0.f;
+#pragma unroll
+  for (int l = 0; l < I; ++l) acc -= Lb[I * kPtLd + l] * Xc[l];
+  Xc[I] = acc * dinv[I];
+  if constexpr (I + 1 < 32) inv32_step<I + 1>(Xc, lane, Lb, dinv);
+}
+
+// row index ti >= tj of the t-th 4 x 4 tile of a lower-triangular tile grid
+__device__ __forceinline__ void tri_decode(int t, int& ti, int& tj) {
+  int i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  ti = i;
+  tj = t - i * (i + 1) / 2;
+}
 
 __global__ void __launch_bounds__(kPtThreads) k_potrf_tile(float* __restrict__ A, long long lda,
                                                           float* __restrict__ Linv, int* err) {
   extern __shared__ float pt_smem[];
-  float* T = pt_smem;               // [128][129]
-  float* X = T + kPt * kPtLd;       // [128][129]
-  float* Sc = X + kPt * kPtLd;      // [3][32][33]
+  float* T = pt_smem;               // [128][129] factor
+  float* X = T + kPt * kPtLd;       // [128][129] inverse
+  float* Sc = X + kPt * kPtLd;      // [3][32][33] scratch
+  float* Dv = Sc + 3 * 32 * 33;     // [128] 1 / L_ii
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int q = tid; q < kPt * kPt; q += kPtThreads) {
-    const int r = q >> 7, c = q & 127;
-    T[r * kPtLd + c] = c <= r ? A[(size_t)r * lda + c] : 0.f;
-    X[r * kPtLd + c] = 0.f;
+  // A: 16-byte aligned rows (lda a multiple of 4)
+#pragma unroll 4
+  for (int q = tid; q < kPt * (kPt / 4); q += kPtThreads) {
+    const int r = q >> 5, c = 4 * (q & 31);
+    const float4 v = *reinterpret_cast<const float4*>(A + (size_t)r * lda + c);
+    float* t = T + r * kPtLd + c;
+    t[0] = c <= r ? v.x : 0.f;
+    t[1] = c + 1 <= r ? v.y : 0.f;
+    t[2] = c + 2 <= r ? v.z : 0.f;
+    t[3] = c + 3 <= r ? v.w : 0.f;
+    float* x = X + r * kPtLd + c;
+    x[0] = x[1] = x[2] = x[3] = 0.f;
   }
   __syncthreads();
   bool bad = false;
   for (int b = 0; b < 4; ++b) {
     const int c0 = 32 * b;
-    if (b > 0) {
-      for (int q = tid; q < (kPt - c0) * 32; q += kPtThreads) {
-        const int r = c0 + (q >> 5), c = c0 + (q & 31);
-        if (r < c) continue;
-        float acc = T[r * kPtLd + c];
-        for (int l = 0; l < c0; ++l) acc -= T[r * kPtLd + l] * T[c * kPtLd + l];
-        T[r * kPtLd + c] = acc;
-      }
-      __syncthreads();
-    }
     if (warp == 0) {
       float R[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) R[j] = j <= lane ? T[(c0 + lane) * kPtLd + c0 + j] : 0.f;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        float dkk = __shfl_sync(0xffffffffu, R[k], k);
-        if (!(dkk > 0.f)) {
-          bad = true;
-          dkk = 1e-30f;
-        }
-        const float piv = sqrtf(dkk), ip = 1.f / piv;
-        if (lane == k) R[k] = piv;
-        else if (lane > k) R[k] *= ip;
-#pragma unroll
-        for (int j = k + 1; j < 32; ++j) {
-          const float ljk = __shfl_sync(0xffffffffu, R[k], j);
-          if (lane >= j) R[j] -= R[k] * ljk;
-        }
-      }
+      chol32_step<0>(R, lane, bad, Dv + c0);
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         if (j <= lane) T[(c0 + lane) * kPtLd + c0 + j] = R[j];
+      __syncwarp();
+      float Xc[32];
+      inv32_step<0>(Xc, lane, T + c0 * kPtLd + c0, Dv + c0);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j >= lane) X[(c0 + j) * kPtLd + c0 + lane] = Xc[j];
     }
     __syncthreads();
-    // rows below the diagonal block: x L_bb^T = a
-    for (int r = c0 + 32 + tid; r < kPt; r += kPtThreads) {
-      float* row = T + r * kPtLd + c0;
-      for (int j = 0; j < 32; ++j) {
-        float acc = row[j];
-        for (int l = 0; l < j; ++l) acc -= row[l] * T[(c0 + j) * kPtLd + c0 + l];
-        row[j] = acc / T[(c0 + j) * kPtLd + c0 + j];
+    const int r0 = c0 + 32, nr = kPt - r0;
+    if (nr > 0) {
+      // rows below: T[r][c0 + j] = sum_l A[r][c0 + l] X_bb[j][l]; items = (row, 4 columns)
+      float out[3][4];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const int it = tid + kPtThreads * m;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[m][i] = 0.f;
+        if (it < nr * 8) {
+          const int r = r0 + (it >> 3), j0 = 4 * (it & 7);
+          const float* ar = T + r * kPtLd + c0;
+          const float* x0 = X + (c0 + j0) * kPtLd + c0;
+#pragma unroll 8
+          for (int l = 0; l < 32; ++l) {
+            const float a = ar[l];
+            out[m][0] += a * x0[l];
+            out[m][1] += a * x0[kPtLd + l];
+            out[m][2] += a * x0[2 * kPtLd + l];
+            out[m][3] += a * x0[3 * kPtLd + l];
+          }
+        }
       }
-    }
-    __syncthreads();
-  }
-  // inverse of the diagonal blocks: warp b, lane c computes column c of inv(L_bb)
-  if (warp < 4) {
-    const int c0 = 32 * warp, c = lane;
-    for (int i = 0; i < 32; ++i) {
-      if (i < c) continue;
-      const float lii = T[(c0 + i) * kPtLd + c0 + i];
-      if (i == c) {
-        X[(c0 + i) * kPtLd + c0 + c] = 1.f / lii;
-      } else {
-        float acc = 0.f;
-        for (int l = c; l < i; ++l) acc += T[(c0 + i) * kPtLd + c0 + l] * X[(c0 + l) * kPtLd + c0 + c];
-        X[(c0 + i) * kPtLd + c0 + c] = -acc / lii;
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const int it = tid + kPtThreads * m;
+        if (it < nr * 8) {
+          float* t = T + (r0 + (it >> 3)) * kPtLd + c0 + 4 * (it & 7);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) t[i] = out[m][i];
+        }
       }
+      __syncthreads();
+      // trailing rank-32 update of the lower triangle, 4 x 4 register tiles
+      const int nt = nr / 4, ntiles = nt * (nt + 1) / 2;
+      for (int t = tid; t < ntiles; t += kPtThreads) {
+        int ti, tj;
+        tri_decode(t, ti, tj);
+        const float* a0 = T + (r0 + 4 * ti) * kPtLd + c0;
+        const float* b0 = T + (r0 + 4 * tj) * kPtLd + c0;
+        float acc[4][4] = {};
+#pragma unroll 4
+        for (int l = 0; l < 32; ++l) {
+          float av[4], bv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            av[i] = a0[i * kPtLd + l];
+            bv[i] = b0[i * kPtLd + l];
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (ti != tj || j <= i) T[(r0 + 4 * ti + i) * kPtLd + r0 + 4 * tj + j] -= acc[i][j];
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
+  // off-diagonal blocks of the inverse, by distance d = bi - bj, 4 x 4 register tiles
   for (int d = 1; d < 4; ++d) {
-    const int nb = 4 - d;  // blocks (bi, bj = bi - d), bi = d .. 3
-    for (int q = tid; q < nb * 1024; q += kPtThreads) {
-      const int blk = q >> 10, e = q & 1023, r = e >> 5, c = e & 31;
+    const int nb = 4 - d;
+    for (int it = tid; it < nb * 64; it += kPtThreads) {
+      const int blk = it >> 6, e = it & 63, r = 4 * (e >> 3), c = 4 * (e & 7);
       const int bi = d + blk, bj = bi - d;
-      float acc = 0.f;
-      for (int k = bj; k < bi; ++k)
-        for (int l = 0; l < 32; ++l)
-          acc += T[(32 * bi + r) * kPtLd + 32 * k + l] * X[(32 * k + l) * kPtLd + 32 * bj + c];
-      Sc[blk * 32 * 33 + r * 33 + c] = acc;
+      float acc[4][4] = {};
+      for (int l = 32 * bj; l < 32 * bi; ++l) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          av[i] = T[(32 * bi + r + i) * kPtLd + l];
+          bv[i] = X[l * kPtLd + 32 * bj + c + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Sc[blk * 32 * 33 + (r + i) * 33 + c + j] = acc[i][j];
     }
     __syncthreads();
-    for (int q = tid; q < nb * 1024; q += kPtThreads) {
-      const int blk = q >> 10, e = q & 1023, r = e >> 5, c = e & 31;
+    for (int it = tid; it < nb * 64; it += kPtThreads) {
+      const int blk = it >> 6, e = it & 63, r = 4 * (e >> 3), c = 4 * (e & 7);
       const int bi = d + blk, bj = bi - d;
-      float acc = 0.f;
-      for (int l = 0; l <= r; ++l) acc += X[(32 * bi + r) * kPtLd + 32 * bi + l] * Sc[blk * 32 * 33 + l * 33 + c];
-      X[(32 * bi + r) * kPtLd + 32 * bj + c] = -acc;
+      float acc[4][4] = {};
+      for (int l = 0; l < r + 4; ++l) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          av[i] = X[(32 * bi + r + i) * kPtLd + 32 * bi + l];  // zero above the diagonal
+          bv[i] = Sc[blk * 32 * 33 + l * 33 + c + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) X[(32 * bi + r + i) * kPtLd + 32 * bj + c + j] = -acc[i][j];
     }
     __syncthreads();
   }
-  for (int q = tid; q < kPt * kPt; q += kPtThreads) {
-    const int r = q >> 7, c = q & 127;
-    if (c <= r) A[(size_t)r * lda + c] = T[r * kPtLd + c];
-    Linv[q] = c <= r ? X[r * kPtLd + c] : 0.f;
+#pragma unroll 4
+  for (int q = tid; q < kPt * (kPt / 4); q += kPtThreads) {
+    const int r = q >> 5, c = 4 * (q & 31);
+    const float* t = T + r * kPtLd + c;
+    const float* x = X + r * kPtLd + c;
+    float* a = A + (size_t)r * lda + c;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (c + i <= r) a[i] = t[i];
+    float4 o = make_float4(c <= r ? x[0] : 0.f, c + 1 <= r ? x[1] : 0.f, c + 2 <= r ? x[2] : 0.f,
+                           c + 3 <= r ? x[3] : 0.f);
+    *reinterpret_cast<float4*>(Linv + (size_t)r * kPt + c) = o;
   }
   if (bad) atomicOr(err, 32);
 }
