@@ -217,37 +217,50 @@ ba_status run_extraction(ba_problem* pb, bool drop, int* rounds_out) {
   CU(cudaMemsetAsync(p->cam_cnt, 0, sizeof(int) * std::max(1, p->C), p->stream));
   int rounds = 0;
   const int max_rounds = p->C + p->P + 2;
-  for (;;) {
+  // One peel round, then the finalisation launched speculatively: a single
+  // readback covers the common case where the first round changes nothing.
+  // If it did change something, peel to the fixed point and finalise again.
+  auto peel_round = [&]() -> ba_status {
     ++rounds;
     CU(cudaMemsetAsync(&p->sc->changed, 0, sizeof(int), p->stream));
     LAUNCH(1, launch_peel_points(p->L, p->valid, p->cam_act, p->pt_act, p->cam_cnt, p->opt.min_pt_obs,
                                  p->sc, p->stream));
     LAUNCH(1, launch_peel_cams(p->L, p->cam_act, p->cam_cnt, p->opt.min_cam_obs, p->sc, p->stream));
-    CU(cudaMemcpyAsync(&p->h_sc->changed, &p->sc->changed, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    ST(sync(p));
-    if (!p->h_sc->changed || rounds >= max_rounds) break;
+    return BA_OK;
+  };
+  auto finalize = [&]() -> ba_status {
+    CU(cudaMemsetAsync(&p->sc->mask_changed, 0, sizeof(int), p->stream));
+    CU(cudaMemsetAsync(&p->sc->n_obs_act, 0, sizeof(int), p->stream));
+    CU(cudaMemsetAsync(&p->sc->n_cam_act, 0, sizeof(int), p->stream));
+    LAUNCH(2, launch_finalize_obs(p->L, p->valid, p->cam_act, p->pt_act, p->obs_act, p->obs_act_co,
+                                  p->sc, p->stream));
+    LAUNCH(1, launch_cam_flags(p->L, p->cam_act, p->cam_flags, p->sc, p->stream));
+    LAUNCH(3, launch_rank(p->cam_flags, p->C, p->crank, p->cam_map, &p->sc->n_cam_free, p->rank_tmp,
+                          p->n_rank_tmp, p->stream));
+    LAUNCH(3, launch_rank(p->pt_act, p->P, p->pt_rank, p->pt_map, &p->sc->n_pt_act, p->rank_tmp,
+                          p->n_rank_tmp, p->stream));
+    CU(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->stream));
+    return sync(p);
+  };
+  ST(peel_round());
+  ST(finalize());
+  if (p->h_sc->changed) {
+    // the speculative pass already compared against the previous masks: keep
+    // its verdict (a spurious "changed" only costs a recomputation)
+    const int spec_mask_changed = p->h_sc->mask_changed;
+    for (;;) {
+      ST(peel_round());
+      CU(cudaMemcpyAsync(&p->h_sc->changed, &p->sc->changed, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+      ST(sync(p));
+      if (!p->h_sc->changed || rounds >= max_rounds) break;
+    }
+    ST(finalize());
+    p->h_sc->mask_changed |= spec_mask_changed;
   }
-  CU(cudaMemsetAsync(&p->sc->mask_changed, 0, sizeof(int), p->stream));
-  CU(cudaMemsetAsync(&p->sc->n_obs_act, 0, sizeof(int), p->stream));
-  LAUNCH(2, launch_finalize_obs(p->L, p->valid, p->cam_act, p->pt_act, p->obs_act, p->obs_act_co,
-                                p->sc, p->stream));
-  LAUNCH(1, launch_cam_flags(p->L, p->cam_act, p->cam_flags, p->stream));
-  LAUNCH(3, launch_rank(p->cam_flags, p->C, p->crank, p->cam_map, &p->sc->n_cam_free, p->rank_tmp,
-                        p->n_rank_tmp, p->stream));
-  LAUNCH(3, launch_rank(p->pt_act, p->P, p->pt_rank, p->pt_map, &p->sc->n_pt_act, p->rank_tmp,
-                        p->n_rank_tmp, p->stream));
-  CU(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->stream));
-  ST(sync(p));
   p->n_cam_free = p->h_sc->n_cam_free;
   p->n_pt_act = p->h_sc->n_pt_act;
   p->n_obs_act = p->h_sc->n_obs_act;
-  {
-    std::vector<uint8_t> ca((size_t)p->C);
-    if (p->C) CU(cudaMemcpy(ca.data(), p->cam_act, (size_t)p->C, cudaMemcpyDeviceToHost));
-    int n = 0;
-    for (uint8_t v : ca) n += v;
-    p->n_cam_act = n;
-  }
+  p->n_cam_act = p->h_sc->n_cam_act;
   if (p->h_sc->mask_changed) {
     p->cost_valid[0] = p->cost_valid[1] = false;
     p->linearized = false;
@@ -322,7 +335,8 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     a.timeout_ns = 2000000000LL;
     size_t smem = spcg_smem_bytes<T>(a.n, a.own_max, a.rows_in_smem);
     int grid = std::min(pb->spcg_grid, Cf);
-    CU(cudaMemsetAsync(pb->bar, 0, sizeof(unsigned), pb->stream));
+    // reduction slots start untagged (tag 0; the first reduction uses tag 1)
+    CU(cudaMemsetAsync(pb->dots, 0, sizeof(double) * 2 * 4 * (size_t)grid, pb->stream));
     CU(cudaEventRecord(pb->evk[0], pb->stream));
     LAUNCH(1, launch_spcg<T>(a, grid, smem, pb->stream));
     CU(cudaEventRecord(pb->evk[1], pb->stream));
@@ -929,7 +943,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   // at most two blocks per SM: fewer blocks means fewer partial vectors to reduce
   pb->pcg_grid = std::max(1, std::min(std::min(per_sm, 2) * pb->num_sms, std::max(1, pb->n_tiles)));
   ST(dalloc_bytes(pb, &pb->partials, R * (size_t)pb->pcg_grid * std::max(1, n_max)));
-  ST(dalloc(pb, &pb->dots, (size_t)2 * 4 * pb->pcg_grid));
+  // dot-product slots of both PCG kernels: [2 parities][grid][4]
+  ST(dalloc(pb, &pb->dots, (size_t)2 * 4 * std::max(pb->pcg_grid, pb->num_sms)));
   ST(dalloc(pb, &pb->bar, 1));
   ST(dalloc(pb, &pb->err, 1));
   // explicit reduced camera system (solver option; automatic for up to 512 cameras)

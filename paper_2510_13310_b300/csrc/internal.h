@@ -135,8 +135,7 @@ cudaError_t launch_peel_cams(const Layout& L, uint8_t* cam_act, int* cam_cnt, in
 cudaError_t launch_finalize_obs(const Layout& L, const uint8_t* valid, const uint8_t* cam_act,
                                 const uint8_t* pt_act, uint8_t* obs_act, uint8_t* obs_act_co,
                                 Scalars* sc, cudaStream_t s);
-cudaError_t launch_cam_flags(const Layout& L, const uint8_t* cam_act, uint8_t* flags,
-                             cudaStream_t s);
+cudaError_t launch_cam_flags(const Layout& L, const uint8_t* cam_act, uint8_t* flags, Scalars* sc, cudaStream_t s);
 // ranks of nonzero flags: rank[i] (-1 if zero), map[rank] = i, *count
 cudaError_t launch_rank(const uint8_t* flags, int n, int* rank, int* map, int* count,
                         int* block_tmp, int n_block_tmp, cudaStream_t s);

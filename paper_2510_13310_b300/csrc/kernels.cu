@@ -266,14 +266,22 @@ cudaError_t launch_finalize_obs(const Layout& L, const uint8_t* valid, const uin
   return cudaGetLastError();
 }
 
+// free-camera flags (active and not gauge) and the number of active cameras
+// (sc->n_cam_act, zeroed by the caller; integer atomics, order-free)
 __global__ void k_cam_flags(int C, const uint8_t* __restrict__ fixed, const uint8_t* __restrict__ cam_act,
-                            uint8_t* __restrict__ flags) {
+                            uint8_t* __restrict__ flags, Scalars* sc) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < C) flags[c] = (uint8_t)(cam_act[c] && !fixed[c]);
+  int act = 0;
+  if (c < C) {
+    act = cam_act[c] ? 1 : 0;
+    flags[c] = (uint8_t)(act && !fixed[c]);
+  }
+  act = warp_sum(act);
+  if ((threadIdx.x & 31) == 0 && act) atomicAdd(&sc->n_cam_act, act);
 }
 
-cudaError_t launch_cam_flags(const Layout& L, const uint8_t* cam_act, uint8_t* flags, cudaStream_t s) {
-  if (L.C > 0) k_cam_flags<<<(L.C + 255) / 256, 256, 0, s>>>(L.C, L.cam_fixed, cam_act, flags);
+cudaError_t launch_cam_flags(const Layout& L, const uint8_t* cam_act, uint8_t* flags, Scalars* sc, cudaStream_t s) {
+  if (L.C > 0) k_cam_flags<<<(L.C + 255) / 256, 256, 0, s>>>(L.C, L.cam_fixed, cam_act, flags, sc);
   return cudaGetLastError();
 }
 

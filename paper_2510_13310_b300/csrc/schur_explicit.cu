@@ -264,72 +264,157 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
 
 constexpr int kSpcgThreads = 512;
 
-__device__ __forceinline__ bool grid_barrier2(unsigned* bar, unsigned target, int* err,
-                                              long long timeout_ns) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(*bar);
-    __threadfence();
-    cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-    uint64_t t0 = globaltimer_ns();
-    while (cnt.load(cuda::memory_order_acquire) < target) {
-      if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
-        atomicOr(err, 1);
-        break;
-      }
-      __nanosleep(20);
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  cuda::atomic_ref<int, cuda::thread_scope_device> e(*err);
-  return (e.load(cuda::memory_order_relaxed) & 1) == 0;
+// Cross-block reductions without a separate barrier.  Each block publishes its
+// FP64 partials as 64-bit words whose 4 low mantissa bits are replaced by the
+// reduction's epoch tag (a relative change below 2^-48), with a release store
+// after its other global writes; warp 0 of every block then polls the G slots
+// until every tag matches, and sums them in a fixed order.
+// Seeing all tags is the barrier: writes a block made before publishing are
+// visible after it.  Slots alternate between two sets by epoch parity, so a
+// block that is one reduction ahead never overwrites a slot still being read.
+__device__ __forceinline__ unsigned long long tag_value(double v, unsigned tag) {
+  return ((unsigned long long)__double_as_longlong(v) & ~0xFull) | (unsigned long long)(tag & 0xFu);
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ double sum_dots2(const double* region, int slot, int G, double* red) {
-  double s = 0.0;
-  for (int g = threadIdx.x; g < G; g += blockDim.x) s += region[4 * g + slot];
-  return block_sum(s, red);
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Called by warp 0 only (all lanes), after a __syncthreads that ordered the
+// block's global writes.  mine: this block's K partials (lane 0's values are
+// published).  out: the K sums over the G blocks (every lane).  Each lane polls
+// its slots g = lane + 32 m in batches of 8 (all loads of a batch in flight at
+// once) until every tag matches; an acquire fence then orders the block's later
+// reads after the other blocks' published writes.  false on timeout.
+template <int K>
+__device__ bool warp0_tagged_allreduce(unsigned long long* slots, int G, int bid, unsigned epoch,
+                                       const double (&mine)[K], double (&out)[K], long long timeout_ns) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long* set = slots + (size_t)(epoch & 1u) * 4 * G;
+  const unsigned tag = epoch & 0xFu;
+  if (lane == 0) {
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < K; ++k) st_release_u64(&set[4 * bid + k], tag_value(mine[k], tag));
+  }
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  bool ok = true;
+  const uint64_t t0 = globaltimer_ns();
+  for (int base = 0; base < G; base += 256) {
+    unsigned long long v[K][8];
+    for (;;) {
+      bool ready = true;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int g = base + lane + 32 * m;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          v[k][m] = g < G ? ld_relaxed_u64(&set[4 * g + k]) : (unsigned long long)tag;
+          ready &= (unsigned)(v[k][m] & 0xFull) == tag;
+        }
+      }
+      if (__all_sync(0xffffffffu, ready)) break;
+      if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
+        ok = false;
+        break;
+      }
+    }
+    if (!__all_sync(0xffffffffu, ok)) break;
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (base + lane + 32 * m < G) acc[k] += __longlong_as_double((long long)(v[k][m] & ~0xFull));
+  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = warp_sum(acc[k]);
+  return __all_sync(0xffffffffu, ok);
+}
+
+template <typename T>
+__host__ __device__ inline int spcg_row_stride(int n) {
+  return sizeof(T) == 4 ? (n + 3) & ~3 : n;  // FP32 rows padded for 16-byte vector loads
 }
 
 template <typename T>
 size_t spcg_smem_bytes(int n, int own_max, int rows_in_smem) {
-  size_t b = sizeof(double) * (2 * kSpcgThreads + 8);            // FP64 reduction scratch
-  b += rows_in_smem ? sizeof(T) * (size_t)9 * own_max * n : 0;  // own rows of S^
-  b += sizeof(T) * (size_t)n;                                    // p^ (full)
-  b += sizeof(T) * (size_t)9 * own_max * 4;                      // x^, r^, q, b^ (owned)
-  b += sizeof(T) * (size_t)81 * own_max;                         // preconditioner blocks
+  const int ns = spcg_row_stride<T>(n);
+  size_t b = sizeof(double) * 16;                                   // broadcast scalars
+  b += rows_in_smem ? sizeof(T) * (size_t)9 * own_max * ns : 0;    // own rows of S^
+  b += sizeof(T) * (size_t)ns;                                      // p^ (full)
+  b += sizeof(T) * (size_t)9 * own_max * 5;                         // x^, r^, q, b^, z (owned)
+  b += sizeof(T) * (size_t)81 * own_max;                            // preconditioner blocks
   return (b + 15) & ~size_t(15);
 }
 
+// Dot products of the owned slice by warp 0 (FP64 accumulation, fixed order).
+template <typename T>
+__device__ __forceinline__ double warp0_dot(const T* a, const T* b, int ne) {
+  double s = 0.0;
+  for (int q = threadIdx.x; q < ne; q += 32) s += (double)a[q] * (double)b[q];
+  return warp_sum(s);
+}
+
+// Persistent PCG on the scaled system: standard preconditioned CG (x0 = 0,
+// block-Jacobi M^), two cross-block reductions per iteration (p^T q, then
+// r^T r and r^T z) and no other grid synchronisation.  alpha, beta and the
+// stopping test are formed by one thread (FP64 division is scarce) and
+// broadcast through shared memory.
 template <typename T>
 __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int G = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int n = a.n;
+  const int n = a.n, ns = spcg_row_stride<T>(n);
   const int f0 = (int)(((long long)a.Cf * bid) / G), f1 = (int)(((long long)a.Cf * (bid + 1)) / G);
   const int e0 = 9 * f0, ne = 9 * (f1 - f0);
   unsigned char* p = smem_raw;
-  double* dbuf = reinterpret_cast<double*>(p);  // [2 * threads]
-  double* dout = dbuf + 2 * kSpcgThreads;       // [8]
-  p += sizeof(double) * (2 * kSpcgThreads + 8);
-  const int cnt = min(ne, (int)blockDim.x);
+  double* sb = reinterpret_cast<double*>(p);  // [16]
+  p += sizeof(double) * 16;
   T* Srows = reinterpret_cast<T*>(p);
-  p += a.rows_in_smem ? sizeof(T) * (size_t)9 * a.own_max * n : 0;
+  p += a.rows_in_smem ? sizeof(T) * (size_t)9 * a.own_max * ns : 0;
   T* ps = reinterpret_cast<T*>(p);
-  p += sizeof(T) * (size_t)n;
+  p += sizeof(T) * (size_t)ns;
   T* xo = reinterpret_cast<T*>(p);
   T* ro = xo + 9 * a.own_max;
   T* qo = ro + 9 * a.own_max;
   T* bo = qo + 9 * a.own_max;
-  T* Mo = bo + 9 * a.own_max;
+  T* zo = bo + 9 * a.own_max;
+  T* Mo = zo + 9 * a.own_max;
   const T* Sg = a.Shat + (size_t)e0 * n;
-  const T* Srow_base = a.rows_in_smem ? Srows : Sg;
+  unsigned long long* slots = reinterpret_cast<unsigned long long*>(a.dots);
   unsigned epoch = 0;
+  const T* dinv = reinterpret_cast<const T*>(a.dscale + n);
 
-  if (a.rows_in_smem)
-    for (size_t q = tid; q < (size_t)ne * n; q += blockDim.x) Srows[q] = Sg[q];
+  if (a.rows_in_smem) {
+    // eight loads per lane in flight: the block's rows come from HBM once per solve
+    for (int r = warp; r < ne; r += nwarps) {
+      const T* src = Sg + (size_t)r * n;
+      T* dst = Srows + (size_t)r * ns;
+      for (int c0 = 0; c0 < ns; c0 += 256) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + 32 * u + lane;
+          v[u] = c < n ? src[c] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + 32 * u + lane;
+          if (c < ns) dst[c] = v[u];
+        }
+      }
+    }
+  }
+  for (int c = n + tid; c < ns; c += blockDim.x) ps[c] = T(0);
   // owned preconditioner blocks of S^: D_f^-1 scaled, M^_f = diag(d) M_f diag(d)
   for (int q = tid; q < 81 * (f1 - f0); q += blockDim.x) {
     int f = q / 81, ij = q - 81 * f, i = ij / 9, j = ij - 9 * i;
@@ -338,39 +423,42 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   }
   for (int q = tid; q < ne; q += blockDim.x) {
     xo[q] = T(0);
-    T bv = (T)((double)a.b[e0 + q] / a.dscale[e0 + q]);
+    T bv = (T)((double)a.b[e0 + q] * (double)dinv[e0 + q]);
     ro[q] = bv;
     bo[q] = bv;
   }
   __syncthreads();
-  double loc_rz = 0.0, loc_bb = 0.0;
   for (int q = tid; q < ne; q += blockDim.x) {
     int f = q / 9, i = q - 9 * f;
     T zz = T(0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) zz += Mo[81 * f + 9 * i + k] * ro[9 * f + k];
     a.z[e0 + q] = zz;
-    double rv = (double)ro[q];
-    loc_rz += rv * (double)zz;
-    loc_bb += rv * rv;
+    zo[q] = zz;
   }
-  int dph = 0;
-  auto dregion = [&](int ph) { return a.dots + (size_t)(ph & 1) * 4 * G; };
-  {
-    double s0, s1;
-    warp0_sum2(loc_rz, loc_bb, cnt, dbuf, dout, s0, s1);
-    if (tid == 0) {
-      dregion(dph)[4 * bid] = s0;
-      dregion(dph)[4 * bid + 1] = s1;
+  __syncthreads();
+  if (warp == 0) {
+    const double mine[2] = {warp0_dot(ro, zo, ne), warp0_dot(ro, ro, ne)};
+    double tot[2];
+    const bool ok = warp0_tagged_allreduce<2>(slots, G, bid, ++epoch, mine, tot, a.timeout_ns);
+    if (lane == 0) {
+      sb[0] = tot[0];
+      sb[1] = tot[1];
+      sb[2] = sqrt(tot[1]);
+      sb[7] = ok ? 1.0 : 0.0;
+      if (!ok) atomicOr(a.err, 1);
     }
+  } else {
+    ++epoch;
   }
-  if (!grid_barrier2(a.bar, (++epoch) * G, a.err, a.timeout_ns)) return;
-  double rz, bb;
-  warp0_sum_slots(dregion(dph), G, 0, 1, dout + 4, rz, bb);
-  ++dph;
-  const double bnorm = sqrt(bb);
+  __syncthreads();
+  if (sb[7] == 0.0) return;
+  double rz = sb[0];
+  const double bnorm = sb[2];
+  const double stop_rr = (a.tol * bnorm) * (a.tol * bnorm);
   int it = 0;
-  double rr_last = bb, beta = 0.0;
+  double rr_last = sb[1];
+  T beta = T(0);
   bool first = true;
   while (bnorm > 0.0 && it < a.max_iters) {
     // p = z (first) or z + beta p: every load of z issued before any use
@@ -381,75 +469,101 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
         int e = base + u * blockDim.x + tid;
         zv[u] = e < n ? a.z[e] : T(0);
       }
-      const T bt = (T)beta;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         int e = base + u * blockDim.x + tid;
-        if (e < n) ps[e] = first ? zv[u] : zv[u] + bt * ps[e];
+        if (e < n) ps[e] = first ? zv[u] : zv[u] + beta * ps[e];
       }
     }
     first = false;
     __syncthreads();
     // q = S^_rows p^: one warp per row
-    for (int r = warp; r < ne; r += nwarps) {
-      const T* row = Srow_base + (size_t)r * n;
-      T acc = T(0);
-      for (int c = lane; c < n; c += 32) acc += row[c] * ps[c];
-      acc = warp_sum(acc);
-      if (lane == 0) qo[r] = acc;
+    if constexpr (sizeof(T) == 4) {
+      if (a.rows_in_smem) {
+        const float4* p4 = reinterpret_cast<const float4*>(ps);
+        for (int r = warp; r < ne; r += nwarps) {
+          const float4* row = reinterpret_cast<const float4*>(Srows + (size_t)r * ns);
+          float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+          for (int c = lane; c < ns / 4; c += 32) {
+            const float4 sv = row[c], pv = p4[c];
+            c0 += sv.x * pv.x;
+            c1 += sv.y * pv.y;
+            c2 += sv.z * pv.z;
+            c3 += sv.w * pv.w;
+          }
+          const float acc = warp_sum((c0 + c1) + (c2 + c3));
+          if (lane == 0) qo[r] = acc;
+        }
+      }
+    }
+    if (sizeof(T) != 4 || !a.rows_in_smem) {
+      const T* base = a.rows_in_smem ? Srows : Sg;
+      const int ld = a.rows_in_smem ? ns : n;
+      for (int r = warp; r < ne; r += nwarps) {
+        const T* row = base + (size_t)r * ld;
+        T acc = T(0);
+        for (int c = lane; c < n; c += 32) acc += row[c] * ps[c];
+        acc = warp_sum(acc);
+        if (lane == 0) qo[r] = acc;
+      }
     }
     __syncthreads();
-    double loc_pq = 0.0;
-    for (int q = tid; q < ne; q += blockDim.x) loc_pq += (double)ps[e0 + q] * (double)qo[q];
-    {
-      double s0, s1;
-      warp0_sum2(loc_pq, 0.0, cnt, dbuf, dout, s0, s1);
-      if (tid == 0) dregion(dph)[4 * bid + 2] = s0;
+    if (warp == 0) {
+      const double mine[1] = {warp0_dot(ps + e0, qo, ne)};
+      double tot[1];
+      const bool ok = warp0_tagged_allreduce<1>(slots, G, bid, ++epoch, mine, tot, a.timeout_ns);
+      if (lane == 0) {
+        const double pq = tot[0];
+        const bool fine = ok && pq > 0.0 && isfinite(pq);
+        sb[3] = fine ? rz / pq : 0.0;
+        sb[7] = fine ? 1.0 : 0.0;
+        if (!ok) atomicOr(a.err, 1);
+        else if (!fine && bid == 0) atomicOr(a.err, 2);
+      }
+    } else {
+      ++epoch;
     }
-    if (!grid_barrier2(a.bar, (++epoch) * G, a.err, a.timeout_ns)) return;
-    double pq, unused;
-    warp0_sum_slots(dregion(dph), G, 2, 2, dout + 4, pq, unused);
-    ++dph;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      if (bid == 0 && tid == 0) atomicOr(a.err, 2);
-      break;
-    }
-    double alpha = rz / pq;
+    __syncthreads();
+    if (sb[7] == 0.0) break;
+    const double alpha = sb[3];
     for (int q = tid; q < ne; q += blockDim.x) {
       xo[q] = (T)((double)xo[q] + alpha * (double)ps[e0 + q]);
       ro[q] = (T)((double)ro[q] - alpha * (double)qo[q]);
     }
     __syncthreads();
-    double loc_rr = 0.0, loc_rz2 = 0.0;
     for (int q = tid; q < ne; q += blockDim.x) {
       int f = q / 9, i = q - 9 * f;
       T zz = T(0);
 #pragma unroll
       for (int k = 0; k < 9; ++k) zz += Mo[81 * f + 9 * i + k] * ro[9 * f + k];
       a.z[e0 + q] = zz;
-      double rv = (double)ro[q];
-      loc_rr += rv * rv;
-      loc_rz2 += rv * (double)zz;
+      zo[q] = zz;
     }
-    {
-      double s0, s1;
-      warp0_sum2(loc_rr, loc_rz2, cnt, dbuf, dout, s0, s1);
-      if (tid == 0) {
-        dregion(dph)[4 * bid] = s0;
-        dregion(dph)[4 * bid + 1] = s1;
+    __syncthreads();
+    if (warp == 0) {
+      const double mine[2] = {warp0_dot(ro, ro, ne), warp0_dot(ro, zo, ne)};
+      double tot[2];
+      const bool ok = warp0_tagged_allreduce<2>(slots, G, bid, ++epoch, mine, tot, a.timeout_ns);
+      if (lane == 0) {
+        sb[4] = tot[0];
+        sb[5] = tot[0] <= stop_rr ? 1.0 : 0.0;
+        sb[6] = rz != 0.0 ? tot[1] / rz : 0.0;
+        sb[0] = tot[1];
+        sb[7] = ok ? 1.0 : 0.0;
+        if (!ok) atomicOr(a.err, 1);
       }
+    } else {
+      ++epoch;
     }
-    if (!grid_barrier2(a.bar, (++epoch) * G, a.err, a.timeout_ns)) return;
-    double rr, rz2;
-    warp0_sum_slots(dregion(dph), G, 0, 1, dout + 4, rr, rz2);
-    ++dph;
+    __syncthreads();
+    if (sb[7] == 0.0) break;
     ++it;
-    rr_last = rr;
-    if (sqrt(rr) <= a.tol * bnorm) break;
-    beta = rz2 / rz;
-    rz = rz2;
+    rr_last = sb[4];
+    if (sb[5] != 0.0) break;
+    beta = (T)sb[6];
+    rz = sb[0];
   }
-  for (int q = tid; q < ne; q += blockDim.x) a.x[e0 + q] = (T)((double)xo[q] / a.dscale[e0 + q]);
+  for (int q = tid; q < ne; q += blockDim.x) a.x[e0 + q] = (T)((double)xo[q] * (double)dinv[e0 + q]);
   if (bid == 0 && tid == 0) {
     a.sc->pcg_iters = it;
     a.sc->pcg_bnorm = bnorm;
