@@ -72,12 +72,15 @@ typedef struct {
   const int32_t* fixed_cams;   /* host array of gauge cameras held constant ({0}) */
   int n_fixed;
   int solver;                  /* reduced camera system: BA_SOLVER_AUTO (explicit when
-                                  9 x cameras <= 4608), BA_SOLVER_IMPLICIT (matrix-free
-                                  Schur matvec), BA_SOLVER_EXPLICIT (dense S formed per
-                                  damping value, PCG on it) */
+                                  9 x cameras <= 4608, else implicit), BA_SOLVER_IMPLICIT
+                                  (matrix-free Schur matvec), BA_SOLVER_EXPLICIT (dense S
+                                  formed per damping value, block-Jacobi PCG on it),
+                                  BA_SOLVER_DENSE (FP32 only: S formed, factored by the
+                                  tensor-core blocked Cholesky, CG preconditioned with
+                                  that factor to pcg_rel_tol) */
 } ba_options;
 
-enum { BA_SOLVER_AUTO = 0, BA_SOLVER_IMPLICIT = 1, BA_SOLVER_EXPLICIT = 2 };
+enum { BA_SOLVER_AUTO = 0, BA_SOLVER_IMPLICIT = 1, BA_SOLVER_EXPLICIT = 2, BA_SOLVER_DENSE = 3 };
 
 typedef struct {
   double cost;        /* F(x) = 1/2 sum rho(|r_k|^2) over the iteration's active set */
@@ -219,7 +222,7 @@ ba_status ba_dense_cholesky(void* stream, int64_t n, const float* A, int64_t lda
 int64_t ba_kernel_launches(const ba_problem* pb);
 
 /* The reduced-camera-system solver the problem resolved to at creation:
- * BA_SOLVER_IMPLICIT or BA_SOLVER_EXPLICIT (0 for a NULL handle). */
+ * BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT or BA_SOLVER_DENSE (0 for a NULL handle). */
 int ba_solver_kind(const ba_problem* pb);
 
 void ba_destroy(ba_problem* pb);

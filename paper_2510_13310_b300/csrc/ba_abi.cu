@@ -103,6 +103,11 @@ struct ba_problem {
   int recompute = 0, cam_in_smem = 0, max_tiles_per_block = 1, g_rows = 0;
   // explicit reduced camera system
   bool explicit_S = false;
+  bool dense = false;            // explicit S factored on the tensor cores (FP32)
+  DenseResult dense_last;
+  DenseWork dw;
+  unsigned dense_epoch = 0;
+  float* dense_b = nullptr;      // [2][n]: scaled right-hand side, scaled solution
   void *Shat = nullptr, *Dblk = nullptr;
   void* Yhat = nullptr;         // [N][kWStride] D^-1 W M per damping value (explicit system)
   int4* covis_runs = nullptr;   // (camera i, camera j, first pair, count), i < j
@@ -315,6 +320,30 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     LAUNCH(5, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
                                (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
                                Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->num_sms, pb->stream));
+    bool solved = false;
+    if constexpr (sizeof(T) == 4) {
+      if (pb->dense) {
+        // b^ = D^-1 b; S^ x^ = b^ by the tensor-core factorisation + CG; x = D^-1 x^
+        const int n = 9 * Cf;
+        const float* dinv = reinterpret_cast<const float*>(pb->dscale + n);
+        float* bh = pb->dense_b;
+        float* xh = pb->dense_b + n;
+        LAUNCH(1, launch_scale_vec(n, (const float*)pb->bvec, dinv, bh, pb->stream));
+        CU(cudaEventRecord(pb->evk[0], pb->stream));
+        DenseResult res;
+        CU(dense_spd_solve(pb->dw, (const float*)pb->Shat, n, n, bh, xh, pb->opt.pcg_rel_tol,
+                           pb->opt.pcg_max_iters, pb->num_sms, pb->stream, &res));
+        CU(cudaEventRecord(pb->evk[1], pb->stream));
+        pb->evk_valid = true;
+        pb->launches += res.launches;
+        LAUNCH(1, launch_scale_vec(n, xh, dinv, (float*)pb->x, pb->stream));
+        LAUNCH(1, launch_set_pcg_info(pb->sc, res.iters, res.rel_res, pb->err,
+                                      ((res.flags & 16) ? 1 : 0) | ((res.flags & 34) ? 2 : 0), pb->stream));
+        pb->dense_last = res;
+        solved = true;
+      }
+    }
+    if (!solved) {
     SpcgArgs<T> a{};
     a.Shat = (const T*)pb->Shat;
     a.Dinv = (const T*)pb->Dinv;
@@ -341,6 +370,7 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     LAUNCH(1, launch_spcg<T>(a, grid, smem, pb->stream));
     CU(cudaEventRecord(pb->evk[1], pb->stream));
     pb->evk_valid = true;
+    }
   }
   LAUNCH(1, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                                   pb->pt_act, pb->crank, (const T*)pb->x, (const T*)pb->Vinv, (const T*)pb->V,
@@ -868,12 +898,22 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   pb->recompute = pb->fp64 ? 0 : 1;
   {
     int so = opts->solver;
-    if (so != BA_SOLVER_AUTO && so != BA_SOLVER_IMPLICIT && so != BA_SOLVER_EXPLICIT) {
+    if (so != BA_SOLVER_AUTO && so != BA_SOLVER_IMPLICIT && so != BA_SOLVER_EXPLICIT && so != BA_SOLVER_DENSE) {
       set_error("unknown solver %d", so);
       return BA_ERR_INVALID_ARG;
     }
-    pb->explicit_S = so == BA_SOLVER_EXPLICIT || (so == BA_SOLVER_AUTO && 9 * C <= 4608);
-    if (pb->explicit_S && (size_t)81 * C * C * (R + 8) > ((size_t)8 << 30)) {
+    if (so == BA_SOLVER_DENSE && pb->fp64) {
+      set_error("BA_SOLVER_DENSE needs BA_FP32 (the factorisation runs on TF32 tensor cores)");
+      return BA_ERR_INVALID_ARG;
+    }
+    // The dense tensor-core solve is opt-in: on the 12M-observation dense
+    // workload (2,000 cameras) forming S from 174M co-visible pairs alone costs
+    // about as much as the whole implicit block-Jacobi PCG, which converges in
+    // 25-46 iterations there; AUTO therefore never picks it.
+    const bool dense = so == BA_SOLVER_DENSE;
+    pb->dense = dense;
+    pb->explicit_S = dense || so == BA_SOLVER_EXPLICIT || (so == BA_SOLVER_AUTO && 9 * C <= 4608);
+    if (pb->explicit_S && (size_t)81 * C * C * (R + (dense ? 4 : 8)) > ((size_t)(dense ? 24 : 8) << 30)) {
       set_error("explicit reduced camera system of order %d is too large", 9 * C);
       return BA_ERR_INVALID_ARG;
     }
@@ -984,6 +1024,19 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     }
     ST(dalloc(pb, &pb->dscale, (size_t)2 * n_max));  // D, then 1/D in the working precision
     ST(dalloc_bytes(pb, &pb->Dblk, R * 45 * (size_t)C));
+    if (pb->dense) {
+      const size_t np = ((size_t)n_max + 127) / 128 * 128;
+      ST(dalloc(pb, &pb->dw.A, np * np));
+      ST(dalloc(pb, &pb->dw.Linv, np * 128));
+      ST(dalloc(pb, &pb->dw.vec, 4 * np));
+      ST(dalloc(pb, &pb->dw.part, (size_t)256));
+      ST(dalloc(pb, &pb->dw.scal, (size_t)8));
+      ST(dalloc(pb, &pb->dw.flags, np / 128));
+      CU(cudaMemset(pb->dw.flags, 0, sizeof(unsigned) * (np / 128)));
+      ST(dalloc(pb, &pb->dw.err, (size_t)1));
+      ST(dalloc(pb, &pb->dense_b, 2 * (size_t)n_max));
+      pb->dw.epoch = &pb->dense_epoch;
+    }
     pb->spcg_grid = std::max(1, std::min(pb->num_sms, C));
     pb->spcg_own_max = std::max(1, (C + pb->spcg_grid - 1) / pb->spcg_grid);
     pb->spcg_rows_in_smem = 1;
@@ -1384,7 +1437,7 @@ int64_t ba_kernel_launches(const ba_problem* pb) { return pb ? pb->launches : 0;
 
 int ba_solver_kind(const ba_problem* pb) {
   if (!pb) return 0;
-  return pb->explicit_S ? BA_SOLVER_EXPLICIT : BA_SOLVER_IMPLICIT;
+  return pb->dense ? BA_SOLVER_DENSE : pb->explicit_S ? BA_SOLVER_EXPLICIT : BA_SOLVER_IMPLICIT;
 }
 
 void ba_destroy(ba_problem* pb) { free_problem(pb); }

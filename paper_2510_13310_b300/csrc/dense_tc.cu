@@ -503,6 +503,328 @@ cudaError_t dense_cholesky_tc(float* A, long long lda, int np, float* Linv, int*
 }
 
 // ---------------------------------------------------------------------------
+// Triangular solves with the blocked factor, L y = r (forward) and L^T x = y
+// (backward), each in one cooperative launch.  Block b takes tiles b, b + G, ...
+// in solve order; tile i waits for the tiles it depends on (a flag per tile,
+// set with release semantics after the tile's values are stored), accumulates
+// r_i - sum_j L_ij y_j as they arrive, and finishes with the diagonal tile's
+// inverse: y_i = L_ii^-1 acc.  Dependencies only point to tiles earlier in
+// every block's order, so with all blocks resident the solve cannot deadlock;
+// waits are bounded (err bit 1 on timeout).
+// ---------------------------------------------------------------------------
+constexpr int kTrThreads = 256;
+
+__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned epoch, long long timeout_ns) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+  if (v == epoch) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+    if (v == epoch) return true;
+    if ((long long)(globaltimer_ns() - t0) > timeout_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void set_flag(unsigned* flag, unsigned epoch) {
+  __threadfence();
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(epoch) : "memory");
+}
+
+// acc[128] (+)= sign * M v for a 128 x 128 row-major tile M (ld), v in shared memory.
+// transpose: acc[c] += sign * sum_r M[r][c] v[r].
+template <bool TRANSPOSE>
+__device__ __forceinline__ void tile_gemv(const float* __restrict__ M, long long ld, const float* v, float* acc,
+                                          float sign, float* red) {
+  const int tid = threadIdx.x;
+  if (!TRANSPOSE) {
+    // row r = tid / 2, half h: columns [64h, 64h + 64)
+    const int r = tid >> 1, h = tid & 1;
+    const float4* m4 = reinterpret_cast<const float4*>(M + (size_t)r * ld + 64 * h);
+    const float4* v4 = reinterpret_cast<const float4*>(v + 64 * h);
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; q += 2) {
+      const float4 a = m4[q], b = v4[q], c = m4[q + 1], d = v4[q + 1];
+      s0 += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+      s1 += c.x * d.x + c.y * d.y + c.z * d.z + c.w * d.w;
+    }
+    float t = s0 + s1;
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    if (h == 0) acc[r] += sign * t;
+  } else {
+    // column c = tid % 128, rows [64h, 64h + 64), h = tid / 128
+    const int c = tid & 127, h = tid >> 7;
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+    for (int r = 64 * h; r < 64 * h + 64; r += 2) {
+      s0 += M[(size_t)r * ld + c] * v[r];
+      s1 += M[(size_t)(r + 1) * ld + c] * v[r + 1];
+    }
+    red[tid] = s0 + s1;
+    __syncthreads();
+    if (h == 0) acc[c] += sign * (red[c] + red[c + 128]);
+  }
+  __syncthreads();
+}
+
+// Forward (!BACK): L y = r.  Backward (BACK): L^T x = y.  rhs, out: np vectors
+// (np = 128 T, 16-byte aligned); L: np x np row-major lower factor (ld); Linv:
+// the T diagonal-tile inverses; flags: T words, epoch unique per call.
+template <bool BACK>
+__global__ void __launch_bounds__(kTrThreads) k_trsv_tiles(const float* __restrict__ L, long long ld,
+                                                           const float* __restrict__ Linv, const float* rhs,
+                                                           float* out, int T, unsigned* flags, unsigned epoch,
+                                                           long long timeout_ns, int* err) {
+  __shared__ __align__(16) float acc[kPt];
+  __shared__ __align__(16) float vb[kPt];
+  __shared__ float red[kTrThreads];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k = blockIdx.x; k < T; k += gridDim.x) {
+    const int i = BACK ? T - 1 - k : k;
+    if (tid < kPt) acc[tid] = rhs[(size_t)i * kPt + tid];
+    __syncthreads();
+    const int jn = BACK ? T - 1 - i : i;  // number of dependencies
+    for (int d = 0; d < jn; ++d) {
+      const int j = BACK ? T - 1 - d : d;
+      if (tid == 0 && !bad && !wait_flag(&flags[j], epoch, timeout_ns)) bad = 1;
+      __syncthreads();
+      if (bad) break;
+      if (tid < kPt) vb[tid] = out[(size_t)j * kPt + tid];
+      __syncthreads();
+      if (!BACK) tile_gemv<false>(L + (size_t)i * kPt * ld + (size_t)j * kPt, ld, vb, acc, -1.f, red);
+      else tile_gemv<true>(L + (size_t)j * kPt * ld + (size_t)i * kPt, ld, vb, acc, -1.f, red);
+    }
+    if (bad) break;
+    if (tid < kPt) vb[tid] = acc[tid];
+    if (tid < kPt) acc[tid] = 0.f;
+    __syncthreads();
+    if (!BACK) tile_gemv<false>(Linv + (size_t)i * kPt * kPt, kPt, vb, acc, 1.f, red);
+    else tile_gemv<true>(Linv + (size_t)i * kPt * kPt, kPt, vb, acc, 1.f, red);
+    if (tid < kPt) out[(size_t)i * kPt + tid] = acc[tid];
+    __syncthreads();
+    if (tid == 0) set_flag(&flags[i], epoch);
+  }
+  if (tid == 0 && bad) atomicOr(err, 1);
+}
+
+cudaError_t dense_trsv(bool back, const float* L, long long ld, const float* Linv, const float* rhs, float* out,
+                       int T, unsigned* flags, unsigned epoch, int* err, int num_sms, cudaStream_t s) {
+  if (T <= 0) return cudaSuccess;
+  int grid = std::min(T, num_sms);
+  long long timeout = 1000000000LL;
+  void* args[] = {(void*)&L, (void*)&ld, (void*)&Linv, (void*)&rhs, (void*)&out, (void*)&T, (void*)&flags,
+                  (void*)&epoch, (void*)&timeout, (void*)&err};
+  const void* fn = back ? reinterpret_cast<const void*>(&k_trsv_tiles<true>)
+                        : reinterpret_cast<const void*>(&k_trsv_tiles<false>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTrThreads), args, 0, s);
+}
+
+// ---------------------------------------------------------------------------
+// Dense preconditioned CG on S^ x = b with M = (L L^T)^-1 from the tensor-core
+// factor.  The factor carries TF32-level error, so it is used as a
+// preconditioner and CG recovers the FP32 solution; when the damped system is
+// nearly singular the iteration count grows rather than the accuracy dropping.
+// Dots in FP64 with a fixed-order two-level reduction; alpha, beta on the
+// device; one host readback per iteration for the stopping test.
+// ---------------------------------------------------------------------------
+constexpr int kDotBlocks = 256;
+
+// padded work matrix: rows/columns n..np the identity, diagonal of the leading
+// block shifted by `shift` (a retry after a non-positive TF32 pivot)
+__global__ void k_pad_shift(float* A, long long ld, int n, int np, float shift) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)np * np;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(q / np), c = (int)(q % np);
+    if (r >= n || c >= n) A[(size_t)r * ld + c] = r == c ? 1.f : 0.f;
+    else if (r == c && shift != 0.f) A[(size_t)r * ld + c] += shift;
+  }
+}
+
+// out[blockIdx] = partial sums of a.b over a grid-stride range (fixed order)
+__global__ void k_dot_partial(const float* __restrict__ a, const float* __restrict__ b, int n, double* part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    s += (double)a[i] * (double)b[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_dot_final(const double* part, int np, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// y = S x over rows [0, n), S row-major with ld (one warp per row)
+__global__ void k_gemv_rows(const float* __restrict__ S, long long ld, const float* __restrict__ x, float* y,
+                            int n) {
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += (gridDim.x * blockDim.x) >> 5) {
+    const float* row = S + (size_t)r * ld;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int c = lane;
+    for (; c + 96 < n; c += 128) {
+      a0 += row[c] * x[c];
+      a1 += row[c + 32] * x[c + 32];
+      a2 += row[c + 64] * x[c + 64];
+      a3 += row[c + 96] * x[c + 96];
+    }
+    for (; c < n; c += 32) a0 += row[c] * x[c];
+    const float t = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) y[r] = t;
+  }
+}
+
+// sc: [0] rz, [1] pq, [2] rr, [3] rz_new, [4] alpha, [5] beta
+__global__ void k_cg_alpha(double* sc) {
+  sc[4] = sc[1] > 0.0 ? sc[0] / sc[1] : 0.0;
+}
+__global__ void k_cg_beta(double* sc) {
+  sc[5] = sc[0] != 0.0 ? sc[3] / sc[0] : 0.0;
+  sc[0] = sc[3];
+}
+// x += alpha p; r -= alpha q
+__global__ void k_cg_xr(float* x, float* r, const float* p, const float* q, const double* sc, int n) {
+  const float al = (float)sc[4];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    x[i] += al * p[i];
+    r[i] -= al * q[i];
+  }
+}
+// p = z + beta p (first: p = z)
+__global__ void k_cg_p(float* p, const float* z, const double* sc, int n, int first) {
+  const float be = first ? 0.f : (float)sc[5];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = z[i] + be * p[i];
+}
+
+__global__ void k_scale_vec(int n, const float* __restrict__ a, const float* __restrict__ d, float* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] * d[i];
+}
+cudaError_t launch_scale_vec(int n, const float* a, const float* d, float* out, cudaStream_t s) {
+  if (n > 0) k_scale_vec<<<std::min((n + 255) / 256, 1024), 256, 0, s>>>(n, a, d, out);
+  return cudaGetLastError();
+}
+__global__ void k_set_pcg_info(Scalars* sc, int iters, double rel, int* err, int errbits) {
+  sc->pcg_iters = iters;
+  sc->pcg_rel_res = rel;
+  if (errbits) atomicOr(err, errbits);
+}
+cudaError_t launch_set_pcg_info(Scalars* sc, int iters, double rel, int* err, int errbits, cudaStream_t s) {
+  k_set_pcg_info<<<1, 1, 0, s>>>(sc, iters, rel, err, errbits);
+  return cudaGetLastError();
+}
+
+cudaError_t dense_dot(const float* a, const float* b, int n, double* part, double* out, cudaStream_t s) {
+  k_dot_partial<<<kDotBlocks, 256, 0, s>>>(a, b, n, part);
+  k_dot_final<<<1, 256, 0, s>>>(part, kDotBlocks, out);
+  return cudaGetLastError();
+}
+
+// Factor S^ (n x n, ld_s) into the padded work matrix and solve S^ x = b.
+cudaError_t dense_spd_solve(const DenseWork& w, const float* S, long long ld_s, int n, const float* b, float* x,
+                            double tol, int max_iters, int num_sms, cudaStream_t s, DenseResult* res) {
+  const int np = (n + kPt - 1) / kPt * kPt, T = np / kPt;
+  res->iters = 0;
+  res->rel_res = 0.0;
+  res->flags = 0;
+  res->shift = 0.0;
+  long long nl = 0;
+  cudaError_t e = cudaSuccess;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    const float shift = attempt == 0 ? 0.f : (attempt == 1 ? 1e-3f : 1e-1f);
+    e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(w.A, sizeof(float) * np, S, sizeof(float) * ld_s, sizeof(float) * n, n,
+                            cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    const long long tot = (long long)np * np;
+    k_pad_shift<<<(unsigned)std::min<long long>((tot + 255) / 256, 65535), 256, 0, s>>>(w.A, np, n, np, shift);
+    ++nl;
+    e = dense_cholesky_tc(w.A, np, np, w.Linv, w.err, s, &nl);
+    if (e != cudaSuccess) return e;
+    int h = 0;
+    e = cudaMemcpyAsync(&h, w.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    res->flags = h;
+    res->shift = shift;
+    if (!(h & 32)) break;
+  }
+  if (res->flags & 16) {
+    res->launches += nl;
+    return cudaSuccess;  // pipeline timeout: reported through flags
+  }
+  // vectors live in padded length np; entries n..np stay zero
+  float *r = w.vec, *z = w.vec + np, *p = w.vec + 2 * (size_t)np, *q = w.vec + 3 * (size_t)np;
+  e = cudaMemsetAsync(w.vec, 0, sizeof(float) * 4 * (size_t)np, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(float) * n, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r, b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int vgrid = std::min((np + 255) / 256, 4 * num_sms);
+  auto precond = [&](const float* in, float* outv) -> cudaError_t {
+    // z = L^-T (L^-1 in): forward into q as scratch, then backward
+    cudaError_t e2 = dense_trsv(false, w.A, np, w.Linv, in, q, T, w.flags, ++*w.epoch, w.err, num_sms, s);
+    if (e2 == cudaSuccess) e2 = dense_trsv(true, w.A, np, w.Linv, q, outv, T, w.flags, ++*w.epoch, w.err, num_sms, s);
+    nl += 2;
+    return e2;
+  };
+  double* sc = w.scal;
+  double h[3] = {0, 0, 0};
+  e = dense_dot(b, b, n, w.part, sc + 2, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  nl += 2;
+  const double bnorm = std::sqrt(h[0]);
+  if (!(bnorm > 0.0)) {
+    res->launches += nl;
+    return cudaSuccess;
+  }
+  e = precond(r, z);
+  if (e == cudaSuccess) e = dense_dot(r, z, n, w.part, sc + 0, s);
+  if (e == cudaSuccess) k_cg_p<<<vgrid, 256, 0, s>>>(p, z, sc, np, 1);
+  nl += 3;
+  int it = 0;
+  double rr = h[0];
+  while (e == cudaSuccess && it < max_iters) {
+    k_gemv_rows<<<std::min((n + 7) / 8, 32 * num_sms), 256, 0, s>>>(S, ld_s, p, q, n);
+    e = dense_dot(p, q, n, w.part, sc + 1, s);
+    k_cg_alpha<<<1, 1, 0, s>>>(sc);
+    k_cg_xr<<<vgrid, 256, 0, s>>>(x, r, p, q, sc, n);
+    if (e == cudaSuccess) e = dense_dot(r, r, n, w.part, sc + 2, s);
+    nl += 7;
+    ++it;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, sc, sizeof(double) * 3, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    rr = h[2];
+    if (!(h[1] > 0.0) || !std::isfinite(rr)) {
+      res->flags |= 2;
+      break;
+    }
+    if (std::sqrt(rr) <= tol * bnorm) break;
+    e = precond(r, z);
+    if (e == cudaSuccess) e = dense_dot(r, z, n, w.part, sc + 3, s);
+    k_cg_beta<<<1, 1, 0, s>>>(sc);
+    k_cg_p<<<vgrid, 256, 0, s>>>(p, z, sc, np, 0);
+    nl += 4;
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  res->iters = it;
+  res->rel_res = std::sqrt(rr) / bnorm;
+  res->launches += nl;
+  return e;
+}
+
+// ---------------------------------------------------------------------------
 // host: tensor maps and launches
 // ---------------------------------------------------------------------------
 

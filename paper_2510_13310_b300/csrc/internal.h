@@ -112,6 +112,33 @@ cudaError_t tc_gemm_nt(const float* A, long long lda, const float* B, long long 
 cudaError_t dense_cholesky_tc(float* A, long long lda, int np, float* Linv, int* err, cudaStream_t s,
                               long long* launches);
 
+// Work buffers of the dense solver (np = n rounded up to 128):
+// A [np][np] factor, Linv [np/128][128][128], vec [4][np], part [256], scal [8],
+// flags [np/128], err [1]; *epoch increases by one per triangular solve.
+struct DenseWork {
+  float* A = nullptr;
+  float* Linv = nullptr;
+  float* vec = nullptr;
+  double* part = nullptr;
+  double* scal = nullptr;
+  unsigned* flags = nullptr;
+  int* err = nullptr;
+  unsigned* epoch = nullptr;  // host counter
+};
+struct DenseResult {
+  int iters = 0;
+  double rel_res = 0.0;
+  int flags = 0;       // 2 breakdown, 16 pipeline timeout, 32 non-positive pivot (after the retries)
+  double shift = 0.0;  // diagonal shift of the factored matrix (0 unless a pivot failed)
+  long long launches = 0;
+};
+cudaError_t dense_trsv(bool back, const float* L, long long ld, const float* Linv, const float* rhs, float* out,
+                       int T, unsigned* flags, unsigned epoch, int* err, int num_sms, cudaStream_t s);
+cudaError_t dense_spd_solve(const DenseWork& w, const float* S, long long ld_s, int n, const float* b, float* x,
+                            double tol, int max_iters, int num_sms, cudaStream_t s, DenseResult* res);
+cudaError_t launch_scale_vec(int n, const float* a, const float* d, float* out, cudaStream_t s);
+cudaError_t launch_set_pcg_info(Scalars* sc, int iters, double rel, int* err, int errbits, cudaStream_t s);
+
 // ---- launchers (return cudaGetLastError of the launch) ----
 template <typename T>
 cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s);

@@ -290,3 +290,44 @@ def test_device_and_host_buffers_agree():
     c_h, p_h = p1.get_params()
     np.testing.assert_array_equal(c_dev.cpu().numpy(), c_h)
     np.testing.assert_array_equal(p_dev.cpu().numpy(), p_h)
+
+
+# ---------------------------------------------------------------------------
+# (d) with the dense solver: tensor-core Cholesky + preconditioned CG (FP32)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_cams,n_pts,track", [(40, 3000, 30), (150, 8000, 40)])
+def test_dense_solver_damped_step_matches_oracle(n_cams, n_pts, track):
+    """Densely co-visible scenes: 40 cameras (one 384-wide factor, 3 tiles) and 150
+    cameras (n = 1341: 11 tiles, two 1024-column panels)."""
+    sc = geometric(n_cams, n_pts, track, track, float(track), seed=77)
+    gpu, orc = pair(sc, ba.BA_FP32, solver=ba.BA_SOLVER_DENSE)
+    assert gpu.explicit_solver is False and ba.lib().ba_solver_kind(gpu.h) == ba.BA_SOLVER_DENSE
+    lam = 1e-3
+    g = gpu.solve_damped(lam)
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    o = orc.solve_step(ne, ext, lam)
+    assert rel_err(g["dc"], o["dc"]) < 2e-2
+    assert rel_err(g["dp"], o["dp"]) < 2e-2
+    assert g["pred_decrease"] == pytest.approx(o["pred_decrease"], rel=2e-2)
+    assert g["pcg_rel_res"] <= 1e-6
+    # the factor is a good preconditioner: CG needs only a few iterations
+    assert g["pcg_iters"] <= 20
+
+
+def test_dense_solver_trajectory_close_to_oracle():
+    sc = geometric(40, 3000, 30, 30, 30.0, seed=78)
+    gpu, orc = pair(sc, ba.BA_FP32, solver=ba.BA_SOLVER_DENSE)
+    log_g = gpu.solve(8)
+    orc.opts.solver = 1
+    _, _, log_o = orc.lm(sc.cams0, sc.pts0, 8)
+    for i, (a, b) in enumerate(zip(log_g, log_o)):
+        assert a["cost"] == pytest.approx(b["cost"], rel=1e-5), i
+
+
+def test_dense_solver_rejects_fp64():
+    sc = tiny()
+    with pytest.raises(ba.BAError):
+        ba.Problem.from_scene(sc, ba.Options(precision=ba.BA_FP64, solver=ba.BA_SOLVER_DENSE))
