@@ -7,6 +7,8 @@ full LM iteration (extraction, residuals/Jacobians, normal equations and
 Schur terms, PCG + back-substitution, candidate evaluation and accept/reject).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload dense --solver dense|implicit   (other scenes, same line)
+  python bench.py --dense-kernels                            (tensor-core GEMM and Cholesky)
 
 Prints one JSON line.  With N > 1 (torchrun) every rank solves its own replica
 on its own GPU ("replicas only": the solve does not shard across GPUs) and the
@@ -103,8 +105,67 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_scene():
-    return scenes.make_scene(WORKLOAD)
+def build_scene(workload=WORKLOAD):
+    return scenes.make_scene(workload)
+
+
+def _workload_name(scene):
+    sp = scene.spec
+    return "%s scene: %d cams, %d pts, %d obs" % (sp.name, sp.n_cams, sp.n_pts, scene.n_obs)
+
+
+def _tf32_peak():
+    """Dense TF32 tensor peak: the measured BF16 burst peak times the nominal
+    TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x nominal tf32/bf16"
+    return 1800.0 * 1.1 / 2.25, "fallback bf16 x nominal tf32/bf16"
+
+
+def run_dense_kernels():
+    """Times the tensor-core kernels on their own: C -= A B^T (TF32, FP32
+    accumulation) and the blocked Cholesky of an SPD matrix of the dense
+    workload's order (17,991), with CUDA events after warm-up."""
+    import torch
+    from paper_2510_13310_b300 import ba
+    dev = torch.device("cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timeit(f, reps):
+        f()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0.record()
+            f()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    peak, src = _tf32_peak()
+    g = torch.Generator(device="cpu").manual_seed(0)
+    out = {"metric": "tensor-core dense kernels", "peak_tf32_tflops": peak, "peak_source": src, "gemm": []}
+    for (M, N, K) in [(8192, 8192, 8192), (16384, 16384, 1024)]:
+        A = torch.randn(M, K, generator=g).to(dev)
+        B = torch.randn(N, K, generator=g).to(dev)
+        C = torch.zeros(M, N, device=dev)
+        ms = timeit(lambda: ba.tc_gemm_nt(A, B, C, alpha=-1.0, beta=1.0), 10)
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        out["gemm"].append({"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "frac": tf / peak})
+        del A, B, C
+    n = 17991
+    X = torch.randn(n, n + 64, generator=g).to(dev) / (n ** 0.5)
+    S = X @ X.T + 0.1 * torch.eye(n, device=dev)
+    d = S.diagonal().sqrt()
+    S = S / d[:, None] / d[None, :]
+    del X
+    ms = timeit(lambda: ba.dense_cholesky(S), 3)
+    out["cholesky"] = {"n": n, "ms_incl_copies": ms, "tflops": n ** 3 / 3.0 / (ms * 1e-3) / 1e12}
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def oracle_cpu_baseline(scene, max_seconds=20.0, max_iters=30):
@@ -125,7 +186,7 @@ def oracle_cpu_baseline(scene, max_seconds=20.0, max_iters=30):
         lam_state = rows[-1]["lam"] if rows else lam_state
     return {"value": done / t_tot, "unit": "LM iters/s", "cores": oracle.get_threads(),
             "kind": "oracle",
-            "sample": f"{done} LM iteration(s) of the 1M-observation scene (FP64, dense Cholesky "
+            "sample": f"{done} LM iteration(s) of the {_workload_name(scene)} (FP64, dense Cholesky "
                       f"of the Schur system), {t_tot:.1f} s"}
 
 
@@ -133,7 +194,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    scene = build_scene()
+    scene = build_scene(args.workload)
     import oracle
     ob = oracle.OracleBA.from_scene(scene)
     cams, pts = scene.cams0.copy(), scene.pts0.copy()
@@ -152,7 +213,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "1M-observation scene: 200 cams, 100k pts, %d obs" % scene.n_obs,
+            "config": {"workload": _workload_name(scene),
                        "n_cams": scene.spec.n_cams, "n_pts": scene.spec.n_pts,
                        "n_obs": scene.n_obs},
             "cpu_baseline": {"value": value, "unit": "LM iters/s", "cores": oracle.get_threads(),
@@ -173,7 +234,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-RMSE comparison")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenes.SPECS),
+                    help="scene (default: the 1M-observation scene)")
+    ap.add_argument("--solver", default="auto", choices=["auto", "implicit", "explicit", "dense"])
+    ap.add_argument("--dense-kernels", action="store_true", help="time the tensor-core kernels only")
     args = ap.parse_args()
+    if args.dense_kernels:
+        return run_dense_kernels()
     if args.impl == "reference":
         return run_reference(args)
 
@@ -192,9 +259,11 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
 
-    scene = build_scene()
+    scene = build_scene(args.workload)
     N = scene.n_obs
-    opts = ba.Options(precision=ba.BA_FP32)
+    solver = {"auto": ba.BA_SOLVER_AUTO, "implicit": ba.BA_SOLVER_IMPLICIT, "explicit": ba.BA_SOLVER_EXPLICIT,
+              "dense": ba.BA_SOLVER_DENSE}[args.solver]
+    opts = ba.Options(precision=ba.BA_FP32, solver=solver)
     prob = ba.Problem.from_scene(scene, opts, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
 
@@ -241,7 +310,13 @@ def main():
     n = 9 * Cf
     mean_it = statistics.mean(i["pcg_iters"] for i in solved) if solved else 0.0
     kern_ms = statistics.mean(i["ms"][4] for i in solved) if solved else None
-    if prob.explicit_solver:
+    kind = prob.solver_kind
+    if kind == ba.BA_SOLVER_DENSE:
+        # the launch covers factorisation + CG; report the factorisation's flops
+        per_launch = n ** 3 / 3.0
+        kname = "dense solve: tensor-core blocked Cholesky (tcgen05 kind::tf32) + preconditioned CG"
+        unit_txt = "n^3/3 flops of the factorisation, n = 9 Cf (timed launch includes the CG)"
+    elif prob.explicit_solver:
         # S^ read once (4 n^2), preconditioner blocks, b, D and 1/D, x out; per
         # iteration the search direction z is written and read once (8 n)
         per_launch = 4 * n * n + 4 * 81 * Cf + 4 * n + 12 * n + 4 * n + mean_it * 8 * n
@@ -253,14 +328,21 @@ def main():
         per_launch = mean_it * (N * (27 * 4 + 4) + P * (6 * 4 + 4))
         kname = "k_pcg (persistent block-Jacobi PCG, implicit Schur matvec)"
         unit_txt = "(112 B x obs + 28 B x points) x iters"
-    achieved = per_launch / (kern_ms * 1e-3) / 1e9 if kern_ms else 0.0
-    roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_source": peak_kind + " (burst copy)",
-                "traffic": NCU_TRAFFIC["k_spcg" if prob.explicit_solver else "k_pcg"],
+    if kind == ba.BA_SOLVER_DENSE:
+        tpeak, tsrc = _tf32_peak()
+        achieved = per_launch / (kern_ms * 1e-3) / 1e12 if kern_ms else 0.0
+        bound, peak, unit, psrc = "tensor", tpeak, "TFLOP/s", tsrc
+    else:
+        achieved = per_launch / (kern_ms * 1e-3) / 1e9 if kern_ms else 0.0
+        bound, peak, unit, psrc = "hbm", hbm, "GB/s", peak_kind + " (burst copy)"
+    roofline = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "peak_source": psrc,
+                "traffic": NCU_TRAFFIC.get("k_spcg" if prob.explicit_solver else "k_pcg")
+                if kind != ba.BA_SOLVER_DENSE else None,
                 "algorithmic_bytes_per_launch": per_launch,
                 "bytes_formula": unit_txt, "launch_ms_mean": kern_ms,
                 "mean_pcg_iters": mean_it, "us_per_pcg_iter": (kern_ms * 1e3 / mean_it) if mean_it else None,
-                "solver": "explicit" if prob.explicit_solver else "implicit"}
+                "solver": {ba.BA_SOLVER_DENSE: "dense", ba.BA_SOLVER_EXPLICIT: "explicit"}.get(kind, "implicit")}
 
     # end to end through the public API from pinned host buffers, one full solve
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -286,8 +368,9 @@ def main():
     # time to the FP64 GPU path's final RMSE
     ttr = None
     if not args.no_ttr:
-        def trajectory(prec):
-            p = ba.Problem.from_scene(scene, ba.Options(precision=prec), stream=stream.cuda_stream)
+        def trajectory(prec, solver=ba.BA_SOLVER_AUTO):
+            p = ba.Problem.from_scene(scene, ba.Options(precision=prec, solver=solver),
+                                      stream=stream.cuda_stream)
             rows, t = [], 0.0
             for _ in range(LM_ITERS):
                 ev0.record(stream)
@@ -300,7 +383,7 @@ def main():
             p.close()
             return rows, F, rm
         rows64, F64, rmse64 = trajectory(ba.BA_FP64)
-        rows32, F32, rmse32 = trajectory(ba.BA_FP32)
+        rows32, F32, rmse32 = trajectory(ba.BA_FP32, solver)
 
         def reach(rows, target_rmse):
             # the end time of the first iteration whose accepted result is within
@@ -331,8 +414,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "1M-observation scene: 200 cams, 100k pts, %d obs, FP32 with "
-                                   "FP64 dots/cost/gain" % N,
+            "config": {"workload": _workload_name(scene) + ", FP32 with FP64 dots/cost/gain",
                        "n_cams": scene.spec.n_cams, "n_pts": P, "n_obs": N,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)"},

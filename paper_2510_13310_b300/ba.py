@@ -303,6 +303,11 @@ class Problem:
         return int(self.L.ba_kernel_launches(self.h))
 
     @property
+    def solver_kind(self) -> int:
+        """BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT or BA_SOLVER_DENSE (ba_solver_kind)."""
+        return int(self.L.ba_solver_kind(self.h))
+
+    @property
     def explicit_solver(self) -> bool:
         """True when the reduced camera system is formed explicitly (BA_SOLVER_EXPLICIT)."""
         return int(self.L.ba_solver_kind(self.h)) == BA_SOLVER_EXPLICIT
