@@ -69,36 +69,40 @@ __global__ void k_eval64(Layout L, ModelParams mp, const double* __restrict__ ca
                          const double* __restrict__ pts64, const uint8_t* __restrict__ act,
                          uint8_t* __restrict__ bits, double* __restrict__ partials) {
   __shared__ double red[32];
-  double acc_cost = 0.0, acc_e2 = 0.0, acc_n = 0.0;
+  double acc_cost = 0.0, acc_e2 = 0.0;
+  int acc_n = 0;
+  // thresholds of the validity predicate as integer keys (FP64 comparisons are FP64-pipe work)
+  const long long kz = dkey(mp.min_depth), kw = dkey((double)mp.img_w), kh = dkey((double)mp.img_h);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += gridDim.x * blockDim.x) {
     int c = L.po_cam[k], p = L.po_pt[k];
     const double* X = pts64 + 3 * (size_t)p;
     double tau = L.po_tau64[k];
-    double sw = tau > 0.0 ? mp.sw_valid : mp.sw_invalid;
+    double sw = __double_as_longlong(tau) > 0 ? mp.sw_valid : mp.sw_invalid;  // tau > 0
     Eval64 e = eval_obs64(camw64 + kCamStride * (size_t)c, X[0], X[1], X[2], L.po_uv64[2 * (size_t)k],
                           L.po_uv64[2 * (size_t)k + 1], tau, sw, mp.cx, mp.cy);
-    double e2 = e.r0 * e.r0 + e.r1 * e.r1;
+    double e2 = fma(e.r0, e.r0, e.r1 * e.r1);
     if (bits) {
-      int ok = e.z > mp.min_depth && e.uh >= 0.0 && e.uh < (double)mp.img_w && e.vh >= 0.0 &&
-               e.vh < (double)mp.img_h;
+      const long long ku = dkey(e.uh), kv = dkey(e.vh);
+      int ok = dkey(e.z) > kz && ku >= 0 && ku < kw && kv >= 0 && kv < kh;
       int b = ok ? 1 : 0;
       if (ok && mp.drop_px > 0.0 && sqrt(e2) > mp.drop_px) b |= 2;
       bits[k] = (uint8_t)b;
     }
     if (act && act[k]) {
-      acc_cost += huber_loss(e2 + e.r2 * e.r2, mp.huber);
+      acc_cost += huber_loss(fma(e.r2, e.r2, e2), mp.huber);
       acc_e2 += e2;
-      acc_n += 1.0;
+      acc_n += 1;
     }
   }
   if (!partials) return;
   double s0 = block_sum(acc_cost, red);
   double s1 = block_sum(acc_e2, red);
-  double s2 = block_sum(acc_n, red);
+  __shared__ int redi[32];
+  int s2 = block_sum(acc_n, redi);
   if (threadIdx.x == 0) {
     partials[3 * blockIdx.x] = s0;
     partials[3 * blockIdx.x + 1] = s1;
-    partials[3 * blockIdx.x + 2] = s2;
+    partials[3 * blockIdx.x + 2] = (double)s2;
   }
 }
 

@@ -24,10 +24,49 @@ __device__ __forceinline__ T huber_weight(T s, T delta) {
   if (delta <= T(0) || s <= delta * delta) return T(1);
   return delta / sqrt(s);
 }
-// Huber loss on the squared norm s.
+// FP64 division and square root are scarce on B300 (a dependent DDIV costs
+// ~400 cycles).  The FP64 evaluation therefore uses Newton-Raphson refinement of
+// FP32 seeds: for 1/a, x <- x + x (1 - a x), each step doubling the correct
+// bits (2^-23 -> 2^-46 -> rounding level); for 1/sqrt(s), y <- y (3 - s y^2) / 2
+// twice, then sqrt(s) = s y with one Newton correction r <- r + (s - r^2) y / 2.
+// Results are within a few ulp of the correctly rounded values.  Arguments
+// outside the FP32 exponent range fall back to the FP64 operations.
+// Comparisons on the integer pipe: for non-NaN doubles the IEEE order equals the
+// signed order of dkey (+0 and -0 both map to 0).  A NaN gets a key beyond every
+// finite value of its sign, so every predicate below that brackets a value from
+// both sides (0 <= u < W) is false for it, as with IEEE comparisons.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : -(b & 0x7FFFFFFFFFFFFFFFll);
+}
+// |a| within [2^-100, 2^100] (exponent field test, no FP64 instruction)
+__device__ __forceinline__ bool fp32_range(double a) {
+  const int e = (int)((unsigned long long)__double_as_longlong(a) >> 52) & 0x7FF;
+  return e >= 1023 - 100 && e <= 1023 + 100;
+}
+
+__device__ __forceinline__ double recip_nr(double a) {
+  if (!fp32_range(a)) return 1.0 / a;
+  double x = (double)__frcp_rn((float)a);
+  x = fma(x, fma(-a, x, 1.0), x);
+  x = fma(x, fma(-a, x, 1.0), x);
+  return x;
+}
+__device__ __forceinline__ double sqrt_nr(double s) {
+  if (__double_as_longlong(s) < 0 || !fp32_range(s)) return sqrt(s);
+  double y = (double)rsqrtf((float)s);
+  const double hs = 0.5 * s;
+  y = y * fma(-hs * y, y, 1.5);
+  y = y * fma(-hs * y, y, 1.5);
+  const double r = s * y;
+  return fma(fma(-r, r, s), 0.5 * y, r);
+}
+
+// Huber loss on the squared norm s (s >= 0 or NaN; the threshold test on the
+// integer pipe).
 __device__ __forceinline__ double huber_loss(double s, double delta) {
-  if (delta <= 0.0 || s <= delta * delta) return s;
-  return 2.0 * delta * sqrt(s) - delta * delta;
+  if (delta <= 0.0 || dkey(s) <= dkey(delta * delta)) return s;
+  return 2.0 * delta * sqrt_nr(s) - delta * delta;
 }
 
 // cw: working camera record (R row-major, t, f, k1, k2).
@@ -100,10 +139,11 @@ __device__ __forceinline__ Eval64 eval_obs64(const double* __restrict__ cw, doub
                                              double X2, double u, double v, double tau, double sw,
                                              double cx, double cy) {
   const double* R = cw;
-  double px = R[0] * X0 + R[1] * X1 + R[2] * X2 + cw[9];
-  double py = R[3] * X0 + R[4] * X1 + R[5] * X2 + cw[10];
-  double pz = R[6] * X0 + R[7] * X1 + R[8] * X2 + cw[11];
-  double xn = px / pz, yn = py / pz;
+  double px = fma(R[0], X0, fma(R[1], X1, fma(R[2], X2, cw[9])));
+  double py = fma(R[3], X0, fma(R[4], X1, fma(R[5], X2, cw[10])));
+  double pz = fma(R[6], X0, fma(R[7], X1, fma(R[8], X2, cw[11])));
+  const double iz = recip_nr(pz);
+  double xn = px * iz, yn = py * iz;
   double rr = xn * xn + yn * yn;
   double fd = cw[12] * (1.0 + rr * (cw[13] + cw[14] * rr));
   Eval64 e;
@@ -112,7 +152,7 @@ __device__ __forceinline__ Eval64 eval_obs64(const double* __restrict__ cw, doub
   e.z = pz;
   e.r0 = e.uh - u;
   e.r1 = e.vh - v;
-  e.r2 = sw * (1.0 / pz - tau);
+  e.r2 = sw * (iz - tau);
   return e;
 }
 

@@ -126,6 +126,24 @@ __device__ __forceinline__ void load_row27<double>(const double* __restrict__ p,
   v[26] = p[26];
 }
 
+// One round of a warp reduce-scatter on a per-lane vector of length M (the
+// first M entries of v): the lane keeps the half selected by bit r of its lane
+// id, sends the other half to lane ^ 2^r and adds what that lane sends back.
+// After the rounds for M = 96, 48, 24, 12, 6 lane L holds the full warp sums of
+// entries 48 b0 + 24 b1 + 12 b2 + 6 b3 + 3 b4 + (0, 1, 2) of the original
+// vector (b_r = bit r of L), in v[0..2]; the order of additions is fixed.
+template <typename T, int M>
+__device__ __forceinline__ void rs_round(T (&v)[96], int lane, int r) {
+  constexpr int H = M / 2;
+  const bool hi = (lane >> r) & 1;
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const T send = hi ? v[i] : v[H + i];
+    const T keep = hi ? v[H + i] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << r);
+  }
+}
+
 // Off-diagonal blocks from the static co-visibility runs: run = every point seen
 // by both cameras i < j, as pairs (k, k2) of point-order observations, ascending
 // in point.  One warp per run: each lane sums Y^_k Y^_k2^T over its subset of the
@@ -161,15 +179,24 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
         for (int s2 = 0; s2 < 9; ++s2)
           acc[9 * r + s2] += y1[3 * r] * y2[3 * s2] + y1[3 * r + 1] * y2[3 * s2 + 1] + y1[3 * r + 2] * y2[3 * s2 + 2];
     }
+    // warp reduce-scatter of the 81 sums (padded to 96): lane keeps three finished sums
+    T v[96];
 #pragma unroll
-    for (int t = 0; t < 81; ++t) acc[t] = warp_sum(acc[t]);
-    for (int t = lane; t < 81; t += 32) {
-      T v = acc[0];
+    for (int t = 0; t < 96; ++t) v[t] = t < 81 ? acc[t] : T(0);
+    rs_round<T, 96>(v, lane, 0);
+    rs_round<T, 48>(v, lane, 1);
+    rs_round<T, 24>(v, lane, 2);
+    rs_round<T, 12>(v, lane, 3);
+    rs_round<T, 6>(v, lane, 4);
+    const int base = 48 * (lane & 1) + 24 * ((lane >> 1) & 1) + 12 * ((lane >> 2) & 1) + 6 * ((lane >> 3) & 1) +
+                     3 * ((lane >> 4) & 1);
 #pragma unroll
-      for (int u = 1; u < 81; ++u)
-        if (u == t) v = acc[u];
-      const int r = t / 9, s2 = t - 9 * r;
-      Shat[(size_t)(9 * a + r) * n + 9 * b + s2] = -v;
+    for (int j = 0; j < 3; ++j) {
+      const int t = base + j;
+      if (t < 81) {
+        const int r = t / 9, s2 = t - 9 * r;
+        Shat[(size_t)(9 * a + r) * n + 9 * b + s2] = -v[j];
+      }
     }
   }
 }
