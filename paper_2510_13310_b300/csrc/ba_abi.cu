@@ -1037,7 +1037,12 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       ST(dalloc(pb, &pb->dense_b, 2 * (size_t)n_max));
       pb->dw.epoch = &pb->dense_epoch;
     }
-    pb->spcg_grid = std::max(1, std::min(pb->num_sms, C));
+    // equal camera counts per block: the slowest block sets the pace of every
+    // cross-block exchange, so ceil(C / k) blocks of k cameras beat an uneven split
+    {
+      const int per = (C + pb->num_sms - 1) / pb->num_sms;
+      pb->spcg_grid = std::max(1, (C + per - 1) / per);
+    }
     pb->spcg_own_max = std::max(1, (C + pb->spcg_grid - 1) / pb->spcg_grid);
     pb->spcg_rows_in_smem = 1;
     for (;;) {
