@@ -113,6 +113,7 @@ struct ba_problem {
   int4* covis_runs = nullptr;   // (camera i, camera j, first pair, count), i < j
   int2* covis_pairs = nullptr;  // point-order observations (k in i, k2 in j) of shared points
   int n_covis_runs = 0;
+  bool form_lanes = false;      // one lane per co-visibility run (many short runs)
   double* dscale = nullptr;
   int spcg_grid = 0, spcg_own_max = 1, spcg_rows_in_smem = 0, bs_grid = 1;
   size_t spcg_smem = 0;
@@ -319,7 +320,7 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   if (Cf > 0) {
     LAUNCH(5, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
                                (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
-                               Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->num_sms, pb->stream));
+                               Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->form_lanes, pb->num_sms, pb->stream));
     bool solved = false;
     if constexpr (sizeof(T) == 4) {
       if (pb->dense) {
@@ -1017,6 +1018,9 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
           if (cnt[q + 1] > cnt[q]) hr.push_back(make_int4(i, j, (int)cnt[q], (int)(cnt[q + 1] - cnt[q])));
         }
       pb->n_covis_runs = (int)hr.size();
+      // one lane per run when there are enough runs for four blocks of 128 lanes
+      // per SM and runs are short (a warp per run would idle in its reduction)
+      pb->form_lanes = (long long)hr.size() >= 4LL * 128 * pb->num_sms && npairs < 128 * hr.size();
       ST(dalloc(pb, &pb->covis_pairs, npairs));
       if (npairs) CU(cudaMemcpy(pb->covis_pairs, hp.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice));
       ST(dalloc(pb, &pb->covis_runs, hr.size()));

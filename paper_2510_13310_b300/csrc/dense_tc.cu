@@ -553,17 +553,32 @@ __device__ __forceinline__ void tile_gemv(const float* __restrict__ M, long long
     t += __shfl_xor_sync(0xffffffffu, t, 1);
     if (h == 0) acc[r] += sign * t;
   } else {
-    // column c = tid % 128, rows [64h, 64h + 64), h = tid / 128
-    const int c = tid & 127, h = tid >> 7;
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll 8
-    for (int r = 64 * h; r < 64 * h + 64; r += 2) {
-      s0 += M[(size_t)r * ld + c] * v[r];
-      s1 += M[(size_t)(r + 1) * ld + c] * v[r + 1];
+    // columns [4 cg, 4 cg + 4), rows [16 rg, 16 rg + 16): 16 float4 loads in flight per
+    // thread; the 8 row groups are summed through shared memory (red: 8 x 128)
+    const int cg = tid & 31, rg = tid >> 5;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float* base = M + (size_t)(16 * rg) * ld + 4 * cg;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const float4 m = *reinterpret_cast<const float4*>(base + (size_t)r * ld);
+      const float vr = v[16 * rg + r];
+      s.x += m.x * vr;
+      s.y += m.y * vr;
+      s.z += m.z * vr;
+      s.w += m.w * vr;
     }
-    red[tid] = s0 + s1;
+    float* rw = red + rg * 128 + 4 * cg;
+    rw[0] = s.x;
+    rw[1] = s.y;
+    rw[2] = s.z;
+    rw[3] = s.w;
     __syncthreads();
-    if (h == 0) acc[c] += sign * (red[c] + red[c + 128]);
+    if (tid < 128) {
+      float t = 0.f;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) t += red[g * 128 + tid];
+      acc[tid] += sign * t;
+    }
   }
   __syncthreads();
 }
@@ -578,7 +593,7 @@ __global__ void __launch_bounds__(kTrThreads) k_trsv_tiles(const float* __restri
                                                            long long timeout_ns, int* err) {
   __shared__ __align__(16) float acc[kPt];
   __shared__ __align__(16) float vb[kPt];
-  __shared__ float red[kTrThreads];
+  __shared__ float red[8 * kPt];
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;

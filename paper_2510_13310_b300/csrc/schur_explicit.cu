@@ -201,6 +201,45 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
   }
 }
 
+// The same blocks with one lane per run, for scenes with very many short runs
+// (every camera pair sharing a few dozen points): each lane accumulates its run
+// in registers and writes the 81 entries itself, so no cross-lane reduction is
+// needed; lanes of a warp take consecutive runs of similar length.
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
+    k_form_S_lanes(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
+                   const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat) {
+  const int n = 9 * Cf;
+  for (int ri = blockIdx.x * blockDim.x + threadIdx.x; ri < n_runs; ri += gridDim.x * blockDim.x) {
+    const int4 rn = runs[ri];
+    const int a = crank[rn.x], b = crank[rn.y];
+    if (a < 0 || b < 0) continue;
+    T acc[81];
+#pragma unroll
+    for (int q = 0; q < 81; ++q) acc[q] = T(0);
+    const int qe = rn.z + rn.w;
+    int2 nxt = pairs[rn.z];
+    for (int q = rn.z; q < qe; ++q) {
+      const int2 pr = nxt;
+      if (q + 1 < qe) nxt = pairs[q + 1];
+      T y2[27];
+      load_row27<T>(Y + kWStride * (size_t)pr.y, y2);
+      const T* y1 = Y + kWStride * (size_t)pr.x;
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        const T a0 = y1[3 * r], a1 = y1[3 * r + 1], a2 = y1[3 * r + 2];
+#pragma unroll
+        for (int s2 = 0; s2 < 9; ++s2)
+          acc[9 * r + s2] += a0 * y2[3 * s2] + a1 * y2[3 * s2 + 1] + a2 * y2[3 * s2 + 2];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+      for (int s2 = 0; s2 < 9; ++s2) Shat[(size_t)(9 * a + r) * n + 9 * b + s2] = -acc[9 * r + s2];
+  }
+}
+
 // Diagonal blocks from the block-Jacobi blocks D_a = U*_a - sum W V*^-1 W^T (packed),
 // scaled; and the lower triangle mirrored from the upper one.
 template <typename T>
@@ -264,7 +303,7 @@ __global__ void k_dscale(int Cf, const T* __restrict__ Ud, double* __restrict__ 
 template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
-                          int Cf, T* Y, T* Shat, int num_sms, cudaStream_t s) {
+                          int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaStream_t s) {
   if (Cf <= 0) return cudaSuccess;
   const int n = 9 * Cf;
   k_dscale<T><<<(n + 255) / 256, 256, 0, s>>>(Cf, Ud, dscale);
@@ -273,9 +312,16 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
   if (e != cudaSuccess) return e;
   if (n_runs > 0) {
     const int wpb = 4;  // warps per 128-thread block
-    int grid = (n_runs + wpb - 1) / wpb;
-    if (grid > 32 * num_sms) grid = 32 * num_sms;
-    k_form_S_runs<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
+    if (lanes) {
+      // many short runs: one lane per run
+      int grid = (n_runs + 127) / 128;
+      if (grid > 16 * num_sms) grid = 16 * num_sms;
+      k_form_S_lanes<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
+    } else {
+      int grid = (n_runs + wpb - 1) / wpb;
+      if (grid > 32 * num_sms) grid = 32 * num_sms;
+      k_form_S_runs<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
+    }
   }
   int nt = (n + 31) / 32;
   k_S_finalize<T><<<dim3(nt, nt), dim3(32, 8), 0, s>>>(Cf, Dblk, dscale, Shat);
@@ -683,7 +729,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
 #define BAB_SINST(T)                                                                                   \
   template cudaError_t launch_form_S<T>(const Layout&, int, const int4*, const int2*, const T*,        \
                                         const T*, const int*, const T*, const T*, double*, int, T*, T*, \
-                                        int, cudaStream_t);                                            \
+                                        bool, int, cudaStream_t);                                      \
   template size_t spcg_smem_bytes<T>(int, int, int);                                                   \
   template const void* spcg_kernel_ptr<T>();                                                           \
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \

@@ -331,3 +331,19 @@ def test_dense_solver_rejects_fp64():
     sc = tiny()
     with pytest.raises(ba.BAError):
         ba.Problem.from_scene(sc, ba.Options(precision=ba.BA_FP64, solver=ba.BA_SOLVER_DENSE))
+
+
+def test_explicit_solver_with_many_short_runs_matches_oracle():
+    """600 cameras sharing a few points per camera pair: ~170k co-visibility runs of
+    ~5 pairs, formed with one lane per run."""
+    sc = geometric(600, 30000, 8, 8, 8.0, seed=79)
+    gpu, orc = pair(sc, ba.BA_FP32, solver=ba.BA_SOLVER_EXPLICIT)
+    lam = 1e-3
+    g = gpu.solve_damped(lam)
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    o = orc.solve_step(ne, ext, lam)
+    assert rel_err(g["dc"], o["dc"]) < 2e-2
+    assert rel_err(g["dp"], o["dp"]) < 2e-2
+    assert g["pred_decrease"] == pytest.approx(o["pred_decrease"], rel=2e-2)
