@@ -375,8 +375,8 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   }
   LAUNCH(1, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                                   pb->pt_act, pb->crank, (const T*)pb->x, (const T*)pb->Vinv, (const T*)pb->V,
-                                  (const T*)pb->gp, lambda, (T*)pb->dp, pb->pred_parts, pb->bs_grid,
-                                  pb->stream));
+                                  (const T*)pb->gp, (const T*)pb->W, lambda, (T*)pb->dp, pb->pred_parts,
+                                  pb->bs_grid, pb->stream));
   LAUNCH(1, launch_pred_cams<T>(Cf, pb->cam_map, (const T*)pb->x, (const T*)pb->Ug, (const T*)pb->dampc,
                                 lambda, pb->pred_parts, pb->bs_grid, pb->stream));
   LAUNCH(1, launch_reduce_pred(pb->pred_parts, pb->bs_grid + 1, pb->sc, pb->stream));

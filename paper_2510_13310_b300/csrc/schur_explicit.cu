@@ -658,15 +658,17 @@ cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_
 int spcg_threads() { return kSpcgThreads; }
 
 // ---------------------------------------------------------------------------
-// Point back-substitution dp = V*^-1 (-g_p - sum_k W_k^T dc_c(k)), W recomputed,
-// and the point part of the predicted decrease.  One thread per point.
+// Point back-substitution dp = V*^-1 (-g_p - sum_k W_k^T dc_c(k)), with the
+// stored W rows when there are any (explicit system), else W recomputed; and the
+// point part of the predicted decrease.  One thread per point.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_backsub_pts(Layout L, ModelParams mp, const T* __restrict__ camw, const T* __restrict__ ptsw,
                               const uint8_t* __restrict__ act_po, const uint8_t* __restrict__ pt_act,
                               const int* __restrict__ crank, const T* __restrict__ x,
                               const T* __restrict__ Vinv, const T* __restrict__ V, const T* __restrict__ gp,
-                              double lambda, T* __restrict__ dp, double* __restrict__ pred_parts) {
+                              const T* __restrict__ Wst, double lambda, T* __restrict__ dp,
+                              double* __restrict__ pred_parts) {
   __shared__ double red[32];
   double pred = 0.0;
   const T* po_uv = reinterpret_cast<const T*>(L.po_uvw);
@@ -683,10 +685,14 @@ __global__ void k_backsub_pts(Layout L, ModelParams mp, const T* __restrict__ ca
       int c = L.po_cam[k];
       int cr = crank[c];
       if (cr < 0) continue;
-      T cw[kCamStride];
-      load_cam_rec(camw, c, cw);
       T W[27];
-      obs_W(cw, X, po_uv[2 * (size_t)k], po_uv[2 * (size_t)k + 1], po_tau[k], mp, W);
+      if (Wst) {
+        load_row27<T>(Wst + kWStride * (size_t)k, W);
+      } else {
+        T cw[kCamStride];
+        load_cam_rec(camw, c, cw);
+        obs_W(cw, X, po_uv[2 * (size_t)k], po_uv[2 * (size_t)k + 1], po_tau[k], mp, W);
+      }
       const T* xv = x + 9 * (size_t)cr;
       T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
@@ -719,10 +725,10 @@ __global__ void k_backsub_pts(Layout L, ModelParams mp, const T* __restrict__ ca
 template <typename T>
 cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
                                const uint8_t* act_po, const uint8_t* pt_act, const int* crank, const T* x,
-                               const T* Vinv, const T* V, const T* gp, double lambda, T* dp,
+                               const T* Vinv, const T* V, const T* gp, const T* Wst, double lambda, T* dp,
                                double* pred_parts, int grid, cudaStream_t s) {
-  k_backsub_pts<T><<<grid, 256, 0, s>>>(L, mp, camw, ptsw, act_po, pt_act, crank, x, Vinv, V, gp, lambda, dp,
-                                         pred_parts);
+  k_backsub_pts<T><<<grid, 256, 0, s>>>(L, mp, camw, ptsw, act_po, pt_act, crank, x, Vinv, V, gp, Wst, lambda,
+                                         dp, pred_parts);
   return cudaGetLastError();
 }
 
@@ -735,8 +741,8 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \
   template cudaError_t launch_backsub_pts<T>(const Layout&, const ModelParams&, const T*, const T*,    \
                                              const uint8_t*, const uint8_t*, const int*, const T*,     \
-                                             const T*, const T*, const T*, double, T*, double*, int,   \
-                                             cudaStream_t);
+                                             const T*, const T*, const T*, const T*, double, T*,       \
+                                             double*, int, cudaStream_t);
 BAB_SINST(float)
 BAB_SINST(double)
 
