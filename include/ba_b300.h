@@ -127,6 +127,18 @@ ba_status ba_get_params(ba_problem* pb, double* cams, double* pts);
 /* Replace the current parameters; the next step re-extracts and re-linearises. */
 ba_status ba_set_params(ba_problem* pb, const double* cams, const double* pts);
 
+/* Checkpoint and resume of an LM run.  The state is everything later iterations
+ * depend on: the FP64 parameters, the damping lambda and nu, the iteration count
+ * (which schedules the residual drop) and the sticky drop bits.  ba_get_state
+ * with blob == NULL stores the size in *bytes; otherwise it writes *bytes bytes
+ * (host memory) or fails with BA_ERR_INVALID_ARG if *bytes is too small.
+ * ba_set_state restores a blob into a problem created from the same
+ * observations (sizes, index arrays, precision; checked through a hash) and
+ * re-extracts at the next step; continuing from a restored state repeats the
+ * uninterrupted run bit for bit (every reduction has a fixed order). */
+ba_status ba_get_state(ba_problem* pb, void* blob, size_t* bytes);
+ba_status ba_set_state(ba_problem* pb, const void* blob, size_t bytes);
+
 /* Active sets of the latest extraction (Sec. 4.2 step 2).  Masks are 0/1 bytes;
  * obs_mask is in the input observation order; cam_rank is the position among
  * active non-gauge cameras, pt_rank among active points, -1 otherwise.

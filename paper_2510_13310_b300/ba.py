@@ -26,6 +26,7 @@ BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT, BA_SOLVER_DENSE = 0, 1, 
 EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
            "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
+           "ba_get_state", "ba_set_state",
            "ba_kernel_launches", "ba_solver_kind", "ba_destroy",
            "ba_status_string", "ba_last_error")
 
@@ -91,6 +92,8 @@ def lib():
         L.ba_kernel_launches.restype = ct.c_int64
         L.ba_solver_kind.argtypes = [vp]
         L.ba_solver_kind.restype = ct.c_int
+        L.ba_get_state.argtypes = [vp, vp, ct.POINTER(ct.c_size_t)]
+        L.ba_set_state.argtypes = [vp, vp, ct.c_size_t]
         L.ba_tc_gemm_nt.argtypes = [vp, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_float, vp, ct.c_int64, vp,
                                     ct.c_int64, ct.c_float, vp, ct.c_int64]
         L.ba_dense_cholesky.argtypes = [vp, ct.c_int64, vp, ct.c_int64, vp, ct.c_int64, ct.POINTER(ct.c_int)]
@@ -100,7 +103,8 @@ def lib():
         L.ba_last_error.restype = ct.c_char_p
         for f in ("ba_create", "ba_lm_step", "ba_solve", "ba_get_params", "ba_set_params",
                   "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped", "ba_eval_cost",
-                  "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky"):
+                  "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
+                  "ba_get_state", "ba_set_state"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -297,6 +301,19 @@ class Problem:
         _check(self.L.ba_backward(self.h, a.p, b.p, ua.p, da.p), "ba_backward",
                allow=(BA_OK, BA_ERR_NOT_CONVERGED))
         return ua.obj, da.obj
+
+    def get_state(self) -> bytes:
+        """ba_get_state: a checkpoint of the LM run (parameters, damping, iteration, drop bits)."""
+        n = ct.c_size_t(0)
+        _check(self.L.ba_get_state(self.h, None, ct.byref(n)), "ba_get_state")
+        buf = (ct.c_ubyte * n.value)()
+        _check(self.L.ba_get_state(self.h, ct.cast(buf, ct.c_void_p), ct.byref(n)), "ba_get_state")
+        return bytes(buf)
+
+    def set_state(self, blob: bytes):
+        """ba_set_state: resume from a checkpoint taken on a problem with the same observations."""
+        buf = (ct.c_ubyte * len(blob)).from_buffer_copy(blob)
+        _check(self.L.ba_set_state(self.h, ct.cast(buf, ct.c_void_p), len(blob)), "ba_set_state")
 
     @property
     def kernel_launches(self):

@@ -122,6 +122,7 @@ struct ba_problem {
   // LM bookkeeping
   int iter = 0;
   double lambda = 1e-4, nu = 2.0;
+  uint64_t obs_hash = 0;        // FNV-1a of the input index arrays (checkpoint identity)
   bool extracted = false, state_changed = true, linearized = false;
   bool bits_valid[2] = {false, false};
   bool cost_valid[2] = {false, false};
@@ -631,6 +632,22 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       set_error("observation %d has an index out of range", k);
       return BA_ERR_INVALID_ARG;
     }
+  }
+  {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](int32_t v) {
+      for (int b = 0; b < 4; ++b) {
+        h ^= (uint64_t)((uint32_t)v >> (8 * b) & 0xFFu);
+        h *= 1099511628211ull;
+      }
+    };
+    mix(C);
+    mix(P);
+    for (int k = 0; k < N; ++k) {
+      mix(h_oc[k]);
+      mix(h_op[k]);
+    }
+    pb->obs_hash = h;
   }
   std::vector<uint8_t> h_fixed((size_t)C, 0);
   for (int32_t f : pb->fixed_list) {
@@ -1273,6 +1290,83 @@ ba_status ba_set_params(ba_problem* pb, const double* cams, const double* pts) {
   pb->state_changed = true;
   pb->linearized = false;
   ST(sync(pb));
+  return BA_OK;
+}
+
+namespace {
+struct StateHeader {
+  uint64_t magic;  // "BAB300ST"
+  uint32_t version, precision;
+  int64_t C, P, N;
+  uint64_t obs_hash;
+  int64_t iter;
+  double lambda, nu;
+};
+constexpr uint64_t kStateMagic = 0x5453303033424142ull;
+size_t state_bytes(const ba_problem* pb) {
+  return sizeof(StateHeader) + sizeof(double) * (9 * (size_t)pb->C + 3 * (size_t)pb->P) + (size_t)pb->N;
+}
+}  // namespace
+
+ba_status ba_get_state(ba_problem* pb, void* blob, size_t* bytes) {
+  if (!pb || !bytes) return BA_ERR_INVALID_ARG;
+  const size_t need = state_bytes(pb);
+  if (!blob) {
+    *bytes = need;
+    return BA_OK;
+  }
+  if (*bytes < need) {
+    set_error("ba_get_state: blob of %zu bytes, %zu needed", *bytes, need);
+    *bytes = need;
+    return BA_ERR_INVALID_ARG;
+  }
+  ST(sync(pb));
+  unsigned char* out = static_cast<unsigned char*>(blob);
+  StateHeader h{kStateMagic, 1u, (uint32_t)(pb->fp64 ? BA_FP64 : BA_FP32), pb->C, pb->P, pb->N, pb->obs_hash,
+                pb->iter, pb->lambda, pb->nu};
+  memcpy(out, &h, sizeof h);
+  out += sizeof h;
+  const int s = pb->cur;
+  if (pb->C) CU(cudaMemcpy(out, pb->cams64[s], sizeof(double) * 9 * (size_t)pb->C, cudaMemcpyDefault));
+  out += sizeof(double) * 9 * (size_t)pb->C;
+  if (pb->P) CU(cudaMemcpy(out, pb->pts64[s], sizeof(double) * 3 * (size_t)pb->P, cudaMemcpyDefault));
+  out += sizeof(double) * 3 * (size_t)pb->P;
+  if (pb->N) CU(cudaMemcpy(out, pb->alive, (size_t)pb->N, cudaMemcpyDefault));
+  *bytes = need;
+  return BA_OK;
+}
+
+ba_status ba_set_state(ba_problem* pb, const void* blob, size_t bytes) {
+  if (!pb || !blob) return BA_ERR_INVALID_ARG;
+  StateHeader h;
+  if (bytes < sizeof h) {
+    set_error("ba_set_state: blob too short");
+    return BA_ERR_INVALID_ARG;
+  }
+  memcpy(&h, blob, sizeof h);
+  if (h.magic != kStateMagic || h.version != 1u) {
+    set_error("ba_set_state: not a state blob of this library");
+    return BA_ERR_INVALID_ARG;
+  }
+  if (h.C != pb->C || h.P != pb->P || h.N != pb->N || h.obs_hash != pb->obs_hash ||
+      h.precision != (uint32_t)(pb->fp64 ? BA_FP64 : BA_FP32) || bytes < state_bytes(pb)) {
+    set_error("ba_set_state: the blob belongs to a different problem (sizes, observations or precision)");
+    return BA_ERR_INVALID_ARG;
+  }
+  if (!(h.lambda > 0.0) || !std::isfinite(h.lambda) || !(h.nu >= 1.0) || !std::isfinite(h.nu) || h.iter < 0) {
+    set_error("ba_set_state: invalid damping state");
+    return BA_ERR_INVALID_ARG;
+  }
+  const unsigned char* in = static_cast<const unsigned char*>(blob) + sizeof h;
+  const double* cams = reinterpret_cast<const double*>(in);
+  const double* pts = cams + 9 * (size_t)pb->C;
+  const unsigned char* alive = reinterpret_cast<const unsigned char*>(pts + 3 * (size_t)pb->P);
+  ST(ba_set_params(pb, cams, pts));
+  if (pb->N) CU(cudaMemcpy(pb->alive, alive, (size_t)pb->N, cudaMemcpyDefault));
+  pb->iter = (int)h.iter;
+  pb->lambda = h.lambda;
+  pb->nu = h.nu;
+  pb->extracted = false;
   return BA_OK;
 }
 
