@@ -109,6 +109,23 @@ def build_scene(workload=WORKLOAD):
     return scenes.make_scene(workload)
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' values (the slowest replica's time); x itself
+    without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, max_ms):
+    """Whole-job LM iterations per second: every replica runs `steps` iterations, the
+    job takes as long as the slowest replica."""
+    return world * steps / (max_ms / 1e3)
+
+
 def _workload_name(scene):
     sp = scene.spec
     return "%s scene: %d cams, %d pts, %d obs" % (sp.name, sp.n_cams, sp.n_pts, scene.n_obs)
@@ -287,12 +304,8 @@ def main():
             step_ms.append(ev0.elapsed_time(ev1))
     torch.cuda.synchronize(dev)
     launches = prob.kernel_launches - launches0
-    tot_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(sum(step_ms), dist, dev)
+    value = job_throughput(world, args.steps, tot_ms)
 
     # Jacobian+Schur throughput: observations through steps (a)+(b) per second
     lin = [i for i in infos if i["ms"][1] > 0]
