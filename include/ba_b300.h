@@ -230,6 +230,13 @@ ba_status ba_tc_gemm_nt(void* stream, int64_t M, int64_t N, int64_t K, float alp
 ba_status ba_dense_cholesky(void* stream, int64_t n, const float* A, int64_t lda, float* L, int64_t ldl,
                             int* flags);
 
+/* Diagnostic of failure detection: launches one block that waits, with the
+ * given limit (ms, at most 5000), on a device flag that nothing sets, using
+ * the bounded wait of the library's cross-block kernels.  Returns
+ * BA_ERR_TIMEOUT (the expected outcome: the wait gave up, the error was reported
+ * through device memory and the context stays usable), or BA_ERR_CUDA. */
+ba_status ba_selftest_wait_timeout(void* stream, double timeout_ms);
+
 /* Number of this library's kernels launched since creation (counts launches). */
 int64_t ba_kernel_launches(const ba_problem* pb);
 

@@ -26,7 +26,7 @@ BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT, BA_SOLVER_DENSE = 0, 1, 
 EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
            "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
-           "ba_get_state", "ba_set_state",
+           "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout",
            "ba_kernel_launches", "ba_solver_kind", "ba_destroy",
            "ba_status_string", "ba_last_error")
 
@@ -94,6 +94,7 @@ def lib():
         L.ba_solver_kind.restype = ct.c_int
         L.ba_get_state.argtypes = [vp, vp, ct.POINTER(ct.c_size_t)]
         L.ba_set_state.argtypes = [vp, vp, ct.c_size_t]
+        L.ba_selftest_wait_timeout.argtypes = [vp, ct.c_double]
         L.ba_tc_gemm_nt.argtypes = [vp, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_float, vp, ct.c_int64, vp,
                                     ct.c_int64, ct.c_float, vp, ct.c_int64]
         L.ba_dense_cholesky.argtypes = [vp, ct.c_int64, vp, ct.c_int64, vp, ct.c_int64, ct.POINTER(ct.c_int)]
@@ -104,7 +105,7 @@ def lib():
         for f in ("ba_create", "ba_lm_step", "ba_solve", "ba_get_params", "ba_set_params",
                   "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped", "ba_eval_cost",
                   "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
-                  "ba_get_state", "ba_set_state"):
+                  "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib

@@ -13,6 +13,8 @@
 #include <vector>
 
 #include "../../include/ba_b300.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using namespace bab;
@@ -496,32 +498,53 @@ ba_status backward_t(ba_problem* pb, const double* dc, const double* dpts, doubl
   return BA_OK;
 }
 
+// NVTX range for the host-side enqueue of one LM phase (visible in Nsight timelines);
+// ends at end() or when leaving the scope.
+struct NvtxScope {
+  bool open = true;
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  void end() {
+    if (open) nvtxRangePop();
+    open = false;
+  }
+  ~NvtxScope() { end(); }
+};
+
 ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   const ba_options& o = pb->opt;
   int k = pb->iter;
   bool drop = o.extract_every > 0 && o.drop_residual_px > 0 && k > 0 && k % o.extract_every == 0;
   CU(cudaEventRecord(pb->ev[0], pb->stream));
+  NvtxScope r_extract("ba: extract");
   if (!pb->extracted || pb->state_changed || drop) {
     ST(run_extraction(pb, drop, nullptr));
     pb->state_changed = false;
   }
   if (!pb->cost_valid[pb->cur]) ST(eval_state(pb, pb->cur, false, true));
   CU(cudaEventRecord(pb->ev[1], pb->stream));
+  r_extract.end();
+  NvtxScope r_lin("ba: linearize");
   if (!pb->linearized) {
     if (pb->fp64) ST(linearize_t<double>(pb));
     else ST(linearize_t<float>(pb));
   }
   CU(cudaEventRecord(pb->ev[2], pb->stream));
+  r_lin.end();
+  NvtxScope r_schur("ba: schur terms");
   double lambda = pb->lambda;
   CU(cudaMemsetAsync(pb->err, 0, sizeof(int), pb->stream));
   if (pb->fp64) ST(schur_t<double>(pb, lambda));
   else ST(schur_t<float>(pb, lambda));
   CU(cudaEventRecord(pb->ev[3], pb->stream));
+  r_schur.end();
+  NvtxScope r_solve("ba: solve");
   pb->evk_valid = false;
   if (pb->fp64) ST(pcg_t<double>(pb, lambda));
   else ST(pcg_t<float>(pb, lambda));
   CU(cudaEventRecord(pb->ev[4], pb->stream));
   CU(cudaEventRecord(pb->ev[5], pb->stream));
+  r_solve.end();
+  NvtxScope r_eval("ba: candidate + evaluate");
   if (pb->fp64) ST(candidate_t<double>(pb));
   else ST(candidate_t<float>(pb));
   int nxt = 1 - pb->cur;

@@ -1011,4 +1011,43 @@ ba_status ba_dense_cholesky(void* stream, int64_t n, const float* A, int64_t lda
   return BA_OK;
 }
 
+// Diagnostic of the bounded waits every cross-block kernel of this library uses:
+// one block waits, with the given limit, on a device flag that nothing sets.
+__global__ void k_wait_selftest(const unsigned* flag, long long timeout_ns, int* out) {
+  if (threadIdx.x == 0) *out = bab::wait_flag(flag, 1u, timeout_ns) ? 1 : 2;
+}
+
+ba_status ba_selftest_wait_timeout(void* stream, double timeout_ms) {
+  if (!(timeout_ms > 0.0) || timeout_ms > 5000.0) {
+    dense_error("ba_selftest_wait_timeout: limit must be in (0, 5000] ms");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* flag = nullptr;
+  int* out = nullptr;
+  cudaError_t e = cudaMallocAsync(&flag, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&out, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32, 0, s>>>(flag, (long long)(timeout_ms * 1e6), out);
+    e = cudaGetLastError();
+  }
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, out, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (flag) cudaFreeAsync(flag, s);
+  if (out) cudaFreeAsync(out, s);
+  if (e != cudaSuccess) {
+    dense_error("ba_selftest_wait_timeout: %s", cudaGetErrorString(e));
+    return BA_ERR_CUDA;
+  }
+  if (h == 2) {
+    dense_error("ba_selftest_wait_timeout: the wait gave up after %.3f ms, as intended", timeout_ms);
+    return BA_ERR_TIMEOUT;
+  }
+  dense_error("ba_selftest_wait_timeout: unexpected outcome %d", h);
+  return BA_ERR_STATE;
+}
+
 }  // extern "C"
