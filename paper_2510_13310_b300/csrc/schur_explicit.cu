@@ -412,6 +412,15 @@ __device__ bool warp0_tagged_allreduce(unsigned long long* slots, int G, int bid
   return __all_sync(0xffffffffu, ok);
 }
 
+// alpha = (r, z) / (p, q) and beta = (r', z') / (r, z) from the FP64 dot products:
+// the FP32 path needs them to FP32 accuracy only (x, r, p are FP32 vectors), and an
+// FP64 division is a long dependent chain on B300; the FP64 path divides in FP64.
+template <typename T>
+__device__ __forceinline__ double spcg_ratio(double num, double den) {
+  if constexpr (sizeof(T) == 4) return (double)__fdiv_rn((float)num, (float)den);
+  else return num / den;
+}
+
 template <typename T>
 __host__ __device__ inline int spcg_row_stride(int n) {
   return sizeof(T) == 4 ? (n + 3) & ~3 : n;  // FP32 rows padded for 16-byte vector loads
@@ -588,7 +597,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
       if (lane == 0) {
         const double pq = tot[0];
         const bool fine = ok && pq > 0.0 && isfinite(pq);
-        sb[3] = fine ? rz / pq : 0.0;
+        sb[3] = fine ? spcg_ratio<T>(rz, pq) : 0.0;
         sb[7] = fine ? 1.0 : 0.0;
         if (!ok) atomicOr(a.err, 1);
         else if (!fine && bid == 0) atomicOr(a.err, 2);
@@ -600,8 +609,13 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     if (sb[7] == 0.0) break;
     const double alpha = sb[3];
     for (int q = tid; q < ne; q += blockDim.x) {
-      xo[q] = (T)((double)xo[q] + alpha * (double)ps[e0 + q]);
-      ro[q] = (T)((double)ro[q] - alpha * (double)qo[q]);
+      if constexpr (sizeof(T) == 4) {
+        xo[q] = fmaf((float)alpha, ps[e0 + q], xo[q]);
+        ro[q] = fmaf(-(float)alpha, qo[q], ro[q]);
+      } else {
+        xo[q] = (T)((double)xo[q] + alpha * (double)ps[e0 + q]);
+        ro[q] = (T)((double)ro[q] - alpha * (double)qo[q]);
+      }
     }
     __syncthreads();
     for (int q = tid; q < ne; q += blockDim.x) {
@@ -620,7 +634,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
       if (lane == 0) {
         sb[4] = tot[0];
         sb[5] = tot[0] <= stop_rr ? 1.0 : 0.0;
-        sb[6] = rz != 0.0 ? tot[1] / rz : 0.0;
+        sb[6] = rz != 0.0 ? spcg_ratio<T>(tot[1], rz) : 0.0;
         sb[0] = tot[1];
         sb[7] = ok ? 1.0 : 0.0;
         if (!ok) atomicOr(a.err, 1);
