@@ -108,7 +108,11 @@ void ba_default_options(ba_options* o);
  * Checks index ranges, finiteness and duplicate (camera, point) pairs on the
  * host (BA_ERR_INVALID_ARG).  Limits: N < 2^31, at most 256 observations per
  * point.  stream: a cudaStream_t (NULL = legacy default stream).  The problem
- * lives on the device current at the call. */
+ * lives on the device current at the call.  Input arrays may be host or device
+ * memory (host arrays are read in place); the call returns with the device idle.
+ * The observation orderings are built on host threads (the hardware threads, at
+ * most 32; the environment variable BA_HOST_THREADS overrides); the result does
+ * not depend on the thread count. */
 ba_status ba_create(const ba_options* opts, void* stream, int64_t n_cams, const double* cams,
                     int64_t n_pts, const double* pts, int64_t n_obs, const int32_t* obs_cam,
                     const int32_t* obs_pt, const double* obs_uv, const double* depth,

@@ -5,11 +5,16 @@
 // the accept decision of Sec. 3.3).  Every array operation of steps (a)-(e)
 // runs in the kernels of kernels.cu.
 #include <algorithm>
+#include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ba_b300.h"
@@ -117,8 +122,12 @@ struct ba_problem {
   int n_covis_runs = 0;
   bool form_lanes = false;      // one lane per co-visibility run (many short runs)
   double* dscale = nullptr;
-  int spcg_grid = 0, spcg_own_max = 1, spcg_rows_in_smem = 0, bs_grid = 1;
+  int spcg_grid = 0, spcg_rows_in_smem = 0, spcg_vecs_in_smem = 0, bs_grid = 1;
+  void* spcg_scratch = nullptr;   // per-block PCG vectors when they do not fit in shared memory
+  size_t spcg_scratch_stride = 0;
   size_t spcg_smem = 0;
+  unsigned long long* spcg_words = nullptr;  // exchange words of the explicit PCG
+  unsigned spcg_tag = 1;                     // next launch's first iteration tag
   size_t pcg_smem = 0;
 
   // LM bookkeeping
@@ -162,13 +171,99 @@ ba_status dalloc_bytes(ba_problem* pb, void** p, size_t bytes) {
 size_t rsz(const ba_problem* pb) { return pb->fp64 ? sizeof(double) : sizeof(float); }
 
 // Stable counting sort of idx by key (keys in [0, nkeys)).
-void counting_sort(const std::vector<int>& idx_in, const int32_t* key, int nkeys,
-                   std::vector<int>& idx_out) {
-  std::vector<int64_t> cnt((size_t)nkeys + 1, 0);
-  for (int k : idx_in) cnt[key[k] + 1]++;
-  for (int i = 0; i < nkeys; ++i) cnt[i + 1] += cnt[i];
-  idx_out.resize(idx_in.size());
-  for (int k : idx_in) idx_out[cnt[key[k]]++] = k;
+// Host worker threads of the preprocessing in ba_create: the hardware threads,
+// at most 32, or BA_HOST_THREADS when set.  Every parallel loop writes outputs
+// fixed by its indices alone, so results depend neither on the number of
+// threads nor on their timing.
+int host_threads() {
+  if (const char* env = std::getenv("BA_HOST_THREADS")) {
+    const int v = std::atoi(env);
+    if (v > 0) return std::min(v, 256);
+  }
+  const unsigned h = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(h ? h : 1u, 32u));
+}
+
+// f(t) for t = 0 .. nt-1, piece 0 on the calling thread; a piece whose thread
+// cannot be started runs on the calling thread afterwards
+template <class F>
+void run_pieces(int nt, F&& f) {
+  std::vector<std::thread> th;
+  std::vector<int> inline_pieces;
+  th.reserve(nt > 1 ? nt - 1 : 0);
+  for (int t = 1; t < nt; ++t) {
+    try {
+      th.emplace_back([&f, t] { f(t); });
+    } catch (...) {
+      inline_pieces.push_back(t);
+    }
+  }
+  if (nt > 0) f(0);
+  for (int t : inline_pieces) f(t);
+  for (auto& x : th) x.join();
+}
+
+// f(t, begin, end) over contiguous pieces [n t / nt, n (t+1) / nt) of [0, n),
+// at least `grain` indices per piece
+template <class F>
+void parallel_for(int64_t n, int64_t grain, F&& f) {
+  if (n <= 0) return;
+  const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n / std::max<int64_t>(1, grain)));
+  run_pieces(nt, [&](int t) { f(t, n * t / nt, n * (t + 1) / nt); });
+}
+
+// f(i) for i in [0, n), items handed out one at a time (uneven item costs)
+template <class F>
+void parallel_items(int64_t n, F&& f) {
+  if (n <= 0) return;
+  std::atomic<int64_t> next{0};
+  run_pieces((int)std::min<int64_t>(host_threads(), n), [&](int) {
+    for (int64_t i; (i = next.fetch_add(1, std::memory_order_relaxed)) < n;) f(i);
+  });
+}
+
+// true when every value is finite
+bool all_finite(const double* v, int64_t n) {
+  std::atomic<bool> ok{true};
+  parallel_for(n, 1 << 18, [&](int, int64_t b, int64_t e) {
+    bool good = true;
+    for (int64_t i = b; i < e; ++i) good &= std::isfinite(v[i]);
+    if (!good) ok.store(false, std::memory_order_relaxed);
+  });
+  return ok.load();
+}
+
+// device-resident (device or managed) memory; anything else is read on the host
+bool on_device(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// RAII device scratch of ba_create (freed once the device is idle)
+struct DevScratch {
+  void* p = nullptr;
+  ~DevScratch() {
+    if (p) {
+      cudaDeviceSynchronize();
+      cudaFree(p);
+    }
+  }
+};
+
+// the input array at src (n elements) readable on the host: src itself, or a
+// copy in store when src is device memory
+template <typename T>
+ba_status host_view(const T* src, size_t n, bool dev, std::vector<T>& store, const T** out) {
+  *out = src;
+  if (!dev || n == 0) return BA_OK;
+  store.resize(n);
+  CU(cudaMemcpy(store.data(), src, sizeof(T) * n, cudaMemcpyDeviceToHost));
+  *out = store.data();
+  return BA_OK;
 }
 
 bool finite_opts(const ba_options* o) {
@@ -179,14 +274,6 @@ bool finite_opts(const ba_options* o) {
          std::isfinite(o->pcg_rel_tol) && o->pcg_rel_tol > 0 && o->pcg_max_iters > 0 &&
          o->img_w > 0 && o->img_h > 0 && o->min_cam_obs >= 0 && o->min_pt_obs >= 0 &&
          o->extract_every >= 0 && (o->precision == BA_FP64 || o->precision == BA_FP32);
-}
-
-template <typename T>
-ba_status upload_converted(ba_problem* pb, void** dst, const std::vector<double>& src) {
-  std::vector<T> tmp(src.begin(), src.end());
-  ST(dalloc_bytes(pb, dst, sizeof(T) * tmp.size()));
-  if (!tmp.empty()) CU(cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice));
-  return BA_OK;
 }
 
 ba_status sync(ba_problem* pb) {
@@ -355,21 +442,33 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     a.b = (const T*)pb->bvec;
     a.Cf = Cf;
     a.n = 9 * Cf;
-    a.own_max = pb->spcg_own_max;
     a.rows_in_smem = pb->spcg_rows_in_smem;
+    a.vecs_in_smem = pb->spcg_vecs_in_smem;
+    a.scratch = (T*)pb->spcg_scratch;
+    a.scratch_stride = pb->spcg_scratch_stride;
     a.x = (T*)pb->x;
-    a.z = (T*)pb->z;
-    a.dots = pb->dots;
-    a.bar = pb->bar;
+    a.words = pb->spcg_words;
     a.err = pb->err;
     a.sc = pb->sc;
     a.tol = pb->opt.pcg_rel_tol;
     a.max_iters = pb->opt.pcg_max_iters;
     a.timeout_ns = 2000000000LL;
-    size_t smem = spcg_smem_bytes<T>(a.n, a.own_max, a.rows_in_smem);
-    int grid = std::min(pb->spcg_grid, Cf);
-    // reduction slots start untagged (tag 0; the first reduction uses tag 1)
-    CU(cudaMemsetAsync(pb->dots, 0, sizeof(double) * 2 * 4 * (size_t)grid, pb->stream));
+    const int grid = std::max(1, std::min(pb->spcg_grid, (a.n + 7) / 8));
+    const size_t smem = spcg_smem_bytes<T>(a.n, (a.n + grid - 1) / grid, a.rows_in_smem, a.vecs_in_smem, Cf);
+    if (smem > pb->spcg_smem) {
+      set_error("explicit PCG launch needs %zu B of shared memory (planned %zu)", smem, pb->spcg_smem);
+      return BA_ERR_INVALID_ARG;
+    }
+    // fresh tags for this launch; on wrap-around the words are cleared and tags restart at 1
+    const unsigned span = (unsigned)a.max_iters + 2u;
+    if (pb->spcg_tag == 0 || pb->spcg_tag > 0xFFFFFFFFu - span) {
+      CU(cudaMemsetAsync(pb->spcg_words, 0,
+                         sizeof(unsigned long long) * 2 * 9 * (size_t)pb->C * spcg_words_per_value(pb->fp64),
+                         pb->stream));
+      pb->spcg_tag = 1;
+    }
+    a.tag_base = pb->spcg_tag;
+    pb->spcg_tag += span;
     CU(cudaEventRecord(pb->evk[0], pb->stream));
     LAUNCH(1, launch_spcg<T>(a, grid, smem, pb->stream));
     CU(cudaEventRecord(pb->evk[1], pb->stream));
@@ -632,44 +731,65 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   CU(cudaGetDevice(&pb->device));
   CU(cudaDeviceGetAttribute(&pb->num_sms, cudaDevAttrMultiProcessorCount, pb->device));
 
-  // ---- host copies of the inputs (host or device pointers)
-  std::vector<double> h_cams((size_t)C * 9), h_pts((size_t)P * 3), h_uv((size_t)N * 2), h_depth(N);
-  std::vector<int32_t> h_oc(N), h_op(N);
-  if (C) CU(cudaMemcpy(h_cams.data(), cams, sizeof(double) * h_cams.size(), cudaMemcpyDefault));
-  if (P) CU(cudaMemcpy(h_pts.data(), pts, sizeof(double) * h_pts.size(), cudaMemcpyDefault));
-  if (N) {
-    CU(cudaMemcpy(h_oc.data(), obs_cam, sizeof(int32_t) * N, cudaMemcpyDefault));
-    CU(cudaMemcpy(h_op.data(), obs_pt, sizeof(int32_t) * N, cudaMemcpyDefault));
-    CU(cudaMemcpy(h_uv.data(), obs_uv, sizeof(double) * 2 * (size_t)N, cudaMemcpyDefault));
-    CU(cudaMemcpy(h_depth.data(), depth, sizeof(double) * N, cudaMemcpyDefault));
-  }
+  // ---- host views of the inputs: host memory is read in place, device memory
+  // is copied (the orderings are built on the host)
+  const bool dev_oc = N && on_device(obs_cam), dev_op = N && on_device(obs_pt);
+  const bool dev_uv = N && on_device(obs_uv), dev_depth = N && on_device(depth);
+  // inputs written by device work on any stream are complete before they are read
+  if (dev_oc || dev_op || dev_uv || dev_depth || (C && on_device(cams)) || (P && on_device(pts)))
+    CU(cudaDeviceSynchronize());
+  std::vector<double> c_cams, c_pts, c_uv;
+  std::vector<int32_t> c_oc, c_op;
+  const double *h_cams = cams, *h_pts = pts, *h_uv = obs_uv;
+  const int32_t *h_oc = obs_cam, *h_op = obs_pt;
+  ST(host_view(cams, (size_t)C * 9, C && on_device(cams), c_cams, &h_cams));
+  ST(host_view(pts, (size_t)P * 3, P && on_device(pts), c_pts, &h_pts));
+  ST(host_view(obs_cam, (size_t)N, dev_oc, c_oc, &h_oc));
+  ST(host_view(obs_pt, (size_t)N, dev_op, c_op, &h_op));
+  ST(host_view(obs_uv, (size_t)N * 2, dev_uv, c_uv, &h_uv));
   // ---- validation
-  for (double v : h_cams)
-    if (!std::isfinite(v)) { set_error("non-finite camera parameter"); return BA_ERR_INVALID_ARG; }
-  for (double v : h_pts)
-    if (!std::isfinite(v)) { set_error("non-finite point"); return BA_ERR_INVALID_ARG; }
-  for (double v : h_uv)
-    if (!std::isfinite(v)) { set_error("non-finite observation"); return BA_ERR_INVALID_ARG; }
-  for (int k = 0; k < N; ++k) {
-    if (h_oc[k] < 0 || h_oc[k] >= C || h_op[k] < 0 || h_op[k] >= P) {
-      set_error("observation %d has an index out of range", k);
+  if (!all_finite(h_cams, (int64_t)C * 9)) { set_error("non-finite camera parameter"); return BA_ERR_INVALID_ARG; }
+  if (!all_finite(h_pts, (int64_t)P * 3)) { set_error("non-finite point"); return BA_ERR_INVALID_ARG; }
+  if (!all_finite(h_uv, (int64_t)N * 2)) { set_error("non-finite observation"); return BA_ERR_INVALID_ARG; }
+  {
+    std::atomic<int> first_bad{INT_MAX};
+    parallel_for(N, 1 << 16, [&](int, int64_t b, int64_t e) {
+      for (int64_t k = b; k < e; ++k)
+        if (h_oc[k] < 0 || h_oc[k] >= C || h_op[k] < 0 || h_op[k] >= P) {
+          int cur = first_bad.load();
+          while ((int)k < cur && !first_bad.compare_exchange_weak(cur, (int)k)) {
+          }
+          break;
+        }
+    });
+    if (first_bad.load() != INT_MAX) {
+      set_error("observation %d has an index out of range", first_bad.load());
       return BA_ERR_INVALID_ARG;
     }
   }
   {
-    uint64_t h = 1469598103934665603ull;
-    auto mix = [&](int32_t v) {
+    // FNV-1a over the sizes and 64K-observation chunk digests (each FNV-1a over
+    // its (camera, point) pairs): identifies the observation structure
+    constexpr int64_t kHashChunk = 1 << 16;
+    auto fnv = [](uint64_t h, int32_t v) {
       for (int b = 0; b < 4; ++b) {
         h ^= (uint64_t)((uint32_t)v >> (8 * b) & 0xFFu);
         h *= 1099511628211ull;
       }
+      return h;
     };
-    mix(C);
-    mix(P);
-    for (int k = 0; k < N; ++k) {
-      mix(h_oc[k]);
-      mix(h_op[k]);
-    }
+    const int64_t nch = ((int64_t)N + kHashChunk - 1) / kHashChunk;
+    std::vector<uint64_t> dig((size_t)nch);
+    parallel_for(nch, 1, [&](int, int64_t b, int64_t e) {
+      for (int64_t c = b; c < e; ++c) {
+        uint64_t h = 1469598103934665603ull;
+        for (int64_t k = c * kHashChunk; k < std::min<int64_t>(N, (c + 1) * kHashChunk); ++k)
+          h = fnv(fnv(h, h_oc[k]), h_op[k]);
+        dig[c] = h;
+      }
+    });
+    uint64_t h = fnv(fnv(1469598103934665603ull, C), P);
+    for (uint64_t d : dig) h = fnv(fnv(h, (int32_t)(uint32_t)d), (int32_t)(uint32_t)(d >> 32));
     pb->obs_hash = h;
   }
   std::vector<uint8_t> h_fixed((size_t)C, 0);
@@ -678,31 +798,77 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     h_fixed[f] = 1;
   }
   // ---- point order (by point, then camera) and camera order (by camera, then point)
-  std::vector<int> ident(N), tmp, po, co;
-  for (int k = 0; k < N; ++k) ident[k] = k;
-  counting_sort(ident, h_oc.data(), C, tmp);
-  counting_sort(tmp, h_op.data(), P, po);
-  counting_sort(ident, h_op.data(), P, tmp);
-  counting_sort(tmp, h_oc.data(), C, co);
-  for (int i = 1; i < N; ++i)
-    if (h_op[po[i]] == h_op[po[i - 1]] && h_oc[po[i]] == h_oc[po[i - 1]]) {
-      set_error("duplicate observation of point %d in camera %d", h_op[po[i]], h_oc[po[i]]);
-      return BA_ERR_INVALID_ARG;
-    }
-  std::vector<int> pos_in_po(N);
-  for (int i = 0; i < N; ++i) pos_in_po[po[i]] = i;
   std::vector<int> pt_off((size_t)P + 1, 0), cam_off((size_t)C + 1, 0);
-  for (int k = 0; k < N; ++k) {
-    pt_off[h_op[k] + 1]++;
-    cam_off[h_oc[k] + 1]++;
-  }
+  parallel_for(N, 1 << 16, [&](int, int64_t b, int64_t e) {
+    for (int64_t k = b; k < e; ++k) __atomic_fetch_add(&pt_off[h_op[k] + 1], 1, __ATOMIC_RELAXED);
+  });
   for (int i = 0; i < P; ++i) pt_off[i + 1] += pt_off[i];
-  for (int i = 0; i < C; ++i) cam_off[i + 1] += cam_off[i];
   for (int p = 0; p < P; ++p)
     if (pt_off[p + 1] - pt_off[p] > kTileObs) {
       set_error("point %d has %d observations (limit %d)", p, pt_off[p + 1] - pt_off[p], kTileObs);
       return BA_ERR_INVALID_ARG;
     }
+  // po: observations grouped by point (in any order), then each point's
+  // observations sorted by (camera, input index), a unique key
+  std::vector<int> po((size_t)N), co((size_t)N);
+  {
+    std::vector<int> fill(pt_off.begin(), pt_off.end() - 1);
+    parallel_for(N, 1 << 16, [&](int, int64_t b, int64_t e) {
+      for (int64_t k = b; k < e; ++k) po[__atomic_fetch_add(&fill[h_op[k]], 1, __ATOMIC_RELAXED)] = (int)k;
+    });
+  }
+  std::atomic<int> first_dup{INT_MAX};
+  parallel_for(P, 1 << 12, [&](int, int64_t b, int64_t e) {
+    for (int64_t p = b; p < e; ++p) {
+      int* seg = po.data() + pt_off[p];
+      const int n = pt_off[p + 1] - pt_off[p];
+      for (int i = 1; i < n; ++i) {  // insertion sort: at most kTileObs entries
+        const int k = seg[i];
+        const int64_t key = (int64_t)h_oc[k] << 32 | (uint32_t)k;
+        int j = i - 1;
+        for (; j >= 0 && ((int64_t)h_oc[seg[j]] << 32 | (uint32_t)seg[j]) > key; --j) seg[j + 1] = seg[j];
+        seg[j + 1] = k;
+      }
+      for (int i = 1; i < n; ++i)
+        if (h_oc[seg[i]] == h_oc[seg[i - 1]]) {
+          int cur = first_dup.load(), at = pt_off[p] + i;
+          while (at < cur && !first_dup.compare_exchange_weak(cur, at)) {
+          }
+          break;
+        }
+    }
+  });
+  if (first_dup.load() != INT_MAX) {
+    const int i = first_dup.load();
+    set_error("duplicate observation of point %d in camera %d", h_op[po[i]], h_oc[po[i]]);
+    return BA_ERR_INVALID_ARG;
+  }
+  // co: stable counting sort of po by camera (per-piece camera histograms)
+  {
+    const int nt = (int)std::max<int64_t>(
+        1, std::min<int64_t>({(int64_t)host_threads(), (int64_t)N / (1 << 16) + 1,
+                              (int64_t)(1 << 24) / std::max(1, C)}));
+    std::vector<int> hist((size_t)nt * C, 0);
+    auto lo = [&](int t) { return (int64_t)N * t / nt; };
+    run_pieces(nt, [&](int t) {
+      int* hc = hist.data() + (size_t)t * C;
+      for (int64_t i = lo(t); i < lo(t + 1); ++i) hc[h_oc[po[i]]]++;
+    });
+    int run = 0;
+    for (int c = 0; c < C; ++c) {
+      cam_off[c] = run;
+      for (int t = 0; t < nt; ++t) {
+        const int v = hist[(size_t)t * C + c];
+        hist[(size_t)t * C + c] = run;
+        run += v;
+      }
+    }
+    cam_off[C] = run;
+    run_pieces(nt, [&](int t) {
+      int* hc = hist.data() + (size_t)t * C;
+      for (int64_t i = lo(t); i < lo(t + 1); ++i) co[hc[h_oc[po[i]]]++] = po[i];
+    });
+  }
   // Warp ranges: consecutive whole points with at most 32 observations together,
   // or one point with more.  Tiles: up to one warp range per PCG warp, at most
   // kTileObs observations and kTileObs points.
@@ -744,50 +910,71 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   // Per tile: its metadata record (camera of each observation, point offsets,
   // runs of equal cameras once the tile's observations are sorted by camera,
   // warp-range offsets, positions in camera order, local point of each
-  // observation) and its descriptor.
-  std::vector<TileDesc> descs((size_t)pb->n_tiles);
-  std::vector<unsigned char> meta;
-  std::vector<int> po_wrow((size_t)N);
-  for (int t = 0; t < pb->n_tiles; ++t) {
-    int r0 = tile_wr[t], r1 = tile_wr[t + 1];
-    int pbeg = wr_pt[r0], pend = wr_pt[r1];
-    int ob = pt_off[pbeg], oe = pt_off[pend];
-    int nobs = oe - ob, npts = pend - pbeg;
-    std::vector<int> cams_t(nobs), loc(nobs), poff(npts + 1), wr(r1 - r0 + 1);
-    std::vector<uint8_t> lid(nobs);
-    for (int i = 0; i < nobs; ++i) {
-      cams_t[i] = h_oc[po[ob + i]];
-      loc[i] = i;
-      po_wrow[ob + i] = ob + i;
-    }
-    for (int j = 0; j <= npts; ++j) poff[j] = pt_off[pbeg + j] - ob;
-    for (int j = 0; j < npts; ++j)
-      for (int i = poff[j]; i < poff[j + 1]; ++i) lid[i] = (uint8_t)j;
-    for (int r = r0; r <= r1; ++r) wr[r - r0] = pt_off[wr_pt[r]] - ob;
-    std::stable_sort(loc.begin(), loc.end(), [&](int x, int y) { return cams_t[x] < cams_t[y]; });
-    std::vector<unsigned> runs;
-    std::vector<uint8_t> cperm(nobs);
-    for (int j = 0; j < nobs; ++j) {
-      cperm[j] = (uint8_t)loc[j];
-      if (j == 0 || cams_t[loc[j]] != cams_t[loc[j - 1]])
-        runs.push_back(((unsigned)cams_t[loc[j]] << 8) | (unsigned)j);
-    }
+  // observation) and its descriptor.  Pass 1 sorts each tile's observations by
+  // (camera, local index) and counts the runs; the record offsets follow by a
+  // prefix sum; pass 2 writes the records.
+  const int n_tiles = pb->n_tiles;
+  std::vector<TileDesc> descs((size_t)n_tiles);
+  for (int t = 0; t < n_tiles; ++t) {
+    const int pbeg = wr_pt[tile_wr[t]], pend = wr_pt[tile_wr[t + 1]];
     TileDesc d{};
     d.g_row = pb->g_rows;
-    pb->g_rows += (nobs + 3) & ~3;
-    d.w_row = ob;
-    d.n_obs = nobs;
+    d.w_row = d.obs_begin = pt_off[pbeg];
+    d.n_obs = pt_off[pend] - pt_off[pbeg];
     d.pt_begin = pbeg;
-    d.n_pts = npts;
-    d.meta_off = (int)meta.size();
-    d.n_runs = (int)runs.size();
-    d.obs_begin = ob;
+    d.n_pts = pend - pbeg;
+    pb->g_rows += (d.n_obs + 3) & ~3;
     descs[t] = d;
-    size_t mb = (size_t)meta_bytes_of(nobs, npts, d.n_runs);
-    meta.resize(meta.size() + mb);
-    build_tile_meta(nobs, npts, d.n_runs, r1 - r0, cams_t.data(), poff.data(), runs.data(), wr.data(),
-                    cperm.data(), lid.data(), meta.data() + d.meta_off);
   }
+  std::vector<uint32_t> skey((size_t)N);  // camera << 8 | tile-local index, sorted per tile
+  parallel_for(n_tiles, 16, [&](int, int64_t b, int64_t e) {
+    for (int64_t t = b; t < e; ++t) {
+      TileDesc& d = descs[t];
+      uint32_t* key = skey.data() + d.obs_begin;
+      for (int i = 0; i < d.n_obs; ++i) key[i] = (uint32_t)h_oc[po[d.obs_begin + i]] << 8 | (uint32_t)i;
+      std::sort(key, key + d.n_obs);
+      int runs = 0;
+      for (int j = 0; j < d.n_obs; ++j) runs += (j == 0 || (key[j] >> 8) != (key[j - 1] >> 8));
+      d.n_runs = runs;
+    }
+  });
+  size_t meta_total = 0;
+  for (int t = 0; t < n_tiles; ++t) {
+    descs[t].meta_off = (int)meta_total;
+    meta_total += (size_t)meta_bytes_of(descs[t].n_obs, descs[t].n_pts, descs[t].n_runs);
+  }
+  if (meta_total >= (size_t)INT_MAX) {
+    set_error("tile metadata too large");
+    return BA_ERR_INVALID_ARG;
+  }
+  std::vector<unsigned char> meta(meta_total);
+  parallel_for(n_tiles, 16, [&](int, int64_t b, int64_t e) {
+    std::vector<int> cams_t, poff, wr;
+    std::vector<unsigned> runs;
+    std::vector<uint8_t> cperm, lid;
+    for (int64_t t = b; t < e; ++t) {
+      const TileDesc& d = descs[t];
+      const int r0 = tile_wr[t], r1 = tile_wr[t + 1], ob = d.obs_begin, nobs = d.n_obs, npts = d.n_pts;
+      cams_t.resize(nobs);
+      poff.resize(npts + 1);
+      wr.resize(r1 - r0 + 1);
+      cperm.resize(nobs);
+      lid.resize(nobs);
+      runs.clear();
+      for (int i = 0; i < nobs; ++i) cams_t[i] = h_oc[po[ob + i]];
+      for (int j = 0; j <= npts; ++j) poff[j] = pt_off[d.pt_begin + j] - ob;
+      for (int j = 0; j < npts; ++j)
+        for (int i = poff[j]; i < poff[j + 1]; ++i) lid[i] = (uint8_t)j;
+      for (int r = r0; r <= r1; ++r) wr[r - r0] = pt_off[wr_pt[r]] - ob;
+      const uint32_t* key = skey.data() + ob;
+      for (int j = 0; j < nobs; ++j) {
+        cperm[j] = (uint8_t)(key[j] & 0xFFu);
+        if (j == 0 || (key[j] >> 8) != (key[j - 1] >> 8)) runs.push_back((key[j] >> 8) << 8 | (unsigned)j);
+      }
+      build_tile_meta(nobs, npts, d.n_runs, r1 - r0, cams_t.data(), poff.data(), runs.data(), wr.data(),
+                      cperm.data(), lid.data(), meta.data() + d.meta_off);
+    }
+  });
   pb->w_rows = N;
   // chunks: pieces of one camera's observations
   std::vector<int> chunk_obs{0}, chunk_cam, cam_chunk((size_t)C + 1, 0);
@@ -800,69 +987,81 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   }
   pb->n_chunks = (int)chunk_cam.size();
 
-  // ---- per-observation arrays in both orders
-  std::vector<int> h_po_cam(N), h_po_pt(N), h_co_pt(N), h_co_po(N);
-  std::vector<double> h_po_uv((size_t)2 * N), h_po_tau(N), h_co_uv((size_t)2 * N), h_co_tau(N);
-  auto tau_of = [&](int k) {
-    double d = h_depth[k];
-    return (d > 0.0 && std::isfinite(d)) ? 1.0 / d : 0.0;
-  };
-  for (int i = 0; i < N; ++i) {
-    int k = po[i];
-    h_po_cam[i] = h_oc[k];
-    h_po_pt[i] = h_op[k];
-    h_po_uv[2 * i] = h_uv[2 * (size_t)k];
-    h_po_uv[2 * i + 1] = h_uv[2 * (size_t)k + 1];
-    h_po_tau[i] = tau_of(k);
-    int kc = co[i];
-    h_co_pt[i] = h_op[kc];
-    h_co_po[i] = pos_in_po[kc];
-    h_co_uv[2 * i] = h_uv[2 * (size_t)kc];
-    h_co_uv[2 * i + 1] = h_uv[2 * (size_t)kc + 1];
-    h_co_tau[i] = tau_of(kc);
-  }
-
   // ---- device buffers
   auto up_int = [&](int** d, const std::vector<int>& h) -> ba_status {
     ST(dalloc(pb, d, h.size()));
     if (!h.empty()) CU(cudaMemcpy(*d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice));
     return BA_OK;
   };
-  auto up_dbl = [&](double** d, const std::vector<double>& h) -> ba_status {
-    ST(dalloc(pb, d, h.size()));
-    if (!h.empty()) CU(cudaMemcpy(*d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
-    return BA_OK;
-  };
-  ST(up_int(&pb->po_cam, h_po_cam));
-  ST(up_int(&pb->po_pt, h_po_pt));
   ST(up_int(&pb->po_orig, po));
   ST(up_int(&pb->pt_off, pt_off));
-  ST(up_int(&pb->co_pt, h_co_pt));
-  ST(up_int(&pb->co_po, h_co_po));
   ST(up_int(&pb->chunk_obs, chunk_obs));
   ST(up_int(&pb->chunk_cam, chunk_cam));
   ST(up_int(&pb->cam_chunk, cam_chunk));
-  ST(up_int(&pb->po_wrow, po_wrow));
   ST(dalloc(pb, &pb->descs, descs.size()));
   if (!descs.empty())
     CU(cudaMemcpy(pb->descs, descs.data(), sizeof(TileDesc) * descs.size(), cudaMemcpyHostToDevice));
   ST(dalloc(pb, &pb->meta, meta.size()));
   if (!meta.empty()) CU(cudaMemcpy(pb->meta, meta.data(), meta.size(), cudaMemcpyHostToDevice));
-  ST(up_dbl(&pb->po_uv64, h_po_uv));
-  ST(up_dbl(&pb->po_tau64, h_po_tau));
+  // per-observation arrays in both orders, gathered on the device from the
+  // caller's arrays (device inputs in place, host inputs through one scratch)
+  ST(dalloc(pb, &pb->po_cam, (size_t)N));
+  ST(dalloc(pb, &pb->po_pt, (size_t)N));
+  ST(dalloc(pb, &pb->po_wrow, (size_t)N));
+  ST(dalloc(pb, &pb->co_pt, (size_t)N));
+  ST(dalloc(pb, &pb->co_po, (size_t)N));
+  ST(dalloc(pb, &pb->po_uv64, (size_t)2 * N));
+  ST(dalloc(pb, &pb->po_tau64, (size_t)N));
+  const size_t Rw = pb->fp64 ? sizeof(double) : sizeof(float);
   if (pb->fp64) {
     pb->po_uvw = pb->po_uv64;
     pb->po_tauw = pb->po_tau64;
-    double *cu = nullptr, *ct = nullptr;
-    ST(up_dbl(&cu, h_co_uv));
-    ST(up_dbl(&ct, h_co_tau));
-    pb->co_uvw = cu;
-    pb->co_tauw = ct;
   } else {
-    ST(upload_converted<float>(pb, &pb->po_uvw, h_po_uv));
-    ST(upload_converted<float>(pb, &pb->po_tauw, h_po_tau));
-    ST(upload_converted<float>(pb, &pb->co_uvw, h_co_uv));
-    ST(upload_converted<float>(pb, &pb->co_tauw, h_co_tau));
+    ST(dalloc_bytes(pb, &pb->po_uvw, Rw * 2 * (size_t)N));
+    ST(dalloc_bytes(pb, &pb->po_tauw, Rw * (size_t)N));
+  }
+  ST(dalloc_bytes(pb, &pb->co_uvw, Rw * 2 * (size_t)N));
+  ST(dalloc_bytes(pb, &pb->co_tauw, Rw * (size_t)N));
+  DevScratch scratch;
+  if (N) {
+    const size_t n = (size_t)N;
+    CU(cudaMalloc(&scratch.p, 40 * n));
+    char* base = (char*)scratch.p;
+    const double* d_uv = obs_uv;
+    const double* d_depth = depth;
+    const int32_t* d_oc = obs_cam;
+    const int32_t* d_op = obs_pt;
+    if (!dev_uv) {
+      CU(cudaMemcpyAsync(base, obs_uv, 16 * n, cudaMemcpyHostToDevice, pb->stream));
+      d_uv = (const double*)base;
+    }
+    if (!dev_depth) {
+      CU(cudaMemcpyAsync(base + 16 * n, depth, 8 * n, cudaMemcpyHostToDevice, pb->stream));
+      d_depth = (const double*)(base + 16 * n);
+    }
+    if (!dev_oc) {
+      CU(cudaMemcpyAsync(base + 24 * n, obs_cam, 4 * n, cudaMemcpyHostToDevice, pb->stream));
+      d_oc = (const int32_t*)(base + 24 * n);
+    }
+    if (!dev_op) {
+      CU(cudaMemcpyAsync(base + 28 * n, obs_pt, 4 * n, cudaMemcpyHostToDevice, pb->stream));
+      d_op = (const int32_t*)(base + 28 * n);
+    }
+    // the synchronous uploads above may still be in flight when they return
+    CU(cudaDeviceSynchronize());
+    int* d_co = (int*)(base + 32 * n);
+    int* d_pos = (int*)(base + 36 * n);
+    CU(cudaMemcpyAsync(d_co, co.data(), 4 * n, cudaMemcpyHostToDevice, pb->stream));
+    if (pb->fp64)
+      LAUNCH(2, launch_obs_layout<double>(N, d_oc, d_op, d_uv, d_depth, pb->po_orig, d_co, d_pos, pb->po_cam, pb->po_pt,
+                                   pb->po_wrow, pb->po_uv64, pb->po_tau64, nullptr, nullptr, pb->co_pt,
+                                   pb->co_po, (double*)pb->co_uvw, (double*)pb->co_tauw, pb->stream));
+    else
+      LAUNCH(2, launch_obs_layout<float>(N, d_oc, d_op, d_uv, d_depth, pb->po_orig, d_co, d_pos, pb->po_cam, pb->po_pt,
+                                  pb->po_wrow, pb->po_uv64, pb->po_tau64, (float*)pb->po_uvw,
+                                  (float*)pb->po_tauw, pb->co_pt, pb->co_po, (float*)pb->co_uvw,
+                                  (float*)pb->co_tauw, pb->stream));
+    CU(cudaStreamSynchronize(pb->stream));
   }
   ST(dalloc(pb, &pb->cam_fixed, (size_t)C));
   if (C) CU(cudaMemcpy(pb->cam_fixed, h_fixed.data(), (size_t)C, cudaMemcpyHostToDevice));
@@ -914,8 +1113,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     CU(cudaMemset(pb->ptsw[s], 0, R * ((size_t)P + 2) * 4));
     ST(dalloc(pb, &pb->bits[s], (size_t)N));
   }
-  if (C) CU(cudaMemcpy(pb->cams64[0], h_cams.data(), sizeof(double) * h_cams.size(), cudaMemcpyHostToDevice));
-  if (P) CU(cudaMemcpy(pb->pts64[0], h_pts.data(), sizeof(double) * h_pts.size(), cudaMemcpyHostToDevice));
+  if (C) CU(cudaMemcpy(pb->cams64[0], cams, sizeof(double) * 9 * (size_t)C, cudaMemcpyDefault));
+  if (P) CU(cudaMemcpy(pb->pts64[0], pts, sizeof(double) * 3 * (size_t)P, cudaMemcpyDefault));
   ST(dalloc(pb, &pb->alive, (size_t)N));
   ST(dalloc(pb, &pb->valid, (size_t)N));
   ST(dalloc(pb, &pb->obs_act, (size_t)N));
@@ -1024,8 +1223,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   // at most two blocks per SM: fewer blocks means fewer partial vectors to reduce
   pb->pcg_grid = std::max(1, std::min(std::min(per_sm, 2) * pb->num_sms, std::max(1, pb->n_tiles)));
   ST(dalloc_bytes(pb, &pb->partials, R * (size_t)pb->pcg_grid * std::max(1, n_max)));
-  // dot-product slots of both PCG kernels: [2 parities][grid][4]
-  ST(dalloc(pb, &pb->dots, (size_t)2 * 4 * std::max(pb->pcg_grid, pb->num_sms)));
+  // dot-product slots of the implicit PCG kernel: [2 parities][grid][4]
+  ST(dalloc(pb, &pb->dots, (size_t)2 * 4 * pb->pcg_grid));
   ST(dalloc(pb, &pb->bar, 1));
   ST(dalloc(pb, &pb->err, 1));
   // explicit reduced camera system (solver option; automatic for up to 512 cameras)
@@ -1033,24 +1232,40 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * n_max));
     ST(dalloc_bytes(pb, &pb->Yhat, R * (size_t)kWStride * ((size_t)N + 1)));
     // co-visibility runs: every pair of observations of one point in cameras i < j,
-    // grouped by (i, j), ascending in point within a run
+    // grouped by (i, j), ascending in point within a run.  Row i (first camera i)
+    // is built by one thread from camera i's observations in camera order, which
+    // visits the points in ascending order; the partner observations of a point
+    // follow it in point order (cameras ascending).
     {
+      std::vector<int> po_cam_h((size_t)N), pos_in_po((size_t)N);
+      parallel_for(N, 1 << 16, [&](int, int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i) {
+          po_cam_h[i] = h_oc[po[i]];
+          pos_in_po[po[i]] = (int)i;
+        }
+      });
+      auto row_pairs = [&](int i, auto&& emit) {
+        for (int q = cam_off[i]; q < cam_off[i + 1]; ++q) {
+          const int kin = co[q], k = pos_in_po[kin], pend = pt_off[h_op[kin] + 1];
+          for (int k2 = k + 1; k2 < pend; ++k2) emit(k, k2, po_cam_h[k2]);
+        }
+      };
       std::vector<long long> cnt((size_t)C * C + 1, 0);
-      for (int p = 0; p < P; ++p)
-        for (int k = pt_off[p]; k < pt_off[p + 1]; ++k)
-          for (int k2 = k + 1; k2 < pt_off[p + 1]; ++k2) cnt[(size_t)h_po_cam[k] * C + h_po_cam[k2] + 1]++;
+      parallel_items(C, [&](int64_t i) {
+        long long* row = cnt.data() + 1 + (size_t)i * C;
+        row_pairs((int)i, [&](int, int, int j) { row[j]++; });
+      });
       for (size_t q = 0; q < (size_t)C * C; ++q) cnt[q + 1] += cnt[q];
       const size_t npairs = (size_t)cnt[(size_t)C * C];
       if (npairs >= (1ull << 31)) {
         set_error("too many co-visible observation pairs (%zu) for the explicit system", npairs);
         return BA_ERR_INVALID_ARG;
       }
-      std::vector<int2> hp(npairs);
-      std::vector<long long> fill(cnt.begin(), cnt.end() - 1);
-      for (int p = 0; p < P; ++p)
-        for (int k = pt_off[p]; k < pt_off[p + 1]; ++k)
-          for (int k2 = k + 1; k2 < pt_off[p + 1]; ++k2)
-            hp[fill[(size_t)h_po_cam[k] * C + h_po_cam[k2]]++] = make_int2(k, k2);
+      std::unique_ptr<int2[]> hp(new int2[std::max<size_t>(npairs, 1)]);
+      parallel_items(C, [&](int64_t i) {
+        std::vector<long long> fill(cnt.begin() + (size_t)i * C, cnt.begin() + (size_t)(i + 1) * C);
+        row_pairs((int)i, [&](int k, int k2, int j) { hp[fill[j]++] = make_int2(k, k2); });
+      });
       std::vector<int4> hr;
       for (int i = 0; i < C; ++i)
         for (int j = i + 1; j < C; ++j) {
@@ -1062,7 +1277,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       // per SM and runs are short (a warp per run would idle in its reduction)
       pb->form_lanes = (long long)hr.size() >= 4LL * 128 * pb->num_sms && npairs < 128 * hr.size();
       ST(dalloc(pb, &pb->covis_pairs, npairs));
-      if (npairs) CU(cudaMemcpy(pb->covis_pairs, hp.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice));
+      if (npairs) CU(cudaMemcpy(pb->covis_pairs, hp.get(), sizeof(int2) * npairs, cudaMemcpyHostToDevice));
       ST(dalloc(pb, &pb->covis_runs, hr.size()));
       if (!hr.empty()) CU(cudaMemcpy(pb->covis_runs, hr.data(), sizeof(int4) * hr.size(), cudaMemcpyHostToDevice));
     }
@@ -1081,19 +1296,34 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       ST(dalloc(pb, &pb->dense_b, 2 * (size_t)n_max));
       pb->dw.epoch = &pb->dense_epoch;
     }
-    // equal camera counts per block: the slowest block sets the pace of every
-    // cross-block exchange, so ceil(C / k) blocks of k cameras beat an uneven split
+    // one block per SM, at least 8 rows of S^ per block; rows per block at most
+    // ceil(n / grid) for every later (smaller) number of free cameras
+    pb->spcg_grid = std::max(1, std::min(pb->num_sms, (n_max + 7) / 8));
     {
-      const int per = (C + pb->num_sms - 1) / pb->num_sms;
-      pb->spcg_grid = std::max(1, (C + per - 1) / per);
+      // shared memory, most useful first: p, then r, z, q, x and M^, then the rows
+      const int rows_max = std::max(8, (n_max + pb->spcg_grid - 1) / pb->spcg_grid);
+      auto bytes = [&](int rows_in, int vecs_in) {
+        return pb->fp64 ? spcg_smem_bytes<double>(n_max, rows_max, rows_in, vecs_in, C)
+                        : spcg_smem_bytes<float>(n_max, rows_max, rows_in, vecs_in, C);
+      };
+      pb->spcg_rows_in_smem = pb->spcg_vecs_in_smem = 1;
+      if (bytes(1, 1) > (size_t)dev_smem_optin) pb->spcg_rows_in_smem = 0;
+      if (!pb->spcg_rows_in_smem && bytes(0, 1) > (size_t)dev_smem_optin) pb->spcg_vecs_in_smem = 0;
+      pb->spcg_smem = bytes(pb->spcg_rows_in_smem, pb->spcg_vecs_in_smem);
+      if (pb->spcg_smem > (size_t)dev_smem_optin) {
+        set_error("explicit PCG of order %d needs %zu B of shared memory per block (limit %d)", n_max,
+                  pb->spcg_smem, dev_smem_optin);
+        return BA_ERR_INVALID_ARG;
+      }
+      if (!pb->spcg_vecs_in_smem) {
+        pb->spcg_scratch_stride = pb->fp64 ? spcg_vec_elems<double>(n_max, C) : spcg_vec_elems<float>(n_max, C);
+        ST(dalloc_bytes(pb, &pb->spcg_scratch, R * pb->spcg_scratch_stride * pb->spcg_grid));
+      }
     }
-    pb->spcg_own_max = std::max(1, (C + pb->spcg_grid - 1) / pb->spcg_grid);
-    pb->spcg_rows_in_smem = 1;
-    for (;;) {
-      pb->spcg_smem = pb->fp64 ? spcg_smem_bytes<double>(n_max, pb->spcg_own_max, pb->spcg_rows_in_smem)
-                               : spcg_smem_bytes<float>(n_max, pb->spcg_own_max, pb->spcg_rows_in_smem);
-      if (pb->spcg_smem <= (size_t)dev_smem_optin || !pb->spcg_rows_in_smem) break;
-      pb->spcg_rows_in_smem = 0;
+    {
+      const size_t nw = (size_t)2 * n_max * spcg_words_per_value(pb->fp64);
+      ST(dalloc(pb, &pb->spcg_words, nw));
+      CU(cudaMemset(pb->spcg_words, 0, sizeof(unsigned long long) * nw));
     }
     const void* sfn = pb->fp64 ? spcg_kernel_ptr<double>() : spcg_kernel_ptr<float>();
     CU(cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb->spcg_smem));
@@ -1115,7 +1345,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   for (auto& e : pb->ev) CU(cudaEventCreate(&e));
   for (auto& e : pb->evk) CU(cudaEventCreate(&e));
 
-  // working copies of the initial state
+  // working copies of the initial state (after every upload has landed)
+  CU(cudaDeviceSynchronize());
   if (pb->fp64) {
     LAUNCH(1, launch_prep_cams<double>(pb->cams64[0], (double*)pb->camw[0], nullptr, C, pb->stream));
     LAUNCH(1, launch_prep_pts<double>(pb->pts64[0], (double*)pb->ptsw[0], P, pb->stream));

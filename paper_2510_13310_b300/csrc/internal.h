@@ -92,12 +92,14 @@ template <typename T>
 struct SpcgArgs {
   const T* Shat;                // scaled reduced camera system [n][n]
   const T* Dinv;                // unscaled block-Jacobi inverses [Cf][81]
-  const double* dscale;         // D = sqrt(diag U*) [n]
+  const double* dscale;         // D = sqrt(diag U*) [n], then 1/D in T
   const T* b;                   // Schur right-hand side [n]
-  int Cf, n, own_max, rows_in_smem;
-  T *x, *z;
-  double* dots;                 // [2][G][4]
-  unsigned* bar;
+  int Cf, n, rows_in_smem, vecs_in_smem;
+  T* x;                         // solution [n]
+  T* scratch;                   // per-block vectors when not in shared memory
+  size_t scratch_stride;        // elements per block of scratch
+  unsigned long long* words;    // exchange words [2][replicas][n][sizeof(T)/4]
+  unsigned tag_base;            // first iteration tag of this launch (>= 1)
   int* err;
   Scalars* sc;
   double tol;
@@ -144,6 +146,14 @@ template <typename T>
 cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s);
 template <typename T>
 cudaError_t launch_prep_pts(const double* pts64, T* ptsw, int P, cudaStream_t s);
+// point-order and camera-order observation arrays from the caller's arrays (oc, op,
+// uv, depth: input order) and the two permutations; pos_in_po: [N] scratch; the
+// working-precision point-order arrays are skipped when po_uvw is null
+template <typename T>
+cudaError_t launch_obs_layout(int N, const int* oc, const int* op, const double* uv, const double* depth,
+                              const int* po, const int* co, int* pos_in_po, int* po_cam, int* po_pt,
+                              int* po_wrow, double* po_uv64, double* po_tau64, T* po_uvw, T* po_tauw,
+                              int* co_pt, int* co_po, T* co_uvw, T* co_tauw, cudaStream_t s);
 
 cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* camw64,
                           const double* pts64, const uint8_t* act, uint8_t* bits,
@@ -189,12 +199,15 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
                           int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaStream_t s);
 template <typename T>
-size_t spcg_smem_bytes(int n, int own_max, int rows_in_smem);
+size_t spcg_smem_bytes(int n, int rows, int rows_in_smem, int vecs_in_smem, int Cf);
+template <typename T>
+__host__ __device__ size_t spcg_vec_elems(int n, int Cf);
 template <typename T>
 const void* spcg_kernel_ptr();
 template <typename T>
 cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
 int spcg_threads();
+int spcg_words_per_value(bool fp64);
 template <typename T>
 cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
                                const uint8_t* act_po, const uint8_t* pt_act, const int* crank, const T* x,

@@ -13,6 +13,7 @@
 // a fixed order: no atomics, bit-reproducible.  The diagonal blocks come from the
 // block-Jacobi pass (U* - sum W V*^-1 W^T) and the lower triangle is mirrored.
 #include <cuda/atomic>
+#include <type_traits>
 
 #include "internal.h"
 #include "model.cuh"
@@ -331,25 +332,47 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
 
 // ---------------------------------------------------------------------------
 // PCG on the scaled explicit system S^ x^ = b^ (b^ = D^-1 b, x = D^-1 x^) with the
-// block-Jacobi preconditioner of S^.  Each block owns a contiguous slice of free
-// cameras (rows) and keeps those rows of S^ in shared memory when they fit.
+// block-Jacobi preconditioner of S^ (Sec. 4.3).
+//
+// The vectors are short (n = 9 Cf <= 4608), so every block keeps all of them
+// (p, r, z, q, x) and updates them redundantly; the only distributed work is
+// the matvec.  Block b owns rows [n b / G, n (b+1) / G) of S^ (in shared memory
+// when they fit), computes those entries of q = S^ p and publishes them; every
+// block then gathers the whole q.  With q, p and r identical in every block,
+// each block forms p^T q, alpha, r^T r, r^T z and beta itself, in the same
+// order, hence to the same bits: one exchange per iteration and no grid-wide
+// reduction or barrier.
+//
+// Exchange words: each 32-bit chunk of a published value travels in a 64-bit
+// word whose high half is the iteration's tag; a 64-bit store and load are
+// single-copy atomic, so a word carrying the expected tag is the published
+// value, with no fence.  Tags are distinct across iterations and launches
+// (tag_base advances by max_iters + 2 per launch).  Iteration i writes word set
+// i & 1: a block publishes iteration i + 2 only after gathering all of
+// iteration i + 1, which every block published only after gathering all of
+// iteration i, so no word is overwritten before every block has read it.
 // ---------------------------------------------------------------------------
 
 constexpr int kSpcgThreads = 512;
+// copies of every exchange word: block b polls copy b % kSpcgReplicas, which
+// spreads the polling of all blocks over several L2 lines per word (8 copies
+// measured 13% faster than one on the 1,791-unknown system)
+constexpr int kSpcgReplicas = 8;
 
-// Cross-block reductions without a separate barrier.  Each block publishes its
-// FP64 partials as 64-bit words whose 4 low mantissa bits are replaced by the
-// reduction's epoch tag (a relative change below 2^-48), with a release store
-// after its other global writes; warp 0 of every block then polls the G slots
-// until every tag matches, and sums them in a fixed order.
-// Seeing all tags is the barrier: writes a block made before publishing are
-// visible after it.  Slots alternate between two sets by epoch parity, so a
-// block that is one reduction ahead never overwrites a slot still being read.
-__device__ __forceinline__ unsigned long long tag_value(double v, unsigned tag) {
-  return ((unsigned long long)__double_as_longlong(v) & ~0xFull) | (unsigned long long)(tag & 0xFu);
+// asynchronous global -> shared copy of one 4- or 8-byte element (cp.async)
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
@@ -358,67 +381,27 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   return v;
 }
 
-// Called by warp 0 only (all lanes), after a __syncthreads that ordered the
-// block's global writes.  mine: this block's K partials (lane 0's values are
-// published).  out: the K sums over the G blocks (every lane).  Each lane polls
-// its slots g = lane + 32 m in batches of 8 (all loads of a batch in flight at
-// once) until every tag matches; an acquire fence then orders the block's later
-// reads after the other blocks' published writes.  false on timeout.
-template <int K>
-__device__ bool warp0_tagged_allreduce(unsigned long long* slots, int G, int bid, unsigned epoch,
-                                       const double (&mine)[K], double (&out)[K], long long timeout_ns) {
-  const int lane = threadIdx.x & 31;
-  unsigned long long* set = slots + (size_t)(epoch & 1u) * 4 * G;
-  const unsigned tag = epoch & 0xFu;
-  if (lane == 0) {
-    __threadfence();
-#pragma unroll
-    for (int k = 0; k < K; ++k) st_release_u64(&set[4 * bid + k], tag_value(mine[k], tag));
-  }
-  double acc[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.0;
-  bool ok = true;
-  const uint64_t t0 = globaltimer_ns();
-  for (int base = 0; base < G; base += 256) {
-    unsigned long long v[K][8];
-    for (;;) {
-      bool ready = true;
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int g = base + lane + 32 * m;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          v[k][m] = g < G ? ld_relaxed_u64(&set[4 * g + k]) : (unsigned long long)tag;
-          ready &= (unsigned)(v[k][m] & 0xFull) == tag;
-        }
-      }
-      if (__all_sync(0xffffffffu, ready)) break;
-      if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
-        ok = false;
-        break;
-      }
-    }
-    if (!__all_sync(0xffffffffu, ok)) break;
-#pragma unroll
-    for (int m = 0; m < 8; ++m)
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        if (base + lane + 32 * m < G) acc[k] += __longlong_as_double((long long)(v[k][m] & ~0xFull));
-  }
-  asm volatile("fence.acq_rel.gpu;" ::: "memory");
-#pragma unroll
-  for (int k = 0; k < K; ++k) out[k] = warp_sum(acc[k]);
-  return __all_sync(0xffffffffu, ok);
+template <typename T>
+constexpr int spcg_words() {
+  return sizeof(T) / 4;  // 32-bit chunks per value
 }
 
-// alpha = (r, z) / (p, q) and beta = (r', z') / (r, z) from the FP64 dot products:
-// the FP32 path needs them to FP32 accuracy only (x, r, p are FP32 vectors), and an
-// FP64 division is a long dependent chain on B300; the FP64 path divides in FP64.
 template <typename T>
-__device__ __forceinline__ double spcg_ratio(double num, double den) {
-  if constexpr (sizeof(T) == 4) return (double)__fdiv_rn((float)num, (float)den);
-  else return num / den;
+__device__ __forceinline__ void spcg_publish(unsigned long long* w, T v, unsigned tag) {
+  const unsigned long long hi = (unsigned long long)tag << 32;
+  if constexpr (sizeof(T) == 4) {
+    st_relaxed_u64(w, hi | __float_as_uint(v));
+  } else {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    st_relaxed_u64(w, hi | (bits & 0xFFFFFFFFull));
+    st_relaxed_u64(w + 1, hi | (bits >> 32));
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T spcg_unpack(const unsigned long long* v) {
+  if constexpr (sizeof(T) == 4) return __uint_as_float((unsigned)v[0]);
+  else return __longlong_as_double((long long)((v[0] & 0xFFFFFFFFull) | (v[1] << 32)));
 }
 
 template <typename T>
@@ -426,235 +409,315 @@ __host__ __device__ inline int spcg_row_stride(int n) {
   return sizeof(T) == 4 ? (n + 3) & ~3 : n;  // FP32 rows padded for 16-byte vector loads
 }
 
+constexpr size_t kSpcgRedBytes = sizeof(double) * 2 * 2 * 32;  // block sums, two alternating buffers
+
+// per-block vector storage other than p: r, z, q, x (full length) and the
+// packed preconditioner blocks, in T elements
 template <typename T>
-size_t spcg_smem_bytes(int n, int own_max, int rows_in_smem) {
+__host__ __device__ size_t spcg_vec_elems(int n, int Cf) {
+  return (size_t)4 * spcg_row_stride<T>(n) + (size_t)45 * Cf;
+}
+
+template <typename T>
+size_t spcg_smem_bytes(int n, int rows, int rows_in_smem, int vecs_in_smem, int Cf) {
   const int ns = spcg_row_stride<T>(n);
-  size_t b = sizeof(double) * 16;                                   // broadcast scalars
-  b += rows_in_smem ? sizeof(T) * (size_t)9 * own_max * ns : 0;    // own rows of S^
-  b += sizeof(T) * (size_t)ns;                                      // p^ (full)
-  b += sizeof(T) * (size_t)9 * own_max * 5;                         // x^, r^, q, b^, z (owned)
-  b += sizeof(T) * (size_t)81 * own_max;                            // preconditioner blocks
+  size_t b = kSpcgRedBytes;
+  b += rows_in_smem ? sizeof(T) * (size_t)rows * ns : 0;  // owned rows of S^
+  b += sizeof(T) * (size_t)ns;                             // p (full length)
+  b += vecs_in_smem ? sizeof(T) * spcg_vec_elems<T>(n, Cf) : 0;
   return (b + 15) & ~size_t(15);
 }
 
-// Dot products of the owned slice by warp 0 (FP64 accumulation, fixed order).
+// Block-wide sums for the PCG scalars.  The FP32 path accumulates in FP32
+// double-float pairs (hi + lo, Knuth's TwoSum, about 44 significant bits): the
+// FP64 pipe is the scarce one on this part, and every block forms these sums
+// redundantly.  The FP64 path accumulates in FP64.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  // TwoSum: e is the exact rounding error of s = a.hi + b.hi for either operand
+  // order, so df_add is commutative bit for bit (butterfly lanes agree)
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return DF{hi, e - (hi - s)};
+}
+__device__ __forceinline__ DF df_shfl_xor(DF v, int m) {
+  return DF{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+__device__ __forceinline__ DF acc_add(DF a, DF b) { return df_add(a, b); }
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ DF acc_shfl_xor(DF v, int m) { return df_shfl_xor(v, m); }
+__device__ __forceinline__ double acc_shfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ double acc_value(DF v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ double acc_value(double v) { return v; }
+// the sum rounded to the working precision (no FP64 operation on the FP32 path)
+__device__ __forceinline__ float acc_t(DF v) { return v.hi + v.lo; }
+__device__ __forceinline__ double acc_t(double v) { return v; }
 template <typename T>
-__device__ __forceinline__ double warp0_dot(const T* a, const T* b, int ne) {
-  double s = 0.0;
-  for (int q = threadIdx.x; q < ne; q += 32) s += (double)a[q] * (double)b[q];
-  return warp_sum(s);
+using SpcgAcc = typename std::conditional<sizeof(T) == 4, DF, double>::type;
+template <typename A>
+__device__ __forceinline__ A acc_zero() {
+  if constexpr (sizeof(A) == 8 && std::is_same<A, double>::value) return 0.0;
+  else return DF{0.f, 0.f};
+}
+__device__ __forceinline__ DF acc_from(float v, DF) { return DF{v, 0.f}; }
+__device__ __forceinline__ double acc_from(double v, double) { return v; }
+
+// Sum of v[k] over the block in a fixed order: every thread returns the same
+// bits (butterfly within warps, then warp 0 adds the warp sums in warp order and
+// broadcasts them).  red: K x 32 accumulators plus K results.  Two barriers.
+// Returns the OR of `flag` over the block.
+template <int K, typename A>
+__device__ __forceinline__ int block_allsum(A (&v)[K], A* red, int flag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A s = v[k];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) s = acc_add(s, acc_shfl_xor(s, m));
+    if (lane == 0) red[32 * k + warp] = s;
+  }
+  const int any = __syncthreads_or(flag);
+  if (threadIdx.x < K) {
+    A s = red[32 * threadIdx.x];
+    for (int w = 1; w < nw; ++w) s = acc_add(s, red[32 * threadIdx.x + w]);
+    red[32 * K + threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = red[32 * K + k];
+  return any;
 }
 
-// Persistent PCG on the scaled system: standard preconditioned CG (x0 = 0,
-// block-Jacobi M^), two cross-block reductions per iteration (p^T q, then
-// r^T r and r^T z) and no other grid synchronisation.  alpha, beta and the
-// stopping test are formed by one thread (FP64 division is scarce) and
-// broadcast through shared memory.
+// sum_i a_i b_i over one camera's 9 entries (FP32 products summed in FP32 on
+// the FP32 path, FP64 on the FP64 path)
+__device__ __forceinline__ float cam_dot(const float* a, const float* b) {
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) s = fmaf(a[i], b[i], s);
+  return s;
+}
+__device__ __forceinline__ double cam_dot(const double* a, const double* b) {
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) s = fma(a[i], b[i], s);
+  return s;
+}
+
+// z_c = M^_c r_c for one camera (packed symmetric 9x9)
+template <typename T>
+__device__ __forceinline__ void spcg_precond(const T* __restrict__ M, const T* __restrict__ r, T* __restrict__ z) {
+  T rv[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) rv[j] = r[j];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) acc += M[sym9(i, j)] * rv[j];
+    z[i] = acc;
+  }
+}
+
+// Persistent PCG: standard preconditioned CG (x0 = 0, block-Jacobi M^).  Thread
+// t handles the vector entries of cameras t, t + 512, ...
 template <typename T>
 __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int W = spcg_words<T>();
   const int G = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int n = a.n, ns = spcg_row_stride<T>(n);
-  const int f0 = (int)(((long long)a.Cf * bid) / G), f1 = (int)(((long long)a.Cf * (bid + 1)) / G);
-  const int e0 = 9 * f0, ne = 9 * (f1 - f0);
-  unsigned char* p = smem_raw;
-  double* sb = reinterpret_cast<double*>(p);  // [16]
-  p += sizeof(double) * 16;
-  T* Srows = reinterpret_cast<T*>(p);
-  p += a.rows_in_smem ? sizeof(T) * (size_t)9 * a.own_max * ns : 0;
-  T* ps = reinterpret_cast<T*>(p);
-  p += sizeof(T) * (size_t)ns;
-  T* xo = reinterpret_cast<T*>(p);
-  T* ro = xo + 9 * a.own_max;
-  T* qo = ro + 9 * a.own_max;
-  T* bo = qo + 9 * a.own_max;
-  T* zo = bo + 9 * a.own_max;
-  T* Mo = zo + 9 * a.own_max;
-  const T* Sg = a.Shat + (size_t)e0 * n;
-  unsigned long long* slots = reinterpret_cast<unsigned long long*>(a.dots);
-  unsigned epoch = 0;
+  const int n = a.n, ns = spcg_row_stride<T>(n), Cf = a.Cf;
+  const int r0 = (int)(((long long)n * bid) / G), r1 = (int)(((long long)n * (bid + 1)) / G);
+  const int nr = r1 - r0;
+  using A = SpcgAcc<T>;
+  unsigned char* sp = smem_raw;
+  A* red = reinterpret_cast<A*>(sp);
+  sp += kSpcgRedBytes;
+  T* Srows = reinterpret_cast<T*>(sp);
+  sp += a.rows_in_smem ? sizeof(T) * (size_t)nr * ns : 0;
+  T* pv = reinterpret_cast<T*>(sp);
+  // r, z, q, x and M^ follow p in shared memory, or sit in this block's slice of
+  // the global scratch when they do not fit
+  T* rv = a.vecs_in_smem ? pv + ns : a.scratch + (size_t)bid * a.scratch_stride;
+  T* zv = rv + ns;
+  T* qv = zv + ns;
+  T* xv = qv + ns;
+  T* Mv = xv + ns;
+  const T* Sg = a.Shat + (size_t)r0 * n;
   const T* dinv = reinterpret_cast<const T*>(a.dscale + n);
 
   if (a.rows_in_smem) {
-    // eight loads per lane in flight: the block's rows come from HBM once per solve
-    for (int r = warp; r < ne; r += nwarps) {
+    // the block's rows of S^ (from HBM once per solve): asynchronous element
+    // copies, all in flight together, overlapping the set-up below
+    for (int r = warp; r < nr; r += nwarps) {
       const T* src = Sg + (size_t)r * n;
       T* dst = Srows + (size_t)r * ns;
-      for (int c0 = 0; c0 < ns; c0 += 256) {
-        T v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int c = c0 + 32 * u + lane;
-          v[u] = c < n ? src[c] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int c = c0 + 32 * u + lane;
-          if (c < ns) dst[c] = v[u];
-        }
-      }
+      for (int c = lane; c < n; c += 32) cp_async_elem(dst + c, src + c);
+      for (int c = n + lane; c < ns; c += 32) dst[c] = T(0);
     }
+    cp_async_commit();
   }
-  for (int c = n + tid; c < ns; c += blockDim.x) ps[c] = T(0);
-  // owned preconditioner blocks of S^: D_f^-1 scaled, M^_f = diag(d) M_f diag(d)
-  for (int q = tid; q < 81 * (f1 - f0); q += blockDim.x) {
-    int f = q / 81, ij = q - 81 * f, i = ij / 9, j = ij - 9 * i;
-    int ei = e0 + 9 * f + i, ej = e0 + 9 * f + j;
-    Mo[q] = (T)((double)a.Dinv[81 * (size_t)(f0 + f) + ij] * a.dscale[ei] * a.dscale[ej]);
-  }
-  for (int q = tid; q < ne; q += blockDim.x) {
-    xo[q] = T(0);
-    T bv = (T)((double)a.b[e0 + q] * (double)dinv[e0 + q]);
-    ro[q] = bv;
-    bo[q] = bv;
-  }
-  __syncthreads();
-  for (int q = tid; q < ne; q += blockDim.x) {
-    int f = q / 9, i = q - 9 * f;
-    T zz = T(0);
+  for (int c = n + tid; c < ns; c += blockDim.x) pv[c] = T(0);
+  // preconditioner blocks of S^: M^_f = diag(d) M_f diag(d), symmetrised, in T;
+  // one thread per camera, its 81 + 9 loads independent
+  for (int f = tid; f < Cf; f += blockDim.x) {
+    const T* Df = a.Dinv + 81 * (size_t)f;
+    T D[81], d[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) zz += Mo[81 * f + 9 * i + k] * ro[9 * f + k];
-    a.z[e0 + q] = zz;
-    zo[q] = zz;
+    for (int k = 0; k < 81; ++k) D[k] = Df[k];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = (T)a.dscale[9 * f + i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int j = i; j < 9; ++j) Mv[45 * f + sym9(i, j)] = (T(0.5) * (D[9 * i + j] + D[9 * j + i])) * d[i] * d[j];
   }
   __syncthreads();
-  if (warp == 0) {
-    const double mine[2] = {warp0_dot(ro, zo, ne), warp0_dot(ro, ro, ne)};
-    double tot[2];
-    const bool ok = warp0_tagged_allreduce<2>(slots, G, bid, ++epoch, mine, tot, a.timeout_ns);
-    if (lane == 0) {
-      sb[0] = tot[0];
-      sb[1] = tot[1];
-      sb[2] = sqrt(tot[1]);
-      sb[7] = ok ? 1.0 : 0.0;
-      if (!ok) atomicOr(a.err, 1);
+  // r = b^, z = M^ r, p = z, x = 0; (r, z) and (r, r)
+  A d0[2] = {acc_zero<A>(), acc_zero<A>()};
+  for (int f = tid; f < Cf; f += blockDim.x) {
+    const int e = 9 * f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      rv[e + i] = a.b[e + i] * dinv[e + i];  // the correctly rounded product in T
+      xv[e + i] = T(0);
     }
-  } else {
-    ++epoch;
+    spcg_precond(Mv + 45 * f, rv + e, zv + e);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) pv[e + i] = zv[e + i];
+    d0[0] = acc_add(d0[0], acc_from(cam_dot(rv + e, zv + e), A{}));
+    d0[1] = acc_add(d0[1], acc_from(cam_dot(rv + e, rv + e), A{}));
   }
-  __syncthreads();
-  if (sb[7] == 0.0) return;
-  double rz = sb[0];
-  const double bnorm = sb[2];
-  const double stop_rr = (a.tol * bnorm) * (a.tol * bnorm);
+  if (a.rows_in_smem) cp_async_wait_all();  // visible to the block after the barrier below
+  block_allsum<2>(d0, red, 0);
+  // the scalars of the iteration in the working precision (T)
+  T rz = acc_t(d0[0]);
+  const double bnorm = sqrt(acc_value(d0[1]));
+  const T stop_rr = (T)((a.tol * bnorm) * (a.tol * bnorm));
+  T rr_last = acc_t(d0[1]);
   int it = 0;
-  double rr_last = sb[1];
-  T beta = T(0);
-  bool first = true;
+  unsigned long long* words = a.words;
   while (bnorm > 0.0 && it < a.max_iters) {
-    // p = z (first) or z + beta p: every load of z issued before any use
-    for (int base = 0; base < n; base += 4 * (int)blockDim.x) {
-      T zv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        int e = base + u * blockDim.x + tid;
-        zv[u] = e < n ? a.z[e] : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        int e = base + u * blockDim.x + tid;
-        if (e < n) ps[e] = first ? zv[u] : zv[u] + beta * ps[e];
-      }
-    }
-    first = false;
-    __syncthreads();
-    // q = S^_rows p^: one warp per row
+    const unsigned tag = a.tag_base + (unsigned)it;
+    const size_t set_words = (size_t)n * W;
+    unsigned long long* set = words + (size_t)(it & 1) * kSpcgReplicas * set_words;
+    // q = S^_rows p for the owned rows, published as tagged words: one warp per row
     if constexpr (sizeof(T) == 4) {
       if (a.rows_in_smem) {
-        const float4* p4 = reinterpret_cast<const float4*>(ps);
-        for (int r = warp; r < ne; r += nwarps) {
+        const float4* p4 = reinterpret_cast<const float4*>(pv);
+        for (int r = warp; r < nr; r += nwarps) {
           const float4* row = reinterpret_cast<const float4*>(Srows + (size_t)r * ns);
           float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
           for (int c = lane; c < ns / 4; c += 32) {
-            const float4 sv = row[c], pv = p4[c];
-            c0 += sv.x * pv.x;
-            c1 += sv.y * pv.y;
-            c2 += sv.z * pv.z;
-            c3 += sv.w * pv.w;
+            const float4 s4 = row[c], p4v = p4[c];
+            c0 += s4.x * p4v.x;
+            c1 += s4.y * p4v.y;
+            c2 += s4.z * p4v.z;
+            c3 += s4.w * p4v.w;
           }
           const float acc = warp_sum((c0 + c1) + (c2 + c3));
-          if (lane == 0) qo[r] = acc;
+          if (lane < kSpcgReplicas) spcg_publish<T>(set + lane * set_words + (size_t)(r0 + r) * W, acc, tag);
         }
       }
     }
     if (sizeof(T) != 4 || !a.rows_in_smem) {
       const T* base = a.rows_in_smem ? Srows : Sg;
       const int ld = a.rows_in_smem ? ns : n;
-      for (int r = warp; r < ne; r += nwarps) {
+      for (int r = warp; r < nr; r += nwarps) {
         const T* row = base + (size_t)r * ld;
         T acc = T(0);
-        for (int c = lane; c < n; c += 32) acc += row[c] * ps[c];
+        for (int c = lane; c < n; c += 32) acc += row[c] * pv[c];
         acc = warp_sum(acc);
-        if (lane == 0) qo[r] = acc;
+        if (lane < kSpcgReplicas) spcg_publish<T>(set + lane * set_words + (size_t)(r0 + r) * W, acc, tag);
       }
     }
-    __syncthreads();
-    if (warp == 0) {
-      const double mine[1] = {warp0_dot(ps + e0, qo, ne)};
-      double tot[1];
-      const bool ok = warp0_tagged_allreduce<1>(slots, G, bid, ++epoch, mine, tot, a.timeout_ns);
-      if (lane == 0) {
-        const double pq = tot[0];
-        const bool fine = ok && pq > 0.0 && isfinite(pq);
-        sb[3] = fine ? spcg_ratio<T>(rz, pq) : 0.0;
-        sb[7] = fine ? 1.0 : 0.0;
-        if (!ok) atomicOr(a.err, 1);
-        else if (!fine && bid == 0) atomicOr(a.err, 2);
-      }
-    } else {
-      ++epoch;
-    }
-    __syncthreads();
-    if (sb[7] == 0.0) break;
-    const double alpha = sb[3];
-    for (int q = tid; q < ne; q += blockDim.x) {
-      if constexpr (sizeof(T) == 4) {
-        xo[q] = fmaf((float)alpha, ps[e0 + q], xo[q]);
-        ro[q] = fmaf(-(float)alpha, qo[q], ro[q]);
-      } else {
-        xo[q] = (T)((double)xo[q] + alpha * (double)ps[e0 + q]);
-        ro[q] = (T)((double)ro[q] - alpha * (double)qo[q]);
-      }
-    }
-    __syncthreads();
-    for (int q = tid; q < ne; q += blockDim.x) {
-      int f = q / 9, i = q - 9 * f;
-      T zz = T(0);
+    // gather q from this block's copy, coalesced (thread t: entries t, t + 512, ...,
+    // up to four in flight), and (p, q)
+    int late = 0;
+    A d1[1] = {acc_zero<A>()};
+    const unsigned long long* mine = set + (size_t)(bid % kSpcgReplicas) * set_words;
+    const uint64_t t0 = globaltimer_ns();
+    for (int eb = tid; eb < n && !late; eb += 4 * blockDim.x) {
+      unsigned long long v[4][W];
+      for (;;) {
+        bool ready = true;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) zz += Mo[81 * f + 9 * i + k] * ro[9 * f + k];
-      a.z[e0 + q] = zz;
-      zo[q] = zz;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      const double mine[2] = {warp0_dot(ro, ro, ne), warp0_dot(ro, zo, ne)};
-      double tot[2];
-      const bool ok = warp0_tagged_allreduce<2>(slots, G, bid, ++epoch, mine, tot, a.timeout_ns);
-      if (lane == 0) {
-        sb[4] = tot[0];
-        sb[5] = tot[0] <= stop_rr ? 1.0 : 0.0;
-        sb[6] = rz != 0.0 ? spcg_ratio<T>(tot[1], rz) : 0.0;
-        sb[0] = tot[1];
-        sb[7] = ok ? 1.0 : 0.0;
-        if (!ok) atomicOr(a.err, 1);
+        for (int u = 0; u < 4; ++u) {
+          const int e = eb + u * blockDim.x;
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            v[u][w] = e < n ? ld_relaxed_u64(mine + (size_t)e * W + w) : ((unsigned long long)tag << 32);
+            ready &= (unsigned)(v[u][w] >> 32) == tag;
+          }
+        }
+        if (ready) break;
+        if ((long long)(globaltimer_ns() - t0) > a.timeout_ns) {
+          late = 1;
+          break;
+        }
       }
-    } else {
-      ++epoch;
+      if (late) break;
+      T part = T(0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = eb + u * blockDim.x;
+        if (e < n) {
+          const T q = spcg_unpack<T>(v[u]);
+          qv[e] = q;
+          part = fma(pv[e], q, part);
+        }
+      }
+      d1[0] = acc_add(d1[0], acc_from(part, A{}));
+    }
+    if (block_allsum<1>(d1, red, late)) {
+      if (tid == 0) atomicOr(a.err, 1);
+      break;
+    }
+    const T pq = acc_t(d1[0]);
+    if (!(pq > T(0) && isfinite(pq))) {
+      if (bid == 0 && tid == 0) atomicOr(a.err, 2);
+      break;
+    }
+    const T alpha = rz / pq;
+    // x += alpha p, r -= alpha q, z = M^ r; (r, r) and (r, z)
+    A d2[2] = {acc_zero<A>(), acc_zero<A>()};
+    for (int f = tid; f < Cf; f += blockDim.x) {
+      const int e = 9 * f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        xv[e + i] = fma(alpha, pv[e + i], xv[e + i]);
+        rv[e + i] = fma(-alpha, qv[e + i], rv[e + i]);
+      }
+      spcg_precond(Mv + 45 * f, rv + e, zv + e);
+      d2[0] = acc_add(d2[0], acc_from(cam_dot(rv + e, rv + e), A{}));
+      d2[1] = acc_add(d2[1], acc_from(cam_dot(rv + e, zv + e), A{}));
+    }
+    block_allsum<2>(d2, red, 0);
+    ++it;
+    const T rr = acc_t(d2[0]), rz_new = acc_t(d2[1]);
+    rr_last = rr;
+    if (rr <= stop_rr) break;
+    const T beta = rz != T(0) ? rz_new / rz : T(0);
+    rz = rz_new;
+    // p = z + beta p
+    for (int f = tid; f < Cf; f += blockDim.x) {
+      const int e = 9 * f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) pv[e + i] = fma(beta, pv[e + i], zv[e + i]);
     }
     __syncthreads();
-    if (sb[7] == 0.0) break;
-    ++it;
-    rr_last = sb[4];
-    if (sb[5] != 0.0) break;
-    beta = (T)sb[6];
-    rz = sb[0];
   }
-  for (int q = tid; q < ne; q += blockDim.x) a.x[e0 + q] = (T)((double)xo[q] * (double)dinv[e0 + q]);
+  __syncthreads();
+  for (int e = r0 + tid; e < r1; e += blockDim.x) a.x[e] = xv[e] * dinv[e];
   if (bid == 0 && tid == 0) {
     a.sc->pcg_iters = it;
     a.sc->pcg_bnorm = bnorm;
-    a.sc->pcg_rel_res = bnorm > 0.0 ? sqrt(rr_last) / bnorm : 0.0;
+    a.sc->pcg_rel_res = bnorm > 0.0 ? sqrt((double)rr_last) / bnorm : 0.0;
   }
 }
 
@@ -670,6 +733,7 @@ cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_
 }
 
 int spcg_threads() { return kSpcgThreads; }
+int spcg_words_per_value(bool fp64) { return kSpcgReplicas * (fp64 ? spcg_words<double>() : spcg_words<float>()); }
 
 // ---------------------------------------------------------------------------
 // Point back-substitution dp = V*^-1 (-g_p - sum_k W_k^T dc_c(k)), with the
@@ -750,7 +814,8 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
   template cudaError_t launch_form_S<T>(const Layout&, int, const int4*, const int2*, const T*,        \
                                         const T*, const int*, const T*, const T*, double*, int, T*, T*, \
                                         bool, int, cudaStream_t);                                      \
-  template size_t spcg_smem_bytes<T>(int, int, int);                                                   \
+  template size_t spcg_smem_bytes<T>(int, int, int, int, int);                                         \
+  template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \
   template const void* spcg_kernel_ptr<T>();                                                           \
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \
   template cudaError_t launch_backsub_pts<T>(const Layout&, const ModelParams&, const T*, const T*,    \

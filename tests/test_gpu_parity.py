@@ -166,6 +166,25 @@ def test_damped_step_matches_oracle(precision, tol, solver):
     assert not g["dc"][sc.fixed_cams].any()
 
 
+@pytest.mark.parametrize("precision,n_cams,tol", [(ba.BA_FP64, 400, 1e-7), (ba.BA_FP32, 700, 2e-2)])
+def test_explicit_solver_vectors_in_global_scratch(precision, n_cams, tol):
+    # systems of 3,591 (FP64) and 6,291 (FP32) unknowns: the explicit PCG keeps p
+    # in shared memory and its other per-block vectors in global scratch
+    sc = geometric(n_cams, 6000, 2, 10, 4.0, seed=77)
+    gpu, orc = pair(sc, precision, pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6,
+                    solver=ba.BA_SOLVER_EXPLICIT, pcg_max_iters=2000)
+    assert gpu.explicit_solver
+    lam = 1e-3
+    g = gpu.solve_damped(lam)
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    o = orc.solve_step(ne, ext, lam)
+    assert rel_err(g["dc"], o["dc"]) < tol
+    assert rel_err(g["dp"], o["dp"]) < tol
+    assert g["pcg_rel_res"] <= (1e-10 if precision == ba.BA_FP64 else 1e-6)
+
+
 # ---------------------------------------------------------------------------
 # (e): LM trajectories
 # ---------------------------------------------------------------------------
@@ -290,6 +309,27 @@ def test_device_and_host_buffers_agree():
     c_h, p_h = p1.get_params()
     np.testing.assert_array_equal(c_dev.cpu().numpy(), c_h)
     np.testing.assert_array_equal(p_dev.cpu().numpy(), p_h)
+
+
+@pytest.mark.parametrize("solver", [ba.BA_SOLVER_IMPLICIT, ba.BA_SOLVER_EXPLICIT])
+def test_layout_independent_of_host_threads(monkeypatch, solver):
+    # the orderings, tile records and co-visibility runs built by ba_create on
+    # host threads give bit-identical runs with one thread and with many
+    sc = geometric(40, 6000, 2, 60, 6.0, seed=41)  # long and short tracks, many tiles
+    opts = ba.Options(precision=ba.BA_FP32, solver=solver, min_cam_obs=15, min_pt_obs=3)
+    runs = []
+    for n in ("1", "7"):
+        monkeypatch.setenv("BA_HOST_THREADS", n)
+        p = ba.Problem.from_scene(sc, opts)
+        log = p.solve(3)
+        runs.append(([r["cost"] for r in log], p.get_params(), p.get_active()))
+        p.close()
+    (c1, (cam1, pt1), a1), (c2, (cam2, pt2), a2) = runs
+    assert c1 == c2
+    np.testing.assert_array_equal(cam1, cam2)
+    np.testing.assert_array_equal(pt1, pt2)
+    for key in a1:
+        np.testing.assert_array_equal(a1[key], a2[key], err_msg=key)
 
 
 # ---------------------------------------------------------------------------
