@@ -38,7 +38,7 @@ METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 
 # DRAM bytes (read + write) of one launch of the roofline kernel, from an ncu
 # capture of this workload (profiles/k_spcg_medium_1M_obs.md); None once the
 # kernel has changed since the counters were taken.
-NCU_TRAFFIC = {"k_spcg": 12999168 + 512, "k_pcg": None}
+NCU_TRAFFIC = {"k_spcg": 13171456 + 32000, "k_pcg": None}
 WORKLOAD = "medium"
 LM_ITERS = 30
 

@@ -135,6 +135,9 @@ struct ba_problem {
   double lambda = 1e-4, nu = 2.0;
   uint64_t obs_hash = 0;        // FNV-1a of the input index arrays (checkpoint identity)
   bool extracted = false, state_changed = true, linearized = false;
+  // the state changed by an accepted step whose validity bits equal those of the
+  // state the active set was extracted from: the extraction would not change it
+  bool same_validity = false, flips_known = false;
   bool bits_valid[2] = {false, false};
   bool cost_valid[2] = {false, false};
   int n_cam_free = 0, n_pt_act = 0, n_obs_act = 0, n_cam_act = 0;
@@ -292,11 +295,16 @@ ba_status sync(ba_problem* pb) {
 // ---------------------------------------------------------------------------
 
 // FP64 pass over a state slot: validity bits (if bits != null) and the cost over
-// the current active set (if with_cost) into sc->cost[slot].
-ba_status eval_state(ba_problem* pb, int slot, bool want_bits, bool with_cost) {
+// the current active set (if with_cost) into sc->cost[slot].  ref_slot >= 0:
+// compare the validity bits with that slot's (sc->valid_flips, cleared here).
+ba_status eval_state(ba_problem* pb, int slot, bool want_bits, bool with_cost, int ref_slot = -1) {
+  const bool cmp = want_bits && ref_slot >= 0 && ref_slot != slot && pb->bits_valid[ref_slot];
+  if (cmp) CU(cudaMemsetAsync(&pb->sc->valid_flips, 0, sizeof(int), pb->stream));
   LAUNCH(1, launch_eval64(pb->L, pb->mp, pb->camw64[slot], pb->pts64[slot],
                           with_cost ? pb->obs_act : nullptr, want_bits ? pb->bits[slot] : nullptr,
+                          cmp ? pb->bits[ref_slot] : nullptr, cmp ? &pb->sc->valid_flips : nullptr,
                           with_cost ? pb->eval_parts : nullptr, pb->eval_grid, pb->stream));
+  pb->flips_known = cmp;
   if (with_cost) LAUNCH(1, launch_reduce_eval(pb->eval_parts, pb->eval_grid, pb->sc, slot, pb->stream));
   if (want_bits) pb->bits_valid[slot] = true;
   if (with_cost) pb->cost_valid[slot] = true;
@@ -615,10 +623,15 @@ ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   bool drop = o.extract_every > 0 && o.drop_residual_px > 0 && k > 0 && k % o.extract_every == 0;
   CU(cudaEventRecord(pb->ev[0], pb->stream));
   NvtxScope r_extract("ba: extract");
-  if (!pb->extracted || pb->state_changed || drop) {
+  if (pb->extracted && pb->state_changed && pb->same_validity && !drop) {
+    // Sec. 4.2: the active set is a function of the validity bits (and the sticky
+    // drops, unchanged outside drop iterations); same bits, same active set
+    pb->state_changed = false;
+  } else if (!pb->extracted || pb->state_changed || drop) {
     ST(run_extraction(pb, drop, nullptr));
     pb->state_changed = false;
   }
+  pb->same_validity = false;
   if (!pb->cost_valid[pb->cur]) ST(eval_state(pb, pb->cur, false, true));
   CU(cudaEventRecord(pb->ev[1], pb->stream));
   r_extract.end();
@@ -647,7 +660,8 @@ ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   if (pb->fp64) ST(candidate_t<double>(pb));
   else ST(candidate_t<float>(pb));
   int nxt = 1 - pb->cur;
-  ST(eval_state(pb, nxt, true, true));
+  ST(eval_state(pb, nxt, true, true, pb->cur));
+  const bool flips_known = pb->flips_known;
   CU(cudaEventRecord(pb->ev[6], pb->stream));
   CU(cudaMemcpyAsync(pb->h_sc, pb->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, pb->stream));
   int h_err = 0;
@@ -682,6 +696,7 @@ ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   if (accept) {
     pb->cur = nxt;
     pb->state_changed = true;
+    pb->same_validity = flips_known && s.valid_flips == 0;
     pb->linearized = false;
     double t = 2.0 * gain - 1.0;
     pb->lambda = lambda * std::max(1.0 / 3.0, 1.0 - t * t * t);
@@ -1542,6 +1557,7 @@ ba_status ba_set_params(ba_problem* pb, const double* cams, const double* pts) {
   }
   pb->bits_valid[s] = pb->cost_valid[s] = false;
   pb->state_changed = true;
+  pb->same_validity = false;
   pb->linearized = false;
   ST(sync(pb));
   return BA_OK;

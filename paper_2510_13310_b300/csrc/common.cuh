@@ -40,6 +40,7 @@ struct Scalars {
   int n_cam_free;
   int n_pt_act;
   int n_cam_act;
+  int valid_flips;       // evaluation: some validity bit differs from the reference slot's
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -157,7 +157,7 @@ cudaError_t launch_obs_layout(int N, const int* oc, const int* op, const double*
 
 cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* camw64,
                           const double* pts64, const uint8_t* act, uint8_t* bits,
-                          double* partials, int grid, cudaStream_t s);
+                          const uint8_t* ref_bits, int* flips, double* partials, int grid, cudaStream_t s);
 cudaError_t launch_reduce_eval(const double* partials, int nparts, Scalars* sc, int slot,
                                cudaStream_t s);
 

@@ -132,9 +132,13 @@ cudaError_t launch_obs_layout(int N, const int* oc, const int* op, const double*
 
 // bits: 1 = geometrically valid (z > min_depth, pixel inside the image),
 //       2 = valid and |r_uv| above the residual-drop threshold.
+// ref_bits (nullable): validity bits of another state; any difference in bit 1
+// sets *flips (the active set extracted from ref_bits then still applies).
 __global__ void k_eval64(Layout L, ModelParams mp, const double* __restrict__ camw64,
                          const double* __restrict__ pts64, const uint8_t* __restrict__ act,
-                         uint8_t* __restrict__ bits, double* __restrict__ partials) {
+                         uint8_t* __restrict__ bits, const uint8_t* __restrict__ ref_bits,
+                         int* __restrict__ flips, double* __restrict__ partials) {
+  int flip = 0;
   __shared__ double red[32];
   double acc_cost = 0.0, acc_e2 = 0.0;
   int acc_n = 0;
@@ -154,12 +158,16 @@ __global__ void k_eval64(Layout L, ModelParams mp, const double* __restrict__ ca
       int b = ok ? 1 : 0;
       if (ok && mp.drop_px > 0.0 && sqrt(e2) > mp.drop_px) b |= 2;
       bits[k] = (uint8_t)b;
+      if (ref_bits) flip |= (b ^ ref_bits[k]) & 1;
     }
     if (act && act[k]) {
       acc_cost += huber_loss(fma(e.r2, e.r2, e2), mp.huber);
       acc_e2 += e2;
       acc_n += 1;
     }
+  }
+  if (ref_bits) {
+    if (__syncthreads_or(flip) && threadIdx.x == 0) atomicOr(flips, 1);
   }
   if (!partials) return;
   double s0 = block_sum(acc_cost, red);
@@ -175,8 +183,9 @@ __global__ void k_eval64(Layout L, ModelParams mp, const double* __restrict__ ca
 
 cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* camw64,
                           const double* pts64, const uint8_t* act, uint8_t* bits,
-                          double* partials, int grid, cudaStream_t s) {
-  k_eval64<<<grid, kBlock, 0, s>>>(L, mp, camw64, pts64, act, bits, partials);
+                          const uint8_t* ref_bits, int* flips, double* partials, int grid, cudaStream_t s) {
+  k_eval64<<<grid, kBlock, 0, s>>>(L, mp, camw64, pts64, act, bits, bits ? ref_bits : nullptr, flips,
+                                    partials);
   return cudaGetLastError();
 }
 
