@@ -1,8 +1,9 @@
 """Benchmark: LM bundle-adjustment iterations/s on the 1M-observation scene.
 
 Workload: 200 cameras, 100k points, ~1M observations (track length 3-20,
-truncated geometric, mean 10), FP32 hot path with FP64 dot products, cost and
-gain ratio; 2% outliers, depth priors on 50% of observations.  A step is one
+truncated geometric, mean 10), FP32 hot path with the cost and gain ratio in
+FP64 and the PCG scalars in FP64 (implicit system) or FP32 double-float pairs
+(explicit system); 2% outliers, depth priors on 50% of observations.  A step is one
 full LM iteration (extraction, residuals/Jacobians, normal equations and
 Schur terms, PCG + back-substitution, candidate evaluation and accept/reject).
 
@@ -35,10 +36,11 @@ from paper_2510_13310_b300 import scenes  # noqa: E402
 
 METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 GPU"
 
-# DRAM bytes (read + write) of one launch of the roofline kernel, from an ncu
-# capture of this workload (profiles/k_spcg_medium_1M_obs.md); None once the
-# kernel has changed since the counters were taken.
-NCU_TRAFFIC = {"k_spcg": 13171456 + 32000, "k_pcg": None}
+# DRAM bytes (read + write) of one launch of each roofline kernel, from ncu
+# captures of this workload (profiles/k_spcg_medium_1M_obs.md,
+# profiles/k_form_S_runs_and_k_eval64_medium_1M_obs.md); None once the kernel
+# has changed since the counters were taken.
+NCU_TRAFFIC = {"k_spcg": 13158912 + 39936, "k_pcg": None, "k_form_S_runs": 355182592 + 15817216}
 WORKLOAD = "medium"
 LM_ITERS = 30
 
@@ -313,8 +315,9 @@ def main():
     schur_ms = statistics.median([i["ms"][2] for i in infos])
     gobs = N / (ab_ms * 1e-3) / 1e9 if ab_ms else None
 
-    # roofline of the dominant kernel (the persistent PCG solve), from CUDA events
-    # recorded by the library around that launch on its stream (ms[4])
+    # roofline of the dominant kernel: of the PCG launch (ms[4]) and the co-visibility
+    # product that forms the explicit system (ms[7]), the one with the larger mean
+    # CUDA-event time over the timed steps (events recorded by the library on its stream)
     hbm, peak_kind = _peaks()
     solved = [i for i in infos if i["pcg_iters"] > 0 and i["ms"][4] > 0]
     P = scene.spec.n_pts
@@ -324,17 +327,18 @@ def main():
     mean_it = statistics.mean(i["pcg_iters"] for i in solved) if solved else 0.0
     kern_ms = statistics.mean(i["ms"][4] for i in solved) if solved else None
     kind = prob.solver_kind
+    solver_name = {ba.BA_SOLVER_DENSE: "dense", ba.BA_SOLVER_EXPLICIT: "explicit"}.get(kind, "implicit")
     if kind == ba.BA_SOLVER_DENSE:
         # the launch covers factorisation + CG; report the factorisation's flops
         per_launch = n ** 3 / 3.0
         kname = "dense solve: tensor-core blocked Cholesky (tcgen05 kind::tf32) + preconditioned CG"
         unit_txt = "n^3/3 flops of the factorisation, n = 9 Cf (timed launch includes the CG)"
     elif prob.explicit_solver:
-        # S^ read once (4 n^2), preconditioner blocks, b, D and 1/D, x out; per
-        # iteration the search direction z is written and read once (8 n)
-        per_launch = 4 * n * n + 4 * 81 * Cf + 4 * n + 12 * n + 4 * n + mean_it * 8 * n
+        # S^ read once (4 n^2); preconditioner blocks (324 Cf), b, D, 1/D and x (20 n).
+        # The per-iteration exchange of q stays in L2.
+        per_launch = 4 * n * n + 324 * Cf + 20 * n
         kname = "k_spcg (persistent block-Jacobi PCG on the explicit scaled Schur matrix, rows in shared memory)"
-        unit_txt = "4 n^2 + 344 Cf + 8 n x iters bytes, n = 9 Cf"
+        unit_txt = "4 n^2 + 324 Cf + 20 n bytes, n = 9 Cf"
     else:
         # per matvec: W rows (27 x 4) + point index (4) per observation, V*^-1 and
         # the point vector per point
@@ -348,14 +352,40 @@ def main():
     else:
         achieved = per_launch / (kern_ms * 1e-3) / 1e9 if kern_ms else 0.0
         bound, peak, unit, psrc = "hbm", hbm, "GB/s", peak_kind + " (burst copy)"
-    roofline = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+    roof_pcg = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "peak_source": psrc,
                 "traffic": NCU_TRAFFIC.get("k_spcg" if prob.explicit_solver else "k_pcg")
                 if kind != ba.BA_SOLVER_DENSE else None,
-                "algorithmic_bytes_per_launch": per_launch,
-                "bytes_formula": unit_txt, "launch_ms_mean": kern_ms,
+                "algorithmic_per_launch": per_launch,
+                "formula": unit_txt, "launch_ms_mean": kern_ms,
                 "mean_pcg_iters": mean_it, "us_per_pcg_iter": (kern_ms * 1e3 / mean_it) if mean_it else None,
-                "solver": {ba.BA_SOLVER_DENSE: "dense", ba.BA_SOLVER_EXPLICIT: "explicit"}.get(kind, "implicit")}
+                "solver": solver_name}
+    roof_form = None
+    form = [i["ms"][7] for i in infos if i["ms"][7] > 0]
+    if form:
+        # 9x9 block products Y^_k Y^_k2^T over co-visible observation pairs whose
+        # cameras are both free: 243 FMA = 486 flops per pair, on the FP32 pipes
+        free = np.ones(scene.spec.n_cams, bool)
+        free[np.asarray(scene.fixed_cams, int)] = False
+        t = np.bincount(scene.obs_pt[free[scene.obs_cam]], minlength=P).astype(np.int64)
+        npairs = int((t * (t - 1) // 2).sum())
+        form_ms = statistics.mean(form)
+        flops = 486.0 * npairs
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_peak = sms * 128 * 2 * 2032e6 / 1e12
+        roof_form = {"kernel": "k_form_S_runs (co-visibility block products forming the explicit system)",
+                     "bound": "alu", "achieved": flops / (form_ms * 1e-3) / 1e12, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": flops / (form_ms * 1e-3) / 1e12 / fp32_peak,
+                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x 2032 MHz",
+                     "traffic": NCU_TRAFFIC.get("k_form_S_runs"), "algorithmic_per_launch": flops,
+                     "formula": "486 flops x co-visible pairs of free cameras", "pairs": npairs,
+                     "hbm_bytes_algorithmic": 8 * npairs + 108 * N + 4 * n * n,
+                     "hbm_frac_of_measured": (8 * npairs + 108 * N + 4 * n * n) / (form_ms * 1e-3) / 1e9 / hbm,
+                     "launch_ms_mean": form_ms}
+    if roof_form is not None and roof_form["launch_ms_mean"] > (kern_ms or 0.0):
+        roofline, roofline_next = roof_form, roof_pcg
+    else:
+        roofline, roofline_next = roof_pcg, roof_form
 
     # end to end through the public API from pinned host buffers, one full solve
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -427,15 +457,16 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": _workload_name(scene) + ", FP32 with FP64 dots/cost/gain",
+            "config": {"workload": _workload_name(scene) + ", FP32 with FP64 cost and gain ratio",
                        "n_cams": scene.spec.n_cams, "n_pts": P, "n_obs": N,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)"},
             "jacobian_schur_gobs_s": gobs, "jacobian_schur_ms": ab_ms, "schur_terms_ms": schur_ms,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_rmse": ttr,
+            "roofline": roofline, "roofline_next": roofline_next, "cpu_baseline": cpu, "e2e": e2e,
+            "time_to_rmse": ttr,
             "gpu_launches": launches, "clocks": clk.summary(),
             "lm_trace": [{"cost": i["cost"], "rmse_px": i["rmse_px"], "accepted": i["accepted"],
-                          "pcg_iters": i["pcg_iters"], "ms": [round(m, 3) for m in i["ms"][:7]]}
+                          "pcg_iters": i["pcg_iters"], "ms": [round(m, 3) for m in i["ms"]]}
                          for i in infos[:5]]}
     print(json.dumps(line), flush=True)
     return 0

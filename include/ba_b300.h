@@ -95,7 +95,8 @@ typedef struct {
   int64_t n_cam_act, n_pt_act, n_obs_act;
   float ms[8];        /* device time per phase: [0] extract, [1] linearize, [2] Schur terms,
                          [3] solve (d) in full, [4] the PCG kernel launch alone (inside [3]),
-                         [5] candidate + evaluation, [6] total; [7] unused */
+                         [5] candidate + evaluation, [6] total; [7] the co-visibility
+                         product kernel alone (explicit system, inside [3]) */
 } ba_iter_info;
 
 typedef struct ba_problem ba_problem;

@@ -116,7 +116,7 @@ struct ba_problem {
   unsigned dense_epoch = 0;
   float* dense_b = nullptr;      // [2][n]: scaled right-hand side, scaled solution
   void *Shat = nullptr, *Dblk = nullptr;
-  void* Yhat = nullptr;         // [N][kWStride] D^-1 W M per damping value (explicit system)
+  void* Yhat = nullptr;         // [N + 1][kWStride] D^-1 W M per damping value (explicit system)
   int4* covis_runs = nullptr;   // (camera i, camera j, first pair, count), i < j
   int2* covis_pairs = nullptr;  // point-order observations (k in i, k2 in j) of shared points
   int n_covis_runs = 0;
@@ -146,6 +146,8 @@ struct ba_problem {
   cudaEvent_t ev[8] = {};
   cudaEvent_t evk[2] = {};  // around the PCG kernel launch of the latest solve
   bool evk_valid = false;
+  cudaEvent_t evf[2] = {};  // around the co-visibility product kernel of the latest formation
+  bool evf_valid = false;
 };
 
 namespace {
@@ -418,7 +420,9 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   if (Cf > 0) {
     LAUNCH(5, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
                                (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
-                               Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->form_lanes, pb->num_sms, pb->stream));
+                               Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->form_lanes, pb->num_sms, pb->evf[0],
+                               pb->evf[1], pb->stream));
+    pb->evf_valid = true;
     bool solved = false;
     if constexpr (sizeof(T) == 4) {
       if (pb->dense) {
@@ -651,6 +655,7 @@ ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   r_schur.end();
   NvtxScope r_solve("ba: solve");
   pb->evk_valid = false;
+  pb->evf_valid = false;
   if (pb->fp64) ST(pcg_t<double>(pb, lambda));
   else ST(pcg_t<float>(pb, lambda));
   CU(cudaEventRecord(pb->ev[4], pb->stream));
@@ -692,6 +697,7 @@ ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
     cudaEventElapsedTime(&info->ms[6], pb->ev[0], pb->ev[6]);
     info->ms[4] = 0.f;
     if (pb->evk_valid) cudaEventElapsedTime(&info->ms[4], pb->evk[0], pb->evk[1]);
+    if (pb->evf_valid) cudaEventElapsedTime(&info->ms[7], pb->evf[0], pb->evf[1]);
   }
   if (accept) {
     pb->cur = nxt;
@@ -1359,6 +1365,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   memset(pb->h_sc, 0, sizeof(Scalars));
   for (auto& e : pb->ev) CU(cudaEventCreate(&e));
   for (auto& e : pb->evk) CU(cudaEventCreate(&e));
+  for (auto& e : pb->evf) CU(cudaEventCreate(&e));
 
   // working copies of the initial state (after every upload has landed)
   CU(cudaDeviceSynchronize());
@@ -1381,6 +1388,8 @@ void free_problem(ba_problem* pb) {
   for (auto& e : pb->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : pb->evk)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : pb->evf)
     if (e) cudaEventDestroy(e);
   delete pb;
 }

@@ -304,13 +304,16 @@ __global__ void k_dscale(int Cf, const T* __restrict__ Ud, double* __restrict__ 
 template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
-                          int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaStream_t s) {
+                          int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaEvent_t ev0, cudaEvent_t ev1,
+                          cudaStream_t s) {
   if (Cf <= 0) return cudaSuccess;
   const int n = 9 * Cf;
   k_dscale<T><<<(n + 255) / 256, 256, 0, s>>>(Cf, Ud, dscale);
   if (L.N > 0) k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
   cudaError_t e = cudaMemsetAsync(Shat, 0, sizeof(T) * (size_t)n * n, s);
   if (e != cudaSuccess) return e;
+  // events (nullable) around the co-visibility product kernel
+  if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
   if (n_runs > 0) {
     const int wpb = 4;  // warps per 128-thread block
     if (lanes) {
@@ -324,6 +327,7 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
       k_form_S_runs<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
     }
   }
+  if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
   int nt = (n + 31) / 32;
   k_S_finalize<T><<<dim3(nt, nt), dim3(32, 8), 0, s>>>(Cf, Dblk, dscale, Shat);
   k_S_diag_upper<T><<<Cf, 128, 0, s>>>(Cf, Dblk, dscale, Shat);
@@ -813,7 +817,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
 #define BAB_SINST(T)                                                                                   \
   template cudaError_t launch_form_S<T>(const Layout&, int, const int4*, const int2*, const T*,        \
                                         const T*, const int*, const T*, const T*, double*, int, T*, T*, \
-                                        bool, int, cudaStream_t);                                      \
+                                        bool, int, cudaEvent_t, cudaEvent_t, cudaStream_t);            \
   template size_t spcg_smem_bytes<T>(int, int, int, int, int);                                         \
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \
   template const void* spcg_kernel_ptr<T>();                                                           \
