@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libba_b300.so")
-SOURCES = ["kernels.cu", "pcg.cu", "schur_explicit.cu", "adjoint.cu", "dense_tc.cu", "noalloc.cu", "ba_abi.cu"]
+SOURCES = ["kernels.cu", "pcg.cu", "schur_explicit.cu", "adjoint.cu", "dense_tc.cu", "noalloc.cu", "layout.cu", "ba_abi.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr",
@@ -24,17 +24,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
         newest = max(os.path.getmtime(f) for f in _deps())
         if os.path.getmtime(LIB) >= newest:
             return LIB
-    objs = []
-    for src in SOURCES:
-        obj = os.path.join(CSRC, src.replace(".cu", ".o"))
-        cmd = [NVCC, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    from concurrent.futures import ThreadPoolExecutor
+
+    objs = [os.path.join(CSRC, src.replace(".cu", ".o")) for src in SOURCES]
+
+    def compile_one(i):
+        cmd = [NVCC, *FLAGS, "-c", os.path.join(CSRC, SOURCES[i]), "-o", objs[i]]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         subprocess.check_call(cmd)
-        objs.append(obj)
+
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
+        list(ex.map(compile_one, range(len(SOURCES))))
     tmp = LIB + ".tmp"
     subprocess.check_call([NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp,
-                           *objs, "-lcudart"])
+                           *objs, "-lcudart", "-lpthread"])
     os.replace(tmp, LIB)
     for o in objs:
         os.remove(o)

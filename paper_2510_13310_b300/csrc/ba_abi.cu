@@ -21,6 +21,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
+#include "layout.h"
 
 using namespace bab;
 
@@ -176,68 +177,6 @@ ba_status dalloc_bytes(ba_problem* pb, void** p, size_t bytes) {
 size_t rsz(const ba_problem* pb) { return pb->fp64 ? sizeof(double) : sizeof(float); }
 
 // Stable counting sort of idx by key (keys in [0, nkeys)).
-// Host worker threads of the preprocessing in ba_create: the hardware threads,
-// at most 32, or BA_HOST_THREADS when set.  Every parallel loop writes outputs
-// fixed by its indices alone, so results depend neither on the number of
-// threads nor on their timing.
-int host_threads() {
-  if (const char* env = std::getenv("BA_HOST_THREADS")) {
-    const int v = std::atoi(env);
-    if (v > 0) return std::min(v, 256);
-  }
-  const unsigned h = std::thread::hardware_concurrency();
-  return (int)std::max(1u, std::min(h ? h : 1u, 32u));
-}
-
-// f(t) for t = 0 .. nt-1, piece 0 on the calling thread; a piece whose thread
-// cannot be started runs on the calling thread afterwards
-template <class F>
-void run_pieces(int nt, F&& f) {
-  std::vector<std::thread> th;
-  std::vector<int> inline_pieces;
-  th.reserve(nt > 1 ? nt - 1 : 0);
-  for (int t = 1; t < nt; ++t) {
-    try {
-      th.emplace_back([&f, t] { f(t); });
-    } catch (...) {
-      inline_pieces.push_back(t);
-    }
-  }
-  if (nt > 0) f(0);
-  for (int t : inline_pieces) f(t);
-  for (auto& x : th) x.join();
-}
-
-// f(t, begin, end) over contiguous pieces [n t / nt, n (t+1) / nt) of [0, n),
-// at least `grain` indices per piece
-template <class F>
-void parallel_for(int64_t n, int64_t grain, F&& f) {
-  if (n <= 0) return;
-  const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n / std::max<int64_t>(1, grain)));
-  run_pieces(nt, [&](int t) { f(t, n * t / nt, n * (t + 1) / nt); });
-}
-
-// f(i) for i in [0, n), items handed out one at a time (uneven item costs)
-template <class F>
-void parallel_items(int64_t n, F&& f) {
-  if (n <= 0) return;
-  std::atomic<int64_t> next{0};
-  run_pieces((int)std::min<int64_t>(host_threads(), n), [&](int) {
-    for (int64_t i; (i = next.fetch_add(1, std::memory_order_relaxed)) < n;) f(i);
-  });
-}
-
-// true when every value is finite
-bool all_finite(const double* v, int64_t n) {
-  std::atomic<bool> ok{true};
-  parallel_for(n, 1 << 18, [&](int, int64_t b, int64_t e) {
-    bool good = true;
-    for (int64_t i = b; i < e; ++i) good &= std::isfinite(v[i]);
-    if (!good) ok.store(false, std::memory_order_relaxed);
-  });
-  return ok.load();
-}
-
 // device-resident (device or managed) memory; anything else is read on the host
 bool on_device(const void* p) {
   cudaPointerAttributes a{};
@@ -768,262 +707,42 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   ST(host_view(obs_cam, (size_t)N, dev_oc, c_oc, &h_oc));
   ST(host_view(obs_pt, (size_t)N, dev_op, c_op, &h_op));
   ST(host_view(obs_uv, (size_t)N * 2, dev_uv, c_uv, &h_uv));
-  // ---- validation
-  if (!all_finite(h_cams, (int64_t)C * 9)) { set_error("non-finite camera parameter"); return BA_ERR_INVALID_ARG; }
-  if (!all_finite(h_pts, (int64_t)P * 3)) { set_error("non-finite point"); return BA_ERR_INVALID_ARG; }
-  if (!all_finite(h_uv, (int64_t)N * 2)) { set_error("non-finite observation"); return BA_ERR_INVALID_ARG; }
+  // ---- validation and the observation layout (host threads)
+  ObsLayout lay;
   {
-    std::atomic<int> first_bad{INT_MAX};
-    parallel_for(N, 1 << 16, [&](int, int64_t b, int64_t e) {
-      for (int64_t k = b; k < e; ++k)
-        if (h_oc[k] < 0 || h_oc[k] >= C || h_op[k] < 0 || h_op[k] >= P) {
-          int cur = first_bad.load();
-          while ((int)k < cur && !first_bad.compare_exchange_weak(cur, (int)k)) {
-          }
-          break;
-        }
-    });
-    if (first_bad.load() != INT_MAX) {
-      set_error("observation %d has an index out of range", first_bad.load());
+    std::string msg;
+    if (build_obs_layout(C, P, N, h_cams, h_pts, h_uv, h_oc, h_op, &lay, &msg)) {
+      set_error("%s", msg.c_str());
       return BA_ERR_INVALID_ARG;
     }
   }
-  {
-    // FNV-1a over the sizes and 64K-observation chunk digests (each FNV-1a over
-    // its (camera, point) pairs): identifies the observation structure
-    constexpr int64_t kHashChunk = 1 << 16;
-    auto fnv = [](uint64_t h, int32_t v) {
-      for (int b = 0; b < 4; ++b) {
-        h ^= (uint64_t)((uint32_t)v >> (8 * b) & 0xFFu);
-        h *= 1099511628211ull;
-      }
-      return h;
-    };
-    const int64_t nch = ((int64_t)N + kHashChunk - 1) / kHashChunk;
-    std::vector<uint64_t> dig((size_t)nch);
-    parallel_for(nch, 1, [&](int, int64_t b, int64_t e) {
-      for (int64_t c = b; c < e; ++c) {
-        uint64_t h = 1469598103934665603ull;
-        for (int64_t k = c * kHashChunk; k < std::min<int64_t>(N, (c + 1) * kHashChunk); ++k)
-          h = fnv(fnv(h, h_oc[k]), h_op[k]);
-        dig[c] = h;
-      }
-    });
-    uint64_t h = fnv(fnv(1469598103934665603ull, C), P);
-    for (uint64_t d : dig) h = fnv(fnv(h, (int32_t)(uint32_t)d), (int32_t)(uint32_t)(d >> 32));
-    pb->obs_hash = h;
-  }
+  pb->obs_hash = lay.obs_hash;
   std::vector<uint8_t> h_fixed((size_t)C, 0);
   for (int32_t f : pb->fixed_list) {
     if (f < 0 || f >= C) { set_error("fixed camera %d out of range", f); return BA_ERR_INVALID_ARG; }
     h_fixed[f] = 1;
   }
-  // ---- point order (by point, then camera) and camera order (by camera, then point)
-  std::vector<int> pt_off((size_t)P + 1, 0), cam_off((size_t)C + 1, 0);
-  parallel_for(N, 1 << 16, [&](int, int64_t b, int64_t e) {
-    for (int64_t k = b; k < e; ++k) __atomic_fetch_add(&pt_off[h_op[k] + 1], 1, __ATOMIC_RELAXED);
-  });
-  for (int i = 0; i < P; ++i) pt_off[i + 1] += pt_off[i];
-  for (int p = 0; p < P; ++p)
-    if (pt_off[p + 1] - pt_off[p] > kTileObs) {
-      set_error("point %d has %d observations (limit %d)", p, pt_off[p + 1] - pt_off[p], kTileObs);
-      return BA_ERR_INVALID_ARG;
-    }
-  // po: observations grouped by point (in any order), then each point's
-  // observations sorted by (camera, input index), a unique key
-  std::vector<int> po((size_t)N), co((size_t)N);
-  {
-    std::vector<int> fill(pt_off.begin(), pt_off.end() - 1);
-    parallel_for(N, 1 << 16, [&](int, int64_t b, int64_t e) {
-      for (int64_t k = b; k < e; ++k) po[__atomic_fetch_add(&fill[h_op[k]], 1, __ATOMIC_RELAXED)] = (int)k;
-    });
-  }
-  std::atomic<int> first_dup{INT_MAX};
-  parallel_for(P, 1 << 12, [&](int, int64_t b, int64_t e) {
-    for (int64_t p = b; p < e; ++p) {
-      int* seg = po.data() + pt_off[p];
-      const int n = pt_off[p + 1] - pt_off[p];
-      for (int i = 1; i < n; ++i) {  // insertion sort: at most kTileObs entries
-        const int k = seg[i];
-        const int64_t key = (int64_t)h_oc[k] << 32 | (uint32_t)k;
-        int j = i - 1;
-        for (; j >= 0 && ((int64_t)h_oc[seg[j]] << 32 | (uint32_t)seg[j]) > key; --j) seg[j + 1] = seg[j];
-        seg[j + 1] = k;
-      }
-      for (int i = 1; i < n; ++i)
-        if (h_oc[seg[i]] == h_oc[seg[i - 1]]) {
-          int cur = first_dup.load(), at = pt_off[p] + i;
-          while (at < cur && !first_dup.compare_exchange_weak(cur, at)) {
-          }
-          break;
-        }
-    }
-  });
-  if (first_dup.load() != INT_MAX) {
-    const int i = first_dup.load();
-    set_error("duplicate observation of point %d in camera %d", h_op[po[i]], h_oc[po[i]]);
-    return BA_ERR_INVALID_ARG;
-  }
-  // co: stable counting sort of po by camera (per-piece camera histograms)
-  {
-    const int nt = (int)std::max<int64_t>(
-        1, std::min<int64_t>({(int64_t)host_threads(), (int64_t)N / (1 << 16) + 1,
-                              (int64_t)(1 << 24) / std::max(1, C)}));
-    std::vector<int> hist((size_t)nt * C, 0);
-    auto lo = [&](int t) { return (int64_t)N * t / nt; };
-    run_pieces(nt, [&](int t) {
-      int* hc = hist.data() + (size_t)t * C;
-      for (int64_t i = lo(t); i < lo(t + 1); ++i) hc[h_oc[po[i]]]++;
-    });
-    int run = 0;
-    for (int c = 0; c < C; ++c) {
-      cam_off[c] = run;
-      for (int t = 0; t < nt; ++t) {
-        const int v = hist[(size_t)t * C + c];
-        hist[(size_t)t * C + c] = run;
-        run += v;
-      }
-    }
-    cam_off[C] = run;
-    run_pieces(nt, [&](int t) {
-      int* hc = hist.data() + (size_t)t * C;
-      for (int64_t i = lo(t); i < lo(t + 1); ++i) co[hc[h_oc[po[i]]]++] = po[i];
-    });
-  }
-  // Warp ranges: consecutive whole points with at most 32 observations together,
-  // or one point with more.  Tiles: up to one warp range per PCG warp, at most
-  // kTileObs observations and kTileObs points.
-  std::vector<int> wr_pt{0};  // first point of each warp range
-  {
-    int cur_obs = 0;
-    for (int p = 0; p < P; ++p) {
-      int len = pt_off[p + 1] - pt_off[p];
-      bool open = wr_pt.back() < p;  // the current range already holds points
-      if (open && (len > 32 || cur_obs + len > 32 || p - wr_pt.back() >= 32)) {
-        wr_pt.push_back(p);
-        cur_obs = 0;
-      }
-      cur_obs += len;
-      if (len > 32) {  // a long point closes its own range
-        wr_pt.push_back(p + 1);
-        cur_obs = 0;
-      }
-    }
-    if (wr_pt.back() != P) wr_pt.push_back(P);
-  }
-  const int n_wr_total = (int)wr_pt.size() - 1;
-  std::vector<int> tile_wr{0};  // first warp range of each tile
-  {
-    int t_obs = 0, t_pts = 0, t_wr = 0;
-    for (int r = 0; r < n_wr_total; ++r) {
-      int r_obs = pt_off[wr_pt[r + 1]] - pt_off[wr_pt[r]], r_pts = wr_pt[r + 1] - wr_pt[r];
-      if (t_wr > 0 && (t_wr + 1 > pcg_warps() || t_obs + r_obs > kTileObs || t_pts + r_pts > kTileObs)) {
-        tile_wr.push_back(r);
-        t_obs = t_pts = t_wr = 0;
-      }
-      t_obs += r_obs;
-      t_pts += r_pts;
-      t_wr += 1;
-    }
-    if (tile_wr.back() != n_wr_total) tile_wr.push_back(n_wr_total);
-  }
-  pb->n_tiles = (int)tile_wr.size() - 1;
-  // Per tile: its metadata record (camera of each observation, point offsets,
-  // runs of equal cameras once the tile's observations are sorted by camera,
-  // warp-range offsets, positions in camera order, local point of each
-  // observation) and its descriptor.  Pass 1 sorts each tile's observations by
-  // (camera, local index) and counts the runs; the record offsets follow by a
-  // prefix sum; pass 2 writes the records.
-  const int n_tiles = pb->n_tiles;
-  std::vector<TileDesc> descs((size_t)n_tiles);
-  for (int t = 0; t < n_tiles; ++t) {
-    const int pbeg = wr_pt[tile_wr[t]], pend = wr_pt[tile_wr[t + 1]];
-    TileDesc d{};
-    d.g_row = pb->g_rows;
-    d.w_row = d.obs_begin = pt_off[pbeg];
-    d.n_obs = pt_off[pend] - pt_off[pbeg];
-    d.pt_begin = pbeg;
-    d.n_pts = pend - pbeg;
-    pb->g_rows += (d.n_obs + 3) & ~3;
-    descs[t] = d;
-  }
-  std::vector<uint32_t> skey((size_t)N);  // camera << 8 | tile-local index, sorted per tile
-  parallel_for(n_tiles, 16, [&](int, int64_t b, int64_t e) {
-    for (int64_t t = b; t < e; ++t) {
-      TileDesc& d = descs[t];
-      uint32_t* key = skey.data() + d.obs_begin;
-      for (int i = 0; i < d.n_obs; ++i) key[i] = (uint32_t)h_oc[po[d.obs_begin + i]] << 8 | (uint32_t)i;
-      std::sort(key, key + d.n_obs);
-      int runs = 0;
-      for (int j = 0; j < d.n_obs; ++j) runs += (j == 0 || (key[j] >> 8) != (key[j - 1] >> 8));
-      d.n_runs = runs;
-    }
-  });
-  size_t meta_total = 0;
-  for (int t = 0; t < n_tiles; ++t) {
-    descs[t].meta_off = (int)meta_total;
-    meta_total += (size_t)meta_bytes_of(descs[t].n_obs, descs[t].n_pts, descs[t].n_runs);
-  }
-  if (meta_total >= (size_t)INT_MAX) {
-    set_error("tile metadata too large");
-    return BA_ERR_INVALID_ARG;
-  }
-  std::vector<unsigned char> meta(meta_total);
-  parallel_for(n_tiles, 16, [&](int, int64_t b, int64_t e) {
-    std::vector<int> cams_t, poff, wr;
-    std::vector<unsigned> runs;
-    std::vector<uint8_t> cperm, lid;
-    for (int64_t t = b; t < e; ++t) {
-      const TileDesc& d = descs[t];
-      const int r0 = tile_wr[t], r1 = tile_wr[t + 1], ob = d.obs_begin, nobs = d.n_obs, npts = d.n_pts;
-      cams_t.resize(nobs);
-      poff.resize(npts + 1);
-      wr.resize(r1 - r0 + 1);
-      cperm.resize(nobs);
-      lid.resize(nobs);
-      runs.clear();
-      for (int i = 0; i < nobs; ++i) cams_t[i] = h_oc[po[ob + i]];
-      for (int j = 0; j <= npts; ++j) poff[j] = pt_off[d.pt_begin + j] - ob;
-      for (int j = 0; j < npts; ++j)
-        for (int i = poff[j]; i < poff[j + 1]; ++i) lid[i] = (uint8_t)j;
-      for (int r = r0; r <= r1; ++r) wr[r - r0] = pt_off[wr_pt[r]] - ob;
-      const uint32_t* key = skey.data() + ob;
-      for (int j = 0; j < nobs; ++j) {
-        cperm[j] = (uint8_t)(key[j] & 0xFFu);
-        if (j == 0 || (key[j] >> 8) != (key[j - 1] >> 8)) runs.push_back((key[j] >> 8) << 8 | (unsigned)j);
-      }
-      build_tile_meta(nobs, npts, d.n_runs, r1 - r0, cams_t.data(), poff.data(), runs.data(), wr.data(),
-                      cperm.data(), lid.data(), meta.data() + d.meta_off);
-    }
-  });
+  pb->n_tiles = lay.n_tiles;
+  pb->g_rows = lay.g_rows;
   pb->w_rows = N;
-  // chunks: pieces of one camera's observations
-  std::vector<int> chunk_obs{0}, chunk_cam, cam_chunk((size_t)C + 1, 0);
-  for (int c = 0; c < C; ++c) {
-    for (int b = cam_off[c]; b < cam_off[c + 1]; b += kChunkObs) {
-      chunk_cam.push_back(c);
-      chunk_obs.push_back(std::min(b + kChunkObs, cam_off[c + 1]));
-    }
-    cam_chunk[c + 1] = (int)chunk_cam.size();
-  }
-  pb->n_chunks = (int)chunk_cam.size();
+  pb->n_chunks = (int)lay.chunk_cam.size();
 
   // ---- device buffers
-  auto up_int = [&](int** d, const std::vector<int>& h) -> ba_status {
-    ST(dalloc(pb, d, h.size()));
-    if (!h.empty()) CU(cudaMemcpy(*d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice));
+  auto up_int = [&](int** d, const int* h, size_t n) -> ba_status {
+    ST(dalloc(pb, d, n));
+    if (n) CU(cudaMemcpy(*d, h, sizeof(int) * n, cudaMemcpyHostToDevice));
     return BA_OK;
   };
-  ST(up_int(&pb->po_orig, po));
-  ST(up_int(&pb->pt_off, pt_off));
-  ST(up_int(&pb->chunk_obs, chunk_obs));
-  ST(up_int(&pb->chunk_cam, chunk_cam));
-  ST(up_int(&pb->cam_chunk, cam_chunk));
-  ST(dalloc(pb, &pb->descs, descs.size()));
-  if (!descs.empty())
-    CU(cudaMemcpy(pb->descs, descs.data(), sizeof(TileDesc) * descs.size(), cudaMemcpyHostToDevice));
-  ST(dalloc(pb, &pb->meta, meta.size()));
-  if (!meta.empty()) CU(cudaMemcpy(pb->meta, meta.data(), meta.size(), cudaMemcpyHostToDevice));
+  ST(up_int(&pb->po_orig, lay.po.data(), (size_t)N));
+  ST(up_int(&pb->pt_off, lay.pt_off.data(), lay.pt_off.size()));
+  ST(up_int(&pb->chunk_obs, lay.chunk_obs.data(), lay.chunk_obs.size()));
+  ST(up_int(&pb->chunk_cam, lay.chunk_cam.data(), lay.chunk_cam.size()));
+  ST(up_int(&pb->cam_chunk, lay.cam_chunk.data(), lay.cam_chunk.size()));
+  ST(dalloc(pb, &pb->descs, lay.descs.size()));
+  if (!lay.descs.empty())
+    CU(cudaMemcpy(pb->descs, lay.descs.data(), sizeof(TileDesc) * lay.descs.size(), cudaMemcpyHostToDevice));
+  ST(dalloc(pb, &pb->meta, lay.meta.size()));
+  if (lay.meta.size()) CU(cudaMemcpy(pb->meta, lay.meta.data(), lay.meta.size(), cudaMemcpyHostToDevice));
   // per-observation arrays in both orders, gathered on the device from the
   // caller's arrays (device inputs in place, host inputs through one scratch)
   ST(dalloc(pb, &pb->po_cam, (size_t)N));
@@ -1072,7 +791,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     CU(cudaDeviceSynchronize());
     int* d_co = (int*)(base + 32 * n);
     int* d_pos = (int*)(base + 36 * n);
-    CU(cudaMemcpyAsync(d_co, co.data(), 4 * n, cudaMemcpyHostToDevice, pb->stream));
+    CU(cudaMemcpyAsync(d_co, lay.co.data(), 4 * n, cudaMemcpyHostToDevice, pb->stream));
     if (pb->fp64)
       LAUNCH(2, launch_obs_layout<double>(N, d_oc, d_op, d_uv, d_depth, pb->po_orig, d_co, d_pos, pb->po_cam, pb->po_pt,
                                    pb->po_wrow, pb->po_uv64, pb->po_tau64, nullptr, nullptr, pb->co_pt,
@@ -1253,52 +972,22 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * n_max));
     ST(dalloc_bytes(pb, &pb->Yhat, R * (size_t)kWStride * ((size_t)N + 1)));
     // co-visibility runs: every pair of observations of one point in cameras i < j,
-    // grouped by (i, j), ascending in point within a run.  Row i (first camera i)
-    // is built by one thread from camera i's observations in camera order, which
-    // visits the points in ascending order; the partner observations of a point
-    // follow it in point order (cameras ascending).
+    // grouped by (i, j), ascending in point within a run (host threads)
     {
-      std::vector<int> po_cam_h((size_t)N), pos_in_po((size_t)N);
-      parallel_for(N, 1 << 16, [&](int, int64_t b, int64_t e) {
-        for (int64_t i = b; i < e; ++i) {
-          po_cam_h[i] = h_oc[po[i]];
-          pos_in_po[po[i]] = (int)i;
-        }
-      });
-      auto row_pairs = [&](int i, auto&& emit) {
-        for (int q = cam_off[i]; q < cam_off[i + 1]; ++q) {
-          const int kin = co[q], k = pos_in_po[kin], pend = pt_off[h_op[kin] + 1];
-          for (int k2 = k + 1; k2 < pend; ++k2) emit(k, k2, po_cam_h[k2]);
-        }
-      };
-      std::vector<long long> cnt((size_t)C * C + 1, 0);
-      parallel_items(C, [&](int64_t i) {
-        long long* row = cnt.data() + 1 + (size_t)i * C;
-        row_pairs((int)i, [&](int, int, int j) { row[j]++; });
-      });
-      for (size_t q = 0; q < (size_t)C * C; ++q) cnt[q + 1] += cnt[q];
-      const size_t npairs = (size_t)cnt[(size_t)C * C];
-      if (npairs >= (1ull << 31)) {
-        set_error("too many co-visible observation pairs (%zu) for the explicit system", npairs);
+      CovisRuns cv;
+      std::string msg;
+      if (build_covis_runs(lay, C, N, &cv, &msg)) {
+        set_error("%s", msg.c_str());
         return BA_ERR_INVALID_ARG;
       }
-      std::unique_ptr<int2[]> hp(new int2[std::max<size_t>(npairs, 1)]);
-      parallel_items(C, [&](int64_t i) {
-        std::vector<long long> fill(cnt.begin() + (size_t)i * C, cnt.begin() + (size_t)(i + 1) * C);
-        row_pairs((int)i, [&](int k, int k2, int j) { hp[fill[j]++] = make_int2(k, k2); });
-      });
-      std::vector<int4> hr;
-      for (int i = 0; i < C; ++i)
-        for (int j = i + 1; j < C; ++j) {
-          size_t q = (size_t)i * C + j;
-          if (cnt[q + 1] > cnt[q]) hr.push_back(make_int4(i, j, (int)cnt[q], (int)(cnt[q + 1] - cnt[q])));
-        }
+      const size_t npairs = cv.npairs;
+      const std::vector<int4>& hr = cv.runs;
       pb->n_covis_runs = (int)hr.size();
       // one lane per run when there are enough runs for four blocks of 128 lanes
       // per SM and runs are short (a warp per run would idle in its reduction)
       pb->form_lanes = (long long)hr.size() >= 4LL * 128 * pb->num_sms && npairs < 128 * hr.size();
       ST(dalloc(pb, &pb->covis_pairs, npairs));
-      if (npairs) CU(cudaMemcpy(pb->covis_pairs, hp.get(), sizeof(int2) * npairs, cudaMemcpyHostToDevice));
+      if (npairs) CU(cudaMemcpy(pb->covis_pairs, cv.pairs.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice));
       ST(dalloc(pb, &pb->covis_runs, hr.size()));
       if (!hr.empty()) CU(cudaMemcpy(pb->covis_runs, hr.data(), sizeof(int4) * hr.size(), cudaMemcpyHostToDevice));
     }

@@ -222,12 +222,7 @@ size_t pcg_smem_bytes(int n, int C, int stages, int own_max, int recompute, int 
 template <typename T>
 const void* pcg_kernel_ptr();
 int pcg_threads();
-int pcg_warps();
 int pcg_max_stages();
-int meta_bytes_of(int n_obs, int n_pts, int n_runs);
-void build_tile_meta(int n_obs, int n_pts, int n_runs, int n_wr, const int* cams, const int* poff,
-                     const unsigned* runs, const int* wr, const uint8_t* cperm, const uint8_t* lid,
-                     unsigned char* out);
 template <typename T>
 cudaError_t launch_pred_cams(int Cf, const int* cam_map, const T* x, const T* Ug, const T* dampc,
                              double lambda, double* pred_parts, int offset, cudaStream_t s);
