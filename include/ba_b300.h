@@ -242,6 +242,19 @@ ba_status ba_dense_cholesky(void* stream, int64_t n, const float* A, int64_t lda
  * through device memory and the context stays usable), or BA_ERR_CUDA. */
 ba_status ba_selftest_wait_timeout(void* stream, double timeout_ms);
 
+/* Diagnostic of ba_create's observation layout: builds it on the device (as
+ * ba_create does) and with the host reference builder, from host arrays (the
+ * arguments of ba_create; depth is not needed), and compares every array:
+ * *mismatch = 0 when they are identical bit for bit, else a bitmask: 1 orders,
+ * 2 offsets, 4 tile descriptors, 8 tile records, 16 camera chunks, 32 structure
+ * hash, 64 co-visibility runs (with_covis != 0), 128 the two disagree on
+ * rejecting the input.  Invalid input is not an error here (both builders must
+ * reject it alike).  Returns BA_OK, BA_ERR_INVALID_ARG (bad arguments),
+ * BA_ERR_OOM or BA_ERR_CUDA. */
+ba_status ba_selftest_layout(int64_t n_cams, const double* cams, int64_t n_pts, const double* pts, int64_t n_obs,
+                             const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv, int with_covis,
+                             int* mismatch);
+
 /* Number of this library's kernels launched since creation (counts launches). */
 int64_t ba_kernel_launches(const ba_problem* pb);
 

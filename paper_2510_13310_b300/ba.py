@@ -26,7 +26,7 @@ BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT, BA_SOLVER_DENSE = 0, 1, 
 EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
            "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
-           "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout",
+           "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout", "ba_selftest_layout",
            "ba_kernel_launches", "ba_solver_kind", "ba_destroy",
            "ba_status_string", "ba_last_error")
 
@@ -95,6 +95,8 @@ def lib():
         L.ba_get_state.argtypes = [vp, vp, ct.POINTER(ct.c_size_t)]
         L.ba_set_state.argtypes = [vp, vp, ct.c_size_t]
         L.ba_selftest_wait_timeout.argtypes = [vp, ct.c_double]
+        L.ba_selftest_layout.argtypes = [ct.c_int64, vp, ct.c_int64, vp, ct.c_int64, vp, vp, vp, ct.c_int,
+                                         ct.POINTER(ct.c_int)]
         L.ba_tc_gemm_nt.argtypes = [vp, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_float, vp, ct.c_int64, vp,
                                     ct.c_int64, ct.c_float, vp, ct.c_int64]
         L.ba_dense_cholesky.argtypes = [vp, ct.c_int64, vp, ct.c_int64, vp, ct.c_int64, ct.POINTER(ct.c_int)]
@@ -105,7 +107,7 @@ def lib():
         for f in ("ba_create", "ba_lm_step", "ba_solve", "ba_get_params", "ba_set_params",
                   "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped", "ba_eval_cost",
                   "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
-                  "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout"):
+                  "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout", "ba_selftest_layout"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -170,6 +172,20 @@ class _Arr:
     @property
     def p(self):
         return ct.c_void_p(self.ptr)
+
+
+def selftest_layout(cams, pts, obs_cam, obs_pt, obs_uv, with_covis=True):
+    """ba_selftest_layout on host arrays: the mismatch bitmask (0 = the device
+    layout equals the host reference layout bit for bit)."""
+    L = lib()
+    arrs = [_Arr(cams, np.float64), _Arr(pts, np.float64), _Arr(obs_cam, np.int32), _Arr(obs_pt, np.int32),
+            _Arr(obs_uv, np.float64)]
+    mm = ct.c_int(-1)
+    _check(L.ba_selftest_layout(int(np.prod(arrs[0].obj.shape)) // 9, arrs[0].p,
+                                int(np.prod(arrs[1].obj.shape)) // 3, arrs[1].p, int(np.prod(arrs[2].obj.shape)),
+                                arrs[2].p, arrs[3].p, arrs[4].p, int(bool(with_covis)), ct.byref(mm)),
+           "ba_selftest_layout")
+    return mm.value
 
 
 def _stream_handle(stream):

@@ -22,6 +22,7 @@
 
 #include "internal.h"
 #include "layout.h"
+#include "layout_dev.h"
 
 using namespace bab;
 
@@ -198,17 +199,6 @@ struct DevScratch {
   }
 };
 
-// the input array at src (n elements) readable on the host: src itself, or a
-// copy in store when src is device memory
-template <typename T>
-ba_status host_view(const T* src, size_t n, bool dev, std::vector<T>& store, const T** out) {
-  *out = src;
-  if (!dev || n == 0) return BA_OK;
-  store.resize(n);
-  CU(cudaMemcpy(store.data(), src, sizeof(T) * n, cudaMemcpyDeviceToHost));
-  *out = store.data();
-  return BA_OK;
-}
 
 bool finite_opts(const ba_options* o) {
   return std::isfinite(o->cx) && std::isfinite(o->cy) && std::isfinite(o->huber_delta) &&
@@ -691,65 +681,81 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   CU(cudaGetDevice(&pb->device));
   CU(cudaDeviceGetAttribute(&pb->num_sms, cudaDevAttrMultiProcessorCount, pb->device));
 
-  // ---- host views of the inputs: host memory is read in place, device memory
-  // is copied (the orderings are built on the host)
+  // ---- inputs on the device: device arrays are used in place, host arrays are
+  // uploaded once into scratch
+  const bool dev_cams = C && on_device(cams), dev_pts = P && on_device(pts);
   const bool dev_oc = N && on_device(obs_cam), dev_op = N && on_device(obs_pt);
   const bool dev_uv = N && on_device(obs_uv), dev_depth = N && on_device(depth);
   // inputs written by device work on any stream are complete before they are read
-  if (dev_oc || dev_op || dev_uv || dev_depth || (C && on_device(cams)) || (P && on_device(pts)))
-    CU(cudaDeviceSynchronize());
-  std::vector<double> c_cams, c_pts, c_uv;
-  std::vector<int32_t> c_oc, c_op;
-  const double *h_cams = cams, *h_pts = pts, *h_uv = obs_uv;
-  const int32_t *h_oc = obs_cam, *h_op = obs_pt;
-  ST(host_view(cams, (size_t)C * 9, C && on_device(cams), c_cams, &h_cams));
-  ST(host_view(pts, (size_t)P * 3, P && on_device(pts), c_pts, &h_pts));
-  ST(host_view(obs_cam, (size_t)N, dev_oc, c_oc, &h_oc));
-  ST(host_view(obs_pt, (size_t)N, dev_op, c_op, &h_op));
-  ST(host_view(obs_uv, (size_t)N * 2, dev_uv, c_uv, &h_uv));
-  // ---- validation and the observation layout (host threads)
-  ObsLayout lay;
+  if (dev_cams || dev_pts || dev_oc || dev_op || dev_uv || dev_depth) CU(cudaDeviceSynchronize());
+  DevScratch scratch;
+  const double *d_cams = cams, *d_pts = pts, *d_uv = obs_uv, *d_depth = depth;
+  const int32_t *d_oc = obs_cam, *d_op = obs_pt;
   {
-    std::string msg;
-    if (build_obs_layout(C, P, N, h_cams, h_pts, h_uv, h_oc, h_op, &lay, &msg)) {
-      set_error("%s", msg.c_str());
-      return BA_ERR_INVALID_ARG;
+    struct Up {
+      const void* src;
+      size_t bytes;
+      bool dev;
+      const void** dst;
+    } ups[] = {{cams, sizeof(double) * 9 * (size_t)C, dev_cams, (const void**)&d_cams},
+               {pts, sizeof(double) * 3 * (size_t)P, dev_pts, (const void**)&d_pts},
+               {obs_uv, sizeof(double) * 2 * (size_t)N, dev_uv, (const void**)&d_uv},
+               {depth, sizeof(double) * (size_t)N, dev_depth, (const void**)&d_depth},
+               {obs_cam, sizeof(int32_t) * (size_t)N, dev_oc, (const void**)&d_oc},
+               {obs_pt, sizeof(int32_t) * (size_t)N, dev_op, (const void**)&d_op}};
+    size_t total = 0;
+    for (const Up& u : ups)
+      if (!u.dev && u.bytes) total += (u.bytes + 255) / 256 * 256;
+    if (total) {
+      CU(cudaMalloc(&scratch.p, total));
+      char* at = static_cast<char*>(scratch.p);
+      for (const Up& u : ups)
+        if (!u.dev && u.bytes) {
+          CU(cudaMemcpyAsync(at, u.src, u.bytes, cudaMemcpyHostToDevice, pb->stream));
+          *u.dst = at;
+          at += (u.bytes + 255) / 256 * 256;
+        }
     }
   }
-  pb->obs_hash = lay.obs_hash;
+  // ---- validation and the observation layout (device; the grouping of points
+  // into tiles on the host)
+  auto dev_alloc = [pb](size_t bytes) -> void* {
+    void* q = nullptr;
+    return dalloc_bytes(pb, &q, bytes) == BA_OK ? q : nullptr;
+  };
+  DevLayout dl;
+  {
+    std::string msg;
+    const int rc = build_obs_layout_dev(C, P, N, d_cams, d_pts, d_uv, d_oc, d_op, dev_alloc, pb->stream, &dl, &msg);
+    if (rc) {
+      set_error("%s", msg.c_str());
+      return rc == 1 ? BA_ERR_INVALID_ARG : rc == 3 ? BA_ERR_OOM : BA_ERR_CUDA;
+    }
+  }
+  pb->obs_hash = dl.obs_hash;
   std::vector<uint8_t> h_fixed((size_t)C, 0);
   for (int32_t f : pb->fixed_list) {
     if (f < 0 || f >= C) { set_error("fixed camera %d out of range", f); return BA_ERR_INVALID_ARG; }
     h_fixed[f] = 1;
   }
-  pb->n_tiles = lay.n_tiles;
-  pb->g_rows = lay.g_rows;
+  pb->n_tiles = dl.n_tiles;
+  pb->g_rows = dl.g_rows;
   pb->w_rows = N;
-  pb->n_chunks = (int)lay.chunk_cam.size();
+  pb->n_chunks = dl.n_chunks;
+  pb->po_orig = dl.po;
+  pb->pt_off = dl.pt_off;
+  pb->chunk_obs = dl.chunk_obs;
+  pb->chunk_cam = dl.chunk_cam;
+  pb->cam_chunk = dl.cam_chunk;
+  pb->descs = dl.descs;
+  pb->meta = dl.meta;
+  pb->po_cam = dl.po_cam;
+  pb->po_pt = dl.po_pt;
+  pb->co_po = dl.co_po;
 
-  // ---- device buffers
-  auto up_int = [&](int** d, const int* h, size_t n) -> ba_status {
-    ST(dalloc(pb, d, n));
-    if (n) CU(cudaMemcpy(*d, h, sizeof(int) * n, cudaMemcpyHostToDevice));
-    return BA_OK;
-  };
-  ST(up_int(&pb->po_orig, lay.po.data(), (size_t)N));
-  ST(up_int(&pb->pt_off, lay.pt_off.data(), lay.pt_off.size()));
-  ST(up_int(&pb->chunk_obs, lay.chunk_obs.data(), lay.chunk_obs.size()));
-  ST(up_int(&pb->chunk_cam, lay.chunk_cam.data(), lay.chunk_cam.size()));
-  ST(up_int(&pb->cam_chunk, lay.cam_chunk.data(), lay.cam_chunk.size()));
-  ST(dalloc(pb, &pb->descs, lay.descs.size()));
-  if (!lay.descs.empty())
-    CU(cudaMemcpy(pb->descs, lay.descs.data(), sizeof(TileDesc) * lay.descs.size(), cudaMemcpyHostToDevice));
-  ST(dalloc(pb, &pb->meta, lay.meta.size()));
-  if (lay.meta.size()) CU(cudaMemcpy(pb->meta, lay.meta.data(), lay.meta.size(), cudaMemcpyHostToDevice));
-  // per-observation arrays in both orders, gathered on the device from the
-  // caller's arrays (device inputs in place, host inputs through one scratch)
-  ST(dalloc(pb, &pb->po_cam, (size_t)N));
-  ST(dalloc(pb, &pb->po_pt, (size_t)N));
+  // ---- per-observation arrays in both orders, gathered on the device
   ST(dalloc(pb, &pb->po_wrow, (size_t)N));
   ST(dalloc(pb, &pb->co_pt, (size_t)N));
-  ST(dalloc(pb, &pb->co_po, (size_t)N));
   ST(dalloc(pb, &pb->po_uv64, (size_t)2 * N));
   ST(dalloc(pb, &pb->po_tau64, (size_t)N));
   const size_t Rw = pb->fp64 ? sizeof(double) : sizeof(float);
@@ -762,46 +768,15 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   }
   ST(dalloc_bytes(pb, &pb->co_uvw, Rw * 2 * (size_t)N));
   ST(dalloc_bytes(pb, &pb->co_tauw, Rw * (size_t)N));
-  DevScratch scratch;
   if (N) {
-    const size_t n = (size_t)N;
-    CU(cudaMalloc(&scratch.p, 40 * n));
-    char* base = (char*)scratch.p;
-    const double* d_uv = obs_uv;
-    const double* d_depth = depth;
-    const int32_t* d_oc = obs_cam;
-    const int32_t* d_op = obs_pt;
-    if (!dev_uv) {
-      CU(cudaMemcpyAsync(base, obs_uv, 16 * n, cudaMemcpyHostToDevice, pb->stream));
-      d_uv = (const double*)base;
-    }
-    if (!dev_depth) {
-      CU(cudaMemcpyAsync(base + 16 * n, depth, 8 * n, cudaMemcpyHostToDevice, pb->stream));
-      d_depth = (const double*)(base + 16 * n);
-    }
-    if (!dev_oc) {
-      CU(cudaMemcpyAsync(base + 24 * n, obs_cam, 4 * n, cudaMemcpyHostToDevice, pb->stream));
-      d_oc = (const int32_t*)(base + 24 * n);
-    }
-    if (!dev_op) {
-      CU(cudaMemcpyAsync(base + 28 * n, obs_pt, 4 * n, cudaMemcpyHostToDevice, pb->stream));
-      d_op = (const int32_t*)(base + 28 * n);
-    }
-    // the synchronous uploads above may still be in flight when they return
-    CU(cudaDeviceSynchronize());
-    int* d_co = (int*)(base + 32 * n);
-    int* d_pos = (int*)(base + 36 * n);
-    CU(cudaMemcpyAsync(d_co, lay.co.data(), 4 * n, cudaMemcpyHostToDevice, pb->stream));
     if (pb->fp64)
-      LAUNCH(2, launch_obs_layout<double>(N, d_oc, d_op, d_uv, d_depth, pb->po_orig, d_co, d_pos, pb->po_cam, pb->po_pt,
-                                   pb->po_wrow, pb->po_uv64, pb->po_tau64, nullptr, nullptr, pb->co_pt,
-                                   pb->co_po, (double*)pb->co_uvw, (double*)pb->co_tauw, pb->stream));
+      LAUNCH(2, launch_obs_layout<double>(N, d_uv, d_depth, dl.po, dl.co, dl.co_po, dl.po_pt, pb->po_wrow,
+                                          pb->po_uv64, pb->po_tau64, nullptr, nullptr, pb->co_pt,
+                                          (double*)pb->co_uvw, (double*)pb->co_tauw, pb->stream));
     else
-      LAUNCH(2, launch_obs_layout<float>(N, d_oc, d_op, d_uv, d_depth, pb->po_orig, d_co, d_pos, pb->po_cam, pb->po_pt,
-                                  pb->po_wrow, pb->po_uv64, pb->po_tau64, (float*)pb->po_uvw,
-                                  (float*)pb->po_tauw, pb->co_pt, pb->co_po, (float*)pb->co_uvw,
-                                  (float*)pb->co_tauw, pb->stream));
-    CU(cudaStreamSynchronize(pb->stream));
+      LAUNCH(2, launch_obs_layout<float>(N, d_uv, d_depth, dl.po, dl.co, dl.co_po, dl.po_pt, pb->po_wrow,
+                                         pb->po_uv64, pb->po_tau64, (float*)pb->po_uvw, (float*)pb->po_tauw,
+                                         pb->co_pt, (float*)pb->co_uvw, (float*)pb->co_tauw, pb->stream));
   }
   ST(dalloc(pb, &pb->cam_fixed, (size_t)C));
   if (C) CU(cudaMemcpy(pb->cam_fixed, h_fixed.data(), (size_t)C, cudaMemcpyHostToDevice));
@@ -853,8 +828,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     CU(cudaMemset(pb->ptsw[s], 0, R * ((size_t)P + 2) * 4));
     ST(dalloc(pb, &pb->bits[s], (size_t)N));
   }
-  if (C) CU(cudaMemcpy(pb->cams64[0], cams, sizeof(double) * 9 * (size_t)C, cudaMemcpyDefault));
-  if (P) CU(cudaMemcpy(pb->pts64[0], pts, sizeof(double) * 3 * (size_t)P, cudaMemcpyDefault));
+  if (C) CU(cudaMemcpyAsync(pb->cams64[0], d_cams, sizeof(double) * 9 * (size_t)C, cudaMemcpyDeviceToDevice, pb->stream));
+  if (P) CU(cudaMemcpyAsync(pb->pts64[0], d_pts, sizeof(double) * 3 * (size_t)P, cudaMemcpyDeviceToDevice, pb->stream));
   ST(dalloc(pb, &pb->alive, (size_t)N));
   ST(dalloc(pb, &pb->valid, (size_t)N));
   ST(dalloc(pb, &pb->obs_act, (size_t)N));
@@ -972,24 +947,21 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * n_max));
     ST(dalloc_bytes(pb, &pb->Yhat, R * (size_t)kWStride * ((size_t)N + 1)));
     // co-visibility runs: every pair of observations of one point in cameras i < j,
-    // grouped by (i, j), ascending in point within a run (host threads)
+    // grouped by (i, j), ascending in point within a run (device)
     {
-      CovisRuns cv;
+      DevCovis cv;
       std::string msg;
-      if (build_covis_runs(lay, C, N, &cv, &msg)) {
+      const int rc = build_covis_runs_dev(dl, C, N, dev_alloc, pb->stream, &cv, &msg);
+      if (rc) {
         set_error("%s", msg.c_str());
-        return BA_ERR_INVALID_ARG;
+        return rc == 1 ? BA_ERR_INVALID_ARG : rc == 3 ? BA_ERR_OOM : BA_ERR_CUDA;
       }
-      const size_t npairs = cv.npairs;
-      const std::vector<int4>& hr = cv.runs;
-      pb->n_covis_runs = (int)hr.size();
+      pb->covis_pairs = cv.pairs;
+      pb->covis_runs = cv.runs;
+      pb->n_covis_runs = cv.n_runs;
       // one lane per run when there are enough runs for four blocks of 128 lanes
       // per SM and runs are short (a warp per run would idle in its reduction)
-      pb->form_lanes = (long long)hr.size() >= 4LL * 128 * pb->num_sms && npairs < 128 * hr.size();
-      ST(dalloc(pb, &pb->covis_pairs, npairs));
-      if (npairs) CU(cudaMemcpy(pb->covis_pairs, cv.pairs.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice));
-      ST(dalloc(pb, &pb->covis_runs, hr.size()));
-      if (!hr.empty()) CU(cudaMemcpy(pb->covis_runs, hr.data(), sizeof(int4) * hr.size(), cudaMemcpyHostToDevice));
+      pb->form_lanes = (long long)cv.n_runs >= 4LL * 128 * pb->num_sms && cv.npairs < 128 * (size_t)cv.n_runs;
     }
     ST(dalloc(pb, &pb->dscale, (size_t)2 * n_max));  // D, then 1/D in the working precision
     ST(dalloc_bytes(pb, &pb->Dblk, R * 45 * (size_t)C));
@@ -1360,6 +1332,95 @@ ba_status ba_get_active(ba_problem* pb, uint8_t* cam_mask, uint8_t* pt_mask, uin
     cudaFree(tmp);
     CU(e);
   }
+  return BA_OK;
+}
+
+ba_status ba_selftest_layout(int64_t n_cams, const double* cams, int64_t n_pts, const double* pts, int64_t n_obs,
+                             const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv, int with_covis,
+                             int* mismatch) {
+  if (!mismatch || n_cams < 0 || n_pts < 0 || n_obs < 0 || n_cams >= (1LL << 24) || n_pts >= (1LL << 30) ||
+      n_obs >= (1LL << 31) - 1024 || (n_cams && !cams) || (n_pts && !pts) ||
+      (n_obs && (!obs_cam || !obs_pt || !obs_uv))) {
+    set_error("ba_selftest_layout: invalid arguments");
+    return BA_ERR_INVALID_ARG;
+  }
+  *mismatch = 0;
+  const int C = (int)n_cams, P = (int)n_pts, N = (int)n_obs;
+  // reference: the host builder
+  ObsLayout H;
+  CovisRuns hc;
+  std::string herr, derr;
+  int hrc = build_obs_layout(C, P, N, cams, pts, obs_uv, obs_cam, obs_pt, &H, &herr);
+  if (!hrc && with_covis) hrc = build_covis_runs(H, C, N, &hc, &herr);
+  // device builder on uploaded copies; its arrays are freed here
+  std::vector<void*> owned;
+  struct Free {
+    std::vector<void*>& v;
+    ~Free() {
+      cudaDeviceSynchronize();
+      for (void* q : v) cudaFree(q);
+    }
+  } free_all{owned};
+  auto alloc = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    owned.push_back(q);
+    return q;
+  };
+  auto up = [&](const void* src, size_t bytes) -> void* {
+    void* q = alloc(bytes);
+    if (q && bytes) cudaMemcpy(q, src, bytes, cudaMemcpyHostToDevice);
+    return q;
+  };
+  const double* d_cams = (const double*)up(cams, sizeof(double) * 9 * (size_t)C);
+  const double* d_pts = (const double*)up(pts, sizeof(double) * 3 * (size_t)P);
+  const double* d_uv = (const double*)up(obs_uv, sizeof(double) * 2 * (size_t)N);
+  const int32_t* d_oc = (const int32_t*)up(obs_cam, sizeof(int32_t) * (size_t)N);
+  const int32_t* d_op = (const int32_t*)up(obs_pt, sizeof(int32_t) * (size_t)N);
+  if (!d_cams || !d_pts || !d_uv || !d_oc || !d_op) {
+    set_error("ba_selftest_layout: device allocation failed");
+    return BA_ERR_OOM;
+  }
+  cudaStream_t st = nullptr;
+  DevLayout D;
+  DevCovis dc;
+  int drc = build_obs_layout_dev(C, P, N, d_cams, d_pts, d_uv, d_oc, d_op, alloc, st, &D, &derr);
+  if (!drc && with_covis) drc = build_covis_runs_dev(D, C, N, alloc, st, &dc, &derr);
+  if (drc >= 2) {
+    set_error("ba_selftest_layout: %s", derr.c_str());
+    return drc == 3 ? BA_ERR_OOM : BA_ERR_CUDA;
+  }
+  if (hrc || drc) {  // both must reject the input with the same message
+    if (hrc != drc || herr != derr) *mismatch |= 128;
+    return BA_OK;
+  }
+  auto same = [&](const void* dev, const void* host, size_t bytes) {
+    if (!bytes) return true;
+    std::vector<unsigned char> tmp(bytes);
+    if (cudaMemcpy(tmp.data(), dev, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    return memcmp(tmp.data(), host, bytes) == 0;
+  };
+  const size_t n4 = sizeof(int) * (size_t)N;
+  if (!same(D.po, H.po.data(), n4) || !same(D.co, H.co.data(), n4) || !same(D.co_po, H.co_po.data(), n4) ||
+      !same(D.po_cam, H.po_cam.data(), n4) || !same(D.po_pt, H.po_pt.data(), n4))
+    *mismatch |= 1;
+  if (!same(D.pt_off, H.pt_off.data(), sizeof(int) * H.pt_off.size()) ||
+      !same(D.cam_off, H.cam_off.data(), sizeof(int) * H.cam_off.size()))
+    *mismatch |= 2;
+  if (D.n_tiles != H.n_tiles || D.g_rows != H.g_rows ||
+      !same(D.descs, H.descs.data(), sizeof(TileDesc) * H.descs.size()))
+    *mismatch |= 4;
+  if (D.meta_bytes != H.meta.size() || !same(D.meta, H.meta.data(), H.meta.size())) *mismatch |= 8;
+  if (D.n_chunks != (int)H.chunk_cam.size() ||
+      !same(D.chunk_obs, H.chunk_obs.data(), sizeof(int) * H.chunk_obs.size()) ||
+      !same(D.chunk_cam, H.chunk_cam.data(), sizeof(int) * H.chunk_cam.size()) ||
+      !same(D.cam_chunk, H.cam_chunk.data(), sizeof(int) * H.cam_chunk.size()))
+    *mismatch |= 16;
+  if (D.obs_hash != H.obs_hash) *mismatch |= 32;
+  if (with_covis && (dc.npairs != hc.npairs || dc.n_runs != (int)hc.runs.size() ||
+                     !same(dc.runs, hc.runs.data(), sizeof(int4) * hc.runs.size()) ||
+                     !same(dc.pairs, hc.pairs.data(), sizeof(int2) * hc.npairs)))
+    *mismatch |= 64;
   return BA_OK;
 }
 

@@ -146,14 +146,14 @@ template <typename T>
 cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s);
 template <typename T>
 cudaError_t launch_prep_pts(const double* pts64, T* ptsw, int P, cudaStream_t s);
-// point-order and camera-order observation arrays from the caller's arrays (oc, op,
-// uv, depth: input order) and the two permutations; pos_in_po: [N] scratch; the
-// working-precision point-order arrays are skipped when po_uvw is null
+// uv and inverse-depth priors in point order and camera order (and the W row of
+// each point-order observation) from the caller's arrays (uv, depth: input order)
+// through the permutations po and co; the working-precision point-order arrays
+// are skipped when po_uvw is null
 template <typename T>
-cudaError_t launch_obs_layout(int N, const int* oc, const int* op, const double* uv, const double* depth,
-                              const int* po, const int* co, int* pos_in_po, int* po_cam, int* po_pt,
-                              int* po_wrow, double* po_uv64, double* po_tau64, T* po_uvw, T* po_tauw,
-                              int* co_pt, int* co_po, T* co_uvw, T* co_tauw, cudaStream_t s);
+cudaError_t launch_obs_layout(int N, const double* uv, const double* depth, const int* po, const int* co,
+                              const int* co_po, const int* po_pt, int* po_wrow, double* po_uv64, double* po_tau64,
+                              T* po_uvw, T* po_tauw, int* co_pt, T* co_uvw, T* co_tauw, cudaStream_t s);
 
 cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* camw64,
                           const double* pts64, const uint8_t* act, uint8_t* bits,

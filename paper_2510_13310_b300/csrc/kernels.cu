@@ -70,18 +70,12 @@ __device__ __forceinline__ double inv_depth_prior(double d) {
 }
 
 template <typename T>
-__global__ void k_obs_point_order(int N, const int* __restrict__ oc, const int* __restrict__ op,
-                                  const double* __restrict__ uv, const double* __restrict__ depth,
-                                  const int* __restrict__ po, int* __restrict__ pos_in_po,
-                                  int* __restrict__ po_cam, int* __restrict__ po_pt,
-                                  int* __restrict__ po_wrow, double* __restrict__ po_uv64,
-                                  double* __restrict__ po_tau64, T* __restrict__ po_uvw,
-                                  T* __restrict__ po_tauw) {
+__global__ void k_obs_point_order(int N, const double* __restrict__ uv, const double* __restrict__ depth,
+                                  const int* __restrict__ po, int* __restrict__ po_wrow,
+                                  double* __restrict__ po_uv64, double* __restrict__ po_tau64,
+                                  T* __restrict__ po_uvw, T* __restrict__ po_tauw) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const int k = po[i];
-    pos_in_po[k] = i;
-    po_cam[i] = oc[k];
-    po_pt[i] = op[k];
     po_wrow[i] = i;
     const double u = uv[2 * (size_t)k], v = uv[2 * (size_t)k + 1], tau = inv_depth_prior(depth[k]);
     po_uv64[2 * (size_t)i] = u;
@@ -96,15 +90,13 @@ __global__ void k_obs_point_order(int N, const int* __restrict__ oc, const int* 
 }
 
 template <typename T>
-__global__ void k_obs_camera_order(int N, const int* __restrict__ op, const double* __restrict__ uv,
-                                   const double* __restrict__ depth, const int* __restrict__ co,
-                                   const int* __restrict__ pos_in_po, int* __restrict__ co_pt,
-                                   int* __restrict__ co_po, T* __restrict__ co_uvw,
+__global__ void k_obs_camera_order(int N, const double* __restrict__ uv, const double* __restrict__ depth,
+                                   const int* __restrict__ co, const int* __restrict__ co_po,
+                                   const int* __restrict__ po_pt, int* __restrict__ co_pt, T* __restrict__ co_uvw,
                                    T* __restrict__ co_tauw) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const int k = co[i];
-    co_pt[i] = op[k];
-    co_po[i] = pos_in_po[k];
+    co_pt[i] = po_pt[co_po[i]];
     co_uvw[2 * (size_t)i] = (T)uv[2 * (size_t)k];
     co_uvw[2 * (size_t)i + 1] = (T)uv[2 * (size_t)k + 1];
     co_tauw[i] = (T)inv_depth_prior(depth[k]);
@@ -112,16 +104,13 @@ __global__ void k_obs_camera_order(int N, const int* __restrict__ op, const doub
 }
 
 template <typename T>
-cudaError_t launch_obs_layout(int N, const int* oc, const int* op, const double* uv, const double* depth,
-                              const int* po, const int* co, int* pos_in_po, int* po_cam, int* po_pt,
-                              int* po_wrow, double* po_uv64, double* po_tau64, T* po_uvw, T* po_tauw,
-                              int* co_pt, int* co_po, T* co_uvw, T* co_tauw, cudaStream_t s) {
+cudaError_t launch_obs_layout(int N, const double* uv, const double* depth, const int* po, const int* co,
+                              const int* co_po, const int* po_pt, int* po_wrow, double* po_uv64, double* po_tau64,
+                              T* po_uvw, T* po_tauw, int* co_pt, T* co_uvw, T* co_tauw, cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
   const int grid = (int)std::min<long long>(((long long)N + 255) / 256, 65535);
-  k_obs_point_order<T><<<grid, 256, 0, s>>>(N, oc, op, uv, depth, po, pos_in_po, po_cam, po_pt, po_wrow,
-                                            po_uv64, po_tau64, po_uvw, po_tauw);
-  k_obs_camera_order<T><<<grid, 256, 0, s>>>(N, op, uv, depth, co, pos_in_po, co_pt, co_po, co_uvw,
-                                             co_tauw);
+  k_obs_point_order<T><<<grid, 256, 0, s>>>(N, uv, depth, po, po_wrow, po_uv64, po_tau64, po_uvw, po_tauw);
+  k_obs_camera_order<T><<<grid, 256, 0, s>>>(N, uv, depth, co, co_po, po_pt, co_pt, co_uvw, co_tauw);
   return cudaGetLastError();
 }
 
@@ -1036,9 +1025,9 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
 #define BAB_INST(T)                                                                                \
   template cudaError_t launch_prep_cams<T>(const double*, T*, double*, int, cudaStream_t);          \
   template cudaError_t launch_prep_pts<T>(const double*, T*, int, cudaStream_t);                    \
-  template cudaError_t launch_obs_layout<T>(int, const int*, const int*, const double*, const double*, \
-                                            const int*, const int*, int*, int*, int*, int*, double*,  \
-                                            double*, T*, T*, int*, int*, T*, T*, cudaStream_t);       \
+  template cudaError_t launch_obs_layout<T>(int, const double*, const double*, const int*, const int*,  \
+                                            const int*, const int*, int*, double*, double*, T*, T*,    \
+                                            int*, T*, T*, cudaStream_t);                               \
   template cudaError_t launch_pt_lin<T>(const Layout&, const ModelParams&, const T*, const T*,      \
                                         const uint8_t*, T*, T*, T*, T*, cudaStream_t);              \
   template cudaError_t launch_cam_accum<T>(const Layout&, const ModelParams&, int, const T*,        \

@@ -281,6 +281,65 @@ uint64_t* radix_sort_items(uint64_t* in, uint64_t* tmp, int64_t n, int key_bits)
 
 }  // namespace
 
+// Warp ranges: consecutive whole points with at most 32 observations together,
+// or one point with more.  Tiles: up to one warp range per PCG warp, at most
+// kTileObs observations and kTileObs points.  Descriptors without their camera
+// runs and metadata offsets.
+void group_tiles(const int* pt_off, int P, std::vector<int>* wr_pt_out, std::vector<int>* tile_wr_out,
+                 std::vector<TileDesc>* descs, int* g_rows) {
+  std::vector<int>& wr_pt = *wr_pt_out;
+  wr_pt.assign(1, 0);
+  {
+    int cur_obs = 0;
+    for (int p = 0; p < P; ++p) {
+      const int len = pt_off[p + 1] - pt_off[p];
+      const bool open = wr_pt.back() < p;  // the current range already holds points
+      if (open && (len > 32 || cur_obs + len > 32 || p - wr_pt.back() >= 32)) {
+        wr_pt.push_back(p);
+        cur_obs = 0;
+      }
+      cur_obs += len;
+      if (len > 32) {  // a long point closes its own range
+        wr_pt.push_back(p + 1);
+        cur_obs = 0;
+      }
+    }
+    if (wr_pt.back() != P) wr_pt.push_back(P);
+  }
+  const int n_wr_total = (int)wr_pt.size() - 1;
+  std::vector<int>& tile_wr = *tile_wr_out;
+  tile_wr.assign(1, 0);
+  {
+    int t_obs = 0, t_pts = 0, t_wr = 0;
+    for (int r = 0; r < n_wr_total; ++r) {
+      const int r_obs = pt_off[wr_pt[r + 1]] - pt_off[wr_pt[r]], r_pts = wr_pt[r + 1] - wr_pt[r];
+      if (t_wr > 0 && (t_wr + 1 > kPcgWarps || t_obs + r_obs > kTileObs || t_pts + r_pts > kTileObs)) {
+        tile_wr.push_back(r);
+        t_obs = t_pts = t_wr = 0;
+      }
+      t_obs += r_obs;
+      t_pts += r_pts;
+      t_wr += 1;
+    }
+    if (tile_wr.back() != n_wr_total) tile_wr.push_back(n_wr_total);
+  }
+  const int n_tiles = (int)tile_wr.size() - 1;
+  descs->assign((size_t)n_tiles, TileDesc{});
+  int rows = 0;
+  for (int t = 0; t < n_tiles; ++t) {
+    const int pbeg = wr_pt[tile_wr[t]], pend = wr_pt[tile_wr[t + 1]];
+    TileDesc d{};
+    d.g_row = rows;
+    d.w_row = d.obs_begin = pt_off[pbeg];
+    d.n_obs = pt_off[pend] - pt_off[pbeg];
+    d.pt_begin = pbeg;
+    d.n_pts = pend - pbeg;
+    rows += (d.n_obs + 3) & ~3;
+    (*descs)[t] = d;
+  }
+  *g_rows = rows;
+}
+
 // ---------------------------------------------------------------------------
 // validation and layout
 // ---------------------------------------------------------------------------
@@ -303,10 +362,10 @@ int build_obs_layout(int C, int P, int N, const double* cams, const double* pts,
       return fail(err, "observation %lld has an index out of range", (long long)first_bad.load());
   }
   {
-    // FNV-1a (over 32-bit words) of the sizes and of 64K-observation chunk
+    // FNV-1a (over 32-bit words) of the sizes and of 4096-observation chunk
     // digests, each over its (camera, point) pairs: identifies the observation
     // structure
-    constexpr int64_t kHashChunk = 1 << 16;
+    constexpr int64_t kHashChunk = 1 << 12;
     auto fnv = [](uint64_t h, int32_t v) { return (h ^ (uint64_t)(uint32_t)v) * 1099511628211ull; };
     const int64_t nch = ((int64_t)N + kHashChunk - 1) / kHashChunk;
     std::vector<uint64_t> dig((size_t)nch);
@@ -411,67 +470,12 @@ int build_obs_layout(int C, int P, int N, const double* cams, const double* pts,
   for (int p = 0; p < P; ++p)
     if (pt_off[p + 1] - pt_off[p] > kTileObs)
       return fail(err, "point %d has %d observations (limit %d)", p, pt_off[p + 1] - pt_off[p], kTileObs);
-  // Warp ranges: consecutive whole points with at most 32 observations together,
-  // or one point with more.  Tiles: up to one warp range per PCG warp, at most
-  // kTileObs observations and kTileObs points.
-  std::vector<int>& wr_pt = L->wr_pt;
-  wr_pt.assign(1, 0);
-  {
-    int cur_obs = 0;
-    for (int p = 0; p < P; ++p) {
-      const int len = pt_off[p + 1] - pt_off[p];
-      const bool open = wr_pt.back() < p;  // the current range already holds points
-      if (open && (len > 32 || cur_obs + len > 32 || p - wr_pt.back() >= 32)) {
-        wr_pt.push_back(p);
-        cur_obs = 0;
-      }
-      cur_obs += len;
-      if (len > 32) {  // a long point closes its own range
-        wr_pt.push_back(p + 1);
-        cur_obs = 0;
-      }
-    }
-    if (wr_pt.back() != P) wr_pt.push_back(P);
-  }
-  const int n_wr_total = (int)wr_pt.size() - 1;
-  std::vector<int>& tile_wr = L->tile_wr;
-  tile_wr.assign(1, 0);
-  {
-    int t_obs = 0, t_pts = 0, t_wr = 0;
-    for (int r = 0; r < n_wr_total; ++r) {
-      const int r_obs = pt_off[wr_pt[r + 1]] - pt_off[wr_pt[r]], r_pts = wr_pt[r + 1] - wr_pt[r];
-      if (t_wr > 0 && (t_wr + 1 > kPcgWarps || t_obs + r_obs > kTileObs || t_pts + r_pts > kTileObs)) {
-        tile_wr.push_back(r);
-        t_obs = t_pts = t_wr = 0;
-      }
-      t_obs += r_obs;
-      t_pts += r_pts;
-      t_wr += 1;
-    }
-    if (tile_wr.back() != n_wr_total) tile_wr.push_back(n_wr_total);
-  }
-  const int n_tiles = (int)tile_wr.size() - 1;
+  group_tiles(pt_off.data(), P, &L->wr_pt, &L->tile_wr, &L->descs, &L->g_rows);
+  const int n_tiles = (int)L->descs.size();
   L->n_tiles = n_tiles;
-  // Per tile: its metadata record (camera of each observation, point offsets,
-  // runs of equal cameras once the tile's observations are sorted by camera,
-  // warp-range offsets, positions in camera order, local point of each
-  // observation) and its descriptor.  Pass 1 sorts each tile's observations by
-  // (camera, local index) and counts the runs; the record offsets follow by a
-  // prefix sum; pass 2 writes the records.
   std::vector<TileDesc>& descs = L->descs;
-  descs.assign((size_t)n_tiles, TileDesc{});
-  L->g_rows = 0;
-  for (int t = 0; t < n_tiles; ++t) {
-    const int pbeg = wr_pt[tile_wr[t]], pend = wr_pt[tile_wr[t + 1]];
-    TileDesc d{};
-    d.g_row = L->g_rows;
-    d.w_row = d.obs_begin = pt_off[pbeg];
-    d.n_obs = pt_off[pend] - pt_off[pbeg];
-    d.pt_begin = pbeg;
-    d.n_pts = pend - pbeg;
-    L->g_rows += (d.n_obs + 3) & ~3;
-    descs[t] = d;
-  }
+  const std::vector<int>& wr_pt = L->wr_pt;
+  const std::vector<int>& tile_wr = L->tile_wr;
   // Each tile's observations in (camera, local index) order are the camera-order
   // observations whose point-order position falls in the tile, in camera order:
   // a stable counting pass of camera order by tile (per-piece tile histograms)

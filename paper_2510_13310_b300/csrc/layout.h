@@ -91,6 +91,11 @@ int build_obs_layout(int C, int P, int N, const double* cams, const double* pts,
                      const int32_t* oc, const int32_t* op, ObsLayout* L, std::string* err,
                      bool wide_keys = false);
 
+// Warp ranges and tiles over the points (pt_off: [P + 1] observation offsets);
+// descriptors without their camera runs and metadata offsets.
+void group_tiles(const int* pt_off, int P, std::vector<int>* wr_pt, std::vector<int>* tile_wr,
+                 std::vector<TileDesc>* descs, int* g_rows);
+
 // co-visibility runs: every pair of observations of one point in cameras i < j,
 // grouped by (i, j), ascending in point within a run
 struct CovisRuns {
