@@ -40,7 +40,7 @@ METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 
 # captures of this workload (profiles/k_spcg_medium_1M_obs.md,
 # profiles/k_form_S_runs_and_k_eval64_medium_1M_obs.md); None once the kernel
 # has changed since the counters were taken.
-NCU_TRAFFIC = {"k_spcg": 13158912 + 39936, "k_pcg": None, "k_form_S_runs": 355182592 + 15817216}
+NCU_TRAFFIC = {"k_spcg": 13158912 + 39936, "k_pcg": None, "k_form_S_runs": 324913408 + 8682496}
 WORKLOAD = "medium"
 LM_ITERS = 30
 

@@ -119,6 +119,7 @@ struct ba_problem {
   float* dense_b = nullptr;      // [2][n]: scaled right-hand side, scaled solution
   void *Shat = nullptr, *Dblk = nullptr;
   void* Yhat = nullptr;         // [N + 1][kWStride] D^-1 W M per damping value (explicit system)
+  void* bs_wx = nullptr;        // [N][3] W_k^T dc of the back-substitution (explicit system)
   int4* covis_runs = nullptr;   // (camera i, camera j, first pair, count), i < j
   int2* covis_pairs = nullptr;  // point-order observations (k in i, k2 in j) of shared points
   int n_covis_runs = 0;
@@ -416,10 +417,10 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     pb->evk_valid = true;
     }
   }
-  LAUNCH(1, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
+  LAUNCH(2, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                                   pb->pt_act, pb->crank, (const T*)pb->x, (const T*)pb->Vinv, (const T*)pb->V,
-                                  (const T*)pb->gp, (const T*)pb->W, lambda, (T*)pb->dp, pb->pred_parts,
-                                  pb->bs_grid, pb->stream));
+                                  (const T*)pb->gp, (const T*)pb->W, lambda, (T*)pb->dp, (T*)pb->bs_wx,
+                                  pb->pred_parts, pb->bs_grid, pb->stream));
   LAUNCH(1, launch_pred_cams<T>(Cf, pb->cam_map, (const T*)pb->x, (const T*)pb->Ug, (const T*)pb->dampc,
                                 lambda, pb->pred_parts, pb->bs_grid, pb->stream));
   LAUNCH(1, launch_reduce_pred(pb->pred_parts, pb->bs_grid + 1, pb->sc, pb->stream));
@@ -946,6 +947,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   if (pb->explicit_S && n_max > 0) {
     ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * n_max));
     ST(dalloc_bytes(pb, &pb->Yhat, R * (size_t)kWStride * ((size_t)N + 1)));
+    ST(dalloc_bytes(pb, &pb->bs_wx, R * 3 * std::max<size_t>(N, 1)));  // W_k^T dc per observation
     // co-visibility runs: every pair of observations of one point in cameras i < j,
     // grouped by (i, j), ascending in point within a run (device)
     {

@@ -213,7 +213,7 @@ template <typename T>
 cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
                                const uint8_t* act_po, const uint8_t* pt_act, const int* crank, const T* x,
                                const T* Vinv, const T* V, const T* gp, const T* Wst, double lambda, T* dp,
-                               double* pred_parts, int grid, cudaStream_t s);
+                               T* wx, double* pred_parts, int grid, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pcg(const PcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
 template <typename T>

@@ -362,10 +362,10 @@ int build_obs_layout(int C, int P, int N, const double* cams, const double* pts,
       return fail(err, "observation %lld has an index out of range", (long long)first_bad.load());
   }
   {
-    // FNV-1a (over 32-bit words) of the sizes and of 4096-observation chunk
+    // FNV-1a (over 32-bit words) of the sizes and of 256-observation chunk
     // digests, each over its (camera, point) pairs: identifies the observation
     // structure
-    constexpr int64_t kHashChunk = 1 << 12;
+    constexpr int64_t kHashChunk = 1 << 8;
     auto fnv = [](uint64_t h, int32_t v) { return (h ^ (uint64_t)(uint32_t)v) * 1099511628211ull; };
     const int64_t nch = ((int64_t)N + kHashChunk - 1) / kHashChunk;
     std::vector<uint64_t> dig((size_t)nch);

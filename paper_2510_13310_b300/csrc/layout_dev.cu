@@ -253,14 +253,14 @@ __global__ void k_check_index(const int32_t* __restrict__ oc, const int32_t* __r
     if (oc[k] < 0 || oc[k] >= C || op[k] < 0 || op[k] >= P) atomicMin(&fl->first_bad, (unsigned long long)k);
 }
 
-// FNV-1a over 32-bit words of each 4096-observation chunk's (camera, point) pairs
+// FNV-1a over 32-bit words of each 256-observation chunk's (camera, point) pairs
 __global__ void k_hash_chunks(const int32_t* __restrict__ oc, const int32_t* __restrict__ op, int N,
                               unsigned long long* __restrict__ dig, int nch) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nch) return;
   unsigned long long h = 1469598103934665603ull;
-  const long long k1 = min((long long)N, ((long long)c + 1) << 12);
-  for (long long k = (long long)c << 12; k < k1; ++k) {
+  const long long k1 = min((long long)N, ((long long)c + 1) << 8);
+  for (long long k = (long long)c << 8; k < k1; ++k) {
     h = (h ^ (unsigned long long)(unsigned)oc[k]) * 1099511628211ull;
     h = (h ^ (unsigned long long)(unsigned)op[k]) * 1099511628211ull;
   }
@@ -436,7 +436,7 @@ int build_obs_layout_dev(int C, int P, int N, const double* d_cams, const double
   Scratch sc(s);
   Flags* fl = sc.get<Flags>(1);
   if (!fl) return fail(err, 2, "device scratch allocation failed");
-  const int nch = (N + 4095) / 4096;
+  const int nch = (N + 255) / 256;
   unsigned long long* dig = sc.get<unsigned long long>(nch);
   DCU(cudaMemsetAsync(fl, 0xFF, 2 * sizeof(unsigned long long), s));
   DCU(cudaMemsetAsync(&fl->nonfinite, 0, sizeof(int), s));

@@ -151,8 +151,10 @@ __device__ __forceinline__ void rs_round(T (&v)[96], int lane, int r) {
 // run in registers, then the lanes are reduced in a fixed order
 // (deterministic).  Inactive observations have Y^ = 0 and add nothing; runs whose
 // cameras are not both free are skipped.
+// Three 128-thread blocks per SM: 81 accumulators and two 27-entry rows per lane
+// fit without spilling (four blocks force 128 registers and spill: 19% slower).
 template <typename T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
     k_form_S_runs(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
                   const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat) {
   const int lane = threadIdx.x & 31;
@@ -740,53 +742,65 @@ int spcg_threads() { return kSpcgThreads; }
 int spcg_words_per_value(bool fp64) { return kSpcgReplicas * (fp64 ? spcg_words<double>() : spcg_words<float>()); }
 
 // ---------------------------------------------------------------------------
-// Point back-substitution dp = V*^-1 (-g_p - sum_k W_k^T dc_c(k)), with the
-// stored W rows when there are any (explicit system), else W recomputed; and the
-// point part of the predicted decrease.  One thread per point.
+// Point back-substitution dp = V*^-1 (-g_p - sum_k W_k^T dc_c(k)) and the point
+// part of the predicted decrease, in two passes: one thread per observation forms
+// W_k^T dc_c(k) (stored W rows when there are any (explicit system), else W
+// recomputed; coalesced over point order), then one thread per point sums its
+// observations' terms in point order.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_backsub_pts(Layout L, ModelParams mp, const T* __restrict__ camw, const T* __restrict__ ptsw,
-                              const uint8_t* __restrict__ act_po, const uint8_t* __restrict__ pt_act,
-                              const int* __restrict__ crank, const T* __restrict__ x,
-                              const T* __restrict__ Vinv, const T* __restrict__ V, const T* __restrict__ gp,
-                              const T* __restrict__ Wst, double lambda, T* __restrict__ dp,
-                              double* __restrict__ pred_parts) {
-  __shared__ double red[32];
-  double pred = 0.0;
+__global__ void k_backsub_obs(Layout L, ModelParams mp, const T* __restrict__ camw, const T* __restrict__ ptsw,
+                              const uint8_t* __restrict__ act_po, const int* __restrict__ crank,
+                              const T* __restrict__ x, const T* __restrict__ Wst, T* __restrict__ wx) {
   const T* po_uv = reinterpret_cast<const T*>(L.po_uvw);
   const T* po_tau = reinterpret_cast<const T*>(L.po_tauw);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < L.P; p += gridDim.x * blockDim.x) {
-    if (!pt_act[p]) {
-      dp[3 * (size_t)p] = dp[3 * (size_t)p + 1] = dp[3 * (size_t)p + 2] = T(0);
-      continue;
-    }
-    const T* X = ptsw + 4 * (size_t)p;
-    double t0 = -(double)gp[3 * (size_t)p], t1 = -(double)gp[3 * (size_t)p + 1], t2 = -(double)gp[3 * (size_t)p + 2];
-    for (int k = L.pt_off[p]; k < L.pt_off[p + 1]; ++k) {
-      if (!act_po[k]) continue;
-      int c = L.po_cam[k];
-      int cr = crank[c];
-      if (cr < 0) continue;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += gridDim.x * blockDim.x) {
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    const int cr = act_po[k] ? crank[L.po_cam[k]] : -1;
+    if (cr >= 0) {
       T W[27];
       if (Wst) {
         load_row27<T>(Wst + kWStride * (size_t)k, W);
       } else {
         T cw[kCamStride];
-        load_cam_rec(camw, c, cw);
-        obs_W(cw, X, po_uv[2 * (size_t)k], po_uv[2 * (size_t)k + 1], po_tau[k], mp, W);
+        load_cam_rec(camw, L.po_cam[k], cw);
+        obs_W(cw, ptsw + 4 * (size_t)L.po_pt[k], po_uv[2 * (size_t)k], po_uv[2 * (size_t)k + 1], po_tau[k], mp, W);
       }
       const T* xv = x + 9 * (size_t)cr;
-      T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
         s0 += W[3 * q] * xv[q];
         s1 += W[3 * q + 1] * xv[q];
         s2 += W[3 * q + 2] * xv[q];
       }
-      t0 -= (double)s0;
-      t1 -= (double)s1;
-      t2 -= (double)s2;
     }
+    wx[3 * (size_t)k] = s0;
+    wx[3 * (size_t)k + 1] = s1;
+    wx[3 * (size_t)k + 2] = s2;
+  }
+}
+
+template <typename T>
+__global__ void k_backsub_pts(Layout L, const uint8_t* __restrict__ pt_act, const T* __restrict__ wx,
+                              const T* __restrict__ Vinv, const T* __restrict__ V, const T* __restrict__ gp,
+                              double lambda, T* __restrict__ dp, double* __restrict__ pred_parts) {
+  __shared__ double red[32];
+  double pred = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < L.P; p += gridDim.x * blockDim.x) {
+    if (!pt_act[p]) {
+      dp[3 * (size_t)p] = dp[3 * (size_t)p + 1] = dp[3 * (size_t)p + 2] = T(0);
+      continue;
+    }
+    // the point's terms summed in the working precision (FP64 is the scarce pipe),
+    // then combined with the gradient in FP64
+    T w0 = T(0), w1 = T(0), w2 = T(0);
+    for (int k = L.pt_off[p]; k < L.pt_off[p + 1]; ++k) {
+      w0 += wx[3 * (size_t)k];
+      w1 += wx[3 * (size_t)k + 1];
+      w2 += wx[3 * (size_t)k + 2];
+    }
+    const double t0 = -(double)gp[3 * (size_t)p] - (double)w0, t1 = -(double)gp[3 * (size_t)p + 1] - (double)w1,
+                 t2 = -(double)gp[3 * (size_t)p + 2] - (double)w2;
     const T* v = Vinv + 6 * (size_t)p;
     T d0 = (T)(v[0] * t0 + v[1] * t1 + v[2] * t2);
     T d1 = (T)(v[1] * t0 + v[3] * t1 + v[4] * t2);
@@ -808,9 +822,12 @@ template <typename T>
 cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
                                const uint8_t* act_po, const uint8_t* pt_act, const int* crank, const T* x,
                                const T* Vinv, const T* V, const T* gp, const T* Wst, double lambda, T* dp,
-                               double* pred_parts, int grid, cudaStream_t s) {
-  k_backsub_pts<T><<<grid, 256, 0, s>>>(L, mp, camw, ptsw, act_po, pt_act, crank, x, Vinv, V, gp, Wst, lambda,
-                                         dp, pred_parts);
+                               T* wx, double* pred_parts, int grid, cudaStream_t s) {
+  if (L.N > 0) {
+    const int g = (int)std::min<long long>(((long long)L.N + 255) / 256, 65535);
+    k_backsub_obs<T><<<g, 256, 0, s>>>(L, mp, camw, ptsw, act_po, crank, x, Wst, wx);
+  }
+  k_backsub_pts<T><<<grid, 256, 0, s>>>(L, pt_act, wx, Vinv, V, gp, lambda, dp, pred_parts);
   return cudaGetLastError();
 }
 
@@ -824,7 +841,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \
   template cudaError_t launch_backsub_pts<T>(const Layout&, const ModelParams&, const T*, const T*,    \
                                              const uint8_t*, const uint8_t*, const int*, const T*,     \
-                                             const T*, const T*, const T*, const T*, double, T*,       \
+                                             const T*, const T*, const T*, const T*, double, T*, T*,   \
                                              double*, int, cudaStream_t);
 BAB_SINST(float)
 BAB_SINST(double)
