@@ -739,7 +739,7 @@ __global__ void k_damp_pts(int P, const T* __restrict__ V, const T* __restrict__
     for (int j = 0; j < 3; ++j) zo[j] = T(0);
     return;
   }
-  double id = 1.0 / det;
+  double id = recip_nr(det);
   double i00 = A * id, i01 = B * id, i02 = Cc * id;
   double i11 = (a * f - c * c) * id, i12 = (b * c - a * e) * id, i22 = (a * d - b * b) * id;
   vo[0] = (T)i00; vo[1] = (T)i01; vo[2] = (T)i02; vo[3] = (T)i11; vo[4] = (T)i12; vo[5] = (T)i22;
@@ -757,8 +757,9 @@ cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_ac
 }
 
 // Per free camera f (one warp each): damped U block, block-Jacobi inverse of the
-// Schur diagonal D_f = U*_f - sum W V*^-1 W^T (FP64 Cholesky in shared memory,
-// the 9 inverse columns solved by 9 lanes), Schur RHS b_f = -g_c + sum W V*^-1 g_p.
+// Schur diagonal D_f = U*_f - sum W V*^-1 W^T (FP64 Cholesky in shared memory
+// across the warp, the 9 inverse columns solved by 9 lanes with the reciprocal
+// pivots), Schur RHS b_f = -g_c + sum W V*^-1 g_p.
 constexpr int kDiagWarps = 4;
 
 template <typename T>
@@ -767,6 +768,7 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
                              T* __restrict__ Dinv, T* __restrict__ b, T* __restrict__ dampc,
                              T* __restrict__ Dblk, int* err) {
   __shared__ double Ds[kDiagWarps][81];
+  __shared__ double Rs[kDiagWarps][9];  // reciprocal pivots 1 / L_jj
   __shared__ int okS[kDiagWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int f = blockIdx.x * kDiagWarps + w;
@@ -792,25 +794,31 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
   }
   if (lane < 9) b[9 * (size_t)f + lane] = (T)(-(double)u[45 + lane] + (double)sch[45 + lane]);
   __syncwarp();
-  if (lane == 0) {
-    // Cholesky D = L L^T in place (lower)
-    int ok = 1;
-    for (int j = 0; j < 9 && ok; ++j) {
-      double s = D[9 * j + j];
-      for (int l = 0; l < j; ++l) s -= D[9 * j + l] * D[9 * j + l];
-      if (!(s > 0.0)) {
-        ok = 0;
-        break;
-      }
-      double dj = sqrt(s), inv = 1.0 / dj;
-      D[9 * j + j] = dj;
-      for (int i = j + 1; i < 9; ++i) {
-        double t = D[9 * i + j];
-        for (int l = 0; l < j; ++l) t -= D[9 * i + l] * D[9 * j + l];
-        D[9 * i + j] = t * inv;
-      }
+  // Cholesky D = L L^T in place (lower), right-looking across the warp: lane 0
+  // takes pivot j (reciprocal square root), the lanes below scale column j, and
+  // the lanes update the trailing lower triangle (one entry each)
+  double* Rp = Rs[w];
+  for (int j = 0; j < 9; ++j) {
+    if (lane == 0) {
+      const double sj = D[9 * j + j];
+      const int good = sj > 0.0;  // false for NaN
+      const double r = good ? rsqrt(sj) : 0.0;
+      D[9 * j + j] = sj * r;
+      Rp[j] = r;
+      okS[w] = good;
     }
-    okS[w] = ok;
+    __syncwarp();
+    if (!okS[w]) break;
+    if (lane > j && lane < 9) D[9 * lane + j] *= Rp[j];
+    __syncwarp();
+    const int m = 8 - j;  // trailing block rows j+1 .. 8
+    for (int q = lane; q < m * (m + 1) / 2; q += 32) {
+      int i0 = 0, k0 = q;
+      while (k0 > i0) k0 -= ++i0;  // q -> (i0, k0), k0 <= i0, row-major lower triangle
+      const int i = j + 1 + i0, k = j + 1 + k0;
+      D[9 * i + k] -= D[9 * i + j] * D[9 * k + j];
+    }
+    __syncwarp();
   }
   __syncwarp();
   T* out = Dinv + 81 * (size_t)f;
@@ -832,14 +840,14 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
       double s = i == j ? 1.0 : 0.0;
 #pragma unroll
       for (int l = 0; l < i; ++l) s -= D[9 * i + l] * x[l];
-      x[i] = s / D[9 * i + i];
+      x[i] = s * Rp[i];
     }
 #pragma unroll
     for (int i = 8; i >= 0; --i) {
       double s = x[i];
 #pragma unroll
       for (int l = i + 1; l < 9; ++l) s -= D[9 * l + i] * x[l];
-      x[i] = s / D[9 * i + i];
+      x[i] = s * Rp[i];
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) out[9 * i + j] = (T)x[i];
