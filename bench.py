@@ -333,18 +333,25 @@ def main():
         per_launch = n ** 3 / 3.0
         kname = "dense solve: tensor-core blocked Cholesky (tcgen05 kind::tf32) + preconditioned CG"
         unit_txt = "n^3/3 flops of the factorisation, n = 9 Cf (timed launch includes the CG)"
-    elif prob.explicit_solver:
+    elif prob.explicit_solver and prob.explicit_layout["rows_in_smem"]:
         # S^ read once (4 n^2); preconditioner blocks (324 Cf), b, D, 1/D and x (20 n).
         # The per-iteration exchange of q stays in L2.
         per_launch = 4 * n * n + 324 * Cf + 20 * n
         kname = "k_spcg (persistent block-Jacobi PCG on the explicit scaled Schur matrix, rows in shared memory)"
         unit_txt = "4 n^2 + 324 Cf + 20 n bytes, n = 9 Cf"
+    elif prob.explicit_solver:
+        # rows of S^ streamed from device memory by every matvec: 4 n^2 per iteration
+        # (S^ does not fit in L2 at these orders), plus the set-up reads
+        per_launch = 4 * n * n * mean_it + 324 * Cf + 20 * n
+        kname = "k_spcg (persistent block-Jacobi PCG on the explicit scaled Schur matrix, rows streamed)"
+        unit_txt = "4 n^2 x iters + 324 Cf + 20 n bytes, n = 9 Cf"
     else:
-        # per matvec: W rows (27 x 4) + point index (4) per observation, V*^-1 and
-        # the point vector per point
-        per_launch = mean_it * (N * (27 * 4 + 4) + P * (6 * 4 + 4))
-        kname = "k_pcg (persistent block-Jacobi PCG, implicit Schur matvec)"
-        unit_txt = "(112 B x obs + 28 B x points) x iters"
+        # per matvec, FP32 (W recomputed from a signed IRLS weight): the weight (4 B)
+        # and the tile record (~13 B) per observation; point coordinates (16 B) and
+        # V*^-1 (24 B) per point
+        per_launch = mean_it * (N * 17 + P * 40)
+        kname = "k_pcg (persistent block-Jacobi PCG, implicit Schur matvec, W recomputed)"
+        unit_txt = "(17 B x obs + 40 B x points) x iters"
     if kind == ba.BA_SOLVER_DENSE:
         tpeak, tsrc = _tf32_peak()
         achieved = per_launch / (kern_ms * 1e-3) / 1e12 if kern_ms else 0.0

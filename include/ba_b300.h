@@ -262,6 +262,15 @@ int64_t ba_kernel_launches(const ba_problem* pb);
  * BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT or BA_SOLVER_DENSE (0 for a NULL handle). */
 int ba_solver_kind(const ba_problem* pb);
 
+/* Placement of the explicit solver's working set, fixed at creation (all
+ * outputs optional, set to 0 for other solvers or a NULL handle):
+ * *rows_in_smem = 1 when each block keeps its rows of S^ in shared memory
+ * (S^ is read from device memory once per solve), 0 when the rows are streamed
+ * from device memory on every matvec; *vecs_in_smem = 1 when the PCG vectors sit
+ * in shared memory, 0 when they sit in per-block device scratch; *grid = blocks
+ * of the persistent PCG launch. */
+void ba_explicit_layout(const ba_problem* pb, int* rows_in_smem, int* vecs_in_smem, int* grid);
+
 void ba_destroy(ba_problem* pb);
 const char* ba_status_string(ba_status s);
 const char* ba_last_error(void);

@@ -27,7 +27,7 @@ EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
            "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
            "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout", "ba_selftest_layout",
-           "ba_kernel_launches", "ba_solver_kind", "ba_destroy",
+           "ba_kernel_launches", "ba_solver_kind", "ba_explicit_layout", "ba_destroy",
            "ba_status_string", "ba_last_error")
 
 
@@ -92,6 +92,8 @@ def lib():
         L.ba_kernel_launches.restype = ct.c_int64
         L.ba_solver_kind.argtypes = [vp]
         L.ba_solver_kind.restype = ct.c_int
+        L.ba_explicit_layout.argtypes = [vp, vp, vp, vp]
+        L.ba_explicit_layout.restype = None
         L.ba_get_state.argtypes = [vp, vp, ct.POINTER(ct.c_size_t)]
         L.ba_set_state.argtypes = [vp, vp, ct.c_size_t]
         L.ba_selftest_wait_timeout.argtypes = [vp, ct.c_double]
@@ -340,6 +342,13 @@ class Problem:
     def solver_kind(self) -> int:
         """BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT or BA_SOLVER_DENSE (ba_solver_kind)."""
         return int(self.L.ba_solver_kind(self.h))
+
+    @property
+    def explicit_layout(self) -> dict:
+        """ba_explicit_layout: where the explicit solver keeps S^ rows and PCG vectors."""
+        r, v, g = ct.c_int(0), ct.c_int(0), ct.c_int(0)
+        self.L.ba_explicit_layout(self.h, ct.byref(r), ct.byref(v), ct.byref(g))
+        return {"rows_in_smem": r.value, "vecs_in_smem": v.value, "grid": g.value}
 
     @property
     def explicit_solver(self) -> bool:

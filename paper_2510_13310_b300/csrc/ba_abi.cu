@@ -364,7 +364,7 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
         LAUNCH(1, launch_scale_vec(n, (const float*)pb->bvec, dinv, bh, pb->stream));
         CU(cudaEventRecord(pb->evk[0], pb->stream));
         DenseResult res;
-        CU(dense_spd_solve(pb->dw, (const float*)pb->Shat, n, n, bh, xh, pb->opt.pcg_rel_tol,
+        CU(dense_spd_solve(pb->dw, (const float*)pb->Shat, spcg_row_stride<float>(n), n, bh, xh, pb->opt.pcg_rel_tol,
                            pb->opt.pcg_max_iters, pb->num_sms, pb->stream, &res));
         CU(cudaEventRecord(pb->evk[1], pb->stream));
         pb->evk_valid = true;
@@ -945,7 +945,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   ST(dalloc(pb, &pb->err, 1));
   // explicit reduced camera system (solver option; automatic for up to 512 cameras)
   if (pb->explicit_S && n_max > 0) {
-    ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * n_max));
+    ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * (pb->fp64 ? spcg_row_stride<double>(n_max) : spcg_row_stride<float>(n_max))));
     ST(dalloc_bytes(pb, &pb->Yhat, R * (size_t)kWStride * ((size_t)N + 1)));
     ST(dalloc_bytes(pb, &pb->bs_wx, R * 3 * std::max<size_t>(N, 1)));  // W_k^T dc per observation
     // co-visibility runs: every pair of observations of one point in cameras i < j,
@@ -1572,6 +1572,13 @@ int64_t ba_kernel_launches(const ba_problem* pb) { return pb ? pb->launches : 0;
 int ba_solver_kind(const ba_problem* pb) {
   if (!pb) return 0;
   return pb->dense ? BA_SOLVER_DENSE : pb->explicit_S ? BA_SOLVER_EXPLICIT : BA_SOLVER_IMPLICIT;
+}
+
+void ba_explicit_layout(const ba_problem* pb, int* rows_in_smem, int* vecs_in_smem, int* grid) {
+  const bool e = pb && pb->explicit_S && !pb->dense;
+  if (rows_in_smem) *rows_in_smem = e ? pb->spcg_rows_in_smem : 0;
+  if (vecs_in_smem) *vecs_in_smem = e ? pb->spcg_vecs_in_smem : 0;
+  if (grid) *grid = e ? pb->spcg_grid : 0;
 }
 
 void ba_destroy(ba_problem* pb) { free_problem(pb); }

@@ -201,6 +201,11 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
                           cudaStream_t s);
 template <typename T>
 size_t spcg_smem_bytes(int n, int rows, int rows_in_smem, int vecs_in_smem, int Cf);
+// row stride of S^: FP32 rows padded to a multiple of 4 entries (zeros)
+template <typename T>
+__host__ __device__ inline int spcg_row_stride(int n) {
+  return sizeof(T) == 4 ? (n + 3) & ~3 : n;
+}
 template <typename T>
 __host__ __device__ size_t spcg_vec_elems(int n, int Cf);
 template <typename T>

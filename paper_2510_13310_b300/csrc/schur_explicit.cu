@@ -20,6 +20,7 @@
 
 namespace bab {
 
+
 template <typename T>
 __device__ __forceinline__ void load_cam_rec(const T* __restrict__ camw, int c, T cw[kCamStride]) {
 #pragma unroll
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
                   const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  const int n = 9 * Cf;
+  const int ld = spcg_row_stride<T>(9 * Cf);
   for (int ri = gw; ri < n_runs; ri += nw) {
     const int4 rn = runs[ri];  // (camera i, camera j, first pair, pair count)
     const int a = crank[rn.x], b = crank[rn.y];
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
       const int t = base + j;
       if (t < 81) {
         const int r = t / 9, s2 = t - 9 * r;
-        Shat[(size_t)(9 * a + r) * n + 9 * b + s2] = -v[j];
+        Shat[(size_t)(9 * a + r) * ld + 9 * b + s2] = -v[j];
       }
     }
   }
@@ -212,7 +213,7 @@ template <typename T>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
     k_form_S_lanes(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
                    const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat) {
-  const int n = 9 * Cf;
+  const int ld = spcg_row_stride<T>(9 * Cf);
   for (int ri = blockIdx.x * blockDim.x + threadIdx.x; ri < n_runs; ri += gridDim.x * blockDim.x) {
     const int4 rn = runs[ri];
     const int a = crank[rn.x], b = crank[rn.y];
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
 #pragma unroll
     for (int r = 0; r < 9; ++r)
 #pragma unroll
-      for (int s2 = 0; s2 < 9; ++s2) Shat[(size_t)(9 * a + r) * n + 9 * b + s2] = -acc[9 * r + s2];
+      for (int s2 = 0; s2 < 9; ++s2) Shat[(size_t)(9 * a + r) * ld + 9 * b + s2] = -acc[9 * r + s2];
   }
 }
 
@@ -249,14 +250,14 @@ template <typename T>
 __global__ void k_S_finalize(int Cf, const T* __restrict__ Dblk, const double* __restrict__ dscale,
                              T* __restrict__ Shat) {
   __shared__ T tile[32][33];
-  const int n = 9 * Cf;
+  const int n = 9 * Cf, ld = spcg_row_stride<T>(n);
   const int bx = blockIdx.x, by = blockIdx.y;  // tile column, tile row
   if (bx > by) return;                          // only tiles on or below the diagonal
   // read the transposed tile (upper triangle source)
   int r0 = bx * 32, c0 = by * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     int r = r0 + i, c = c0 + threadIdx.x;
-    tile[i][threadIdx.x] = (r < n && c < n) ? Shat[(size_t)r * n + c] : T(0);
+    tile[i][threadIdx.x] = (r < n && c < n) ? Shat[(size_t)r * ld + c] : T(0);
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -266,9 +267,9 @@ __global__ void k_S_finalize(int Cf, const T* __restrict__ Dblk, const double* _
     if (fr == fc) {
       int ir = r - 9 * fr, ic = c - 9 * fc;
       const T* di = reinterpret_cast<const T*>(dscale + n);
-      Shat[(size_t)r * n + c] = Dblk[45 * (size_t)fr + sym9(ir, ic)] * di[r] * di[c];
+      Shat[(size_t)r * ld + c] = Dblk[45 * (size_t)fr + sym9(ir, ic)] * di[r] * di[c];
     } else if (c < r) {
-      Shat[(size_t)r * n + c] = tile[threadIdx.x][i];
+      Shat[(size_t)r * ld + c] = tile[threadIdx.x][i];
     }
   }
 }
@@ -279,13 +280,13 @@ __global__ void k_S_diag_upper(int Cf, const T* __restrict__ Dblk, const double*
                                T* __restrict__ Shat) {
   int f = blockIdx.x;
   if (f >= Cf) return;
-  int n = 9 * Cf;
+  int n = 9 * Cf, ld = spcg_row_stride<T>(n);
   for (int q = threadIdx.x; q < 81; q += blockDim.x) {
     int ir = q / 9, ic = q - 9 * ir;
     if (ic <= ir) continue;
     int r = 9 * f + ir, c = 9 * f + ic;
     const T* di = reinterpret_cast<const T*>(dscale + n);
-    Shat[(size_t)r * n + c] = Dblk[45 * (size_t)f + sym9(ir, ic)] * di[r] * di[c];
+    Shat[(size_t)r * ld + c] = Dblk[45 * (size_t)f + sym9(ir, ic)] * di[r] * di[c];
   }
 }
 
@@ -312,7 +313,7 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
   const int n = 9 * Cf;
   k_dscale<T><<<(n + 255) / 256, 256, 0, s>>>(Cf, Ud, dscale);
   if (L.N > 0) k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
-  cudaError_t e = cudaMemsetAsync(Shat, 0, sizeof(T) * (size_t)n * n, s);
+  cudaError_t e = cudaMemsetAsync(Shat, 0, sizeof(T) * (size_t)n * spcg_row_stride<T>(n), s);
   if (e != cudaSuccess) return e;
   // events (nullable) around the co-visibility product kernel
   if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
@@ -410,10 +411,6 @@ __device__ __forceinline__ T spcg_unpack(const unsigned long long* v) {
   else return __longlong_as_double((long long)((v[0] & 0xFFFFFFFFull) | (v[1] << 32)));
 }
 
-template <typename T>
-__host__ __device__ inline int spcg_row_stride(int n) {
-  return sizeof(T) == 4 ? (n + 3) & ~3 : n;  // FP32 rows padded for 16-byte vector loads
-}
 
 constexpr size_t kSpcgRedBytes = sizeof(double) * 2 * 2 * 32;  // block sums, two alternating buffers
 
@@ -554,17 +551,16 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   T* qv = zv + ns;
   T* xv = qv + ns;
   T* Mv = xv + ns;
-  const T* Sg = a.Shat + (size_t)r0 * n;
+  const T* Sg = a.Shat + (size_t)r0 * ns;
   const T* dinv = reinterpret_cast<const T*>(a.dscale + n);
 
   if (a.rows_in_smem) {
     // the block's rows of S^ (from HBM once per solve): asynchronous element
     // copies, all in flight together, overlapping the set-up below
     for (int r = warp; r < nr; r += nwarps) {
-      const T* src = Sg + (size_t)r * n;
+      const T* src = Sg + (size_t)r * ns;
       T* dst = Srows + (size_t)r * ns;
-      for (int c = lane; c < n; c += 32) cp_async_elem(dst + c, src + c);
-      for (int c = n + lane; c < ns; c += 32) dst[c] = T(0);
+      for (int c = lane; c < ns; c += 32) cp_async_elem(dst + c, src + c);  // padding entries are zero
     }
     cp_async_commit();
   }
@@ -631,11 +627,36 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
         }
       }
     }
-    if (sizeof(T) != 4 || !a.rows_in_smem) {
+    if constexpr (sizeof(T) == 4) {
+      if (!a.rows_in_smem) {
+        // rows streamed from device memory: 16-byte loads, four in flight per lane
+        const float4* p4 = reinterpret_cast<const float4*>(pv);
+        const int rs = ns / 4;
+        for (int r = warp; r < nr; r += nwarps) {
+          const float4* row = reinterpret_cast<const float4*>(Sg + (size_t)r * ns);
+          float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+          int c = lane;
+          for (; c + 96 < rs; c += 128) {
+            const float4 s0 = __ldg(row + c), s1 = __ldg(row + c + 32), s2 = __ldg(row + c + 64),
+                         s3 = __ldg(row + c + 96);
+            const float4 q0 = p4[c], q1 = p4[c + 32], q2 = p4[c + 64], q3 = p4[c + 96];
+            c0 = fmaf(s0.x, q0.x, fmaf(s0.y, q0.y, fmaf(s0.z, q0.z, fmaf(s0.w, q0.w, c0))));
+            c1 = fmaf(s1.x, q1.x, fmaf(s1.y, q1.y, fmaf(s1.z, q1.z, fmaf(s1.w, q1.w, c1))));
+            c2 = fmaf(s2.x, q2.x, fmaf(s2.y, q2.y, fmaf(s2.z, q2.z, fmaf(s2.w, q2.w, c2))));
+            c3 = fmaf(s3.x, q3.x, fmaf(s3.y, q3.y, fmaf(s3.z, q3.z, fmaf(s3.w, q3.w, c3))));
+          }
+          for (; c < rs; c += 32) {
+            const float4 s0 = __ldg(row + c), q0 = p4[c];
+            c0 = fmaf(s0.x, q0.x, fmaf(s0.y, q0.y, fmaf(s0.z, q0.z, fmaf(s0.w, q0.w, c0))));
+          }
+          const float acc = warp_sum((c0 + c1) + (c2 + c3));
+          if (lane < kSpcgReplicas) spcg_publish<T>(set + lane * set_words + (size_t)(r0 + r) * W, acc, tag);
+        }
+      }
+    } else {
       const T* base = a.rows_in_smem ? Srows : Sg;
-      const int ld = a.rows_in_smem ? ns : n;
       for (int r = warp; r < nr; r += nwarps) {
-        const T* row = base + (size_t)r * ld;
+        const T* row = base + (size_t)r * ns;
         T acc = T(0);
         for (int c = lane; c < n; c += 32) acc += row[c] * pv[c];
         acc = warp_sum(acc);
