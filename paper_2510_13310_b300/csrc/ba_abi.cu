@@ -1009,7 +1009,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       ST(dalloc(pb, &pb->spcg_words, nw));
       CU(cudaMemset(pb->spcg_words, 0, sizeof(unsigned long long) * nw));
     }
-    const void* sfn = pb->fp64 ? spcg_kernel_ptr<double>() : spcg_kernel_ptr<float>();
+    const bool rs = pb->spcg_rows_in_smem != 0;
+    const void* sfn = pb->fp64 ? spcg_kernel_ptr<double>(rs) : spcg_kernel_ptr<float>(rs);
     CU(cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb->spcg_smem));
     int sper = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, sfn, spcg_threads(), pb->spcg_smem));

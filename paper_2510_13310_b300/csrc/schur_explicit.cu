@@ -412,13 +412,14 @@ __device__ __forceinline__ T spcg_unpack(const unsigned long long* v) {
 }
 
 
-constexpr size_t kSpcgRedBytes = sizeof(double) * 2 * 2 * 32;  // block sums, two alternating buffers
+constexpr int kSpcgRedStride = 64;  // warp sums of one block reduction (K x 16, K <= 4)
+constexpr size_t kSpcgRedBytes = sizeof(double) * 2 * kSpcgRedStride;  // two alternating buffers
 
 // per-block vector storage other than p: r, z, q, x (full length) and the
-// packed preconditioner blocks, in T elements
+// preconditioner blocks (9x9 each), in T elements
 template <typename T>
 __host__ __device__ size_t spcg_vec_elems(int n, int Cf) {
-  return (size_t)4 * spcg_row_stride<T>(n) + (size_t)45 * Cf;
+  return (size_t)4 * spcg_row_stride<T>(n) + (size_t)81 * Cf;
 }
 
 template <typename T>
@@ -431,68 +432,38 @@ size_t spcg_smem_bytes(int n, int rows, int rows_in_smem, int vecs_in_smem, int 
   return (b + 15) & ~size_t(15);
 }
 
-// Block-wide sums for the PCG scalars.  The FP32 path accumulates in FP32
-// double-float pairs (hi + lo, Knuth's TwoSum, about 44 significant bits): the
-// FP64 pipe is the scarce one on this part, and every block forms these sums
-// redundantly.  The FP64 path accumulates in FP64.
-struct DF {
-  float hi, lo;
-};
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  // TwoSum: e is the exact rounding error of s = a.hi + b.hi for either operand
-  // order, so df_add is commutative bit for bit (butterfly lanes agree)
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  float e = (a.hi - (s - bb)) + (b.hi - bb);
-  e += a.lo + b.lo;
-  const float hi = s + e;
-  return DF{hi, e - (hi - s)};
-}
-__device__ __forceinline__ DF df_shfl_xor(DF v, int m) {
-  return DF{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
-}
-__device__ __forceinline__ DF acc_add(DF a, DF b) { return df_add(a, b); }
-__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
-__device__ __forceinline__ DF acc_shfl_xor(DF v, int m) { return df_shfl_xor(v, m); }
-__device__ __forceinline__ double acc_shfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
-__device__ __forceinline__ double acc_value(DF v) { return (double)v.hi + (double)v.lo; }
-__device__ __forceinline__ double acc_value(double v) { return v; }
-// the sum rounded to the working precision (no FP64 operation on the FP32 path)
-__device__ __forceinline__ float acc_t(DF v) { return v.hi + v.lo; }
-__device__ __forceinline__ double acc_t(double v) { return v; }
-template <typename T>
-using SpcgAcc = typename std::conditional<sizeof(T) == 4, DF, double>::type;
-template <typename A>
-__device__ __forceinline__ A acc_zero() {
-  if constexpr (sizeof(A) == 8 && std::is_same<A, double>::value) return 0.0;
-  else return DF{0.f, 0.f};
-}
-__device__ __forceinline__ DF acc_from(float v, DF) { return DF{v, 0.f}; }
-__device__ __forceinline__ double acc_from(double v, double) { return v; }
-
-// Sum of v[k] over the block in a fixed order: every thread returns the same
-// bits (butterfly within warps, then warp 0 adds the warp sums in warp order and
-// broadcasts them).  red: K x 32 accumulators plus K results.  Two barriers.
+// Block-wide sums for the PCG scalars, in the working precision T: the sums are
+// of non-negative terms ((r, r), (r, z), (p, S^ p) with S^ and M^ positive
+// definite), so plain T accumulation keeps their relative error near
+// log2(n) ulps.  Every thread returns the same bits: a butterfly within each
+// warp, then every thread adds the warp sums in one fixed tree.  One barrier:
+// callers alternate between two `red` buffers, so a call never overwrites warp
+// sums that a thread may still be reading from the previous call.
 // Returns the OR of `flag` over the block.
-template <int K, typename A>
-__device__ __forceinline__ int block_allsum(A (&v)[K], A* red, int flag) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+template <int K, typename T>
+__device__ __forceinline__ int block_allsum(T (&v)[K], T* red, int flag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kSpcgThreads / 32;
+  static_assert(NW == 16, "the fixed summation tree is written for 16 warps");
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    A s = v[k];
+    T s = v[k];
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) s = acc_add(s, acc_shfl_xor(s, m));
-    if (lane == 0) red[32 * k + warp] = s;
+    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) red[NW * k + warp] = s;
   }
   const int any = __syncthreads_or(flag);
-  if (threadIdx.x < K) {
-    A s = red[32 * threadIdx.x];
-    for (int w = 1; w < nw; ++w) s = acc_add(s, red[32 * threadIdx.x + w]);
-    red[32 * K + threadIdx.x] = s;
-  }
-  __syncthreads();
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = red[32 * K + k];
+  for (int k = 0; k < K; ++k) {
+    T w[NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) w[i] = red[NW * k + i];
+#pragma unroll
+    for (int h = NW / 2; h > 0; h >>= 1)
+#pragma unroll
+      for (int i = 0; i < h; ++i) w[i] += w[i + h];
+    v[k] = w[0];
+  }
   return any;
 }
 
@@ -511,7 +482,7 @@ __device__ __forceinline__ double cam_dot(const double* a, const double* b) {
   return s;
 }
 
-// z_c = M^_c r_c for one camera (packed symmetric 9x9)
+// z_c = M^_c r_c for one camera (symmetric 9x9 stored in full, row-major)
 template <typename T>
 __device__ __forceinline__ void spcg_precond(const T* __restrict__ M, const T* __restrict__ r, T* __restrict__ z) {
   T rv[9];
@@ -521,14 +492,16 @@ __device__ __forceinline__ void spcg_precond(const T* __restrict__ M, const T* _
   for (int i = 0; i < 9; ++i) {
     T acc = T(0);
 #pragma unroll
-    for (int j = 0; j < 9; ++j) acc += M[sym9(i, j)] * rv[j];
+    for (int j = 0; j < 9; ++j) acc += M[9 * i + j] * rv[j];
     z[i] = acc;
   }
 }
 
 // Persistent PCG: standard preconditioned CG (x0 = 0, block-Jacobi M^).  Thread
 // t handles the vector entries of cameras t, t + 512, ...
-template <typename T>
+// kRows: the block's rows of S^ sit in shared memory (else streamed from device
+// memory by every matvec); one instance per placement keeps registers in check
+template <typename T, bool kRows>
 __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int W = spcg_words<T>();
@@ -537,12 +510,12 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   const int n = a.n, ns = spcg_row_stride<T>(n), Cf = a.Cf;
   const int r0 = (int)(((long long)n * bid) / G), r1 = (int)(((long long)n * (bid + 1)) / G);
   const int nr = r1 - r0;
-  using A = SpcgAcc<T>;
   unsigned char* sp = smem_raw;
-  A* red = reinterpret_cast<A*>(sp);
+  T* red = reinterpret_cast<T*>(sp);
+  int rb = 0;  // which of the two reduction buffers the next block sum uses
   sp += kSpcgRedBytes;
   T* Srows = reinterpret_cast<T*>(sp);
-  sp += a.rows_in_smem ? sizeof(T) * (size_t)nr * ns : 0;
+  sp += kRows ? sizeof(T) * (size_t)nr * ns : 0;
   T* pv = reinterpret_cast<T*>(sp);
   // r, z, q, x and M^ follow p in shared memory, or sit in this block's slice of
   // the global scratch when they do not fit
@@ -554,7 +527,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   const T* Sg = a.Shat + (size_t)r0 * ns;
   const T* dinv = reinterpret_cast<const T*>(a.dscale + n);
 
-  if (a.rows_in_smem) {
+  if constexpr (kRows) {
     // the block's rows of S^ (from HBM once per solve): asynchronous element
     // copies, all in flight together, overlapping the set-up below
     for (int r = warp; r < nr; r += nwarps) {
@@ -565,23 +538,21 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     cp_async_commit();
   }
   for (int c = n + tid; c < ns; c += blockDim.x) pv[c] = T(0);
-  // preconditioner blocks of S^: M^_f = diag(d) M_f diag(d), symmetrised, in T;
-  // one thread per camera, its 81 + 9 loads independent
+  // preconditioner blocks of S^: M^_f = diag(d) M_f diag(d), symmetrised, in T
+  // (the same expression for (i, j) and (j, i), so M^_f is symmetric bit for bit)
   for (int f = tid; f < Cf; f += blockDim.x) {
     const T* Df = a.Dinv + 81 * (size_t)f;
-    T D[81], d[9];
-#pragma unroll
-    for (int k = 0; k < 81; ++k) D[k] = Df[k];
+    T d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = (T)a.dscale[9 * f + i];
 #pragma unroll
     for (int i = 0; i < 9; ++i)
 #pragma unroll
-      for (int j = i; j < 9; ++j) Mv[45 * f + sym9(i, j)] = (T(0.5) * (D[9 * i + j] + D[9 * j + i])) * d[i] * d[j];
+      for (int j = 0; j < 9; ++j) Mv[81 * f + 9 * i + j] = (T(0.5) * (Df[9 * i + j] + Df[9 * j + i])) * (d[i] * d[j]);
   }
   __syncthreads();
   // r = b^, z = M^ r, p = z, x = 0; (r, z) and (r, r)
-  A d0[2] = {acc_zero<A>(), acc_zero<A>()};
+  T d0[2] = {T(0), T(0)};
   for (int f = tid; f < Cf; f += blockDim.x) {
     const int e = 9 * f;
 #pragma unroll
@@ -589,19 +560,20 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
       rv[e + i] = a.b[e + i] * dinv[e + i];  // the correctly rounded product in T
       xv[e + i] = T(0);
     }
-    spcg_precond(Mv + 45 * f, rv + e, zv + e);
+    spcg_precond(Mv + 81 * f, rv + e, zv + e);
 #pragma unroll
     for (int i = 0; i < 9; ++i) pv[e + i] = zv[e + i];
-    d0[0] = acc_add(d0[0], acc_from(cam_dot(rv + e, zv + e), A{}));
-    d0[1] = acc_add(d0[1], acc_from(cam_dot(rv + e, rv + e), A{}));
+    d0[0] += cam_dot(rv + e, zv + e);
+    d0[1] += cam_dot(rv + e, rv + e);
   }
-  if (a.rows_in_smem) cp_async_wait_all();  // visible to the block after the barrier below
-  block_allsum<2>(d0, red, 0);
+  if constexpr (kRows) cp_async_wait_all();  // visible to the block after the barrier below
+  block_allsum<2>(d0, red + kSpcgRedStride * rb, 0);
+  rb ^= 1;
   // the scalars of the iteration in the working precision (T)
-  T rz = acc_t(d0[0]);
-  const double bnorm = sqrt(acc_value(d0[1]));
+  T rz = d0[0];
+  const double bnorm = sqrt((double)d0[1]);
   const T stop_rr = (T)((a.tol * bnorm) * (a.tol * bnorm));
-  T rr_last = acc_t(d0[1]);
+  T rr_last = d0[1];
   int it = 0;
   unsigned long long* words = a.words;
   while (bnorm > 0.0 && it < a.max_iters) {
@@ -610,7 +582,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     unsigned long long* set = words + (size_t)(it & 1) * kSpcgReplicas * set_words;
     // q = S^_rows p for the owned rows, published as tagged words: one warp per row
     if constexpr (sizeof(T) == 4) {
-      if (a.rows_in_smem) {
+      if constexpr (kRows) {
         const float4* p4 = reinterpret_cast<const float4*>(pv);
         for (int r = warp; r < nr; r += nwarps) {
           const float4* row = reinterpret_cast<const float4*>(Srows + (size_t)r * ns);
@@ -628,7 +600,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
       }
     }
     if constexpr (sizeof(T) == 4) {
-      if (!a.rows_in_smem) {
+      if (!kRows) {
         // rows streamed from device memory: 16-byte loads, four in flight per lane
         const float4* p4 = reinterpret_cast<const float4*>(pv);
         const int rs = ns / 4;
@@ -654,7 +626,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
         }
       }
     } else {
-      const T* base = a.rows_in_smem ? Srows : Sg;
+      const T* base = kRows ? Srows : Sg;
       for (int r = warp; r < nr; r += nwarps) {
         const T* row = base + (size_t)r * ns;
         T acc = T(0);
@@ -666,7 +638,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     // gather q from this block's copy, coalesced (thread t: entries t, t + 512, ...,
     // up to four in flight), and (p, q)
     int late = 0;
-    A d1[1] = {acc_zero<A>()};
+    T d1[1] = {T(0)};
     const unsigned long long* mine = set + (size_t)(bid % kSpcgReplicas) * set_words;
     const uint64_t t0 = globaltimer_ns();
     for (int eb = tid; eb < n && !late; eb += 4 * blockDim.x) {
@@ -699,44 +671,69 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
           part = fma(pv[e], q, part);
         }
       }
-      d1[0] = acc_add(d1[0], acc_from(part, A{}));
+      d1[0] += part;
     }
-    if (block_allsum<1>(d1, red, late)) {
+    if (block_allsum<1>(d1, red + kSpcgRedStride * rb, late)) {
       if (tid == 0) atomicOr(a.err, 1);
       break;
     }
-    const T pq = acc_t(d1[0]);
+    rb ^= 1;
+    const T pq = d1[0];
     if (!(pq > T(0) && isfinite(pq))) {
       if (bid == 0 && tid == 0) atomicOr(a.err, 2);
       break;
     }
     const T alpha = rz / pq;
-    // x += alpha p, r -= alpha q, z = M^ r; (r, r) and (r, z)
-    A d2[2] = {acc_zero<A>(), acc_zero<A>()};
-    for (int f = tid; f < Cf; f += blockDim.x) {
-      const int e = 9 * f;
+    // x += alpha p, r -= alpha q, z = M^ r; (r, r) and (r, z).  Two threads per
+    // camera (rows 0-4 and 5-8, adjacent lanes); the loop's trip count is the
+    // same for every thread, so the whole warp meets at __syncwarp.
+    T d2[2] = {T(0), T(0)};
+    for (int base = 0; base < 2 * Cf; base += blockDim.x) {
+      const int t = base + tid, f = t >> 1, h = t & 1;
+      const bool on = t < 2 * Cf;
+      const int e = 9 * f, i0 = h ? 5 : 0, nrow = h ? 4 : 5;
+      T ro[5];  // this thread's rows of r after the update
+      if (on) {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        xv[e + i] = fma(alpha, pv[e + i], xv[e + i]);
-        rv[e + i] = fma(-alpha, qv[e + i], rv[e + i]);
+        for (int ii = 0; ii < 5; ++ii) {
+          ro[ii] = T(0);
+          if (ii < nrow) {
+            const int i = e + i0 + ii;
+            xv[i] = fma(alpha, pv[i], xv[i]);
+            ro[ii] = fma(-alpha, qv[i], rv[i]);
+            rv[i] = ro[ii];
+          }
+        }
       }
-      spcg_precond(Mv + 45 * f, rv + e, zv + e);
-      d2[0] = acc_add(d2[0], acc_from(cam_dot(rv + e, rv + e), A{}));
-      d2[1] = acc_add(d2[1], acc_from(cam_dot(rv + e, zv + e), A{}));
+      __syncwarp();
+      if (on) {
+        T rc[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) rc[j] = rv[e + j];
+        const T* M = Mv + 81 * f + 9 * i0;
+#pragma unroll
+        for (int ii = 0; ii < 5; ++ii) {
+          if (ii < nrow) {
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) acc += M[9 * ii + j] * rc[j];
+            zv[e + i0 + ii] = acc;
+            d2[0] = fma(ro[ii], ro[ii], d2[0]);
+            d2[1] = fma(ro[ii], acc, d2[1]);
+          }
+        }
+      }
     }
-    block_allsum<2>(d2, red, 0);
+    block_allsum<2>(d2, red + kSpcgRedStride * rb, 0);
+    rb ^= 1;
     ++it;
-    const T rr = acc_t(d2[0]), rz_new = acc_t(d2[1]);
+    const T rr = d2[0], rz_new = d2[1];
     rr_last = rr;
     if (rr <= stop_rr) break;
     const T beta = rz != T(0) ? rz_new / rz : T(0);
     rz = rz_new;
-    // p = z + beta p
-    for (int f = tid; f < Cf; f += blockDim.x) {
-      const int e = 9 * f;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) pv[e + i] = fma(beta, pv[e + i], zv[e + i]);
-    }
+    // p = z + beta p, entry-parallel over the block
+    for (int e = tid; e < n; e += blockDim.x) pv[e] = fma(beta, pv[e], zv[e]);
     __syncthreads();
   }
   __syncthreads();
@@ -749,14 +746,16 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
 }
 
 template <typename T>
-const void* spcg_kernel_ptr() {
-  return reinterpret_cast<const void*>(&k_spcg<T>);
+const void* spcg_kernel_ptr(bool rows_in_smem) {
+  return rows_in_smem ? reinterpret_cast<const void*>(&k_spcg<T, true>)
+                      : reinterpret_cast<const void*>(&k_spcg<T, false>);
 }
 
 template <typename T>
 cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s) {
   void* args[] = {const_cast<SpcgArgs<T>*>(&a)};
-  return cudaLaunchCooperativeKernel(spcg_kernel_ptr<T>(), dim3(grid), dim3(kSpcgThreads), args, smem, s);
+  return cudaLaunchCooperativeKernel(spcg_kernel_ptr<T>(a.rows_in_smem != 0), dim3(grid), dim3(kSpcgThreads), args,
+                                     smem, s);
 }
 
 int spcg_threads() { return kSpcgThreads; }
@@ -858,7 +857,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
                                         bool, int, cudaEvent_t, cudaEvent_t, cudaStream_t);            \
   template size_t spcg_smem_bytes<T>(int, int, int, int, int);                                         \
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \
-  template const void* spcg_kernel_ptr<T>();                                                           \
+  template const void* spcg_kernel_ptr<T>(bool);                                                         \
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \
   template cudaError_t launch_backsub_pts<T>(const Layout&, const ModelParams&, const T*, const T*,    \
                                              const uint8_t*, const uint8_t*, const int*, const T*,     \
