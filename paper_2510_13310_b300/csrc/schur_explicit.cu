@@ -412,14 +412,36 @@ __device__ __forceinline__ T spcg_unpack(const unsigned long long* v) {
 }
 
 
+// Preconditioner block of one camera, symmetric 9x9 stored in full: rows 0-4 at
+// 9 i, rows 5-8 from entry 48 on (each half starts on a 16-byte boundary), 84
+// entries per camera
+constexpr int kMStride = 84;
+__host__ __device__ constexpr int mrow(int i) { return 9 * i + (i >= 5 ? 3 : 0); }
+
 constexpr int kSpcgRedStride = 64;  // warp sums of one block reduction (K x 16, K <= 4)
-constexpr size_t kSpcgRedBytes = sizeof(double) * 2 * kSpcgRedStride;  // two alternating buffers
+// two alternating block-sum buffers, then the matvec's per-warp row partials (16 x 16 FP32)
+constexpr size_t kSpcgSumBytes = sizeof(double) * 2 * kSpcgRedStride;
+constexpr size_t kSpcgRedBytes = kSpcgSumBytes + sizeof(float) * 16 * 16;
+
+// One step of a transposing butterfly: CNT values per lane become CNT / 2, each
+// the sum of this lane's and lane ^ M's values for the half of the rows this
+// lane keeps (the lower half when bit M of the lane is clear).
+template <int M, int CNT>
+__device__ __forceinline__ void tstep(float (&v)[16], int lane) {
+  const bool up = lane & M;
+#pragma unroll
+  for (int i = 0; i < CNT / 2; ++i) {
+    const float snd = up ? v[i] : v[i + CNT / 2];
+    const float kp = up ? v[i + CNT / 2] : v[i];
+    v[i] = kp + __shfl_xor_sync(0xffffffffu, snd, M);
+  }
+}
 
 // per-block vector storage other than p: r, z, q, x (full length) and the
-// preconditioner blocks (9x9 each), in T elements
+// preconditioner blocks (kMStride each), in T elements
 template <typename T>
 __host__ __device__ size_t spcg_vec_elems(int n, int Cf) {
-  return (size_t)4 * spcg_row_stride<T>(n) + (size_t)81 * Cf;
+  return (size_t)4 * spcg_row_stride<T>(n) + (size_t)kMStride * Cf;
 }
 
 template <typename T>
@@ -482,7 +504,7 @@ __device__ __forceinline__ double cam_dot(const double* a, const double* b) {
   return s;
 }
 
-// z_c = M^_c r_c for one camera (symmetric 9x9 stored in full, row-major)
+// z_c = M^_c r_c for one camera
 template <typename T>
 __device__ __forceinline__ void spcg_precond(const T* __restrict__ M, const T* __restrict__ r, T* __restrict__ z) {
   T rv[9];
@@ -492,7 +514,7 @@ __device__ __forceinline__ void spcg_precond(const T* __restrict__ M, const T* _
   for (int i = 0; i < 9; ++i) {
     T acc = T(0);
 #pragma unroll
-    for (int j = 0; j < 9; ++j) acc += M[9 * i + j] * rv[j];
+    for (int j = 0; j < 9; ++j) acc += M[mrow(i) + j] * rv[j];
     z[i] = acc;
   }
 }
@@ -548,7 +570,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
 #pragma unroll
     for (int i = 0; i < 9; ++i)
 #pragma unroll
-      for (int j = 0; j < 9; ++j) Mv[81 * f + 9 * i + j] = (T(0.5) * (Df[9 * i + j] + Df[9 * j + i])) * (d[i] * d[j]);
+      for (int j = 0; j < 9; ++j) Mv[kMStride * f + mrow(i) + j] = (T(0.5) * (Df[9 * i + j] + Df[9 * j + i])) * (d[i] * d[j]);
   }
   __syncthreads();
   // r = b^, z = M^ r, p = z, x = 0; (r, z) and (r, r)
@@ -560,7 +582,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
       rv[e + i] = a.b[e + i] * dinv[e + i];  // the correctly rounded product in T
       xv[e + i] = T(0);
     }
-    spcg_precond(Mv + 81 * f, rv + e, zv + e);
+    spcg_precond(Mv + kMStride * f, rv + e, zv + e);
 #pragma unroll
     for (int i = 0; i < 9; ++i) pv[e + i] = zv[e + i];
     d0[0] += cam_dot(rv + e, zv + e);
@@ -575,27 +597,55 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   const T stop_rr = (T)((a.tol * bnorm) * (a.tol * bnorm));
   T rr_last = d0[1];
   int it = 0;
+  T alpha = T(0);
+  bool x_pending = false;  // x still lacks the last alpha p
   unsigned long long* words = a.words;
   while (bnorm > 0.0 && it < a.max_iters) {
     const unsigned tag = a.tag_base + (unsigned)it;
     const size_t set_words = (size_t)n * W;
     unsigned long long* set = words + (size_t)(it & 1) * kSpcgReplicas * set_words;
-    // q = S^_rows p for the owned rows, published as tagged words: one warp per row
+    // q = S^_rows p for the owned rows, published as tagged words
     if constexpr (sizeof(T) == 4) {
       if constexpr (kRows) {
+        // column split: warp w takes a slice of the float4 columns of every owned
+        // row, so p is read from shared memory once per block; per chunk of 16
+        // rows, a transposing butterfly leaves lane l with row (l >> 1)'s warp
+        // partial, and warp r adds row r's 16 warp partials in a fixed order
         const float4* p4 = reinterpret_cast<const float4*>(pv);
-        for (int r = warp; r < nr; r += nwarps) {
-          const float4* row = reinterpret_cast<const float4*>(Srows + (size_t)r * ns);
-          float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-          for (int c = lane; c < ns / 4; c += 32) {
-            const float4 s4 = row[c], p4v = p4[c];
-            c0 += s4.x * p4v.x;
-            c1 += s4.y * p4v.y;
-            c2 += s4.z * p4v.z;
-            c3 += s4.w * p4v.w;
+        float* part = reinterpret_cast<float*>(smem_raw + kSpcgSumBytes);
+        const int nc4 = ns / 4;
+        const int c0 = (nc4 * warp) / nwarps, c1 = (nc4 * (warp + 1)) / nwarps;
+        for (int rc0 = 0; rc0 < nr; rc0 += 16) {
+          const int nrc = min(16, nr - rc0);
+          float v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+          for (int c = c0 + lane; c < c1; c += 32) {
+            const float4 pp = p4[c];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              if (i < nrc) {
+                const float4 s4 = reinterpret_cast<const float4*>(Srows + (size_t)(rc0 + i) * ns)[c];
+                v[i] = fmaf(s4.x, pp.x, fmaf(s4.y, pp.y, fmaf(s4.z, pp.z, fmaf(s4.w, pp.w, v[i]))));
+              }
+            }
           }
-          const float acc = warp_sum((c0 + c1) + (c2 + c3));
-          if (lane < kSpcgReplicas) spcg_publish<T>(set + lane * set_words + (size_t)(r0 + r) * W, acc, tag);
+          tstep<16, 16>(v, lane);
+          tstep<8, 8>(v, lane);
+          tstep<4, 4>(v, lane);
+          tstep<2, 2>(v, lane);
+          v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+          const int row = (lane >> 1) & 15;
+          if (!(lane & 1) && row < nrc) part[16 * row + warp] = v[0];
+          __syncthreads();
+          if (warp < nrc) {
+            float sr = lane < 16 ? part[16 * warp + lane] : 0.f;
+#pragma unroll
+            for (int m = 8; m > 0; m >>= 1) sr += __shfl_xor_sync(0xffffffffu, sr, m);
+            if (lane < kSpcgReplicas)
+              spcg_publish<T>(set + lane * set_words + (size_t)(r0 + rc0 + warp) * W, sr, tag);
+          }
+          if (rc0 + 16 < nr) __syncthreads();  // part is rewritten by the next chunk
         }
       }
     }
@@ -683,40 +733,54 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
       if (bid == 0 && tid == 0) atomicOr(a.err, 2);
       break;
     }
-    const T alpha = rz / pq;
-    // x += alpha p, r -= alpha q, z = M^ r; (r, r) and (r, z).  Two threads per
-    // camera (rows 0-4 and 5-8, adjacent lanes); the loop's trip count is the
-    // same for every thread, so the whole warp meets at __syncwarp.
+    alpha = rz / pq;
+    // r -= alpha q, z = M^ r; (r, r) and (r, z) (x is updated with p below).  Two
+    // threads per camera, adjacent lanes: rows 0-4 and rows 5-8; each takes the
+    // other's rows of r by shuffle.  The loop's trip count is the same for every
+    // thread, so whole warps meet at the shuffles.
     T d2[2] = {T(0), T(0)};
     for (int base = 0; base < 2 * Cf; base += blockDim.x) {
       const int t = base + tid, f = t >> 1, h = t & 1;
       const bool on = t < 2 * Cf;
       const int e = 9 * f, i0 = h ? 5 : 0, nrow = h ? 4 : 5;
       T ro[5];  // this thread's rows of r after the update
-      if (on) {
 #pragma unroll
-        for (int ii = 0; ii < 5; ++ii) {
-          ro[ii] = T(0);
-          if (ii < nrow) {
-            const int i = e + i0 + ii;
-            xv[i] = fma(alpha, pv[i], xv[i]);
-            ro[ii] = fma(-alpha, qv[i], rv[i]);
-            rv[i] = ro[ii];
-          }
+      for (int ii = 0; ii < 5; ++ii) {
+        ro[ii] = T(0);
+        if (on && ii < nrow) {
+          const int i = e + i0 + ii;
+          ro[ii] = fma(-alpha, qv[i], rv[i]);
+          rv[i] = ro[ii];
         }
       }
-      __syncwarp();
-      if (on) {
-        T rc[9];
+      T rc[9];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) rc[j] = rv[e + j];
-        const T* M = Mv + 81 * f + 9 * i0;
+      for (int ii = 0; ii < 5; ++ii) {
+        const T o = __shfl_xor_sync(0xffffffffu, ro[ii], 1);
+        if (ii < 4) rc[5 + ii] = h ? ro[ii] : o;
+        rc[ii] = h ? o : ro[ii];
+      }
+      if (on) {
+        const T* M = Mv + kMStride * f + (h ? 48 : 0);
+        T m[48];
+        if constexpr (sizeof(T) == 4) {
+          const float4* M4 = reinterpret_cast<const float4*>(M);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < 9 || !h) v4 = M4[k];
+            m[4 * k] = v4.x, m[4 * k + 1] = v4.y, m[4 * k + 2] = v4.z, m[4 * k + 3] = v4.w;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 45; ++k) m[k] = (k < 36 || !h) ? M[k] : T(0);
+        }
 #pragma unroll
         for (int ii = 0; ii < 5; ++ii) {
           if (ii < nrow) {
             T acc = T(0);
 #pragma unroll
-            for (int j = 0; j < 9; ++j) acc += M[9 * ii + j] * rc[j];
+            for (int j = 0; j < 9; ++j) acc += m[9 * ii + j] * rc[j];
             zv[e + i0 + ii] = acc;
             d2[0] = fma(ro[ii], ro[ii], d2[0]);
             d2[1] = fma(ro[ii], acc, d2[1]);
@@ -727,15 +791,23 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     block_allsum<2>(d2, red + kSpcgRedStride * rb, 0);
     rb ^= 1;
     ++it;
+    x_pending = true;
     const T rr = d2[0], rz_new = d2[1];
     rr_last = rr;
     if (rr <= stop_rr) break;
     const T beta = rz != T(0) ? rz_new / rz : T(0);
     rz = rz_new;
-    // p = z + beta p, entry-parallel over the block
-    for (int e = tid; e < n; e += blockDim.x) pv[e] = fma(beta, pv[e], zv[e]);
+    // x += alpha p, p = z + beta p, entry-parallel over the block
+    for (int e = tid; e < n; e += blockDim.x) {
+      const T pe = pv[e];
+      xv[e] = fma(alpha, pe, xv[e]);
+      pv[e] = fma(beta, pe, zv[e]);
+    }
+    x_pending = false;
     __syncthreads();
   }
+  if (x_pending)
+    for (int e = tid; e < n; e += blockDim.x) xv[e] = fma(alpha, pv[e], xv[e]);
   __syncthreads();
   for (int e = r0 + tid; e < r1; e += blockDim.x) a.x[e] = xv[e] * dinv[e];
   if (bid == 0 && tid == 0) {
