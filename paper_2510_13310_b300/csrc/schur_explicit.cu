@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     }
     cp_async_commit();
   }
-  for (int c = n + tid; c < ns; c += blockDim.x) pv[c] = T(0);
+  for (int c = n + tid; c < ns; c += blockDim.x) pv[c] = zv[c] = xv[c] = T(0);
   // preconditioner blocks of S^: M^_f = diag(d) M_f diag(d), symmetrised, in T
   // (the same expression for (i, j) and (j, i), so M^_f is symmetric bit for bit)
   for (int f = tid; f < Cf; f += blockDim.x) {
@@ -599,6 +599,10 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   int it = 0;
   T alpha = T(0);
   bool x_pending = false;  // x still lacks the last alpha p
+  // FP32 with the rows in shared memory: x += a_prev p and p = z + b p are applied
+  // by each warp to its own column slice inside the next matvec (no separate pass)
+  constexpr bool kFused = sizeof(T) == 4 && kRows;
+  T a_prev = T(0), b_next = T(0);  // a_prev = 0, b_next = 0 leave x = 0 and p = z
   unsigned long long* words = a.words;
   while (bnorm > 0.0 && it < a.max_iters) {
     const unsigned tag = a.tag_base + (unsigned)it;
@@ -615,13 +619,25 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
         float* part = reinterpret_cast<float*>(smem_raw + kSpcgSumBytes);
         const int nc4 = ns / 4;
         const int c0 = (nc4 * warp) / nwarps, c1 = (nc4 * (warp + 1)) / nwarps;
-        for (int rc0 = 0; rc0 < nr; rc0 += 16) {
-          const int nrc = min(16, nr - rc0);
+        // (one pass even without rows: the x and p updates of the slice happen in it)
+        for (int rc0 = 0; rc0 == 0 || rc0 < nr; rc0 += 16) {
+          const int nrc = max(0, min(16, nr - rc0));
           float v[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = 0.f;
           for (int c = c0 + lane; c < c1; c += 32) {
-            const float4 pp = p4[c];
+            float4 pp = p4[c];
+            if (rc0 == 0) {
+              // this warp's columns of x and p (read by no other warp before the barrier below)
+              const float4 zz = reinterpret_cast<const float4*>(zv)[c];
+              float4 xx = reinterpret_cast<const float4*>(xv)[c];
+              xx.x = fmaf(a_prev, pp.x, xx.x), xx.y = fmaf(a_prev, pp.y, xx.y);
+              xx.z = fmaf(a_prev, pp.z, xx.z), xx.w = fmaf(a_prev, pp.w, xx.w);
+              pp.x = fmaf(b_next, pp.x, zz.x), pp.y = fmaf(b_next, pp.y, zz.y);
+              pp.z = fmaf(b_next, pp.z, zz.z), pp.w = fmaf(b_next, pp.w, zz.w);
+              reinterpret_cast<float4*>(xv)[c] = xx;
+              reinterpret_cast<float4*>(pv)[c] = pp;
+            }
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
               if (i < nrc) {
@@ -685,6 +701,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
         if (lane < kSpcgReplicas) spcg_publish<T>(set + lane * set_words + (size_t)(r0 + r) * W, acc, tag);
       }
     }
+    if constexpr (kFused) x_pending = false;  // the matvec pass applied a_prev p
     // gather q from this block's copy, coalesced (thread t: entries t, t + 512, ...,
     // up to four in flight), and (p, q)
     int late = 0;
@@ -797,14 +814,19 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     if (rr <= stop_rr) break;
     const T beta = rz != T(0) ? rz_new / rz : T(0);
     rz = rz_new;
-    // x += alpha p, p = z + beta p, entry-parallel over the block
-    for (int e = tid; e < n; e += blockDim.x) {
-      const T pe = pv[e];
-      xv[e] = fma(alpha, pe, xv[e]);
-      pv[e] = fma(beta, pe, zv[e]);
+    if constexpr (kFused) {
+      a_prev = alpha;
+      b_next = beta;
+    } else {
+      // x += alpha p, p = z + beta p, entry-parallel over the block
+      for (int e = tid; e < n; e += blockDim.x) {
+        const T pe = pv[e];
+        xv[e] = fma(alpha, pe, xv[e]);
+        pv[e] = fma(beta, pe, zv[e]);
+      }
+      x_pending = false;
+      __syncthreads();
     }
-    x_pending = false;
-    __syncthreads();
   }
   if (x_pending)
     for (int e = tid; e < n; e += blockDim.x) xv[e] = fma(alpha, pv[e], xv[e]);
