@@ -73,6 +73,10 @@ struct ba_problem {
   // layout arrays (device)
   int *po_cam = nullptr, *po_pt = nullptr, *po_orig = nullptr, *pt_off = nullptr;
   double *po_uv64 = nullptr, *po_tau64 = nullptr;
+  float4* po_uvdf = nullptr;  // double-float copies for the FP32 problems' evaluation
+  F2* po_taudf = nullptr;
+  F2* camdf = nullptr;
+  float4* ptdf = nullptr;
   void *po_uvw = nullptr, *po_tauw = nullptr, *co_uvw = nullptr, *co_tauw = nullptr;
   int *co_pt = nullptr, *co_po = nullptr, *po_wrow = nullptr;
   int *chunk_obs = nullptr, *chunk_cam = nullptr, *cam_chunk = nullptr;
@@ -226,16 +230,22 @@ ba_status sync(ba_problem* pb) {
 // evaluation and extraction
 // ---------------------------------------------------------------------------
 
-// FP64 pass over a state slot: validity bits (if bits != null) and the cost over
+// Evaluation pass over a state slot (FP64, or double-float for FP32 problems): validity bits (if bits != null) and the cost over
 // the current active set (if with_cost) into sc->cost[slot].  ref_slot >= 0:
 // compare the validity bits with that slot's (sc->valid_flips, cleared here).
 ba_status eval_state(ba_problem* pb, int slot, bool want_bits, bool with_cost, int ref_slot = -1) {
   const bool cmp = want_bits && ref_slot >= 0 && ref_slot != slot && pb->bits_valid[ref_slot];
   if (cmp) CU(cudaMemsetAsync(&pb->sc->valid_flips, 0, sizeof(int), pb->stream));
-  LAUNCH(1, launch_eval64(pb->L, pb->mp, pb->camw64[slot], pb->pts64[slot],
-                          with_cost ? pb->obs_act : nullptr, want_bits ? pb->bits[slot] : nullptr,
-                          cmp ? pb->bits[ref_slot] : nullptr, cmp ? &pb->sc->valid_flips : nullptr,
-                          with_cost ? pb->eval_parts : nullptr, pb->eval_grid, pb->stream));
+  if (pb->fp64)
+    LAUNCH(1, launch_eval64(pb->L, pb->mp, pb->camw64[slot], pb->pts64[slot],
+                            with_cost ? pb->obs_act : nullptr, want_bits ? pb->bits[slot] : nullptr,
+                            cmp ? pb->bits[ref_slot] : nullptr, cmp ? &pb->sc->valid_flips : nullptr,
+                            with_cost ? pb->eval_parts : nullptr, pb->eval_grid, pb->stream));
+  else
+    LAUNCH(2, launch_eval_df(pb->L, pb->mp, pb->camw64[slot], pb->pts64[slot], pb->camdf, pb->ptdf,
+                             with_cost ? pb->obs_act : nullptr, want_bits ? pb->bits[slot] : nullptr,
+                             cmp ? pb->bits[ref_slot] : nullptr, cmp ? &pb->sc->valid_flips : nullptr,
+                             with_cost ? pb->eval_parts : nullptr, pb->eval_grid, pb->stream));
   pb->flips_known = cmp;
   if (with_cost) LAUNCH(1, launch_reduce_eval(pb->eval_parts, pb->eval_grid, pb->sc, slot, pb->stream));
   if (want_bits) pb->bits_valid[slot] = true;
@@ -779,6 +789,13 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
                                          pb->po_uv64, pb->po_tau64, (float*)pb->po_uvw, (float*)pb->po_tauw,
                                          pb->co_pt, (float*)pb->co_uvw, (float*)pb->co_tauw, pb->stream));
   }
+  if (!pb->fp64) {
+    ST(dalloc(pb, &pb->po_uvdf, (size_t)N));
+    ST(dalloc(pb, &pb->po_taudf, (size_t)N));
+    ST(dalloc(pb, &pb->camdf, (size_t)16 * C));
+    ST(dalloc(pb, &pb->ptdf, (size_t)2 * P));
+    if (N) LAUNCH(1, launch_obs_df(N, pb->po_uv64, pb->po_tau64, pb->po_uvdf, pb->po_taudf, pb->stream));
+  }
   ST(dalloc(pb, &pb->cam_fixed, (size_t)C));
   if (C) CU(cudaMemcpy(pb->cam_fixed, h_fixed.data(), (size_t)C, cudaMemcpyHostToDevice));
 
@@ -793,6 +810,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   L.po_orig = pb->po_orig;
   L.po_uv64 = pb->po_uv64;
   L.po_tau64 = pb->po_tau64;
+  L.po_uvdf = pb->po_uvdf;
+  L.po_taudf = pb->po_taudf;
   L.po_uvw = pb->po_uvw;
   L.po_tauw = pb->po_tauw;
   L.pt_off = pb->pt_off;
@@ -1021,7 +1040,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   }
   pb->bs_grid = std::max(1, std::min(pb->num_sms * 8, (P + 255) / 256));
   ST(dalloc(pb, &pb->pred_parts, (size_t)std::max(pb->pcg_grid, pb->bs_grid) + 1));
-  pb->eval_grid = std::max(1, std::min(pb->num_sms * 8, (N + kBlock - 1) / kBlock));
+  // double-float evaluation (FP32 problems): fewer, longer-lived threads amortise each thread's FP64 tail
+  pb->eval_grid = std::max(1, std::min(pb->num_sms * (pb->fp64 ? 8 : 4), (N + kBlock - 1) / kBlock));
   ST(dalloc(pb, &pb->eval_parts, (size_t)3 * pb->eval_grid));
   ST(dalloc(pb, &pb->sc, 1));
   CU(cudaMemset(pb->sc, 0, sizeof(Scalars)));

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "df.cuh"
 
 namespace bab {
 
@@ -42,6 +43,13 @@ struct Layout {
   const int* chunk_cam;    // [n_chunks]
   const int* cam_chunk;    // [C+1] chunk range of each camera
   const uint8_t* cam_fixed;  // [C]
+  const float4* po_uvdf;   // [N] (u, v) as double-float pairs (FP32 problems; else null)
+  const F2* po_taudf;      // [N] tau as a double-float pair (FP32 problems; else null)
+};
+
+// model constants of the double-float evaluation as (hi, lo) pairs
+struct EvalDFConst {
+  F2 cx, cy, huber, huber2, two_huber, sw_valid, sw_invalid, min_depth, img_w, img_h, drop2;
 };
 
 struct ModelParams {
@@ -158,6 +166,12 @@ cudaError_t launch_obs_layout(int N, const double* uv, const double* depth, cons
 cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* camw64,
                           const double* pts64, const uint8_t* act, uint8_t* bits,
                           const uint8_t* ref_bits, int* flips, double* partials, int grid, cudaStream_t s);
+// double-float evaluation of FP32 problems (same outputs as launch_eval64);
+// camdf [C][16] and ptdf [P][2] are scratch for the converted state
+cudaError_t launch_eval_df(const Layout& L, const ModelParams& mp, const double* camw64, const double* pts64,
+                           F2* camdf, float4* ptdf, const uint8_t* act, uint8_t* bits, const uint8_t* ref_bits,
+                           int* flips, double* partials, int grid, cudaStream_t s);
+cudaError_t launch_obs_df(int N, const double* uv64, const double* tau64, float4* uvdf, F2* taudf, cudaStream_t s);
 cudaError_t launch_reduce_eval(const double* partials, int nparts, Scalars* sc, int slot,
                                cudaStream_t s);
 

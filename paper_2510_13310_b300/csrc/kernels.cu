@@ -6,6 +6,7 @@
 // reduced per camera.  No kernel uses global floating-point atomics: camera
 // sums go through fixed-order chunk partials, point sums through per-tile
 // shared memory.
+#include "df.cuh"
 #include "internal.h"
 #include "model.cuh"
 
@@ -175,6 +176,204 @@ cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* 
                           const uint8_t* ref_bits, int* flips, double* partials, int grid, cudaStream_t s) {
   k_eval64<<<grid, kBlock, 0, s>>>(L, mp, camw64, pts64, act, bits, bits ? ref_bits : nullptr, flips,
                                     partials);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The same evaluation in double-float arithmetic (FP32 problems): FP64 is the
+// scarce pipe on this part, and the projection needs ~1e-15 relative accuracy
+// only because the residual uh - u cancels three to four digits.  Every
+// validity decision whose double-float margin is within 2^-30 of the scale of
+// its operands, and every observation with a non-finite intermediate, is
+// re-evaluated in FP64 (eval_obs64), so the bits follow the FP64 definition.
+// ---------------------------------------------------------------------------
+
+// cameras [C][32] floats: R (9), t (3), f, k1, k2 as (hi, lo) pairs; points
+// [P][2] float4: (X0, X1), (X2, 0)
+__global__ void k_state_df(int C, int P, const double* __restrict__ camw64, const double* __restrict__ pts64,
+                           F2* __restrict__ camdf, float4* __restrict__ ptdf) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(C * 16, P); i += gridDim.x * blockDim.x) {
+    if (i < C * 16) {
+      const int c = i >> 4, q = i & 15;
+      camdf[16 * (size_t)c + q] = q < 15 ? f2_from_double(camw64[kCamStride * (size_t)c + q]) : F2{0.f, 0.f};
+    }
+    if (i < P) {
+      const F2 x0 = f2_from_double(pts64[3 * (size_t)i]), x1 = f2_from_double(pts64[3 * (size_t)i + 1]),
+               x2 = f2_from_double(pts64[3 * (size_t)i + 2]);
+      ptdf[2 * (size_t)i] = make_float4(x0.h, x0.l, x1.h, x1.l);
+      ptdf[2 * (size_t)i + 1] = make_float4(x2.h, x2.l, 0.f, 0.f);
+    }
+  }
+}
+
+// observations in point order: (u, v) and tau as (hi, lo) pairs, once at creation
+__global__ void k_obs_df(int N, const double* __restrict__ uv64, const double* __restrict__ tau64,
+                         float4* __restrict__ uvdf, F2* __restrict__ taudf) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    const F2 u = f2_from_double(uv64[2 * (size_t)k]), v = f2_from_double(uv64[2 * (size_t)k + 1]);
+    uvdf[k] = make_float4(u.h, u.l, v.h, v.l);
+    taudf[k] = f2_from_double(tau64[k]);
+  }
+}
+
+// |d| is not clearly away from 0 at the scale `scale` of the compared values
+__device__ __forceinline__ bool near_zero(F2 d, float scale) { return fabsf(d.h) <= scale * 0x1p-30f; }
+
+__global__ void __launch_bounds__(kBlock) k_eval_df(Layout L, ModelParams mp, EvalDFConst ec, const F2* __restrict__ camdf,
+                                                    const float4* __restrict__ ptdf, const double* __restrict__ camw64,
+                                                    const double* __restrict__ pts64, const uint8_t* __restrict__ act,
+                                                    uint8_t* __restrict__ bits, const uint8_t* __restrict__ ref_bits,
+                                                    int* __restrict__ flips, double* __restrict__ partials,
+                                                    int cam_smem) {
+  // the camera table in shared memory when it fits, 9 float4 per camera (the
+  // odd stride spreads the lanes' random cameras over the bank groups)
+  extern __shared__ __align__(16) float4 cam_s[];
+  const bool cam_in_smem = cam_smem;
+  if (cam_in_smem) {
+    const float4* src = reinterpret_cast<const float4*>(camdf);
+    for (int i = threadIdx.x; i < 8 * L.C; i += blockDim.x) cam_s[9 * (i >> 3) + (i & 7)] = src[i];
+    __syncthreads();
+  }
+  int flip = 0;
+  F2 acc_cost{0.f, 0.f}, acc_e2{0.f, 0.f};
+  int acc_n = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += gridDim.x * blockDim.x) {
+    const int c = L.po_cam[k], p = L.po_pt[k];
+    F2 cw[16];
+    {
+      const float4* cr = cam_in_smem ? cam_s + 9 * c : reinterpret_cast<const float4*>(camdf) + 8 * (size_t)c;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = cr[q];
+        cw[2 * q] = F2{v.x, v.y};
+        cw[2 * q + 1] = F2{v.z, v.w};
+      }
+    }
+    const float4 xa = ptdf[2 * (size_t)p], xb = ptdf[2 * (size_t)p + 1];
+    const F2 X0{xa.x, xa.y}, X1{xa.z, xa.w}, X2{xb.x, xb.y};
+    const float4 uv = L.po_uvdf[k];
+    const F2 tau = L.po_taudf[k];
+    const bool has_d = tau.h > 0.f;
+    const F2 px = f2_add(f2_fma(cw[0], X0, f2_fma(cw[1], X1, f2_mul(cw[2], X2))), cw[9]);
+    const F2 py = f2_add(f2_fma(cw[3], X0, f2_fma(cw[4], X1, f2_mul(cw[5], X2))), cw[10]);
+    const F2 pz = f2_add(f2_fma(cw[6], X0, f2_fma(cw[7], X1, f2_mul(cw[8], X2))), cw[11]);
+    const F2 iz = f2_recip(pz);
+    const F2 xn = f2_mul(px, iz), yn = f2_mul(py, iz);
+    const F2 rr = f2_fma(xn, xn, f2_mul(yn, yn));
+    const F2 dist = f2_fma(rr, f2_fma(cw[14], rr, cw[13]), F2{1.f, 0.f});
+    const F2 fd = f2_mul(cw[12], dist);
+    const F2 uh = f2_fma(fd, xn, ec.cx), vh = f2_fma(fd, yn, ec.cy);
+    const F2 r0 = f2_sub(uh, F2{uv.x, uv.y}), r1 = f2_sub(vh, F2{uv.z, uv.w});
+    const F2 r2 = f2_mul(has_d ? ec.sw_valid : ec.sw_invalid, f2_sub(iz, tau));
+    const F2 e2 = f2_fma(r0, r0, f2_mul(r1, r1));
+    const F2 s = f2_fma(r2, r2, e2);
+    bool slow = !(f2_finite(uh) && f2_finite(vh) && f2_finite(pz) && f2_finite(s));
+    int b = 0;
+    if (bits && !slow) {
+      const F2 dz = f2_sub(pz, ec.min_depth);
+      const F2 du = f2_sub(uh, ec.img_w), dv = f2_sub(vh, ec.img_h);
+      const float su = fabsf(uh.h) + fabsf(ec.cx.h) + fabsf(ec.img_w.h);
+      const float sv = fabsf(vh.h) + fabsf(ec.cy.h) + fabsf(ec.img_h.h);
+      slow = near_zero(dz, fabsf(pz.h) + fabsf(ec.min_depth.h)) || near_zero(uh, su) || near_zero(du, su) ||
+             near_zero(vh, sv) || near_zero(dv, sv);
+      const bool ok = dz.h > 0.f && uh.h >= 0.f && du.h < 0.f && vh.h >= 0.f && dv.h < 0.f;
+      b = ok ? 1 : 0;
+      if (ok && ec.drop2.h > 0.f) {
+        const F2 dd = f2_sub(e2, ec.drop2);
+        slow = slow || near_zero(dd, e2.h + ec.drop2.h);
+        if (dd.h > 0.f) b |= 2;
+      }
+    }
+    F2 rho = s, e2v = e2;
+    if (slow) {
+      // FP64 evaluation of this observation (rare)
+      const double* X = pts64 + 3 * (size_t)p;
+      const double tau64 = L.po_tau64[k];
+      const double sw = __double_as_longlong(tau64) > 0 ? mp.sw_valid : mp.sw_invalid;
+      const Eval64 e = eval_obs64(camw64 + kCamStride * (size_t)c, X[0], X[1], X[2], L.po_uv64[2 * (size_t)k],
+                                  L.po_uv64[2 * (size_t)k + 1], tau64, sw, mp.cx, mp.cy);
+      const double e2d = fma(e.r0, e.r0, e.r1 * e.r1);
+      if (bits) {
+        const long long kz = dkey(mp.min_depth), kw = dkey((double)mp.img_w), kh = dkey((double)mp.img_h);
+        const long long ku = dkey(e.uh), kv = dkey(e.vh);
+        const int ok = dkey(e.z) > kz && ku >= 0 && ku < kw && kv >= 0 && kv < kh;
+        b = ok ? 1 : 0;
+        if (ok && mp.drop_px > 0.0 && sqrt(e2d) > mp.drop_px) b |= 2;
+      }
+      e2v = f2_from_double(e2d);
+      rho = f2_from_double(huber_loss(fma(e.r2, e.r2, e2d), mp.huber));
+    } else if (ec.huber.h > 0.f && f2_sub(s, ec.huber2).h > 0.f) {
+      rho = f2_sub(f2_mul(ec.two_huber, f2_sqrt(s)), ec.huber2);  // 2 delta sqrt(s) - delta^2
+    }
+    if (bits) {
+      bits[k] = (uint8_t)b;
+      if (ref_bits) flip |= (b ^ ref_bits[k]) & 1;
+    }
+    if (act && act[k]) {
+      acc_cost = f2_add(acc_cost, rho);
+      acc_e2 = f2_add(acc_e2, e2v);
+      acc_n += 1;
+    }
+  }
+  if (ref_bits) {
+    if (__syncthreads_or(flip) && threadIdx.x == 0) atomicOr(flips, 1);
+  }
+  if (!partials) return;
+  // warp sums in double-float (fixed butterfly), then the warp sums in FP64 in warp order
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    acc_cost = f2_add(acc_cost, F2{__shfl_xor_sync(0xffffffffu, acc_cost.h, m), __shfl_xor_sync(0xffffffffu, acc_cost.l, m)});
+    acc_e2 = f2_add(acc_e2, F2{__shfl_xor_sync(0xffffffffu, acc_e2.h, m), __shfl_xor_sync(0xffffffffu, acc_e2.l, m)});
+    acc_n += __shfl_xor_sync(0xffffffffu, acc_n, m);
+  }
+  __shared__ double ws[3][kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    ws[0][warp] = f2_to_double(acc_cost);
+    ws[1][warp] = f2_to_double(acc_e2);
+    ws[2][warp] = (double)acc_n;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) t += ws[threadIdx.x][w];
+    partials[3 * blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+static F2 host_f2(double x) {
+  const float h = (float)x;
+  return F2{h, (float)(x - (double)h)};
+}
+
+cudaError_t launch_eval_df(const Layout& L, const ModelParams& mp, const double* camw64, const double* pts64,
+                           F2* camdf, float4* ptdf, const uint8_t* act, uint8_t* bits, const uint8_t* ref_bits,
+                           int* flips, double* partials, int grid, cudaStream_t s) {
+  const int nconv = std::max(L.C * 16, L.P);
+  if (nconv > 0)
+    k_state_df<<<std::min((nconv + 255) / 256, 4096), 256, 0, s>>>(L.C, L.P, camw64, pts64, camdf, ptdf);
+  EvalDFConst ec;
+  ec.cx = host_f2(mp.cx);
+  ec.cy = host_f2(mp.cy);
+  ec.huber = host_f2(mp.huber > 0.0 ? mp.huber : 0.0);
+  ec.huber2 = host_f2(mp.huber > 0.0 ? mp.huber * mp.huber : 0.0);
+  ec.two_huber = host_f2(mp.huber > 0.0 ? 2.0 * mp.huber : 0.0);
+  ec.sw_valid = host_f2(mp.sw_valid);
+  ec.sw_invalid = host_f2(mp.sw_invalid);
+  ec.min_depth = host_f2(mp.min_depth);
+  ec.img_w = host_f2((double)mp.img_w);
+  ec.img_h = host_f2((double)mp.img_h);
+  ec.drop2 = host_f2(mp.drop_px > 0.0 ? mp.drop_px * mp.drop_px : 0.0);
+  const size_t cam_bytes = (size_t)144 * L.C;
+  const int cam_smem = cam_bytes <= 48 * 1024 ? 1 : 0;
+  k_eval_df<<<grid, kBlock, cam_smem ? cam_bytes : 0, s>>>(L, mp, ec, camdf, ptdf, camw64, pts64, act, bits,
+                                                          bits ? ref_bits : nullptr, flips, partials, cam_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_obs_df(int N, const double* uv64, const double* tau64, float4* uvdf, F2* taudf, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  k_obs_df<<<std::min((N + 255) / 256, 65535), 256, 0, s>>>(N, uv64, tau64, uvdf, taudf);
   return cudaGetLastError();
 }
 
