@@ -1,9 +1,9 @@
 """Benchmark: LM bundle-adjustment iterations/s on the 1M-observation scene.
 
 Workload: 200 cameras, 100k points, ~1M observations (track length 3-20,
-truncated geometric, mean 10), FP32 hot path with the cost and gain ratio in
-FP64 and the PCG scalars in FP64 (implicit system) or FP32 double-float pairs
-(explicit system); 2% outliers, depth priors on 50% of observations.  A step is one
+truncated geometric, mean 10), FP32 hot path with the cost in double-float
+arithmetic (FP32 pairs; 1e-12 relative to FP64), the gain ratio in FP64 and the
+PCG scalars in FP64 (implicit system) or FP32 (explicit system); 2% outliers, depth priors on 50% of observations.  A step is one
 full LM iteration (extraction, residuals/Jacobians, normal equations and
 Schur terms, PCG + back-substitution, candidate evaluation and accept/reject).
 
@@ -470,7 +470,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": _workload_name(scene) + ", FP32 with FP64 cost and gain ratio",
+            "config": {"workload": _workload_name(scene) + ", FP32 with double-float cost and FP64 gain ratio",
                        "n_cams": scene.spec.n_cams, "n_pts": P, "n_obs": N,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)"},

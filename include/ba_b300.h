@@ -53,9 +53,12 @@ typedef enum {
 typedef enum { BA_FP64 = 0, BA_FP32 = 1 } ba_precision;
 
 typedef struct {
-  ba_precision precision;      /* BA_FP64: every step in FP64.  BA_FP32: (a),(b),(d) in FP32
-                                  with FP64 PCG dot products; cost, gain ratio and the
-                                  extraction predicate always in FP64 */
+  ba_precision precision;      /* BA_FP64: every step in FP64.  BA_FP32: (a),(b),(d) in FP32;
+                                  the cost in double-float arithmetic (FP32 pairs, ~48-bit
+                                  significand; 1e-12 relative to the FP64 cost), the gain
+                                  ratio in FP64, the extraction predicate with FP64 semantics
+                                  (decisions within rounding of a threshold are re-evaluated
+                                  in FP64) */
   int img_w, img_h;            /* image size for the in-frustum test (640, 480) */
   double cx, cy;               /* principal point, held fixed (320, 240) */
   double huber_delta;          /* Huber threshold on |r| in px (1.0); <= 0: squared loss */
@@ -167,8 +170,9 @@ ba_status ba_linearize(ba_problem* pb, double* U, double* V, double* W, double* 
 ba_status ba_solve_damped(ba_problem* pb, double lambda, double* dc, double* dp,
                           ba_iter_info* info);
 
-/* FP64 cost 1/2 sum rho and RMSE of the given parameters over the current
- * active set (NULL cams/pts: the current parameters). */
+/* Cost 1/2 sum rho and RMSE of the given parameters over the current active
+ * set (NULL cams/pts: the current parameters); FP64 for BA_FP64 problems,
+ * double-float for BA_FP32 problems (see ba_options.precision). */
 ba_status ba_eval_cost(ba_problem* pb, const double* cams, const double* pts, double* cost,
                        double* rmse_px);
 

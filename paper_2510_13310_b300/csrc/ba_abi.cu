@@ -887,7 +887,32 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     // 25-46 iterations there; AUTO therefore never picks it.
     const bool dense = so == BA_SOLVER_DENSE;
     pb->dense = dense;
-    pb->explicit_S = dense || so == BA_SOLVER_EXPLICIT || (so == BA_SOLVER_AUTO && 9 * C <= 4608);
+    bool auto_explicit = false;
+    if (so == BA_SOLVER_AUTO) {
+      if (9 * C <= 4608) {
+        auto_explicit = true;  // S^ rows in shared memory: a few microseconds per PCG iteration
+      } else {
+        // Per-LM-step cost model, constants measured on this part (FP32, 148 SMs):
+        // explicit = forming S^ (0.1 ns per co-visible pair, 3 passes of 4 n^2 bytes,
+        // 50 ps per observation for Y^) + iterations x (4 n^2 bytes streamed at
+        // 4.9 TB/s + 10 us); implicit = iterations x (66 ps per observation +
+        // 245 ps per point).  40 iterations assumed (25-70 measured on the
+        // large and dense workloads).  A function of the problem's sizes only,
+        // so the choice is deterministic.
+        double pairs = 0.0;
+        for (int p = 0; p < P; ++p) {
+          const double t = (double)(dl.h_pt_off[p + 1] - dl.h_pt_off[p]);
+          pairs += 0.5 * t * (t - 1.0);
+        }
+        const double n = 9.0 * C, it = 40.0;
+        const double t_exp = pairs * 0.1e-9 + 3.0 * 4.0 * n * n / 6.5e12 + N * 50e-12 +
+                             it * (4.0 * n * n / 4.9e12 + 10e-6);
+        const double t_imp = it * (N * 66e-12 + P * 245e-12);
+        // and only within the explicit system's memory bound below
+        auto_explicit = t_exp < t_imp && (size_t)81 * C * C * (R + 8) <= ((size_t)8 << 30);
+      }
+    }
+    pb->explicit_S = dense || so == BA_SOLVER_EXPLICIT || auto_explicit;
     if (pb->explicit_S && (size_t)81 * C * C * (R + (dense ? 4 : 8)) > ((size_t)(dense ? 24 : 8) << 30)) {
       set_error("explicit reduced camera system of order %d is too large", 9 * C);
       return BA_ERR_INVALID_ARG;

@@ -166,6 +166,21 @@ def test_damped_step_matches_oracle(precision, tol, solver):
     assert not g["dc"][sc.fixed_cams].any()
 
 
+def test_auto_solver_choice_follows_the_cost_model():
+    """AUTO: the explicit system whenever 9 C <= 4608; above that, the per-step cost
+    model (formation + streamed S^ against the implicit matvec).  A scene of 700
+    cameras with tracks of 2-4 has few co-visible pairs but a 6,300-order S^ whose
+    streaming costs more per iteration than the implicit matvec over 20k
+    observations: implicit."""
+    small = ba.Problem.from_scene(geometric(40, 3000, 2, 10, 5.0, seed=5), ba.Options())
+    assert small.solver_kind == ba.BA_SOLVER_EXPLICIT and small.explicit_layout["rows_in_smem"] == 1
+    sparse = ba.Problem.from_scene(geometric(700, 8000, 2, 4, 3.0, seed=6), ba.Options())
+    assert sparse.solver_kind == ba.BA_SOLVER_IMPLICIT
+    assert sparse.explicit_layout == {"rows_in_smem": 0, "vecs_in_smem": 0, "grid": 0}
+    small.close()
+    sparse.close()
+
+
 @pytest.mark.parametrize("precision,n_cams,tol", [(ba.BA_FP64, 400, 1e-7), (ba.BA_FP32, 700, 2e-2)])
 def test_explicit_solver_vectors_in_global_scratch(precision, n_cams, tol):
     # systems of 3,591 (FP64) and 6,291 (FP32) unknowns: the explicit PCG keeps p
