@@ -37,10 +37,9 @@ from paper_2510_13310_b300 import scenes  # noqa: E402
 METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 GPU"
 
 # DRAM bytes (read + write) of one launch of each roofline kernel, from ncu
-# captures of this workload (profiles/k_spcg_medium_1M_obs.md,
-# profiles/k_form_S_runs_and_k_eval64_medium_1M_obs.md); None once the kernel
-# has changed since the counters were taken.
-NCU_TRAFFIC = {"k_spcg": 13158912 + 39936, "k_pcg": None, "k_form_S_runs": 324913408 + 8682496}
+# captures of this workload (profiles/top_kernels_traffic_medium_1M_obs.md); None
+# once the kernel has changed since the counters were taken.
+NCU_TRAFFIC = {"k_spcg": 13152000 + 27136, "k_pcg": None, "k_form_S_runs": 325550080 + 8276736}
 WORKLOAD = "medium"
 LM_ITERS = 30
 
