@@ -240,14 +240,13 @@ ba_status eval_state(ba_problem* pb, int slot, bool want_bits, bool with_cost, i
     LAUNCH(1, launch_eval64(pb->L, pb->mp, pb->camw64[slot], pb->pts64[slot],
                             with_cost ? pb->obs_act : nullptr, want_bits ? pb->bits[slot] : nullptr,
                             cmp ? pb->bits[ref_slot] : nullptr, cmp ? &pb->sc->valid_flips : nullptr,
-                            with_cost ? pb->eval_parts : nullptr, pb->eval_grid, pb->stream));
+                            with_cost ? pb->eval_parts : nullptr, pb->sc, slot, pb->eval_grid, pb->stream));
   else
     LAUNCH(2, launch_eval_df(pb->L, pb->mp, pb->camw64[slot], pb->pts64[slot], pb->camdf, pb->ptdf,
                              with_cost ? pb->obs_act : nullptr, want_bits ? pb->bits[slot] : nullptr,
                              cmp ? pb->bits[ref_slot] : nullptr, cmp ? &pb->sc->valid_flips : nullptr,
-                             with_cost ? pb->eval_parts : nullptr, pb->eval_grid, pb->stream));
+                             with_cost ? pb->eval_parts : nullptr, pb->sc, slot, pb->eval_grid, pb->stream));
   pb->flips_known = cmp;
-  if (with_cost) LAUNCH(1, launch_reduce_eval(pb->eval_parts, pb->eval_grid, pb->sc, slot, pb->stream));
   if (want_bits) pb->bits_valid[slot] = true;
   if (with_cost) pb->cost_valid[slot] = true;
   return BA_OK;
@@ -429,11 +428,9 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   }
   LAUNCH(2, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                                   pb->pt_act, pb->crank, (const T*)pb->x, (const T*)pb->Vinv, (const T*)pb->V,
-                                  (const T*)pb->gp, (const T*)pb->W, lambda, (T*)pb->dp, (T*)pb->bs_wx,
-                                  pb->pred_parts, pb->bs_grid, pb->stream));
-  LAUNCH(1, launch_pred_cams<T>(Cf, pb->cam_map, (const T*)pb->x, (const T*)pb->Ug, (const T*)pb->dampc,
-                                lambda, pb->pred_parts, pb->bs_grid, pb->stream));
-  LAUNCH(1, launch_reduce_pred(pb->pred_parts, pb->bs_grid + 1, pb->sc, pb->stream));
+                                  (const T*)pb->gp, (const T*)pb->W, lambda, (T*)pb->dp, (T*)pb->bs_wx, Cf,
+                                  pb->cam_map, (const T*)pb->Ug, (const T*)pb->dampc, pb->pred_parts, pb->sc,
+                                  pb->bs_grid, pb->stream));
   return BA_OK;
 }
 

@@ -41,6 +41,8 @@ struct Scalars {
   int n_pt_act;
   int n_cam_act;
   int valid_flips;       // evaluation: some validity bit differs from the reference slot's
+  unsigned done_eval;    // blocks of the evaluation kernel that have written their partials
+  unsigned done_pred;    // blocks of the back-substitution kernel likewise
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -70,6 +72,19 @@ __device__ T block_sum(T v, T* red /* >= 32 entries */) {
   T s = T(0);
   for (int i = 0; i < nw; ++i) s += red[i];
   return s;
+}
+
+// Last-block-done: every block has written its partials (the writers fence, then
+// one atomic increment per block); returns true in the block that arrived last,
+// to which all partials are visible (read them with __ldcg).  That block resets
+// the counter for the next launch.
+__device__ __forceinline__ bool last_block_done(unsigned* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
 }
 
 // FP64 is scarce on B300 (a small fraction of the FP32 rate), so FP64 sums run

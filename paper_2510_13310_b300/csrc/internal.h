@@ -163,14 +163,17 @@ cudaError_t launch_obs_layout(int N, const double* uv, const double* depth, cons
                               const int* co_po, const int* po_pt, int* po_wrow, double* po_uv64, double* po_tau64,
                               T* po_uvw, T* po_tauw, int* co_pt, T* co_uvw, T* co_tauw, cudaStream_t s);
 
+// partials (nullable): per-block sums; the last block reduces them into
+// sc->cost[slot], rmse_sum[slot], n_act[slot]
 cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* camw64,
                           const double* pts64, const uint8_t* act, uint8_t* bits,
-                          const uint8_t* ref_bits, int* flips, double* partials, int grid, cudaStream_t s);
+                          const uint8_t* ref_bits, int* flips, double* partials, Scalars* sc, int slot, int grid,
+                          cudaStream_t s);
 // double-float evaluation of FP32 problems (same outputs as launch_eval64);
 // camdf [C][16] and ptdf [P][2] are scratch for the converted state
 cudaError_t launch_eval_df(const Layout& L, const ModelParams& mp, const double* camw64, const double* pts64,
                            F2* camdf, float4* ptdf, const uint8_t* act, uint8_t* bits, const uint8_t* ref_bits,
-                           int* flips, double* partials, int grid, cudaStream_t s);
+                           int* flips, double* partials, Scalars* sc, int slot, int grid, cudaStream_t s);
 cudaError_t launch_obs_df(int N, const double* uv64, const double* tau64, float4* uvdf, F2* taudf, cudaStream_t s);
 cudaError_t launch_reduce_eval(const double* partials, int nparts, Scalars* sc, int slot,
                                cudaStream_t s);
@@ -232,7 +235,8 @@ template <typename T>
 cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
                                const uint8_t* act_po, const uint8_t* pt_act, const int* crank, const T* x,
                                const T* Vinv, const T* V, const T* gp, const T* Wst, double lambda, T* dp,
-                               T* wx, double* pred_parts, int grid, cudaStream_t s);
+                               T* wx, int Cf, const int* cam_map, const T* Ug, const T* dampc, double* pred_parts,
+                               Scalars* sc, int grid, cudaStream_t s);  // also sc->pred (points and cameras)
 template <typename T>
 cudaError_t launch_pcg(const PcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
 template <typename T>

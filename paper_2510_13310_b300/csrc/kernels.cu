@@ -120,6 +120,28 @@ cudaError_t launch_obs_layout(int N, const double* uv, const double* depth, cons
 // (Eq. BA objective with depth; Sec. 4.2 step 1 validity)
 // ---------------------------------------------------------------------------
 
+// sc->cost[slot] = 1/2 sum, rmse_sum, n_act from the blocks' partials, in the
+// last block of the evaluation kernel (the fixed order of k_reduce_eval)
+__device__ __forceinline__ void eval_finish(const double* __restrict__ partials, Scalars* sc, int slot) {
+  if (!last_block_done(&sc->done_eval)) return;
+  __shared__ double red[32];
+  double a = 0, b = 0, c = 0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    a += __ldcg(partials + 3 * i);
+    b += __ldcg(partials + 3 * i + 1);
+    c += __ldcg(partials + 3 * i + 2);
+  }
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  c = block_sum(c, red);
+  if (threadIdx.x == 0) {
+    sc->cost[slot] = 0.5 * a;
+    sc->rmse_sum[slot] = b;
+    sc->n_act[slot] = c;
+    sc->done_eval = 0u;
+  }
+}
+
 // bits: 1 = geometrically valid (z > min_depth, pixel inside the image),
 //       2 = valid and |r_uv| above the residual-drop threshold.
 // ref_bits (nullable): validity bits of another state; any difference in bit 1
@@ -127,7 +149,7 @@ cudaError_t launch_obs_layout(int N, const double* uv, const double* depth, cons
 __global__ void k_eval64(Layout L, ModelParams mp, const double* __restrict__ camw64,
                          const double* __restrict__ pts64, const uint8_t* __restrict__ act,
                          uint8_t* __restrict__ bits, const uint8_t* __restrict__ ref_bits,
-                         int* __restrict__ flips, double* __restrict__ partials) {
+                         int* __restrict__ flips, double* __restrict__ partials, Scalars* sc, int slot) {
   int flip = 0;
   __shared__ double red[32];
   double acc_cost = 0.0, acc_e2 = 0.0;
@@ -169,13 +191,15 @@ __global__ void k_eval64(Layout L, ModelParams mp, const double* __restrict__ ca
     partials[3 * blockIdx.x + 1] = s1;
     partials[3 * blockIdx.x + 2] = (double)s2;
   }
+  eval_finish(partials, sc, slot);
 }
 
 cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* camw64,
                           const double* pts64, const uint8_t* act, uint8_t* bits,
-                          const uint8_t* ref_bits, int* flips, double* partials, int grid, cudaStream_t s) {
+                          const uint8_t* ref_bits, int* flips, double* partials, Scalars* sc, int slot, int grid,
+                          cudaStream_t s) {
   k_eval64<<<grid, kBlock, 0, s>>>(L, mp, camw64, pts64, act, bits, bits ? ref_bits : nullptr, flips,
-                                    partials);
+                                    partials, sc, slot);
   return cudaGetLastError();
 }
 
@@ -224,7 +248,7 @@ __global__ void __launch_bounds__(kBlock) k_eval_df(Layout L, ModelParams mp, Ev
                                                     const double* __restrict__ pts64, const uint8_t* __restrict__ act,
                                                     uint8_t* __restrict__ bits, const uint8_t* __restrict__ ref_bits,
                                                     int* __restrict__ flips, double* __restrict__ partials,
-                                                    int cam_smem) {
+                                                    Scalars* sc, int slot, int cam_smem) {
   // the camera table in shared memory when it fits, 9 float4 per camera (the
   // odd stride spreads the lanes' random cameras over the bank groups)
   extern __shared__ __align__(16) float4 cam_s[];
@@ -339,6 +363,7 @@ __global__ void __launch_bounds__(kBlock) k_eval_df(Layout L, ModelParams mp, Ev
     for (int w = 0; w < kBlock / 32; ++w) t += ws[threadIdx.x][w];
     partials[3 * blockIdx.x + threadIdx.x] = t;
   }
+  eval_finish(partials, sc, slot);
 }
 
 static F2 host_f2(double x) {
@@ -348,7 +373,7 @@ static F2 host_f2(double x) {
 
 cudaError_t launch_eval_df(const Layout& L, const ModelParams& mp, const double* camw64, const double* pts64,
                            F2* camdf, float4* ptdf, const uint8_t* act, uint8_t* bits, const uint8_t* ref_bits,
-                           int* flips, double* partials, int grid, cudaStream_t s) {
+                           int* flips, double* partials, Scalars* sc, int slot, int grid, cudaStream_t s) {
   const int nconv = std::max(L.C * 16, L.P);
   if (nconv > 0)
     k_state_df<<<std::min((nconv + 255) / 256, 4096), 256, 0, s>>>(L.C, L.P, camw64, pts64, camdf, ptdf);
@@ -367,7 +392,8 @@ cudaError_t launch_eval_df(const Layout& L, const ModelParams& mp, const double*
   const size_t cam_bytes = (size_t)144 * L.C;
   const int cam_smem = cam_bytes <= 48 * 1024 ? 1 : 0;
   k_eval_df<<<grid, kBlock, cam_smem ? cam_bytes : 0, s>>>(L, mp, ec, camdf, ptdf, camw64, pts64, act, bits,
-                                                          bits ? ref_bits : nullptr, flips, partials, cam_smem);
+                                                          bits ? ref_bits : nullptr, flips, partials, sc, slot,
+                                                          cam_smem);
   return cudaGetLastError();
 }
 
@@ -1157,7 +1183,8 @@ cudaError_t launch_candidate(int C, int P, const int* crank, const T* x, const T
                              const double* cams_src, const double* pts_src, double* cams_dst,
                              double* pts_dst, double* camw64_dst, T* camw_dst, T* ptsw_dst,
                              cudaStream_t s) {
-  if (C > 0) k_candidate_cams<T><<<(C + 127) / 128, 128, 0, s>>>(C, crank, x, cams_src, cams_dst, camw64_dst, camw_dst);
+  // 32-thread blocks: the FP64 rotation work (sincos, atan2) of 32 cameras per SM
+  if (C > 0) k_candidate_cams<T><<<(C + 31) / 32, 32, 0, s>>>(C, crank, x, cams_src, cams_dst, camw64_dst, camw_dst);
   if (P > 0) k_candidate_pts<T><<<(P + 255) / 256, 256, 0, s>>>(P, dp, pts_src, pts_dst, ptsw_dst);
   return cudaGetLastError();
 }

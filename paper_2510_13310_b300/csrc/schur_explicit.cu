@@ -897,7 +897,9 @@ __global__ void k_backsub_obs(Layout L, ModelParams mp, const T* __restrict__ ca
 template <typename T>
 __global__ void k_backsub_pts(Layout L, const uint8_t* __restrict__ pt_act, const T* __restrict__ wx,
                               const T* __restrict__ Vinv, const T* __restrict__ V, const T* __restrict__ gp,
-                              double lambda, T* __restrict__ dp, double* __restrict__ pred_parts) {
+                              double lambda, T* __restrict__ dp, int Cf, const int* __restrict__ cam_map,
+                              const T* __restrict__ x, const T* __restrict__ Ug, const T* __restrict__ dampc,
+                              double* __restrict__ pred_parts, Scalars* sc) {
   __shared__ double red[32];
   double pred = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < L.P; p += gridDim.x * blockDim.x) {
@@ -928,20 +930,38 @@ __global__ void k_backsub_pts(Layout L, const uint8_t* __restrict__ pt_act, cons
                     fmin(fmax((double)vv[5], 1e-6), 1e32)};
     for (int i = 0; i < 3; ++i) pred += dd[i] * (lambda * dg[i] * dd[i] - (double)gp[3 * (size_t)p + i]);
   }
+  // the camera part dc^T (lambda D dc - g_c), spread over the same blocks
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 9 * Cf; e += gridDim.x * blockDim.x) {
+    const int f = e / 9, i = e - 9 * f;
+    const double d = (double)x[e];
+    pred += d * (lambda * (double)dampc[e] * d - (double)Ug[54 * (size_t)cam_map[f] + 45 + i]);
+  }
   double s = block_sum(pred, red);
   if (threadIdx.x == 0) pred_parts[blockIdx.x] = s;
+  // the last block adds the partials in block order: sc->pred = 1/2 sum
+  if (last_block_done(&sc->done_pred)) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) a += __ldcg(pred_parts + i);
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) {
+      sc->pred = 0.5 * a;
+      sc->done_pred = 0u;
+    }
+  }
 }
 
 template <typename T>
 cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
                                const uint8_t* act_po, const uint8_t* pt_act, const int* crank, const T* x,
                                const T* Vinv, const T* V, const T* gp, const T* Wst, double lambda, T* dp,
-                               T* wx, double* pred_parts, int grid, cudaStream_t s) {
+                               T* wx, int Cf, const int* cam_map, const T* Ug, const T* dampc, double* pred_parts,
+                               Scalars* sc, int grid, cudaStream_t s) {
   if (L.N > 0) {
     const int g = (int)std::min<long long>(((long long)L.N + 255) / 256, 65535);
     k_backsub_obs<T><<<g, 256, 0, s>>>(L, mp, camw, ptsw, act_po, crank, x, Wst, wx);
   }
-  k_backsub_pts<T><<<grid, 256, 0, s>>>(L, pt_act, wx, Vinv, V, gp, lambda, dp, pred_parts);
+  k_backsub_pts<T><<<grid, 256, 0, s>>>(L, pt_act, wx, Vinv, V, gp, lambda, dp, Cf, cam_map, x, Ug, dampc,
+                                        pred_parts, sc);
   return cudaGetLastError();
 }
 
@@ -956,7 +976,8 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
   template cudaError_t launch_backsub_pts<T>(const Layout&, const ModelParams&, const T*, const T*,    \
                                              const uint8_t*, const uint8_t*, const int*, const T*,     \
                                              const T*, const T*, const T*, const T*, double, T*, T*,   \
-                                             double*, int, cudaStream_t);
+                                             int, const int*, const T*, const T*, double*, Scalars*, int, \
+                                             cudaStream_t);
 BAB_SINST(float)
 BAB_SINST(double)
 
