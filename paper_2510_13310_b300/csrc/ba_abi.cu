@@ -345,7 +345,8 @@ ba_status schur_t(ba_problem* pb, double lambda) {
   LAUNCH(1, launch_cam_reduce<T>(pb->L, (const T*)pb->cam_part, (T*)pb->Sg, pb->stream));
   LAUNCH(1, launch_schur_diag<T>(pb->n_cam_free, pb->cam_map, (const T*)pb->Ug, (const T*)pb->Sg, lambda,
                                  (T*)pb->Ud, (T*)pb->Dinv, (T*)pb->bvec, (T*)pb->dampc,
-                                 pb->explicit_S ? (T*)pb->Dblk : nullptr, pb->err, pb->stream));
+                                 pb->explicit_S ? (T*)pb->Dblk : nullptr,
+                                 pb->explicit_S ? pb->dscale : nullptr, pb->err, pb->stream));
   return BA_OK;
 }
 
@@ -357,7 +358,7 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   CU(cudaMemsetAsync(&pb->sc->pcg_iters, 0, sizeof(int), pb->stream));
   CU(cudaMemsetAsync(&pb->sc->pcg_rel_res, 0, sizeof(double), pb->stream));
   if (Cf > 0) {
-    LAUNCH(5, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
+    LAUNCH(4, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
                                (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
                                Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->form_lanes, pb->num_sms, pb->evf[0],
                                pb->evf[1], pb->stream));

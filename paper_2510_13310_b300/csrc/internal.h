@@ -210,7 +210,8 @@ cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_ac
                             T* Vinv, T* z0, int* err, cudaStream_t s);
 template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
-                              T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, int* err, cudaStream_t s);
+                              T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, double* dscale, int* err,
+                              cudaStream_t s);  // dscale (nullable): D and 1/D of the explicit system
 template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,

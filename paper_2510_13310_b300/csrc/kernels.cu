@@ -991,9 +991,13 @@ template <typename T>
 __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* __restrict__ Ug,
                              const T* __restrict__ Sg, double lambda, T* __restrict__ Ud,
                              T* __restrict__ Dinv, T* __restrict__ b, T* __restrict__ dampc,
-                             T* __restrict__ Dblk, int* err) {
-  __shared__ double Ds[kDiagWarps][81];
-  __shared__ double Rs[kDiagWarps][9];  // reciprocal pivots 1 / L_jj
+                             T* __restrict__ Dblk, double* __restrict__ dscale, int* err) {
+  // D = U* - W V*^-1 W^T, its Cholesky factor and its inverse in FP64 (the two
+  // terms can nearly cancel; an FP32 factorisation measurably weakens the
+  // preconditioner of the undamped adjoint system)
+  using A = double;
+  __shared__ A Ds[kDiagWarps][81];
+  __shared__ A Rs[kDiagWarps][9];  // reciprocal pivots 1 / L_jj
   __shared__ int okS[kDiagWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int f = blockIdx.x * kDiagWarps + w;
@@ -1001,7 +1005,7 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
   const int c = cam_map[f];
   const T* u = Ug + 54 * (size_t)c;
   const T* sch = Sg + 54 * (size_t)c;
-  double* D = Ds[w];
+  A* D = Ds[w];
   for (int q = lane; q < 81; q += 32) {
     int i = q / 9, j = q - 9 * i;
     double uij = u[sym9(i, j)];
@@ -1011,10 +1015,17 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
       uij += lambda * dc;
     }
     double v = uij - (double)sch[sym9(i, j)];
-    D[q] = v;
+    D[q] = (A)v;
     if (j >= i) {
       Ud[45 * (size_t)f + sym9(i, j)] = (T)uij;
       if (Dblk) Dblk[45 * (size_t)f + sym9(i, j)] = (T)v;
+    }
+    if (dscale && i == j) {
+      // Jacobi scaling of the explicit system: D = sqrt(diag U*), then 1/D in T
+      const double d = (double)(T)uij;
+      const double sd = sqrt(d > 0.0 ? d : 1e-30);
+      dscale[9 * (size_t)f + i] = sd;
+      reinterpret_cast<T*>(dscale + 9 * (size_t)Cf)[9 * (size_t)f + i] = (T)(1.0 / sd);
     }
   }
   if (lane < 9) b[9 * (size_t)f + lane] = (T)(-(double)u[45 + lane] + (double)sch[45 + lane]);
@@ -1022,12 +1033,12 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
   // Cholesky D = L L^T in place (lower), right-looking across the warp: lane 0
   // takes pivot j (reciprocal square root), the lanes below scale column j, and
   // the lanes update the trailing lower triangle (one entry each)
-  double* Rp = Rs[w];
+  A* Rp = Rs[w];
   for (int j = 0; j < 9; ++j) {
     if (lane == 0) {
-      const double sj = D[9 * j + j];
-      const int good = sj > 0.0;  // false for NaN
-      const double r = good ? rsqrt(sj) : 0.0;
+      const A sj = D[9 * j + j];
+      const int good = sj > A(0);  // false for NaN
+      const A r = good ? rsqrt(sj) : A(0);
       D[9 * j + j] = sj * r;
       Rp[j] = r;
       okS[w] = good;
@@ -1059,17 +1070,17 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
   if (lane < 9) {
     // column `lane` of the inverse: solve L L^T x = e_lane
     const int j = lane;
-    double x[9];
+    A x[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      double s = i == j ? 1.0 : 0.0;
+      A s = i == j ? A(1) : A(0);
 #pragma unroll
       for (int l = 0; l < i; ++l) s -= D[9 * i + l] * x[l];
       x[i] = s * Rp[i];
     }
 #pragma unroll
     for (int i = 8; i >= 0; --i) {
-      double s = x[i];
+      A s = x[i];
 #pragma unroll
       for (int l = i + 1; l < 9; ++l) s -= D[9 * l + i] * x[l];
       x[i] = s * Rp[i];
@@ -1081,10 +1092,11 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
 
 template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
-                              T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, int* err, cudaStream_t s) {
+                              T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, double* dscale, int* err, cudaStream_t s) {
   if (Cf > 0)
     k_schur_diag<T><<<(Cf + kDiagWarps - 1) / kDiagWarps, 32 * kDiagWarps, 0, s>>>(Cf, cam_map, Ug, Sg, lambda, Ud,
-                                                                                    Dinv, b, dampc, Dblk, err);
+                                                                                    Dinv, b, dampc, Dblk, dscale,
+                                                                                    err);
   return cudaGetLastError();
 }
 
@@ -1271,7 +1283,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
   template cudaError_t launch_damp_pts<T>(int, const T*, const T*, const uint8_t*, double, T*, T*,  \
                                           int*, cudaStream_t);                                      \
   template cudaError_t launch_schur_diag<T>(int, const int*, const T*, const T*, double, T*, T*,    \
-                                            T*, T*, T*, int*, cudaStream_t);                        \
+                                            T*, T*, T*, double*, int*, cudaStream_t);               \
   template cudaError_t launch_pred_cams<T>(int, const int*, const T*, const T*, const T*, double,   \
                                            double*, int, cudaStream_t);                             \
   template cudaError_t launch_candidate<T>(int, int, const int*, const T*, const T*, const double*, \

@@ -290,19 +290,6 @@ __global__ void k_S_diag_upper(int Cf, const T* __restrict__ Dblk, const double*
   }
 }
 
-// D = sqrt(diag U*) in FP64, and 1/D in the working precision (dscale + n) so that
-// per-entry work needs no FP64 division.
-template <typename T>
-__global__ void k_dscale(int Cf, const T* __restrict__ Ud, double* __restrict__ dscale) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  int n = 9 * Cf;
-  if (e >= n) return;
-  int f = e / 9, i = e - 9 * f;
-  double d = (double)Ud[45 * (size_t)f + sym9(i, i)];
-  double sd = sqrt(d > 0.0 ? d : 1e-30);
-  dscale[e] = sd;
-  reinterpret_cast<T*>(dscale + n)[e] = (T)(1.0 / sd);
-}
 
 template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
@@ -311,7 +298,7 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
                           cudaStream_t s) {
   if (Cf <= 0) return cudaSuccess;
   const int n = 9 * Cf;
-  k_dscale<T><<<(n + 255) / 256, 256, 0, s>>>(Cf, Ud, dscale);
+  // dscale (D and 1/D) was written by the Schur-diagonal kernel
   if (L.N > 0) k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
   cudaError_t e = cudaMemsetAsync(Shat, 0, sizeof(T) * (size_t)n * spcg_row_stride<T>(n), s);
   if (e != cudaSuccess) return e;
