@@ -96,10 +96,12 @@ typedef struct {
   int pcg_iters;
   double pcg_rel_res;
   int64_t n_cam_act, n_pt_act, n_obs_act;
-  float ms[8];        /* device time per phase: [0] extract, [1] linearize, [2] Schur terms,
-                         [3] solve (d) in full, [4] the PCG kernel launch alone (inside [3]),
+  float ms[8];        /* device time per phase: [0] extract, [1] linearize, [2] Schur terms
+                         (for the explicit system the formation of S^ runs concurrently on the
+                         main stream and [2] ends with the Schur-diagonal chain on a side stream),
+                         [3] solve (d) from there, [4] the PCG kernel launch alone (inside [3]),
                          [5] candidate + evaluation, [6] total; [7] the co-visibility
-                         product kernel alone (explicit system, inside [3]) */
+                         product kernel alone (explicit system) */
 } ba_iter_info;
 
 typedef struct ba_problem ba_problem;

@@ -153,7 +153,13 @@ struct ba_problem {
   cudaEvent_t ev[8] = {};
   cudaEvent_t evk[2] = {};  // around the PCG kernel launch of the latest solve
   bool evk_valid = false;
-  cudaEvent_t evf[2] = {};  // around the co-visibility product kernel of the latest formation
+  cudaEvent_t evf[2] = {};
+  // explicit system: the Schur-diagonal chain (k_cam_accum<1>, k_cam_reduce,
+  // k_schur_diag) runs on a high-priority side stream while the main stream forms
+  // S^; `join` marks its end, waited on before anything that reads its outputs
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool join_pending = false;  // around the co-visibility product kernel of the latest formation
   bool evf_valid = false;
 };
 
@@ -337,16 +343,32 @@ ba_status linearize_t(ba_problem* pb) {
 template <typename T>
 ba_status schur_t(ba_problem* pb, double lambda) {
   int s = pb->cur;
+  if (pb->join_pending) {  // a previous chain whose solve did not run (error path)
+    CU(cudaStreamWaitEvent(pb->stream, pb->join, 0));
+    pb->join_pending = false;
+  }
   LAUNCH(1, launch_damp_pts<T>(pb->P, (const T*)pb->V, (const T*)pb->gp, pb->pt_act, lambda, (T*)pb->Vinv,
                                (T*)pb->z0, pb->err, pb->stream));
+  cudaStream_t cs = pb->stream;
+  if (pb->explicit_S && pb->side) {
+    CU(cudaEventRecord(pb->fork, pb->stream));
+    CU(cudaStreamWaitEvent(pb->side, pb->fork, 0));
+    cs = pb->side;
+    // the Jacobi scaling the formation needs now (it depends on U* only)
+    LAUNCH(1, launch_dscale<T>(pb->n_cam_free, pb->cam_map, (const T*)pb->Ug, lambda, pb->dscale, pb->stream));
+  }
   LAUNCH(1, launch_cam_accum<T>(pb->L, pb->mp, 1, (const T*)pb->camw[s], (const T*)pb->ptsw[s],
                                 pb->obs_act_co, pb->cam_act, pb->crank, (const T*)pb->Vinv,
-                                (const T*)pb->z0, (T*)pb->cam_part, pb->stream));
-  LAUNCH(1, launch_cam_reduce<T>(pb->L, (const T*)pb->cam_part, (T*)pb->Sg, pb->stream));
+                                (const T*)pb->z0, (T*)pb->cam_part, cs));
+  LAUNCH(1, launch_cam_reduce<T>(pb->L, (const T*)pb->cam_part, (T*)pb->Sg, cs));
   LAUNCH(1, launch_schur_diag<T>(pb->n_cam_free, pb->cam_map, (const T*)pb->Ug, (const T*)pb->Sg, lambda,
                                  (T*)pb->Ud, (T*)pb->Dinv, (T*)pb->bvec, (T*)pb->dampc,
                                  pb->explicit_S ? (T*)pb->Dblk : nullptr,
-                                 pb->explicit_S ? pb->dscale : nullptr, pb->err, pb->stream));
+                                 pb->explicit_S && !pb->side ? pb->dscale : nullptr, pb->err, cs));
+  if (cs != pb->stream) {
+    CU(cudaEventRecord(pb->join, cs));
+    pb->join_pending = true;
+  }
   return BA_OK;
 }
 
@@ -361,8 +383,9 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     LAUNCH(4, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
                                (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
                                Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->form_lanes, pb->num_sms, pb->evf[0],
-                               pb->evf[1], pb->stream));
+                               pb->evf[1], pb->join_pending ? pb->join : nullptr, pb->stream));
     pb->evf_valid = true;
+    pb->join_pending = false;  // launch_form_S made the main stream wait for the chain
     bool solved = false;
     if constexpr (sizeof(T) == 4) {
       if (pb->dense) {
@@ -426,6 +449,10 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     CU(cudaEventRecord(pb->evk[1], pb->stream));
     pb->evk_valid = true;
     }
+  }
+  if (pb->join_pending) {  // no formation ran (no free camera): still join the chain
+    CU(cudaStreamWaitEvent(pb->stream, pb->join, 0));
+    pb->join_pending = false;
   }
   LAUNCH(2, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                                   pb->pt_act, pb->crank, (const T*)pb->x, (const T*)pb->Vinv, (const T*)pb->V,
@@ -589,7 +616,9 @@ ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   CU(cudaMemsetAsync(pb->err, 0, sizeof(int), pb->stream));
   if (pb->fp64) ST(schur_t<double>(pb, lambda));
   else ST(schur_t<float>(pb, lambda));
-  CU(cudaEventRecord(pb->ev[3], pb->stream));
+  // end of the Schur terms: on the side stream when the chain runs there (the
+  // formation of S^ on the main stream overlaps it and is counted in the solve)
+  CU(cudaEventRecord(pb->ev[3], pb->join_pending ? pb->side : pb->stream));
   r_schur.end();
   NvtxScope r_solve("ba: solve");
   pb->evk_valid = false;
@@ -1071,6 +1100,13 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   CU(cudaMallocHost(&pb->h_sc, sizeof(Scalars)));
   memset(pb->h_sc, 0, sizeof(Scalars));
   for (auto& e : pb->ev) CU(cudaEventCreate(&e));
+  if (pb->explicit_S) {
+    int lo = 0, hi = 0;
+    CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CU(cudaStreamCreateWithPriority(&pb->side, cudaStreamNonBlocking, hi));
+    CU(cudaEventCreateWithFlags(&pb->fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&pb->join, cudaEventDisableTiming));
+  }
   for (auto& e : pb->evk) CU(cudaEventCreate(&e));
   for (auto& e : pb->evf) CU(cudaEventCreate(&e));
 
@@ -1090,6 +1126,12 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
 void free_problem(ba_problem* pb) {
   if (!pb) return;
   if (pb->stream) cudaStreamSynchronize(pb->stream);
+  if (pb->side) {
+    cudaStreamSynchronize(pb->side);
+    cudaStreamDestroy(pb->side);
+  }
+  if (pb->fork) cudaEventDestroy(pb->fork);
+  if (pb->join) cudaEventDestroy(pb->join);
   for (void* p : pb->allocs) cudaFree(p);
   if (pb->h_sc) cudaFreeHost(pb->h_sc);
   for (auto& e : pb->ev)

@@ -216,7 +216,10 @@ template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
                           int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaEvent_t ev0, cudaEvent_t ev1,
-                          cudaStream_t s);
+                          cudaEvent_t join, cudaStream_t s);  // join (nullable): waited on before the
+                                                              // diagonal blocks are written
+template <typename T>
+cudaError_t launch_dscale(int Cf, const int* cam_map, const T* Ug, double lambda, double* dscale, cudaStream_t s);
 template <typename T>
 size_t spcg_smem_bytes(int n, int rows, int rows_in_smem, int vecs_in_smem, int Cf);
 // row stride of S^: FP32 rows padded to a multiple of 4 entries (zeros)

@@ -291,11 +291,35 @@ __global__ void k_S_diag_upper(int Cf, const T* __restrict__ Dblk, const double*
 }
 
 
+// Jacobi scaling of the explicit system from the damped U blocks alone:
+// D = sqrt(diag U*) in FP64 and 1/D in the working precision (dscale + 9 Cf), with
+// U*_ii = U_ii + lambda clamp(U_ii) rounded to T exactly as the Schur-diagonal
+// kernel stores it
+template <typename T>
+__global__ void k_dscale(int Cf, const int* __restrict__ cam_map, const T* __restrict__ Ug, double lambda,
+                         double* __restrict__ dscale) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 9 * Cf) return;
+  const int f = e / 9, i = e - 9 * f;
+  double u = (double)Ug[54 * (size_t)cam_map[f] + sym9(i, i)];
+  u += lambda * fmin(fmax(u, 1e-6), 1e32);
+  const double d = (double)(T)u;
+  const double sd = sqrt(d > 0.0 ? d : 1e-30);
+  dscale[e] = sd;
+  reinterpret_cast<T*>(dscale + 9 * (size_t)Cf)[e] = (T)(1.0 / sd);
+}
+
+template <typename T>
+cudaError_t launch_dscale(int Cf, const int* cam_map, const T* Ug, double lambda, double* dscale, cudaStream_t s) {
+  if (Cf > 0) k_dscale<T><<<(9 * Cf + 255) / 256, 256, 0, s>>>(Cf, cam_map, Ug, lambda, dscale);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
                           int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaEvent_t ev0, cudaEvent_t ev1,
-                          cudaStream_t s) {
+                          cudaEvent_t join, cudaStream_t s) {
   if (Cf <= 0) return cudaSuccess;
   const int n = 9 * Cf;
   // dscale (D and 1/D) was written by the Schur-diagonal kernel
@@ -318,6 +342,8 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
     }
   }
   if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
+  // the diagonal blocks come from the Schur-diagonal kernel (on another stream when `join`)
+  if (join && (e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
   int nt = (n + 31) / 32;
   k_S_finalize<T><<<dim3(nt, nt), dim3(32, 8), 0, s>>>(Cf, Dblk, dscale, Shat);
   k_S_diag_upper<T><<<Cf, 128, 0, s>>>(Cf, Dblk, dscale, Shat);
@@ -955,7 +981,8 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
 #define BAB_SINST(T)                                                                                   \
   template cudaError_t launch_form_S<T>(const Layout&, int, const int4*, const int2*, const T*,        \
                                         const T*, const int*, const T*, const T*, double*, int, T*, T*, \
-                                        bool, int, cudaEvent_t, cudaEvent_t, cudaStream_t);            \
+                                        bool, int, cudaEvent_t, cudaEvent_t, cudaEvent_t, cudaStream_t); \
+  template cudaError_t launch_dscale<T>(int, const int*, const T*, double, double*, cudaStream_t);       \
   template size_t spcg_smem_bytes<T>(int, int, int, int, int);                                         \
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \
   template const void* spcg_kernel_ptr<T>(bool);                                                         \
