@@ -154,9 +154,11 @@ struct ba_problem {
   cudaEvent_t evk[2] = {};  // around the PCG kernel launch of the latest solve
   bool evk_valid = false;
   cudaEvent_t evf[2] = {};
-  // explicit system: the Schur-diagonal chain (k_cam_accum<1>, k_cam_reduce,
-  // k_schur_diag) runs on a high-priority side stream while the main stream forms
-  // S^; `join` marks its end, waited on before anything that reads its outputs
+  // high-priority side stream for work that overlaps the main stream: the camera
+  // side of the linearisation (k_cam_accum<0>, k_cam_reduce) next to k_pt_lin,
+  // and for the explicit system the Schur-diagonal chain (k_cam_accum<1>,
+  // k_cam_reduce, k_schur_diag) next to the formation of S^; `join` marks the
+  // chain's end, waited on before anything that reads its outputs
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   bool join_pending = false;  // around the co-visibility product kernel of the latest formation
@@ -328,14 +330,29 @@ ba_status run_extraction(ba_problem* pb, bool drop, int* rounds_out) {
 template <typename T>
 ba_status linearize_t(ba_problem* pb) {
   int s = pb->cur;
+  if (pb->join_pending) {
+    CU(cudaStreamWaitEvent(pb->stream, pb->join, 0));
+    pb->join_pending = false;
+  }
+  if (pb->side) CU(cudaEventRecord(pb->fork, pb->stream));
   // W rows are stored when the matvec streams them or the explicit system is formed
   LAUNCH(1, launch_pt_lin<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                              (pb->recompute && !pb->explicit_S) ? nullptr : (T*)pb->W,
                              pb->recompute ? (T*)pb->wsgn : nullptr, (T*)pb->V, (T*)pb->gp, pb->stream));
+  // the camera side reads neither W nor V: it runs on the side stream alongside
+  cudaStream_t cs = pb->stream;
+  if (pb->side) {
+    CU(cudaStreamWaitEvent(pb->side, pb->fork, 0));
+    cs = pb->side;
+  }
   LAUNCH(1, launch_cam_accum<T>(pb->L, pb->mp, 0, (const T*)pb->camw[s], (const T*)pb->ptsw[s],
                                 pb->obs_act_co, pb->cam_act, pb->crank, nullptr, nullptr,
-                                (T*)pb->cam_part, pb->stream));
-  LAUNCH(1, launch_cam_reduce<T>(pb->L, (const T*)pb->cam_part, (T*)pb->Ug, pb->stream));
+                                (T*)pb->cam_part, cs));
+  LAUNCH(1, launch_cam_reduce<T>(pb->L, (const T*)pb->cam_part, (T*)pb->Ug, cs));
+  if (cs != pb->stream) {
+    CU(cudaEventRecord(pb->join, cs));
+    CU(cudaStreamWaitEvent(pb->stream, pb->join, 0));
+  }
   pb->linearized = true;
   return BA_OK;
 }
@@ -351,7 +368,7 @@ ba_status schur_t(ba_problem* pb, double lambda) {
                                (T*)pb->z0, pb->err, pb->stream));
   cudaStream_t cs = pb->stream;
   if (pb->explicit_S && pb->side) {
-    CU(cudaEventRecord(pb->fork, pb->stream));
+    CU(cudaEventRecord(pb->fork, pb->stream));  // after the point damping
     CU(cudaStreamWaitEvent(pb->side, pb->fork, 0));
     cs = pb->side;
     // the Jacobi scaling the formation needs now (it depends on U* only)
@@ -1100,7 +1117,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   CU(cudaMallocHost(&pb->h_sc, sizeof(Scalars)));
   memset(pb->h_sc, 0, sizeof(Scalars));
   for (auto& e : pb->ev) CU(cudaEventCreate(&e));
-  if (pb->explicit_S) {
+  {
     int lo = 0, hi = 0;
     CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     CU(cudaStreamCreateWithPriority(&pb->side, cudaStreamNonBlocking, hi));
