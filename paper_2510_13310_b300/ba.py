@@ -27,7 +27,7 @@ EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
            "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
            "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout", "ba_selftest_layout",
-           "ba_kernel_launches", "ba_solver_kind", "ba_explicit_layout", "ba_destroy",
+           "ba_kernel_launches", "ba_solver_kind", "ba_explicit_layout", "ba_destroy", "ba_release_cache",
            "ba_status_string", "ba_last_error")
 
 
@@ -103,6 +103,8 @@ def lib():
                                     ct.c_int64, ct.c_float, vp, ct.c_int64]
         L.ba_dense_cholesky.argtypes = [vp, ct.c_int64, vp, ct.c_int64, vp, ct.c_int64, ct.POINTER(ct.c_int)]
         L.ba_destroy.argtypes = [vp]
+        L.ba_release_cache.argtypes = []
+        L.ba_release_cache.restype = None
         L.ba_status_string.argtypes = [ct.c_int]
         L.ba_status_string.restype = ct.c_char_p
         L.ba_last_error.restype = ct.c_char_p
@@ -174,6 +176,11 @@ class _Arr:
     @property
     def p(self):
         return ct.c_void_p(self.ptr)
+
+
+def release_cache():
+    """ba_release_cache: return the device buffers of destroyed problems to the driver."""
+    lib().ba_release_cache()
 
 
 def selftest_layout(cams, pts, obs_cam, obs_pt, obs_uv, with_covis=True):

@@ -12,7 +12,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -167,11 +169,75 @@ struct ba_problem {
 
 namespace {
 
+// Device memory cache of the process: ba_destroy returns a problem's buffers
+// here instead of to the driver, and ba_create takes buffers of the same
+// (rounded) size back, so a process that creates problems repeatedly (serving,
+// batches of scenes) maps no new device memory after the first.  Keyed by
+// (device, size); ba_release_cache() frees everything.  BA_NO_ALLOC_CACHE=1
+// disables it.
+struct AllocCache {
+  std::mutex mu;
+  std::multimap<std::pair<int, size_t>, void*> free_blocks;
+  std::map<void*, std::pair<int, size_t>> sizes;  // every block handed out, with its key
+};
+AllocCache& alloc_cache() {
+  static AllocCache* c = new AllocCache();  // never destroyed: safe at process exit
+  return *c;
+}
+bool alloc_cache_on() {
+  static const bool on = [] {
+    const char* v = std::getenv("BA_NO_ALLOC_CACHE");
+    return !(v && v[0] && v[0] != '0');
+  }();
+  return on;
+}
+size_t cache_round(size_t bytes) { return (std::max<size_t>(bytes, 16) + 511) / 512 * 512; }
+
+// device memory for the current device: from the cache when a block of the
+// rounded size is free, else cudaMalloc
+cudaError_t cached_malloc(void** q, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const size_t rb = cache_round(bytes);
+  if (alloc_cache_on()) {
+    AllocCache& c = alloc_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.free_blocks.find({dev, rb});
+    if (it != c.free_blocks.end()) {
+      *q = it->second;
+      c.free_blocks.erase(it);
+      return cudaSuccess;
+    }
+  }
+  e = cudaMalloc(q, rb);
+  if (e == cudaSuccess && alloc_cache_on()) {
+    AllocCache& c = alloc_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.sizes[*q] = {dev, rb};
+  }
+  return e;
+}
+// back to the cache (the caller has synchronised every stream that used it)
+void cached_free(void* q) {
+  if (!q) return;
+  if (alloc_cache_on()) {
+    AllocCache& c = alloc_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.sizes.find(q);
+    if (it != c.sizes.end()) {
+      c.free_blocks.insert({it->second, q});
+      return;
+    }
+  }
+  cudaFree(q);
+}
+
 template <typename X>
 ba_status dalloc(ba_problem* pb, X** p, size_t count) {
   void* q = nullptr;
   size_t bytes = std::max<size_t>(sizeof(X) * count, 16);
-  cudaError_t e = cudaMalloc(&q, bytes);
+  cudaError_t e = cached_malloc(&q, bytes);
   if (e != cudaSuccess) {
     set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     return BA_ERR_OOM;
@@ -207,7 +273,7 @@ struct DevScratch {
   ~DevScratch() {
     if (p) {
       cudaDeviceSynchronize();
-      cudaFree(p);
+      cached_free(p);
     }
   }
 };
@@ -762,7 +828,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     for (const Up& u : ups)
       if (!u.dev && u.bytes) total += (u.bytes + 255) / 256 * 256;
     if (total) {
-      CU(cudaMalloc(&scratch.p, total));
+      CU(cached_malloc(&scratch.p, total));
       char* at = static_cast<char*>(scratch.p);
       for (const Up& u : ups)
         if (!u.dev && u.bytes) {
@@ -1149,7 +1215,7 @@ void free_problem(ba_problem* pb) {
   }
   if (pb->fork) cudaEventDestroy(pb->fork);
   if (pb->join) cudaEventDestroy(pb->join);
-  for (void* p : pb->allocs) cudaFree(p);
+  for (void* p : pb->allocs) cached_free(p);
   if (pb->h_sc) cudaFreeHost(pb->h_sc);
   for (auto& e : pb->ev)
     if (e) cudaEventDestroy(e);
@@ -1685,6 +1751,20 @@ void ba_explicit_layout(const ba_problem* pb, int* rows_in_smem, int* vecs_in_sm
 }
 
 void ba_destroy(ba_problem* pb) { free_problem(pb); }
+
+void ba_release_cache(void) {
+  AllocCache& c = alloc_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : c.free_blocks) {
+    cudaSetDevice(kv.first.first);
+    cudaFree(kv.second);
+    c.sizes.erase(kv.second);
+  }
+  c.free_blocks.clear();
+  cudaSetDevice(cur);
+}
 
 const char* ba_status_string(ba_status s) {
   switch (s) {

@@ -166,6 +166,30 @@ def test_damped_step_matches_oracle(precision, tol, solver):
     assert not g["dc"][sc.fixed_cams].any()
 
 
+@pytest.mark.parametrize("solver", [ba.BA_SOLVER_EXPLICIT, ba.BA_SOLVER_IMPLICIT])
+def test_reused_device_buffers_give_identical_runs(solver):
+    """ba_destroy hands a problem's buffers to the process cache and the next
+    ba_create takes them back with the previous problem's contents: the runs must
+    not depend on that (no buffer is read before it is written)."""
+    sc = geometric(12, 3000, 2, 12, 5.0, seed=41)
+    def run():
+        p = ba.Problem.from_scene(sc, ba.Options(solver=solver))
+        log = [p.lm_step()["cost"] for _ in range(6)]
+        cams, pts = p.get_params()
+        p.close()
+        return log, cams, pts
+    first = run()
+    other = ba.Problem.from_scene(geometric(12, 3000, 2, 12, 5.0, seed=7), ba.Options(solver=solver))
+    other.lm_step()
+    other.close()  # its buffers, now dirty, go back to the cache
+    second = run()
+    ba.release_cache()
+    third = run()
+    for r in (second, third):
+        assert r[0] == first[0]
+        assert np.array_equal(r[1], first[1]) and np.array_equal(r[2], first[2])
+
+
 def test_auto_solver_choice_follows_the_cost_model():
     """AUTO: the explicit system whenever 9 C <= 4608; above that, the per-step cost
     model (formation + streamed S^ against the implicit matvec).  A scene of 700
