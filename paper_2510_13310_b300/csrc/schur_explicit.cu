@@ -687,14 +687,16 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
           const float4* row = reinterpret_cast<const float4*>(Sg + (size_t)r * ns);
           float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
           int c = lane;
-          for (; c + 96 < rs; c += 128) {
-            const float4 s0 = __ldg(row + c), s1 = __ldg(row + c + 32), s2 = __ldg(row + c + 64),
-                         s3 = __ldg(row + c + 96);
-            const float4 q0 = p4[c], q1 = p4[c + 32], q2 = p4[c + 64], q3 = p4[c + 96];
-            c0 = fmaf(s0.x, q0.x, fmaf(s0.y, q0.y, fmaf(s0.z, q0.z, fmaf(s0.w, q0.w, c0))));
-            c1 = fmaf(s1.x, q1.x, fmaf(s1.y, q1.y, fmaf(s1.z, q1.z, fmaf(s1.w, q1.w, c1))));
-            c2 = fmaf(s2.x, q2.x, fmaf(s2.y, q2.y, fmaf(s2.z, q2.z, fmaf(s2.w, q2.w, c2))));
-            c3 = fmaf(s3.x, q3.x, fmaf(s3.y, q3.y, fmaf(s3.z, q3.z, fmaf(s3.w, q3.w, c3))));
+          for (; c + 224 < rs; c += 256) {
+            float4 sv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sv[u] = __ldcs(row + c + 32 * u);  // streamed once per iteration
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const float4 q0 = p4[c + 32 * u];
+              float& cu = (u & 3) == 0 ? c0 : (u & 3) == 1 ? c1 : (u & 3) == 2 ? c2 : c3;
+              cu = fmaf(sv[u].x, q0.x, fmaf(sv[u].y, q0.y, fmaf(sv[u].z, q0.z, fmaf(sv[u].w, q0.w, cu))));
+            }
           }
           for (; c < rs; c += 32) {
             const float4 s0 = __ldg(row + c), q0 = p4[c];
