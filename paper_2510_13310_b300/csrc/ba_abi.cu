@@ -163,7 +163,12 @@ struct ba_problem {
   // chain's end, waited on before anything that reads its outputs
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
-  bool join_pending = false;  // around the co-visibility product kernel of the latest formation
+  bool join_pending = false;
+  // LM step: the camera candidate (FP64 rotation updates, latency-bound) runs on
+  // the side stream as soon as dc is known, alongside the point back-substitution
+  bool cand_early_ok = false;   // set by the LM step around its solve
+  bool cand_cams_done = false;  // launched early for this step; `cand_join` marks its end
+  cudaEvent_t cand_fork = nullptr, cand_join = nullptr;  // around the co-visibility product kernel of the latest formation
   bool evf_valid = false;
 };
 
@@ -537,6 +542,17 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     CU(cudaStreamWaitEvent(pb->stream, pb->join, 0));
     pb->join_pending = false;
   }
+  if (pb->cand_early_ok && pb->side) {
+    // dc is final: the camera candidate on the side stream, next to the back-substitution
+    int sl = pb->cur, d = 1 - pb->cur;
+    CU(cudaEventRecord(pb->cand_fork, pb->stream));
+    CU(cudaStreamWaitEvent(pb->side, pb->cand_fork, 0));
+    LAUNCH(1, launch_candidate<T>(pb->C, 0, pb->crank, (const T*)pb->x, (const T*)pb->dp, pb->cams64[sl],
+                                  pb->pts64[sl], pb->cams64[d], pb->pts64[d], pb->camw64[d],
+                                  pb->fp64 ? nullptr : (T*)pb->camw[d], (T*)pb->ptsw[d], pb->side));
+    CU(cudaEventRecord(pb->cand_join, pb->side));
+    pb->cand_cams_done = true;
+  }
   LAUNCH(2, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                                   pb->pt_act, pb->crank, (const T*)pb->x, (const T*)pb->Vinv, (const T*)pb->V,
                                   (const T*)pb->gp, (const T*)pb->W, lambda, (T*)pb->dp, (T*)pb->bs_wx, Cf,
@@ -605,9 +621,13 @@ ba_status pcg_t(ba_problem* pb, double lambda) {
 template <typename T>
 ba_status candidate_t(ba_problem* pb) {
   int s = pb->cur, d = 1 - pb->cur;
-  LAUNCH(2, launch_candidate<T>(pb->C, pb->P, pb->crank, (const T*)pb->x, (const T*)pb->dp, pb->cams64[s],
-                                pb->pts64[s], pb->cams64[d], pb->pts64[d], pb->camw64[d],
-                                pb->fp64 ? nullptr : (T*)pb->camw[d], (T*)pb->ptsw[d], pb->stream));
+  const bool early = pb->cand_cams_done;
+  LAUNCH(early ? 1 : 2, launch_candidate<T>(early ? 0 : pb->C, pb->P, pb->crank, (const T*)pb->x, (const T*)pb->dp,
+                                            pb->cams64[s], pb->pts64[s], pb->cams64[d], pb->pts64[d],
+                                            pb->camw64[d], pb->fp64 ? nullptr : (T*)pb->camw[d],
+                                            (T*)pb->ptsw[d], pb->stream));
+  if (early) CU(cudaStreamWaitEvent(pb->stream, pb->cand_join, 0));
+  pb->cand_cams_done = false;
   pb->bits_valid[d] = false;
   pb->cost_valid[d] = false;
   return BA_OK;
@@ -706,8 +726,14 @@ ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   NvtxScope r_solve("ba: solve");
   pb->evk_valid = false;
   pb->evf_valid = false;
-  if (pb->fp64) ST(pcg_t<double>(pb, lambda));
-  else ST(pcg_t<float>(pb, lambda));
+  pb->cand_early_ok = true;
+  ba_status solve_st = pb->fp64 ? pcg_t<double>(pb, lambda) : pcg_t<float>(pb, lambda);
+  pb->cand_early_ok = false;
+  if (solve_st != BA_OK && pb->cand_cams_done) {  // the step stops here: settle the early kernel
+    CU(cudaStreamWaitEvent(pb->stream, pb->cand_join, 0));
+    pb->cand_cams_done = false;
+  }
+  ST(solve_st);
   CU(cudaEventRecord(pb->ev[4], pb->stream));
   CU(cudaEventRecord(pb->ev[5], pb->stream));
   r_solve.end();
@@ -1189,6 +1215,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     CU(cudaStreamCreateWithPriority(&pb->side, cudaStreamNonBlocking, hi));
     CU(cudaEventCreateWithFlags(&pb->fork, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&pb->join, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&pb->cand_fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&pb->cand_join, cudaEventDisableTiming));
   }
   for (auto& e : pb->evk) CU(cudaEventCreate(&e));
   for (auto& e : pb->evf) CU(cudaEventCreate(&e));
@@ -1215,6 +1243,8 @@ void free_problem(ba_problem* pb) {
   }
   if (pb->fork) cudaEventDestroy(pb->fork);
   if (pb->join) cudaEventDestroy(pb->join);
+  if (pb->cand_fork) cudaEventDestroy(pb->cand_fork);
+  if (pb->cand_join) cudaEventDestroy(pb->cand_join);
   for (void* p : pb->allocs) cached_free(p);
   if (pb->h_sc) cudaFreeHost(pb->h_sc);
   for (auto& e : pb->ev)
