@@ -175,8 +175,6 @@ cudaError_t launch_eval_df(const Layout& L, const ModelParams& mp, const double*
                            F2* camdf, float4* ptdf, const uint8_t* act, uint8_t* bits, const uint8_t* ref_bits,
                            int* flips, double* partials, Scalars* sc, int slot, int grid, cudaStream_t s);
 cudaError_t launch_obs_df(int N, const double* uv64, const double* tau64, float4* uvdf, F2* taudf, cudaStream_t s);
-cudaError_t launch_reduce_eval(const double* partials, int nparts, Scalars* sc, int slot,
-                               cudaStream_t s);
 
 cudaError_t launch_extract_begin(const Layout& L, uint8_t* alive, const uint8_t* bits,
                                  uint8_t* valid, int drop, cudaStream_t s);

@@ -121,7 +121,8 @@ cudaError_t launch_obs_layout(int N, const double* uv, const double* depth, cons
 // ---------------------------------------------------------------------------
 
 // sc->cost[slot] = 1/2 sum, rmse_sum, n_act from the blocks' partials, in the
-// last block of the evaluation kernel (the fixed order of k_reduce_eval)
+// last block of the evaluation kernel: each sum over the block partials in a
+// fixed thread assignment and tree
 __device__ __forceinline__ void eval_finish(const double* __restrict__ partials, Scalars* sc, int slot) {
   if (!last_block_done(&sc->done_eval)) return;
   __shared__ double red[32];
@@ -403,30 +404,6 @@ cudaError_t launch_obs_df(int N, const double* uv64, const double* tau64, float4
   return cudaGetLastError();
 }
 
-__global__ void k_reduce_eval(const double* __restrict__ partials, int n, Scalars* sc, int slot) {
-  __shared__ double red[32];
-  double a = 0, b = 0, c = 0;
-  // fixed assignment of partials to threads and a fixed tree: deterministic
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    a += partials[3 * i];
-    b += partials[3 * i + 1];
-    c += partials[3 * i + 2];
-  }
-  a = block_sum(a, red);
-  b = block_sum(b, red);
-  c = block_sum(c, red);
-  if (threadIdx.x == 0) {
-    sc->cost[slot] = 0.5 * a;
-    sc->rmse_sum[slot] = b;
-    sc->n_act[slot] = c;
-  }
-}
-
-cudaError_t launch_reduce_eval(const double* partials, int nparts, Scalars* sc, int slot,
-                               cudaStream_t s) {
-  k_reduce_eval<<<1, 256, 0, s>>>(partials, nparts, sc, slot);
-  return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // dynamic parameter extraction (Sec. 4.2 steps 1-2)
