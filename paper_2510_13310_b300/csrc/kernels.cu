@@ -719,12 +719,23 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
     T w = o.wrob;
     if (wsgn) wsgn[(size_t)d.g_row + i] = tau > T(0) ? w : -w;
     if (W) {
+      // the row in registers, then stored as 16-byte words (the 28-word row
+      // stride puts the 8 lanes of a quarter-warp on distinct bank groups)
+      using V4 = typename Vec4<T>::type;
+      T wr[kWStride];
 #pragma unroll
       for (int a = 0; a < 9; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-          wrow[3 * a + b] = w * (o.Jc[0][a] * o.Jp[0][b] + o.Jc[1][a] * o.Jp[1][b] + o.Jc[2][a] * o.Jp[2][b]);
-      wrow[27] = T(0);
+          wr[3 * a + b] = w * (o.Jc[0][a] * o.Jp[0][b] + o.Jc[1][a] * o.Jp[1][b] + o.Jc[2][a] * o.Jp[2][b]);
+      wr[27] = T(0);
+      V4* w4 = reinterpret_cast<V4*>(wrow);
+#pragma unroll
+      for (int q = 0; q < kWStride / 4; ++q) {
+        V4 v;
+        v.x = wr[4 * q], v.y = wr[4 * q + 1], v.z = wr[4 * q + 2], v.w = wr[4 * q + 3];
+        w4[q] = v;
+      }
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -736,8 +747,11 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
   }
   __syncthreads();
   if (W) {
-    T* Wdst = W + kWStride * (size_t)d.w_row;
-    for (int j = threadIdx.x; j < kWStride * n; j += blockDim.x) Wdst[j] = Ws[j];
+    // 16-byte coalesced copy of the tile's rows (rows are 16-byte aligned)
+    using V4 = typename Vec4<T>::type;
+    V4* Wdst = reinterpret_cast<V4*>(W + kWStride * (size_t)d.w_row);
+    const V4* Wsrc = reinterpret_cast<const V4*>(Ws);
+    for (int j = threadIdx.x; j < (kWStride / 4) * n; j += blockDim.x) Wdst[j] = Wsrc[j];
   }
   for (int p = pb + threadIdx.x; p < pe; p += blockDim.x) {
     T acc[9];
