@@ -531,95 +531,143 @@ __device__ __forceinline__ void set_flag(unsigned* flag, unsigned epoch) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(epoch) : "memory");
 }
 
-// acc[128] (+)= sign * M v for a 128 x 128 row-major tile M (ld), v in shared memory.
-// transpose: acc[c] += sign * sum_r M[r][c] v[r].
-template <bool TRANSPOSE>
-__device__ __forceinline__ void tile_gemv(const float* __restrict__ M, long long ld, const float* v, float* acc,
-                                          float sign, float* red) {
-  const int tid = threadIdx.x;
-  if (!TRANSPOSE) {
-    // row r = tid / 2, half h: columns [64h, 64h + 64)
-    const int r = tid >> 1, h = tid & 1;
-    const float4* m4 = reinterpret_cast<const float4*>(M + (size_t)r * ld + 64 * h);
-    const float4* v4 = reinterpret_cast<const float4*>(v + 64 * h);
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int q = 0; q < 16; q += 2) {
-      const float4 a = m4[q], b = v4[q], c = m4[q + 1], d = v4[q + 1];
-      s0 += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
-      s1 += c.x * d.x + c.y * d.y + c.z * d.z + c.w * d.w;
-    }
-    float t = s0 + s1;
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
-    if (h == 0) acc[r] += sign * t;
-  } else {
-    // columns [4 cg, 4 cg + 4), rows [16 rg, 16 rg + 16): 16 float4 loads in flight per
-    // thread; the 8 row groups are summed through shared memory (red: 8 x 128)
-    const int cg = tid & 31, rg = tid >> 5;
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float* base = M + (size_t)(16 * rg) * ld + 4 * cg;
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const float4 m = *reinterpret_cast<const float4*>(base + (size_t)r * ld);
-      const float vr = v[16 * rg + r];
-      s.x += m.x * vr;
-      s.y += m.y * vr;
-      s.z += m.z * vr;
-      s.w += m.w * vr;
-    }
-    float* rw = red + rg * 128 + 4 * cg;
-    rw[0] = s.x;
-    rw[1] = s.y;
-    rw[2] = s.z;
-    rw[3] = s.w;
-    __syncthreads();
-    if (tid < 128) {
-      float t = 0.f;
-#pragma unroll
-      for (int g = 0; g < 8; ++g) t += red[g * 128 + tid];
-      acc[tid] += sign * t;
-    }
-  }
-  __syncthreads();
-}
-
 // Forward (!BACK): L y = r.  Backward (BACK): L^T x = y.  rhs, out: np vectors
 // (np = 128 T, 16-byte aligned); L: np x np row-major lower factor (ld); Linv:
 // the T diagonal-tile inverses; flags: T words, epoch unique per call.
+//
+// Block b takes the tile rows b, b + G, ... in solve order.  Within a tile row,
+// warp w owns tile rows [16 w, 16 w + 16) and lane l the float4 column chunk l,
+// so every load instruction reads whole 512-byte rows.  Forward: each lane keeps
+// 16 row partials over its 4 columns; backward (transposed tiles): 4 column
+// partials over the warp's 16 rows.  The dependency tiles stream through
+// registers one tile ahead of the arithmetic, each warp polls the dependencies'
+// flags itself (no block barrier per dependency), and the diagonal inverse is
+// copied into shared memory at the start of the row.  Partials are reduced
+// across lanes (forward) or warps (backward) once per tile row.
 template <bool BACK>
 __global__ void __launch_bounds__(kTrThreads) k_trsv_tiles(const float* __restrict__ L, long long ld,
                                                            const float* __restrict__ Linv, const float* rhs,
                                                            float* out, int T, unsigned* flags, unsigned epoch,
                                                            long long timeout_ns, int* err) {
-  __shared__ __align__(16) float acc[kPt];
-  __shared__ __align__(16) float vb[kPt];
-  __shared__ float red[8 * kPt];
-  __shared__ int bad;
-  const int tid = threadIdx.x;
+  extern __shared__ __align__(16) float trsv_dyn[];
+  float* inv = trsv_dyn;                          // [kPt * kPt] the diagonal tile's inverse (dynamic)
+  __shared__ __align__(16) float sv[kPt];         // r_i - sum_j (...) for the tile row
+  __shared__ float red[8][kPt];                   // backward: per-warp column partials
+  __shared__ volatile int bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) bad = 0;
   __syncthreads();
-  for (int k = blockIdx.x; k < T; k += gridDim.x) {
+  for (int k = blockIdx.x; k < T && !bad; k += gridDim.x) {
     const int i = BACK ? T - 1 - k : k;
-    if (tid < kPt) acc[tid] = rhs[(size_t)i * kPt + tid];
-    __syncthreads();
-    const int jn = BACK ? T - 1 - i : i;  // number of dependencies
-    for (int d = 0; d < jn; ++d) {
-      const int j = BACK ? T - 1 - d : d;
-      if (tid == 0 && !bad && !wait_flag(&flags[j], epoch, timeout_ns)) bad = 1;
-      __syncthreads();
-      if (bad) break;
-      if (tid < kPt) vb[tid] = out[(size_t)j * kPt + tid];
-      __syncthreads();
-      if (!BACK) tile_gemv<false>(L + (size_t)i * kPt * ld + (size_t)j * kPt, ld, vb, acc, -1.f, red);
-      else tile_gemv<true>(L + (size_t)j * kPt * ld + (size_t)i * kPt, ld, vb, acc, -1.f, red);
+    // the diagonal inverse, asynchronously into shared memory (16 x 16 bytes per thread)
+    {
+      const float* src = Linv + (size_t)i * kPt * kPt;
+#pragma unroll
+      for (int u = 0; u < (kPt * kPt) / (4 * kTrThreads); ++u) {
+        const int e = 4 * (tid + u * kTrThreads);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(inv + e);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + e) : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    if (bad) break;
-    if (tid < kPt) vb[tid] = acc[tid];
-    if (tid < kPt) acc[tid] = 0.f;
+    const int jn = BACK ? T - 1 - i : i;  // number of dependencies
+    // tile of dependency d: forward L_ij (j = d), backward L_ji (j = T - 1 - d), both
+    // read as 16 rows x one float4 column chunk per lane
+    auto tile_ptr = [&](int d) -> const float* {
+      const int j = BACK ? T - 1 - d : d;
+      return BACK ? L + (size_t)j * kPt * ld + (size_t)i * kPt : L + (size_t)i * kPt * ld + (size_t)j * kPt;
+    };
+    float acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+    float4 cur[16];
+    if (jn > 0) {
+      const float* t = tile_ptr(0) + (size_t)(16 * warp) * ld + 4 * lane;
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) cur[rr] = __ldcs(reinterpret_cast<const float4*>(t + (size_t)rr * ld));
+    }
+    for (int d = 0; d < jn; ++d) {
+      float4 nxt[16];
+      if (d + 1 < jn) {
+        const float* t = tile_ptr(d + 1) + (size_t)(16 * warp) * ld + 4 * lane;
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) nxt[rr] = __ldcs(reinterpret_cast<const float4*>(t + (size_t)rr * ld));
+      }
+      const int j = BACK ? T - 1 - d : d;
+      // every lane waits for the dependency itself (acquire), bounded
+      if (!wait_flag(&flags[j], epoch, timeout_ns)) bad = 1;
+      if (bad) break;
+      const float* y = out + (size_t)j * kPt;
+      if (!BACK) {
+        const float4 v = *reinterpret_cast<const float4*>(y + 4 * lane);
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr)
+          acc[rr] = fmaf(cur[rr].x, v.x, fmaf(cur[rr].y, v.y, fmaf(cur[rr].z, v.z, fmaf(cur[rr].w, v.w, acc[rr]))));
+      } else {
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+          const float vr = y[16 * warp + rr];
+          acc[0] = fmaf(cur[rr].x, vr, acc[0]);
+          acc[1] = fmaf(cur[rr].y, vr, acc[1]);
+          acc[2] = fmaf(cur[rr].z, vr, acc[2]);
+          acc[3] = fmaf(cur[rr].w, vr, acc[3]);
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) cur[rr] = nxt[rr];
+    }
+    // s = r_i - the sum, for the tile row
+    if (!BACK) {
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) {
+        const float t = warp_sum(acc[rr]);
+        if (lane == 0) sv[16 * warp + rr] = rhs[(size_t)i * kPt + 16 * warp + rr] - t;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) red[warp][4 * lane + c] = acc[c];
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    if (!BACK) tile_gemv<false>(Linv + (size_t)i * kPt * kPt, kPt, vb, acc, 1.f, red);
-    else tile_gemv<true>(Linv + (size_t)i * kPt * kPt, kPt, vb, acc, 1.f, red);
-    if (tid < kPt) out[(size_t)i * kPt + tid] = acc[tid];
+    if (bad) break;
+    if (BACK && tid < kPt) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += red[w][tid];
+      sv[tid] = rhs[(size_t)i * kPt + tid] - t;
+    }
+    if (BACK) __syncthreads();
+    // out_i = Linv_i s (forward) or Linv_i^T s (backward), from shared memory
+    if (!BACK) {
+      const float4 v = *reinterpret_cast<const float4*>(sv + 4 * lane);
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) {
+        const float4 m = *reinterpret_cast<const float4*>(inv + (16 * warp + rr) * kPt + 4 * lane);
+        const float t = warp_sum(m.x * v.x + m.y * v.y + m.z * v.z + m.w * v.w);
+        if (lane == 0) out[(size_t)i * kPt + 16 * warp + rr] = t;
+      }
+    } else {
+      float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) {
+        const float4 m = *reinterpret_cast<const float4*>(inv + (16 * warp + rr) * kPt + 4 * lane);
+        const float vr = sv[16 * warp + rr];
+        o[0] = fmaf(m.x, vr, o[0]);
+        o[1] = fmaf(m.y, vr, o[1]);
+        o[2] = fmaf(m.z, vr, o[2]);
+        o[3] = fmaf(m.w, vr, o[3]);
+      }
+      __syncthreads();  // red is rewritten
+#pragma unroll
+      for (int c = 0; c < 4; ++c) red[warp][4 * lane + c] = o[c];
+      __syncthreads();
+      if (tid < kPt) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += red[w][tid];
+        out[(size_t)i * kPt + tid] = t;
+      }
+    }
     __syncthreads();
     if (tid == 0) set_flag(&flags[i], epoch);
   }
@@ -629,13 +677,22 @@ __global__ void __launch_bounds__(kTrThreads) k_trsv_tiles(const float* __restri
 cudaError_t dense_trsv(bool back, const float* L, long long ld, const float* Linv, const float* rhs, float* out,
                        int T, unsigned* flags, unsigned epoch, int* err, int num_sms, cudaStream_t s) {
   if (T <= 0) return cudaSuccess;
+  constexpr int kTrSmem = kPt * kPt * 4;  // the diagonal inverse
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_trsv_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_trsv_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   int grid = std::min(T, num_sms);
   long long timeout = 1000000000LL;
   void* args[] = {(void*)&L, (void*)&ld, (void*)&Linv, (void*)&rhs, (void*)&out, (void*)&T, (void*)&flags,
                   (void*)&epoch, (void*)&timeout, (void*)&err};
   const void* fn = back ? reinterpret_cast<const void*>(&k_trsv_tiles<true>)
                         : reinterpret_cast<const void*>(&k_trsv_tiles<false>);
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTrThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTrThreads), args, kTrSmem, s);
 }
 
 // ---------------------------------------------------------------------------
