@@ -77,8 +77,9 @@ struct ba_problem {
   double *po_uv64 = nullptr, *po_tau64 = nullptr;
   float4* po_uvdf = nullptr;  // double-float copies for the FP32 problems' evaluation
   F2* po_taudf = nullptr;
-  F2* camdf = nullptr;
-  float4* ptdf = nullptr;
+  F2* camdf[2] = {nullptr, nullptr};      // per state slot; current when df_current[slot]
+  float4* ptdf[2] = {nullptr, nullptr};
+  bool df_current[2] = {false, false};    // written by the candidate kernels with the slot
   void *po_uvw = nullptr, *po_tauw = nullptr, *co_uvw = nullptr, *co_tauw = nullptr;
   int *co_pt = nullptr, *co_po = nullptr, *po_wrow = nullptr;
   int *chunk_obs = nullptr, *chunk_cam = nullptr, *cam_chunk = nullptr;
@@ -321,11 +322,14 @@ ba_status eval_state(ba_problem* pb, int slot, bool want_bits, bool with_cost, i
                             cmp ? pb->bits[ref_slot] : nullptr, cmp ? &pb->sc->valid_flips : nullptr,
                             with_cost ? pb->eval_parts : nullptr, pb->sc, slot, pb->eval_grid, pb->stream));
   else
-    LAUNCH(2, launch_eval_df(pb->L, pb->mp, pb->camw64[slot], pb->pts64[slot], pb->camdf, pb->ptdf,
+    LAUNCH(pb->df_current[slot] ? 1 : 2,
+           launch_eval_df(pb->L, pb->mp, pb->camw64[slot], pb->pts64[slot], pb->camdf[slot], pb->ptdf[slot],
+                          !pb->df_current[slot],
                              with_cost ? pb->obs_act : nullptr, want_bits ? pb->bits[slot] : nullptr,
                              cmp ? pb->bits[ref_slot] : nullptr, cmp ? &pb->sc->valid_flips : nullptr,
                              with_cost ? pb->eval_parts : nullptr, pb->sc, slot, pb->eval_grid, pb->stream));
   pb->flips_known = cmp;
+  if (!pb->fp64) pb->df_current[slot] = true;
   if (want_bits) pb->bits_valid[slot] = true;
   if (with_cost) pb->cost_valid[slot] = true;
   return BA_OK;
@@ -468,7 +472,7 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   CU(cudaMemsetAsync(&pb->sc->pcg_iters, 0, sizeof(int), pb->stream));
   CU(cudaMemsetAsync(&pb->sc->pcg_rel_res, 0, sizeof(double), pb->stream));
   if (Cf > 0) {
-    LAUNCH(4, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
+    LAUNCH(3, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
                                (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
                                Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->form_lanes, pb->num_sms, pb->evf[0],
                                pb->evf[1], pb->join_pending ? pb->join : nullptr, pb->stream));
@@ -549,7 +553,8 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     CU(cudaStreamWaitEvent(pb->side, pb->cand_fork, 0));
     LAUNCH(1, launch_candidate<T>(pb->C, 0, pb->crank, (const T*)pb->x, (const T*)pb->dp, pb->cams64[sl],
                                   pb->pts64[sl], pb->cams64[d], pb->pts64[d], pb->camw64[d],
-                                  pb->fp64 ? nullptr : (T*)pb->camw[d], (T*)pb->ptsw[d], pb->side));
+                                  pb->fp64 ? nullptr : (T*)pb->camw[d], (T*)pb->ptsw[d], pb->camdf[d], pb->ptdf[d],
+                                  pb->side));
     CU(cudaEventRecord(pb->cand_join, pb->side));
     pb->cand_cams_done = true;
   }
@@ -625,9 +630,10 @@ ba_status candidate_t(ba_problem* pb) {
   LAUNCH(early ? 1 : 2, launch_candidate<T>(early ? 0 : pb->C, pb->P, pb->crank, (const T*)pb->x, (const T*)pb->dp,
                                             pb->cams64[s], pb->pts64[s], pb->cams64[d], pb->pts64[d],
                                             pb->camw64[d], pb->fp64 ? nullptr : (T*)pb->camw[d],
-                                            (T*)pb->ptsw[d], pb->stream));
+                                            (T*)pb->ptsw[d], pb->camdf[d], pb->ptdf[d], pb->stream));
   if (early) CU(cudaStreamWaitEvent(pb->stream, pb->cand_join, 0));
   pb->cand_cams_done = false;
+  pb->df_current[d] = !pb->fp64;  // the candidate kernels wrote its double-float copy
   pb->bits_valid[d] = false;
   pb->cost_valid[d] = false;
   return BA_OK;
@@ -928,8 +934,10 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   if (!pb->fp64) {
     ST(dalloc(pb, &pb->po_uvdf, (size_t)N));
     ST(dalloc(pb, &pb->po_taudf, (size_t)N));
-    ST(dalloc(pb, &pb->camdf, (size_t)16 * C));
-    ST(dalloc(pb, &pb->ptdf, (size_t)2 * P));
+    for (int sl = 0; sl < 2; ++sl) {
+      ST(dalloc(pb, &pb->camdf[sl], (size_t)16 * C));
+      ST(dalloc(pb, &pb->ptdf[sl], (size_t)2 * P));
+    }
     if (N) LAUNCH(1, launch_obs_df(N, pb->po_uv64, pb->po_tau64, pb->po_uvdf, pb->po_taudf, pb->stream));
   }
   ST(dalloc(pb, &pb->cam_fixed, (size_t)C));
@@ -1427,6 +1435,7 @@ ba_status ba_set_params(ba_problem* pb, const double* cams, const double* pts) {
     LAUNCH(1, launch_prep_pts<float>(pb->pts64[s], (float*)pb->ptsw[s], pb->P, pb->stream));
   }
   pb->bits_valid[s] = pb->cost_valid[s] = false;
+  pb->df_current[s] = false;
   pb->state_changed = true;
   pb->same_validity = false;
   pb->linearized = false;
@@ -1703,6 +1712,7 @@ ba_status ba_eval_cost(ba_problem* pb, const double* cams, const double* pts, do
     else if (pb->P) CU(cudaMemcpyAsync(pb->pts64[slot], pb->pts64[pb->cur], sizeof(double) * 3 * (size_t)pb->P, cudaMemcpyDeviceToDevice, pb->stream));
     LAUNCH(1, launch_prep_cams<double>(pb->cams64[slot], pb->camw64[slot], nullptr, pb->C, pb->stream));
     pb->bits_valid[slot] = false;
+    pb->df_current[slot] = false;
   }
   ST(eval_state(pb, slot, false, true));
   if (slot != pb->cur) pb->cost_valid[slot] = false;

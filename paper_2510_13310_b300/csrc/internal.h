@@ -170,10 +170,11 @@ cudaError_t launch_eval64(const Layout& L, const ModelParams& mp, const double* 
                           const uint8_t* ref_bits, int* flips, double* partials, Scalars* sc, int slot, int grid,
                           cudaStream_t s);
 // double-float evaluation of FP32 problems (same outputs as launch_eval64);
-// camdf [C][16] and ptdf [P][2] are scratch for the converted state
+// camdf [C][16] and ptdf [P][2]: the state slot as double-float pairs
 cudaError_t launch_eval_df(const Layout& L, const ModelParams& mp, const double* camw64, const double* pts64,
-                           F2* camdf, float4* ptdf, const uint8_t* act, uint8_t* bits, const uint8_t* ref_bits,
-                           int* flips, double* partials, Scalars* sc, int slot, int grid, cudaStream_t s);
+                           F2* camdf, float4* ptdf, bool convert, const uint8_t* act, uint8_t* bits,
+                           const uint8_t* ref_bits, int* flips, double* partials, Scalars* sc, int slot, int grid,
+                           cudaStream_t s);  // convert: fill camdf/ptdf from camw64/pts64 first
 cudaError_t launch_obs_df(int N, const double* uv64, const double* tau64, float4* uvdf, F2* taudf, cudaStream_t s);
 
 cudaError_t launch_extract_begin(const Layout& L, uint8_t* alive, const uint8_t* bits,
@@ -256,7 +257,7 @@ template <typename T>
 cudaError_t launch_candidate(int C, int P, const int* crank, const T* x, const T* dp,
                              const double* cams_src, const double* pts_src, double* cams_dst,
                              double* pts_dst, double* camw64_dst, T* camw_dst, T* ptsw_dst,
-                             cudaStream_t s);
+                             F2* camdf_dst, float4* ptdf_dst, cudaStream_t s);  // *df_dst nullable
 template <typename T>
 cudaError_t launch_scatter_cams(int C, const int* crank, const T* x, double* dc, cudaStream_t s);
 template <typename T>

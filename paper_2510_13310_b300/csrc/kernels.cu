@@ -373,10 +373,11 @@ static F2 host_f2(double x) {
 }
 
 cudaError_t launch_eval_df(const Layout& L, const ModelParams& mp, const double* camw64, const double* pts64,
-                           F2* camdf, float4* ptdf, const uint8_t* act, uint8_t* bits, const uint8_t* ref_bits,
-                           int* flips, double* partials, Scalars* sc, int slot, int grid, cudaStream_t s) {
+                           F2* camdf, float4* ptdf, bool convert, const uint8_t* act, uint8_t* bits,
+                           const uint8_t* ref_bits, int* flips, double* partials, Scalars* sc, int slot, int grid,
+                           cudaStream_t s) {
   const int nconv = std::max(L.C * 16, L.P);
-  if (nconv > 0)
+  if (convert && nconv > 0)
     k_state_df<<<std::min((nconv + 255) / 256, 4096), 256, 0, s>>>(L.C, L.P, camw64, pts64, camdf, ptdf);
   EvalDFConst ec;
   ec.cx = host_f2(mp.cx);
@@ -1135,7 +1136,7 @@ cudaError_t launch_reduce_pred(const double* parts, int n, Scalars* sc, cudaStre
 template <typename T>
 __global__ void k_candidate_cams(int C, const int* __restrict__ crank, const T* __restrict__ x,
                                  const double* __restrict__ src, double* __restrict__ dst,
-                                 double* __restrict__ camw64, T* __restrict__ camw) {
+                                 double* __restrict__ camw64, T* __restrict__ camw, F2* __restrict__ camdf) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const double* s = src + 9 * (size_t)c;
@@ -1160,11 +1161,13 @@ __global__ void k_candidate_cams(int C, const int* __restrict__ crank, const T* 
   for (int i = 0; i < kCamStride; ++i) camw64[kCamStride * (size_t)c + i] = rec[i];
   if (camw)
     for (int i = 0; i < kCamStride; ++i) camw[kCamStride * (size_t)c + i] = (T)rec[i];
+  if (camdf)  // the double-float copy the FP32 problems' evaluation reads
+    for (int i = 0; i < 16; ++i) camdf[16 * (size_t)c + i] = i < 15 ? f2_from_double(rec[i]) : F2{0.f, 0.f};
 }
 
 template <typename T>
 __global__ void k_candidate_pts(int P, const T* __restrict__ dp, const double* __restrict__ src,
-                                double* __restrict__ dst, T* __restrict__ ptsw) {
+                                double* __restrict__ dst, T* __restrict__ ptsw, float4* __restrict__ ptdf) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   double v[3];
@@ -1179,16 +1182,22 @@ __global__ void k_candidate_pts(int P, const T* __restrict__ dp, const double* _
   q.z = (T)v[2];
   q.w = T(0);
   reinterpret_cast<V4*>(ptsw)[p] = q;
+  if (ptdf) {
+    const F2 x0 = f2_from_double(v[0]), x1 = f2_from_double(v[1]), x2 = f2_from_double(v[2]);
+    ptdf[2 * (size_t)p] = make_float4(x0.h, x0.l, x1.h, x1.l);
+    ptdf[2 * (size_t)p + 1] = make_float4(x2.h, x2.l, 0.f, 0.f);
+  }
 }
 
 template <typename T>
 cudaError_t launch_candidate(int C, int P, const int* crank, const T* x, const T* dp,
                              const double* cams_src, const double* pts_src, double* cams_dst,
                              double* pts_dst, double* camw64_dst, T* camw_dst, T* ptsw_dst,
-                             cudaStream_t s) {
+                             F2* camdf_dst, float4* ptdf_dst, cudaStream_t s) {
   // 32-thread blocks: the FP64 rotation work (sincos, atan2) of 32 cameras per SM
-  if (C > 0) k_candidate_cams<T><<<(C + 31) / 32, 32, 0, s>>>(C, crank, x, cams_src, cams_dst, camw64_dst, camw_dst);
-  if (P > 0) k_candidate_pts<T><<<(P + 255) / 256, 256, 0, s>>>(P, dp, pts_src, pts_dst, ptsw_dst);
+  if (C > 0)
+    k_candidate_cams<T><<<(C + 31) / 32, 32, 0, s>>>(C, crank, x, cams_src, cams_dst, camw64_dst, camw_dst, camdf_dst);
+  if (P > 0) k_candidate_pts<T><<<(P + 255) / 256, 256, 0, s>>>(P, dp, pts_src, pts_dst, ptsw_dst, ptdf_dst);
   return cudaGetLastError();
 }
 
@@ -1279,7 +1288,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
                                            double*, int, cudaStream_t);                             \
   template cudaError_t launch_candidate<T>(int, int, const int*, const T*, const T*, const double*, \
                                            const double*, double*, double*, double*, T*, T*,        \
-                                           cudaStream_t);                                           \
+                                           F2*, float4*, cudaStream_t);                             \
   template cudaError_t launch_scatter_cams<T>(int, const int*, const T*, double*, cudaStream_t);    \
   template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);              \
   template cudaError_t launch_permute_rows<T>(const int*, const int*, const T*, int, double*, int,    \

@@ -252,12 +252,17 @@ __global__ void k_S_finalize(int Cf, const T* __restrict__ Dblk, const double* _
   __shared__ T tile[32][33];
   const int n = 9 * Cf, ld = spcg_row_stride<T>(n);
   const int bx = blockIdx.x, by = blockIdx.y;  // tile column, tile row
-  if (bx > by) return;                          // only tiles on or below the diagonal
-  // read the transposed tile (upper triangle source)
-  int r0 = bx * 32, c0 = by * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    int r = r0 + i, c = c0 + threadIdx.x;
-    tile[i][threadIdx.x] = (r < n && c < n) ? Shat[(size_t)r * ld + c] : T(0);
+  // tiles on or below the diagonal, and the first tile above it (a 9 x 9 camera
+  // block can straddle two 32-tiles: its upper entries there are written too)
+  if (bx > by + 1) return;
+  const bool mirror = bx <= by;
+  if (mirror) {
+    // read the transposed tile (upper triangle source)
+    int r0 = bx * 32, c0 = by * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      int r = r0 + i, c = c0 + threadIdx.x;
+      tile[i][threadIdx.x] = (r < n && c < n) ? Shat[(size_t)r * ld + c] : T(0);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -268,28 +273,11 @@ __global__ void k_S_finalize(int Cf, const T* __restrict__ Dblk, const double* _
       int ir = r - 9 * fr, ic = c - 9 * fc;
       const T* di = reinterpret_cast<const T*>(dscale + n);
       Shat[(size_t)r * ld + c] = Dblk[45 * (size_t)fr + sym9(ir, ic)] * di[r] * di[c];
-    } else if (c < r) {
+    } else if (mirror && c < r) {
       Shat[(size_t)r * ld + c] = tile[threadIdx.x][i];
     }
   }
 }
-
-// Diagonal blocks of the upper triangle too (the mirror above writes only c <= r).
-template <typename T>
-__global__ void k_S_diag_upper(int Cf, const T* __restrict__ Dblk, const double* __restrict__ dscale,
-                               T* __restrict__ Shat) {
-  int f = blockIdx.x;
-  if (f >= Cf) return;
-  int n = 9 * Cf, ld = spcg_row_stride<T>(n);
-  for (int q = threadIdx.x; q < 81; q += blockDim.x) {
-    int ir = q / 9, ic = q - 9 * ir;
-    if (ic <= ir) continue;
-    int r = 9 * f + ir, c = 9 * f + ic;
-    const T* di = reinterpret_cast<const T*>(dscale + n);
-    Shat[(size_t)r * ld + c] = Dblk[45 * (size_t)f + sym9(ir, ic)] * di[r] * di[c];
-  }
-}
-
 
 // Jacobi scaling of the explicit system from the damped U blocks alone:
 // D = sqrt(diag U*) in FP64 and 1/D in the working precision (dscale + 9 Cf), with
@@ -346,7 +334,6 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
   if (join && (e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
   int nt = (n + 31) / 32;
   k_S_finalize<T><<<dim3(nt, nt), dim3(32, 8), 0, s>>>(Cf, Dblk, dscale, Shat);
-  k_S_diag_upper<T><<<Cf, 128, 0, s>>>(Cf, Dblk, dscale, Shat);
   return cudaGetLastError();
 }
 
