@@ -877,10 +877,31 @@ __global__ void __launch_bounds__(kCamThreads) k_cam_accum(
     }
   }
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // warp reduce-scatter of the 54 sums (padded to 64): each round a lane keeps
+  // half of its entries and adds its partner's copy of them (62 shuffles instead
+  // of 54 x 5); lane L ends with entries 32 b0 + 16 b1 + 8 b2 + 4 b3 + 2 b4 + (0, 1)
+  {
+    T v[64];
 #pragma unroll
-  for (int j = 0; j < 54; ++j) {
-    T v = warp_sum(acc[j]);
-    if (lane == 0) red[wid][j] = v;
+    for (int j = 0; j < 64; ++j) v[j] = j < 54 ? acc[j] : T(0);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const int H = 32 >> r;
+      const bool hi = (lane >> r) & 1;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        if (i < H) {
+          const T send = hi ? v[i] : v[H + i];
+          const T keep = hi ? v[H + i] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << r);
+        }
+      }
+    }
+    const int base = 32 * (lane & 1) + 16 * ((lane >> 1) & 1) + 8 * ((lane >> 2) & 1) + 4 * ((lane >> 3) & 1) +
+                     2 * ((lane >> 4) & 1);
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+      if (base + t < 54) red[wid][base + t] = v[t];
   }
   __syncthreads();
   for (int j = threadIdx.x; j < 54; j += blockDim.x) {
