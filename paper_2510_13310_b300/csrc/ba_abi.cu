@@ -134,6 +134,7 @@ struct ba_problem {
   double* dscale = nullptr;
   int spcg_grid = 0, spcg_rows_in_smem = 0, spcg_vecs_in_smem = 0, bs_grid = 1;
   void* spcg_scratch = nullptr;   // per-block PCG vectors when they do not fit in shared memory
+  void* spcg_M = nullptr;         // the preconditioner blocks, one copy for all blocks (with spcg_scratch)
   size_t spcg_scratch_stride = 0;
   size_t spcg_smem = 0;
   unsigned long long* spcg_words = nullptr;  // exchange words of the explicit PCG
@@ -513,6 +514,11 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     a.vecs_in_smem = pb->spcg_vecs_in_smem;
     a.scratch = (T*)pb->spcg_scratch;
     a.scratch_stride = pb->spcg_scratch_stride;
+    a.Mshared = nullptr;
+    if (pb->spcg_M) {
+      LAUNCH(1, launch_spcg_precond<T>(Cf, (const T*)pb->Dinv, pb->dscale, (T*)pb->spcg_M, pb->stream));
+      a.Mshared = (const T*)pb->spcg_M;
+    }
     a.x = (T*)pb->x;
     a.words = pb->spcg_words;
     a.err = pb->err;
@@ -1188,8 +1194,11 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
         return BA_ERR_INVALID_ARG;
       }
       if (!pb->spcg_vecs_in_smem) {
-        pb->spcg_scratch_stride = pb->fp64 ? spcg_vec_elems<double>(n_max, C) : spcg_vec_elems<float>(n_max, C);
+        // r, z, q, x per block (the preconditioner blocks are shared: spcg_M)
+        pb->spcg_scratch_stride =
+            (size_t)4 * (pb->fp64 ? spcg_row_stride<double>(n_max) : spcg_row_stride<float>(n_max));
         ST(dalloc_bytes(pb, &pb->spcg_scratch, R * pb->spcg_scratch_stride * pb->spcg_grid));
+        ST(dalloc_bytes(pb, &pb->spcg_M, R * (size_t)kSpcgMStride * std::max(1, C)));
       }
     }
     {

@@ -104,6 +104,7 @@ struct SpcgArgs {
   const T* b;                   // Schur right-hand side [n]
   int Cf, n, rows_in_smem, vecs_in_smem;
   T* x;                         // solution [n]
+  const T* Mshared;              // preconditioner blocks shared by all blocks (nullable)
   T* scratch;                   // per-block vectors when not in shared memory
   size_t scratch_stride;        // elements per block of scratch
   unsigned long long* words;    // exchange words [2][replicas][n][sizeof(T)/4]
@@ -232,6 +233,10 @@ template <typename T>
 const void* spcg_kernel_ptr(bool rows_in_smem);
 template <typename T>
 cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
+// the explicit PCG's preconditioner blocks into M [Cf][kSpcgMStride], for a shared copy
+constexpr int kSpcgMStride = 84;
+template <typename T>
+cudaError_t launch_spcg_precond(int Cf, const T* Dinv, const double* dscale, T* M, cudaStream_t s);
 int spcg_threads();
 int spcg_words_per_value(bool fp64);
 template <typename T>

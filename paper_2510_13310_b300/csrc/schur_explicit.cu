@@ -415,7 +415,7 @@ __device__ __forceinline__ T spcg_unpack(const unsigned long long* v) {
 // Preconditioner block of one camera, symmetric 9x9 stored in full: rows 0-4 at
 // 9 i, rows 5-8 from entry 48 on (each half starts on a 16-byte boundary), 84
 // entries per camera
-constexpr int kMStride = 84;
+constexpr int kMStride = kSpcgMStride;
 __host__ __device__ constexpr int mrow(int i) { return 9 * i + (i >= 5 ? 3 : 0); }
 
 constexpr int kSpcgRedStride = 64;  // warp sums of one block reduction (K x 16, K <= 4)
@@ -519,6 +519,36 @@ __device__ __forceinline__ void spcg_precond(const T* __restrict__ M, const T* _
   }
 }
 
+// Preconditioner blocks of S^: M^_f = diag(d) M_f diag(d), symmetrised, in T
+// (the same expression for (i, j) and (j, i), so M^_f is symmetric bit for bit),
+// cameras f = t0, t0 + stride, ...
+template <typename T>
+__device__ __forceinline__ void spcg_build_precond(int Cf, const T* __restrict__ Dinv, const double* __restrict__ dscale,
+                                                   T* __restrict__ M, int t0, int stride) {
+  for (int f = t0; f < Cf; f += stride) {
+    const T* Df = Dinv + 81 * (size_t)f;
+    T d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = (T)dscale[9 * f + i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int j = 0; j < 9; ++j) M[kMStride * f + mrow(i) + j] = (T(0.5) * (Df[9 * i + j] + Df[9 * j + i])) * (d[i] * d[j]);
+  }
+}
+
+template <typename T>
+__global__ void k_spcg_precond(int Cf, const T* __restrict__ Dinv, const double* __restrict__ dscale,
+                               T* __restrict__ M) {
+  spcg_build_precond<T>(Cf, Dinv, dscale, M, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <typename T>
+cudaError_t launch_spcg_precond(int Cf, const T* Dinv, const double* dscale, T* M, cudaStream_t s) {
+  if (Cf > 0) k_spcg_precond<T><<<(Cf + 127) / 128, 128, 0, s>>>(Cf, Dinv, dscale, M);
+  return cudaGetLastError();
+}
+
 // Persistent PCG: standard preconditioned CG (x0 = 0, block-Jacobi M^).  Thread
 // t handles the vector entries of cameras t, t + 512, ...
 // kRows: the block's rows of S^ sit in shared memory (else streamed from device
@@ -545,7 +575,10 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   T* zv = rv + ns;
   T* qv = zv + ns;
   T* xv = qv + ns;
-  T* Mv = xv + ns;
+  // preconditioner blocks: this block's copy, or one copy shared by all blocks
+  // (built before the launch) when the vectors live in device scratch
+  T* Mv = a.Mshared ? nullptr : xv + ns;
+  const T* Mr = a.Mshared ? a.Mshared : Mv;
   const T* Sg = a.Shat + (size_t)r0 * ns;
   const T* dinv = reinterpret_cast<const T*>(a.dscale + n);
 
@@ -560,18 +593,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     cp_async_commit();
   }
   for (int c = n + tid; c < ns; c += blockDim.x) pv[c] = zv[c] = xv[c] = T(0);
-  // preconditioner blocks of S^: M^_f = diag(d) M_f diag(d), symmetrised, in T
-  // (the same expression for (i, j) and (j, i), so M^_f is symmetric bit for bit)
-  for (int f = tid; f < Cf; f += blockDim.x) {
-    const T* Df = a.Dinv + 81 * (size_t)f;
-    T d[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) d[i] = (T)a.dscale[9 * f + i];
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-#pragma unroll
-      for (int j = 0; j < 9; ++j) Mv[kMStride * f + mrow(i) + j] = (T(0.5) * (Df[9 * i + j] + Df[9 * j + i])) * (d[i] * d[j]);
-  }
+  if (Mv) spcg_build_precond<T>(Cf, a.Dinv, a.dscale, Mv, tid, blockDim.x);
   __syncthreads();
   // r = b^, z = M^ r, p = z, x = 0; (r, z) and (r, r)
   T d0[2] = {T(0), T(0)};
@@ -582,7 +604,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
       rv[e + i] = a.b[e + i] * dinv[e + i];  // the correctly rounded product in T
       xv[e + i] = T(0);
     }
-    spcg_precond(Mv + kMStride * f, rv + e, zv + e);
+    spcg_precond(Mr + kMStride * f, rv + e, zv + e);
 #pragma unroll
     for (int i = 0; i < 9; ++i) pv[e + i] = zv[e + i];
     d0[0] += cam_dot(rv + e, zv + e);
@@ -780,7 +802,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
         rc[ii] = h ? o : ro[ii];
       }
       if (on) {
-        const T* M = Mv + kMStride * f + (h ? 48 : 0);
+        const T* M = Mr + kMStride * f + (h ? 48 : 0);
         T m[48];
         if constexpr (sizeof(T) == 4) {
           const float4* M4 = reinterpret_cast<const float4*>(M);
@@ -976,6 +998,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \
   template const void* spcg_kernel_ptr<T>(bool);                                                         \
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \
+  template cudaError_t launch_spcg_precond<T>(int, const T*, const double*, T*, cudaStream_t);          \
   template cudaError_t launch_backsub_pts<T>(const Layout&, const ModelParams&, const T*, const T*,    \
                                              const uint8_t*, const uint8_t*, const int*, const T*,     \
                                              const T*, const T*, const T*, const T*, double, T*, T*,   \
