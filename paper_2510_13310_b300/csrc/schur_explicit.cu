@@ -324,8 +324,11 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
       if (grid > 16 * num_sms) grid = 16 * num_sms;
       k_form_S_lanes<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
     } else {
+      // resident blocks only (three per SM in FP32), striding over the runs: no
+      // partly filled last wave
       int grid = (n_runs + wpb - 1) / wpb;
-      if (grid > 32 * num_sms) grid = 32 * num_sms;
+      const int resident = (sizeof(T) == 4 ? 3 : 1) * num_sms;
+      if (grid > resident) grid = resident;
       k_form_S_runs<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
     }
   }
