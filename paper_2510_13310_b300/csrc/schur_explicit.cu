@@ -321,7 +321,7 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
     if (lanes) {
       // many short runs: one lane per run
       int grid = (n_runs + 127) / 128;
-      if (grid > 16 * num_sms) grid = 16 * num_sms;
+      if (grid > 16 * num_sms) grid = 16 * num_sms;  // (a resident-only grid measured slower here)
       k_form_S_lanes<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
     } else {
       // resident blocks only (three per SM in FP32), striding over the runs: no
