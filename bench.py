@@ -39,7 +39,7 @@ METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 
 # DRAM bytes (read + write) of one launch of each roofline kernel, from ncu
 # captures of this workload (profiles/top_kernels_traffic_medium_1M_obs.md); None
 # once the kernel has changed since the counters were taken.
-NCU_TRAFFIC = {"k_spcg": 13152000 + 27136, "k_pcg": None, "k_form_S_runs": 325550080 + 8276736}
+NCU_TRAFFIC = {"k_spcg": 13138944 + 66560, "k_pcg": None, "k_form_S_runs": 303936768 + 7791360}
 WORKLOAD = "medium"
 LM_ITERS = 30
 E2E_RUNS = 3
