@@ -117,6 +117,31 @@ def test_extraction_bit_exact(thresholds):
         np.testing.assert_array_equal(np.flatnonzero(g["pt_mask"]), np.unique(sc.obs_pt[v]))
 
 
+def test_validity_decisions_at_the_threshold_follow_fp64():
+    """FP32 problems evaluate in double-float and re-evaluate in FP64 every validity
+    decision that falls within rounding of its threshold.  With min_depth 8 ulps
+    above or below one observation's FP64 depth (FP64 on both sides decides it the
+    same way; double-float alone could not), masks and ranks match the oracle bit
+    for bit and that observation gets the FP64 decision."""
+    from scipy.spatial.transform import Rotation
+    sc = geometric(12, 1500, 2, 8, 4.0, seed=8)
+    z = np.array([(Rotation.from_rotvec(sc.cams0[c, :3]).apply(sc.pts0[p]) + sc.cams0[c, 3:6])[2]
+                  for c, p in zip(sc.obs_cam, sc.obs_pt)])
+    order = np.argsort(z)
+    for k in (order[3], order[len(order) // 2]):
+        for sign in (-1.0, 1.0):
+            md = float(z[k] + sign * 8.0 * np.spacing(z[k]))
+            gpu, orc = pair(sc, ba.BA_FP32, min_depth=md)
+            gpu.extract()
+            g = gpu.get_active()
+            geom, _ = orc.predicate(sc.cams0, sc.pts0)
+            assert bool(geom[k]) == (sign < 0)
+            e = orc.extract(geom)
+            for key in ("cam_mask", "pt_mask", "obs_mask", "cam_rank", "pt_rank"):
+                np.testing.assert_array_equal(g[key], e[key], err_msg=key)
+            gpu.close()
+
+
 def test_extraction_residual_drop_and_order_invariance():
     sc = geometric(20, 3000, 2, 10, 5.0, seed=23)
     opt = dict(min_cam_obs=15, min_pt_obs=2, drop_residual_px=4.0, extract_every=5)
