@@ -191,6 +191,30 @@ def test_damped_step_matches_oracle(precision, tol, solver):
     assert not g["dc"][sc.fixed_cams].any()
 
 
+@pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-7), (ba.BA_FP32, 2e-2)])
+def test_explicit_step_with_many_short_runs_matches_oracle(precision, tol):
+    """About 99k co-visible camera pairs of a few shared points each: the explicit
+    system is formed by the kernel for many short co-visibility runs (chosen at
+    4 x 128 runs per SM and more) rather than the warp-per-run kernel."""
+    sc = geometric(450, 6000, 12, 12, 12.0, seed=57)
+    tracks = np.sort(sc.obs_cam.reshape(-1, 12), axis=1).astype(np.int64)
+    iu, ju = np.triu_indices(12, 1)
+    n_runs = np.unique(tracks[:, iu] * sc.spec.n_cams + tracks[:, ju]).size
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert n_runs >= 4 * 128 * sms
+    gpu, orc = pair(sc, precision, pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6,
+                    solver=ba.BA_SOLVER_EXPLICIT)
+    lam = 1e-3
+    g = gpu.solve_damped(lam)
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    o = orc.solve_step(ne, ext, lam)
+    assert rel_err(g["dc"], o["dc"]) < tol
+    assert rel_err(g["dp"], o["dp"]) < tol
+    assert g["pred_decrease"] == pytest.approx(o["pred_decrease"], rel=tol)
+
+
 @pytest.mark.parametrize("solver", [ba.BA_SOLVER_EXPLICIT, ba.BA_SOLVER_IMPLICIT])
 def test_reused_device_buffers_give_identical_runs(solver):
     """ba_destroy hands a problem's buffers to the process cache and the next
