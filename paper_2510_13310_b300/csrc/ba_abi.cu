@@ -848,6 +848,20 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   // inputs written by device work on any stream are complete before they are read
   if (dev_cams || dev_pts || dev_oc || dev_op || dev_uv || dev_depth) CU(cudaDeviceSynchronize());
   DevScratch scratch;
+  // the values (cameras, points, pixels, depths) upload on a second stream behind
+  // the observation indices, overlapping the index sorts of the layout; destroyed
+  // (after its copies end) before the scratch they land in
+  struct ValueStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t idx_done = nullptr;
+    ~ValueStream() {
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+      if (idx_done) cudaEventDestroy(idx_done);
+    }
+  } vals;
   const double *d_cams = cams, *d_pts = pts, *d_uv = obs_uv, *d_depth = depth;
   const int32_t *d_oc = obs_cam, *d_op = obs_pt;
   {
@@ -856,24 +870,39 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       size_t bytes;
       bool dev;
       const void** dst;
-    } ups[] = {{cams, sizeof(double) * 9 * (size_t)C, dev_cams, (const void**)&d_cams},
-               {pts, sizeof(double) * 3 * (size_t)P, dev_pts, (const void**)&d_pts},
-               {obs_uv, sizeof(double) * 2 * (size_t)N, dev_uv, (const void**)&d_uv},
-               {depth, sizeof(double) * (size_t)N, dev_depth, (const void**)&d_depth},
-               {obs_cam, sizeof(int32_t) * (size_t)N, dev_oc, (const void**)&d_oc},
-               {obs_pt, sizeof(int32_t) * (size_t)N, dev_op, (const void**)&d_op}};
+      bool value;
+    } ups[] = {{obs_cam, sizeof(int32_t) * (size_t)N, dev_oc, (const void**)&d_oc, false},
+               {obs_pt, sizeof(int32_t) * (size_t)N, dev_op, (const void**)&d_op, false},
+               {cams, sizeof(double) * 9 * (size_t)C, dev_cams, (const void**)&d_cams, true},
+               {pts, sizeof(double) * 3 * (size_t)P, dev_pts, (const void**)&d_pts, true},
+               {obs_uv, sizeof(double) * 2 * (size_t)N, dev_uv, (const void**)&d_uv, true},
+               {depth, sizeof(double) * (size_t)N, dev_depth, (const void**)&d_depth, true}};
     size_t total = 0;
+    bool host_values = false;
     for (const Up& u : ups)
-      if (!u.dev && u.bytes) total += (u.bytes + 255) / 256 * 256;
+      if (!u.dev && u.bytes) {
+        total += (u.bytes + 255) / 256 * 256;
+        host_values |= u.value;
+      }
     if (total) {
       CU(cached_malloc(&scratch.p, total));
+      if (host_values) {
+        CU(cudaStreamCreateWithFlags(&vals.s, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&vals.idx_done, cudaEventDisableTiming));
+      }
       char* at = static_cast<char*>(scratch.p);
-      for (const Up& u : ups)
-        if (!u.dev && u.bytes) {
-          CU(cudaMemcpyAsync(at, u.src, u.bytes, cudaMemcpyHostToDevice, pb->stream));
-          *u.dst = at;
-          at += (u.bytes + 255) / 256 * 256;
+      for (int pass = 0; pass < 2; ++pass) {  // the indices, then the values
+        if (pass == 1 && vals.s) {
+          CU(cudaEventRecord(vals.idx_done, pb->stream));
+          CU(cudaStreamWaitEvent(vals.s, vals.idx_done, 0));
         }
+        for (const Up& u : ups)
+          if (u.value == (pass == 1) && !u.dev && u.bytes) {
+            CU(cudaMemcpyAsync(at, u.src, u.bytes, cudaMemcpyHostToDevice, u.value && vals.s ? vals.s : pb->stream));
+            *u.dst = at;
+            at += (u.bytes + 255) / 256 * 256;
+          }
+      }
     }
   }
   // ---- validation and the observation layout (device; the grouping of points
@@ -885,7 +914,8 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   DevLayout dl;
   {
     std::string msg;
-    const int rc = build_obs_layout_dev(C, P, N, d_cams, d_pts, d_uv, d_oc, d_op, dev_alloc, pb->stream, &dl, &msg);
+    const int rc =
+        build_obs_layout_dev(C, P, N, d_cams, d_pts, d_uv, d_oc, d_op, dev_alloc, pb->stream, vals.s, &dl, &msg);
     if (rc) {
       set_error("%s", msg.c_str());
       return rc == 1 ? BA_ERR_INVALID_ARG : rc == 3 ? BA_ERR_OOM : BA_ERR_CUDA;
@@ -1603,7 +1633,7 @@ ba_status ba_selftest_layout(int64_t n_cams, const double* cams, int64_t n_pts, 
   cudaStream_t st = nullptr;
   DevLayout D;
   DevCovis dc;
-  int drc = build_obs_layout_dev(C, P, N, d_cams, d_pts, d_uv, d_oc, d_op, alloc, st, &D, &derr);
+  int drc = build_obs_layout_dev(C, P, N, d_cams, d_pts, d_uv, d_oc, d_op, alloc, st, nullptr, &D, &derr);
   if (!drc && with_covis) drc = build_covis_runs_dev(D, C, N, alloc, st, &dc, &derr);
   if (drc >= 2) {
     set_error("ba_selftest_layout: %s", derr.c_str());

@@ -430,9 +430,10 @@ __global__ void k_cv_counts(int4* __restrict__ runs, int n_runs, int npairs) {
 // host drivers
 // ---------------------------------------------------------------------------
 
-int build_obs_layout_dev(int C, int P, int N, const double* d_cams, const double* d_pts, const double* d_uv,
-                         const int32_t* d_oc, const int32_t* d_op, const DevAlloc& alloc, cudaStream_t s,
-                         DevLayout* L, std::string* err) {
+namespace {
+int build_obs_layout_impl(int C, int P, int N, const double* d_cams, const double* d_pts, const double* d_uv,
+                          const int32_t* d_oc, const int32_t* d_op, bool check_values, const DevAlloc& alloc,
+                          cudaStream_t s, DevLayout* L, std::string* err) {
   Scratch sc(s);
   Flags* fl = sc.get<Flags>(1);
   if (!fl) return fail(err, 2, "device scratch allocation failed");
@@ -440,10 +441,10 @@ int build_obs_layout_dev(int C, int P, int N, const double* d_cams, const double
   unsigned long long* dig = sc.get<unsigned long long>(nch);
   DCU(cudaMemsetAsync(fl, 0xFF, 2 * sizeof(unsigned long long), s));
   DCU(cudaMemsetAsync(&fl->nonfinite, 0, sizeof(int), s));
-  if (C) k_check_finite<<<grid_for(9LL * C, 256), 256, 0, s>>>(d_cams, 9LL * C, 1, fl);
-  if (P) k_check_finite<<<grid_for(3LL * P, 256), 256, 0, s>>>(d_pts, 3LL * P, 2, fl);
+  if (C && check_values) k_check_finite<<<grid_for(9LL * C, 256), 256, 0, s>>>(d_cams, 9LL * C, 1, fl);
+  if (P && check_values) k_check_finite<<<grid_for(3LL * P, 256), 256, 0, s>>>(d_pts, 3LL * P, 2, fl);
   if (N) {
-    k_check_finite<<<grid_for(2LL * N, 256), 256, 0, s>>>(d_uv, 2LL * N, 4, fl);
+    if (check_values) k_check_finite<<<grid_for(2LL * N, 256), 256, 0, s>>>(d_uv, 2LL * N, 4, fl);
     k_check_index<<<grid_for(N, 256), 256, 0, s>>>(d_oc, d_op, N, C, P, fl);
     k_hash_chunks<<<(nch + 127) / 128, 128, 0, s>>>(d_oc, d_op, N, dig, nch);
   }
@@ -565,6 +566,32 @@ int build_obs_layout_dev(int C, int P, int N, const double* d_cams, const double
   L->h_cam_off = std::move(cam_off);
   DCU(cudaStreamSynchronize(s));  // host vectors above are released on return
   return 0;
+}
+}  // namespace
+
+int build_obs_layout_dev(int C, int P, int N, const double* d_cams, const double* d_pts, const double* d_uv,
+                         const int32_t* d_oc, const int32_t* d_op, const DevAlloc& alloc, cudaStream_t s,
+                         cudaStream_t vs, DevLayout* L, std::string* err) {
+  if (!vs) return build_obs_layout_impl(C, P, N, d_cams, d_pts, d_uv, d_oc, d_op, true, alloc, s, L, err);
+  // the value checks run on vs behind the values' uploads while the index work
+  // runs on s; their result is read last but reported first (the order of the
+  // checks is the same as with one stream)
+  Scratch vsc(vs);
+  Flags* fl = vsc.get<Flags>(1);
+  if (!fl) return fail(err, 2, "device scratch allocation failed");
+  DCU(cudaMemsetAsync(&fl->nonfinite, 0, sizeof(int), vs));
+  if (C) k_check_finite<<<grid_for(9LL * C, 256), 256, 0, vs>>>(d_cams, 9LL * C, 1, fl);
+  if (P) k_check_finite<<<grid_for(3LL * P, 256), 256, 0, vs>>>(d_pts, 3LL * P, 2, fl);
+  if (N) k_check_finite<<<grid_for(2LL * N, 256), 256, 0, vs>>>(d_uv, 2LL * N, 4, fl);
+  DCU(cudaGetLastError());
+  const int rc = build_obs_layout_impl(C, P, N, d_cams, d_pts, d_uv, d_oc, d_op, false, alloc, s, L, err);
+  int nonfinite = 0;
+  DCU(cudaStreamSynchronize(vs));
+  DCU(cudaMemcpy(&nonfinite, &fl->nonfinite, sizeof(int), cudaMemcpyDeviceToHost));
+  if (nonfinite & 1) return fail(err, 1, "non-finite camera parameter");
+  if (nonfinite & 2) return fail(err, 1, "non-finite point");
+  if (nonfinite & 4) return fail(err, 1, "non-finite observation");
+  return rc;
 }
 
 int build_covis_runs_dev(const DevLayout& L, int C, int N, const DevAlloc& alloc, cudaStream_t s, DevCovis* out,

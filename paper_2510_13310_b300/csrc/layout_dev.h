@@ -38,9 +38,11 @@ struct DevCovis {
 
 // d_*: device arrays.  Returns 0; 1 invalid input, 2 CUDA error, 3 out of memory
 // (message in *err).  The same checks, messages and layout as build_obs_layout.
+// vs (nullable): a second stream on which d_cams, d_pts and d_uv become ready
+// (their finiteness is checked there, overlapping the index work on s).
 int build_obs_layout_dev(int C, int P, int N, const double* d_cams, const double* d_pts, const double* d_uv,
                          const int32_t* d_oc, const int32_t* d_op, const DevAlloc& alloc, cudaStream_t s,
-                         DevLayout* L, std::string* err);
+                         cudaStream_t vs, DevLayout* L, std::string* err);
 int build_covis_runs_dev(const DevLayout& L, int C, int N, const DevAlloc& alloc, cudaStream_t s, DevCovis* out,
                          std::string* err);
 

@@ -49,3 +49,30 @@ def test_nonfinite_parameters_refused():
     with pytest.raises(ba.BAError, match="invalid argument"):
         p.set_params(cams, sc.pts0)
     p.lm_step()  # the problem is unchanged and usable
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_create_from_host_arrays_reports_errors_in_check_order(pinned):
+    """Host arrays: the indices upload first and are sorted while the values
+    upload on a second stream and are checked there; a non-finite value is still
+    reported before an index error, as when every check runs on one stream."""
+    sc = scenes.make_scene("small", scale=0.5)
+    host = (lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()) if pinned else np.ascontiguousarray
+
+    def create(cams, pts, oc, op, uv, depth):
+        return ba.Problem(host(cams), host(pts), host(oc), host(op), host(uv), host(depth))
+
+    args = [sc.cams0, sc.pts0, sc.obs_cam, sc.obs_pt, sc.obs_uv, sc.depth]
+    bad_uv = sc.obs_uv.copy()
+    bad_uv[7, 0] = np.nan
+    bad_oc = sc.obs_cam.copy()
+    bad_oc[3] = sc.spec.n_cams
+    for (uv, oc), msg in [((bad_uv, sc.obs_cam), "non-finite observation"),
+                          ((sc.obs_uv, bad_oc), "index out of range"),
+                          ((bad_uv, bad_oc), "non-finite observation")]:
+        with pytest.raises(ba.BAError, match="invalid argument"):
+            create(args[0], args[1], oc, args[3], uv, args[5])
+        assert msg in ba.lib().ba_last_error().decode()
+    # and a valid problem from the same host arrays solves
+    p = create(*args)
+    p.lm_step()
