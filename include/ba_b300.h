@@ -279,8 +279,10 @@ void ba_explicit_layout(const ba_problem* pb, int* rows_in_smem, int* vecs_in_sm
 
 /* Free a problem.  Its device buffers go to a process-wide cache that later
  * ba_create calls draw from (no new device mappings when problems of similar
- * sizes are created repeatedly); ba_release_cache returns every cached buffer to
- * the driver.  Setting BA_NO_ALLOC_CACHE=1 in the environment disables the cache. */
+ * sizes are created repeatedly), and ba_create's temporary layout scratch comes
+ * from a pool that keeps its memory; ba_release_cache returns every cached buffer
+ * and the pool's unused memory to the driver.  Setting BA_NO_ALLOC_CACHE=1 in the
+ * environment disables the buffer cache. */
 void ba_destroy(ba_problem* pb);
 void ba_release_cache(void);
 const char* ba_status_string(ba_status s);

@@ -1843,6 +1843,7 @@ void ba_release_cache(void) {
   }
   c.free_blocks.clear();
   cudaSetDevice(cur);
+  release_scratch_pools();
 }
 
 const char* ba_status_string(ba_status s) {

@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <map>
+#include <mutex>
 
 #include "layout_dev.h"
 #include "tile_meta.cuh"
@@ -19,17 +21,44 @@ namespace {
 // device scratch (stream-ordered allocations, released at scope exit)
 // ---------------------------------------------------------------------------
 
+// Stream-ordered scratch from a memory pool of the library's own per device that
+// keeps its memory when freed (release threshold: unlimited), so that building a
+// second layout maps no new memory; released by release_scratch_pools().
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaMemPool_t scratch_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+  uint64_t keep = ~0ull;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  g_pools[dev] = pool;
+  return pool;
+}
+
 struct Scratch {
   cudaStream_t s;
+  cudaMemPool_t pool;
   std::vector<void*> ptrs;
-  explicit Scratch(cudaStream_t st) : s(st) {}
+  explicit Scratch(cudaStream_t st) : s(st), pool(scratch_pool()) {}
   ~Scratch() {
     for (void* p : ptrs) cudaFreeAsync(p, s);
   }
   template <typename T>
   T* get(size_t n) {
     void* p = nullptr;
-    if (cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(T), s) != cudaSuccess) return nullptr;
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    if ((pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s)) != cudaSuccess)
+      return nullptr;
     ptrs.push_back(p);
     return static_cast<T*>(p);
   }
@@ -568,6 +597,11 @@ int build_obs_layout_impl(int C, int P, int N, const double* d_cams, const doubl
   return 0;
 }
 }  // namespace
+
+void release_scratch_pools() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (auto& kv : g_pools) cudaMemPoolTrimTo(kv.second, 0);
+}
 
 int build_obs_layout_dev(int C, int P, int N, const double* d_cams, const double* d_pts, const double* d_uv,
                          const int32_t* d_oc, const int32_t* d_op, const DevAlloc& alloc, cudaStream_t s,
