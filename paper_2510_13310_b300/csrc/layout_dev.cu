@@ -283,15 +283,29 @@ __global__ void k_check_index(const int32_t* __restrict__ oc, const int32_t* __r
 }
 
 // FNV-1a over 32-bit words of each 256-observation chunk's (camera, point) pairs
-__global__ void k_hash_chunks(const int32_t* __restrict__ oc, const int32_t* __restrict__ op, int N,
-                              unsigned long long* __restrict__ dig, int nch) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nch) return;
+// FNV-1a over each 256-observation chunk (camera, point of every observation in
+// input order).  Each 64-thread block stages its 16 chunks in shared memory with
+// coalesced loads (row stride 257: the 16 hashing threads read distinct banks),
+// then one thread per chunk runs the sequential hash.
+constexpr int kHashChunks = 16;
+__global__ void __launch_bounds__(64) k_hash_chunks(const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
+                                                    int N, unsigned long long* __restrict__ dig, int nch) {
+  __shared__ int32_t soc[kHashChunks * 257], sop[kHashChunks * 257];
+  const long long base = (long long)blockIdx.x * (kHashChunks * 256);
+  for (int e = threadIdx.x; e < kHashChunks * 256; e += blockDim.x) {
+    const long long k = base + e;
+    const int at = (e >> 8) * 257 + (e & 255);
+    soc[at] = k < N ? oc[k] : 0;
+    sop[at] = k < N ? op[k] : 0;
+  }
+  __syncthreads();
+  const int t = threadIdx.x, c = blockIdx.x * kHashChunks + t;
+  if (t >= kHashChunks || c >= nch) return;
   unsigned long long h = 1469598103934665603ull;
-  const long long k1 = min((long long)N, ((long long)c + 1) << 8);
-  for (long long k = (long long)c << 8; k < k1; ++k) {
-    h = (h ^ (unsigned long long)(unsigned)oc[k]) * 1099511628211ull;
-    h = (h ^ (unsigned long long)(unsigned)op[k]) * 1099511628211ull;
+  const int n = (int)(min((long long)N, ((long long)c + 1) << 8) - ((long long)c << 8));
+  for (int i = 0; i < n; ++i) {
+    h = (h ^ (unsigned long long)(unsigned)soc[t * 257 + i]) * 1099511628211ull;
+    h = (h ^ (unsigned long long)(unsigned)sop[t * 257 + i]) * 1099511628211ull;
   }
   dig[c] = h;
 }
@@ -475,7 +489,7 @@ int build_obs_layout_impl(int C, int P, int N, const double* d_cams, const doubl
   if (N) {
     if (check_values) k_check_finite<<<grid_for(2LL * N, 256), 256, 0, s>>>(d_uv, 2LL * N, 4, fl);
     k_check_index<<<grid_for(N, 256), 256, 0, s>>>(d_oc, d_op, N, C, P, fl);
-    k_hash_chunks<<<(nch + 127) / 128, 128, 0, s>>>(d_oc, d_op, N, dig, nch);
+    k_hash_chunks<<<(nch + kHashChunks - 1) / kHashChunks, 64, 0, s>>>(d_oc, d_op, N, dig, nch);
   }
   DCU(cudaGetLastError());
   Flags h_fl;
