@@ -987,10 +987,63 @@ __global__ void k_damp_pts(int P, const T* __restrict__ V, const T* __restrict__
   zo[2] = (T)(i02 * g0 + i12 * g1 + i22 * g2);
 }
 
+// FP32 problems: the same damped inverse in double-float arithmetic (about 48
+// significant bits, on the FP32 pipe instead of the narrow FP64 one); the results
+// are rounded to FP32 as before.  The clamp and the determinant's sign test are
+// taken on the leading FP32 word, which carries the sign and magnitude.
+__device__ __forceinline__ F2 f2_of(float x) { return F2{x, 0.f}; }
+__device__ __forceinline__ float f2_round(F2 a) { return __fadd_rn(a.h, a.l); }
+
+__global__ void k_damp_pts_df(int P, const float* __restrict__ V, const float* __restrict__ gp,
+                              const uint8_t* __restrict__ pt_act, F2 lambda, float* __restrict__ Vinv,
+                              float* __restrict__ z0, int* err) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float* vo = Vinv + 6 * (size_t)p;
+  float* zo = z0 + 3 * (size_t)p;
+  if (!pt_act[p]) {
+    for (int j = 0; j < 6; ++j) vo[j] = 0.f;
+    for (int j = 0; j < 3; ++j) zo[j] = 0.f;
+    return;
+  }
+  const float* v = V + 6 * (size_t)p;
+  const float v0 = v[0], v3 = v[3], v5 = v[5];
+  const F2 b = f2_of(v[1]), c = f2_of(v[2]), e = f2_of(v[4]);
+  auto damp = [&](float x) { return f2_add(f2_of(x), f2_mul(lambda, f2_of(fminf(fmaxf(x, 1e-6f), 1e32f)))); };
+  const F2 a = damp(v0), d = damp(v3), f = damp(v5);
+  // adjugate of the symmetric matrix
+  const F2 A = f2_sub(f2_mul(d, f), f2_mul(e, e)), B = f2_sub(f2_mul(c, e), f2_mul(b, f)),
+           Cc = f2_sub(f2_mul(b, e), f2_mul(c, d));
+  const F2 det = f2_add(f2_add(f2_mul(a, A), f2_mul(b, B)), f2_mul(c, Cc));
+  if (!(det.h > 0.f) || !f2_finite(det)) {
+    atomicOr(err, 4);
+    for (int j = 0; j < 6; ++j) vo[j] = 0.f;
+    for (int j = 0; j < 3; ++j) zo[j] = 0.f;
+    return;
+  }
+  const F2 id = f2_recip(det);
+  const F2 i00 = f2_mul(A, id), i01 = f2_mul(B, id), i02 = f2_mul(Cc, id);
+  const F2 i11 = f2_mul(f2_sub(f2_mul(a, f), f2_mul(c, c)), id);
+  const F2 i12 = f2_mul(f2_sub(f2_mul(b, c), f2_mul(a, e)), id);
+  const F2 i22 = f2_mul(f2_sub(f2_mul(a, d), f2_mul(b, b)), id);
+  vo[0] = f2_round(i00); vo[1] = f2_round(i01); vo[2] = f2_round(i02);
+  vo[3] = f2_round(i11); vo[4] = f2_round(i12); vo[5] = f2_round(i22);
+  const F2 g0 = f2_of(gp[3 * (size_t)p]), g1 = f2_of(gp[3 * (size_t)p + 1]), g2 = f2_of(gp[3 * (size_t)p + 2]);
+  zo[0] = f2_round(f2_add(f2_add(f2_mul(i00, g0), f2_mul(i01, g1)), f2_mul(i02, g2)));
+  zo[1] = f2_round(f2_add(f2_add(f2_mul(i01, g0), f2_mul(i11, g1)), f2_mul(i12, g2)));
+  zo[2] = f2_round(f2_add(f2_add(f2_mul(i02, g0), f2_mul(i12, g1)), f2_mul(i22, g2)));
+}
+
 template <typename T>
 cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_act, double lambda,
                             T* Vinv, T* z0, int* err, cudaStream_t s) {
-  if (P > 0) k_damp_pts<T><<<(P + 255) / 256, 256, 0, s>>>(P, V, gp, pt_act, lambda, Vinv, z0, err);
+  if (P <= 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    const float lh = (float)lambda;
+    const F2 lam{lh, (float)(lambda - (double)lh)};
+    k_damp_pts_df<<<(P + 255) / 256, 256, 0, s>>>(P, V, gp, pt_act, lam, Vinv, z0, err);
+  } else
+    k_damp_pts<T><<<(P + 255) / 256, 256, 0, s>>>(P, V, gp, pt_act, lambda, Vinv, z0, err);
   return cudaGetLastError();
 }
 
