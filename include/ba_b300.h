@@ -50,6 +50,9 @@ typedef enum {
   BA_ERR_TIMEOUT = 7        /* an in-kernel grid barrier gave up waiting */
 } ba_status;
 
+/* Arithmetic of steps (a)-(e).  The tensor-core form of the dense reduced camera
+ * system (FP32 with the TF32 blocked Cholesky) is not a third precision here: it
+ * is BA_FP32 with solver = BA_SOLVER_DENSE. */
 typedef enum { BA_FP64 = 0, BA_FP32 = 1 } ba_precision;
 
 typedef struct {
@@ -81,9 +84,16 @@ typedef struct {
                                   BA_SOLVER_DENSE (FP32 only: S formed, factored by the
                                   tensor-core blocked Cholesky, CG preconditioned with
                                   that factor to pcg_rel_tol) */
+  int extract_mode;            /* BA_EXTRACT_DYNAMIC: step (c) at the start of every iteration
+                                  whose state changed (Sec. 4.2 steps 1-3).  BA_EXTRACT_ONCE:
+                                  one-shot pruning, the alternative Sec. 4.2 argues against:
+                                  validity and peeling at the first iteration only, the active
+                                  set then frozen (no residual drops); ba_set_params and
+                                  ba_set_state start a new run and extract again */
 } ba_options;
 
 enum { BA_SOLVER_AUTO = 0, BA_SOLVER_IMPLICIT = 1, BA_SOLVER_EXPLICIT = 2, BA_SOLVER_DENSE = 3 };
+enum { BA_EXTRACT_DYNAMIC = 0, BA_EXTRACT_ONCE = 1 };
 
 typedef struct {
   double cost;        /* F(x) = 1/2 sum rho(|r_k|^2) over the iteration's active set */
@@ -111,6 +121,10 @@ void ba_default_options(ba_options* o);
 
 /* Create a problem: cams [C][9], pts [P][3], obs_cam/obs_pt [N] (int32 indices),
  * obs_uv [N][2] pixels, depth [N] metric depth prior (<= 0 or NaN: none).
+ * These are the unknowns and measurements of the BA objective with depth
+ * (Sec. 3.2, Eq. BA objective; Sec. 4.1, depth residual with the mask m = 1 when
+ * a prior is given): the parameter vector x = [c; p] and the observation set
+ * from which Sec. 4.2 step 1 builds O_valid at every iteration.
  * Checks index ranges, finiteness and duplicate (camera, point) pairs on the
  * host (BA_ERR_INVALID_ARG).  Limits: N < 2^31, at most 256 observations per
  * point.  stream: a cudaStream_t (NULL = legacy default stream).  The problem
@@ -128,13 +142,17 @@ ba_status ba_create(const ba_options* opts, void* stream, int64_t n_cams, const 
  * Returns BA_ERR_NOT_CONVERGED when PCG hit its cap (the iteration still ran). */
 ba_status ba_lm_step(ba_problem* pb, ba_iter_info* info);
 
-/* Up to max_iters LM iterations; log has max_iters entries or is NULL. */
+/* Up to max_iters LM iterations (Sec. 3.3: the LM loop; each iteration is one
+ * ba_lm_step); log has max_iters entries or is NULL.  Stops early only on an
+ * error other than BA_ERR_NOT_CONVERGED; *n_done (nullable) gets the count. */
 ba_status ba_solve(ba_problem* pb, int max_iters, ba_iter_info* log, int* n_done);
 
-/* Current parameters, cams [C][9] and pts [P][3]. */
+/* Current parameters, cams [C][9] and pts [P][3]: the full arrays c and p of
+ * Sec. 4.2, inactive entries unchanged since they left the active set (step 3). */
 ba_status ba_get_params(ba_problem* pb, double* cams, double* pts);
 
-/* Replace the current parameters; the next step re-extracts and re-linearises. */
+/* Replace the full parameter arrays c and p (Sec. 4.2); the next step re-runs
+ * the validity check and extraction (step 1) and re-linearises. */
 ba_status ba_set_params(ba_problem* pb, const double* cams, const double* pts);
 
 /* Checkpoint and resume of an LM run.  The state is everything later iterations
@@ -198,8 +216,9 @@ ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_d
 
 /* FP64 cost of a state without allocating device memory.  The paper has no
  * counterpart: this is an interface for callers that cannot call cudaMalloc,
- * such as code captured into a CUDA graph, code running under a framework that
- * owns all device memory, or code that must avoid the synchronisation an
+ * such as code running under a framework that owns all device memory (its
+ * allocator accounts for every byte, or the budget is fixed at start-up), or
+ * latency-critical code that must avoid the device-wide synchronisation an
  * allocation can cause.  Returns on the stream (asynchronously)
  * out[0] = 1/2 sum rho(|r_k|^2), out[1] = reprojection RMSE, out[2] = number of
  * observations counted, over observations with obs_mask[k] != 0 (NULL: all),
@@ -208,11 +227,15 @@ ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_d
  * ignored).  Observations whose indices are out of range are skipped.
  * Every array (inputs and out) must be readable/writable by kernels of the
  * current device: device memory of that device, managed memory, or mapped
- * page-locked host memory; anything else is rejected (BA_ERR_INVALID_ARG).
+ * page-locked host memory passed as its device alias (the same address under
+ * unified addressing); anything else is rejected (BA_ERR_INVALID_ARG).  Sizes
+ * are not checked against the arrays: each must hold its stated count.
  * Scratch is a fixed device array in the library (about 0.55 MB per device
  * that loads it, held until exit): n_cams above 4096 is rejected with
  * BA_ERR_INVALID_ARG.  The first call on a device looks that array up
- * (cudaGetSymbolAddress); make it before any stream capture.  Every call
+ * (cudaGetSymbolAddress) and keeps its address for the life of the process;
+ * make it before any stream capture, and do not call this after a reset of the
+ * device (cudaDeviceReset) in the same process.  Every call
  * shares the array, so calls whose work overlaps on the GPU (other streams,
  * other host threads) race; order them on one stream.  Nothing in the scratch
  * needs clearing: each call writes every entry it reads. */
@@ -277,7 +300,8 @@ int ba_solver_kind(const ba_problem* pb);
  * of the persistent PCG launch. */
 void ba_explicit_layout(const ba_problem* pb, int* rows_in_smem, int* vecs_in_smem, int* grid);
 
-/* Free a problem.  Its device buffers go to a process-wide cache that later
+/* Free a problem (the paper has no counterpart: resource management of this
+ * interface).  Its device buffers go to a process-wide cache that later
  * ba_create calls draw from (no new device mappings when problems of similar
  * sizes are created repeatedly), and ba_create's temporary layout scratch comes
  * from a pool that keeps its memory; ba_release_cache returns every cached buffer

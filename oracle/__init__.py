@@ -34,7 +34,8 @@ class Opts(ct.Structure):
                 ("invalid_depth_weight", ct.c_double), ("min_depth", ct.c_double),
                 ("extract_every", ct.c_int), ("drop_residual_px", ct.c_double),
                 ("min_cam_obs", ct.c_int), ("min_pt_obs", ct.c_int), ("lambda0", ct.c_double),
-                ("pcg_rel_tol", ct.c_double), ("pcg_max_iters", ct.c_int), ("solver", ct.c_int)]
+                ("pcg_rel_tol", ct.c_double), ("pcg_max_iters", ct.c_int), ("solver", ct.c_int),
+                ("extract_mode", ct.c_int)]
 
 
 class IterLog(ct.Structure):
@@ -78,6 +79,10 @@ def lib():
         L.oracle_backward.argtypes = [ct.POINTER(Problem), ct.POINTER(Opts), P_f64, P_f64, P_u8,
                                       P_i32, P_i32, c_i64, P_f64, P_f64, P_f64, P_f64]
         L.oracle_backward.restype = ct.c_int
+        L.oracle_lm_accept.argtypes = [ct.c_double, ct.c_double, ct.c_double]
+        L.oracle_lm_accept.restype = ct.c_int
+        L.oracle_lm_damping.argtypes = [ct.c_int, ct.c_double, ct.POINTER(ct.c_double),
+                                        ct.POINTER(ct.c_double)]
         L.oracle_set_threads.argtypes = [ct.c_int]
         L.oracle_get_threads.restype = ct.c_int
         _LIB = L
@@ -110,6 +115,7 @@ class OracleOptions:
     pcg_rel_tol: float = 1e-6
     pcg_max_iters: int = 500
     solver: int = 0  # 0 dense Cholesky of the Schur system, 1 PCG
+    extract_mode: int = 0  # 0 dynamic (every iteration), 1 one-shot at the first iteration
 
     def to_c(self) -> Opts:
         return Opts(**dataclasses.asdict(self))
@@ -274,6 +280,17 @@ def observe(cam, X, uv, tau, wt, cx=320.0, cy=240.0):
     lib().oracle_observe(_p(_f64(cam), P_f64), _p(_f64(X), P_f64), _p(_f64(uv), P_f64), tau, wt,
                          cx, cy, _p(r, P_f64), _p(Jc, P_f64), _p(Jp, P_f64), ct.byref(z), _p(uvh, P_f64))
     return r, Jc.reshape(3, 9), Jp.reshape(3, 3), z.value, uvh
+
+
+def lm_accept(F, Fc, pred) -> bool:
+    return bool(lib().oracle_lm_accept(float(F), float(Fc), float(pred)))
+
+
+def lm_damping(accepted, gain, lam, nu):
+    """One damping update; returns (lambda, nu) after the step."""
+    a, b = ct.c_double(lam), ct.c_double(nu)
+    lib().oracle_lm_damping(int(bool(accepted)), float(gain), ct.byref(a), ct.byref(b))
+    return a.value, b.value
 
 
 def set_threads(n: int):

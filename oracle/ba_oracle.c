@@ -36,6 +36,7 @@ void oracle_default_opts(oracle_opts* o) {
   o->pcg_rel_tol = 1e-6;
   o->pcg_max_iters = 500;
   o->solver = 0;
+  o->extract_mode = 0;
 }
 
 void oracle_set_threads(int n) {
@@ -899,6 +900,32 @@ void oracle_apply_step(int64_t n_cams, int64_t n_pts, const double* cams, const 
 /* LM loop (Sec. 3.3) with dynamic parameter extraction every iteration        */
 /* ------------------------------------------------------------------------- */
 
+/* Gain-ratio test of Sec. 3.3's LM loop.  The paper names Marquardt damping but
+ * not its control; the reading is Nielsen's rule as given by Madsen, Nielsen and
+ * Tingleff, "Methods for non-linear least squares problems" (2004), Sec. 3.2:
+ * gain = (F(x) - F(x + h)) / (L(0) - L(h)); the step is taken when the gain is
+ * positive; here "positive" is gain > 1e-3, and a non-finite candidate cost or
+ * a non-positive predicted decrease rejects. */
+int oracle_lm_accept(double F, double Fc, double pred) {
+  double gain = (F - Fc) / pred;
+  return isfinite(Fc) && isfinite(gain) && pred > 0.0 && gain > 1e-3;
+}
+
+/* Nielsen's damping update (same source, Eq. 2.21 and Algorithm 3.16):
+ * accepted: mu <- mu * max(1/3, 1 - (2 gain - 1)^3), nu <- 2;
+ * rejected: mu <- mu * nu, nu <- 2 nu. */
+void oracle_lm_damping(int accepted, double gain, double* lambda, double* nu) {
+  if (accepted) {
+    double t = 2.0 * gain - 1.0;
+    double f = 1.0 - t * t * t;
+    *lambda *= f > 1.0 / 3.0 ? f : 1.0 / 3.0;
+    *nu = 2.0;
+  } else {
+    *lambda *= *nu;
+    *nu *= 2.0;
+  }
+}
+
 int oracle_lm(const oracle_problem* pb, const oracle_opts* o, int max_iters, double* cams,
               double* pts, oracle_iter_log* log, uint8_t* alive_io) {
   int64_t C = pb->n_cams, P = pb->n_pts, N = pb->n_obs;
@@ -929,10 +956,14 @@ int oracle_lm(const oracle_problem* pb, const oracle_opts* o, int max_iters, dou
   double F = 0.0, rmse = 0.0;
   int it;
   for (it = 0; it < max_iters; ++it) {
-    int drop_now = o->extract_every > 0 && o->drop_residual_px > 0.0 && it > 0 &&
+    /* one-shot mode: validity, drop and peeling at the first iteration only,
+     * the active set frozen afterwards (the static pruning Sec. 4.2 contrasts
+     * with its per-iteration extraction) */
+    int once = o->extract_mode == 1;
+    int drop_now = !once && o->extract_every > 0 && o->drop_residual_px > 0.0 && it > 0 &&
                    it % o->extract_every == 0;
     int relin = state_changed || drop_now || it == 0;
-    if (relin) {
+    if (relin && (!once || it == 0)) {
       /* Sec. 4.2 step 1: re-evaluate validity with the current state */
       oracle_predicate(pb, o, cams, pts, geom, res);
       if (drop_now) /* reading: sticky residual drop of geometrically valid observations */
@@ -957,7 +988,7 @@ int oracle_lm(const oracle_problem* pb, const oracle_opts* o, int max_iters, dou
       oracle_apply_step(C, P, cams, pts, dc, dp, cams2, pts2);
       Fc = oracle_cost(pb, o, cams2, pts2, obs_mask, NULL);
       gain = (F - Fc) / pred;
-      if (isfinite(Fc) && isfinite(gain) && pred > 0.0 && gain > 1e-3) accepted = 1;
+      accepted = oracle_lm_accept(F, Fc, pred);
     }
     if (log) {
       oracle_iter_log* L = log + it;
@@ -978,17 +1009,12 @@ int oracle_lm(const oracle_problem* pb, const oracle_opts* o, int max_iters, dou
       L->n_pt_act = n_pt_act;
       L->n_obs_act = na;
     }
+    oracle_lm_damping(accepted, gain, &lambda, &nu);
     if (accepted) {
       memcpy(cams, cams2, sizeof(double) * 9 * (size_t)C);
       memcpy(pts, pts2, sizeof(double) * 3 * (size_t)P);
-      double t = 2.0 * gain - 1.0;
-      double f = 1.0 - t * t * t;
-      lambda *= f > 1.0 / 3.0 ? f : 1.0 / 3.0;
-      nu = 2.0;
       state_changed = 1;
     } else {
-      lambda *= nu;
-      nu *= 2.0;
       state_changed = 0;
     }
   }

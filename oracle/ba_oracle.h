@@ -50,6 +50,8 @@ typedef struct {
   double pcg_rel_tol;
   int pcg_max_iters;
   int solver;                   /* 0: dense Cholesky of the Schur system; 1: block-Jacobi PCG */
+  int extract_mode;             /* 0: extraction at every iteration whose state changed (Sec. 4.2);
+                                   1: one-shot, at the first iteration only, active set frozen */
 } oracle_opts;
 
 typedef struct {
@@ -119,6 +121,14 @@ int oracle_solve_step(const oracle_problem* pb, const oracle_opts* o, const doub
 /* x <- x (+) dx: rotation by left composition, the rest additive. */
 void oracle_apply_step(int64_t n_cams, int64_t n_pts, const double* cams, const double* pts,
                        const double* dc, const double* dp, double* cams_out, double* pts_out);
+
+/* Accept test of one LM step: 1 when gain = (F - Fc) / pred > 1e-3 with Fc
+ * finite and pred > 0 (Sec. 3.3; Nielsen's rule). */
+int oracle_lm_accept(double F, double Fc, double pred);
+
+/* Damping update after a step: accepted, lambda *= max(1/3, 1 - (2 gain - 1)^3)
+ * and nu = 2; rejected, lambda *= nu and nu *= 2. */
+void oracle_lm_damping(int accepted, double gain, double* lambda, double* nu);
 
 /* Full LM loop.  cams/pts are updated in place; log has max_iters entries (or NULL);
  * alive [N] is the sticky residual-drop state (NULL = internal, all alive).

@@ -21,6 +21,7 @@ BA_OK, BA_ERR_INVALID_ARG, BA_ERR_CUDA, BA_ERR_OOM = 0, 1, 2, 3
 BA_ERR_NOT_CONVERGED, BA_ERR_NONFINITE, BA_ERR_STATE, BA_ERR_TIMEOUT = 4, 5, 6, 7
 BA_FP64, BA_FP32 = 0, 1
 BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT, BA_SOLVER_DENSE = 0, 1, 2, 3
+BA_EXTRACT_DYNAMIC, BA_EXTRACT_ONCE = 0, 1
 
 # every symbol include/ba_b300.h declares
 EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
@@ -39,7 +40,7 @@ class _Options(ct.Structure):
                 ("drop_residual_px", ct.c_double), ("min_cam_obs", ct.c_int),
                 ("min_pt_obs", ct.c_int), ("lambda0", ct.c_double), ("pcg_rel_tol", ct.c_double),
                 ("pcg_max_iters", ct.c_int), ("fixed_cams", ct.POINTER(ct.c_int32)),
-                ("n_fixed", ct.c_int), ("solver", ct.c_int)]
+                ("n_fixed", ct.c_int), ("solver", ct.c_int), ("extract_mode", ct.c_int)]
 
 
 class _IterInfo(ct.Structure):
@@ -152,6 +153,7 @@ class Options:
     pcg_max_iters: int = 500
     fixed_cams: tuple = (0,)
     solver: int = BA_SOLVER_AUTO
+    extract_mode: int = 0  # BA_EXTRACT_DYNAMIC; 1 = BA_EXTRACT_ONCE (one-shot pruning)
 
 
 class _Arr:
@@ -368,14 +370,52 @@ def _c_options(o: Options):
     c = _Options(o.precision, o.img_w, o.img_h, o.cx, o.cy, o.huber_delta, o.depth_weight,
                  o.invalid_depth_weight, o.min_depth, o.extract_every, o.drop_residual_px,
                  o.min_cam_obs, o.min_pt_obs, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
-                 fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(fixed), o.solver)
+                 fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(fixed), o.solver, o.extract_mode)
     return c, fixed
+
+
+def _check_noalloc_args(cams, pts, obs_cam, obs_pt, obs_uv, depth, out, obs_mask):
+    """Types, layout and sizes of ba_eval_cost_noalloc's tensors (the C ABI takes
+    bare pointers and cannot check them).  Raises ValueError."""
+    import torch
+
+    spec = [("cams", cams, torch.float64), ("pts", pts, torch.float64),
+            ("obs_cam", obs_cam, torch.int32), ("obs_pt", obs_pt, torch.int32),
+            ("obs_uv", obs_uv, torch.float64), ("depth", depth, torch.float64),
+            ("out", out, torch.float64)]
+    if obs_mask is not None:
+        spec.append(("obs_mask", obs_mask, (torch.uint8, torch.bool)))
+    for name, t, dt in spec:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"eval_cost_noalloc: {name} must be a torch tensor")
+        ok = t.dtype in dt if isinstance(dt, tuple) else t.dtype == dt
+        if not ok:
+            raise ValueError(f"eval_cost_noalloc: {name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"eval_cost_noalloc: {name} must be contiguous")
+    if cams.numel() % 9 or pts.numel() % 3:
+        raise ValueError("eval_cost_noalloc: cams must hold [C][9] and pts [P][3] values")
+    n = obs_cam.numel()
+    if obs_pt.numel() != n or depth.numel() != n or obs_uv.numel() != 2 * n or (
+            obs_mask is not None and obs_mask.numel() != n):
+        raise ValueError("eval_cost_noalloc: obs_pt, depth, obs_mask need N entries and obs_uv 2N "
+                         f"(N = {n})")
+    if out.numel() < 3:
+        raise ValueError("eval_cost_noalloc: out needs 3 entries")
+    devs = {t.device for _, t, _ in spec}
+    if len(devs) != 1 or next(iter(devs)).type != "cuda":
+        raise ValueError("eval_cost_noalloc: every tensor must be on one CUDA device")
+    if next(iter(devs)).index != torch.cuda.current_device():
+        raise ValueError("eval_cost_noalloc: the tensors must be on the current CUDA device")
 
 
 def eval_cost_noalloc(cams, pts, obs_cam, obs_pt, obs_uv, depth, out, obs_mask=None,
                       options: Options | None = None, stream=None):
-    """ba_eval_cost_noalloc: every argument a CUDA tensor of the current device
-    (out: float64 with 3 entries).  Enqueued on the stream; nothing is allocated."""
+    """ba_eval_cost_noalloc: every argument a contiguous CUDA tensor of the current
+    device (cams/pts/obs_uv/depth/out float64, indices int32, obs_mask uint8 or bool,
+    out with 3 entries); wrong types, layouts or sizes raise ValueError.  Enqueued
+    on the stream; nothing is allocated."""
+    _check_noalloc_args(cams, pts, obs_cam, obs_pt, obs_uv, depth, out, obs_mask)
     L = lib()
     copt, _fixed = _c_options(options or Options())
     n_cams = cams.numel() // 9

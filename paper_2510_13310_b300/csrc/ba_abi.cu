@@ -293,7 +293,8 @@ bool finite_opts(const ba_options* o) {
          std::isfinite(o->min_depth) && std::isfinite(o->lambda0) && o->lambda0 > 0 &&
          std::isfinite(o->pcg_rel_tol) && o->pcg_rel_tol > 0 && o->pcg_max_iters > 0 &&
          o->img_w > 0 && o->img_h > 0 && o->min_cam_obs >= 0 && o->min_pt_obs >= 0 &&
-         o->extract_every >= 0 && (o->precision == BA_FP64 || o->precision == BA_FP32);
+         o->extract_every >= 0 && (o->precision == BA_FP64 || o->precision == BA_FP32) &&
+         (o->extract_mode == BA_EXTRACT_DYNAMIC || o->extract_mode == BA_EXTRACT_ONCE);
 }
 
 ba_status sync(ba_problem* pb) {
@@ -646,7 +647,8 @@ ba_status candidate_t(ba_problem* pb) {
 }
 
 ba_status ensure_extracted(ba_problem* pb) {
-  if (!pb->extracted || pb->state_changed) {
+  const bool once = pb->opt.extract_mode == BA_EXTRACT_ONCE;
+  if (!pb->extracted || (pb->state_changed && !once)) {
     ST(run_extraction(pb, false, nullptr));
     pb->state_changed = false;
   }
@@ -704,10 +706,14 @@ struct NvtxScope {
 ba_status lm_step(ba_problem* pb, ba_iter_info* info) {
   const ba_options& o = pb->opt;
   int k = pb->iter;
-  bool drop = o.extract_every > 0 && o.drop_residual_px > 0 && k > 0 && k % o.extract_every == 0;
+  // one-shot mode: the active set of the first extraction stays for the whole run
+  const bool once = o.extract_mode == BA_EXTRACT_ONCE;
+  bool drop = !once && o.extract_every > 0 && o.drop_residual_px > 0 && k > 0 && k % o.extract_every == 0;
   CU(cudaEventRecord(pb->ev[0], pb->stream));
   NvtxScope r_extract("ba: extract");
-  if (pb->extracted && pb->state_changed && pb->same_validity && !drop) {
+  if (once && pb->extracted) {
+    pb->state_changed = false;
+  } else if (pb->extracted && pb->state_changed && pb->same_validity && !drop) {
     // Sec. 4.2: the active set is a function of the validity bits (and the sticky
     // drops, unchanged outside drop iterations); same bits, same active set
     pb->state_changed = false;
@@ -1399,6 +1405,7 @@ void ba_default_options(ba_options* o) {
   o->fixed_cams = kGauge;
   o->n_fixed = 1;
   o->solver = BA_SOLVER_AUTO;
+  o->extract_mode = BA_EXTRACT_DYNAMIC;
 }
 
 ba_status ba_create(const ba_options* opts, void* stream, int64_t n_cams, const double* cams,

@@ -1,12 +1,11 @@
 // noalloc.cu -- ba_eval_cost_noalloc: the FP64 robust cost of a state without any
 // device allocation.
 //
-// Some callers cannot call cudaMalloc: code recorded into a CUDA graph while a
-// stream is being captured (allocation is not a capturable operation), host code
-// running under a framework that owns all device memory and forbids raw
-// allocations (custom calls of graph-compiling frameworks, fixed-budget
-// real-time pipelines), or code that must not take the implicit device-wide
-// synchronisation an allocation can cause.  This entry point evaluates
+// Some callers cannot call cudaMalloc: host code running under a framework that
+// owns all device memory and forbids raw allocations (its allocator must account
+// for every byte, or the budget is fixed when the process starts, as in embedded
+// and real-time pipelines), and latency-critical loops that must not take the
+// implicit device-wide synchronisation an allocation can cause.  This entry point evaluates
 // F = 1/2 sum rho(|r_k|^2) and the reprojection RMSE from caller-provided
 // device arrays, using as scratch only a file-scope device array of fixed
 // size that lives as long as the library is loaded.
@@ -58,7 +57,8 @@ __global__ void k_na_eval(int C, int P, int N, const double* __restrict__ rec,
                           ModelParams mp, double* __restrict__ partials) {
   __shared__ double red[32];
   double acc_cost = 0.0, acc_e2 = 0.0, acc_n = 0.0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
     if (mask && !mask[k]) continue;
     int c = obs_cam[k], p = obs_pt[k];
     if (c < 0 || c >= C || p < 0 || p >= P) continue;
@@ -109,7 +109,9 @@ void fail_msg(const char* fmt, const char* arg) {
 }
 
 // True when the pointer can be read by kernels on the current device: device or
-// managed memory of this device, or page-locked host memory mapped into it.
+// managed memory of this device, or page-locked host memory mapped into it whose
+// device alias is the pointer itself (unified addressing); the kernels are given
+// the pointer as passed, so a host pointer with a different device alias is refused.
 bool device_accessible(const void* p, int dev) {
   if (!p) return true;
   cudaPointerAttributes at{};
@@ -119,12 +121,13 @@ bool device_accessible(const void* p, int dev) {
   }
   if (at.type == cudaMemoryTypeDevice) return at.device == dev;
   if (at.type == cudaMemoryTypeManaged) return true;
-  if (at.type == cudaMemoryTypeHost) return at.devicePointer != nullptr;
+  if (at.type == cudaMemoryTypeHost) return at.devicePointer == p;
   return false;
 }
 
 // Device address of the scratch array on the current device, looked up once per
-// device (the first call on a device must not happen during stream capture).
+// device and kept for the life of the process (the first call on a device must
+// not happen during stream capture; a device reset in between is not supported).
 ba_status scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

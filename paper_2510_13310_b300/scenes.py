@@ -172,12 +172,21 @@ def project_points(R: np.ndarray, t: np.ndarray, f: np.ndarray, k1: np.ndarray,
 
 def make_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = True,
                outliers: bool = True, depth_priors: bool = True,
-               scale: float | None = None, shuffle: bool = True) -> Scene:
+               scale: float | None = None, shuffle: bool = True,
+               frustum_exit_frac: float = 0.0) -> Scene:
     """Generate a seeded scene.
 
     `noise=False` removes pixel and depth noise, `outliers=False` removes the
     outliers, `depth_priors=False` clears every prior.  `scale` shrinks the
-    camera and point counts (for reduced-size parity cases)."""
+    camera and point counts (for reduced-size parity cases).
+
+    `frustum_exit_frac` injects frustum exits: that fraction of the points with
+    horizontal radius >= 0.5 starts lifted to height 1.35 (+ U(0, 0.1)) above the
+    camera plane, which puts it above the image of its nearer cameras (camera-frame
+    depth below ~2.8) and inside the image of its farther ones, while its true
+    position projects inside every image.  Those observations are invalid at the
+    start and valid at the solution.  The draw comes after every other draw, so
+    the rest of the scene is the same as without it."""
     if isinstance(spec, str):
         spec = SPECS[spec]
     if scale is not None:
@@ -246,6 +255,12 @@ def make_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = 
 
     if shuffle:
         perm = rng.permutation(N)
+    if frustum_exit_frac > 0.0:
+        wide = np.flatnonzero(np.hypot(pts_gt[:, 0], pts_gt[:, 1]) >= 0.5)
+        lift = wide[rng.random(wide.shape[0]) < frustum_exit_frac]
+        pts0[lift, 2] = 1.35 + 0.1 * rng.random(lift.shape[0])
+
+    if shuffle:
         obs_cam, obs_pt, uv, depth, is_out = obs_cam[perm], obs_pt[perm], uv[perm], depth[perm], is_out[perm]
 
     return Scene(spec, np.ascontiguousarray(cams_gt), pts_gt, np.ascontiguousarray(cams0),

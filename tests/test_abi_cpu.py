@@ -56,3 +56,40 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(ba, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         ba.lib()
+
+
+def _noalloc_args(torch, n=5, C=3, P=4):
+    return dict(cams=torch.zeros(C, 9, dtype=torch.float64), pts=torch.zeros(P, 3, dtype=torch.float64),
+                obs_cam=torch.zeros(n, dtype=torch.int32), obs_pt=torch.zeros(n, dtype=torch.int32),
+                obs_uv=torch.zeros(n, 2, dtype=torch.float64), depth=torch.zeros(n, dtype=torch.float64),
+                out=torch.zeros(3, dtype=torch.float64), obs_mask=torch.ones(n, dtype=torch.uint8))
+
+
+@pytest.mark.parametrize("change, match", [
+    (lambda a, t: a.update(cams=a["cams"].float()), "cams must be"),
+    (lambda a, t: a.update(pts=a["pts"].to(t.float32)), "pts must be"),
+    (lambda a, t: a.update(obs_cam=a["obs_cam"].long()), "obs_cam must be"),
+    (lambda a, t: a.update(obs_pt=a["obs_pt"].long()), "obs_pt must be"),
+    (lambda a, t: a.update(obs_uv=a["obs_uv"].float()), "obs_uv must be"),
+    (lambda a, t: a.update(depth=a["depth"].float()), "depth must be"),
+    (lambda a, t: a.update(out=a["out"].float()), "out must be"),
+    (lambda a, t: a.update(obs_mask=a["obs_mask"].int()), "obs_mask must be"),
+    (lambda a, t: a.update(obs_uv=t.zeros(2, 5, dtype=t.float64).T), "obs_uv must be contiguous"),
+    (lambda a, t: a.update(cams=t.zeros(3, 8, dtype=t.float64)), r"cams must hold"),
+    (lambda a, t: a.update(pts=t.zeros(4, 2, dtype=t.float64)), r"cams must hold"),
+    (lambda a, t: a.update(obs_pt=t.zeros(4, dtype=t.int32)), "need N entries"),
+    (lambda a, t: a.update(depth=t.zeros(6, dtype=t.float64)), "need N entries"),
+    (lambda a, t: a.update(obs_uv=t.zeros(4, 2, dtype=t.float64)), "need N entries"),
+    (lambda a, t: a.update(obs_mask=t.ones(4, dtype=t.uint8)), "need N entries"),
+    (lambda a, t: a.update(out=t.zeros(2, dtype=t.float64)), "out needs 3"),
+    (lambda a, t: None, "one CUDA device"),  # well-formed CPU tensors: not device memory
+])
+def test_noalloc_binding_rejects_bad_tensors(change, match):
+    """The C ABI takes bare pointers; the binding refuses what would make its kernels
+    read or write out of bounds.  Every check but the device one runs on the CPU."""
+    torch = pytest.importorskip("torch")
+    a = _noalloc_args(torch)
+    change(a, torch)
+    with pytest.raises(ValueError, match=match):
+        ba.eval_cost_noalloc(a["cams"], a["pts"], a["obs_cam"], a["obs_pt"], a["obs_uv"],
+                             a["depth"], a["out"], obs_mask=a["obs_mask"])

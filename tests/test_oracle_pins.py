@@ -481,3 +481,131 @@ def test_adjoint_matches_finite_differences_of_reconverged_oracle():
         assert abs(fd - dd[k]) <= 2e-3 * dscale, (k, fd, dd[k])
     # observations without a prior have no depth gradient
     assert np.all(dd[~(sc.depth > 0)] == 0.0)
+
+
+# --------------------------------------------------------------------------
+# LM control (Sec. 3.3): accept rule, damping schedule, reported RMSE
+# --------------------------------------------------------------------------
+# The paper names Marquardt damping but not its control; the reading is
+# Nielsen's rule as given by Madsen, Nielsen & Tingleff, "Methods for non-linear
+# least squares problems" (2004), Eq. 2.21 / Algorithm 3.16.  The expected values
+# below were worked by hand from that rule and are written out as literals.
+
+@pytest.mark.parametrize("lam, nu, accepted, gain, lam_new, nu_new", [
+    (1e-4, 2.0, True, 0.5, 1e-4, 2.0),              # t = 0: factor 1
+    (1e-4, 2.0, True, 0.75, 8.75e-5, 2.0),          # t = 0.5: 1 - 0.125
+    (1e-4, 2.0, True, 0.25, 1.125e-4, 2.0),         # t = -0.5: 1 + 0.125
+    (1e-4, 2.0, True, 0.9, 4.88e-5, 2.0),           # t = 0.8: 1 - 0.512
+    (1e-4, 2.0, True, 0.002, 1.988047936e-4, 2.0),  # t = -0.996: 1 + 0.988047936
+    (1e-4, 2.0, True, 1.0, 1e-4 / 3, 2.0),          # t = 1: 0, clamped to 1/3
+    (3e-2, 2.0, True, 2.0, 1e-2, 2.0),              # t = 3: -26, clamped to 1/3
+    (1e-4, 16.0, True, 0.5, 1e-4, 2.0),             # an accept resets nu
+    (1e-4, 2.0, False, -5.0, 2e-4, 4.0),            # reject: lambda * nu, nu doubles
+    (2e-4, 4.0, False, 1e-4, 8e-4, 8.0),
+    (8e-4, 8.0, False, float("nan"), 6.4e-3, 16.0),
+])
+def test_damping_update_hand_worked(lam, nu, accepted, gain, lam_new, nu_new):
+    got_l, got_n = oracle.lm_damping(accepted, gain, lam, nu)
+    assert got_l == pytest.approx(lam_new, rel=1e-15)
+    assert got_n == nu_new
+
+
+@pytest.mark.parametrize("F, Fc, pred, expect", [
+    (10.0, 9.0, 1.0, True),          # gain 1
+    (10.0, 9.999, 1.0, False),       # gain 1e-3 exactly: not above the threshold
+    (10.0, 9.9989, 1.0, True),       # gain 1.1e-3
+    (10.0, 10.5, 1.0, False),        # cost went up
+    (10.0, 9.0, 0.0, False),         # no predicted decrease
+    (10.0, 9.0, -1.0, False),        # negative predicted decrease (gain -1 anyway)
+    (10.0, 11.0, -1.0, False),       # both negative: gain +1, still rejected
+    (10.0, float("nan"), 1.0, False),
+    (10.0, float("inf"), 1.0, False),
+])
+def test_accept_rule_hand_worked(F, Fc, pred, expect):
+    assert oracle.lm_accept(F, Fc, pred) == expect
+
+
+def test_lm_trace_reject_chains_and_resets():
+    """A start 30 degrees off with lambda0 = 1e-12 forces a chain of rejected steps.
+    Fixed in advance: after an accepted step (or at the start) consecutive rejects
+    multiply lambda by exactly 2, 4, 8, ...; an accepted step changes lambda by a
+    factor in [1/3, 2), below 1 exactly when the gain exceeds 1/2, and exactly 1/3
+    when the gain is at least (1 + (2/3)^(1/3)) / 2 = 0.93680; the accept decision
+    is gain > 1e-3 with the gain recomputed from the logged costs."""
+    spec = dataclasses.replace(scenes.SPECS["small"], n_cams=5, n_pts=40, track_min=3,
+                               track_max=3, track_mean=3, seed=7, rot_perturb_deg=30.0)
+    sc = scenes.make_scene(spec)
+    ob = oracle.OracleBA.from_scene(sc, oracle.OracleOptions(lambda0=1e-12))
+    _, _, rows = ob.lm(sc.cams0, sc.pts0, 16)
+    acc = [r["accepted"] for r in rows]
+    assert sum(acc) >= 3 and len(acc) - sum(acc) >= 5, acc
+    assert rows[0]["lam"] == 1e-12
+    run = 0  # rejects since the last accept
+    for prev, nxt in zip(rows, rows[1:]):
+        gain = (prev["cost"] - prev["cand_cost"]) / prev["pred_decrease"]
+        assert prev["accepted"] == (np.isfinite(gain) and prev["pred_decrease"] > 0 and gain > 1e-3)
+        ratio = nxt["lam"] / prev["lam"]
+        if prev["accepted"]:
+            run = 0
+            assert 1.0 / 3.0 * (1 - 1e-15) <= ratio < 2.0
+            assert (ratio < 1.0) == (gain > 0.5)
+            if gain >= 0.9368:
+                assert ratio == pytest.approx(1.0 / 3.0, rel=1e-15)
+        else:
+            run += 1
+            assert ratio == 2.0 ** run, (run, ratio)
+        # a rejected step leaves the state, the active set and so the cost unchanged
+        if not prev["accepted"]:
+            assert nxt["cost"] == prev["cost"]
+            assert nxt["n_obs_act"] == prev["n_obs_act"]
+
+
+def test_rmse_and_cost_at_ground_truth_with_known_offsets():
+    """At the true state with exact depth priors, every residual is a pixel offset
+    that we place: RMSE = sqrt(mean |offset|^2) over the active observations and
+    F = 1/2 sum rho(|offset|^2) with the Huber closed form, whatever the camera model."""
+    spec = dataclasses.replace(scenes.SPECS["small"], n_cams=6, n_pts=60, track_min=4,
+                               track_max=4, track_mean=4, seed=5)
+    sc = scenes.make_scene(spec, noise=False, outliers=False)
+    rng = np.random.default_rng(17)
+    mags = rng.choice([0.3, 0.6, 0.9, 2.0, 5.0], size=sc.n_obs)
+    ang = rng.uniform(0, 2 * math.pi, sc.n_obs)
+    off = mags[:, None] * np.stack([np.cos(ang), np.sin(ang)], 1)
+    mask = (rng.random(sc.n_obs) < 0.7).astype(np.uint8)
+    for delta in (1.0, 0.0):
+        ob = oracle.OracleBA(sc.cams0.shape[0], sc.pts0.shape[0], sc.obs_cam, sc.obs_pt,
+                             sc.obs_uv + off, sc.depth, sc.fixed_cams,
+                             oracle.OracleOptions(huber_delta=delta))
+        for m in (None, mask):
+            sel = np.ones(sc.n_obs, bool) if m is None else m.astype(bool)
+            F, rmse = ob.cost(sc.cams_gt, sc.pts_gt, m)
+            s = mags[sel]
+            assert rmse == pytest.approx(math.sqrt(np.mean(s ** 2)), rel=1e-12)
+            rho = np.where(s <= delta, s ** 2, 2 * delta * s - delta ** 2) if delta > 0 else s ** 2
+            assert F == pytest.approx(0.5 * rho.sum(), rel=1e-11)
+
+
+# --------------------------------------------------------------------------
+# one-shot pruning vs dynamic extraction (Sec. 4.2)
+# --------------------------------------------------------------------------
+
+def test_one_shot_freezes_the_first_active_set_and_dynamic_readmits():
+    """Injected frustum exits: points that start above the image of their nearer
+    cameras.  One-shot pruning keeps the first iteration's active set for the whole
+    run; per-iteration extraction (Sec. 4.2 step 3) re-admits the observations once
+    the points come back into view, and ends with the smaller point error."""
+    sc = scenes.make_scene("small", frustum_exit_frac=0.3)
+    out = {}
+    for mode in (0, 1):
+        ob = oracle.OracleBA.from_scene(sc, oracle.OracleOptions(extract_mode=mode))
+        g0, _ = ob.predicate(sc.cams0, sc.pts0)
+        c, p, rows = ob.lm(sc.cams0, sc.pts0, 12)
+        acts = [r["n_obs_act"] for r in rows]
+        assert acts[0] == int(g0.sum()) < sc.n_obs  # the injected exits are invalid at the start
+        out[mode] = (acts, np.linalg.norm(p - sc.pts_gt, axis=1).mean())
+    acts_once, err_once = out[1]
+    acts_dyn, err_dyn = out[0]
+    assert len(set(acts_once)) == 1
+    gt_valid, _ = oracle.OracleBA.from_scene(sc).predicate(sc.cams_gt, sc.pts_gt)
+    assert acts_dyn[-1] > acts_dyn[0] and acts_dyn[-1] >= int(gt_valid.sum()) - 10
+    assert err_dyn < err_once

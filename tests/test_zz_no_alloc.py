@@ -1,7 +1,8 @@
 """ba_eval_cost_noalloc: the FP64 cost of a state for callers that cannot allocate
-device memory (code captured into a CUDA graph, frameworks that own every
-device allocation).  It must agree with ba_eval_cost, the problem-based entry
-point, on the same state and active set, call after call.
+device memory (code under a framework that owns every device allocation, or with
+a memory budget fixed at start-up).  It must agree with ba_eval_cost, the
+problem-based entry point, and with the FP64 CPU oracle on the same state and
+active set, call after call.
 
 Kept in a file that pytest collects last, so a run that stops at the first
 failure has already run every other test."""
@@ -10,6 +11,7 @@ import ctypes as ct
 import numpy as np
 import pytest
 
+import oracle
 from paper_2510_13310_b300 import ba, scenes
 
 pytestmark = pytest.mark.gpu
@@ -33,14 +35,19 @@ def test_noalloc_cost_matches_problem_cost_on_two_calls():
            _dev(sc.obs_uv, torch.float64), _dev(sc.depth, torch.float64)]
     m = _dev(mask, torch.uint8)
     out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ob = oracle.OracleBA.from_scene(sc, oracle.OracleOptions(invalid_depth_weight=1e-3))
     for cams, pts in ((sc.cams0, sc.pts0), (sc.cams_gt, sc.pts_gt)):
         F_ref, rmse_ref = prob.eval_cost(cams, pts)
+        F_or, rmse_or = ob.cost(cams, pts, mask)
         ba.eval_cost_noalloc(_dev(cams, torch.float64), _dev(pts, torch.float64), *obs, out,
                              obs_mask=m, options=opts)
         torch.cuda.synchronize()
         F, rmse, n = out.tolist()
         assert F == pytest.approx(F_ref, rel=1e-12)
         assert rmse == pytest.approx(rmse_ref, rel=1e-12)
+        # FP64 on both sides, summed in different orders
+        assert F == pytest.approx(F_or, rel=1e-12)
+        assert rmse == pytest.approx(rmse_or, rel=1e-12)
         assert n == int(mask.sum())
 
 
