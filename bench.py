@@ -3,7 +3,8 @@
 Workload: 200 cameras, 100k points, ~1M observations (track length 3-20,
 truncated geometric, mean 10), FP32 hot path with the cost in double-float
 arithmetic (FP32 pairs; 1e-12 relative to FP64), the gain ratio in FP64 and the
-PCG scalars in FP64 (implicit system) or FP32 (explicit system); 2% outliers, depth priors on 50% of observations.  A step is one
+PCG dots in FP64 (implicit system) or compensated double-float sums of FP64-level
+accuracy (explicit system); 2% outliers, depth priors on 50% of observations.  A step is one
 full LM iteration (extraction, residuals/Jacobians, normal equations and
 Schur terms, PCG + back-substitution, candidate evaluation and accept/reject).
 
@@ -39,7 +40,7 @@ METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 
 # DRAM bytes (read + write) of one launch of each roofline kernel, from ncu
 # captures of this workload (profiles/top_kernels_traffic_medium_1M_obs.md); None
 # once the kernel has changed since the counters were taken.
-NCU_TRAFFIC = {"k_spcg": 13138944 + 66560, "k_pcg": None, "k_form_S_runs": 303936768 + 7791360}
+NCU_TRAFFIC = {"k_spcg": None, "k_pcg": None, "k_form_S_runs": 303936768 + 7791360}
 WORKLOAD = "medium"
 LM_ITERS = 30
 E2E_RUNS = 3
@@ -479,7 +480,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": _workload_name(scene) + ", FP32 with double-float cost and FP64 gain ratio",
+            "config": {"workload": _workload_name(scene) + ", FP32 with double-float cost, FP64-accurate PCG "
+                                                            "dots (double-float) and FP64 gain ratio",
                        "n_cams": scene.spec.n_cams, "n_pts": P, "n_obs": N,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)"},

@@ -1,4 +1,5 @@
-"""ctypes wrapper of the FP64 CPU oracle (oracle/ba_oracle.c).
+"""ctypes wrapper of the FP64 CPU oracles (oracle/ba_oracle.c: bundle adjustment;
+oracle/gp_oracle.c: depth-constrained global positioning).
 
 TEST INFRASTRUCTURE ONLY.  The oracle is what the CUDA path is checked against;
 only the tests, the smoke check and the benchmark's CPU-baseline leg use it.
@@ -36,6 +37,16 @@ class Opts(ct.Structure):
                 ("min_cam_obs", ct.c_int), ("min_pt_obs", ct.c_int), ("lambda0", ct.c_double),
                 ("pcg_rel_tol", ct.c_double), ("pcg_max_iters", ct.c_int), ("solver", ct.c_int),
                 ("extract_mode", ct.c_int)]
+
+
+class GPProblem(ct.Structure):
+    _fields_ = [("n_cams", c_i64), ("n_pts", c_i64), ("n_obs", c_i64),
+                ("obs_cam", P_i32), ("obs_pt", P_i32), ("rays", P_f64),
+                ("depth", P_f64), ("fixed", P_u8)]
+
+
+class GPOpts(ct.Structure):
+    _fields_ = [("huber_delta", ct.c_double), ("lambda0", ct.c_double)]
 
 
 class IterLog(ct.Structure):
@@ -83,6 +94,19 @@ def lib():
         L.oracle_lm_accept.restype = ct.c_int
         L.oracle_lm_damping.argtypes = [ct.c_int, ct.c_double, ct.POINTER(ct.c_double),
                                         ct.POINTER(ct.c_double)]
+        GP = ct.POINTER(GPProblem)
+        GO = ct.POINTER(GPOpts)
+        L.oracle_gp_residual.argtypes = [P_f64, P_f64, P_f64, ct.c_double, P_f64, P_f64, P_f64, P_f64]
+        L.oracle_gp_free_set.argtypes = [GP, P_i32]
+        L.oracle_gp_free_set.restype = c_i64
+        L.oracle_gp_cost.argtypes = [GP, GO, P_f64, P_f64, P_f64, P_f64]
+        L.oracle_gp_cost.restype = ct.c_double
+        L.oracle_gp_normal_equations.argtypes = [GP, GO, P_f64, P_f64, P_f64] + [P_f64] * 9
+        L.oracle_gp_solve_step.argtypes = [GP, GO, P_f64, P_f64, P_f64, ct.c_double, P_f64, P_f64,
+                                           P_f64, P_f64]
+        L.oracle_gp_solve_step.restype = ct.c_int
+        L.oracle_gp_lm.argtypes = [GP, GO, ct.c_int, P_f64, P_f64, P_f64, ct.POINTER(IterLog)]
+        L.oracle_gp_lm.restype = ct.c_int
         L.oracle_set_threads.argtypes = [ct.c_int]
         L.oracle_get_threads.restype = ct.c_int
         _LIB = L
@@ -255,6 +279,92 @@ class OracleBA:
         if st != 0:
             raise RuntimeError("oracle backward: factorisation failed")
         return duv, dd
+
+
+@dataclasses.dataclass
+class OracleGPOptions:
+    huber_delta: float = 0.1
+    lambda0: float = 1e-4
+
+    def to_c(self) -> GPOpts:
+        return GPOpts(**dataclasses.asdict(self))
+
+
+class OracleGP:
+    """Depth-constrained global positioning (Sec. 3.1, 4.1) of one problem, host arrays
+    in input order; scales are full-length [N] (pinned entries are ignored)."""
+
+    def __init__(self, n_cams, n_pts, obs_cam, obs_pt, rays, depth, fixed_cams=(0,),
+                 opts: OracleGPOptions | None = None):
+        self.L = lib()
+        self.n_cams, self.n_pts = int(n_cams), int(n_pts)
+        self.obs_cam = np.ascontiguousarray(obs_cam, dtype=np.int32)
+        self.obs_pt = np.ascontiguousarray(obs_pt, dtype=np.int32)
+        self.rays = _f64(rays).reshape(-1, 3)
+        self.depth = _f64(depth)
+        self.fixed = np.zeros(self.n_cams, dtype=np.uint8)
+        self.fixed[np.asarray(fixed_cams, dtype=np.int64)] = 1
+        self.n_obs = int(self.obs_cam.shape[0])
+        self.opts = opts or OracleGPOptions()
+        self._pb = GPProblem(self.n_cams, self.n_pts, self.n_obs, _p(self.obs_cam, P_i32),
+                             _p(self.obs_pt, P_i32), _p(self.rays, P_f64), _p(self.depth, P_f64),
+                             _p(self.fixed, P_u8))
+
+    @classmethod
+    def from_scene(cls, sc, opts: OracleGPOptions | None = None):
+        return cls(sc.centres0.shape[0], sc.pts0.shape[0], sc.obs_cam, sc.obs_pt, sc.rays, sc.depth,
+                   sc.fixed_cams, opts)
+
+    def _o(self):
+        return ct.byref(self.opts.to_c())
+
+    def free_set(self):
+        fr = np.zeros(self.n_obs, np.int32)
+        n = self.L.oracle_gp_free_set(ct.byref(self._pb), _p(fr, P_i32))
+        return fr, int(n)
+
+    def cost(self, centres, pts, scales):
+        rms = ct.c_double(0)
+        F = self.L.oracle_gp_cost(ct.byref(self._pb), self._o(), _p(_f64(centres), P_f64),
+                                  _p(_f64(pts), P_f64), _p(_f64(scales), P_f64), ct.byref(rms))
+        return F, rms.value
+
+    def normal_equations(self, centres, pts, scales):
+        C, P, N = self.n_cams, self.n_pts, self.n_obs
+        out = dict(U=np.zeros((C, 3, 3)), V=np.zeros((P, 3, 3)), W=np.zeros((N, 3, 3)),
+                   Hts=np.zeros((N, 3)), HXs=np.zeros((N, 3)), Q=np.zeros(N), gt=np.zeros((C, 3)),
+                   gX=np.zeros((P, 3)), gs=np.zeros(N))
+        self.L.oracle_gp_normal_equations(ct.byref(self._pb), self._o(), _p(_f64(centres), P_f64),
+                                          _p(_f64(pts), P_f64), _p(_f64(scales), P_f64),
+                                          *[_p(out[k], P_f64) for k in ("U", "V", "W", "Hts", "HXs", "Q",
+                                                                        "gt", "gX", "gs")])
+        return out
+
+    def solve_step(self, centres, pts, scales, lam):
+        dt = np.zeros((self.n_cams, 3)); dX = np.zeros((self.n_pts, 3)); ds = np.zeros(self.n_obs)
+        pred = ct.c_double(0)
+        st = self.L.oracle_gp_solve_step(ct.byref(self._pb), self._o(), _p(_f64(centres), P_f64),
+                                         _p(_f64(pts), P_f64), _p(_f64(scales), P_f64), float(lam),
+                                         _p(dt, P_f64), _p(dX, P_f64), _p(ds, P_f64), ct.byref(pred))
+        return dict(status=st, dt=dt, dX=dX, ds=ds, pred_decrease=pred.value)
+
+    def lm(self, centres0, pts0, scales0, max_iters):
+        t = _f64(centres0).copy(); X = _f64(pts0).copy(); s = _f64(scales0).copy()
+        log = (IterLog * max(1, max_iters))()
+        n = self.L.oracle_gp_lm(ct.byref(self._pb), self._o(), int(max_iters), _p(t, P_f64),
+                                _p(X, P_f64), _p(s, P_f64), log)
+        rows = [dict(cost=log[i].cost, rms=log[i].rmse_px, lam=log[i].lambda_, gain=log[i].gain,
+                     pred_decrease=log[i].pred_decrease, cand_cost=log[i].cand_cost,
+                     accepted=bool(log[i].accepted), n_cam_free=log[i].n_cam_act,
+                     n_pt_act=log[i].n_pt_act, n_free=log[i].n_obs_act) for i in range(n)]
+        return t, X, s, rows
+
+
+def gp_residual(t, X, v, s):
+    u = np.zeros(3); Jt = np.zeros(9); JX = np.zeros(9); Js = np.zeros(3)
+    lib().oracle_gp_residual(_p(_f64(t), P_f64), _p(_f64(X), P_f64), _p(_f64(v), P_f64), float(s),
+                             _p(u, P_f64), _p(Jt, P_f64), _p(JX, P_f64), _p(Js, P_f64))
+    return u, Jt.reshape(3, 3), JX.reshape(3, 3), Js
 
 
 def rotvec_to_matrix(w):

@@ -15,6 +15,7 @@
 #include <cuda/atomic>
 #include <type_traits>
 
+#include "df.cuh"
 #include "internal.h"
 #include "model.cuh"
 
@@ -457,54 +458,98 @@ size_t spcg_smem_bytes(int n, int rows, int rows_in_smem, int vecs_in_smem, int 
   return (b + 15) & ~size_t(15);
 }
 
-// Block-wide sums for the PCG scalars, in the working precision T: the sums are
-// of non-negative terms ((r, r), (r, z), (p, S^ p) with S^ and M^ positive
-// definite), so plain T accumulation keeps their relative error near
-// log2(n) ulps.  Every thread returns the same bits: a butterfly within each
-// warp, then every thread adds the warp sums in one fixed tree.  One barrier:
-// callers alternate between two `red` buffers, so a call never overwrites warp
-// sums that a thread may still be reading from the previous call.
-// Returns the OR of `flag` over the block.
-template <int K, typename T>
-__device__ __forceinline__ int block_allsum(T (&v)[K], T* red, int flag) {
+// PCG dot products and their scalars.  FP64 problems sum in FP64.  FP32 problems
+// keep FP64-level accuracy on the FP32 pipe (B300 issues FP64 at 1/64 of the FP32
+// rate, so 512 threads spending one FP64 instruction each would cost ~0.1 us):
+// every product a b enters as its exact TwoProduct pair, every addition is a
+// TwoSum whose exact error joins a low-order word, and alpha = (r, z) / (p, q),
+// beta = (r, z)' / (r, z) are double-float quotients rounded once to FP32.
+// The accumulated dot agrees with the exact dot of the FP32 vectors to ~2^-44
+// relative (the low word's own rounding); the sums are of products of FP32
+// vectors, so this is what FP64 dots of the same vectors deliver.
+template <typename T>
+struct DotT;
+template <>
+struct DotT<double> {
+  using type = double;
+};
+template <>
+struct DotT<float> {
+  using type = F2;  // unevaluated hi + lo, lo not renormalised until read
+};
+template <typename T>
+using Dot = typename DotT<T>::type;
+
+__device__ __forceinline__ void dot_zero(double& d) { d = 0.0; }
+__device__ __forceinline__ void dot_zero(F2& d) { d = F2{0.f, 0.f}; }
+__device__ __forceinline__ void dot_fma(double& d, double a, double b) { d = fma(a, b, d); }
+__device__ __forceinline__ void dot_fma(F2& d, float a, float b) {
+  const float pr = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -pr);  // a b = pr + pe exactly
+  const F2 t = two_sum(d.h, pr);
+  d.h = t.h;
+  d.l = __fadd_rn(d.l, __fadd_rn(t.l, pe));
+}
+// a + b with the same bits whichever operand comes first (TwoSum's error is exact)
+__device__ __forceinline__ double dot_add(double a, double b) { return a + b; }
+__device__ __forceinline__ F2 dot_add(F2 a, F2 b) {
+  const F2 t = two_sum(a.h, b.h);
+  return F2{t.h, __fadd_rn(__fadd_rn(a.l, b.l), t.l)};
+}
+__device__ __forceinline__ double dot_shfl(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ F2 dot_shfl(F2 v, int m) {
+  return F2{__shfl_xor_sync(0xffffffffu, v.h, m), __shfl_xor_sync(0xffffffffu, v.l, m)};
+}
+__device__ __forceinline__ double dot_norm(double v) { return v; }
+__device__ __forceinline__ F2 dot_norm(F2 v) { return fast_two_sum(v.h, v.l); }
+__device__ __forceinline__ double dot_value(double v) { return v; }
+__device__ __forceinline__ double dot_value(F2 v) { return f2_to_double(v); }
+// a / b in the working precision
+__device__ __forceinline__ double dot_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float dot_div(F2 a, F2 b) {
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const F2 r = f2_sub(a, f2_mul(F2{q1, 0.f}, b));  // a - q1 b, small
+  return __fadd_rn(q1, __fdiv_rn(r.h, b.h));
+}
+__device__ __forceinline__ bool dot_le(double a, double b) { return a <= b; }
+__device__ __forceinline__ bool dot_le(F2 a, F2 b) { return a.h < b.h || (a.h == b.h && a.l <= b.l); }
+__device__ __forceinline__ bool dot_nonzero(double a) { return a != 0.0; }
+__device__ __forceinline__ bool dot_nonzero(F2 a) { return a.h != 0.f; }  // normalised: lo = 0 when hi = 0
+__device__ __forceinline__ bool dot_pos_finite(double a) { return a > 0.0 && isfinite(a); }
+__device__ __forceinline__ bool dot_pos_finite(F2 a) { return a.h > 0.f && f2_finite(a); }
+
+// Block-wide sums of K dots: a butterfly within each warp, then every thread adds
+// the 16 warp sums in one fixed tree, so every thread holds the same bits (for
+// FP32 problems, the normalised double-float).  One barrier: callers alternate
+// between two `red` buffers (kSpcgRedStride doubles each).  Returns the OR of
+// `flag` over the block.
+template <int K, typename D>
+__device__ __forceinline__ int block_allsum_dot(D (&v)[K], void* red_raw, int flag) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = kSpcgThreads / 32;
   static_assert(NW == 16, "the fixed summation tree is written for 16 warps");
+  static_assert(K * NW * sizeof(D) <= kSpcgRedStride * sizeof(double), "reduction buffer");
+  D* red = reinterpret_cast<D*>(red_raw);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    T s = v[k];
+    D s = v[k];
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    for (int m = 16; m > 0; m >>= 1) s = dot_add(s, dot_shfl(s, m));
     if (lane == 0) red[NW * k + warp] = s;
   }
   const int any = __syncthreads_or(flag);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    T w[NW];
+    D w[NW];
 #pragma unroll
     for (int i = 0; i < NW; ++i) w[i] = red[NW * k + i];
 #pragma unroll
     for (int h = NW / 2; h > 0; h >>= 1)
 #pragma unroll
-      for (int i = 0; i < h; ++i) w[i] += w[i + h];
-    v[k] = w[0];
+      for (int i = 0; i < h; ++i) w[i] = dot_add(w[i], w[i + h]);
+    v[k] = dot_norm(w[0]);
   }
   return any;
-}
-
-// sum_i a_i b_i over one camera's 9 entries (FP32 products summed in FP32 on
-// the FP32 path, FP64 on the FP64 path)
-__device__ __forceinline__ float cam_dot(const float* a, const float* b) {
-  float s = 0.f;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) s = fmaf(a[i], b[i], s);
-  return s;
-}
-__device__ __forceinline__ double cam_dot(const double* a, const double* b) {
-  double s = 0.0;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) s = fma(a[i], b[i], s);
-  return s;
 }
 
 // z_c = M^_c r_c for one camera
@@ -599,7 +644,10 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   if (Mv) spcg_build_precond<T>(Cf, a.Dinv, a.dscale, Mv, tid, blockDim.x);
   __syncthreads();
   // r = b^, z = M^ r, p = z, x = 0; (r, z) and (r, r)
-  T d0[2] = {T(0), T(0)};
+  using D = Dot<T>;
+  D d0[2];
+  dot_zero(d0[0]);
+  dot_zero(d0[1]);
   for (int f = tid; f < Cf; f += blockDim.x) {
     const int e = 9 * f;
 #pragma unroll
@@ -609,18 +657,25 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     }
     spcg_precond(Mr + kMStride * f, rv + e, zv + e);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) pv[e + i] = zv[e + i];
-    d0[0] += cam_dot(rv + e, zv + e);
-    d0[1] += cam_dot(rv + e, rv + e);
+    for (int i = 0; i < 9; ++i) {
+      pv[e + i] = zv[e + i];
+      dot_fma(d0[0], rv[e + i], zv[e + i]);
+      dot_fma(d0[1], rv[e + i], rv[e + i]);
+    }
   }
   if constexpr (kRows) cp_async_wait_all();  // visible to the block after the barrier below
-  block_allsum<2>(d0, red + kSpcgRedStride * rb, 0);
+  block_allsum_dot<2>(d0, red + kSpcgRedStride * rb, 0);
   rb ^= 1;
-  // the scalars of the iteration in the working precision (T)
-  T rz = d0[0];
-  const double bnorm = sqrt((double)d0[1]);
-  const T stop_rr = (T)((a.tol * bnorm) * (a.tol * bnorm));
-  T rr_last = d0[1];
+  // the iteration's dots carried as D, the step lengths in the working precision
+  D rz = d0[0];
+  const double bnorm = sqrt(dot_value(d0[1]));
+  D stop_rr;
+  {
+    const double st = (a.tol * bnorm) * (a.tol * bnorm);
+    if constexpr (sizeof(T) == 4) stop_rr = f2_from_double(st);
+    else stop_rr = st;
+  }
+  D rr_last = d0[1];
   int it = 0;
   T alpha = T(0);
   bool x_pending = false;  // x still lacks the last alpha p
@@ -732,7 +787,8 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     // gather q from this block's copy, coalesced (thread t: entries t, t + 512, ...,
     // up to four in flight), and (p, q)
     int late = 0;
-    T d1[1] = {T(0)};
+    D d1[1];
+    dot_zero(d1[0]);
     const unsigned long long* mine = set + (size_t)(bid % kSpcgReplicas) * set_words;
     const uint64_t t0 = globaltimer_ns();
     for (int eb = tid; eb < n && !late; eb += 4 * blockDim.x) {
@@ -755,34 +811,34 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
         }
       }
       if (late) break;
-      T part = T(0);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = eb + u * blockDim.x;
         if (e < n) {
           const T q = spcg_unpack<T>(v[u]);
           qv[e] = q;
-          part = fma(pv[e], q, part);
+          dot_fma(d1[0], pv[e], q);
         }
       }
-      d1[0] += part;
     }
-    if (block_allsum<1>(d1, red + kSpcgRedStride * rb, late)) {
+    if (block_allsum_dot<1>(d1, red + kSpcgRedStride * rb, late)) {
       if (tid == 0) atomicOr(a.err, 1);
       break;
     }
     rb ^= 1;
-    const T pq = d1[0];
-    if (!(pq > T(0) && isfinite(pq))) {
+    const D pq = d1[0];
+    if (!dot_pos_finite(pq)) {
       if (bid == 0 && tid == 0) atomicOr(a.err, 2);
       break;
     }
-    alpha = rz / pq;
+    alpha = dot_div(rz, pq);
     // r -= alpha q, z = M^ r; (r, r) and (r, z) (x is updated with p below).  Two
     // threads per camera, adjacent lanes: rows 0-4 and rows 5-8; each takes the
     // other's rows of r by shuffle.  The loop's trip count is the same for every
     // thread, so whole warps meet at the shuffles.
-    T d2[2] = {T(0), T(0)};
+    D d2[2];
+    dot_zero(d2[0]);
+    dot_zero(d2[1]);
     for (int base = 0; base < 2 * Cf; base += blockDim.x) {
       const int t = base + tid, f = t >> 1, h = t & 1;
       const bool on = t < 2 * Cf;
@@ -826,20 +882,20 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
 #pragma unroll
             for (int j = 0; j < 9; ++j) acc += m[9 * ii + j] * rc[j];
             zv[e + i0 + ii] = acc;
-            d2[0] = fma(ro[ii], ro[ii], d2[0]);
-            d2[1] = fma(ro[ii], acc, d2[1]);
+            dot_fma(d2[0], ro[ii], ro[ii]);
+            dot_fma(d2[1], ro[ii], acc);
           }
         }
       }
     }
-    block_allsum<2>(d2, red + kSpcgRedStride * rb, 0);
+    block_allsum_dot<2>(d2, red + kSpcgRedStride * rb, 0);
     rb ^= 1;
     ++it;
     x_pending = true;
-    const T rr = d2[0], rz_new = d2[1];
+    const D rr = d2[0], rz_new = d2[1];
     rr_last = rr;
-    if (rr <= stop_rr) break;
-    const T beta = rz != T(0) ? rz_new / rz : T(0);
+    if (dot_le(rr, stop_rr)) break;
+    const T beta = dot_nonzero(rz) ? (T)dot_div(rz_new, rz) : T(0);
     rz = rz_new;
     if constexpr (kFused) {
       a_prev = alpha;
@@ -862,7 +918,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   if (bid == 0 && tid == 0) {
     a.sc->pcg_iters = it;
     a.sc->pcg_bnorm = bnorm;
-    a.sc->pcg_rel_res = bnorm > 0.0 ? sqrt((double)rr_last) / bnorm : 0.0;
+    a.sc->pcg_rel_res = bnorm > 0.0 ? sqrt(dot_value(rr_last)) / bnorm : 0.0;
   }
 }
 

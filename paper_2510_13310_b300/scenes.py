@@ -267,3 +267,73 @@ def make_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = 
                  np.ascontiguousarray(pts0), np.ascontiguousarray(obs_cam, dtype=np.int32),
                  np.ascontiguousarray(obs_pt, dtype=np.int32), np.ascontiguousarray(uv),
                  np.ascontiguousarray(depth), is_out, fixed)
+
+
+# ---------------------------------------------------------------------------
+# global positioning scenes (Sec. 3.1 / 4.1): rays from known rotations
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class GPScene:
+    spec: SceneSpec
+    centres_gt: np.ndarray  # [C,3] camera centres
+    pts_gt: np.ndarray      # [P,3]
+    centres0: np.ndarray    # [C,3] initial state
+    pts0: np.ndarray        # [P,3]
+    scales0: np.ndarray     # [N] initial scale of every observation (1 / initial range)
+    obs_cam: np.ndarray     # [N] int32
+    obs_pt: np.ndarray      # [N] int32
+    rays: np.ndarray        # [N,3] unit ray from the camera centre toward the feature (world frame)
+    depth: np.ndarray       # [N] metric range prior along the ray, 0 where none
+    is_outlier: np.ndarray  # [N] bool
+    fixed_cams: np.ndarray  # [F] int32
+
+    @property
+    def n_obs(self) -> int:
+        return int(self.obs_cam.shape[0])
+
+
+def make_gp_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = True,
+                  outliers: bool = True, depth_priors: bool = True,
+                  scale: float | None = None) -> GPScene:
+    """A global-positioning scene on the same geometry and tracks as make_scene:
+    the rays are the true camera-to-point directions (rotations are known in GP),
+    perturbed by an angular noise of pixel_sigma / focal radians per axis and
+    renormalised; outliers are uniform random directions; a Bernoulli fraction
+    `depth_frac` of observations carries a metric range prior
+    |X - c| (1 + N(0, depth_sigma)).  Start: centres moved by trans_perturb * 3 in
+    a random direction (camera 0, the gauge, kept), points by N(0, pt_perturb),
+    every scale 1 / |X0 - c0|."""
+    base = make_scene(spec, seed=seed, noise=False, outliers=False, depth_priors=False,
+                      scale=scale, shuffle=True)
+    spec = base.spec
+    rng = np.random.Generator(np.random.PCG64((spec.seed if seed is None else seed) + 7919))
+    R = Rotation.from_rotvec(base.cams_gt[:, :3]).as_matrix()
+    centres = -np.einsum("cji,cj->ci", R, base.cams_gt[:, 3:6])
+    C, P, N = spec.n_cams, spec.n_pts, base.n_obs
+    diff = base.pts_gt[base.obs_pt] - centres[base.obs_cam]
+    rng_len = np.linalg.norm(diff, axis=1)
+    rays = diff / rng_len[:, None]
+    if noise:
+        rays = rays + (spec.pixel_sigma / spec.focal) * rng.standard_normal((N, 3))
+        rays /= np.linalg.norm(rays, axis=1, keepdims=True)
+    is_out = np.zeros(N, dtype=bool)
+    if outliers and spec.outlier_frac > 0:
+        is_out = rng.random(N) < spec.outlier_frac
+        r = rng.standard_normal((int(is_out.sum()), 3))
+        rays[is_out] = r / np.linalg.norm(r, axis=1, keepdims=True)
+    depth = np.zeros(N)
+    if depth_priors and spec.depth_frac > 0:
+        has = rng.random(N) < spec.depth_frac
+        dn = spec.depth_sigma * rng.standard_normal(N) if noise else np.zeros(N)
+        depth[has] = rng_len[has] * (1.0 + dn[has])
+    fixed = np.array([0], dtype=np.int32)
+    dirs = rng.standard_normal((C, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    centres0 = centres + spec.trans_perturb * 3.0 * dirs
+    centres0[fixed] = centres[fixed]
+    pts0 = base.pts_gt + spec.pt_perturb * rng.standard_normal((P, 3))
+    scales0 = 1.0 / np.linalg.norm(pts0[base.obs_pt] - centres0[base.obs_cam], axis=1)
+    return GPScene(spec, np.ascontiguousarray(centres), base.pts_gt, np.ascontiguousarray(centres0),
+                   np.ascontiguousarray(pts0), np.ascontiguousarray(scales0), base.obs_cam, base.obs_pt,
+                   np.ascontiguousarray(rays), np.ascontiguousarray(depth), is_out, fixed)
