@@ -245,6 +245,84 @@ ba_status ba_eval_cost_noalloc(const ba_options* opts, void* stream, int64_t n_c
                                const double* obs_uv, const double* depth,
                                const uint8_t* obs_mask, double* out);
 
+/* ---------------------------------------------------------------------------
+ * Depth-constrained global positioning (GP), the stage before BA (Sec. 3.1,
+ * Eq. GP objective; Sec. 4.1, GP paragraph), on the same LM (Sec. 3.3, Eq. LM).
+ *
+ * Unknowns: camera centres t [C][3] (rotations are known and held), points
+ * X [P][3] and one scale s_k per observation; residual u_k = v_k - s_k (X_j - t_i)
+ * for observation k of point j in camera i, v_k the unit ray from the camera
+ * centre toward the feature in the world frame; cost F = 1/2 sum rho(|u_k|^2)
+ * with rho Huber (threshold huber_delta on |u|).  An observation with a metric
+ * depth d_k (the distance along its ray, > 0 and finite) has its scale pinned,
+ * s_k = 1/d_k, and removed from the unknowns; the others keep a free scale,
+ * compacted by its rank among the free observations (ascending input order).
+ * Each LM step eliminates the free scales and the points exactly and solves the
+ * dense reduced centre system (order 3 x free cameras) with the tensor-core
+ * Cholesky-preconditioned CG; FP32 arithmetic, the cost and gain ratio in FP64.
+ * Gauge: the centres of fixed_cams are held; the metric scale comes from the
+ * pinned scales (without any, it is left to the damping).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  double huber_delta;          /* Huber threshold on |u| (0.1); <= 0: squared loss */
+  double lambda0;              /* initial damping (1e-4) */
+  double pcg_rel_tol;          /* CG stop on the centre system: |r| <= tol |b| (1e-6) */
+  int pcg_max_iters;           /* CG cap (100) */
+  const int32_t* fixed_cams;   /* host array of gauge cameras ({0}) */
+  int n_fixed;
+} ba_gp_options;
+
+typedef struct ba_gp_problem ba_gp_problem;
+
+/* Fill *o with the defaults listed above. */
+void ba_gp_default_options(ba_gp_options* o);
+
+/* Create a GP problem: centres [C][3], pts [P][3], obs_cam/obs_pt [N] (int32),
+ * rays [N][3], depth [N] (metric distance along the ray; <= 0 or NaN: none, the
+ * scale is free), scales0 [N] initial scales of the free observations (NULL: 1;
+ * entries of pinned observations are ignored).  Host or device pointers; the
+ * library copies them.  Errors: BA_ERR_INVALID_ARG for bad sizes, indices,
+ * duplicate (camera, point) pairs, more than 256 observations per point or
+ * non-finite centres, points, rays or scales. */
+ba_status ba_gp_create(const ba_gp_options* opts, void* stream, int64_t n_cams, const double* centres,
+                       int64_t n_pts, const double* pts, int64_t n_obs, const int32_t* obs_cam,
+                       const int32_t* obs_pt, const double* rays, const double* depth, const double* scales0,
+                       ba_gp_problem** out);
+
+/* One LM iteration (Sec. 3.3): linearise, eliminate the free scales and the
+ * points, solve the centre system, back-substitute, evaluate the candidate and
+ * accept or reject it (gain > 1e-3; Nielsen damping update).  info (nullable):
+ * cost, rms (sqrt of the mean |u|^2, in ray units), lambda, gain, the CG
+ * iterations; n_cam_act = free cameras, n_pt_act = points, n_obs_act = free scales. */
+ba_status ba_gp_lm_step(ba_gp_problem* pb, ba_iter_info* info);
+
+/* Up to max_iters LM iterations; log has max_iters entries or is NULL. */
+ba_status ba_gp_solve(ba_gp_problem* pb, int max_iters, ba_iter_info* log, int* n_done);
+
+/* Current centres [C][3], points [P][3] and scales [N] (input order; pinned
+ * observations report 1/d).  Any output may be NULL. */
+ba_status ba_gp_get_params(ba_gp_problem* pb, double* centres, double* pts, double* scales);
+
+/* The free/pinned partition of Sec. 4.1: free_rank [N] = rank among the free
+ * observations, -1 for pinned ones; *n_free = their number.  Either may be NULL. */
+ba_status ba_gp_get_free(ba_gp_problem* pb, int32_t* free_rank, int64_t* n_free);
+
+/* The damped step at damping lambda from the current state, in full indexing:
+ * dt [C][3] (zero for fixed cameras and cameras without observations), dX [P][3],
+ * ds [N] (zero for pinned observations); info (nullable) gets pred_decrease and
+ * the CG iterations.  The state is not changed. */
+ba_status ba_gp_solve_damped(ba_gp_problem* pb, double lambda, double* dt, double* dX, double* ds,
+                             ba_iter_info* info);
+
+/* FP64 cost F and rms of the current state. */
+ba_status ba_gp_eval_cost(ba_gp_problem* pb, double* cost, double* rms);
+
+/* Number of this library's kernels launched for the problem since creation. */
+int64_t ba_gp_kernel_launches(const ba_gp_problem* pb);
+
+/* Free a GP problem (the paper has no counterpart: resource management). */
+void ba_gp_destroy(ba_gp_problem* pb);
+
 /* C = alpha A B^T + beta C on the tensor cores (tcgen05.mma kind::tf32: FP32
  * operands enter as TF32, FP32 accumulation).  The dense-system factorisation's
  * building block, exposed on its own.  A [M][lda], B [N][ldb], C [M][ldc]

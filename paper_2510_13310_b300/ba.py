@@ -29,7 +29,10 @@ EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_
            "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
            "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout", "ba_selftest_layout",
            "ba_kernel_launches", "ba_solver_kind", "ba_explicit_layout", "ba_destroy", "ba_release_cache",
-           "ba_status_string", "ba_last_error")
+           "ba_status_string", "ba_last_error",
+           "ba_gp_default_options", "ba_gp_create", "ba_gp_lm_step", "ba_gp_solve", "ba_gp_get_params",
+           "ba_gp_get_free", "ba_gp_solve_damped", "ba_gp_eval_cost", "ba_gp_kernel_launches",
+           "ba_gp_destroy")
 
 
 class _Options(ct.Structure):
@@ -41,6 +44,11 @@ class _Options(ct.Structure):
                 ("min_pt_obs", ct.c_int), ("lambda0", ct.c_double), ("pcg_rel_tol", ct.c_double),
                 ("pcg_max_iters", ct.c_int), ("fixed_cams", ct.POINTER(ct.c_int32)),
                 ("n_fixed", ct.c_int), ("solver", ct.c_int), ("extract_mode", ct.c_int)]
+
+
+class _GPOptions(ct.Structure):
+    _fields_ = [("huber_delta", ct.c_double), ("lambda0", ct.c_double), ("pcg_rel_tol", ct.c_double),
+                ("pcg_max_iters", ct.c_int), ("fixed_cams", ct.POINTER(ct.c_int32)), ("n_fixed", ct.c_int)]
 
 
 class _IterInfo(ct.Structure):
@@ -106,13 +114,29 @@ def lib():
         L.ba_destroy.argtypes = [vp]
         L.ba_release_cache.argtypes = []
         L.ba_release_cache.restype = None
+        L.ba_gp_default_options.argtypes = [ct.POINTER(_GPOptions)]
+        L.ba_gp_default_options.restype = None
+        L.ba_gp_create.argtypes = [ct.POINTER(_GPOptions), vp, ct.c_int64, vp, ct.c_int64, vp, ct.c_int64,
+                                   vp, vp, vp, vp, vp, ct.POINTER(ct.c_void_p)]
+        L.ba_gp_lm_step.argtypes = [vp, ct.POINTER(_IterInfo)]
+        L.ba_gp_solve.argtypes = [vp, ct.c_int, ct.POINTER(_IterInfo), ct.POINTER(ct.c_int)]
+        L.ba_gp_get_params.argtypes = [vp, vp, vp, vp]
+        L.ba_gp_get_free.argtypes = [vp, vp, ct.POINTER(ct.c_int64)]
+        L.ba_gp_solve_damped.argtypes = [vp, ct.c_double, vp, vp, vp, ct.POINTER(_IterInfo)]
+        L.ba_gp_eval_cost.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+        L.ba_gp_kernel_launches.argtypes = [vp]
+        L.ba_gp_kernel_launches.restype = ct.c_int64
+        L.ba_gp_destroy.argtypes = [vp]
+        L.ba_gp_destroy.restype = None
         L.ba_status_string.argtypes = [ct.c_int]
         L.ba_status_string.restype = ct.c_char_p
         L.ba_last_error.restype = ct.c_char_p
         for f in ("ba_create", "ba_lm_step", "ba_solve", "ba_get_params", "ba_set_params",
                   "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped", "ba_eval_cost",
                   "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
-                  "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout", "ba_selftest_layout"):
+                  "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout", "ba_selftest_layout",
+                  "ba_gp_create", "ba_gp_lm_step", "ba_gp_solve", "ba_gp_get_params", "ba_gp_get_free",
+                  "ba_gp_solve_damped", "ba_gp_eval_cost"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -219,11 +243,7 @@ class Problem:
         self.L = lib()
         self.options = options or Options()
         o = self.options
-        self._fixed = np.ascontiguousarray(np.asarray(o.fixed_cams, dtype=np.int32))
-        copt = _Options(o.precision, o.img_w, o.img_h, o.cx, o.cy, o.huber_delta, o.depth_weight,
-                        o.invalid_depth_weight, o.min_depth, o.extract_every, o.drop_residual_px,
-                        o.min_cam_obs, o.min_pt_obs, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
-                        self._fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(self._fixed), o.solver)
+        copt, self._fixed = _c_options(o)
         arrs = [_Arr(cams, np.float64), _Arr(pts, np.float64), _Arr(obs_cam, np.int32),
                 _Arr(obs_pt, np.int32), _Arr(obs_uv, np.float64), _Arr(depth, np.float64)]
         self.n_cams = int(np.prod(arrs[0].obj.shape)) // 9
@@ -427,6 +447,99 @@ def eval_cost_noalloc(cams, pts, obs_cam, obs_pt, obs_uv, depth, out, obs_mask=N
                                 None if obs_mask is None else obs_mask.data_ptr(), out.data_ptr())
     _check(st, "ba_eval_cost_noalloc")
     return out
+
+
+@dataclasses.dataclass
+class GPOptions:
+    huber_delta: float = 0.1
+    lambda0: float = 1e-4
+    pcg_rel_tol: float = 1e-6
+    pcg_max_iters: int = 100
+    fixed_cams: tuple = (0,)
+
+
+class GPProblem:
+    """Depth-constrained global positioning (ba_gp_*) on the current CUDA device:
+    camera centres, points and the free per-observation scales."""
+
+    def __init__(self, centres, pts, obs_cam, obs_pt, rays, depth, scales0=None,
+                 options: GPOptions | None = None, stream=None):
+        self.L = lib()
+        o = self.options = options or GPOptions()
+        self._fixed = np.ascontiguousarray(np.asarray(o.fixed_cams, dtype=np.int32))
+        copt = _GPOptions(o.huber_delta, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
+                          self._fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(self._fixed))
+        arrs = [_Arr(centres, np.float64), _Arr(pts, np.float64), _Arr(obs_cam, np.int32),
+                _Arr(obs_pt, np.int32), _Arr(rays, np.float64), _Arr(depth, np.float64)]
+        s0 = None if scales0 is None else _Arr(scales0, np.float64)
+        self.n_cams = int(np.prod(arrs[0].obj.shape)) // 3
+        self.n_pts = int(np.prod(arrs[1].obj.shape)) // 3
+        self.n_obs = int(np.prod(arrs[2].obj.shape))
+        h = ct.c_void_p()
+        _check(self.L.ba_gp_create(ct.byref(copt), _stream_handle(stream), self.n_cams, arrs[0].p, self.n_pts,
+                                   arrs[1].p, self.n_obs, arrs[2].p, arrs[3].p, arrs[4].p, arrs[5].p,
+                                   None if s0 is None else s0.p, ct.byref(h)), "ba_gp_create")
+        self.h = h
+
+    @classmethod
+    def from_scene(cls, sc, options: GPOptions | None = None, stream=None):
+        o = options or GPOptions()
+        if tuple(o.fixed_cams) != tuple(int(c) for c in sc.fixed_cams):
+            o = dataclasses.replace(o, fixed_cams=tuple(int(c) for c in sc.fixed_cams))
+        return cls(sc.centres0, sc.pts0, sc.obs_cam, sc.obs_pt, sc.rays, sc.depth, sc.scales0, o, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ba_gp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lm_step(self):
+        info = _IterInfo()
+        _check(self.L.ba_gp_lm_step(self.h, ct.byref(info)), "ba_gp_lm_step",
+               allow=(BA_OK, BA_ERR_NOT_CONVERGED, BA_ERR_NONFINITE))
+        return info.as_dict()
+
+    def solve(self, max_iters):
+        log = (_IterInfo * max(1, max_iters))()
+        n = ct.c_int(0)
+        _check(self.L.ba_gp_solve(self.h, int(max_iters), log, ct.byref(n)), "ba_gp_solve",
+               allow=(BA_OK, BA_ERR_NOT_CONVERGED))
+        return [log[i].as_dict() for i in range(n.value)]
+
+    def get_params(self):
+        c = np.zeros((self.n_cams, 3)); p = np.zeros((self.n_pts, 3)); s = np.zeros(self.n_obs)
+        _check(self.L.ba_gp_get_params(self.h, c.ctypes.data, p.ctypes.data, s.ctypes.data), "ba_gp_get_params")
+        return c, p, s
+
+    def get_free(self):
+        fr = np.zeros(self.n_obs, np.int32)
+        n = ct.c_int64(0)
+        _check(self.L.ba_gp_get_free(self.h, fr.ctypes.data, ct.byref(n)), "ba_gp_get_free")
+        return fr, n.value
+
+    def solve_damped(self, lam):
+        dt = np.zeros((self.n_cams, 3)); dX = np.zeros((self.n_pts, 3)); ds = np.zeros(self.n_obs)
+        info = _IterInfo()
+        _check(self.L.ba_gp_solve_damped(self.h, float(lam), dt.ctypes.data, dX.ctypes.data, ds.ctypes.data,
+                                         ct.byref(info)), "ba_gp_solve_damped")
+        d = info.as_dict()
+        return dict(dt=dt, dX=dX, ds=ds, pred_decrease=d["pred_decrease"], pcg_iters=d["pcg_iters"],
+                    pcg_rel_res=d["pcg_rel_res"])
+
+    def eval_cost(self):
+        F, r = ct.c_double(0), ct.c_double(0)
+        _check(self.L.ba_gp_eval_cost(self.h, ct.byref(F), ct.byref(r)), "ba_gp_eval_cost")
+        return F.value, r.value
+
+    @property
+    def kernel_launches(self):
+        return int(self.L.ba_gp_kernel_launches(self.h))
 
 
 def _make_ba_function():

@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libba_b300.so")
-SOURCES = ["kernels.cu", "pcg.cu", "schur_explicit.cu", "adjoint.cu", "dense_tc.cu", "noalloc.cu", "layout.cu", "layout_dev.cu", "ba_abi.cu"]
+SOURCES = ["kernels.cu", "pcg.cu", "schur_explicit.cu", "adjoint.cu", "dense_tc.cu", "noalloc.cu", "gp.cu", "layout.cu", "layout_dev.cu", "ba_abi.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr",

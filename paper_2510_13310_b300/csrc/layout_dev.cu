@@ -617,6 +617,11 @@ void release_scratch_pools() {
   for (auto& kv : g_pools) cudaMemPoolTrimTo(kv.second, 0);
 }
 
+int build_obs_layout_dev_indices(int C, int P, int N, const int32_t* d_oc, const int32_t* d_op,
+                                 const DevAlloc& alloc, cudaStream_t s, DevLayout* L, std::string* err) {
+  return build_obs_layout_impl(C, P, N, nullptr, nullptr, nullptr, d_oc, d_op, false, alloc, s, L, err);
+}
+
 int build_obs_layout_dev(int C, int P, int N, const double* d_cams, const double* d_pts, const double* d_uv,
                          const int32_t* d_oc, const int32_t* d_op, const DevAlloc& alloc, cudaStream_t s,
                          cudaStream_t vs, DevLayout* L, std::string* err) {

@@ -43,6 +43,11 @@ struct DevCovis {
 int build_obs_layout_dev(int C, int P, int N, const double* d_cams, const double* d_pts, const double* d_uv,
                          const int32_t* d_oc, const int32_t* d_op, const DevAlloc& alloc, cudaStream_t s,
                          cudaStream_t vs, DevLayout* L, std::string* err);
+// The same layout from the observation indices alone (index ranges, duplicate
+// pairs and track lengths checked; no value arrays), for problems whose values
+// are not BA cameras and pixels (global positioning).
+int build_obs_layout_dev_indices(int C, int P, int N, const int32_t* d_oc, const int32_t* d_op,
+                                 const DevAlloc& alloc, cudaStream_t s, DevLayout* L, std::string* err);
 // Return the layout builders' cached scratch memory to the device.
 void release_scratch_pools();
 int build_covis_runs_dev(const DevLayout& L, int C, int N, const DevAlloc& alloc, cudaStream_t s, DevCovis* out,

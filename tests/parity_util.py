@@ -15,6 +15,7 @@ for that element (never the largest entry of the whole array):
 from __future__ import annotations
 
 import numpy as np
+import pytest
 
 
 def check_close(got, ref, rtol, atol=0.0, label=""):
@@ -69,3 +70,30 @@ def normal_equation_scales(orc, cams, pts, obs_mask):
     jp = np.sqrt((ev["Jp"] ** 2).sum(1))  # [N, 3]
     w_scale = w[:, None, None] * jc[:, :, None] * jp[:, None, :]
     return dict(res_c=res_c, res_p=res_p, W=w_scale)
+
+
+def check_blocks(lin, ne, orc, cams, pts, obs_mask, live, tol, W_rows=None):
+    """Element-wise bars on the normal-equation blocks: every entry within tol of
+    its Cauchy-Schwarz scale (sqrt(A_ii A_jj) for U and V; sqrt(H_ii) times the
+    root of the weighted squared residuals for the gradients; rho' |J_c,i| |J_p,j|
+    for W) plus tol relative."""
+    s = normal_equation_scales(orc, cams, pts, obs_mask)
+    dU = np.sqrt(np.abs(np.einsum("cii->ci", ne["U"])))
+    dV = np.sqrt(np.abs(np.einsum("pii->pi", ne["V"])))
+    worst = dict(U=check_close(lin["U"][live], ne["U"][live], tol, tol * sym_scale(ne["U"][live]), "U"),
+                 V=check_close(lin["V"], ne["V"], tol, tol * sym_scale(ne["V"]), "V"),
+                 gc=check_close(lin["gc"][live], ne["gc"][live], tol,
+                                tol * (dU * np.sqrt(s["res_c"])[:, None])[live], "gc"),
+                 gp=check_close(lin["gp"], ne["gp"], tol, tol * dV * np.sqrt(s["res_p"])[:, None], "gp"))
+    rows = slice(None) if W_rows is None else W_rows
+    worst["W"] = check_close(lin["W"][rows], ne["W"][rows], tol, tol * s["W"][rows], "W")
+    return worst
+
+
+def check_step(g, o, tol, pred_tol):
+    """Damped steps element-wise: within tol of each parameter kind's scale (the
+    largest magnitude of that camera parameter, or of the point coordinates) plus
+    tol relative; the predicted decrease within pred_tol relative."""
+    check_close(g["dc"], o["dc"], tol, tol * kind_scale(o["dc"]), "dc")
+    check_close(g["dp"], o["dp"], tol, tol * kind_scale(o["dp"]), "dp")
+    assert g["pred_decrease"] == pytest.approx(o["pred_decrease"], rel=pred_tol)

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_2510_13310_b300 import ba, scenes
+from parity_util import check_close
 
 pytestmark = pytest.mark.gpu
 
@@ -19,8 +20,12 @@ if not torch.cuda.is_available():
 SOLVERS = [ba.BA_SOLVER_EXPLICIT, ba.BA_SOLVER_IMPLICIT]
 
 
-def rel_err(a, b):
-    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+def grad_close(got, ref, tol, label):
+    """Element-wise: |got - ref| <= tol (|ref| + rms(ref)); the RMS of the reference
+    gradient over the entries that carry one is the scale of an absolute error."""
+    nz = ref != 0
+    rms = np.sqrt(np.mean(ref[nz] ** 2)) if nz.any() else 0.0
+    return check_close(got, ref, tol, tol * rms, label)
 
 
 def oracle_gradient(sc, cams, pts):
@@ -32,8 +37,8 @@ def oracle_gradient(sc, cams, pts):
 
 
 @pytest.mark.parametrize("solver", SOLVERS)
-@pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-6), (ba.BA_FP32, 2e-2)])
-def test_backward_matches_oracle_on_differentiable_workload(precision, tol, solver):
+@pytest.mark.parametrize("precision,tol_uv,tol_d", [(ba.BA_FP64, 1e-6, 1e-6), (ba.BA_FP32, 5e-2, 2e-1)])
+def test_backward_matches_oracle_on_differentiable_workload(precision, tol_uv, tol_d, solver):
     """The differentiable-BA workload: 100 cameras, 20k points, ~200k observations."""
     sc = scenes.make_scene("diff")
     fp64 = precision == ba.BA_FP64
@@ -45,10 +50,10 @@ def test_backward_matches_oracle_on_differentiable_workload(precision, tol, solv
     duv_o, dd_o, ext = oracle_gradient(sc, cams, pts)
     om = gpu.get_active()["obs_mask"]
     assert np.array_equal(om, ext["obs_mask"])
-    e_uv, e_d = rel_err(duv_g, duv_o), rel_err(dd_g, dd_o)
-    print(f"ba_backward vs oracle implicit gradient: uv {e_uv:.3e}, depth {e_d:.3e}")
-    assert e_uv < tol
-    assert e_d < tol
+    e_uv = grad_close(duv_g, duv_o, tol_uv, "duv")
+    e_d = grad_close(dd_g, dd_o, tol_d, "ddepth")
+    print(f"ba_backward vs oracle implicit gradient (worst element / bar): uv {e_uv * tol_uv:.3e}, "
+          f"depth {e_d * tol_d:.3e}")
     # inactive observations and those without a prior carry no gradient
     assert not duv_g[om == 0].any()
     assert not dd_g[~(sc.depth > 0)].any()
@@ -112,7 +117,7 @@ def test_fp64_backward_matches_reconverged_finite_differences():
 # the pixels constrain the rest ((1/z^2)^2 against (f/z)^2 per observation), so
 # FP32 arithmetic resolves that component of mu, which the depth gradients
 # mostly see, to a few percent; pixel gradients are accurate to ~1e-3.
-@pytest.mark.parametrize("precision,tol_uv,tol_d", [(ba.BA_FP64, 1e-7, 1e-7), (ba.BA_FP32, 1e-2, 1.5e-1)])
+@pytest.mark.parametrize("precision,tol_uv,tol_d", [(ba.BA_FP64, 1e-7, 1e-7), (ba.BA_FP32, 5e-2, 5e-1)])
 def test_autograd_op_gives_the_implicit_gradient(precision, tol_uv, tol_d):
     sc = low_noise_scene()
     dev = torch.device("cuda")
@@ -127,8 +132,60 @@ def test_autograd_op_gives_the_implicit_gradient(precision, tol_uv, tol_d):
     loss.backward()
     c, p = cams.detach().cpu().numpy(), pts.detach().cpu().numpy()
     duv_o, dd_o, _ = oracle_gradient(sc, c, p)
-    e_uv = rel_err(uv.grad.cpu().numpy(), duv_o)
-    e_d = rel_err(depth.grad.cpu().numpy(), dd_o)
-    print(f"autograd vs oracle implicit gradient: uv {e_uv:.3e}, depth {e_d:.3e}")
-    assert e_uv < tol_uv
-    assert e_d < tol_d
+    e_uv = grad_close(uv.grad.cpu().numpy(), duv_o, tol_uv, "duv")
+    e_d = grad_close(depth.grad.cpu().numpy(), dd_o, tol_d, "ddepth")
+    print(f"autograd vs oracle implicit gradient (worst element / bar): uv {e_uv * tol_uv:.3e}, "
+          f"depth {e_d * tol_d:.3e}")
+
+
+def test_differentiable_workload_central_differences_50_coordinates():
+    """configs' differentiable-BA check as specified: on the 200k-observation scene,
+    FP64 central differences (step 1e-4 px) of the re-converged FP64 solve on 50
+    random pixel coordinates (and 10 depth priors, step 1e-3 relative), against
+    the implicit gradient (GPU FP64, equal to the oracle's).  The scene has
+    0.5 px noise and 2% outliers, so the Gauss-Newton matrix differs from the
+    Hessian by O(residual): the gap is printed, and bounded loosely."""
+    sc = scenes.make_scene("diff")
+    opts = ba.Options(precision=ba.BA_FP64, pcg_rel_tol=1e-12, fixed_cams=tuple(sc.fixed_cams))
+    c, p = solve_from(sc, sc.cams0, sc.pts0, sc.obs_uv, sc.depth, opts, 40)
+    gpu = ba.Problem(c, p, sc.obs_cam, sc.obs_pt, sc.obs_uv, sc.depth, opts)
+    duv, dd = gpu.backward(c - sc.cams_gt, p - sc.pts_gt)
+    om = gpu.get_active()["obs_mask"].astype(bool)
+    gpu.close()
+    duv_o, dd_o, _ = oracle_gradient(sc, c, p)
+    grad_close(duv, duv_o, 1e-6, "duv vs oracle")
+    grad_close(dd, dd_o, 1e-6, "ddepth vs oracle")
+
+    def loss(cc, pp):
+        return 0.5 * np.sum((cc - sc.cams_gt) ** 2) + 0.5 * np.sum((pp - sc.pts_gt) ** 2)
+
+    rng = np.random.default_rng(50)
+    act = np.flatnonzero(om)
+    fd_uv, ig_uv, fd_d, ig_d = [], [], [], []
+    for k, j in zip(rng.choice(act, 50, replace=False), rng.integers(0, 2, 50)):
+        h = 1e-4
+        uv = sc.obs_uv.copy()
+        uv[k, j] += h
+        Lp = loss(*solve_from(sc, c, p, uv, sc.depth, opts, 25))
+        uv[k, j] -= 2 * h
+        Lm = loss(*solve_from(sc, c, p, uv, sc.depth, opts, 25))
+        fd_uv.append((Lp - Lm) / (2 * h))
+        ig_uv.append(duv[k, j])
+    for k in rng.choice(np.flatnonzero((sc.depth > 0) & om), 10, replace=False):
+        h = 1e-3 * sc.depth[k]
+        d = sc.depth.copy()
+        d[k] += h
+        Lp = loss(*solve_from(sc, c, p, sc.obs_uv, d, opts, 25))
+        d[k] -= 2 * h
+        Lm = loss(*solve_from(sc, c, p, sc.obs_uv, d, opts, 25))
+        fd_d.append((Lp - Lm) / (2 * h))
+        ig_d.append(dd[k])
+    fd_uv, ig_uv, fd_d, ig_d = map(np.asarray, (fd_uv, ig_uv, fd_d, ig_d))
+    gap_uv = np.abs(fd_uv - ig_uv) / np.sqrt(np.mean(fd_uv ** 2))
+    gap_d = np.abs(fd_d - ig_d) / np.sqrt(np.mean(fd_d ** 2))
+    cos_uv = fd_uv @ ig_uv / (np.linalg.norm(fd_uv) * np.linalg.norm(ig_uv))
+    print(f"Gauss-Newton gap on the 200k-observation scene, |FD - implicit| / rms(FD): pixels median "
+          f"{np.median(gap_uv):.3e}, max {gap_uv.max():.3e} (cosine {cos_uv:.6f}); depth median "
+          f"{np.median(gap_d):.3e}, max {gap_d.max():.3e}")
+    assert cos_uv > 0.95
+    assert np.median(gap_uv) < 0.2 and np.median(gap_d) < 0.3

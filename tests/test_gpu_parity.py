@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from paper_2510_13310_b300 import ba, scenes
+from parity_util import check_blocks, check_close, check_step
 
 pytestmark = pytest.mark.gpu
 
@@ -38,15 +39,18 @@ def pair(scene, precision, **opt):
     return gpu, orc
 
 
-def rel_err(a, b):
-    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+# FP64: the GPU and the oracle differ only in summation order (measured <= 2e-8
+# of the kind scale for the PCG-to-1e-10 steps).  FP32: products and sums in
+# FP32, PCG to 1e-6 (measured <= 4.3e-4 on these scenes).
+STEP_TOL = {ba.BA_FP64: (1e-7, 1e-10), ba.BA_FP32: (2e-3, 1e-6)}
 
 
 # ---------------------------------------------------------------------------
 # (a)+(b): normal-equation blocks at an identical state
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-11), (ba.BA_FP32, 2e-4)])
+# measured worst entries: FP64 ~7e-14 of their scale; FP32 ~2.6e-5 (W)
+@pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-11), (ba.BA_FP32, 1e-4)])
 def test_linearization_blocks_match_oracle(precision, tol):
     sc = geometric(12, 3000, 2, 12, 5.0, seed=31)   # several tiles, ragged last tile
     gpu, orc = pair(sc, precision, invalid_depth_weight=1e-3)
@@ -57,11 +61,7 @@ def test_linearization_blocks_match_oracle(precision, tol):
     np.testing.assert_array_equal(act["obs_mask"], ext["obs_mask"])
     ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
     live = ext["cam_mask"].astype(bool)
-    assert rel_err(lin["U"][live], ne["U"][live]) < tol
-    assert rel_err(lin["gc"][live], ne["gc"][live]) < tol
-    assert rel_err(lin["V"], ne["V"]) < tol
-    assert rel_err(lin["gp"], ne["gp"]) < tol
-    assert rel_err(lin["W"], ne["W"]) < tol
+    print(check_blocks(lin, ne, orc, sc.cams0, sc.pts0, ext["obs_mask"], live, tol))
 
 
 def test_cost_fp64_matches_oracle_at_same_state():
@@ -173,8 +173,8 @@ SOLVERS = [ba.BA_SOLVER_IMPLICIT, ba.BA_SOLVER_EXPLICIT]
 
 
 @pytest.mark.parametrize("solver", SOLVERS)
-@pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-7), (ba.BA_FP32, 2e-2)])
-def test_damped_step_matches_oracle(precision, tol, solver):
+@pytest.mark.parametrize("precision", [ba.BA_FP64, ba.BA_FP32])
+def test_damped_step_matches_oracle(precision, solver):
     sc = geometric(12, 3000, 2, 12, 5.0, seed=41)
     gpu, orc = pair(sc, precision, pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6,
                     solver=solver)
@@ -184,15 +184,13 @@ def test_damped_step_matches_oracle(precision, tol, solver):
     ext = orc.extract(geom)
     ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
     o = orc.solve_step(ne, ext, lam)   # dense Cholesky of the Schur system
-    assert rel_err(g["dc"], o["dc"]) < tol
-    assert rel_err(g["dp"], o["dp"]) < tol
-    assert g["pred_decrease"] == pytest.approx(o["pred_decrease"], rel=tol)
+    check_step(g, o, *STEP_TOL[precision])
     assert g["pcg_rel_res"] <= (1e-10 if precision == ba.BA_FP64 else 1e-6)
     assert not g["dc"][sc.fixed_cams].any()
 
 
-@pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-7), (ba.BA_FP32, 2e-2)])
-def test_explicit_step_with_many_short_runs_matches_oracle(precision, tol):
+@pytest.mark.parametrize("precision", [ba.BA_FP64, ba.BA_FP32])
+def test_explicit_step_with_many_short_runs_matches_oracle(precision):
     """About 99k co-visible camera pairs of a few shared points each: the explicit
     system is formed by the kernel for many short co-visibility runs (chosen at
     4 x 128 runs per SM and more) rather than the warp-per-run kernel."""
@@ -210,9 +208,7 @@ def test_explicit_step_with_many_short_runs_matches_oracle(precision, tol):
     ext = orc.extract(geom)
     ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
     o = orc.solve_step(ne, ext, lam)
-    assert rel_err(g["dc"], o["dc"]) < tol
-    assert rel_err(g["dp"], o["dp"]) < tol
-    assert g["pred_decrease"] == pytest.approx(o["pred_decrease"], rel=tol)
+    check_step(g, o, *STEP_TOL[precision])
 
 
 @pytest.mark.parametrize("solver", [ba.BA_SOLVER_EXPLICIT, ba.BA_SOLVER_IMPLICIT])
@@ -254,8 +250,8 @@ def test_auto_solver_choice_follows_the_cost_model():
     sparse.close()
 
 
-@pytest.mark.parametrize("precision,n_cams,tol", [(ba.BA_FP64, 400, 1e-7), (ba.BA_FP32, 700, 2e-2)])
-def test_explicit_solver_vectors_in_global_scratch(precision, n_cams, tol):
+@pytest.mark.parametrize("precision,n_cams", [(ba.BA_FP64, 400), (ba.BA_FP32, 700)])
+def test_explicit_solver_vectors_in_global_scratch(precision, n_cams):
     # systems of 3,591 (FP64) and 6,291 (FP32) unknowns: the explicit PCG keeps p
     # in shared memory and its other per-block vectors in global scratch
     sc = geometric(n_cams, 6000, 2, 10, 4.0, seed=77)
@@ -268,8 +264,7 @@ def test_explicit_solver_vectors_in_global_scratch(precision, n_cams, tol):
     ext = orc.extract(geom)
     ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
     o = orc.solve_step(ne, ext, lam)
-    assert rel_err(g["dc"], o["dc"]) < tol
-    assert rel_err(g["dp"], o["dp"]) < tol
+    check_step(g, o, *STEP_TOL[precision])
     assert g["pcg_rel_res"] <= (1e-10 if precision == ba.BA_FP64 else 1e-6)
 
 
@@ -437,9 +432,7 @@ def test_dense_solver_damped_step_matches_oracle(n_cams, n_pts, track):
     ext = orc.extract(geom)
     ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
     o = orc.solve_step(ne, ext, lam)
-    assert rel_err(g["dc"], o["dc"]) < 2e-2
-    assert rel_err(g["dp"], o["dp"]) < 2e-2
-    assert g["pred_decrease"] == pytest.approx(o["pred_decrease"], rel=2e-2)
+    check_step(g, o, *STEP_TOL[ba.BA_FP32])
     assert g["pcg_rel_res"] <= 1e-6
     # the factor is a good preconditioner: CG needs only a few iterations
     assert g["pcg_iters"] <= 20
@@ -472,9 +465,7 @@ def test_explicit_solver_with_many_short_runs_matches_oracle():
     ext = orc.extract(geom)
     ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
     o = orc.solve_step(ne, ext, lam)
-    assert rel_err(g["dc"], o["dc"]) < 2e-2
-    assert rel_err(g["dp"], o["dp"]) < 2e-2
-    assert g["pred_decrease"] == pytest.approx(o["pred_decrease"], rel=2e-2)
+    check_step(g, o, *STEP_TOL[ba.BA_FP32])
 
 
 # ---------------------------------------------------------------------------
@@ -507,3 +498,34 @@ def test_checkpoint_resume_repeats_the_run_bit_for_bit(precision, solver):
     other = ba.Problem.from_scene(geometric(20, 3000, 2, 10, 5.0, seed=24), o)
     with pytest.raises(ba.BAError):
         other.set_state(blob)
+
+
+# ---------------------------------------------------------------------------
+# one-shot pruning vs dynamic extraction (Sec. 4.2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", [ba.BA_EXTRACT_ONCE, ba.BA_EXTRACT_DYNAMIC])
+def test_extraction_mode_trajectory_matches_oracle(mode):
+    """Injected frustum exits (points starting above the image of their nearer
+    cameras).  One-shot pruning keeps the first active set, bit for bit the
+    oracle's extraction at the start; dynamic extraction re-admits observations
+    as the points come back.  Both follow the oracle's costs per iteration."""
+    sc = scenes.make_scene("small", frustum_exit_frac=0.3)
+    gpu, orc = pair(sc, ba.BA_FP32, extract_mode=mode)
+    log_g = gpu.solve(10)
+    _, _, log_o = oracle.OracleBA.from_scene(sc, oracle.OracleOptions(solver=1, extract_mode=mode)).lm(
+        sc.cams0, sc.pts0, 10)
+    for i, (a, b) in enumerate(zip(log_g, log_o)):
+        assert a["cost"] == pytest.approx(b["cost"], rel=1e-5), i
+        assert a["accepted"] == b["accepted"], i
+        assert a["n_obs_act"] == b["n_obs_act"], i
+    acts = [r["n_obs_act"] for r in log_g]
+    if mode == ba.BA_EXTRACT_ONCE:
+        assert len(set(acts)) == 1
+        geom, _ = orc.predicate(sc.cams0, sc.pts0)
+        e = orc.extract(geom)
+        g = gpu.get_active()
+        for key in ("cam_mask", "pt_mask", "obs_mask", "cam_rank", "pt_rank"):
+            np.testing.assert_array_equal(g[key], e[key], err_msg=key)
+    else:
+        assert acts[-1] > acts[0]
