@@ -188,6 +188,48 @@ def run_dense_kernels():
     return 0
 
 
+def run_gp_measure(torch, ba, dev, stream, steps=8, warmup=3):
+    """Depth-constrained global positioning on the same geometry (200 cameras, 100k
+    points, ~1M observations, rays with 0.5 px angular noise, 2% outliers, metric
+    range priors on 50%): LM iterations/s over `steps` timed iterations (CUDA
+    events, L2 flushed between steps) and per-phase device times.  The dominant
+    phase's roofline: the point-side linearisation streams per observation the ray
+    (16 B), the camera centre (16 B, L2), the scale (4 B) and writes its 80 B
+    record and 48 B Schur factor; per point 16 B in and 64 B out."""
+    sc = scenes.make_gp_scene(WORKLOAD)
+    prob = ba.GPProblem.from_scene(sc, stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(warmup):
+        prob.lm_step()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, infos = [], []
+    for _ in range(steps):
+        flush.zero_()
+        ev0.record(stream)
+        infos.append(prob.lm_step())
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    N, P = sc.n_obs, sc.spec.n_pts
+    lin_ms = statistics.median(i["ms"][0] for i in infos)
+    hbm, kind = _peaks()
+    lin_bytes = N * (16 + 16 + 4 + 80 + 48) + P * (16 + 64)
+    out = {"metric": "GP LM iters/s", "value": steps / (sum(ms) / 1e3), "unit": "LM iters/s",
+           "ms_per_step": statistics.mean(ms), "workload": _workload_name(sc) + " (global positioning)",
+           "n_free_scales": int(infos[0]["n_obs_act"]), "cg_iters": [i["pcg_iters"] for i in infos],
+           "phase_ms_median": {"linearize (point pass + camera chunks)": lin_ms,
+                               "Schur diagonal + S formation": statistics.median(i["ms"][1] for i in infos),
+                               "dense tensor-core solve": statistics.median(i["ms"][2] for i in infos),
+                               "back-substitution + candidate + cost": statistics.median(i["ms"][3] for i in infos)},
+           "final_cost": infos[-1]["cost"], "gpu_launches": prob.kernel_launches,
+           "roofline_linearize": {"bound": "hbm", "achieved": lin_bytes / (lin_ms * 1e-3) / 1e9, "peak": hbm,
+                                  "unit": "GB/s", "frac": lin_bytes / (lin_ms * 1e-3) / 1e9 / hbm,
+                                  "peak_source": kind + " (burst copy)",
+                                  "formula": "164 B x obs + 80 B x points"}}
+    prob.close()
+    return out
+
+
 def oracle_cpu_baseline(scene, max_seconds=20.0, max_iters=30):
     """The FP64 CPU oracle (test infrastructure) on a bounded sample: LM iterations
     of the same scene until max_seconds of work or max_iters."""
@@ -204,10 +246,18 @@ def oracle_cpu_baseline(scene, max_seconds=20.0, max_iters=30):
         t_tot += time.perf_counter() - t0
         done += 1
         lam_state = rows[-1]["lam"] if rows else lam_state
-    return {"value": done / t_tot, "unit": "LM iters/s", "cores": oracle.get_threads(),
+    # the same oracle on one host thread: one iteration (bounded)
+    cores = oracle.get_threads()
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    ob.lm(cams, pts, 1, alive=alive)
+    t1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    return {"value": done / t_tot, "unit": "LM iters/s", "cores": cores,
             "kind": "oracle",
             "sample": f"{done} LM iteration(s) of the {_workload_name(scene)} (FP64, dense Cholesky "
-                      f"of the Schur system), {t_tot:.1f} s"}
+                      f"of the Schur system), {t_tot:.1f} s",
+            "one_thread": {"value": 1.0 / t1, "unit": "LM iters/s", "sample": "1 LM iteration, 1 thread"}}
 
 
 def run_reference(args):
@@ -254,6 +304,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-RMSE comparison")
+    ap.add_argument("--no-gp", action="store_true", help="skip the global-positioning measurement")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenes.SPECS),
                     help="scene (default: the 1M-observation scene)")
     ap.add_argument("--solver", default="auto", choices=["auto", "implicit", "explicit", "dense"])
@@ -315,6 +366,29 @@ def main():
     ab_ms = statistics.median([i["ms"][1] + i["ms"][2] for i in lin]) if lin else None
     schur_ms = statistics.median([i["ms"][2] for i in infos])
     gobs = N / (ab_ms * 1e-3) / 1e9 if ab_ms else None
+    # (a)+(b) against HBM: 124 B per observation (uv 8, prior 4, point index 4, W row
+    # write 108) plus 12 B read and 36 B written per point
+    ab_bytes = 124 * N + 48 * scene.spec.n_pts
+    ab_roof = {"bytes_algorithmic": ab_bytes, "ms": ab_ms,
+               "achieved_gbs": ab_bytes / (ab_ms * 1e-3) / 1e9 if ab_ms else None,
+               "frac_of_hbm": ab_bytes / (ab_ms * 1e-3) / 1e9 / _peaks()[0] if ab_ms else None}
+    # step (c) alone (ba_extract: validity bits, peel, ranks, one host readback),
+    # against its bytes: per observation bits, alive, valid, two masks (5 B) and the
+    # camera and point indices of the peel (8 B); per camera and point ~16 B
+    ext_ms = []
+    for _ in range(5):
+        flush.zero_()
+        ev0.record(stream)
+        prob.extract()
+        ev1.record(stream)
+        ev1.synchronize()
+        ext_ms.append(ev0.elapsed_time(ev1))
+    ext_ms = statistics.median(ext_ms)
+    ext_bytes = 13 * N + 16 * (scene.spec.n_cams + scene.spec.n_pts)
+    ext_roof = {"bytes_algorithmic": ext_bytes, "ms": ext_ms,
+                "achieved_gbs": ext_bytes / (ext_ms * 1e-3) / 1e9,
+                "frac_of_hbm": ext_bytes / (ext_ms * 1e-3) / 1e9 / _peaks()[0],
+                "note": "~10 launches and one blocking readback of the counts: latency-bound"}
 
     # roofline of the dominant kernel: of the PCG launch (ms[4]) and the co-visibility
     # product that forms the explicit system (ms[7]), the one with the larger mean
@@ -435,8 +509,14 @@ def main():
     ttr = None
     if not args.no_ttr:
         def trajectory(prec, solver=ba.BA_SOLVER_AUTO):
-            p = ba.Problem.from_scene(scene, ba.Options(precision=prec, solver=solver),
-                                      stream=stream.cuda_stream)
+            try:
+                p = ba.Problem.from_scene(scene, ba.Options(precision=prec, solver=solver),
+                                          stream=stream.cuda_stream)
+            except ba.BAError:
+                # the FP64 implicit PCG keeps each block's cameras in shared memory and
+                # does not fit 2,000 FP64 cameras: the FP64 reference runs the explicit PCG
+                p = ba.Problem.from_scene(scene, ba.Options(precision=prec, solver=ba.BA_SOLVER_EXPLICIT),
+                                          stream=stream.cuda_stream)
             rows, t = [], 0.0
             for _ in range(LM_ITERS):
                 ev0.record(stream)
@@ -467,6 +547,10 @@ def main():
                "fp64_total_s": rows64[-1][0], "fp32_total_s": rows32[-1][0],
                "rule": "first iteration whose result RMSE is within 1e-5 of the FP64 final RMSE"}
 
+    gp = None
+    if not args.no_gp and args.workload == WORKLOAD:
+        gp = run_gp_measure(torch, ba, dev, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_cpu_baseline(scene)
@@ -486,6 +570,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)"},
             "jacobian_schur_gobs_s": gobs, "jacobian_schur_ms": ab_ms, "schur_terms_ms": schur_ms,
+            "jacobian_schur_hbm": ab_roof, "extraction_hbm": ext_roof, "gp": gp,
             "roofline": roofline, "roofline_next": roofline_next, "cpu_baseline": cpu, "e2e": e2e,
             "time_to_rmse": ttr,
             "gpu_launches": launches, "clocks": clk.summary(),

@@ -36,7 +36,7 @@ class Opts(ct.Structure):
                 ("extract_every", ct.c_int), ("drop_residual_px", ct.c_double),
                 ("min_cam_obs", ct.c_int), ("min_pt_obs", ct.c_int), ("lambda0", ct.c_double),
                 ("pcg_rel_tol", ct.c_double), ("pcg_max_iters", ct.c_int), ("solver", ct.c_int),
-                ("extract_mode", ct.c_int)]
+                ("extract_mode", ct.c_int), ("nu0", ct.c_double)]
 
 
 class GPProblem(ct.Structure):
@@ -140,6 +140,7 @@ class OracleOptions:
     pcg_max_iters: int = 500
     solver: int = 0  # 0 dense Cholesky of the Schur system, 1 PCG
     extract_mode: int = 0  # 0 dynamic (every iteration), 1 one-shot at the first iteration
+    nu0: float = 2.0  # initial damping growth factor (a restart after rejected steps)
 
     def to_c(self) -> Opts:
         return Opts(**dataclasses.asdict(self))

@@ -37,6 +37,7 @@ void oracle_default_opts(oracle_opts* o) {
   o->pcg_max_iters = 500;
   o->solver = 0;
   o->extract_mode = 0;
+  o->nu0 = 2.0;
 }
 
 void oracle_set_threads(int n) {
@@ -950,7 +951,7 @@ int oracle_lm(const oracle_problem* pb, const oracle_opts* o, int max_iters, dou
   double* cams2 = (double*)malloc(sizeof(double) * 9 * ((size_t)C + 1));
   double* pts2 = (double*)malloc(sizeof(double) * 3 * ((size_t)P + 1));
 
-  double lambda = o->lambda0, nu = 2.0;
+  double lambda = o->lambda0, nu = o->nu0 > 0.0 ? o->nu0 : 2.0;
   int state_changed = 1;
   int64_t n_cam_free = 0, n_pt_act = 0;
   double F = 0.0, rmse = 0.0;

@@ -52,6 +52,7 @@ typedef struct {
   int solver;                   /* 0: dense Cholesky of the Schur system; 1: block-Jacobi PCG */
   int extract_mode;             /* 0: extraction at every iteration whose state changed (Sec. 4.2);
                                    1: one-shot, at the first iteration only, active set frozen */
+  double nu0;                   /* initial damping growth factor nu (<= 0: 2, the rule's start) */
 } oracle_opts;
 
 typedef struct {

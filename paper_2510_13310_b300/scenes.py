@@ -61,7 +61,10 @@ SPECS = {
                        depth_frac=0.3, depth_sigma=0.03, seed=1002),
     "diff": SceneSpec("diff", 100, 20_000, 10, 10, 10.0, seed=1003),
     "dense": SceneSpec("dense", 2_000, 400_000, 30, 30, 30.0, seed=1004),
+    "window": SceneSpec("window", 1_500, 300_000, 3, 12, 6.0, seed=1005),
 }
+# scenes whose tracks are windows of neighbouring cameras
+WINDOWED = {"window"}
 
 
 @dataclasses.dataclass
@@ -170,15 +173,39 @@ def project_points(R: np.ndarray, t: np.ndarray, f: np.ndarray, k1: np.ndarray,
     return uv, P[:, 2]
 
 
+def _window_tracks(rng, pts: np.ndarray, C: int, lengths: np.ndarray):
+    """Windowed co-visibility: the track of a point takes the `lengths[p]`
+    consecutive cameras (on the circle of C) centred on the camera whose azimuth
+    is nearest the point's, so cameras i and j share points only when
+    |i - j| < max track length (a block-banded reduced camera system)."""
+    phi = np.arctan2(pts[:, 1], pts[:, 0])
+    centre = np.rint(phi / (2.0 * math.pi) * C).astype(np.int64) % C
+    offs = np.zeros(len(lengths) + 1, dtype=np.int64)
+    np.cumsum(lengths, out=offs[1:])
+    out = np.empty(int(offs[-1]), dtype=np.int32)
+    for L in np.unique(lengths):
+        rows = np.flatnonzero(lengths == L)
+        start = centre[rows] - (L - 1) // 2
+        cams = (start[:, None] + np.arange(L)[None, :]) % C
+        # the order inside a track is random, as with drawn subsets
+        cams = np.take_along_axis(cams, rng.permuted(np.tile(np.arange(L), (rows.size, 1)), axis=1), axis=1)
+        out[(offs[rows][:, None] + np.arange(L)[None, :]).ravel()] = cams.ravel()
+    return out, offs
+
+
 def make_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = True,
                outliers: bool = True, depth_priors: bool = True,
                scale: float | None = None, shuffle: bool = True,
-               frustum_exit_frac: float = 0.0) -> Scene:
+               frustum_exit_frac: float = 0.0, covis: str | None = None) -> Scene:
     """Generate a seeded scene.
 
     `noise=False` removes pixel and depth noise, `outliers=False` removes the
     outliers, `depth_priors=False` clears every prior.  `scale` shrinks the
     camera and point counts (for reduced-size parity cases).
+
+    `covis` chooses the cameras of each track: "random" (distinct cameras drawn
+    uniformly) or "window" (the angularly nearest cameras; the default for the
+    scenes in WINDOWED).
 
     `frustum_exit_frac` injects frustum exits: that fraction of the points with
     horizontal radius >= 0.5 starts lifted to height 1.35 (+ U(0, 0.1)) above the
@@ -188,7 +215,10 @@ def make_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = 
     start and valid at the solution.  The draw comes after every other draw, so
     the rest of the scene is the same as without it."""
     if isinstance(spec, str):
+        if covis is None:
+            covis = "window" if spec in WINDOWED else "random"
         spec = SPECS[spec]
+    covis = covis or "random"
     if scale is not None:
         spec = dataclasses.replace(spec, n_cams=max(4, int(round(spec.n_cams * scale))),
                                    n_pts=max(8, int(round(spec.n_pts * scale))))
@@ -220,7 +250,10 @@ def make_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = 
 
     # tracks
     lengths = _track_lengths(rng, spec)
-    cams_flat, offs = _random_subsets(rng, C, lengths)
+    if covis == "window":
+        cams_flat, offs = _window_tracks(rng, pts_gt, C, lengths)
+    else:
+        cams_flat, offs = _random_subsets(rng, C, lengths)
     obs_pt = np.repeat(np.arange(P, dtype=np.int32), lengths)
     obs_cam = cams_flat.astype(np.int32)
     N = obs_cam.shape[0]

@@ -124,10 +124,13 @@ def test_large_workload_configured_schedule():
                 np.testing.assert_array_equal(g[key], e[key], err_msg=f"k={k0} {key}")
         seg += [step() for _ in range(k0 + 1, k1)]
         # the oracle's run of the segment from the same state, damping and drop bits
-        # (no drop inside a segment; the restart's nu is 2, as after an accepted step)
-        if k0 > 0:
-            assert rows[-1]["accepted"]
+        # (no drop inside a segment): lambda as logged, nu doubled once per reject
+        # since the last accepted step
+        rejects = 0
+        while rejects < len(rows) and not rows[-1 - rejects]["accepted"]:
+            rejects += 1
         orc.opts.lambda0 = seg[0]["lam"]
+        orc.opts.nu0 = 2.0 ** (1 + rejects)
         orc.opts.extract_every = 0
         _, _, log_o = orc.lm(cams, pts, k1 - k0, alive=alive.astype(np.uint8).copy())
         for k, (a, o) in enumerate(zip(seg, log_o), start=k0):
