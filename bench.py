@@ -129,6 +129,25 @@ def job_throughput(world, steps, max_ms):
     return world * steps / (max_ms / 1e3)
 
 
+def _covis_pairs(scene):
+    """Flags over the C x C camera pairs (i < j) that share at least one point."""
+    C = scene.spec.n_cams
+    order = np.argsort(scene.obs_pt, kind="stable")
+    cams, pts = scene.obs_cam[order].astype(np.int64), scene.obs_pt[order]
+    off = np.searchsorted(pts, np.arange(scene.spec.n_pts + 1))
+    flags = np.zeros(C * C, bool)
+    lens = np.diff(off)
+    for L in np.unique(lens):
+        rows = np.flatnonzero(lens == L)
+        if L < 2:
+            continue
+        tr = cams[(off[rows][:, None] + np.arange(L)[None, :])]
+        iu, ju = np.triu_indices(L, 1)
+        a, b = np.minimum(tr[:, iu], tr[:, ju]), np.maximum(tr[:, iu], tr[:, ju])
+        flags[(a * C + b).ravel()] = True
+    return flags
+
+
 def _workload_name(scene):
     sp = scene.spec
     return "%s scene: %d cams, %d pts, %d obs" % (sp.name, sp.n_cams, sp.n_pts, scene.n_obs)
@@ -307,7 +326,7 @@ def main():
     ap.add_argument("--no-gp", action="store_true", help="skip the global-positioning measurement")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenes.SPECS),
                     help="scene (default: the 1M-observation scene)")
-    ap.add_argument("--solver", default="auto", choices=["auto", "implicit", "explicit", "dense"])
+    ap.add_argument("--solver", default="auto", choices=["auto", "implicit", "explicit", "dense", "sparse"])
     ap.add_argument("--dense-kernels", action="store_true", help="time the tensor-core kernels only")
     args = ap.parse_args()
     if args.dense_kernels:
@@ -333,7 +352,7 @@ def main():
     scene = build_scene(args.workload)
     N = scene.n_obs
     solver = {"auto": ba.BA_SOLVER_AUTO, "implicit": ba.BA_SOLVER_IMPLICIT, "explicit": ba.BA_SOLVER_EXPLICIT,
-              "dense": ba.BA_SOLVER_DENSE}[args.solver]
+              "dense": ba.BA_SOLVER_DENSE, "sparse": ba.BA_SOLVER_SPARSE}[args.solver]
     opts = ba.Options(precision=ba.BA_FP32, solver=solver)
     prob = ba.Problem.from_scene(scene, opts, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
@@ -402,12 +421,20 @@ def main():
     mean_it = statistics.mean(i["pcg_iters"] for i in solved) if solved else 0.0
     kern_ms = statistics.mean(i["ms"][4] for i in solved) if solved else None
     kind = prob.solver_kind
-    solver_name = {ba.BA_SOLVER_DENSE: "dense", ba.BA_SOLVER_EXPLICIT: "explicit"}.get(kind, "implicit")
+    solver_name = {ba.BA_SOLVER_DENSE: "dense", ba.BA_SOLVER_EXPLICIT: "explicit",
+                   ba.BA_SOLVER_SPARSE: "sparse"}.get(kind, "implicit")
     if kind == ba.BA_SOLVER_DENSE:
         # the launch covers factorisation + CG; report the factorisation's flops
         per_launch = n ** 3 / 3.0
         kname = "dense solve: tensor-core blocked Cholesky (tcgen05 kind::tf32) + preconditioned CG"
         unit_txt = "n^3/3 flops of the factorisation, n = 9 Cf (timed launch includes the CG)"
+    elif kind == ba.BA_SOLVER_SPARSE:
+        # the stored blocks (2 per co-visible camera pair + the diagonal, 84 floats
+        # each) read by every matvec, plus the set-up reads
+        n_runs = int(np.count_nonzero(_covis_pairs(scene)))
+        per_launch = (2 * n_runs + Cf) * 336 * mean_it + 324 * Cf + 20 * n
+        kname = "k_spcg (block-sparse explicit Schur matrix, block-row matvec)"
+        unit_txt = "(2 co-visible pairs + Cf) x 336 B x iters + 324 Cf + 20 n bytes"
     elif prob.explicit_solver and prob.explicit_layout["rows_in_smem"]:
         # S^ read once (4 n^2); preconditioner blocks (324 Cf), b, D, 1/D and x (20 n).
         # The per-iteration exchange of q stays in L2.

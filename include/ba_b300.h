@@ -83,7 +83,12 @@ typedef struct {
                                   formed per damping value, block-Jacobi PCG on it),
                                   BA_SOLVER_DENSE (FP32 only: S formed, factored by the
                                   tensor-core blocked Cholesky, CG preconditioned with
-                                  that factor to pcg_rel_tol) */
+                                  that factor to pcg_rel_tol), BA_SOLVER_SPARSE (S formed
+                                  as the 9x9 blocks of co-visible camera pairs only,
+                                  block-Jacobi PCG with a block-row matvec: the sparse
+                                  co-visibility regime).  AUTO above 4608 unknowns
+                                  prices implicit, dense explicit and block-sparse per
+                                  LM step from the problem's sizes and co-visible pairs */
   int extract_mode;            /* BA_EXTRACT_DYNAMIC: step (c) at the start of every iteration
                                   whose state changed (Sec. 4.2 steps 1-3).  BA_EXTRACT_ONCE:
                                   one-shot pruning, the alternative Sec. 4.2 argues against:
@@ -92,7 +97,8 @@ typedef struct {
                                   ba_set_state start a new run and extract again */
 } ba_options;
 
-enum { BA_SOLVER_AUTO = 0, BA_SOLVER_IMPLICIT = 1, BA_SOLVER_EXPLICIT = 2, BA_SOLVER_DENSE = 3 };
+enum { BA_SOLVER_AUTO = 0, BA_SOLVER_IMPLICIT = 1, BA_SOLVER_EXPLICIT = 2, BA_SOLVER_DENSE = 3,
+       BA_SOLVER_SPARSE = 4 };
 enum { BA_EXTRACT_DYNAMIC = 0, BA_EXTRACT_ONCE = 1 };
 
 typedef struct {
@@ -258,8 +264,9 @@ ba_status ba_eval_cost_noalloc(const ba_options* opts, void* stream, int64_t n_c
  * s_k = 1/d_k, and removed from the unknowns; the others keep a free scale,
  * compacted by its rank among the free observations (ascending input order).
  * Each LM step eliminates the free scales and the points exactly and solves the
- * dense reduced centre system (order 3 x free cameras) with the tensor-core
- * Cholesky-preconditioned CG; FP32 arithmetic, the cost and gain ratio in FP64.
+ * dense reduced centre system (order 3 x free cameras) by block-Jacobi PCG or the
+ * tensor-core Cholesky-preconditioned CG (ba_gp_options.solver); FP32
+ * arithmetic, the cost and gain ratio in FP64.
  * Gauge: the centres of fixed_cams are held; the metric scale comes from the
  * pinned scales (without any, it is left to the damping).
  * ------------------------------------------------------------------------- */
@@ -267,9 +274,13 @@ typedef struct {
   double huber_delta;          /* Huber threshold on |u| (0.1); <= 0: squared loss */
   double lambda0;              /* initial damping (1e-4) */
   double pcg_rel_tol;          /* CG stop on the centre system: |r| <= tol |b| (1e-6) */
-  int pcg_max_iters;           /* CG cap (100) */
+  int pcg_max_iters;           /* CG cap (500) */
   const int32_t* fixed_cams;   /* host array of gauge cameras ({0}) */
   int n_fixed;
+  int solver;                  /* centre system: BA_SOLVER_AUTO or BA_SOLVER_EXPLICIT (block-Jacobi
+                                  PCG, three cameras per 9x9 preconditioner block, the explicit
+                                  PCG kernel of BA) or BA_SOLVER_DENSE (tensor-core Cholesky
+                                  preconditioned CG) */
 } ba_gp_options;
 
 typedef struct ba_gp_problem ba_gp_problem;
@@ -366,7 +377,8 @@ ba_status ba_selftest_layout(int64_t n_cams, const double* cams, int64_t n_pts, 
 int64_t ba_kernel_launches(const ba_problem* pb);
 
 /* The reduced-camera-system solver the problem resolved to at creation:
- * BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT or BA_SOLVER_DENSE (0 for a NULL handle). */
+ * BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT, BA_SOLVER_DENSE or BA_SOLVER_SPARSE
+ * (0 for a NULL handle). */
 int ba_solver_kind(const ba_problem* pb);
 
 /* Placement of the explicit solver's working set, fixed at creation (all

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libba_b300.so")
 BA_OK, BA_ERR_INVALID_ARG, BA_ERR_CUDA, BA_ERR_OOM = 0, 1, 2, 3
 BA_ERR_NOT_CONVERGED, BA_ERR_NONFINITE, BA_ERR_STATE, BA_ERR_TIMEOUT = 4, 5, 6, 7
 BA_FP64, BA_FP32 = 0, 1
-BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT, BA_SOLVER_DENSE = 0, 1, 2, 3
+BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT, BA_SOLVER_DENSE, BA_SOLVER_SPARSE = 0, 1, 2, 3, 4
 BA_EXTRACT_DYNAMIC, BA_EXTRACT_ONCE = 0, 1
 
 # every symbol include/ba_b300.h declares
@@ -48,7 +48,8 @@ class _Options(ct.Structure):
 
 class _GPOptions(ct.Structure):
     _fields_ = [("huber_delta", ct.c_double), ("lambda0", ct.c_double), ("pcg_rel_tol", ct.c_double),
-                ("pcg_max_iters", ct.c_int), ("fixed_cams", ct.POINTER(ct.c_int32)), ("n_fixed", ct.c_int)]
+                ("pcg_max_iters", ct.c_int), ("fixed_cams", ct.POINTER(ct.c_int32)), ("n_fixed", ct.c_int),
+                ("solver", ct.c_int)]
 
 
 class _IterInfo(ct.Structure):
@@ -454,8 +455,9 @@ class GPOptions:
     huber_delta: float = 0.1
     lambda0: float = 1e-4
     pcg_rel_tol: float = 1e-6
-    pcg_max_iters: int = 100
+    pcg_max_iters: int = 500
     fixed_cams: tuple = (0,)
+    solver: int = BA_SOLVER_AUTO  # or BA_SOLVER_EXPLICIT (block-Jacobi PCG), BA_SOLVER_DENSE (tensor cores)
 
 
 class GPProblem:
@@ -468,7 +470,7 @@ class GPProblem:
         o = self.options = options or GPOptions()
         self._fixed = np.ascontiguousarray(np.asarray(o.fixed_cams, dtype=np.int32))
         copt = _GPOptions(o.huber_delta, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
-                          self._fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(self._fixed))
+                          self._fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(self._fixed), o.solver)
         arrs = [_Arr(centres, np.float64), _Arr(pts, np.float64), _Arr(obs_cam, np.int32),
                 _Arr(obs_pt, np.int32), _Arr(rays, np.float64), _Arr(depth, np.float64)]
         s0 = None if scales0 is None else _Arr(scales0, np.float64)

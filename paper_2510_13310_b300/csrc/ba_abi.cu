@@ -120,6 +120,10 @@ struct ba_problem {
   // explicit reduced camera system
   bool explicit_S = false;
   bool dense = false;            // explicit S factored on the tensor cores (FP32)
+  bool sparse = false;           // explicit S stored as 9x9 blocks of co-visible pairs (block-sparse)
+  int* brp = nullptr;            // block rows by camera: [C + 1] offsets into bent
+  int2* bent = nullptr;          // (column camera, block slot), ascending column within a row
+  void* Bs = nullptr;            // blocks [2 n_runs + C][kBlkStride]: run r at 2r (and 2r+1 transposed), diagonals last
   DenseResult dense_last;
   DenseWork dw;
   unsigned dense_epoch = 0;
@@ -476,8 +480,9 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   if (Cf > 0) {
     LAUNCH(3, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
                                (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
-                               Cf, (T*)pb->Yhat, (T*)pb->Shat, pb->form_lanes, pb->num_sms, pb->evf[0],
-                               pb->evf[1], pb->join_pending ? pb->join : nullptr, pb->stream));
+                               Cf, (T*)pb->Yhat, pb->sparse ? (T*)pb->Bs : (T*)pb->Shat, pb->form_lanes,
+                               pb->num_sms, pb->evf[0], pb->evf[1], pb->join_pending ? pb->join : nullptr,
+                               pb->stream, pb->cam_map, pb->sparse));
     pb->evf_valid = true;
     pb->join_pending = false;  // launch_form_S made the main stream wait for the chain
     bool solved = false;
@@ -527,7 +532,15 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     a.tol = pb->opt.pcg_rel_tol;
     a.max_iters = pb->opt.pcg_max_iters;
     a.timeout_ns = 2000000000LL;
-    const int grid = std::max(1, std::min(pb->spcg_grid, (a.n + 7) / 8));
+    if (pb->sparse) {
+      a.brp = pb->brp;
+      a.bent = pb->bent;
+      a.Bs = (const T*)pb->Bs;
+      a.crank = pb->crank;
+      a.cam_map = pb->cam_map;
+    }
+    // the block-sparse kernel owns whole cameras: at least one per block
+    const int grid = std::max(1, std::min(pb->spcg_grid, pb->sparse ? Cf : (a.n + 7) / 8));
     const size_t smem = spcg_smem_bytes<T>(a.n, (a.n + grid - 1) / grid, a.rows_in_smem, a.vecs_in_smem, Cf);
     if (smem > pb->spcg_smem) {
       set_error("explicit PCG launch needs %zu B of shared memory (planned %zu)", smem, pb->spcg_smem);
@@ -1057,9 +1070,12 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   // FP32 recomputes the W blocks inside the Schur matvec from a signed IRLS weight
   // per observation; FP64 stores them (FP64 arithmetic is the scarce resource there)
   pb->recompute = pb->fp64 ? 0 : 1;
+  bool auto_sparse_cand = false;
+  double auto_t_exp = 1e300, auto_t_imp = 1e300, auto_pairs = 0.0;
   {
     int so = opts->solver;
-    if (so != BA_SOLVER_AUTO && so != BA_SOLVER_IMPLICIT && so != BA_SOLVER_EXPLICIT && so != BA_SOLVER_DENSE) {
+    if (so != BA_SOLVER_AUTO && so != BA_SOLVER_IMPLICIT && so != BA_SOLVER_EXPLICIT && so != BA_SOLVER_DENSE &&
+        so != BA_SOLVER_SPARSE) {
       set_error("unknown solver %d", so);
       return BA_ERR_INVALID_ARG;
     }
@@ -1096,10 +1112,17 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
         const double t_imp = it * (N * 66e-12 + P * 245e-12);
         // and only within the explicit system's memory bound below
         auto_explicit = t_exp < t_imp && (size_t)81 * C * C * (R + 8) <= ((size_t)8 << 30);
+        // the block-sparse system is priced once the co-visibility runs are known
+        auto_sparse_cand = true;
+        auto_t_exp = auto_explicit ? t_exp : 1e300;
+        auto_t_imp = t_imp;
+        auto_pairs = pairs;
       }
     }
-    pb->explicit_S = dense || so == BA_SOLVER_EXPLICIT || auto_explicit;
-    if (pb->explicit_S && (size_t)81 * C * C * (R + (dense ? 4 : 8)) > ((size_t)(dense ? 24 : 8) << 30)) {
+    pb->sparse = so == BA_SOLVER_SPARSE;
+    pb->explicit_S = dense || so == BA_SOLVER_EXPLICIT || pb->sparse || auto_explicit || auto_sparse_cand;
+    if (pb->explicit_S && !pb->sparse && !auto_sparse_cand &&
+        (size_t)81 * C * C * (R + (dense ? 4 : 8)) > ((size_t)(dense ? 24 : 8) << 30)) {
       set_error("explicit reduced camera system of order %d is too large", 9 * C);
       return BA_ERR_INVALID_ARG;
     }
@@ -1173,28 +1196,63 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   ST(dalloc(pb, &pb->dots, (size_t)2 * 4 * pb->pcg_grid));
   ST(dalloc(pb, &pb->bar, 1));
   ST(dalloc(pb, &pb->err, 1));
+  // co-visibility runs: every pair of observations of one point in cameras i < j,
+  // grouped by (i, j), ascending in point within a run (device); the explicit
+  // systems are formed over them
+  if (pb->explicit_S && n_max > 0) {
+    DevCovis cv;
+    std::string msg;
+    const int rc = build_covis_runs_dev(dl, C, N, dev_alloc, pb->stream, &cv, &msg);
+    if (rc) {
+      set_error("%s", msg.c_str());
+      return rc == 1 ? BA_ERR_INVALID_ARG : rc == 3 ? BA_ERR_OOM : BA_ERR_CUDA;
+    }
+    pb->covis_pairs = cv.pairs;
+    pb->covis_runs = cv.runs;
+    pb->n_covis_runs = cv.n_runs;
+    // one lane per run when there are enough runs for four blocks of 128 lanes
+    // per SM and runs are short (a warp per run would idle in its reduction)
+    pb->form_lanes = (long long)cv.n_runs >= 4LL * 128 * pb->num_sms && cv.npairs < 128 * (size_t)cv.n_runs;
+    if (auto_sparse_cand) {
+      // AUTO, priced now that the co-visible camera pairs are known: the
+      // block-sparse system forms the same blocks and streams its 2 n_runs + C
+      // stored blocks per PCG iteration (~4 TB/s from L2 and HBM) + 8 us
+      const double nblk = 2.0 * cv.n_runs + C, it = 40.0;
+      const double t_sp = auto_pairs * 0.1e-9 + N * 50e-12 + it * (nblk * kBlkStride * R / 4e12 + 8e-6);
+      if (t_sp < auto_t_exp && t_sp < auto_t_imp) pb->sparse = true;
+      else if (!(auto_t_exp < auto_t_imp)) pb->explicit_S = false;
+    }
+    if (pb->sparse && (size_t)(2 * (size_t)cv.n_runs + C) * kBlkStride * R > ((size_t)16 << 30)) {
+      set_error("block-sparse reduced camera system of %d blocks is too large", 2 * cv.n_runs + C);
+      return BA_ERR_INVALID_ARG;
+    }
+    if (pb->sparse) {
+      // block rows by camera: the transposed blocks of runs (j, c) (ascending j < c),
+      // the diagonal block, the blocks of runs (c, j) (ascending j > c)
+      std::vector<int4> h_runs((size_t)cv.n_runs);
+      if (cv.n_runs)
+        CU(cudaMemcpy(h_runs.data(), cv.runs, sizeof(int4) * (size_t)cv.n_runs, cudaMemcpyDeviceToHost));
+      std::vector<int> rp((size_t)C + 1, 0), fill;
+      for (const int4& r : h_runs) rp[r.x + 1]++, rp[r.y + 1]++;
+      for (int c = 0; c < C; ++c) rp[c + 1] += rp[c] + 1;
+      fill.assign(rp.begin(), rp.end() - 1);
+      std::vector<int2> ent((size_t)rp[C]);
+      for (int r = 0; r < cv.n_runs; ++r) ent[fill[h_runs[r].y]++] = make_int2(h_runs[r].x, 2 * r + 1);
+      for (int c = 0; c < C; ++c) ent[fill[c]++] = make_int2(c, 2 * cv.n_runs + c);
+      for (int r = 0; r < cv.n_runs; ++r) ent[fill[h_runs[r].x]++] = make_int2(h_runs[r].y, 2 * r);
+      ST(dalloc(pb, &pb->brp, (size_t)C + 1));
+      ST(dalloc(pb, &pb->bent, ent.size()));
+      CU(cudaMemcpy(pb->brp, rp.data(), sizeof(int) * rp.size(), cudaMemcpyHostToDevice));
+      if (!ent.empty()) CU(cudaMemcpy(pb->bent, ent.data(), sizeof(int2) * ent.size(), cudaMemcpyHostToDevice));
+      ST(dalloc_bytes(pb, &pb->Bs, R * kBlkStride * (2 * (size_t)cv.n_runs + C)));
+    }
+  }
   // explicit reduced camera system (solver option; automatic for up to 512 cameras)
   if (pb->explicit_S && n_max > 0) {
-    ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * (pb->fp64 ? spcg_row_stride<double>(n_max) : spcg_row_stride<float>(n_max))));
+    if (!pb->sparse)
+      ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * (pb->fp64 ? spcg_row_stride<double>(n_max) : spcg_row_stride<float>(n_max))));
     ST(dalloc_bytes(pb, &pb->Yhat, R * (size_t)kWStride * ((size_t)N + 1)));
     ST(dalloc_bytes(pb, &pb->bs_wx, R * 3 * std::max<size_t>(N, 1)));  // W_k^T dc per observation
-    // co-visibility runs: every pair of observations of one point in cameras i < j,
-    // grouped by (i, j), ascending in point within a run (device)
-    {
-      DevCovis cv;
-      std::string msg;
-      const int rc = build_covis_runs_dev(dl, C, N, dev_alloc, pb->stream, &cv, &msg);
-      if (rc) {
-        set_error("%s", msg.c_str());
-        return rc == 1 ? BA_ERR_INVALID_ARG : rc == 3 ? BA_ERR_OOM : BA_ERR_CUDA;
-      }
-      pb->covis_pairs = cv.pairs;
-      pb->covis_runs = cv.runs;
-      pb->n_covis_runs = cv.n_runs;
-      // one lane per run when there are enough runs for four blocks of 128 lanes
-      // per SM and runs are short (a warp per run would idle in its reduction)
-      pb->form_lanes = (long long)cv.n_runs >= 4LL * 128 * pb->num_sms && cv.npairs < 128 * (size_t)cv.n_runs;
-    }
     ST(dalloc(pb, &pb->dscale, (size_t)2 * n_max));  // D, then 1/D in the working precision
     ST(dalloc_bytes(pb, &pb->Dblk, R * 45 * (size_t)C));
     if (pb->dense) {
@@ -1221,7 +1279,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
                         : spcg_smem_bytes<float>(n_max, rows_max, rows_in, vecs_in, C);
       };
       pb->spcg_rows_in_smem = pb->spcg_vecs_in_smem = 1;
-      if (bytes(1, 1) > (size_t)dev_smem_optin) pb->spcg_rows_in_smem = 0;
+      if (pb->sparse || bytes(1, 1) > (size_t)dev_smem_optin) pb->spcg_rows_in_smem = 0;
       if (!pb->spcg_rows_in_smem && bytes(0, 1) > (size_t)dev_smem_optin) pb->spcg_vecs_in_smem = 0;
       pb->spcg_smem = bytes(pb->spcg_rows_in_smem, pb->spcg_vecs_in_smem);
       if (pb->spcg_smem > (size_t)dev_smem_optin) {
@@ -1243,7 +1301,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       CU(cudaMemset(pb->spcg_words, 0, sizeof(unsigned long long) * nw));
     }
     const bool rs = pb->spcg_rows_in_smem != 0;
-    const void* sfn = pb->fp64 ? spcg_kernel_ptr<double>(rs) : spcg_kernel_ptr<float>(rs);
+    const void* sfn = pb->fp64 ? spcg_kernel_ptr<double>(rs, pb->sparse) : spcg_kernel_ptr<float>(rs, pb->sparse);
     CU(cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb->spcg_smem));
     int sper = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, sfn, spcg_threads(), pb->spcg_smem));
@@ -1826,7 +1884,8 @@ int64_t ba_kernel_launches(const ba_problem* pb) { return pb ? pb->launches : 0;
 
 int ba_solver_kind(const ba_problem* pb) {
   if (!pb) return 0;
-  return pb->dense ? BA_SOLVER_DENSE : pb->explicit_S ? BA_SOLVER_EXPLICIT : BA_SOLVER_IMPLICIT;
+  return pb->dense ? BA_SOLVER_DENSE : pb->sparse ? BA_SOLVER_SPARSE : pb->explicit_S ? BA_SOLVER_EXPLICIT
+                                                                                    : BA_SOLVER_IMPLICIT;
 }
 
 void ba_explicit_layout(const ba_problem* pb, int* rows_in_smem, int* vecs_in_smem, int* grid) {

@@ -293,6 +293,71 @@ __global__ void __launch_bounds__(kThreads) k_gp_form_S(int n_runs, const int4* 
   }
 }
 
+// Identity rows of the padding that makes the centre system a whole number of
+// 9-unknown super-blocks (three cameras each) for the block-Jacobi PCG.
+__global__ void k_gp_pad(int n, int n_pad, float* Sh, long long ld) {
+  const int r = n + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n_pad) Sh[(size_t)r * ld + r] = 1.f;
+}
+
+// Block-Jacobi preconditioner of the scaled centre system: the inverse of each
+// 9x9 diagonal super-block, by Cholesky factorisation (FP32, one thread per block;
+// a block that fails to factor falls back to the inverse diagonal).
+__global__ void k_gp_superblock_inv(int Cs, const float* __restrict__ Sh, long long ld, float* __restrict__ Dinv) {
+  const int sb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sb >= Cs) return;
+  float L[81], Inv[81];
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j) L[9 * i + j] = Sh[(size_t)(9 * sb + i) * ld + 9 * sb + j];
+  bool ok = true;
+  for (int j = 0; j < 9 && ok; ++j) {
+    float d = L[9 * j + j];
+    for (int k = 0; k < j; ++k) d -= L[9 * j + k] * L[9 * j + k];
+    if (!(d > 0.f)) {
+      ok = false;
+      break;
+    }
+    d = sqrtf(d);
+    L[9 * j + j] = d;
+    for (int i = j + 1; i < 9; ++i) {
+      float v = L[9 * i + j];
+      for (int k = 0; k < j; ++k) v -= L[9 * i + k] * L[9 * j + k];
+      L[9 * i + j] = v / d;
+    }
+  }
+  if (ok) {
+    // columns of (L L^T)^-1: forward then backward substitution of each unit vector
+    for (int c = 0; c < 9; ++c) {
+      float y[9];
+      for (int i = 0; i < 9; ++i) {
+        float v = i == c ? 1.f : 0.f;
+        for (int k = 0; k < i; ++k) v -= L[9 * i + k] * y[k];
+        y[i] = v / L[9 * i + i];
+      }
+      for (int i = 8; i >= 0; --i) {
+        float v = y[i];
+        for (int k = i + 1; k < 9; ++k) v -= L[9 * k + i] * Inv[9 * k + c];
+        Inv[9 * i + c] = v / L[9 * i + i];
+      }
+    }
+  } else {
+    for (int i = 0; i < 81; ++i) Inv[i] = 0.f;
+    for (int i = 0; i < 9; ++i) {
+      const float d = Sh[(size_t)(9 * sb + i) * ld + 9 * sb + i];
+      Inv[10 * i] = d > 0.f ? 1.f / d : 1.f;
+    }
+  }
+  for (int i = 0; i < 81; ++i) Dinv[81 * (size_t)sb + i] = Inv[i];
+}
+
+__global__ void k_gp_ones(int n, double* __restrict__ dscale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    dscale[i] = 1.0;
+    reinterpret_cast<float*>(dscale + n)[i] = 1.f;
+  }
+}
+
 __global__ void k_gp_scale(int n, const float* __restrict__ a, const float* __restrict__ d, float* __restrict__ o) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) o[i] = a[i] * d[i];
@@ -558,6 +623,17 @@ struct ba_gp_problem {
   float *xh = nullptr, *dt = nullptr, *ds = nullptr;
   double *pred_parts = nullptr, *eval_parts = nullptr, *scales_out = nullptr, *steps_out = nullptr;
   int bs_grid = 1, eval_grid = 1;
+  // centre-system solver: block-Jacobi PCG on 9-unknown super-blocks (three
+  // cameras) with the explicit PCG kernel, or the tensor-core dense solve
+  bool use_dense = false;
+  int Cs = 0, n_pad = 0;
+  float* Dinv = nullptr;         // [Cs][81] inverses of the diagonal super-blocks
+  double* dscale = nullptr;      // unit scaling for the PCG kernel (the system is scaled already)
+  float *pcg_scratch = nullptr, *pcg_M = nullptr;
+  size_t pcg_scratch_stride = 0, pcg_smem = 0;
+  int pcg_grid = 1, pcg_rows_in_smem = 1, pcg_vecs_in_smem = 1;
+  unsigned long long* words = nullptr;
+  unsigned tag = 1;
   DenseWork dw;
   unsigned dense_epoch = 0;
   Scalars* sc = nullptr;
@@ -802,19 +878,60 @@ ba_status gp_create_impl(const ba_gp_options* opts, void* stream, int64_t n_cams
   GST(galloc(pb, &pb->Sdiag, (size_t)6 * pb->Cf));
   GST(galloc(pb, &pb->camrec, (size_t)pb->Cf));
   GST(galloc(pb, &pb->b, (size_t)pb->n));
-  GST(galloc(pb, &pb->bh, (size_t)pb->n));
-  GST(galloc(pb, &pb->xh, (size_t)pb->n));
+  GST(galloc(pb, &pb->bh, (size_t)std::max(pb->n_pad, pb->n)));
+  GST(galloc(pb, &pb->xh, (size_t)std::max(pb->n_pad, pb->n)));
   GST(galloc(pb, &pb->dt, (size_t)pb->n));
   GST(galloc(pb, &pb->dsc, (size_t)pb->n));
   GST(galloc(pb, &pb->dX, (size_t)P));
   GST(galloc(pb, &pb->ds, (size_t)pb->F));
-  pb->ld = ((long long)pb->n + 3) / 4 * 4;
-  if ((size_t)pb->n * pb->ld * 4 > ((size_t)16 << 30)) {
-    gp_error("centre system of order %d is too large for the dense solve", pb->n);
+  pb->use_dense = opts->solver == BA_SOLVER_DENSE;
+  if (opts->solver != BA_SOLVER_AUTO && opts->solver != BA_SOLVER_EXPLICIT && opts->solver != BA_SOLVER_DENSE) {
+    gp_error("GP solver must be BA_SOLVER_AUTO, BA_SOLVER_EXPLICIT or BA_SOLVER_DENSE");
     return BA_ERR_INVALID_ARG;
   }
-  GST(galloc(pb, &pb->Sh, (size_t)pb->n * pb->ld));
-  {
+  pb->Cs = (pb->Cf + 2) / 3;
+  pb->n_pad = 9 * pb->Cs;
+  pb->ld = spcg_row_stride<float>(std::max(pb->n_pad, 1));
+  if ((size_t)pb->n_pad * pb->ld * 4 > ((size_t)16 << 30)) {
+    gp_error("centre system of order %d is too large for the explicit solve", pb->n);
+    return BA_ERR_INVALID_ARG;
+  }
+  GST(galloc(pb, &pb->Sh, (size_t)std::max(pb->n_pad, 1) * pb->ld));
+  if (!pb->use_dense && pb->Cf > 0) {
+    const int n = pb->n_pad;
+    GST(galloc(pb, &pb->Dinv, (size_t)81 * pb->Cs));
+    GST(galloc(pb, &pb->dscale, (size_t)2 * n));
+    GLAUNCH(pb, 1, gpk::k_gp_ones<<<gpk::blocks(n, 256), 256, 0, pb->stream>>>(n, pb->dscale));
+    const size_t nw = (size_t)2 * n * spcg_words_per_value(false);
+    GST(galloc(pb, &pb->words, nw));
+    GCU(cudaMemsetAsync(pb->words, 0, sizeof(unsigned long long) * nw, pb->stream));
+    int optin = 0;
+    GCU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pb->device));
+    pb->pcg_grid = std::max(1, std::min(pb->num_sms, (n + 7) / 8));
+    const int rows_max = std::max(8, (n + pb->pcg_grid - 1) / pb->pcg_grid);
+    auto bytes = [&](int ri, int vi) { return spcg_smem_bytes<float>(n, rows_max, ri, vi, pb->Cs); };
+    if (bytes(1, 1) > (size_t)optin) pb->pcg_rows_in_smem = 0;
+    if (!pb->pcg_rows_in_smem && bytes(0, 1) > (size_t)optin) pb->pcg_vecs_in_smem = 0;
+    pb->pcg_smem = bytes(pb->pcg_rows_in_smem, pb->pcg_vecs_in_smem);
+    if (pb->pcg_smem > (size_t)optin) {
+      gp_error("centre system PCG of order %d needs %zu B of shared memory per block", n, pb->pcg_smem);
+      return BA_ERR_INVALID_ARG;
+    }
+    if (!pb->pcg_vecs_in_smem) {
+      pb->pcg_scratch_stride = (size_t)4 * spcg_row_stride<float>(n);
+      GST(galloc(pb, &pb->pcg_scratch, pb->pcg_scratch_stride * pb->pcg_grid));
+      GST(galloc(pb, &pb->pcg_M, (size_t)kSpcgMStride * pb->Cs));
+    }
+    const void* fn = spcg_kernel_ptr<float>(pb->pcg_rows_in_smem != 0);
+    GCU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb->pcg_smem));
+    int per = 0;
+    GCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, spcg_threads(), pb->pcg_smem));
+    if (per < 1 || pb->pcg_grid > per * pb->num_sms) {
+      gp_error("centre system PCG kernel cannot be resident");
+      return BA_ERR_INVALID_ARG;
+    }
+  }
+  if (pb->use_dense) {
     const size_t np = ((size_t)pb->n + 127) / 128 * 128;
     GST(galloc(pb, &pb->dw.A, np * np));
     GST(galloc(pb, &pb->dw.Linv, np * 128));
@@ -869,17 +986,62 @@ ba_status gp_solve_damped(ba_gp_problem* pb, double lambda, DenseResult* dres) {
   if (Cf) {
     GLAUNCH(pb, 1, gpk::k_gp_cam_finish<<<gpk::blocks(Cf, 128), 128, 0, pb->stream>>>(
                        Cf, pb->cam_map, pb->cam_chunk, pb->part, lam, pb->Sdiag, pb->b, pb->dsc, pb->camrec, pb->err));
-    GCU(cudaMemsetAsync(pb->Sh, 0, sizeof(float) * (size_t)n * pb->ld, pb->stream));
+    GCU(cudaMemsetAsync(pb->Sh, 0, sizeof(float) * (size_t)pb->n_pad * pb->ld, pb->stream));
+    if (pb->n_pad > n)
+      GLAUNCH(pb, 1, gpk::k_gp_pad<<<1, 32, 0, pb->stream>>>(n, pb->n_pad, pb->Sh, pb->ld));
     GLAUNCH(pb, 1, gpk::k_gp_S_diag<<<gpk::blocks(Cf, 128), 128, 0, pb->stream>>>(Cf, pb->Sdiag, pb->dsc, pb->Sh, pb->ld));
     if (pb->n_runs)
       GLAUNCH(pb, 1, gpk::k_gp_form_S<<<std::min(gpk::blocks(pb->n_runs, 4), 32 * pb->num_sms), gpk::kThreads, 0,
                                         pb->stream>>>(pb->n_runs, pb->runs, pb->pairs, pb->crank, pb->rec, pb->Y,
                                                       pb->dsc, pb->Sh, pb->ld));
+    if (pb->n_pad > n) GCU(cudaMemsetAsync(pb->bh + n, 0, sizeof(float) * (pb->n_pad - n), pb->stream));
     GLAUNCH(pb, 1, gpk::k_gp_scale<<<gpk::blocks(n, 256), 256, 0, pb->stream>>>(n, pb->b, pb->dsc, pb->bh));
     GCU(cudaEventRecord(pb->ev[2], pb->stream));
-    GCU(dense_spd_solve(pb->dw, pb->Sh, pb->ld, n, pb->bh, pb->xh, pb->opt.pcg_rel_tol, pb->opt.pcg_max_iters,
-                        pb->num_sms, pb->stream, dres));
-    pb->launches += dres->launches;
+    if (pb->use_dense) {
+      GCU(dense_spd_solve(pb->dw, pb->Sh, pb->ld, n, pb->bh, pb->xh, pb->opt.pcg_rel_tol, pb->opt.pcg_max_iters,
+                          pb->num_sms, pb->stream, dres));
+      pb->launches += dres->launches;
+    } else {
+      // block-Jacobi PCG on the scaled system with the explicit PCG kernel: three
+      // cameras form one of its 9-unknown blocks; unit scaling (already scaled)
+      GLAUNCH(pb, 1, gpk::k_gp_superblock_inv<<<gpk::blocks(pb->Cs, 64), 64, 0, pb->stream>>>(pb->Cs, pb->Sh, pb->ld,
+                                                                                              pb->Dinv));
+      SpcgArgs<float> a{};
+      a.Shat = pb->Sh;
+      a.Dinv = pb->Dinv;
+      a.dscale = pb->dscale;
+      a.b = pb->bh;
+      a.Cf = pb->Cs;
+      a.n = pb->n_pad;
+      a.rows_in_smem = pb->pcg_rows_in_smem;
+      a.vecs_in_smem = pb->pcg_vecs_in_smem;
+      a.scratch = pb->pcg_scratch;
+      a.scratch_stride = pb->pcg_scratch_stride;
+      a.Mshared = nullptr;
+      if (pb->pcg_M) {
+        GCU(launch_spcg_precond<float>(pb->Cs, pb->Dinv, pb->dscale, pb->pcg_M, pb->stream));
+        pb->launches += 1;
+        a.Mshared = pb->pcg_M;
+      }
+      a.x = pb->xh;
+      a.words = pb->words;
+      a.err = pb->err;
+      a.sc = pb->sc;
+      a.tol = pb->opt.pcg_rel_tol;
+      a.max_iters = pb->opt.pcg_max_iters;
+      a.timeout_ns = 2000000000LL;
+      const unsigned span = (unsigned)a.max_iters + 2u;
+      if (pb->tag == 0 || pb->tag > 0xFFFFFFFFu - span) {
+        GCU(cudaMemsetAsync(pb->words, 0, sizeof(unsigned long long) * 2 * (size_t)pb->n_pad *
+                                              spcg_words_per_value(false), pb->stream));
+        pb->tag = 1;
+      }
+      a.tag_base = pb->tag;
+      pb->tag += span;
+      GCU(launch_spcg<float>(a, pb->pcg_grid, pb->pcg_smem, pb->stream));
+      pb->launches += 1;
+      dres->iters = -1;  // read back with the scalars
+    }
     GLAUNCH(pb, 1, gpk::k_gp_scale<<<gpk::blocks(n, 256), 256, 0, pb->stream>>>(n, pb->xh, pb->dsc, pb->dt));
   } else {
     GCU(cudaEventRecord(pb->ev[2], pb->stream));
@@ -912,9 +1074,13 @@ ba_status gp_lm_step(ba_gp_problem* pb, ba_iter_info* info) {
   GCU(cudaMemcpyAsync(&h_err, pb->err, sizeof(int), cudaMemcpyDeviceToHost, pb->stream));
   GST(gp_sync(pb));
   const Scalars& sc = *pb->h_sc;
+  if (dres.iters < 0) {  // the PCG kernel's own count and residual
+    dres.iters = sc.pcg_iters;
+    dres.rel_res = sc.pcg_rel_res;
+  }
   const double F = sc.cost[s], Fc = sc.cost[d], pred = sc.pred;
   const double gain = (F - Fc) / pred;
-  const bool timeout = (dres.flags & 16) != 0;
+  const bool timeout = (dres.flags & 16) != 0 || (h_err & 1) != 0;
   const bool ok = std::isfinite(Fc) && std::isfinite(gain) && pred > 0.0 && !timeout && !(h_err & 4);
   const bool accept = ok && gain > 1e-3;
   if (info) {
@@ -966,9 +1132,10 @@ void ba_gp_default_options(ba_gp_options* o) {
   o->huber_delta = 0.1;
   o->lambda0 = 1e-4;
   o->pcg_rel_tol = 1e-6;
-  o->pcg_max_iters = 100;
+  o->pcg_max_iters = 500;
   o->fixed_cams = kGauge;
   o->n_fixed = 1;
+  o->solver = BA_SOLVER_AUTO;
 }
 
 ba_status ba_gp_create(const ba_gp_options* opts, void* stream, int64_t n_cams, const double* centres,
@@ -1056,8 +1223,8 @@ ba_status ba_gp_solve_damped(ba_gp_problem* pb, double lambda, double* dt, doubl
     memset(info, 0, sizeof *info);
     info->lambda = lambda;
     info->pred_decrease = pb->h_sc->pred;
-    info->pcg_iters = dres.iters;
-    info->pcg_rel_res = dres.rel_res;
+    info->pcg_iters = dres.iters < 0 ? pb->h_sc->pcg_iters : dres.iters;
+    info->pcg_rel_res = dres.iters < 0 ? pb->h_sc->pcg_rel_res : dres.rel_res;
   }
   return BA_OK;
 }

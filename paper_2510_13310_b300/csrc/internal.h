@@ -114,7 +114,17 @@ struct SpcgArgs {
   double tol;
   int max_iters;
   long long timeout_ns;
+  // block-sparse S^ (nullable otherwise): block rows by camera, entries (column
+  // camera, block slot), blocks of kBlkStride entries; ranks and their cameras
+  const int* brp;
+  const int2* bent;
+  const T* Bs;
+  const int* crank;
+  const int* cam_map;
 };
+// entries per stored 9x9 block of the block-sparse system (row-major, padded to
+// 16 bytes in FP32)
+constexpr int kBlkStride = 84;
 
 // message returned by ba_last_error() for the calling thread
 void set_last_error_message(const char* msg);
@@ -216,8 +226,10 @@ template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
                           int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaEvent_t ev0, cudaEvent_t ev1,
-                          cudaEvent_t join, cudaStream_t s);  // join (nullable): waited on before the
+                          cudaEvent_t join, cudaStream_t s,   // join (nullable): waited on before the
                                                               // diagonal blocks are written
+                          const int* cam_map = nullptr,       // sparse: Shat is the block storage
+                          bool sparse = false);
 template <typename T>
 cudaError_t launch_dscale(int Cf, const int* cam_map, const T* Ug, double lambda, double* dscale, cudaStream_t s);
 template <typename T>
@@ -230,7 +242,7 @@ __host__ __device__ inline int spcg_row_stride(int n) {
 template <typename T>
 __host__ __device__ size_t spcg_vec_elems(int n, int Cf);
 template <typename T>
-const void* spcg_kernel_ptr(bool rows_in_smem);
+const void* spcg_kernel_ptr(bool rows_in_smem, bool sparse = false);
 template <typename T>
 cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
 // the explicit PCG's preconditioner blocks into M [Cf][kSpcgMStride], for a shared copy

@@ -155,7 +155,9 @@ __device__ __forceinline__ void rs_round(T (&v)[96], int lane, int r) {
 // cameras are not both free are skipped.
 // Three 128-thread blocks per SM: 81 accumulators and two 27-entry rows per lane
 // fit without spilling (four blocks force 128 registers and spill: 19% slower).
-template <typename T>
+// kSparse: Shat is the block storage of the block-sparse system: run r's block
+// goes to slot 2 r and its transpose to slot 2 r + 1 (kBlkStride entries each).
+template <typename T, bool kSparse>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
     k_form_S_runs(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
                   const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat) {
@@ -200,7 +202,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
       const int t = base + j;
       if (t < 81) {
         const int r = t / 9, s2 = t - 9 * r;
-        Shat[(size_t)(9 * a + r) * ld + 9 * b + s2] = -v[j];
+        if constexpr (kSparse) {
+          Shat[(size_t)kBlkStride * (2 * (size_t)ri) + 9 * r + s2] = -v[j];
+          Shat[(size_t)kBlkStride * (2 * (size_t)ri + 1) + 9 * s2 + r] = -v[j];
+        } else {
+          Shat[(size_t)(9 * a + r) * ld + 9 * b + s2] = -v[j];
+        }
       }
     }
   }
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
 // (every camera pair sharing a few dozen points): each lane accumulates its run
 // in registers and writes the 81 entries itself, so no cross-lane reduction is
 // needed; lanes of a warp take consecutive runs of similar length.
-template <typename T>
+template <typename T, bool kSparse>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
     k_form_S_lanes(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
                    const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat) {
@@ -241,8 +248,28 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
 #pragma unroll
     for (int r = 0; r < 9; ++r)
 #pragma unroll
-      for (int s2 = 0; s2 < 9; ++s2) Shat[(size_t)(9 * a + r) * ld + 9 * b + s2] = -acc[9 * r + s2];
+      for (int s2 = 0; s2 < 9; ++s2) {
+        if constexpr (kSparse) {
+          Shat[(size_t)kBlkStride * (2 * (size_t)ri) + 9 * r + s2] = -acc[9 * r + s2];
+          Shat[(size_t)kBlkStride * (2 * (size_t)ri + 1) + 9 * s2 + r] = -acc[9 * r + s2];
+        } else {
+          Shat[(size_t)(9 * a + r) * ld + 9 * b + s2] = -acc[9 * r + s2];
+        }
+      }
   }
+}
+
+// Diagonal blocks of the block-sparse system, scaled: slot 2 n_runs + c for the
+// camera c of rank f, from the packed block-Jacobi block D_f.
+template <typename T>
+__global__ void k_S_diag_blocks(int Cf, const int* __restrict__ cam_map, const T* __restrict__ Dblk,
+                                const double* __restrict__ dscale, int n_runs, T* __restrict__ Bs) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 81 * Cf) return;
+  const int f = e / 81, t = e - 81 * f, r = t / 9, c = t - 9 * r;
+  const T* di = reinterpret_cast<const T*>(dscale + 9 * (size_t)Cf);
+  Bs[(size_t)kBlkStride * (2 * (size_t)n_runs + cam_map[f]) + t] =
+      Dblk[45 * (size_t)f + sym9(r, c)] * di[9 * f + r] * di[9 * f + c];
 }
 
 // Diagonal blocks from the block-Jacobi blocks D_a = U*_a - sum W V*^-1 W^T (packed),
@@ -308,13 +335,17 @@ template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
                           int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaEvent_t ev0, cudaEvent_t ev1,
-                          cudaEvent_t join, cudaStream_t s) {
+                          cudaEvent_t join, cudaStream_t s, const int* cam_map, bool sparse) {
   if (Cf <= 0) return cudaSuccess;
   const int n = 9 * Cf;
   // dscale (D and 1/D) was written by the Schur-diagonal kernel
   if (L.N > 0) k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
-  cudaError_t e = cudaMemsetAsync(Shat, 0, sizeof(T) * (size_t)n * spcg_row_stride<T>(n), s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  // the dense system is cleared (blocks of pairs that share no point stay zero);
+  // the block-sparse one stores only written blocks (the matvec skips blocks
+  // whose cameras are not both free)
+  if (!sparse && (e = cudaMemsetAsync(Shat, 0, sizeof(T) * (size_t)n * spcg_row_stride<T>(n), s)) != cudaSuccess)
+    return e;
   // events (nullable) around the co-visibility product kernel
   if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
   if (n_runs > 0) {
@@ -323,19 +354,25 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
       // many short runs: one lane per run
       int grid = (n_runs + 127) / 128;
       if (grid > 16 * num_sms) grid = 16 * num_sms;  // (a resident-only grid measured slower here)
-      k_form_S_lanes<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
+      if (sparse) k_form_S_lanes<T, true><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
+      else k_form_S_lanes<T, false><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
     } else {
       // resident blocks only (three per SM in FP32), striding over the runs: no
       // partly filled last wave
       int grid = (n_runs + wpb - 1) / wpb;
       const int resident = (sizeof(T) == 4 ? 3 : 1) * num_sms;
       if (grid > resident) grid = resident;
-      k_form_S_runs<T><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
+      if (sparse) k_form_S_runs<T, true><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
+      else k_form_S_runs<T, false><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
     }
   }
   if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
   // the diagonal blocks come from the Schur-diagonal kernel (on another stream when `join`)
   if (join && (e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
+  if (sparse) {
+    k_S_diag_blocks<T><<<(81 * Cf + 255) / 256, 256, 0, s>>>(Cf, cam_map, Dblk, dscale, n_runs, Shat);
+    return cudaGetLastError();
+  }
   int nt = (n + 31) / 32;
   k_S_finalize<T><<<dim3(nt, nt), dim3(32, 8), 0, s>>>(Cf, Dblk, dscale, Shat);
   return cudaGetLastError();
@@ -601,14 +638,17 @@ cudaError_t launch_spcg_precond(int Cf, const T* Dinv, const double* dscale, T* 
 // t handles the vector entries of cameras t, t + 512, ...
 // kRows: the block's rows of S^ sit in shared memory (else streamed from device
 // memory by every matvec); one instance per placement keeps registers in check
-template <typename T, bool kRows>
+// kSparse: the block-sparse system; block b owns whole cameras (ranks
+// [Cf b / G, Cf (b+1) / G)) and forms their rows of q from the stored blocks.
+template <typename T, bool kRows, bool kSparse>
 __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int W = spcg_words<T>();
   const int G = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int n = a.n, ns = spcg_row_stride<T>(n), Cf = a.Cf;
-  const int r0 = (int)(((long long)n * bid) / G), r1 = (int)(((long long)n * (bid + 1)) / G);
+  const int r0 = kSparse ? 9 * (int)(((long long)Cf * bid) / G) : (int)(((long long)n * bid) / G);
+  const int r1 = kSparse ? 9 * (int)(((long long)Cf * (bid + 1)) / G) : (int)(((long long)n * (bid + 1)) / G);
   const int nr = r1 - r0;
   unsigned char* sp = smem_raw;
   T* red = reinterpret_cast<T*>(sp);
@@ -689,6 +729,36 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     const size_t set_words = (size_t)n * W;
     unsigned long long* set = words + (size_t)(it & 1) * kSpcgReplicas * set_words;
     // q = S^_rows p for the owned rows, published as tagged words
+    if constexpr (kSparse) {
+      // one warp per owned camera; three groups of nine lanes take every third
+      // block of the row, lane a of a group row a of the block; the groups' sums
+      // are added in a fixed order and lanes 0-8 publish the camera's 9 entries
+      const int grp = lane / 9, ra = lane - 9 * grp;
+      for (int f = r0 / 9 + warp; f < r1 / 9; f += nwarps) {
+        const int c = a.cam_map[f];
+        const int e0 = a.brp[c], e1 = a.brp[c + 1];
+        T acc = T(0);
+        if (lane < 27) {
+          for (int e = e0 + grp; e < e1; e += 3) {
+            const int2 ent = a.bent[e];  // (column camera, block slot)
+            const int cf = a.crank[ent.x];
+            if (cf < 0) continue;
+            const T* row = a.Bs + (size_t)kBlkStride * ent.y + 9 * ra;
+            const T* pj = pv + 9 * cf;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc = fma(__ldg(row + t), pj[t], acc);
+          }
+        }
+        const T v1 = __shfl_down_sync(0xffffffffu, acc, 9);
+        const T v2 = __shfl_down_sync(0xffffffffu, acc, 18);
+        if (lane < 9) {
+          const T q = (acc + v1) + v2;
+#pragma unroll
+          for (int rep = 0; rep < kSpcgReplicas; ++rep)
+            spcg_publish<T>(set + rep * set_words + (size_t)(9 * f + lane) * W, q, tag);
+        }
+      }
+    } else {
     if constexpr (sizeof(T) == 4) {
       if constexpr (kRows) {
         // column split: warp w takes a slice of the float4 columns of every owned
@@ -783,6 +853,7 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
         if (lane < kSpcgReplicas) spcg_publish<T>(set + lane * set_words + (size_t)(r0 + r) * W, acc, tag);
       }
     }
+    }  // dense
     if constexpr (kFused) x_pending = false;  // the matvec pass applied a_prev p
     // gather q from this block's copy, coalesced (thread t: entries t, t + 512, ...,
     // up to four in flight), and (p, q)
@@ -923,16 +994,17 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
 }
 
 template <typename T>
-const void* spcg_kernel_ptr(bool rows_in_smem) {
-  return rows_in_smem ? reinterpret_cast<const void*>(&k_spcg<T, true>)
-                      : reinterpret_cast<const void*>(&k_spcg<T, false>);
+const void* spcg_kernel_ptr(bool rows_in_smem, bool sparse) {
+  if (sparse) return reinterpret_cast<const void*>(&k_spcg<T, false, true>);
+  return rows_in_smem ? reinterpret_cast<const void*>(&k_spcg<T, true, false>)
+                      : reinterpret_cast<const void*>(&k_spcg<T, false, false>);
 }
 
 template <typename T>
 cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s) {
   void* args[] = {const_cast<SpcgArgs<T>*>(&a)};
-  return cudaLaunchCooperativeKernel(spcg_kernel_ptr<T>(a.rows_in_smem != 0), dim3(grid), dim3(kSpcgThreads), args,
-                                     smem, s);
+  return cudaLaunchCooperativeKernel(spcg_kernel_ptr<T>(a.rows_in_smem != 0, a.Bs != nullptr), dim3(grid),
+                                     dim3(kSpcgThreads), args, smem, s);
 }
 
 int spcg_threads() { return kSpcgThreads; }
@@ -1051,11 +1123,12 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
 #define BAB_SINST(T)                                                                                   \
   template cudaError_t launch_form_S<T>(const Layout&, int, const int4*, const int2*, const T*,        \
                                         const T*, const int*, const T*, const T*, double*, int, T*, T*, \
-                                        bool, int, cudaEvent_t, cudaEvent_t, cudaEvent_t, cudaStream_t); \
+                                        bool, int, cudaEvent_t, cudaEvent_t, cudaEvent_t, cudaStream_t, \
+                                        const int*, bool);                                              \
   template cudaError_t launch_dscale<T>(int, const int*, const T*, double, double*, cudaStream_t);       \
   template size_t spcg_smem_bytes<T>(int, int, int, int, int);                                         \
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \
-  template const void* spcg_kernel_ptr<T>(bool);                                                         \
+  template const void* spcg_kernel_ptr<T>(bool, bool);                                                   \
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \
   template cudaError_t launch_spcg_precond<T>(int, const T*, const double*, T*, cudaStream_t);          \
   template cudaError_t launch_backsub_pts<T>(const Layout&, const ModelParams&, const T*, const T*,    \

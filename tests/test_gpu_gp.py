@@ -56,16 +56,20 @@ def test_gp_cost_fp64_matches_oracle():
     assert rms == pytest.approx(rms_o, rel=1e-12)
 
 
+@pytest.mark.parametrize("solver", [ba.BA_SOLVER_AUTO, ba.BA_SOLVER_DENSE])
 @pytest.mark.parametrize("n_cams,n_pts,lo,hi,mean,depth_frac", [
-    (12, 3000, 2, 12, 5.0, 0.5),    # several chunks per camera, ragged tracks
+    (12, 3000, 2, 12, 5.0, 0.5),    # several chunks per camera, ragged tracks, 11 free cameras
     (40, 6000, 3, 20, 8.0, 0.05),   # mostly free scales
     (30, 4000, 2, 8, 4.0, 1.0),     # every scale pinned
 ])
-def test_gp_damped_step_matches_oracle(n_cams, n_pts, lo, hi, mean, depth_frac):
+def test_gp_damped_step_matches_oracle(n_cams, n_pts, lo, hi, mean, depth_frac, solver):
+    """Both centre-system solvers: block-Jacobi PCG on three-camera blocks (AUTO;
+    11 and 29 free cameras leave a padded last block) and the tensor-core
+    Cholesky-preconditioned CG."""
     spec = dataclasses.replace(scenes.SPECS["medium"], n_cams=n_cams, n_pts=n_pts, track_min=lo,
                                track_max=hi, track_mean=mean, seed=11, depth_frac=depth_frac)
     sc = scenes.make_gp_scene(spec)
-    gpu, orc = pair(sc, pcg_rel_tol=1e-7)
+    gpu, orc = pair(sc, pcg_rel_tol=1e-6, solver=solver)
     for lam in (1e-2, 1e-4):
         g = gpu.solve_damped(lam)
         o = orc.solve_step(sc.centres0, sc.pts0, sc.scales0, lam)
@@ -79,9 +83,10 @@ def test_gp_damped_step_matches_oracle(n_cams, n_pts, lo, hi, mean, depth_frac):
         assert not g["ds"][sc.depth > 0].any()
 
 
-def test_gp_trajectory_matches_oracle():
+@pytest.mark.parametrize("solver", [ba.BA_SOLVER_AUTO, ba.BA_SOLVER_DENSE])
+def test_gp_trajectory_matches_oracle(solver):
     sc = gp_scene(20, 4000, 3, 12, 6.0, seed=21)
-    gpu, orc = pair(sc)
+    gpu, orc = pair(sc, solver=solver)
     log_g = gpu.solve(8)
     t_o, X_o, s_o, log_o = orc.lm(sc.centres0, sc.pts0, sc.scales0, 8)
     for i, (a, b) in enumerate(zip(log_g, log_o)):

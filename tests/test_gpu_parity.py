@@ -529,3 +529,68 @@ def test_extraction_mode_trajectory_matches_oracle(mode):
             np.testing.assert_array_equal(g[key], e[key], err_msg=key)
     else:
         assert acts[-1] > acts[0]
+
+
+# ---------------------------------------------------------------------------
+# (d) with the block-sparse explicit system (sparse co-visibility)
+# ---------------------------------------------------------------------------
+
+def window_scene(n_cams, n_pts, lo, hi, mean, seed, **kw):
+    spec = dataclasses.replace(scenes.SPECS["window"], n_cams=n_cams, n_pts=n_pts, track_min=lo,
+                               track_max=hi, track_mean=mean, seed=seed)
+    return scenes.make_scene(spec, covis="window", **kw)
+
+
+@pytest.mark.parametrize("precision", [ba.BA_FP64, ba.BA_FP32])
+def test_sparse_solver_damped_step_matches_oracle(precision):
+    """Windowed tracks (each point seen by the cameras nearest its azimuth): a
+    block-banded reduced camera system stored as the 9x9 blocks of its co-visible
+    camera pairs; the damped step against the oracle's dense Cholesky solve."""
+    sc = window_scene(120, 12000, 3, 10, 6.0, seed=91)
+    gpu, orc = pair(sc, precision, pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6,
+                    solver=ba.BA_SOLVER_SPARSE, pcg_max_iters=2000)
+    assert gpu.solver_kind == ba.BA_SOLVER_SPARSE
+    lam = 1e-3
+    g = gpu.solve_damped(lam)
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    o = orc.solve_step(ne, ext, lam)
+    check_step(g, o, *STEP_TOL[precision])
+    assert g["pcg_rel_res"] <= (1e-10 if precision == ba.BA_FP64 else 1e-6)
+
+
+def test_sparse_solver_trajectory_and_extraction_match_oracle():
+    """LM iterations with the block-sparse system follow the oracle per iteration,
+    also when extraction removes cameras (thresholds (15, 2) and a residual drop):
+    blocks of pairs whose cameras left the solve are skipped by the matvec.  FP64:
+    the narrow baselines of windowed tracks make the FP32 steps differ from the
+    FP64 ones by more than the 1e-5 cost bar (the FP32 steps are checked above)."""
+    sc = window_scene(80, 8000, 3, 10, 6.0, seed=92)
+    opt = dict(min_cam_obs=15, min_pt_obs=2, drop_residual_px=4.0, extract_every=3)
+    gpu, orc = pair(sc, ba.BA_FP64, solver=ba.BA_SOLVER_SPARSE, pcg_rel_tol=1e-10, pcg_max_iters=2000, **opt)
+    log_g = gpu.solve(8)
+    orc.opts.solver = 1
+    _, _, log_o = orc.lm(sc.cams0, sc.pts0, 8)
+    for i, (a, b) in enumerate(zip(log_g, log_o)):
+        assert a["cost"] == pytest.approx(b["cost"], rel=1e-5), i
+        assert a["accepted"] == b["accepted"], i
+        assert a["n_obs_act"] == b["n_obs_act"], i
+
+
+def test_sparse_and_dense_explicit_agree_and_auto_prefers_sparse():
+    """The block-sparse and the dense explicit systems hold the same blocks: their
+    damped steps agree to FP32 rounding of the PCG.  On a windowed scene with many
+    cameras, AUTO prices the block-sparse system cheapest."""
+    sc = window_scene(150, 15000, 3, 10, 6.0, seed=93)
+    steps = []
+    for solver in (ba.BA_SOLVER_SPARSE, ba.BA_SOLVER_EXPLICIT):
+        p = ba.Problem.from_scene(sc, ba.Options(precision=ba.BA_FP64, solver=solver, pcg_rel_tol=1e-12,
+                                                 pcg_max_iters=3000))
+        steps.append(p.solve_damped(1e-3))
+        p.close()
+    check_step(steps[0], steps[1], 1e-8, 1e-10)
+    big = window_scene(900, 60000, 3, 10, 6.0, seed=94)
+    p = ba.Problem.from_scene(big, ba.Options())
+    assert p.solver_kind == ba.BA_SOLVER_SPARSE
+    p.close()
