@@ -95,11 +95,21 @@ typedef struct {
                                   validity and peeling at the first iteration only, the active
                                   set then frozen (no residual drops); ba_set_params and
                                   ba_set_state start a new run and extract again */
+  int camera_model;            /* BA_CAMERA_RADIAL: [w, t, f, k1, k2], P = Exp(w) X + t with radial
+                                  distortion (the workloads' camera).  BA_CAMERA_CENTRE: the
+                                  parameterisation of Sec. 3.2 (camera centre, rotation, focal
+                                  length, no distortion) in the same nine slots [w, c, f, k1, k2]:
+                                  P = Exp(w) (X - c); k1, k2 are ignored and left unchanged (the
+                                  paper stores the rotation as a quaternion; the axis-angle slots
+                                  hold the same rotation, and the update is the same left
+                                  increment).  With BA_FP32 the centre model needs an explicit
+                                  solver; ba_backward needs BA_CAMERA_RADIAL. */
 } ba_options;
 
 enum { BA_SOLVER_AUTO = 0, BA_SOLVER_IMPLICIT = 1, BA_SOLVER_EXPLICIT = 2, BA_SOLVER_DENSE = 3,
        BA_SOLVER_SPARSE = 4 };
 enum { BA_EXTRACT_DYNAMIC = 0, BA_EXTRACT_ONCE = 1 };
+enum { BA_CAMERA_RADIAL = 0, BA_CAMERA_CENTRE = 1 };
 
 typedef struct {
   double cost;        /* F(x) = 1/2 sum rho(|r_k|^2) over the iteration's active set */
@@ -228,9 +238,9 @@ ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_d
  * allocation can cause.  Returns on the stream (asynchronously)
  * out[0] = 1/2 sum rho(|r_k|^2), out[1] = reprojection RMSE, out[2] = number of
  * observations counted, over observations with obs_mask[k] != 0 (NULL: all),
- * in the input order; the camera model, Huber loss, depth residual and weights
- * are those of ba_lm_step, taken from opts (precision and extraction fields are
- * ignored).  Observations whose indices are out of range are skipped.
+ * in the input order; the camera model (opts->camera_model), Huber loss, depth
+ * residual and weights are those of ba_lm_step, taken from opts (precision,
+ * solver and extraction fields are ignored).  Observations whose indices are out of range are skipped.
  * Every array (inputs and out) must be readable/writable by kernels of the
  * current device: device memory of that device, managed memory, or mapped
  * page-locked host memory passed as its device alias (the same address under

@@ -36,7 +36,7 @@ class Opts(ct.Structure):
                 ("extract_every", ct.c_int), ("drop_residual_px", ct.c_double),
                 ("min_cam_obs", ct.c_int), ("min_pt_obs", ct.c_int), ("lambda0", ct.c_double),
                 ("pcg_rel_tol", ct.c_double), ("pcg_max_iters", ct.c_int), ("solver", ct.c_int),
-                ("extract_mode", ct.c_int), ("nu0", ct.c_double)]
+                ("extract_mode", ct.c_int), ("nu0", ct.c_double), ("camera_model", ct.c_int)]
 
 
 class GPProblem(ct.Structure):
@@ -67,6 +67,8 @@ def lib():
         L.oracle_so3_left_jacobian_inv.argtypes = [P_f64, P_f64]
         L.oracle_observe.argtypes = [P_f64, P_f64, P_f64, ct.c_double, ct.c_double, ct.c_double,
                                      ct.c_double, P_f64, P_f64, P_f64, P_f64, P_f64]
+        L.oracle_observe_model.argtypes = [ct.c_int, P_f64, P_f64, P_f64, ct.c_double, ct.c_double,
+                                           ct.c_double, ct.c_double, P_f64, P_f64, P_f64, P_f64, P_f64]
         L.oracle_eval_obs.argtypes = [ct.POINTER(Problem), ct.POINTER(Opts), P_f64, P_f64, P_f64,
                                       P_f64, P_f64, P_f64, P_f64]
         L.oracle_cost.argtypes = [ct.POINTER(Problem), ct.POINTER(Opts), P_f64, P_f64, P_u8, P_f64]
@@ -141,6 +143,7 @@ class OracleOptions:
     solver: int = 0  # 0 dense Cholesky of the Schur system, 1 PCG
     extract_mode: int = 0  # 0 dynamic (every iteration), 1 one-shot at the first iteration
     nu0: float = 2.0  # initial damping growth factor (a restart after rejected steps)
+    camera_model: int = 0  # 0 radial [w, t, f, k1, k2]; 1 centre + rotation + focal [w, c, f, -, -]
 
     def to_c(self) -> Opts:
         return Opts(**dataclasses.asdict(self))
@@ -386,10 +389,11 @@ def rotvec_compose(a, b):
     return o
 
 
-def observe(cam, X, uv, tau, wt, cx=320.0, cy=240.0):
+def observe(cam, X, uv, tau, wt, cx=320.0, cy=240.0, model=0):
     r = np.zeros(3); Jc = np.zeros(27); Jp = np.zeros(9); z = ct.c_double(0); uvh = np.zeros(2)
-    lib().oracle_observe(_p(_f64(cam), P_f64), _p(_f64(X), P_f64), _p(_f64(uv), P_f64), tau, wt,
-                         cx, cy, _p(r, P_f64), _p(Jc, P_f64), _p(Jp, P_f64), ct.byref(z), _p(uvh, P_f64))
+    lib().oracle_observe_model(int(model), _p(_f64(cam), P_f64), _p(_f64(X), P_f64), _p(_f64(uv), P_f64),
+                               tau, wt, cx, cy, _p(r, P_f64), _p(Jc, P_f64), _p(Jp, P_f64), ct.byref(z),
+                               _p(uvh, P_f64))
     return r, Jc.reshape(3, 9), Jp.reshape(3, 3), z.value, uvh
 
 

@@ -38,6 +38,7 @@ void oracle_default_opts(oracle_opts* o) {
   o->solver = 0;
   o->extract_mode = 0;
   o->nu0 = 2.0;
+  o->camera_model = 0;
 }
 
 void oracle_set_threads(int n) {
@@ -154,14 +155,32 @@ static double depth_wt(const oracle_opts* o, double d) {
 void oracle_observe(const double cam[9], const double X[3], const double uv[2], double tau,
                     double wt, double cx, double cy, double r[3], double Jc[27], double Jp[9],
                     double* zout, double uvhat[2]) {
+  oracle_observe_model(0, cam, X, uv, tau, wt, cx, cy, r, Jc, Jp, zout, uvhat);
+}
+
+/* Camera models.  0: the 9-parameter radial camera, P = R X + t.  1: the
+ * parameterisation of Sec. 3.2 (camera centre, rotation, focal length; no
+ * distortion), stored in the same nine slots as [w, c, f, 0, 0]: P = R (X - c),
+ * the rotation increment left-multiplicative as for model 0; the k1, k2 slots are
+ * ignored (no column), so the step leaves them unchanged. */
+void oracle_observe_model(int model, const double cam[9], const double X[3], const double uv[2],
+                          double tau, double wt, double cx, double cy, double r[3], double Jc[27],
+                          double Jp[9], double* zout, double uvhat[2]) {
   double R[9];
   oracle_rotvec_to_matrix(cam, R);
   const double* t = cam + 3;
-  double f = cam[6], k1 = cam[7], k2 = cam[8];
+  double f = cam[6], k1 = model == 1 ? 0.0 : cam[7], k2 = model == 1 ? 0.0 : cam[8];
   double RX[3], P[3];
-  for (int i = 0; i < 3; ++i) {
-    RX[i] = R[3 * i + 0] * X[0] + R[3 * i + 1] * X[1] + R[3 * i + 2] * X[2];
-    P[i] = RX[i] + t[i];
+  if (model == 1) {
+    double d[3] = {X[0] - t[0], X[1] - t[1], X[2] - t[2]};
+    for (int i = 0; i < 3; ++i) P[i] = R[3 * i + 0] * d[0] + R[3 * i + 1] * d[1] + R[3 * i + 2] * d[2];
+    /* the rotation increment acts on R (X - c) = P */
+    for (int i = 0; i < 3; ++i) RX[i] = P[i];
+  } else {
+    for (int i = 0; i < 3; ++i) {
+      RX[i] = R[3 * i + 0] * X[0] + R[3 * i + 1] * X[1] + R[3 * i + 2] * X[2];
+      P[i] = RX[i] + t[i];
+    }
   }
   double z = P[2];
   double xn = P[0] / z, yn = P[1] / z;
@@ -196,14 +215,21 @@ void oracle_observe(const double cam[9], const double X[3], const double uv[2], 
   D[2][2] = -sw * iz * iz;
 
   if (Jc) {
-    /* dP/d(dw) = -[R X]x for the left increment Exp(dw) R */
+    /* dP/d(dw) = -[R X]x (model 0) or -[R (X - c)]x (model 1) for the left
+     * increment Exp(dw) R */
     double A[3][3] = {{0.0, RX[2], -RX[1]}, {-RX[2], 0.0, RX[0]}, {RX[1], -RX[0], 0.0}};
     for (int m = 0; m < 3; ++m) {
       for (int j = 0; j < 3; ++j) {
         double s = 0;
         for (int l = 0; l < 3; ++l) s += D[m][l] * A[l][j];
-        Jc[9 * m + j] = s;          /* rotation */
-        Jc[9 * m + 3 + j] = D[m][j]; /* translation: dP/dt = I */
+        Jc[9 * m + j] = s; /* rotation */
+        if (model == 1) {  /* centre: dP/dc = -R */
+          double sc = 0;
+          for (int l = 0; l < 3; ++l) sc += D[m][l] * R[3 * l + j];
+          Jc[9 * m + 3 + j] = -sc;
+        } else {
+          Jc[9 * m + 3 + j] = D[m][j]; /* translation: dP/dt = I */
+        }
       }
     }
     /* intrinsics */
@@ -216,6 +242,8 @@ void oracle_observe(const double cam[9], const double X[3], const double uv[2], 
     Jc[9 * 2 + 6] = 0.0;
     Jc[9 * 2 + 7] = 0.0;
     Jc[9 * 2 + 8] = 0.0;
+    if (model == 1)
+      for (int m = 0; m < 3; ++m) Jc[9 * m + 7] = Jc[9 * m + 8] = 0.0;
   }
   if (Jp) { /* dP/dX = R */
     for (int m = 0; m < 3; ++m)
@@ -235,7 +263,7 @@ void oracle_eval_obs(const oracle_problem* pb, const oracle_opts* o, const doubl
   for (int64_t k = 0; k < N; ++k) {
     int c = pb->obs_cam[k], p = pb->obs_pt[k];
     double d = pb->depth[k];
-    oracle_observe(cams + 9 * (int64_t)c, pts + 3 * (int64_t)p, pb->obs_uv + 2 * k, depth_tau(d),
+    oracle_observe_model(o->camera_model, cams + 9 * (int64_t)c, pts + 3 * (int64_t)p, pb->obs_uv + 2 * k, depth_tau(d),
                    depth_wt(o, d), o->cx, o->cy, r ? r + 3 * k : NULL, Jc ? Jc + 27 * k : NULL,
                    Jp ? Jp + 9 * k : NULL, z ? z + k : NULL, uvhat ? uvhat + 2 * k : NULL);
   }
@@ -266,7 +294,7 @@ double oracle_cost(const oracle_problem* pb, const oracle_opts* o, const double*
     if (mask && !mask[k]) continue;
     double r[3];
     double d = pb->depth[k];
-    oracle_observe(cams + 9 * (int64_t)pb->obs_cam[k], pts + 3 * (int64_t)pb->obs_pt[k],
+    oracle_observe_model(o->camera_model, cams + 9 * (int64_t)pb->obs_cam[k], pts + 3 * (int64_t)pb->obs_pt[k],
                    pb->obs_uv + 2 * k, depth_tau(d), depth_wt(o, d), o->cx, o->cy, r, NULL,
                    NULL, NULL, NULL);
     double s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
@@ -299,7 +327,7 @@ void oracle_predicate(const oracle_problem* pb, const oracle_opts* o, const doub
   for (int64_t k = 0; k < N; ++k) {
     double r[3], z, uvh[2];
     double d = pb->depth[k];
-    oracle_observe(cams + 9 * (int64_t)pb->obs_cam[k], pts + 3 * (int64_t)pb->obs_pt[k],
+    oracle_observe_model(o->camera_model, cams + 9 * (int64_t)pb->obs_cam[k], pts + 3 * (int64_t)pb->obs_pt[k],
                    pb->obs_uv + 2 * k, depth_tau(d), depth_wt(o, d), o->cx, o->cy, r, NULL,
                    NULL, &z, uvh);
     int ok = z > o->min_depth && uvh[0] >= 0.0 && uvh[0] < (double)o->img_w && uvh[1] >= 0.0 &&
@@ -1115,7 +1143,7 @@ int oracle_backward(const oracle_problem* pb, const oracle_opts* o, const double
       double d = pb->depth[k];
       double r[3], Jc[27], Jp[9];
       double wt = depth_wt(o, d);
-      oracle_observe(cams + 9 * (int64_t)c, pts + 3 * (int64_t)p, pb->obs_uv + 2 * k,
+      oracle_observe_model(o->camera_model, cams + 9 * (int64_t)c, pts + 3 * (int64_t)p, pb->obs_uv + 2 * k,
                      depth_tau(d), wt, o->cx, o->cy, r, Jc, Jp, NULL, NULL);
       double s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
       double rw = huber_w(s, o->huber_delta);

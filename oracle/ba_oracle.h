@@ -53,6 +53,8 @@ typedef struct {
   int extract_mode;             /* 0: extraction at every iteration whose state changed (Sec. 4.2);
                                    1: one-shot, at the first iteration only, active set frozen */
   double nu0;                   /* initial damping growth factor nu (<= 0: 2, the rule's start) */
+  int camera_model;             /* 0: radial [w, t, f, k1, k2], P = R X + t;
+                                   1: Sec. 3.2's centre + rotation + focal, [w, c, f, -, -], P = R (X - c) */
 } oracle_opts;
 
 typedef struct {
@@ -77,6 +79,11 @@ void oracle_rotvec_compose(const double a[3], const double b[3], double out[3]);
 void oracle_observe(const double cam[9], const double X[3], const double uv[2], double tau,
                     double wt, double cx, double cy, double r[3], double Jc[27], double Jp[9],
                     double* z, double uvhat[2]);
+
+/* oracle_observe for a camera model (see oracle_opts.camera_model). */
+void oracle_observe_model(int model, const double cam[9], const double X[3], const double uv[2],
+                          double tau, double wt, double cx, double cy, double r[3], double Jc[27],
+                          double Jp[9], double* z, double uvhat[2]);
 
 /* Per-observation residuals / Jacobians / depth / projection for all N observations.
  * Any output may be NULL. */

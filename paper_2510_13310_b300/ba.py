@@ -22,6 +22,7 @@ BA_ERR_NOT_CONVERGED, BA_ERR_NONFINITE, BA_ERR_STATE, BA_ERR_TIMEOUT = 4, 5, 6, 
 BA_FP64, BA_FP32 = 0, 1
 BA_SOLVER_AUTO, BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT, BA_SOLVER_DENSE, BA_SOLVER_SPARSE = 0, 1, 2, 3, 4
 BA_EXTRACT_DYNAMIC, BA_EXTRACT_ONCE = 0, 1
+BA_CAMERA_RADIAL, BA_CAMERA_CENTRE = 0, 1
 
 # every symbol include/ba_b300.h declares
 EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_params",
@@ -43,7 +44,8 @@ class _Options(ct.Structure):
                 ("drop_residual_px", ct.c_double), ("min_cam_obs", ct.c_int),
                 ("min_pt_obs", ct.c_int), ("lambda0", ct.c_double), ("pcg_rel_tol", ct.c_double),
                 ("pcg_max_iters", ct.c_int), ("fixed_cams", ct.POINTER(ct.c_int32)),
-                ("n_fixed", ct.c_int), ("solver", ct.c_int), ("extract_mode", ct.c_int)]
+                ("n_fixed", ct.c_int), ("solver", ct.c_int), ("extract_mode", ct.c_int),
+                ("camera_model", ct.c_int)]
 
 
 class _GPOptions(ct.Structure):
@@ -179,6 +181,7 @@ class Options:
     fixed_cams: tuple = (0,)
     solver: int = BA_SOLVER_AUTO
     extract_mode: int = 0  # BA_EXTRACT_DYNAMIC; 1 = BA_EXTRACT_ONCE (one-shot pruning)
+    camera_model: int = 0  # BA_CAMERA_RADIAL; 1 = BA_CAMERA_CENTRE (centre + rotation + focal)
 
 
 class _Arr:
@@ -391,8 +394,29 @@ def _c_options(o: Options):
     c = _Options(o.precision, o.img_w, o.img_h, o.cx, o.cy, o.huber_delta, o.depth_weight,
                  o.invalid_depth_weight, o.min_depth, o.extract_every, o.drop_residual_px,
                  o.min_cam_obs, o.min_pt_obs, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
-                 fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(fixed), o.solver, o.extract_mode)
+                 fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(fixed), o.solver, o.extract_mode,
+                 o.camera_model)
     return c, fixed
+
+
+def paper_cameras(centres, quats, focal):
+    """Cameras in the parameterisation of Sec. 3.2 (centre c [C,3], unit quaternion
+    (w, x, y, z) of the world-to-camera rotation [C,4], focal [C]) as the library's
+    nine slots under BA_CAMERA_CENTRE: [axis-angle of the rotation, c, f, 0, 0]."""
+    from scipy.spatial.transform import Rotation
+    q = np.asarray(quats, dtype=np.float64)
+    rv = Rotation.from_quat(np.stack([q[:, 1], q[:, 2], q[:, 3], q[:, 0]], 1)).as_rotvec()
+    C = q.shape[0]
+    return np.concatenate([rv, np.asarray(centres, np.float64).reshape(C, 3),
+                           np.asarray(focal, np.float64).reshape(C, 1), np.zeros((C, 2))], axis=1)
+
+
+def paper_cameras_from(cams):
+    """The inverse of paper_cameras: (centres, quaternions (w, x, y, z), focal)."""
+    from scipy.spatial.transform import Rotation
+    cams = np.asarray(cams, dtype=np.float64)
+    xyzw = Rotation.from_rotvec(cams[:, :3]).as_quat()
+    return cams[:, 3:6].copy(), np.stack([xyzw[:, 3], xyzw[:, 0], xyzw[:, 1], xyzw[:, 2]], 1), cams[:, 6].copy()
 
 
 def _check_noalloc_args(cams, pts, obs_cam, obs_pt, obs_uv, depth, out, obs_mask):

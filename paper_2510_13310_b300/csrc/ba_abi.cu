@@ -298,7 +298,8 @@ bool finite_opts(const ba_options* o) {
          std::isfinite(o->pcg_rel_tol) && o->pcg_rel_tol > 0 && o->pcg_max_iters > 0 &&
          o->img_w > 0 && o->img_h > 0 && o->min_cam_obs >= 0 && o->min_pt_obs >= 0 &&
          o->extract_every >= 0 && (o->precision == BA_FP64 || o->precision == BA_FP32) &&
-         (o->extract_mode == BA_EXTRACT_DYNAMIC || o->extract_mode == BA_EXTRACT_ONCE);
+         (o->extract_mode == BA_EXTRACT_DYNAMIC || o->extract_mode == BA_EXTRACT_ONCE) &&
+         (o->camera_model == BA_CAMERA_RADIAL || o->camera_model == BA_CAMERA_CENTRE);
 }
 
 ba_status sync(ba_problem* pb) {
@@ -574,7 +575,7 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     LAUNCH(1, launch_candidate<T>(pb->C, 0, pb->crank, (const T*)pb->x, (const T*)pb->dp, pb->cams64[sl],
                                   pb->pts64[sl], pb->cams64[d], pb->pts64[d], pb->camw64[d],
                                   pb->fp64 ? nullptr : (T*)pb->camw[d], (T*)pb->ptsw[d], pb->camdf[d], pb->ptdf[d],
-                                  pb->side));
+                                  pb->side, pb->mp.cam_model));
     CU(cudaEventRecord(pb->cand_join, pb->side));
     pb->cand_cams_done = true;
   }
@@ -650,7 +651,8 @@ ba_status candidate_t(ba_problem* pb) {
   LAUNCH(early ? 1 : 2, launch_candidate<T>(early ? 0 : pb->C, pb->P, pb->crank, (const T*)pb->x, (const T*)pb->dp,
                                             pb->cams64[s], pb->pts64[s], pb->cams64[d], pb->pts64[d],
                                             pb->camw64[d], pb->fp64 ? nullptr : (T*)pb->camw[d],
-                                            (T*)pb->ptsw[d], pb->camdf[d], pb->ptdf[d], pb->stream));
+                                            (T*)pb->ptsw[d], pb->camdf[d], pb->ptdf[d], pb->stream,
+                                            pb->mp.cam_model));
   if (early) CU(cudaStreamWaitEvent(pb->stream, pb->cand_join, 0));
   pb->cand_cams_done = false;
   pb->df_current[d] = !pb->fp64;  // the candidate kernels wrote its double-float copy
@@ -1026,6 +1028,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   L.cam_fixed = pb->cam_fixed;
 
   ModelParams& mp = pb->mp;
+  mp.cam_model = opts->camera_model;
   mp.cx = opts->cx;
   mp.cy = opts->cy;
   mp.huber = opts->huber_delta;
@@ -1083,6 +1086,13 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       set_error("BA_SOLVER_DENSE needs BA_FP32 (the factorisation runs on TF32 tensor cores)");
       return BA_ERR_INVALID_ARG;
     }
+    // the FP32 implicit PCG recomputes the radial model's Jacobian blocks itself;
+    // the centre model runs on the stored blocks of the other solvers
+    const bool no_implicit = !pb->fp64 && opts->camera_model == BA_CAMERA_CENTRE;
+    if (so == BA_SOLVER_IMPLICIT && no_implicit) {
+      set_error("BA_CAMERA_CENTRE with BA_FP32 needs an explicit solver (EXPLICIT, SPARSE or DENSE)");
+      return BA_ERR_INVALID_ARG;
+    }
     // The dense tensor-core solve is opt-in: on the 12M-observation dense
     // workload (2,000 cameras) forming S from 174M co-visible pairs alone costs
     // about as much as the whole implicit block-Jacobi PCG, which converges in
@@ -1109,7 +1119,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
         const double n = 9.0 * C, it = 40.0;
         const double t_exp = pairs * 0.1e-9 + 3.0 * 4.0 * n * n / 6.5e12 + N * 50e-12 +
                              it * (4.0 * n * n / 4.9e12 + 10e-6);
-        const double t_imp = it * (N * 66e-12 + P * 245e-12);
+        const double t_imp = no_implicit ? 1e300 : it * (N * 66e-12 + P * 245e-12);
         // and only within the explicit system's memory bound below
         auto_explicit = t_exp < t_imp && (size_t)81 * C * C * (R + 8) <= ((size_t)8 << 30);
         // the block-sparse system is priced once the co-visibility runs are known
@@ -1335,10 +1345,10 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   // working copies of the initial state (after every upload has landed)
   CU(cudaDeviceSynchronize());
   if (pb->fp64) {
-    LAUNCH(1, launch_prep_cams<double>(pb->cams64[0], (double*)pb->camw[0], nullptr, C, pb->stream));
+    LAUNCH(1, launch_prep_cams<double>(pb->cams64[0], (double*)pb->camw[0], nullptr, C, pb->stream, pb->mp.cam_model));
     LAUNCH(1, launch_prep_pts<double>(pb->pts64[0], (double*)pb->ptsw[0], P, pb->stream));
   } else {
-    LAUNCH(1, launch_prep_cams<float>(pb->cams64[0], (float*)pb->camw[0], pb->camw64[0], C, pb->stream));
+    LAUNCH(1, launch_prep_cams<float>(pb->cams64[0], (float*)pb->camw[0], pb->camw64[0], C, pb->stream, pb->mp.cam_model));
     LAUNCH(1, launch_prep_pts<float>(pb->pts64[0], (float*)pb->ptsw[0], P, pb->stream));
   }
   ST(sync(pb));
@@ -1532,10 +1542,10 @@ ba_status ba_set_params(ba_problem* pb, const double* cams, const double* pts) {
   if (pb->C) CU(cudaMemcpy(pb->cams64[s], hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice));
   if (pb->P) CU(cudaMemcpy(pb->pts64[s], hp.data(), sizeof(double) * hp.size(), cudaMemcpyHostToDevice));
   if (pb->fp64) {
-    LAUNCH(1, launch_prep_cams<double>(pb->cams64[s], (double*)pb->camw[s], nullptr, pb->C, pb->stream));
+    LAUNCH(1, launch_prep_cams<double>(pb->cams64[s], (double*)pb->camw[s], nullptr, pb->C, pb->stream, pb->mp.cam_model));
     LAUNCH(1, launch_prep_pts<double>(pb->pts64[s], (double*)pb->ptsw[s], pb->P, pb->stream));
   } else {
-    LAUNCH(1, launch_prep_cams<float>(pb->cams64[s], (float*)pb->camw[s], pb->camw64[s], pb->C, pb->stream));
+    LAUNCH(1, launch_prep_cams<float>(pb->cams64[s], (float*)pb->camw[s], pb->camw64[s], pb->C, pb->stream, pb->mp.cam_model));
     LAUNCH(1, launch_prep_pts<float>(pb->pts64[s], (float*)pb->ptsw[s], pb->P, pb->stream));
   }
   pb->bits_valid[s] = pb->cost_valid[s] = false;
@@ -1814,7 +1824,7 @@ ba_status ba_eval_cost(ba_problem* pb, const double* cams, const double* pts, do
     else if (pb->C) CU(cudaMemcpyAsync(pb->cams64[slot], pb->cams64[pb->cur], sizeof(double) * 9 * (size_t)pb->C, cudaMemcpyDeviceToDevice, pb->stream));
     if (pts && pb->P) CU(cudaMemcpyAsync(pb->pts64[slot], pts, sizeof(double) * 3 * (size_t)pb->P, cudaMemcpyDefault, pb->stream));
     else if (pb->P) CU(cudaMemcpyAsync(pb->pts64[slot], pb->pts64[pb->cur], sizeof(double) * 3 * (size_t)pb->P, cudaMemcpyDeviceToDevice, pb->stream));
-    LAUNCH(1, launch_prep_cams<double>(pb->cams64[slot], pb->camw64[slot], nullptr, pb->C, pb->stream));
+    LAUNCH(1, launch_prep_cams<double>(pb->cams64[slot], pb->camw64[slot], nullptr, pb->C, pb->stream, pb->mp.cam_model));
     pb->bits_valid[slot] = false;
     pb->df_current[slot] = false;
   }
@@ -1831,6 +1841,11 @@ ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_d
                       double* dL_duv, double* dL_ddepth) {
   if (!pb || !dL_dcams || !dL_dpts || !dL_duv || !dL_ddepth) {
     set_error("ba_backward: NULL argument");
+    return BA_ERR_INVALID_ARG;
+  }
+  if (pb->mp.cam_model != BA_CAMERA_RADIAL) {
+    // the undamped system has no k1, k2 columns under the centre model: singular
+    set_error("ba_backward: the implicit adjoint is defined for BA_CAMERA_RADIAL");
     return BA_ERR_INVALID_ARG;
   }
   ST(ensure_linearized(pb));

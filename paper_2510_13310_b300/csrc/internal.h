@@ -53,6 +53,7 @@ struct EvalDFConst {
 };
 
 struct ModelParams {
+  int cam_model;   // 0 radial, 1 centre + rotation + focal (model.cuh)
   double cx, cy, huber, sw_valid, sw_invalid, min_depth, drop_px;
   int img_w, img_h;
 };
@@ -162,7 +163,8 @@ cudaError_t launch_set_pcg_info(Scalars* sc, int iters, double rel, int* err, in
 
 // ---- launchers (return cudaGetLastError of the launch) ----
 template <typename T>
-cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s);
+cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s,
+                             int model = 0);  // camera model of the working records (model.cuh)
 template <typename T>
 cudaError_t launch_prep_pts(const double* pts64, T* ptsw, int P, cudaStream_t s);
 // uv and inverse-depth priors in point order and camera order (and the W row of
@@ -274,7 +276,8 @@ template <typename T>
 cudaError_t launch_candidate(int C, int P, const int* crank, const T* x, const T* dp,
                              const double* cams_src, const double* pts_src, double* cams_dst,
                              double* pts_dst, double* camw64_dst, T* camw_dst, T* ptsw_dst,
-                             F2* camdf_dst, float4* ptdf_dst, cudaStream_t s);  // *df_dst nullable
+                             F2* camdf_dst, float4* ptdf_dst, cudaStream_t s,  // *df_dst nullable
+                             int model = 0);
 template <typename T>
 cudaError_t launch_scatter_cams(int C, const int* crank, const T* x, double* dc, cudaStream_t s);
 template <typename T>

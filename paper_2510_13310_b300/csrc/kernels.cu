@@ -18,25 +18,19 @@ namespace bab {
 
 template <typename T>
 __global__ void k_prep_cams(const double* __restrict__ cams64, T* __restrict__ camw,
-                            double* __restrict__ camw64, int C) {
+                            double* __restrict__ camw64, int C, int model) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
-  const double* cp = cams64 + 9 * (size_t)c;
-  double R[9];
-  double w[3] = {cp[0], cp[1], cp[2]};
-  rotvec_matrix(w, R);
   double rec[kCamStride];
-  for (int i = 0; i < 9; ++i) rec[i] = R[i];
-  for (int i = 0; i < 6; ++i) rec[9 + i] = cp[3 + i];
-  rec[15] = 0.0;
+  cam_record(cams64 + 9 * (size_t)c, model, rec);
   for (int i = 0; i < kCamStride; ++i) camw[kCamStride * (size_t)c + i] = (T)rec[i];
   if (camw64)
     for (int i = 0; i < kCamStride; ++i) camw64[kCamStride * (size_t)c + i] = rec[i];
 }
 
 template <typename T>
-cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s) {
-  if (C > 0) k_prep_cams<T><<<(C + 127) / 128, 128, 0, s>>>(cams64, camw, camw64, C);
+cudaError_t launch_prep_cams(const double* cams64, T* camw, double* camw64, int C, cudaStream_t s, int model) {
+  if (C > 0) k_prep_cams<T><<<(C + 127) / 128, 128, 0, s>>>(cams64, camw, camw64, C, model);
   return cudaGetLastError();
 }
 
@@ -1210,7 +1204,8 @@ cudaError_t launch_reduce_pred(const double* parts, int n, Scalars* sc, cudaStre
 template <typename T>
 __global__ void k_candidate_cams(int C, const int* __restrict__ crank, const T* __restrict__ x,
                                  const double* __restrict__ src, double* __restrict__ dst,
-                                 double* __restrict__ camw64, T* __restrict__ camw, F2* __restrict__ camdf) {
+                                 double* __restrict__ camw64, T* __restrict__ camw, F2* __restrict__ camdf,
+                                 int model) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const double* s = src + 9 * (size_t)c;
@@ -1226,12 +1221,8 @@ __global__ void k_candidate_cams(int C, const int* __restrict__ crank, const T* 
     for (int i = 0; i < 9; ++i) o[i] = s[i];
   }
   for (int i = 0; i < 9; ++i) dst[9 * (size_t)c + i] = o[i];
-  double R[9];
-  rotvec_matrix(o, R);
   double rec[kCamStride];
-  for (int i = 0; i < 9; ++i) rec[i] = R[i];
-  for (int i = 0; i < 6; ++i) rec[9 + i] = o[3 + i];
-  rec[15] = 0.0;
+  cam_record(o, model, rec);
   for (int i = 0; i < kCamStride; ++i) camw64[kCamStride * (size_t)c + i] = rec[i];
   if (camw)
     for (int i = 0; i < kCamStride; ++i) camw[kCamStride * (size_t)c + i] = (T)rec[i];
@@ -1267,10 +1258,11 @@ template <typename T>
 cudaError_t launch_candidate(int C, int P, const int* crank, const T* x, const T* dp,
                              const double* cams_src, const double* pts_src, double* cams_dst,
                              double* pts_dst, double* camw64_dst, T* camw_dst, T* ptsw_dst,
-                             F2* camdf_dst, float4* ptdf_dst, cudaStream_t s) {
+                             F2* camdf_dst, float4* ptdf_dst, cudaStream_t s, int model) {
   // 32-thread blocks: the FP64 rotation work (sincos, atan2) of 32 cameras per SM
   if (C > 0)
-    k_candidate_cams<T><<<(C + 31) / 32, 32, 0, s>>>(C, crank, x, cams_src, cams_dst, camw64_dst, camw_dst, camdf_dst);
+    k_candidate_cams<T><<<(C + 31) / 32, 32, 0, s>>>(C, crank, x, cams_src, cams_dst, camw64_dst, camw_dst, camdf_dst,
+                                                     model);
   if (P > 0) k_candidate_pts<T><<<(P + 255) / 256, 256, 0, s>>>(P, dp, pts_src, pts_dst, ptsw_dst, ptdf_dst);
   return cudaGetLastError();
 }
@@ -1343,7 +1335,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
 // explicit instantiations
 // ---------------------------------------------------------------------------
 #define BAB_INST(T)                                                                                \
-  template cudaError_t launch_prep_cams<T>(const double*, T*, double*, int, cudaStream_t);          \
+  template cudaError_t launch_prep_cams<T>(const double*, T*, double*, int, cudaStream_t, int);     \
   template cudaError_t launch_prep_pts<T>(const double*, T*, int, cudaStream_t);                    \
   template cudaError_t launch_obs_layout<T>(int, const double*, const double*, const int*, const int*,  \
                                             const int*, const int*, int*, double*, double*, T*, T*,    \
@@ -1362,7 +1354,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
                                            double*, int, cudaStream_t);                             \
   template cudaError_t launch_candidate<T>(int, int, const int*, const T*, const T*, const double*, \
                                            const double*, double*, double*, double*, T*, T*,        \
-                                           F2*, float4*, cudaStream_t);                             \
+                                           F2*, float4*, cudaStream_t, int);                        \
   template cudaError_t launch_scatter_cams<T>(int, const int*, const T*, double*, cudaStream_t);    \
   template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);              \
   template cudaError_t launch_permute_rows<T>(const int*, const int*, const T*, int, double*, int,    \

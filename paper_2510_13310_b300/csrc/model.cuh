@@ -5,6 +5,14 @@
 // r_d = 1/Depth - m/d, into r = [u^ - u, v^ - v, sqrt(w) r_d].  The camera block
 // uses the left rotation increment: dP/d(dw) = -[R X]x, dP/dt = I; the point
 // block is dP/dX = R.
+//
+// Camera models, both in the nine slots [w, t or c, f, k1, k2] of a camera and
+// projected through one working record (R, t, f, k1, k2, model):
+//   0 (radial):  P = R X + t, distortion 1 + k1 rr + k2 rr^2;
+//   1 (Sec. 3.2's parameterisation: centre, rotation, focal length):
+//                P = R (X - c), no distortion; the record holds t = -R c and
+//                k1 = k2 = 0, the Jacobian has dP/d(dw) = -[P]x, dP/dc = -R and
+//                no k1, k2 columns.
 #pragma once
 #include "common.cuh"
 
@@ -103,6 +111,8 @@ __device__ __forceinline__ void linearize_obs(const T* __restrict__ cw, T X0, T 
   T D12 = fd * dyz - g * yn * rr * iz;
   T D22 = -sw * iz * iz;
 
+  // model 1: the rotation increment acts on R (X - c) = P
+  if (cw[15] != T(0)) a0 = px, a1 = py, a2 = pz;
   // rotation columns: D * (-[a]x) with -[a]x = [[0,a2,-a1],[-a2,0,a0],[a1,-a0,0]]
   o.Jc[0][0] = -D01 * a2 + D02 * a1;
   o.Jc[0][1] = D00 * a2 - D02 * a0;
@@ -127,6 +137,16 @@ __device__ __forceinline__ void linearize_obs(const T* __restrict__ cw, T X0, T 
     o.Jp[0][j] = D00 * R[j] + D01 * R[3 + j] + D02 * R[6 + j];
     o.Jp[1][j] = D10 * R[j] + D11 * R[3 + j] + D12 * R[6 + j];
     o.Jp[2][j] = D22 * R[6 + j];
+  }
+  if (cw[15] != T(0)) {
+    // model 1: centre columns -D R, no distortion columns
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) o.Jc[m][3 + j] = -o.Jp[m][j];
+      o.Jc[m][7] = T(0);
+      o.Jc[m][8] = T(0);
+    }
   }
 }
 
@@ -182,6 +202,25 @@ __device__ __forceinline__ void rotvec_matrix(const double w[3], double R[9]) {
   R[6] = cb * w[2] * w[0] - sa * w[1];
   R[7] = cb * w[2] * w[1] + sa * w[0];
   R[8] = c + cb * w[2] * w[2];
+}
+
+// Working record of a camera's nine parameters (see the camera models above):
+// R (9), t (3), f, k1, k2, model.
+__device__ __forceinline__ void cam_record(const double* __restrict__ p, int model, double rec[16]) {
+  const double w[3] = {p[0], p[1], p[2]};
+  double R[9];
+  rotvec_matrix(w, R);
+  for (int i = 0; i < 9; ++i) rec[i] = R[i];
+  if (model == 1) {
+    for (int i = 0; i < 3; ++i) rec[9 + i] = -(R[3 * i] * p[3] + R[3 * i + 1] * p[4] + R[3 * i + 2] * p[5]);
+    rec[12] = p[6];
+    rec[13] = 0.0;
+    rec[14] = 0.0;
+    rec[15] = 1.0;
+  } else {
+    for (int i = 0; i < 6; ++i) rec[9 + i] = p[3 + i];
+    rec[15] = 0.0;
+  }
 }
 
 // Left composition of rotations in axis-angle form, Log(Exp(a) Exp(b)), through

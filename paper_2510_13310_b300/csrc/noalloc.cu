@@ -34,17 +34,12 @@ namespace {
 std::mutex g_na_mutex;
 double* g_na_ptr[64] = {};  // device address of g_na_scratch, per device ordinal
 
-__global__ void k_na_prep_cams(const double* __restrict__ cams, int C, double* __restrict__ rec) {
+__global__ void k_na_prep_cams(const double* __restrict__ cams, int C, int model, double* __restrict__ rec) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
-  const double* cp = cams + 9 * (size_t)c;
-  double w[3] = {cp[0], cp[1], cp[2]};
-  double R[9];
-  rotvec_matrix(w, R);
-  double* o = rec + kCamStride * (size_t)c;
-  for (int i = 0; i < 9; ++i) o[i] = R[i];
-  for (int i = 0; i < 6; ++i) o[9 + i] = cp[3 + i];
-  o[15] = 0.0;
+  double r[kCamStride];
+  cam_record(cams + 9 * (size_t)c, model, r);
+  for (int i = 0; i < kCamStride; ++i) rec[kCamStride * (size_t)c + i] = r[i];
 }
 
 // Input-order variant of the FP64 evaluation: every block writes its own partial
@@ -194,7 +189,7 @@ extern "C" ba_status ba_eval_cost_noalloc(const ba_options* opts, void* stream, 
   mp.sw_invalid = sqrt(opts->invalid_depth_weight);
   cudaStream_t s = (cudaStream_t)stream;
   int C = (int)n_cams, P = (int)n_pts, N = (int)n_obs;
-  if (C > 0) k_na_prep_cams<<<(C + 127) / 128, 128, 0, s>>>(cams, C, rec);
+  if (C > 0) k_na_prep_cams<<<(C + 127) / 128, 128, 0, s>>>(cams, C, opts->camera_model == 1 ? 1 : 0, rec);
   int grid = (N + kNaThreads - 1) / kNaThreads;
   grid = grid < 1 ? 1 : (grid > kNaBlocks ? kNaBlocks : grid);
   k_na_eval<<<grid, kNaThreads, 0, s>>>(C, P, N, rec, pts, obs_cam, obs_pt, obs_uv, depth, obs_mask,

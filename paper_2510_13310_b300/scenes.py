@@ -196,12 +196,18 @@ def _window_tracks(rng, pts: np.ndarray, C: int, lengths: np.ndarray):
 def make_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = True,
                outliers: bool = True, depth_priors: bool = True,
                scale: float | None = None, shuffle: bool = True,
-               frustum_exit_frac: float = 0.0, covis: str | None = None) -> Scene:
+               frustum_exit_frac: float = 0.0, covis: str | None = None,
+               camera_model: str = "radial") -> Scene:
     """Generate a seeded scene.
 
     `noise=False` removes pixel and depth noise, `outliers=False` removes the
     outliers, `depth_priors=False` clears every prior.  `scale` shrinks the
     camera and point counts (for reduced-size parity cases).
+
+    `camera_model` "centre" gives cameras in the parameterisation of Sec. 3.2
+    (centre, rotation, focal length, no distortion) in the nine slots
+    [w, c, f, 0, 0]: measurements synthesised with k1 = k2 = 0, the start moves
+    each centre by trans_perturb * |c| in a random direction.
 
     `covis` chooses the cameras of each track: "random" (distinct cameras drawn
     uniformly) or "window" (the angularly nearest cameras; the default for the
@@ -237,7 +243,11 @@ def make_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = 
     focal = spec.focal * (1.0 + 0.02 * rng.standard_normal(C))
     k1 = 0.01 * rng.standard_normal(C)
     k2 = 0.01 * rng.standard_normal(C)
-    cams_gt = np.concatenate([Rotation.from_matrix(Rs).as_rotvec(), ts,
+    centre_model = camera_model == "centre"
+    if centre_model:
+        k1[:] = 0.0
+        k2[:] = 0.0
+    cams_gt = np.concatenate([Rotation.from_matrix(Rs).as_rotvec(), centres if centre_model else ts,
                               focal[:, None], k1[:, None], k2[:, None]], axis=1)
 
     # points uniform in the unit sphere
@@ -281,7 +291,8 @@ def make_scene(spec: SceneSpec | str, *, seed: int | None = None, noise: bool = 
     dirs = rng.standard_normal((C, 3))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
     rot0 = Rotation.from_rotvec(axes * math.radians(spec.rot_perturb_deg)) * Rotation.from_matrix(Rs)
-    t0 = ts + spec.trans_perturb * np.linalg.norm(ts, axis=1, keepdims=True) * dirs
+    base_t = centres if centre_model else ts
+    t0 = base_t + spec.trans_perturb * np.linalg.norm(base_t, axis=1, keepdims=True) * dirs
     cams0 = np.concatenate([rot0.as_rotvec(), t0, cams_gt[:, 6:9]], axis=1)
     cams0[fixed] = cams_gt[fixed]
     pts0 = pts_gt + spec.pt_perturb * rng.standard_normal((P, 3))

@@ -594,3 +594,69 @@ def test_sparse_and_dense_explicit_agree_and_auto_prefers_sparse():
     p = ba.Problem.from_scene(big, ba.Options())
     assert p.solver_kind == ba.BA_SOLVER_SPARSE
     p.close()
+
+
+# ---------------------------------------------------------------------------
+# the camera parameterisation of Sec. 3.2 (BA_CAMERA_CENTRE)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [(ba.BA_FP64, 1e-11), (ba.BA_FP32, 1e-4)])
+def test_centre_model_blocks_match_oracle(precision, tol):
+    sc = geometric(12, 3000, 2, 12, 5.0, seed=31, camera_model="centre")
+    gpu, orc = pair(sc, precision, camera_model=ba.BA_CAMERA_CENTRE, solver=ba.BA_SOLVER_EXPLICIT)
+    lin = gpu.linearize()
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    np.testing.assert_array_equal(gpu.get_active()["obs_mask"], ext["obs_mask"])
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    print(check_blocks(lin, ne, orc, sc.cams0, sc.pts0, ext["obs_mask"], ext["cam_mask"].astype(bool), tol))
+    assert not lin["U"][:, 7:, :].any() and not lin["W"][:, 7:, :].any()  # no distortion rows
+
+
+@pytest.mark.parametrize("precision,solver", [(ba.BA_FP64, ba.BA_SOLVER_IMPLICIT),
+                                              (ba.BA_FP64, ba.BA_SOLVER_EXPLICIT),
+                                              (ba.BA_FP32, ba.BA_SOLVER_EXPLICIT),
+                                              (ba.BA_FP32, ba.BA_SOLVER_SPARSE)])
+def test_centre_model_damped_step_matches_oracle(precision, solver):
+    sc = geometric(12, 3000, 2, 12, 5.0, seed=41, camera_model="centre")
+    gpu, orc = pair(sc, precision, camera_model=ba.BA_CAMERA_CENTRE, solver=solver,
+                    pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6)
+    lam = 1e-3
+    g = gpu.solve_damped(lam)
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    o = orc.solve_step(ne, ext, lam)
+    check_step(g, o, *STEP_TOL[precision])
+    assert not g["dc"][:, 7:].any()
+
+
+def test_centre_model_trajectory_and_restrictions():
+    """FP32 LM with the centre model follows the oracle per iteration; the FP32
+    implicit solver (which recomputes the radial model's blocks) is refused, as is
+    the adjoint (no k1, k2 columns: the undamped system is singular); the
+    allocation-free cost follows the model too."""
+    sc = geometric(40, 20000, 3, 20, 10.0, seed=1001, camera_model="centre")
+    gpu, orc = pair(sc, ba.BA_FP32, camera_model=ba.BA_CAMERA_CENTRE)
+    assert gpu.solver_kind == ba.BA_SOLVER_EXPLICIT
+    log_g = gpu.solve(8)
+    orc.opts.solver = 1
+    c_o, p_o, log_o = orc.lm(sc.cams0, sc.pts0, 8)
+    for i, (a, b) in enumerate(zip(log_g, log_o)):
+        assert a["cost"] == pytest.approx(b["cost"], rel=1e-5), i
+        assert a["accepted"] == b["accepted"], i
+    c_g, _ = gpu.get_params()
+    np.testing.assert_array_equal(c_g[:, 7:], sc.cams0[:, 7:])  # k1, k2 untouched
+    with pytest.raises(ba.BAError):
+        ba.Problem.from_scene(sc, ba.Options(camera_model=ba.BA_CAMERA_CENTRE, solver=ba.BA_SOLVER_IMPLICIT))
+    with pytest.raises(ba.BAError):
+        gpu.backward(np.zeros_like(sc.cams0), np.zeros_like(sc.pts0))
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ba.eval_cost_noalloc(dev(sc.cams_gt, torch.float64), dev(sc.pts_gt, torch.float64),
+                         dev(sc.obs_cam, torch.int32), dev(sc.obs_pt, torch.int32),
+                         dev(sc.obs_uv, torch.float64), dev(sc.depth, torch.float64), out,
+                         options=ba.Options(camera_model=ba.BA_CAMERA_CENTRE))
+    torch.cuda.synchronize()
+    F_o, _ = orc.cost(sc.cams_gt, sc.pts_gt)
+    assert out[0].item() == pytest.approx(F_o, rel=1e-12)

@@ -609,3 +609,73 @@ def test_one_shot_freezes_the_first_active_set_and_dynamic_readmits():
     gt_valid, _ = oracle.OracleBA.from_scene(sc).predicate(sc.cams_gt, sc.pts_gt)
     assert acts_dyn[-1] > acts_dyn[0] and acts_dyn[-1] >= int(gt_valid.sum()) - 10
     assert err_dyn < err_once
+
+
+# --------------------------------------------------------------------------
+# the camera parameterisation of Sec. 3.2 (centre, rotation, focal length)
+# --------------------------------------------------------------------------
+
+def test_centre_model_projection_closed_form_and_equivalence():
+    """P = R (X - c): with R = I the pixel is f (X - c)_xy / (X - c)_z + (cx, cy); and
+    the same camera as [w, t = -R c, f, 0, 0] under the radial model projects the
+    same (one rotation, two parameterisations of its position)."""
+    X = np.array([0.3, -0.2, 0.5])
+    cam = np.array([0, 0, 0, 0.1, 0.05, -2.5, 480.0, 0.3, -0.2])  # k1, k2 ignored
+    r, _, _, z, uvh = oracle.observe(cam, X, np.zeros(2), 0.0, 0.0, model=1)
+    d = X - cam[3:6]
+    assert z == pytest.approx(d[2], abs=1e-15)
+    np.testing.assert_allclose(uvh, [480 * d[0] / d[2] + 320, 480 * d[1] / d[2] + 240], atol=1e-12)
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        w = rng.normal(size=3) * 0.5
+        c = rng.normal(size=3) + [0, 0, -3]
+        R = Rotation.from_rotvec(w).as_matrix()
+        X = rng.normal(size=3) * 0.3
+        cam1 = np.concatenate([w, c, [500.0, 0.0, 0.0]])
+        cam0 = np.concatenate([w, -R @ c, [500.0, 0.0, 0.0]])
+        a = oracle.observe(cam1, X, [300.0, 200.0], 0.3, 1.0, model=1)
+        b = oracle.observe(cam0, X, [300.0, 200.0], 0.3, 1.0, model=0)
+        np.testing.assert_allclose(a[0], b[0], rtol=1e-12, atol=1e-9)
+        np.testing.assert_allclose(a[2], b[2], rtol=1e-12, atol=1e-12)  # point block is the same
+
+
+def test_centre_model_jacobian_central_fd():
+    rng = np.random.default_rng(6)
+    for trial in range(30):
+        cam = np.concatenate([rng.normal(size=3) * 0.6, rng.normal(size=3) * 0.3 + [0, 0, -3],
+                              [500 + 20 * rng.normal(), 0.1, -0.1]])
+        X = rng.normal(size=3) * 0.5
+        uv = rng.uniform(0, 600, 2)
+        tau, wt = (1 / 3.1, 1.0) if trial % 2 else (0.0, 0.25)
+        r0, Jc, Jp, _, _ = oracle.observe(cam, X, uv, tau, wt, model=1)
+        h = 1e-6
+        for i in range(9):
+            rp = oracle.observe(_perturb_cam(cam, i, h), X, uv, tau, wt, model=1)[0]
+            rm = oracle.observe(_perturb_cam(cam, i, -h), X, uv, tau, wt, model=1)[0]
+            fd = (rp - rm) / (2 * h)
+            np.testing.assert_allclose(Jc[:, i], fd, rtol=1e-7, atol=1e-7 * max(1.0, np.abs(fd).max()))
+        assert not Jc[:, 7:].any()  # no distortion columns
+
+
+def test_centre_model_step_vs_dense_and_noise_free_convergence():
+    sc = tiny_scene(noise=True, outliers=True, camera_model="centre")
+    opts = oracle.OracleOptions(camera_model=1, invalid_depth_weight=1e-3)
+    ob = oracle.OracleBA.from_scene(sc, opts)
+    cams, pts = sc.cams0, sc.pts0
+    geom, _ = ob.predicate(cams, pts)
+    ext = ob.extract(geom)
+    ne = ob.normal_equations(cams, pts, ext["obs_mask"])
+    H, g, free, act = _dense_system(ob, cams, pts, ext["obs_mask"], ext)
+    lam = 1e-2
+    dx = np.linalg.solve(H + lam * np.diag(np.clip(np.diag(H), 1e-6, 1e32)), -g)
+    st = ob.solve_step(ne, ext, lam)
+    got = np.concatenate([st["dc"][free].ravel(), st["dp"][act].ravel()])
+    np.testing.assert_allclose(got, dx, rtol=1e-4, atol=1e-6 * np.abs(dx).max())
+    assert not st["dc"][:, 7:].any()
+    # exact measurements: the LM reaches zero cost and the true cameras
+    sc0 = scenes.make_scene("small", noise=False, outliers=False, camera_model="centre")
+    ob0 = oracle.OracleBA.from_scene(sc0, oracle.OracleOptions(camera_model=1))
+    assert ob0.cost(sc0.cams_gt, sc0.pts_gt)[0] < 1e-18
+    c, p, rows = ob0.lm(sc0.cams0, sc0.pts0, 20)
+    assert ob0.cost(c, p)[0] <= 1e-20 * rows[0]["cost"]
+    np.testing.assert_allclose(c[:, 3:7], sc0.cams_gt[:, 3:7], atol=1e-7)
