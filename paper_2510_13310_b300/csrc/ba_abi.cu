@@ -45,6 +45,7 @@ void set_error(const char* fmt, ...) {
   do {                                                                               \
     cudaError_t _e = (expr);                                                         \
     if (_e != cudaSuccess) {                                                         \
+      cudaGetLastError(); /* reported here: not left for the caller's next check */  \
       set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
       return _e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA;             \
     }                                                                                \

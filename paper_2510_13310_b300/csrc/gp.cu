@@ -662,6 +662,7 @@ void gp_error(const char* fmt, ...) {
   do {                                                                                         \
     cudaError_t _e = (expr);                                                                   \
     if (_e != cudaSuccess) {                                                                   \
+      cudaGetLastError(); /* reported here: not left for the caller's next check */            \
       gp_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__);    \
       return _e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA;                       \
     }                                                                                          \
@@ -824,6 +825,10 @@ ba_status gp_create_impl(const ba_gp_options* opts, void* stream, int64_t n_cams
       }
     pb->Cf = (int)map.size();
     pb->n = 3 * pb->Cf;
+    // the block-Jacobi PCG takes the centre system in 9-unknown super-blocks of
+    // three cameras: order padded to 9 ceil(Cf / 3) with identity rows
+    pb->Cs = (pb->Cf + 2) / 3;
+    pb->n_pad = 9 * pb->Cs;
     GST(galloc(pb, &pb->crank, (size_t)C));
     GST(galloc(pb, &pb->cam_map, (size_t)pb->Cf));
     if (C) GCU(cudaMemcpyAsync(pb->crank, rank.data(), sizeof(int) * C, cudaMemcpyHostToDevice, pb->stream));
@@ -889,8 +894,6 @@ ba_status gp_create_impl(const ba_gp_options* opts, void* stream, int64_t n_cams
     gp_error("GP solver must be BA_SOLVER_AUTO, BA_SOLVER_EXPLICIT or BA_SOLVER_DENSE");
     return BA_ERR_INVALID_ARG;
   }
-  pb->Cs = (pb->Cf + 2) / 3;
-  pb->n_pad = 9 * pb->Cs;
   pb->ld = spcg_row_stride<float>(std::max(pb->n_pad, 1));
   if ((size_t)pb->n_pad * pb->ld * 4 > ((size_t)16 << 30)) {
     gp_error("centre system of order %d is too large for the explicit solve", pb->n);
