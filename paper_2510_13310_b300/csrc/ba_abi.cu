@@ -543,13 +543,14 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     }
     // the block-sparse kernel owns whole cameras: at least one per block
     const int grid = std::max(1, std::min(pb->spcg_grid, pb->sparse ? Cf : (a.n + 7) / 8));
-    const size_t smem = spcg_smem_bytes<T>(a.n, (a.n + grid - 1) / grid, a.rows_in_smem, a.vecs_in_smem, Cf);
+    const size_t smem = pb->sparse ? bspcg_smem_bytes<T>(Cf, grid)
+                                   : spcg_smem_bytes<T>(a.n, (a.n + grid - 1) / grid, a.rows_in_smem, a.vecs_in_smem, Cf);
     if (smem > pb->spcg_smem) {
       set_error("explicit PCG launch needs %zu B of shared memory (planned %zu)", smem, pb->spcg_smem);
       return BA_ERR_INVALID_ARG;
     }
     // fresh tags for this launch; on wrap-around the words are cleared and tags restart at 1
-    const unsigned span = (unsigned)a.max_iters + 2u;
+    const unsigned span = (unsigned)a.max_iters + 3u;
     if (pb->spcg_tag == 0 || pb->spcg_tag > 0xFFFFFFFFu - span) {
       CU(cudaMemsetAsync(pb->spcg_words, 0,
                          sizeof(unsigned long long) * 2 * 9 * (size_t)pb->C * spcg_words_per_value(pb->fp64),
@@ -559,7 +560,8 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
     a.tag_base = pb->spcg_tag;
     pb->spcg_tag += span;
     CU(cudaEventRecord(pb->evk[0], pb->stream));
-    LAUNCH(1, launch_spcg<T>(a, grid, smem, pb->stream));
+    if (pb->sparse) LAUNCH(1, launch_bspcg<T>(a, grid, smem, pb->stream));
+    else LAUNCH(1, launch_spcg<T>(a, grid, smem, pb->stream));
     CU(cudaEventRecord(pb->evk[1], pb->stream));
     pb->evk_valid = true;
     }
@@ -1311,8 +1313,14 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       ST(dalloc(pb, &pb->spcg_words, nw));
       CU(cudaMemset(pb->spcg_words, 0, sizeof(unsigned long long) * nw));
     }
+    if (pb->sparse) {
+      // partitioned PCG: each block keeps its cameras' slices only
+      pb->spcg_grid = std::max(1, std::min(pb->num_sms, C));
+      pb->spcg_smem = pb->fp64 ? bspcg_smem_bytes<double>(C, pb->spcg_grid) : bspcg_smem_bytes<float>(C, pb->spcg_grid);
+    }
     const bool rs = pb->spcg_rows_in_smem != 0;
-    const void* sfn = pb->fp64 ? spcg_kernel_ptr<double>(rs, pb->sparse) : spcg_kernel_ptr<float>(rs, pb->sparse);
+    const void* sfn = pb->sparse ? (pb->fp64 ? bspcg_kernel_ptr<double>() : bspcg_kernel_ptr<float>())
+                                 : (pb->fp64 ? spcg_kernel_ptr<double>(rs) : spcg_kernel_ptr<float>(rs));
     CU(cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb->spcg_smem));
     int sper = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, sfn, spcg_threads(), pb->spcg_smem));

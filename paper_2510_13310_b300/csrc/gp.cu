@@ -301,53 +301,63 @@ __global__ void k_gp_pad(int n, int n_pad, float* Sh, long long ld) {
 }
 
 // Block-Jacobi preconditioner of the scaled centre system: the inverse of each
-// 9x9 diagonal super-block, by Cholesky factorisation (FP32, one thread per block;
-// a block that fails to factor falls back to the inverse diagonal).
-__global__ void k_gp_superblock_inv(int Cs, const float* __restrict__ Sh, long long ld, float* __restrict__ Dinv) {
-  const int sb = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sb >= Cs) return;
-  float L[81], Inv[81];
-  for (int i = 0; i < 9; ++i)
-    for (int j = 0; j < 9; ++j) L[9 * i + j] = Sh[(size_t)(9 * sb + i) * ld + 9 * sb + j];
+// 9x9 diagonal super-block by Cholesky factorisation (FP32), one warp per block:
+// lane i holds row i during the right-looking factorisation, then lane c solves
+// for column c of the inverse from the factor in shared memory.  A block that
+// fails to factor falls back to its inverse diagonal.
+constexpr int kSbWarps = 4;
+__global__ void __launch_bounds__(32 * kSbWarps) k_gp_superblock_inv(int Cs, const float* __restrict__ Sh, long long ld,
+                                                                      float* __restrict__ Dinv) {
+  __shared__ float Ls[kSbWarps][81];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int sb = blockIdx.x * kSbWarps + wl;
+  if (sb >= Cs) return;  // whole warps leave together
+  float row[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) row[j] = lane < 9 ? Sh[(size_t)(9 * sb + lane) * ld + 9 * sb + j] : 0.f;
+  const float diag = lane < 9 ? row[lane < 9 ? lane : 0] : 1.f;
   bool ok = true;
-  for (int j = 0; j < 9 && ok; ++j) {
-    float d = L[9 * j + j];
-    for (int k = 0; k < j; ++k) d -= L[9 * j + k] * L[9 * j + k];
-    if (!(d > 0.f)) {
-      ok = false;
-      break;
-    }
-    d = sqrtf(d);
-    L[9 * j + j] = d;
-    for (int i = j + 1; i < 9; ++i) {
-      float v = L[9 * i + j];
-      for (int k = 0; k < j; ++k) v -= L[9 * i + k] * L[9 * j + k];
-      L[9 * i + j] = v / d;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float akk = __shfl_sync(0xffffffffu, row[k], k);
+    ok = ok && akk > 0.f;
+    const float dk = sqrtf(fmaxf(akk, 1e-30f));
+    // column k of L: L[i][k] = A[i][k] / d for i > k, d on the diagonal
+    const float lik = lane == k ? dk : (lane > k ? row[k] / dk : 0.f);
+    row[k] = lik;
+#pragma unroll
+    for (int j = k + 1; j < 9; ++j) {
+      const float ljk = __shfl_sync(0xffffffffu, lik, j);
+      if (lane > k && j <= lane) row[j] -= lik * ljk;
     }
   }
-  if (ok) {
-    // columns of (L L^T)^-1: forward then backward substitution of each unit vector
-    for (int c = 0; c < 9; ++c) {
-      float y[9];
-      for (int i = 0; i < 9; ++i) {
-        float v = i == c ? 1.f : 0.f;
-        for (int k = 0; k < i; ++k) v -= L[9 * i + k] * y[k];
-        y[i] = v / L[9 * i + i];
-      }
-      for (int i = 8; i >= 0; --i) {
-        float v = y[i];
-        for (int k = i + 1; k < 9; ++k) v -= L[9 * k + i] * Inv[9 * k + c];
-        Inv[9 * i + c] = v / L[9 * i + i];
-      }
-    }
-  } else {
-    for (int i = 0; i < 81; ++i) Inv[i] = 0.f;
+  if (lane < 9)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) Ls[wl][9 * lane + j] = j <= lane ? row[j] : 0.f;
+  __syncwarp();
+  float inv[9];
+  if (ok && lane < 9) {
+    // column c = lane: L y = e_c, then L^T x = y
+    float y[9];
+#pragma unroll
     for (int i = 0; i < 9; ++i) {
-      const float d = Sh[(size_t)(9 * sb + i) * ld + 9 * sb + i];
-      Inv[10 * i] = d > 0.f ? 1.f / d : 1.f;
+      float v = i == lane ? 1.f : 0.f;
+#pragma unroll
+      for (int k2 = 0; k2 < i; ++k2) v -= Ls[wl][9 * i + k2] * y[k2];
+      y[i] = v / Ls[wl][9 * i + i];
+    }
+#pragma unroll
+    for (int i = 8; i >= 0; --i) {
+      float v = y[i];
+#pragma unroll
+      for (int k2 = i + 1; k2 < 9; ++k2) v -= Ls[wl][9 * k2 + i] * inv[k2];
+      inv[i] = v / Ls[wl][9 * i + i];
     }
   }
-  for (int i = 0; i < 81; ++i) Dinv[81 * (size_t)sb + i] = Inv[i];
+  if (lane < 9)
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      Dinv[81 * (size_t)sb + 9 * i + lane] = ok ? inv[i] : (i == lane ? (diag > 0.f ? 1.f / diag : 1.f) : 0.f);
 }
 
 __global__ void k_gp_ones(int n, double* __restrict__ dscale) {
@@ -1007,8 +1017,8 @@ ba_status gp_solve_damped(ba_gp_problem* pb, double lambda, DenseResult* dres) {
     } else {
       // block-Jacobi PCG on the scaled system with the explicit PCG kernel: three
       // cameras form one of its 9-unknown blocks; unit scaling (already scaled)
-      GLAUNCH(pb, 1, gpk::k_gp_superblock_inv<<<gpk::blocks(pb->Cs, 64), 64, 0, pb->stream>>>(pb->Cs, pb->Sh, pb->ld,
-                                                                                              pb->Dinv));
+      GLAUNCH(pb, 1, gpk::k_gp_superblock_inv<<<gpk::blocks(pb->Cs, gpk::kSbWarps), 32 * gpk::kSbWarps, 0,
+                                                pb->stream>>>(pb->Cs, pb->Sh, pb->ld, pb->Dinv));
       SpcgArgs<float> a{};
       a.Shat = pb->Sh;
       a.Dinv = pb->Dinv;

@@ -247,6 +247,13 @@ template <typename T>
 const void* spcg_kernel_ptr(bool rows_in_smem, bool sparse = false);
 template <typename T>
 cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
+// partitioned PCG on the block-sparse system (each block owns a slice of cameras)
+template <typename T>
+cudaError_t launch_bspcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
+template <typename T>
+size_t bspcg_smem_bytes(int Cf, int grid);
+template <typename T>
+const void* bspcg_kernel_ptr();
 // the explicit PCG's preconditioner blocks into M [Cf][kSpcgMStride], for a shared copy
 constexpr int kSpcgMStride = 84;
 template <typename T>

@@ -1007,6 +1007,281 @@ cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_
                                      dim3(kSpcgThreads), args, smem, s);
 }
 
+// ---------------------------------------------------------------------------
+// Partitioned PCG on the block-sparse system.  With few blocks per row, the
+// redundant design above (every block updates every vector entry) spends its
+// time on the full-length vector work; here block b owns the cameras of ranks
+// [Cf b / G, Cf (b+1) / G) and keeps only their slices of x, r, z, p and q.  Per
+// iteration: (1) the matvec of the owned block rows, reading the p entries of
+// other blocks' cameras from their published words; (2) the block's partial
+// (p, q), published, and the G partials summed by every block in one fixed order
+// (the same alpha everywhere); (3) the slice updates, z = M r, the partials (r, r)
+// and (r, z), exchanged the same way; (4) p = z + beta p, published.  Word sets
+// alternate by iteration parity: a block writes iteration i + 2 only after it
+// summed every block's last partials of i + 1, which each block published after
+// its reads of iteration i.  Tags: tag_base for the set-up exchange, tag_base + 1
+// + it for iteration it (a launch spans max_iters + 3 tags).
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T poll_word(const unsigned long long* w, unsigned tag, long long timeout_ns, int* late) {
+  constexpr int W = spcg_words<T>();
+  unsigned long long v[W];
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    bool ready = true;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      v[k] = ld_relaxed_u64(w + k);
+      ready &= (unsigned)(v[k] >> 32) == tag;
+    }
+    if (ready) return spcg_unpack<T>(v);
+    if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
+      *late = 1;
+      return T(0);
+    }
+  }
+}
+
+// partials of one exchange: K dots of this block, published as K values (their
+// hi and lo words for FP32), then the G blocks' values summed in block order
+template <int K, typename D>
+__device__ __forceinline__ int exchange_partials(D (&v)[K], void* red, unsigned long long* set, int G, int bid,
+                                                 unsigned tag, long long timeout_ns, int late_in) {
+  using T = std::conditional_t<std::is_same<D, double>::value, double, float>;
+  constexpr int W = spcg_words<T>();
+  constexpr int NV = std::is_same<D, double>::value ? 1 : 2;  // values per dot
+  int late = late_in;
+  late = block_allsum_dot<K>(v, red, late);
+  if (threadIdx.x < K * NV) {
+    const int k = threadIdx.x / NV;
+    T val;
+    if constexpr (NV == 1) val = (T)reinterpret_cast<const double*>(&v[k])[0];
+    else val = (threadIdx.x & 1) ? reinterpret_cast<const F2*>(&v[k])->l : reinterpret_cast<const F2*>(&v[k])->h;
+    spcg_publish<T>(set + ((size_t)bid * 8 + threadIdx.x) * W, val, tag);
+  }
+  D acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) dot_zero(acc[k]);
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if constexpr (NV == 1) {
+        acc[k] = dot_add(acc[k], poll_word<T>(set + ((size_t)g * 8 + k) * W, tag, timeout_ns, &late));
+      } else {
+        const float h = poll_word<float>(set + ((size_t)g * 8 + 2 * k) * W, tag, timeout_ns, &late);
+        const float l = poll_word<float>(set + ((size_t)g * 8 + 2 * k + 1) * W, tag, timeout_ns, &late);
+        acc[k] = dot_add(acc[k], F2{h, l});
+      }
+    }
+  }
+  late = block_allsum_dot<K>(acc, reinterpret_cast<char*>(red) + kSpcgRedStride * sizeof(double), late);
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = acc[k];
+  return late;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSpcgThreads, 1) k_bspcg(SpcgArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using D = Dot<T>;
+  constexpr int W = spcg_words<T>();
+  const int G = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int Cf = a.Cf, n = a.n;
+  const int f0 = (int)(((long long)Cf * bid) / G), f1 = (int)(((long long)Cf * (bid + 1)) / G);
+  const int nf = f1 - f0, m = 9 * nf;
+  // shared memory: two block-sum buffers, the slices x r z p q, preconditioner blocks
+  unsigned char* sp = smem_raw;
+  void* red = sp;
+  sp += 4 * kSpcgRedStride * sizeof(double);
+  T* xs = reinterpret_cast<T*>(sp);
+  T* rs = xs + m;
+  T* zs = rs + m;
+  T* ps = zs + m;
+  T* qs = ps + m;
+  T* Ms = qs + m;  // kMStride per owned camera
+  const T* dinv = reinterpret_cast<const T*>(a.dscale + n);
+  unsigned long long* pw = a.words;                                    // [2][n][W]
+  unsigned long long* swd = a.words + (size_t)2 * n * W;               // [2][G][8][W]
+  const size_t ps_words = (size_t)n * W, ss_words = (size_t)G * 8 * W;
+  int late = 0;
+  for (int f = tid; f < nf; f += blockDim.x) {
+    // the owned cameras' preconditioner blocks (scaled, symmetrised)
+    const T* Df = a.Dinv + 81 * (size_t)(f0 + f);
+    T d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = (T)a.dscale[9 * (f0 + f) + i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int j = 0; j < 9; ++j) Ms[kMStride * f + mrow(i) + j] = (T(0.5) * (Df[9 * i + j] + Df[9 * j + i])) * (d[i] * d[j]);
+  }
+  __syncthreads();
+  // r = b^, z = M^ r, p = z, x = 0 on the owned slice; (r, z) and (r, r)
+  D d0[2];
+  dot_zero(d0[0]);
+  dot_zero(d0[1]);
+  for (int f = tid; f < nf; f += blockDim.x) {
+    const int e = 9 * f, ge = 9 * (f0 + f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      rs[e + i] = a.b[ge + i] * dinv[ge + i];
+      xs[e + i] = T(0);
+    }
+    spcg_precond(Ms + kMStride * f, rs + e, zs + e);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      ps[e + i] = zs[e + i];
+      dot_fma(d0[0], rs[e + i], zs[e + i]);
+      dot_fma(d0[1], rs[e + i], rs[e + i]);
+    }
+  }
+  const unsigned tag0 = a.tag_base;
+  late = exchange_partials<2>(d0, red, swd + ss_words, G, bid, tag0, a.timeout_ns, late);
+  D rz = d0[0];
+  const double bnorm = sqrt(dot_value(d0[1]));
+  D stop_rr;
+  {
+    const double st = (a.tol * bnorm) * (a.tol * bnorm);
+    if constexpr (sizeof(T) == 4) stop_rr = f2_from_double(st);
+    else stop_rr = st;
+  }
+  D rr_last = d0[1];
+  int it = 0;
+  const int grp = lane / 9, ra = lane - 9 * grp;
+  while (bnorm > 0.0 && it < a.max_iters && !late) {
+    const unsigned tag = a.tag_base + 1u + (unsigned)it;
+    unsigned long long* pset = pw + (size_t)(it & 1) * ps_words;
+    unsigned long long* sset = swd + (size_t)(it & 1) * ss_words;
+    // publish this iteration's p slice
+    for (int e = tid; e < m; e += blockDim.x) spcg_publish<T>(pset + (size_t)(9 * f0 + e) * W, ps[e], tag);
+    __syncthreads();  // the slice is read from shared memory below by other warps
+    // matvec of the owned block rows: one warp per camera, three groups of nine
+    // lanes; the p entries of four rounds of three blocks are polled together
+    // (one L2 round trip for twelve blocks instead of one per three)
+    constexpr int kRounds = 4;
+    for (int f = warp; f < nf; f += nwarps) {
+      const int c = a.cam_map[f0 + f];
+      const int e0 = a.brp[c], e1 = a.brp[c + 1];
+      T acc = T(0);
+      for (int eb = e0; eb < e1; eb += 3 * kRounds) {
+        int2 ent[kRounds];
+        int cf[kRounds];
+        T pv[kRounds];
+        unsigned long long wv[kRounds][W];
+        bool remote[kRounds];
+#pragma unroll
+        for (int u = 0; u < kRounds; ++u) {
+          const int e = eb + 3 * u + grp;
+          ent[u] = make_int2(0, 0);
+          cf[u] = -1;
+          if (lane < 27 && e < e1) {
+            ent[u] = a.bent[e];
+            cf[u] = a.crank[ent[u].x];
+          }
+          remote[u] = cf[u] >= 0 && (cf[u] < f0 || cf[u] >= f1);
+          pv[u] = (cf[u] >= 0 && !remote[u]) ? ps[9 * (cf[u] - f0) + ra] : T(0);
+        }
+        // lane ra of a group fetches entry ra of p for the column camera
+        const uint64_t t0 = globaltimer_ns();
+        for (;;) {
+          bool ready = true;
+#pragma unroll
+          for (int u = 0; u < kRounds; ++u)
+            if (remote[u]) {
+#pragma unroll
+              for (int k = 0; k < W; ++k) {
+                wv[u][k] = ld_relaxed_u64(pset + (size_t)(9 * cf[u] + ra) * W + k);
+                ready &= (unsigned)(wv[u][k] >> 32) == tag;
+              }
+            }
+          if (ready) break;
+          if ((long long)(globaltimer_ns() - t0) > a.timeout_ns) {
+            late = 1;
+            break;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kRounds; ++u) {
+          if (remote[u]) pv[u] = late ? T(0) : spcg_unpack<T>(wv[u]);
+          const T* row = a.Bs + (size_t)kBlkStride * ent[u].y + 9 * ra;
+#pragma unroll
+          for (int t = 0; t < 9; ++t) {
+            const T pt = __shfl_sync(0xffffffffu, pv[u], 9 * grp + t);
+            if (cf[u] >= 0) acc = fma(__ldg(row + t), pt, acc);
+          }
+        }
+      }
+      const T v1 = __shfl_down_sync(0xffffffffu, acc, 9);
+      const T v2 = __shfl_down_sync(0xffffffffu, acc, 18);
+      if (lane < 9) qs[9 * f + lane] = (acc + v1) + v2;
+    }
+    __syncthreads();
+    D d1[1];
+    dot_zero(d1[0]);
+    for (int e = tid; e < m; e += blockDim.x) dot_fma(d1[0], ps[e], qs[e]);
+    late = exchange_partials<1>(d1, red, sset, G, bid, tag, a.timeout_ns, late);
+    if (late) break;
+    const D pq = d1[0];
+    if (!dot_pos_finite(pq)) {
+      if (bid == 0 && tid == 0) atomicOr(a.err, 2);
+      break;
+    }
+    const T alpha = (T)dot_div(rz, pq);
+    D d2[2];
+    dot_zero(d2[0]);
+    dot_zero(d2[1]);
+    for (int e = tid; e < m; e += blockDim.x) {
+      xs[e] = fma(alpha, ps[e], xs[e]);
+      rs[e] = fma(-alpha, qs[e], rs[e]);
+    }
+    __syncthreads();
+    for (int f = tid; f < nf; f += blockDim.x) {
+      spcg_precond(Ms + kMStride * f, rs + 9 * f, zs + 9 * f);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        dot_fma(d2[0], rs[9 * f + i], rs[9 * f + i]);
+        dot_fma(d2[1], rs[9 * f + i], zs[9 * f + i]);
+      }
+    }
+    late = exchange_partials<2>(d2, red, sset + (size_t)2 * W, G, bid, tag, a.timeout_ns, late);
+    ++it;
+    const D rr = d2[0], rz_new = d2[1];
+    rr_last = rr;
+    if (late || dot_le(rr, stop_rr)) break;
+    const T beta = dot_nonzero(rz) ? (T)dot_div(rz_new, rz) : T(0);
+    rz = rz_new;
+    for (int e = tid; e < m; e += blockDim.x) ps[e] = fma(beta, ps[e], zs[e]);
+    __syncthreads();
+  }
+  if (late && tid == 0) atomicOr(a.err, 1);
+  __syncthreads();
+  for (int e = tid; e < m; e += blockDim.x) a.x[9 * f0 + e] = xs[e] * dinv[9 * f0 + e];
+  if (bid == 0 && tid == 0) {
+    a.sc->pcg_iters = it;
+    a.sc->pcg_bnorm = bnorm;
+    a.sc->pcg_rel_res = bnorm > 0.0 ? sqrt(dot_value(rr_last)) / bnorm : 0.0;
+  }
+}
+
+template <typename T>
+size_t bspcg_smem_bytes(int Cf, int grid) {
+  const int nf = (Cf + grid - 1) / grid + 1;
+  return 4 * kSpcgRedStride * sizeof(double) + sizeof(T) * ((size_t)5 * 9 * nf + (size_t)kMStride * nf) + 16;
+}
+
+template <typename T>
+const void* bspcg_kernel_ptr() {
+  return reinterpret_cast<const void*>(&k_bspcg<T>);
+}
+
+template <typename T>
+cudaError_t launch_bspcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s) {
+  void* args[] = {const_cast<SpcgArgs<T>*>(&a)};
+  return cudaLaunchCooperativeKernel(bspcg_kernel_ptr<T>(), dim3(grid), dim3(kSpcgThreads), args, smem, s);
+}
+
 int spcg_threads() { return kSpcgThreads; }
 int spcg_words_per_value(bool fp64) { return kSpcgReplicas * (fp64 ? spcg_words<double>() : spcg_words<float>()); }
 
@@ -1130,6 +1405,9 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \
   template const void* spcg_kernel_ptr<T>(bool, bool);                                                   \
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \
+  template cudaError_t launch_bspcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                 \
+  template size_t bspcg_smem_bytes<T>(int, int);                                                       \
+  template const void* bspcg_kernel_ptr<T>();                                                          \
   template cudaError_t launch_spcg_precond<T>(int, const T*, const double*, T*, cudaStream_t);          \
   template cudaError_t launch_backsub_pts<T>(const Layout&, const ModelParams&, const T*, const T*,    \
                                              const uint8_t*, const uint8_t*, const int*, const T*,     \
