@@ -40,7 +40,7 @@ METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 
 # DRAM bytes (read + write) of one launch of each roofline kernel, from ncu
 # captures of this workload (profiles/top_kernels_traffic_medium_1M_obs.md); None
 # once the kernel has changed since the counters were taken.
-NCU_TRAFFIC = {"k_spcg": None, "k_pcg": None, "k_form_S_runs": 303936768 + 7791360}
+NCU_TRAFFIC = {"k_spcg": 13155328 + 19200, "k_pcg": None, "k_form_S_runs": 303936768 + 7791360}
 WORKLOAD = "medium"
 LM_ITERS = 30
 E2E_RUNS = 3
