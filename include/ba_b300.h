@@ -225,6 +225,12 @@ ba_status ba_eval_cost(ba_problem* pb, const double* cams, const double* pts, do
  * entries are dropped.  Outputs: dL_duv [N][2], dL_ddepth [N] in the input
  * order, zero for inactive observations.  Gradients with respect to the initial
  * parameters are zero (not returned).  The next LM step re-linearises.
+ * BA_FP32 problems refine mu four times against the FP64 residual a - H mu (H
+ * from the FP64 state), each correction solved with the same FP32 solver; the
+ * corrections reuse the formed reduced camera system (explicit and block-sparse
+ * solvers) or its tensor-core factor (dense solver), and mu and the outputs are
+ * formed in FP64.  The first ba_backward of an FP32 problem allocates the
+ * refinement's buffers (about 24 N + 72 P + 144 C bytes of device memory). 
  * Errors: BA_ERR_NONFINITE if the undamped system is singular, BA_ERR_NOT_CONVERGED
  * if PCG hit pcg_max_iters (outputs still written). */
 ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_dpts,

@@ -94,6 +94,11 @@ struct ba_problem {
   double* cams64[2] = {nullptr, nullptr};
   double* pts64[2] = {nullptr, nullptr};
   double* camw64[2] = {nullptr, nullptr};
+  // adjoint refinement (FP32 problems, allocated by the first ba_backward): the
+  // right-hand side, mu, per-observation rho' J mu, (H mu)_p and camera-chunk partials
+  bool reuse_system = false;  // the next explicit solve reuses the formed S^ / dense factor
+  double *adj_ac = nullptr, *adj_ap = nullptr, *adj_muc = nullptr, *adj_mup = nullptr, *adj_u = nullptr,
+         *adj_hp = nullptr, *adj_part = nullptr;
   void* camw[2] = {nullptr, nullptr};
   void* ptsw[2] = {nullptr, nullptr};
   uint8_t* bits[2] = {nullptr, nullptr};
@@ -480,13 +485,18 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   CU(cudaMemsetAsync(&pb->sc->pcg_iters, 0, sizeof(int), pb->stream));
   CU(cudaMemsetAsync(&pb->sc->pcg_rel_res, 0, sizeof(double), pb->stream));
   if (Cf > 0) {
-    LAUNCH(3, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
-                               (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
-                               Cf, (T*)pb->Yhat, pb->sparse ? (T*)pb->Bs : (T*)pb->Shat, pb->form_lanes,
-                               pb->num_sms, pb->evf[0], pb->evf[1], pb->join_pending ? pb->join : nullptr,
-                               pb->stream, pb->cam_map, pb->sparse));
-    pb->evf_valid = true;
-    pb->join_pending = false;  // launch_form_S made the main stream wait for the chain
+    if (pb->reuse_system) {
+      // S^ (and the dense factor) of the previous solve at the same state and damping
+      if (pb->join_pending) CU(cudaStreamWaitEvent(pb->stream, pb->join, 0));
+    } else {
+      LAUNCH(3, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
+                                 (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
+                                 Cf, (T*)pb->Yhat, pb->sparse ? (T*)pb->Bs : (T*)pb->Shat, pb->form_lanes,
+                                 pb->num_sms, pb->evf[0], pb->evf[1], pb->join_pending ? pb->join : nullptr,
+                                 pb->stream, pb->cam_map, pb->sparse));
+      pb->evf_valid = true;
+    }
+    pb->join_pending = false;  // the main stream waits for the chain
     bool solved = false;
     if constexpr (sizeof(T) == 4) {
       if (pb->dense) {
@@ -498,8 +508,9 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
         LAUNCH(1, launch_scale_vec(n, (const float*)pb->bvec, dinv, bh, pb->stream));
         CU(cudaEventRecord(pb->evk[0], pb->stream));
         DenseResult res;
+        if (pb->reuse_system) res.flags = pb->dense_last.flags, res.shift = pb->dense_last.shift;
         CU(dense_spd_solve(pb->dw, (const float*)pb->Shat, spcg_row_stride<float>(n), n, bh, xh, pb->opt.pcg_rel_tol,
-                           pb->opt.pcg_max_iters, pb->num_sms, pb->stream, &res));
+                           pb->opt.pcg_max_iters, pb->num_sms, pb->stream, &res, pb->reuse_system));
         CU(cudaEventRecord(pb->evk[1], pb->stream));
         pb->evk_valid = true;
         pb->launches += res.launches;
@@ -695,17 +706,59 @@ ba_status solve_damped(ba_problem* pb, double lambda) {
 }
 
 // Implicit adjoint: undamped Schur solve of H mu = dL/dtheta (gradient slot
-// replaced by -dL/dtheta), then rho'_k (J_k mu) per observation.
+// replaced by -dL/dtheta), then rho'_k (J_k mu) per observation.  FP32 problems
+// refine mu against the FP64 residual a - H mu (kAdjRefineSteps corrections, each
+// solved by the same FP32 Schur solve), accumulate it in FP64 and form the
+// outputs in FP64: the scale direction of a problem with depth priors is too
+// weakly determined for a single FP32 solve.
+constexpr int kAdjRefineSteps = 4;
 template <typename T>
 ba_status backward_t(ba_problem* pb, const double* dc, const double* dpts, double* duv, double* dd) {
-  LAUNCH(1, launch_adjoint_rhs<T>(pb->C, pb->P, pb->cams64[pb->cur], pb->crank, pb->pt_act, dc, dpts,
-                                  (T*)pb->Ug, (T*)pb->gp, pb->stream));
+  const bool refine = !pb->fp64;
+  const int C = pb->C, P = pb->P, N = pb->N;
+  if (refine && !pb->adj_ac) {
+    ST(dalloc(pb, &pb->adj_ac, (size_t)9 * C));
+    ST(dalloc(pb, &pb->adj_ap, (size_t)3 * P));
+    ST(dalloc(pb, &pb->adj_muc, (size_t)9 * C));
+    ST(dalloc(pb, &pb->adj_mup, (size_t)3 * P));
+    ST(dalloc(pb, &pb->adj_u, (size_t)3 * N));
+    ST(dalloc(pb, &pb->adj_hp, (size_t)3 * P));
+    ST(dalloc(pb, &pb->adj_part, (size_t)9 * std::max(1, pb->n_chunks)));
+  }
+  LAUNCH(1, launch_adjoint_rhs<T>(C, P, pb->cams64[pb->cur], pb->crank, pb->pt_act, dc, dpts, (T*)pb->Ug,
+                                  (T*)pb->gp, pb->stream, refine ? pb->adj_ac : nullptr,
+                                  refine ? pb->adj_ap : nullptr));
   pb->linearized = false;  // the gradient slots now hold the adjoint right-hand side
   ST(schur_t<T>(pb, 0.0));
   ST(pcg_t<T>(pb, 0.0));
   int s = pb->cur;
-  LAUNCH(1, launch_adjoint_obs<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
-                                  pb->crank, (const T*)pb->x, (const T*)pb->dp, duv, dd, pb->stream));
+  if (!refine) {
+    LAUNCH(1, launch_adjoint_obs<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
+                                    pb->crank, (const T*)pb->x, (const T*)pb->dp, duv, dd, pb->stream));
+    return BA_OK;
+  }
+  const int Cf = pb->n_cam_free;
+  LAUNCH(1, launch_adj_mu_add<T>(Cf, P, (const T*)pb->x, (const T*)pb->dp, pb->adj_muc, pb->adj_mup, true,
+                                 pb->stream));
+  // the corrections reuse the formed S^ (explicit and block-sparse systems) or the
+  // dense factor: only the reduced right-hand side, the PCG and the back-substitution run
+  ba_status st = BA_OK;
+  for (int r = 0; r < kAdjRefineSteps && st == BA_OK; ++r) {
+    LAUNCH(2, launch_adj_hmu(pb->L, pb->mp, pb->camw64[s], pb->pts64[s], pb->obs_act, pb->obs_act_co, pb->crank,
+                             pb->adj_muc, pb->adj_mup, pb->adj_u, pb->adj_hp, pb->adj_part, pb->stream));
+    LAUNCH(1, launch_adj_residual<T>(C, P, pb->L.cam_chunk, pb->crank, pb->pt_act, pb->adj_part, pb->adj_hp,
+                                     pb->adj_ac, pb->adj_ap, (T*)pb->Ug, (T*)pb->gp, pb->stream));
+    pb->reuse_system = true;
+    st = schur_t<T>(pb, 0.0);
+    if (st == BA_OK) st = pcg_t<T>(pb, 0.0);
+    pb->reuse_system = false;
+    if (st == BA_OK)
+      LAUNCH(1, launch_adj_mu_add<T>(Cf, P, (const T*)pb->x, (const T*)pb->dp, pb->adj_muc, pb->adj_mup, false,
+                                     pb->stream));
+  }
+  ST(st);
+  LAUNCH(1, launch_adjoint_obs64(pb->L, pb->mp, pb->camw64[s], pb->pts64[s], pb->obs_act, pb->crank, pb->adj_muc,
+                                 pb->adj_mup, duv, dd, pb->stream));
   return BA_OK;
 }
 
@@ -1124,10 +1177,11 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
                              it * (4.0 * n * n / 4.9e12 + 10e-6);
         const double t_imp = no_implicit ? 1e300 : it * (N * 66e-12 + P * 245e-12);
         // and only within the explicit system's memory bound below
-        auto_explicit = t_exp < t_imp && (size_t)81 * C * C * (R + 8) <= ((size_t)8 << 30);
+        const bool exp_fits = (size_t)81 * C * C * (R + 8) <= ((size_t)8 << 30);
+        auto_explicit = t_exp < t_imp && exp_fits;
         // the block-sparse system is priced once the co-visibility runs are known
         auto_sparse_cand = true;
-        auto_t_exp = auto_explicit ? t_exp : 1e300;
+        auto_t_exp = exp_fits ? t_exp : 1e300;
         auto_t_imp = t_imp;
         auto_pairs = pairs;
       }
@@ -1190,20 +1244,27 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     pb->pcg_stages -= 1;
   }
   if (pb->pcg_smem > (size_t)dev_smem_optin) {
-    set_error("camera system of %d cameras needs %zu B of shared memory per block (limit %d)", C,
-              pb->pcg_smem, dev_smem_optin);
-    return BA_ERR_INVALID_ARG;
+    // the implicit kernel keeps the camera vectors in shared memory; an explicit
+    // system (chosen, or a candidate of AUTO) needs none of it
+    if (!pb->explicit_S) {
+      set_error("camera system of %d cameras needs %zu B of shared memory per block (limit %d)", C,
+                pb->pcg_smem, dev_smem_optin);
+      return BA_ERR_INVALID_ARG;
+    }
+    auto_t_imp = 1e300;
+    pb->pcg_grid = 1;
+  } else {
+    const void* kfn = pb->fp64 ? pcg_kernel_ptr<double>() : pcg_kernel_ptr<float>();
+    CU(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb->pcg_smem));
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, pcg_threads(), pb->pcg_smem));
+    if (per_sm < 1) {
+      set_error("PCG kernel cannot be resident");
+      return BA_ERR_INVALID_ARG;
+    }
+    // at most two blocks per SM: fewer blocks means fewer partial vectors to reduce
+    pb->pcg_grid = std::max(1, std::min(std::min(per_sm, 2) * pb->num_sms, std::max(1, pb->n_tiles)));
   }
-  const void* kfn = pb->fp64 ? pcg_kernel_ptr<double>() : pcg_kernel_ptr<float>();
-  CU(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb->pcg_smem));
-  int per_sm = 0;
-  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, pcg_threads(), pb->pcg_smem));
-  if (per_sm < 1) {
-    set_error("PCG kernel cannot be resident");
-    return BA_ERR_INVALID_ARG;
-  }
-  // at most two blocks per SM: fewer blocks means fewer partial vectors to reduce
-  pb->pcg_grid = std::max(1, std::min(std::min(per_sm, 2) * pb->num_sms, std::max(1, pb->n_tiles)));
   ST(dalloc_bytes(pb, &pb->partials, R * (size_t)pb->pcg_grid * std::max(1, n_max)));
   // dot-product slots of the implicit PCG kernel: [2 parities][grid][4]
   ST(dalloc(pb, &pb->dots, (size_t)2 * 4 * pb->pcg_grid));

@@ -802,15 +802,20 @@ cudaError_t dense_dot(const float* a, const float* b, int n, double* part, doubl
 
 // Factor S^ (n x n, ld_s) into the padded work matrix and solve S^ x = b.
 cudaError_t dense_spd_solve(const DenseWork& w, const float* S, long long ld_s, int n, const float* b, float* x,
-                            double tol, int max_iters, int num_sms, cudaStream_t s, DenseResult* res) {
+                            double tol, int max_iters, int num_sms, cudaStream_t s, DenseResult* res,
+                            bool reuse_factor) {
   const int np = (n + kPt - 1) / kPt * kPt, T = np / kPt;
   res->iters = 0;
   res->rel_res = 0.0;
-  res->flags = 0;
-  res->shift = 0.0;
+  if (reuse_factor) {
+    res->flags &= 32;  // the factor of the previous call stands, with its shift and pivot flag
+  } else {
+    res->flags = 0;
+    res->shift = 0.0;
+  }
   long long nl = 0;
   cudaError_t e = cudaSuccess;
-  for (int attempt = 0; attempt < 3; ++attempt) {
+  for (int attempt = 0; attempt < 3 && !reuse_factor; ++attempt) {
     const float shift = attempt == 0 ? 0.f : (attempt == 1 ? 1e-3f : 1e-1f);
     e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
     if (e == cudaSuccess)

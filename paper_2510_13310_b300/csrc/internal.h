@@ -156,8 +156,11 @@ struct DenseResult {
 };
 cudaError_t dense_trsv(bool back, const float* L, long long ld, const float* Linv, const float* rhs, float* out,
                        int T, unsigned* flags, unsigned epoch, int* err, int num_sms, cudaStream_t s);
+// reuse_factor: S and the factor in w.A are those of the previous call (whose
+// result *res still holds); only the preconditioned CG runs
 cudaError_t dense_spd_solve(const DenseWork& w, const float* S, long long ld_s, int n, const float* b, float* x,
-                            double tol, int max_iters, int num_sms, cudaStream_t s, DenseResult* res);
+                            double tol, int max_iters, int num_sms, cudaStream_t s, DenseResult* res,
+                            bool reuse_factor = false);
 cudaError_t launch_scale_vec(int n, const float* a, const float* d, float* out, cudaStream_t s);
 cudaError_t launch_set_pcg_info(Scalars* sc, int iters, double rel, int* err, int errbits, cudaStream_t s);
 
@@ -287,9 +290,27 @@ cudaError_t launch_candidate(int C, int P, const int* crank, const T* x, const T
                              int model = 0);
 template <typename T>
 cudaError_t launch_scatter_cams(int C, const int* crank, const T* x, double* dc, cudaStream_t s);
+// a_c [9C], a_p [3P] (nullable): the right-hand side dL/dtheta in the solve's coordinates, FP64
 template <typename T>
 cudaError_t launch_adjoint_rhs(int C, int P, const double* cams64, const int* crank, const uint8_t* pt_act,
-                               const double* dL_dc, const double* dL_dp, T* Ug, T* gp, cudaStream_t s);
+                               const double* dL_dc, const double* dL_dp, T* Ug, T* gp, cudaStream_t s,
+                               double* a_c = nullptr, double* a_p = nullptr);
+// FP64-residual refinement of the adjoint solve (adjoint.cu): H mu in FP64 from the
+// FP64 state (u_obs [3N] point order, hmu_p [3P], part [9 n_chunks]), the residual
+// a - H mu into the gradient slots, mu accumulation, and the outputs from mu
+cudaError_t launch_adj_hmu(const Layout& L, const ModelParams& mp, const double* camw64, const double* pts64,
+                           const uint8_t* act_po, const uint8_t* act_co, const int* crank, const double* mu_c,
+                           const double* mu_p, double* u_obs, double* hmu_p, double* part, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_residual(int C, int P, const int* cam_chunk, const int* crank, const uint8_t* pt_act,
+                                const double* part, const double* hmu_p, const double* a_c, const double* a_p,
+                                T* Ug, T* gp, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_mu_add(int Cf, int P, const T* x, const T* dp, double* mu_c, double* mu_p, bool first,
+                              cudaStream_t s);
+cudaError_t launch_adjoint_obs64(const Layout& L, const ModelParams& mp, const double* camw64, const double* pts64,
+                                 const uint8_t* act_po, const int* crank, const double* mu_c, const double* mu_p,
+                                 double* duv, double* ddepth, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adjoint_obs(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
                                const uint8_t* act_po, const int* crank, const T* x, const T* dp, double* duv,
