@@ -555,9 +555,11 @@ __device__ __forceinline__ bool dot_nonzero(F2 a) { return a.h != 0.f; }  // nor
 __device__ __forceinline__ bool dot_pos_finite(double a) { return a > 0.0 && isfinite(a); }
 __device__ __forceinline__ bool dot_pos_finite(F2 a) { return a.h > 0.f && f2_finite(a); }
 
-// Block-wide sums of K dots: a butterfly within each warp, then every thread adds
-// the 16 warp sums in one fixed tree, so every thread holds the same bits (for
-// FP32 problems, the normalised double-float).  One barrier: callers alternate
+// Block-wide sums of K dots: a butterfly within each warp, then in every warp
+// lanes l and l + 16 take warp sum l and a second butterfly over 16 lanes adds
+// them, so every thread holds the same bits (dot_add is commutative bit for bit;
+// for FP32 problems, the normalised double-float).  The tree is the pairwise
+// one (w_i + w_i+8, then + 4, + 2, + 1).  One barrier: callers alternate
 // between two `red` buffers (kSpcgRedStride doubles each).  Returns the OR of
 // `flag` over the block.
 template <int K, typename D>
@@ -577,14 +579,10 @@ __device__ __forceinline__ int block_allsum_dot(D (&v)[K], void* red_raw, int fl
   const int any = __syncthreads_or(flag);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    D w[NW];
+    D s = red[NW * k + (lane & (NW - 1))];
 #pragma unroll
-    for (int i = 0; i < NW; ++i) w[i] = red[NW * k + i];
-#pragma unroll
-    for (int h = NW / 2; h > 0; h >>= 1)
-#pragma unroll
-      for (int i = 0; i < h; ++i) w[i] = dot_add(w[i], w[i + h]);
-    v[k] = dot_norm(w[0]);
+    for (int m = NW / 2; m > 0; m >>= 1) s = dot_add(s, dot_shfl(s, m));
+    v[k] = dot_norm(s);
   }
   return any;
 }
