@@ -327,6 +327,8 @@ def main():
     ap.add_argument("--gp-only", action="store_true", help="only the global-positioning measurement")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenes.SPECS),
                     help="scene (default: the 1M-observation scene)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="working precision of the timed path (the configured workload is FP32)")
     ap.add_argument("--solver", default="auto", choices=["auto", "implicit", "explicit", "dense", "sparse"])
     ap.add_argument("--dense-kernels", action="store_true", help="time the tensor-core kernels only")
     args = ap.parse_args()
@@ -362,7 +364,8 @@ def main():
     N = scene.n_obs
     solver = {"auto": ba.BA_SOLVER_AUTO, "implicit": ba.BA_SOLVER_IMPLICIT, "explicit": ba.BA_SOLVER_EXPLICIT,
               "dense": ba.BA_SOLVER_DENSE, "sparse": ba.BA_SOLVER_SPARSE}[args.solver]
-    opts = ba.Options(precision=ba.BA_FP32, solver=solver)
+    fp64 = args.precision == "fp64"
+    opts = ba.Options(precision=ba.BA_FP64 if fp64 else ba.BA_FP32, solver=solver)
     prob = ba.Problem.from_scene(scene, opts, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
 
@@ -427,6 +430,7 @@ def main():
     n_fixed = 1
     Cf = int(solved[0]["n_cam_act"]) - n_fixed if solved else 0
     n = 9 * Cf
+    esz = 8 if fp64 else 4  # bytes per element of the working precision
     mean_it = statistics.mean(i["pcg_iters"] for i in solved) if solved else 0.0
     kern_ms = statistics.mean(i["ms"][4] for i in solved) if solved else None
     kind = prob.solver_kind
@@ -441,23 +445,23 @@ def main():
         # the stored blocks (2 per co-visible camera pair + the diagonal, 84 floats
         # each) read by every matvec, plus the set-up reads
         n_runs = int(np.count_nonzero(_covis_pairs(scene)))
-        per_launch = (2 * n_runs + Cf) * 336 * mean_it + 324 * Cf + 20 * n
+        per_launch = ((2 * n_runs + Cf) * 84 * esz * mean_it + 81 * esz * Cf + 5 * esz * n)
         kname = "k_spcg (block-sparse explicit Schur matrix, block-row matvec)"
-        unit_txt = "(2 co-visible pairs + Cf) x 336 B x iters + 324 Cf + 20 n bytes"
+        unit_txt = f"(2 co-visible pairs + Cf) x 84 x {esz} B x iters + 81 x {esz} Cf + 5 x {esz} n bytes"
     elif prob.explicit_solver and prob.explicit_layout["rows_in_smem"]:
         # the explicit-S PCG iteration's algorithmic bytes: its matvec reads all of
         # S^ (4 n^2) once per iteration; plus the set-up reads (preconditioner
         # blocks 324 Cf; b, D, 1/D and x 20 n).  The rows stay in shared memory after
         # the first read, so the DRAM traffic (ncu) is about one read of S^.
-        per_launch = 4 * n * n * mean_it + 324 * Cf + 20 * n
+        per_launch = esz * (n * n * mean_it + 81 * Cf + 5 * n)
         kname = "k_spcg (persistent block-Jacobi PCG on the explicit scaled Schur matrix, rows in shared memory)"
-        unit_txt = "4 n^2 x iters + 324 Cf + 20 n bytes, n = 9 Cf (S^ rows held in shared memory)"
+        unit_txt = f"{esz} (n^2 x iters + 81 Cf + 5 n) bytes, n = 9 Cf (S^ rows held in shared memory)"
     elif prob.explicit_solver:
         # rows of S^ streamed from device memory by every matvec: 4 n^2 per iteration
         # (S^ does not fit in L2 at these orders), plus the set-up reads
-        per_launch = 4 * n * n * mean_it + 324 * Cf + 20 * n
+        per_launch = esz * (n * n * mean_it + 81 * Cf + 5 * n)
         kname = "k_spcg (persistent block-Jacobi PCG on the explicit scaled Schur matrix, rows streamed)"
-        unit_txt = "4 n^2 x iters + 324 Cf + 20 n bytes, n = 9 Cf"
+        unit_txt = f"{esz} (n^2 x iters + 81 Cf + 5 n) bytes, n = 9 Cf"
     else:
         # per matvec, FP32 (W recomputed from a signed IRLS weight): the weight (4 B)
         # and the tile record (~13 B) per observation; point coordinates (16 B) and
@@ -600,10 +604,11 @@ def main():
         return 0
     line = {"metric": METRIC, "value": value, "unit": "LM iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
             "data": "synthetic",
-            "config": {"workload": _workload_name(scene) + ", FP32 with double-float cost, FP64-accurate PCG "
-                                                            "dots (double-float) and FP64 gain ratio",
+            "config": {"workload": _workload_name(scene) + (", FP64 throughout" if fp64 else
+                                                            ", FP32 with double-float cost, FP64-accurate PCG "
+                                                            "dots (double-float) and FP64 gain ratio"),
                        "n_cams": scene.spec.n_cams, "n_pts": P, "n_obs": N,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)"},
