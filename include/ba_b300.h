@@ -392,6 +392,17 @@ ba_status ba_selftest_layout(int64_t n_cams, const double* cams, int64_t n_pts, 
 /* Number of this library's kernels launched since creation (counts launches). */
 int64_t ba_kernel_launches(const ba_problem* pb);
 
+/* Index checks of the debug build.  A library compiled with -DBA_DEBUG_BOUNDS
+ * (libba_b300_debug.so) checks every index it loads from the observation layout
+ * or the co-visibility runs before the gather that uses it; a failed check
+ * records the kernel site and the index (the first failure per source file) and
+ * the access uses index 0 instead, so a corrupted layout cannot read or write
+ * out of bounds.  This call reports the first recorded failure: *site = -1 for a
+ * release build (no checks; no CUDA call is made), 0 when no check failed, else
+ * the site number (>= 1) with the failing index in *index; reset != 0 clears
+ * the records.  Synchronises with the device.  Returns BA_OK or BA_ERR_CUDA. */
+ba_status ba_debug_bounds(int reset, int64_t* site, int64_t* index);
+
 /* The reduced-camera-system solver the problem resolved to at creation:
  * BA_SOLVER_IMPLICIT, BA_SOLVER_EXPLICIT, BA_SOLVER_DENSE or BA_SOLVER_SPARSE
  * (0 for a NULL handle). */

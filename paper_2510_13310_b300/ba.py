@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libba_b300.so")
+# BA_DEBUG_BOUNDS=1 selects the build with the device index checks (ba_debug_bounds)
+LIB_PATH = os.path.join(_HERE, "libba_b300_debug.so" if os.environ.get("BA_DEBUG_BOUNDS") == "1"
+                        else "libba_b300.so")
 
 BA_OK, BA_ERR_INVALID_ARG, BA_ERR_CUDA, BA_ERR_OOM = 0, 1, 2, 3
 BA_ERR_NOT_CONVERGED, BA_ERR_NONFINITE, BA_ERR_STATE, BA_ERR_TIMEOUT = 4, 5, 6, 7
@@ -29,7 +31,7 @@ EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
            "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
            "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout", "ba_selftest_layout",
-           "ba_kernel_launches", "ba_solver_kind", "ba_explicit_layout", "ba_destroy", "ba_release_cache",
+           "ba_kernel_launches", "ba_debug_bounds", "ba_solver_kind", "ba_explicit_layout", "ba_destroy", "ba_release_cache",
            "ba_status_string", "ba_last_error",
            "ba_gp_default_options", "ba_gp_create", "ba_gp_lm_step", "ba_gp_solve", "ba_gp_get_params",
            "ba_gp_get_free", "ba_gp_solve_damped", "ba_gp_eval_cost", "ba_gp_kernel_launches",
@@ -98,6 +100,7 @@ def lib():
         L.ba_solve_damped.argtypes = [vp, ct.c_double, vp, vp, ct.POINTER(_IterInfo)]
         L.ba_eval_cost.argtypes = [vp, vp, vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         L.ba_backward.argtypes = [vp, vp, vp, vp, vp]
+        L.ba_debug_bounds.argtypes = [ct.c_int, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64)]
         L.ba_eval_cost_noalloc.argtypes = [ct.POINTER(_Options), vp, ct.c_int64, vp, ct.c_int64, vp,
                                            ct.c_int64, vp, vp, vp, vp, vp, vp]
         L.ba_kernel_launches.argtypes = [vp]
@@ -621,6 +624,14 @@ def bundle_adjust(cams0, pts0, obs_uv, depth, obs_cam, obs_pt, options: Options 
     if _BAFunction is None:
         _BAFunction = _make_ba_function()
     return _BAFunction.apply(cams0, pts0, obs_uv, depth, obs_cam, obs_pt, options or Options(), iters)
+
+
+def debug_bounds(reset=False):
+    """The first failed device index check of a BA_DEBUG_BOUNDS build as (site,
+    index); (0, 0) when none failed; (-1, 0) for the release library."""
+    site, index = ct.c_int64(), ct.c_int64()
+    _check(lib().ba_debug_bounds(1 if reset else 0, ct.byref(site), ct.byref(index)), "ba_debug_bounds")
+    return site.value, index.value
 
 
 def tc_gemm_nt(A, B, C=None, alpha=1.0, beta=0.0, stream=None):

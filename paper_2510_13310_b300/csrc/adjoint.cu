@@ -110,7 +110,7 @@ __global__ void k_adj_hmu_pts(Layout L, ModelParams mp, const double* __restrict
       u[0] = u[1] = u[2] = 0.0;
       continue;
     }
-    const int c = L.po_cam[k], cr = crank[c];
+    const int c = bidx(L.po_cam[k], L.C, 20), cr = crank[c];
     const double tau = L.po_tau64[k];
     const double sw = tau > 0.0 ? mp.sw_valid : mp.sw_invalid;
     ObsLin<double> ol;
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_hmu_cams(Layout L, ModelPar
   if (crank[c] >= 0) {
     for (int kc = L.chunk_obs[q] + threadIdx.x; kc < L.chunk_obs[q + 1]; kc += blockDim.x) {
       if (!act_co[kc]) continue;
-      const int k = L.co_po[kc], p = L.co_pt[kc];
+      const int k = bidx(L.co_po[kc], L.N, 21), p = bidx(L.co_pt[kc], L.P, 21);
       const double tau = L.po_tau64[k];
       const double sw = tau > 0.0 ? mp.sw_valid : mp.sw_invalid;
       ObsLin<double> ol;
@@ -225,14 +225,14 @@ __global__ void k_adjoint_obs64(Layout L, ModelParams mp, const double* __restri
                                 double* __restrict__ ddepth) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= L.N) return;
-  const int o = L.po_orig[k];
+  const int o = bidx(L.po_orig[k], L.N, 24);
   if (!act_po[k]) {
     duv[2 * (size_t)o] = 0.0;
     duv[2 * (size_t)o + 1] = 0.0;
     ddepth[o] = 0.0;
     return;
   }
-  const int c = L.po_cam[k], p = L.po_pt[k], cr = crank[c];
+  const int c = bidx(L.po_cam[k], L.C, 22), p = bidx(L.po_pt[k], L.P, 22), cr = crank[c];
   const double tau = L.po_tau64[k];
   const double sw = tau > 0.0 ? mp.sw_valid : mp.sw_invalid;
   ObsLin<double> ol;
@@ -300,7 +300,7 @@ __global__ void k_adjoint_obs(Layout L, ModelParams mp, const T* __restrict__ ca
                               double* __restrict__ ddepth) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= L.N) return;
-  const int o = L.po_orig[k];
+  const int o = bidx(L.po_orig[k], L.N, 24);
   if (!act_po[k]) {
     duv[2 * (size_t)o] = 0.0;
     duv[2 * (size_t)o + 1] = 0.0;
@@ -309,7 +309,7 @@ __global__ void k_adjoint_obs(Layout L, ModelParams mp, const T* __restrict__ ca
   }
   const T* po_uv = reinterpret_cast<const T*>(L.po_uvw);
   const T* po_tau = reinterpret_cast<const T*>(L.po_tauw);
-  const int c = L.po_cam[k], p = L.po_pt[k];
+  const int c = bidx(L.po_cam[k], L.C, 23), p = bidx(L.po_pt[k], L.P, 23);
   T cw[kCamStride];
 #pragma unroll
   for (int q = 0; q < kCamStride; ++q) cw[q] = camw[kCamStride * (size_t)c + q];
@@ -359,5 +359,7 @@ cudaError_t launch_adjoint_obs(const Layout& L, const ModelParams& mp, const T* 
                                              double*, cudaStream_t);
 BAB_INST_ADJ(float)
 BAB_INST_ADJ(double)
+
+BA_BOUNDS_QUERY(bounds_fault_adjoint)
 
 }  // namespace bab

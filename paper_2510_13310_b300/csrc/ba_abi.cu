@@ -1967,6 +1967,32 @@ ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_d
 
 int64_t ba_kernel_launches(const ba_problem* pb) { return pb ? pb->launches : 0; }
 
+ba_status ba_debug_bounds(int reset, int64_t* site, int64_t* index) {
+  if (site) *site = -1;
+  if (index) *index = 0;
+#ifdef BA_DEBUG_BOUNDS
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("ba_debug_bounds: %s", cudaGetErrorString(cudaGetLastError()));
+    return BA_ERR_CUDA;
+  }
+  unsigned long long first = 0;
+  for (unsigned long long v : {bounds_fault_kernels(reset != 0), bounds_fault_schur(reset != 0),
+                               bounds_fault_adjoint(reset != 0)}) {
+    if (v == ~0ull) {
+      set_error("ba_debug_bounds: reading the records failed");
+      cudaGetLastError();
+      return BA_ERR_CUDA;
+    }
+    if (!first) first = v;
+  }
+  if (site) *site = (int64_t)(first >> 32);
+  if (index) *index = (int64_t)(int32_t)(first & 0xffffffffull);
+#else
+  (void)reset;
+#endif
+  return BA_OK;
+}
+
 int ba_solver_kind(const ba_problem* pb) {
   if (!pb) return 0;
   return pb->dense ? BA_SOLVER_DENSE : pb->sparse ? BA_SOLVER_SPARSE : pb->explicit_S ? BA_SOLVER_EXPLICIT

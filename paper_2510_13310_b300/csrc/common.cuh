@@ -151,4 +151,36 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
+// Index checks of the BA_DEBUG_BOUNDS build, at the gathers that use an index
+// loaded from the observation layout or the co-visibility runs.  bidx(i, n, site)
+// returns i when 0 <= i < n; otherwise it records the first failure of this
+// translation unit as ((site + 1) << 32) | (uint32) i and returns 0, so the access
+// stays in bounds and the kernel's control flow (its barriers) is unchanged.
+// Release builds compile the checks away.  BA_BOUNDS_QUERY(fn) defines the host
+// function reading (and optionally clearing) this translation unit's record.
+#ifdef BA_DEBUG_BOUNDS
+static __device__ unsigned long long g_bounds_fault;
+__device__ __forceinline__ int bidx(long long i, long long n, int site) {
+  if (i < 0 || i >= n) {
+    atomicCAS(&g_bounds_fault, 0ull, ((unsigned long long)(site + 1) << 32) | (unsigned)(i & 0xffffffffLL));
+    return 0;
+  }
+  return (int)i;
+}
+#define BA_BOUNDS_QUERY(fn)                                                       \
+  unsigned long long fn(bool reset) {                                             \
+    unsigned long long v = 0;                                                     \
+    if (cudaMemcpyFromSymbol(&v, g_bounds_fault, sizeof v) != cudaSuccess) return ~0ull; \
+    if (reset) {                                                                  \
+      const unsigned long long z = 0;                                             \
+      if (cudaMemcpyToSymbol(g_bounds_fault, &z, sizeof z) != cudaSuccess) return ~0ull; \
+    }                                                                             \
+    return v;                                                                     \
+  }
+#else
+__device__ __forceinline__ int bidx(long long i, long long, int) { return (int)i; }
+#define BA_BOUNDS_QUERY(fn) \
+  unsigned long long fn(bool) { return 0; }
+#endif
+
 }  // namespace bab

@@ -323,4 +323,11 @@ template <typename T>
 cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, int src_stride,
                                 double* dst, int N, int width, cudaStream_t s);
 
+// first index-check failure of each translation unit in BA_DEBUG_BOUNDS builds
+// (((site + 1) << 32) | index, 0 if none; ~0 if it could not be read), cleared
+// when reset; 0 in release builds
+unsigned long long bounds_fault_kernels(bool reset);
+unsigned long long bounds_fault_schur(bool reset);
+unsigned long long bounds_fault_adjoint(bool reset);
+
 }  // namespace bab

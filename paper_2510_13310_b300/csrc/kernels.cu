@@ -152,7 +152,7 @@ __global__ void k_eval64(Layout L, ModelParams mp, const double* __restrict__ ca
   // thresholds of the validity predicate as integer keys (FP64 comparisons are FP64-pipe work)
   const long long kz = dkey(mp.min_depth), kw = dkey((double)mp.img_w), kh = dkey((double)mp.img_h);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += gridDim.x * blockDim.x) {
-    int c = L.po_cam[k], p = L.po_pt[k];
+    int c = bidx(L.po_cam[k], L.C, 0), p = bidx(L.po_pt[k], L.P, 1);
     const double* X = pts64 + 3 * (size_t)p;
     double tau = L.po_tau64[k];
     double sw = __double_as_longlong(tau) > 0 ? mp.sw_valid : mp.sw_invalid;  // tau > 0
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) k_eval_df(Layout L, ModelParams mp, Ev
   F2 acc_cost{0.f, 0.f}, acc_e2{0.f, 0.f};
   int acc_n = 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += gridDim.x * blockDim.x) {
-    const int c = L.po_cam[k], p = L.po_pt[k];
+    const int c = bidx(L.po_cam[k], L.C, 2), p = bidx(L.po_pt[k], L.P, 3);
     F2 cw[16];
     {
       const float4* cr = cam_in_smem ? cam_s + 9 * c : reinterpret_cast<const float4*>(camdf) + 8 * (size_t)c;
@@ -703,9 +703,9 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
       continue;
     }
     T cw[kCamStride];
-    load_cam(camw, L.po_cam[k], cw);
+    load_cam(camw, bidx(L.po_cam[k], L.C, 4), cw);
     T X0, X1, X2;
-    load_pt(ptsw, L.po_pt[k], X0, X1, X2);
+    load_pt(ptsw, bidx(L.po_pt[k], L.P, 5), X0, X1, X2);
     T tau = tauw[k];
     T sw = tau > T(0) ? (T)mp.sw_valid : (T)mp.sw_invalid;
     ObsLin<T> o;
@@ -814,7 +814,7 @@ __global__ void __launch_bounds__(kCamThreads) k_cam_accum(
   for (int j = 0; j < 54; ++j) acc[j] = T(0);
   for (int k = kb + threadIdx.x; k < ke; k += blockDim.x) {
     if (!act_co[k]) continue;
-    int p = L.co_pt[k];
+    int p = bidx(L.co_pt[k], L.P, 6);
     T X0, X1, X2;
     load_pt(ptsw, p, X0, X1, X2);
     T tau = tauw[k];
@@ -1362,5 +1362,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
 
 BAB_INST(float)
 BAB_INST(double)
+
+BA_BOUNDS_QUERY(bounds_fault_kernels)
 
 }  // namespace bab

@@ -52,7 +52,7 @@ __device__ __forceinline__ void obs_W(const T* cw, const T* X, T u, T v, T tau, 
 constexpr int kYRows = 128;
 
 template <typename T>
-__global__ void __launch_bounds__(kYRows) k_form_Y(int N, const int* __restrict__ po_cam,
+__global__ void __launch_bounds__(kYRows) k_form_Y(int N, int C, int P, const int* __restrict__ po_cam,
                                                   const int* __restrict__ po_pt, const T* __restrict__ W,
                                                   const T* __restrict__ Vinv, const int* __restrict__ crank,
                                                   const double* __restrict__ dscale, int Cf,
@@ -69,13 +69,13 @@ __global__ void __launch_bounds__(kYRows) k_form_Y(int N, const int* __restrict_
   if (t < rows) {
     const int k = k0 + t;
     T* y = buf + kWStride * t;
-    const int a = crank[po_cam[k]];
+    const int a = crank[bidx(po_cam[k], C, 10)];
     if (a < 0) {
 #pragma unroll
       for (int q = 0; q < 27; ++q) y[q] = T(0);
     } else {
       const T* dinv = reinterpret_cast<const T*>(dscale + 9 * Cf) + 9 * a;
-      const T* vi = Vinv + 6 * (size_t)po_pt[k];
+      const T* vi = Vinv + 6 * (size_t)bidx(po_pt[k], P, 11);
       const T v00 = vi[0], v01 = vi[1], v02 = vi[2], v11 = vi[3], v12 = vi[4], v22 = vi[5];
       T l00 = T(0), l10 = T(0), l20 = T(0), l11 = T(0), l21 = T(0), l22 = T(0);
       if (v00 > T(0)) {
@@ -160,13 +160,14 @@ __device__ __forceinline__ void rs_round(T (&v)[96], int lane, int r) {
 template <typename T, bool kSparse>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
     k_form_S_runs(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
-                  const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat) {
+                  const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat, int C,
+                  int N) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int ld = spcg_row_stride<T>(9 * Cf);
   for (int ri = gw; ri < n_runs; ri += nw) {
     const int4 rn = runs[ri];  // (camera i, camera j, first pair, pair count)
-    const int a = crank[rn.x], b = crank[rn.y];
+    const int a = crank[bidx(rn.x, C, 12)], b = crank[bidx(rn.y, C, 12)];
     if (a < 0 || b < 0) continue;
     T acc[81];
 #pragma unroll
@@ -178,8 +179,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
       const int2 pr = nxt;
       if (q + 32 < qe) nxt = pairs[q + 32];  // next pair's indices in flight during this one
       T y1[27], y2[27];
-      load_row27<T>(Y + kWStride * (size_t)pr.x, y1);
-      load_row27<T>(Y + kWStride * (size_t)pr.y, y2);
+      load_row27<T>(Y + kWStride * (size_t)bidx(pr.x, N, 13), y1);
+      load_row27<T>(Y + kWStride * (size_t)bidx(pr.y, N, 13), y2);
 #pragma unroll
       for (int r = 0; r < 9; ++r)
 #pragma unroll
@@ -220,11 +221,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
 template <typename T, bool kSparse>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
     k_form_S_lanes(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
-                   const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat) {
+                   const T* __restrict__ Y, const int* __restrict__ crank, int Cf, T* __restrict__ Shat, int C,
+                   int N) {
   const int ld = spcg_row_stride<T>(9 * Cf);
   for (int ri = blockIdx.x * blockDim.x + threadIdx.x; ri < n_runs; ri += gridDim.x * blockDim.x) {
     const int4 rn = runs[ri];
-    const int a = crank[rn.x], b = crank[rn.y];
+    const int a = crank[bidx(rn.x, C, 14)], b = crank[bidx(rn.y, C, 14)];
     if (a < 0 || b < 0) continue;
     T acc[81];
 #pragma unroll
@@ -235,8 +237,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
       const int2 pr = nxt;
       if (q + 1 < qe) nxt = pairs[q + 1];
       T y2[27];
-      load_row27<T>(Y + kWStride * (size_t)pr.y, y2);
-      const T* y1 = Y + kWStride * (size_t)pr.x;
+      load_row27<T>(Y + kWStride * (size_t)bidx(pr.y, N, 15), y2);
+      const T* y1 = Y + kWStride * (size_t)bidx(pr.x, N, 15);
 #pragma unroll
       for (int r = 0; r < 9; ++r) {
         const T a0 = y1[3 * r], a1 = y1[3 * r + 1], a2 = y1[3 * r + 2];
@@ -339,7 +341,7 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
   if (Cf <= 0) return cudaSuccess;
   const int n = 9 * Cf;
   // dscale (D and 1/D) was written by the Schur-diagonal kernel
-  if (L.N > 0) k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
+  if (L.N > 0) k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.C, L.P, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
   cudaError_t e = cudaSuccess;
   // the dense system is cleared (blocks of pairs that share no point stay zero);
   // the block-sparse one stores only written blocks (the matvec skips blocks
@@ -354,16 +356,16 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
       // many short runs: one lane per run
       int grid = (n_runs + 127) / 128;
       if (grid > 16 * num_sms) grid = 16 * num_sms;  // (a resident-only grid measured slower here)
-      if (sparse) k_form_S_lanes<T, true><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
-      else k_form_S_lanes<T, false><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
+      if (sparse) k_form_S_lanes<T, true><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat, L.C, L.N);
+      else k_form_S_lanes<T, false><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat, L.C, L.N);
     } else {
       // resident blocks only (three per SM in FP32), striding over the runs: no
       // partly filled last wave
       int grid = (n_runs + wpb - 1) / wpb;
       const int resident = (sizeof(T) == 4 ? 3 : 1) * num_sms;
       if (grid > resident) grid = resident;
-      if (sparse) k_form_S_runs<T, true><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
-      else k_form_S_runs<T, false><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat);
+      if (sparse) k_form_S_runs<T, true><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat, L.C, L.N);
+      else k_form_S_runs<T, false><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat, L.C, L.N);
     }
   }
   if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
@@ -1298,15 +1300,15 @@ __global__ void k_backsub_obs(Layout L, ModelParams mp, const T* __restrict__ ca
   const T* po_tau = reinterpret_cast<const T*>(L.po_tauw);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += gridDim.x * blockDim.x) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
-    const int cr = act_po[k] ? crank[L.po_cam[k]] : -1;
+    const int cr = act_po[k] ? crank[bidx(L.po_cam[k], L.C, 16)] : -1;
     if (cr >= 0) {
       T W[27];
       if (Wst) {
         load_row27<T>(Wst + kWStride * (size_t)k, W);
       } else {
         T cw[kCamStride];
-        load_cam_rec(camw, L.po_cam[k], cw);
-        obs_W(cw, ptsw + 4 * (size_t)L.po_pt[k], po_uv[2 * (size_t)k], po_uv[2 * (size_t)k + 1], po_tau[k], mp, W);
+        load_cam_rec(camw, bidx(L.po_cam[k], L.C, 16), cw);
+        obs_W(cw, ptsw + 4 * (size_t)bidx(L.po_pt[k], L.P, 17), po_uv[2 * (size_t)k], po_uv[2 * (size_t)k + 1], po_tau[k], mp, W);
       }
       const T* xv = x + 9 * (size_t)cr;
 #pragma unroll
@@ -1414,5 +1416,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
                                              cudaStream_t);
 BAB_SINST(float)
 BAB_SINST(double)
+
+BA_BOUNDS_QUERY(bounds_fault_schur)
 
 }  // namespace bab

@@ -27,6 +27,19 @@ def test_library_builds_and_exports_header_symbols():
     assert set(names) == set(ba.EXPORTS)
 
 
+def test_debug_bounds_library_builds_and_exports_header_symbols():
+    """The BA_DEBUG_BOUNDS variant exports the same symbols; the release library
+    reports that it carries no index checks (site -1) without touching a device."""
+    path = build.build(debug_bounds=True)
+    assert path.endswith("libba_b300_debug.so")
+    D = ct.CDLL(path)
+    for n in _declared():
+        assert hasattr(D, n), n
+    assert ba.LIB_PATH.endswith("libba_b300.so") or os.environ.get("BA_DEBUG_BOUNDS") == "1"
+    if not ba.LIB_PATH.endswith("_debug.so"):
+        assert ba.debug_bounds() == (-1, 0)
+
+
 def test_defaults_and_status_strings():
     L = ba.lib()
     o = ba._Options()
