@@ -138,7 +138,9 @@ struct ba_problem {
   void* Yhat = nullptr;         // [N + 1][kWStride] D^-1 W M per damping value (explicit system)
   void* bs_wx = nullptr;        // [N][3] W_k^T dc of the back-substitution (explicit system)
   int4* covis_runs = nullptr;   // (camera i, camera j, first pair, count), i < j
-  int2* covis_pairs = nullptr;  // point-order observations (k in i, k2 in j) of shared points
+  int2* covis_pairs = nullptr;  // point-order observations (k in i, k2 in j) of shared points; FP32
+                                // explicit systems: camera-order (owner's row, other's row), see CamForm
+  CamForm cform;                // FP32 explicit systems: the camera-owned formation (n_blocks > 0)
   int n_covis_runs = 0;
   bool form_lanes = false;      // one lane per co-visibility run (many short runs)
   double* dscale = nullptr;
@@ -493,7 +495,7 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
                                  (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
                                  Cf, (T*)pb->Yhat, pb->sparse ? (T*)pb->Bs : (T*)pb->Shat, pb->form_lanes,
                                  pb->num_sms, pb->evf[0], pb->evf[1], pb->join_pending ? pb->join : nullptr,
-                                 pb->stream, pb->cam_map, pb->sparse));
+                                 pb->stream, pb->cam_map, pb->sparse, pb->cform.n_blocks ? &pb->cform : nullptr));
       pb->evf_valid = true;
     }
     pb->join_pending = false;  // the main stream waits for the chain
@@ -1287,6 +1289,42 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     // one lane per run when there are enough runs for four blocks of 128 lanes
     // per SM and runs are short (a warp per run would idle in its reduction)
     pb->form_lanes = (long long)cv.n_runs >= 4LL * 128 * pb->num_sms && cv.npairs < 128 * (size_t)cv.n_runs;
+    // FP32 with very many short runs (the lane-per-run regime: ~1,000 runs per camera
+    // on the 2,000-camera dense workload): camera-owned formation.  With few runs
+    // per camera its blocks would hold few live lanes, each walking its run's pairs
+    // one dependent gather at a time; the warp-per-run kernel is faster there
+    // (0.23 against 0.50 ms on the 200-camera bench workload).
+    if (!pb->fp64 && pb->form_lanes) {
+      // runs grouped by owner camera, blocks of up to 128 runs
+      int* po_co = nullptr;
+      ST(dalloc(pb, &po_co, (size_t)N));
+      LAUNCH(2, launch_owner_pairs(N, dl.co_po, po_co, cv.n_runs, cv.runs, cv.pairs, pb->stream));
+      std::vector<int4> h_runs((size_t)cv.n_runs);
+      CU(cudaMemcpy(h_runs.data(), cv.runs, sizeof(int4) * (size_t)cv.n_runs, cudaMemcpyDeviceToHost));
+      std::vector<int> own_off((size_t)C + 1, 0), own((size_t)cv.n_runs);
+      auto owner = [](const int4& r) { return run_owner_first(r.x, r.y) ? r.x : r.y; };
+      for (const int4& r : h_runs) own_off[owner(r) + 1]++;
+      for (int c = 0; c < C; ++c) own_off[c + 1] += own_off[c];
+      {
+        std::vector<int> fill(own_off.begin(), own_off.end() - 1);
+        for (int r = 0; r < cv.n_runs; ++r) own[fill[owner(h_runs[r])]++] = r;
+      }
+      std::vector<int4> blocks;
+      for (int c = 0; c < C; ++c)
+        for (int g = own_off[c]; g < own_off[c + 1]; g += 128)
+          blocks.push_back(make_int4(c, g, std::min(128, own_off[c + 1] - g), 0));
+      int* d_own = nullptr;
+      int4* d_blocks = nullptr;
+      ST(dalloc(pb, &d_own, own.size()));
+      ST(dalloc(pb, &d_blocks, blocks.size()));
+      CU(cudaMemcpy(d_own, own.data(), sizeof(int) * own.size(), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(d_blocks, blocks.data(), sizeof(int4) * blocks.size(), cudaMemcpyHostToDevice));
+      pb->cform.blocks = d_blocks;
+      pb->cform.n_blocks = (int)blocks.size();
+      pb->cform.own_run = d_own;
+      pb->cform.cam_off = dl.cam_off;
+      pb->cform.po_co = po_co;
+    }
     if (auto_sparse_cand) {
       // AUTO, priced now that the co-visible camera pairs are known: the
       // block-sparse system forms the same blocks and streams its 2 n_runs + C

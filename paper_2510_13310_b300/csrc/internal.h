@@ -227,6 +227,22 @@ template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
                               T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, double* dscale, int* err,
                               cudaStream_t s);  // dscale (nullable): D and 1/D of the explicit system
+// Camera-owned formation of the explicit system (FP32): every co-visibility run
+// (i, j) is summed by its owner camera (run_owner_first), whose Y^ rows, stored in
+// camera order, are staged in shared memory chunk by chunk; pairs hold (owner's
+// camera-order row, other's camera-order row).  Block d covers blocks[d] =
+// (camera, first index into own_run, run count, 0).
+struct CamForm {
+  const int4* blocks = nullptr;
+  int n_blocks = 0;
+  const int* own_run = nullptr;  // runs grouped by owner camera
+  const int* cam_off = nullptr;  // [C + 1] camera-order offsets
+  const int* po_co = nullptr;    // [N] camera-order position of each point-order observation
+};
+__host__ __device__ constexpr bool run_owner_first(int i, int j) { return ((i + j) & 1) == 0; }
+cudaError_t launch_owner_pairs(int N, const int* co_po, int* po_co, int n_runs, const int4* runs, int2* pairs,
+                               cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
@@ -234,7 +250,8 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
                           cudaEvent_t join, cudaStream_t s,   // join (nullable): waited on before the
                                                               // diagonal blocks are written
                           const int* cam_map = nullptr,       // sparse: Shat is the block storage
-                          bool sparse = false);
+                          bool sparse = false,
+                          const CamForm* cf = nullptr);       // FP32: camera-owned formation
 template <typename T>
 cudaError_t launch_dscale(int Cf, const int* cam_map, const T* Ug, double lambda, double* dscale, cudaStream_t s);
 template <typename T>

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kYRows) k_form_Y(int N, int C, int P, const in
                                                   const int* __restrict__ po_pt, const T* __restrict__ W,
                                                   const T* __restrict__ Vinv, const int* __restrict__ crank,
                                                   const double* __restrict__ dscale, int Cf,
-                                                  T* __restrict__ Y) {
+                                                  T* __restrict__ Y, const int* __restrict__ dst_row) {
   __shared__ __align__(16) T buf[kYRows * kWStride];
   constexpr int kVec = (int)(kWStride * sizeof(T) / 16);  // 16-byte words per row
   const int k0 = blockIdx.x * kYRows;
@@ -101,8 +101,16 @@ __global__ void __launch_bounds__(kYRows) k_form_Y(int N, int C, int P, const in
     }
   }
   __syncthreads();
-  uint4* dst = reinterpret_cast<uint4*>(Y + kWStride * (size_t)k0);
-  for (int i = threadIdx.x; i < rows * kVec; i += kYRows) dst[i] = sb[i];
+  if (dst_row) {
+    // camera-order rows: consecutive lanes store consecutive 16-byte words of a row
+    for (int i = threadIdx.x; i < rows * kVec; i += kYRows) {
+      const int r = i / kVec;
+      reinterpret_cast<uint4*>(Y + kWStride * (size_t)dst_row[k0 + r])[i - r * kVec] = sb[i];
+    }
+  } else {
+    uint4* dst = reinterpret_cast<uint4*>(Y + kWStride * (size_t)k0);
+    for (int i = threadIdx.x; i < rows * kVec; i += kYRows) dst[i] = sb[i];
+  }
 }
 
 template <typename T>
@@ -261,6 +269,120 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Camera-owned formation (FP32).  The kernels above read both Y^ rows of every
+// pair from L2 or device memory.  Here run (i, j) is summed by one owner camera
+// (run_owner_first: i when i + j is even, else j; about half of each camera's
+// runs), and a block takes up to 128 runs of one owner, one lane per run: the
+// block stages the owner's Y^ rows (camera order, ascending in point) in shared
+// memory kCfRows at a time, and each lane adds, for its run's pairs within the
+// staged rows, the owner row from shared memory times the other camera's row
+// from device memory.  The owner's rows cross into the SM once per block
+// instead of once per pair.  Each lane sums its run in pair order (fixed), so
+// the result is deterministic.
+// ---------------------------------------------------------------------------
+constexpr int kCfThreads = 128;
+constexpr int kCfRows = 384;  // staged rows per chunk: 384 x 112 B = 42 KB
+
+__global__ void k_po_co(int N, const int* __restrict__ co_po, int* __restrict__ po_co) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < N) po_co[co_po[j]] = j;
+}
+
+// pairs of run r, in place: point-order (k in i, k2 in j) -> camera-order
+// (owner's row, other's row)
+__global__ void k_owner_pairs(int n_runs, const int4* __restrict__ runs, const int* __restrict__ po_co,
+                              int2* __restrict__ pairs) {
+  const int r = blockIdx.x;
+  if (r >= n_runs) return;
+  const int4 rn = runs[r];
+  const bool first = run_owner_first(rn.x, rn.y);
+  for (int q = rn.z + threadIdx.x; q < rn.z + rn.w; q += blockDim.x) {
+    const int2 pr = pairs[q];
+    const int a = po_co[pr.x], b = po_co[pr.y];
+    pairs[q] = first ? make_int2(a, b) : make_int2(b, a);
+  }
+}
+
+cudaError_t launch_owner_pairs(int N, const int* co_po, int* po_co, int n_runs, const int4* runs, int2* pairs,
+                               cudaStream_t s) {
+  if (N > 0) k_po_co<<<(N + 255) / 256, 256, 0, s>>>(N, co_po, po_co);
+  if (n_runs > 0) k_owner_pairs<<<n_runs, 128, 0, s>>>(n_runs, runs, po_co, pairs);
+  return cudaGetLastError();
+}
+
+// the run's block S_ij (i < j) from acc = sum Y_owner Y_other^T (S_ij itself when
+// the owner is i, its transpose when the owner is j), negated, into the dense
+// system or the block storage
+template <bool kSparse>
+__device__ __forceinline__ void store_run_block(const float (&acc)[81], bool owner_first, int ri, int a, int b,
+                                                int ld, float* __restrict__ Shat) {
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const float v = -(owner_first ? acc[9 * r + c] : acc[9 * c + r]);  // S_ij[r][c]
+      if constexpr (kSparse) {
+        Shat[(size_t)kBlkStride * (2 * (size_t)ri) + 9 * r + c] = v;
+        Shat[(size_t)kBlkStride * (2 * (size_t)ri + 1) + 9 * c + r] = v;
+      } else {
+        Shat[(size_t)(9 * a + r) * ld + 9 * b + c] = v;
+      }
+    }
+}
+
+template <bool kSparse>
+__global__ void __launch_bounds__(kCfThreads, 4)
+    k_form_S_cam(const int4* __restrict__ blocks, const int* __restrict__ own_run, const int4* __restrict__ runs,
+                 const int2* __restrict__ pairs, const int* __restrict__ cam_off, const float* __restrict__ Y,
+                 const int* __restrict__ crank, int Cf, float* __restrict__ Shat, int n_runs, int C, int N) {
+  __shared__ __align__(16) uint4 stage[kCfRows * 7];
+  const int4 bd = blocks[blockIdx.x];  // (owner camera, first own_run index, runs, unused)
+  const int cam = bidx(bd.x, C, 30);
+  const int t = threadIdx.x;
+  const int lo = cam_off[cam], hi = cam_off[cam + 1];  // the owner camera's rows
+  int ri = -1, a = -1, b = -1, cur = 0, end = 0;
+  bool first = true;
+  if (t < bd.z) {
+    ri = bidx(own_run[bd.y + t], n_runs, 31);
+    const int4 rn = runs[ri];
+    a = crank[bidx(rn.x, C, 32)];
+    b = crank[bidx(rn.y, C, 32)];
+    first = run_owner_first(rn.x, rn.y);
+    cur = rn.z;
+    end = rn.z + rn.w;
+  }
+  const bool live = t < bd.z && a >= 0 && b >= 0;
+  int2 pr = live && cur < end ? pairs[cur] : make_int2(0x7fffffff, 0);  // the lane's next pair
+  float acc[81];
+#pragma unroll
+  for (int q = 0; q < 81; ++q) acc[q] = 0.f;
+  const uint4* Y4 = reinterpret_cast<const uint4*>(Y);
+  for (int s0 = lo; s0 < hi; s0 += kCfRows) {
+    const int n = min(kCfRows, hi - s0);
+    __syncthreads();  // the previous chunk's rows are no longer read
+    for (int i = t; i < n * 7; i += kCfThreads) stage[i] = Y4[(size_t)7 * s0 + i];
+    __syncthreads();
+    if (!live) continue;
+    const int s1 = s0 + n;
+    while (cur < end && pr.x < s1) {
+      const int2 nx = cur + 1 < end ? pairs[cur + 1] : make_int2(0x7fffffff, 0);  // in flight meanwhile
+      float y2[27];
+      load_row27<float>(Y + kWStride * (size_t)bidx(pr.y, N, 33), y2);
+      const float* y1 = reinterpret_cast<const float*>(stage + 7 * bidx(pr.x - s0, n, 34));
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        const float a0 = y1[3 * r], a1 = y1[3 * r + 1], a2 = y1[3 * r + 2];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[9 * r + c] += a0 * y2[3 * c] + a1 * y2[3 * c + 1] + a2 * y2[3 * c + 2];
+      }
+      pr = nx;
+      ++cur;
+    }
+  }
+  if (live) store_run_block<kSparse>(acc, first, ri, a, b, spcg_row_stride<float>(9 * Cf), Shat);
+}
+
 // Diagonal blocks of the block-sparse system, scaled: slot 2 n_runs + c for the
 // camera c of rank f, from the packed block-Jacobi block D_f.
 template <typename T>
@@ -337,11 +459,14 @@ template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
                           int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaEvent_t ev0, cudaEvent_t ev1,
-                          cudaEvent_t join, cudaStream_t s, const int* cam_map, bool sparse) {
+                          cudaEvent_t join, cudaStream_t s, const int* cam_map, bool sparse, const CamForm* cf) {
+  if (sizeof(T) != 4) cf = nullptr;  // FP64 keeps point-order rows and the pair kernels
   if (Cf <= 0) return cudaSuccess;
   const int n = 9 * Cf;
   // dscale (D and 1/D) was written by the Schur-diagonal kernel
-  if (L.N > 0) k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.C, L.P, L.po_cam, L.po_pt, W, Vinv, crank, dscale, Cf, Y);
+  if (L.N > 0)
+    k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.C, L.P, L.po_cam, L.po_pt, W, Vinv, crank,
+                                                               dscale, Cf, Y, cf ? cf->po_co : nullptr);
   cudaError_t e = cudaSuccess;
   // the dense system is cleared (blocks of pairs that share no point stay zero);
   // the block-sparse one stores only written blocks (the matvec skips blocks
@@ -350,7 +475,16 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
     return e;
   // events (nullable) around the co-visibility product kernel
   if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
-  if (n_runs > 0) {
+  if (n_runs > 0 && cf) {
+    if constexpr (sizeof(T) == 4) {
+      if (sparse)
+        k_form_S_cam<true><<<cf->n_blocks, kCfThreads, 0, s>>>(cf->blocks, cf->own_run, runs, pairs, cf->cam_off, Y,
+                                                               crank, Cf, Shat, n_runs, L.C, L.N);
+      else
+        k_form_S_cam<false><<<cf->n_blocks, kCfThreads, 0, s>>>(cf->blocks, cf->own_run, runs, pairs, cf->cam_off, Y,
+                                                                crank, Cf, Shat, n_runs, L.C, L.N);
+    }
+  } else if (n_runs > 0) {
     const int wpb = 4;  // warps per 128-thread block
     if (lanes) {
       // many short runs: one lane per run
@@ -1399,7 +1533,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
   template cudaError_t launch_form_S<T>(const Layout&, int, const int4*, const int2*, const T*,        \
                                         const T*, const int*, const T*, const T*, double*, int, T*, T*, \
                                         bool, int, cudaEvent_t, cudaEvent_t, cudaEvent_t, cudaStream_t, \
-                                        const int*, bool);                                              \
+                                        const int*, bool, const CamForm*);                              \
   template cudaError_t launch_dscale<T>(int, const int*, const T*, double, double*, cudaStream_t);       \
   template size_t spcg_smem_bytes<T>(int, int, int, int, int);                                         \
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \

@@ -189,19 +189,21 @@ def test_damped_step_matches_oracle(precision, solver):
     assert not g["dc"][sc.fixed_cams].any()
 
 
-@pytest.mark.parametrize("precision", [ba.BA_FP64, ba.BA_FP32])
-def test_explicit_step_with_many_short_runs_matches_oracle(precision):
-    """About 99k co-visible camera pairs of a few shared points each: the explicit
-    system is formed by the kernel for many short co-visibility runs (chosen at
-    4 x 128 runs per SM and more) rather than the warp-per-run kernel."""
+@pytest.mark.parametrize("precision,solver", [(ba.BA_FP64, ba.BA_SOLVER_EXPLICIT),
+                                              (ba.BA_FP32, ba.BA_SOLVER_EXPLICIT),
+                                              (ba.BA_FP32, ba.BA_SOLVER_SPARSE)])
+def test_explicit_step_with_many_short_runs_matches_oracle(precision, solver):
+    """About 99k co-visible camera pairs of a few shared points each (4 x 128 runs
+    per SM and more): FP64 forms the explicit system with one lane per run, FP32
+    with the camera-owned formation (owner rows staged in shared memory), into the
+    dense and the block-sparse storage."""
     sc = geometric(450, 6000, 12, 12, 12.0, seed=57)
     tracks = np.sort(sc.obs_cam.reshape(-1, 12), axis=1).astype(np.int64)
     iu, ju = np.triu_indices(12, 1)
     n_runs = np.unique(tracks[:, iu] * sc.spec.n_cams + tracks[:, ju]).size
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert n_runs >= 4 * 128 * sms
-    gpu, orc = pair(sc, precision, pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6,
-                    solver=ba.BA_SOLVER_EXPLICIT)
+    gpu, orc = pair(sc, precision, pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6, solver=solver)
     lam = 1e-3
     g = gpu.solve_damped(lam)
     geom, _ = orc.predicate(sc.cams0, sc.pts0)
