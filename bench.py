@@ -434,6 +434,7 @@ def main():
     mean_it = statistics.mean(i["pcg_iters"] for i in solved) if solved else 0.0
     kern_ms = statistics.mean(i["ms"][4] for i in solved) if solved else None
     kind = prob.solver_kind
+    form_kernel = prob.formation_kernel
     solver_name = {ba.BA_SOLVER_DENSE: "dense", ba.BA_SOLVER_EXPLICIT: "explicit",
                    ba.BA_SOLVER_SPARSE: "sparse"}.get(kind, "implicit")
     if kind == ba.BA_SOLVER_DENSE:
@@ -498,15 +499,14 @@ def main():
         flops = 486.0 * npairs
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         fp32_peak = sms * 128 * 2 * 2032e6 / 1e12
-        # the kernel the library picks (one lane per run for very many short runs)
-        n_runs_est = int(((np.bincount(scene.obs_cam, minlength=scene.spec.n_cams) > 0).sum()) ** 2 // 2)
-        lanes = npairs < 128 * max(n_runs_est, 1) and n_runs_est >= 4 * 128 * torch.cuda.get_device_properties(dev).multi_processor_count
-        roof_form = {"kernel": ("k_form_S_lanes" if lanes else "k_form_S_runs")
+        # the kernel the library picked at creation
+        fname = form_kernel or "k_form_S_runs"
+        roof_form = {"kernel": fname
                      + " (co-visibility block products forming the explicit system)",
                      "bound": "alu", "achieved": flops / (form_ms * 1e-3) / 1e12, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": flops / (form_ms * 1e-3) / 1e12 / fp32_peak,
                      "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x 2032 MHz",
-                     "traffic": NCU_TRAFFIC.get("k_form_S_runs") if args.workload == WORKLOAD and not lanes else None,
+                     "traffic": NCU_TRAFFIC.get(fname) if args.workload == WORKLOAD else None,
                      "algorithmic_per_launch": flops,
                      "formula": "486 flops x co-visible pairs of free cameras", "pairs": npairs,
                      "hbm_bytes_algorithmic": 8 * npairs + 108 * N + 4 * n * n,

@@ -417,6 +417,14 @@ int ba_solver_kind(const ba_problem* pb);
  * of the persistent PCG launch. */
 void ba_explicit_layout(const ba_problem* pb, int* rows_in_smem, int* vecs_in_smem, int* grid);
 
+/* The kernel that forms the off-diagonal blocks of an explicit reduced camera
+ * system (Eq. LM, Schur form), chosen at creation from the co-visibility runs:
+ * 1 one warp per camera pair (k_form_S_runs), 2 one lane per camera pair
+ * (k_form_S_lanes: FP64 with very many short runs), 3 camera-owned formation
+ * (k_form_S_cam: FP32 with very many short runs); 0 for the implicit solver or a
+ * NULL handle. */
+int ba_formation_kernel(const ba_problem* pb);
+
 /* Free a problem (the paper has no counterpart: resource management of this
  * interface).  Its device buffers go to a process-wide cache that later
  * ba_create calls draw from (no new device mappings when problems of similar

@@ -31,7 +31,7 @@ EXPORTS = ("ba_default_options", "ba_create", "ba_lm_step", "ba_solve", "ba_get_
            "ba_set_params", "ba_get_active", "ba_extract", "ba_linearize", "ba_solve_damped",
            "ba_eval_cost", "ba_backward", "ba_eval_cost_noalloc", "ba_tc_gemm_nt", "ba_dense_cholesky",
            "ba_get_state", "ba_set_state", "ba_selftest_wait_timeout", "ba_selftest_layout",
-           "ba_kernel_launches", "ba_debug_bounds", "ba_solver_kind", "ba_explicit_layout", "ba_destroy", "ba_release_cache",
+           "ba_kernel_launches", "ba_debug_bounds", "ba_solver_kind", "ba_explicit_layout", "ba_formation_kernel", "ba_destroy", "ba_release_cache",
            "ba_status_string", "ba_last_error",
            "ba_gp_default_options", "ba_gp_create", "ba_gp_lm_step", "ba_gp_solve", "ba_gp_get_params",
            "ba_gp_get_free", "ba_gp_solve_damped", "ba_gp_eval_cost", "ba_gp_kernel_launches",
@@ -109,6 +109,8 @@ def lib():
         L.ba_solver_kind.restype = ct.c_int
         L.ba_explicit_layout.argtypes = [vp, vp, vp, vp]
         L.ba_explicit_layout.restype = None
+        L.ba_formation_kernel.argtypes = [vp]
+        L.ba_formation_kernel.restype = ct.c_int
         L.ba_get_state.argtypes = [vp, vp, ct.POINTER(ct.c_size_t)]
         L.ba_set_state.argtypes = [vp, vp, ct.c_size_t]
         L.ba_selftest_wait_timeout.argtypes = [vp, ct.c_double]
@@ -380,6 +382,11 @@ class Problem:
         return int(self.L.ba_solver_kind(self.h))
 
     @property
+    @property
+    def formation_kernel(self) -> str | None:
+        """ba_formation_kernel: the kernel forming the explicit system's blocks."""
+        return {1: "k_form_S_runs", 2: "k_form_S_lanes", 3: "k_form_S_cam"}.get(self.L.ba_formation_kernel(self.h))
+
     def explicit_layout(self) -> dict:
         """ba_explicit_layout: where the explicit solver keeps S^ rows and PCG vectors."""
         r, v, g = ct.c_int(0), ct.c_int(0), ct.c_int(0)

@@ -2005,6 +2005,11 @@ ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_d
 
 int64_t ba_kernel_launches(const ba_problem* pb) { return pb ? pb->launches : 0; }
 
+int ba_formation_kernel(const ba_problem* pb) {
+  if (!pb || !pb->explicit_S || pb->n_covis_runs == 0) return 0;
+  return pb->cform.n_blocks ? 3 : pb->form_lanes ? 2 : 1;
+}
+
 ba_status ba_debug_bounds(int reset, int64_t* site, int64_t* index) {
   if (site) *site = -1;
   if (index) *index = 0;

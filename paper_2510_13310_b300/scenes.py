@@ -62,6 +62,9 @@ SPECS = {
     "diff": SceneSpec("diff", 100, 20_000, 10, 10, 10.0, seed=1003),
     "dense": SceneSpec("dense", 2_000, 400_000, 30, 30, 30.0, seed=1004),
     "window": SceneSpec("window", 1_500, 300_000, 3, 12, 6.0, seed=1005),
+    # a mid-size scene in the many-runs regime (nearly every camera pair shares a few
+    # points): the camera-owned formation with its Y^ rows (134 MB) past L2
+    "dense_mid": SceneSpec("dense_mid", 500, 100_000, 12, 12, 12.0, seed=1006),
 }
 # scenes whose tracks are windows of neighbouring cameras
 WINDOWED = {"window"}
