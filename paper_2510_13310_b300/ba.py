@@ -382,11 +382,11 @@ class Problem:
         return int(self.L.ba_solver_kind(self.h))
 
     @property
-    @property
     def formation_kernel(self) -> str | None:
         """ba_formation_kernel: the kernel forming the explicit system's blocks."""
         return {1: "k_form_S_runs", 2: "k_form_S_lanes", 3: "k_form_S_cam"}.get(self.L.ba_formation_kernel(self.h))
 
+    @property
     def explicit_layout(self) -> dict:
         """ba_explicit_layout: where the explicit solver keeps S^ rows and PCG vectors."""
         r, v, g = ct.c_int(0), ct.c_int(0), ct.c_int(0)
