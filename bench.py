@@ -37,10 +37,13 @@ from paper_2510_13310_b300 import scenes  # noqa: E402
 
 METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 GPU"
 
-# DRAM bytes (read + write) of one launch of each roofline kernel, from ncu
-# captures of this workload (profiles/top_kernels_traffic_medium_1M_obs.md); None
-# once the kernel has changed since the counters were taken.
-NCU_TRAFFIC = {"k_spcg": None, "k_pcg": None, "k_form_S_runs": 303936768 + 7791360}
+# DRAM bytes (read + write) of one launch of a roofline kernel on a workload, from
+# ncu captures (profiles/k_spcg_medium_1M_obs.md,
+# profiles/top_kernels_traffic_medium_1M_obs.md,
+# profiles/k_form_S_cam_dense_mid_1M_obs.md); absent once the kernel has changed
+# since the counters were taken, or for workloads not captured.
+NCU_TRAFFIC = {("medium", "k_spcg"): 13154816 + 26368, ("medium", "k_form_S_runs"): 303936768 + 7791360,
+               ("dense_mid", "k_form_S_cam"): 367535616 + 51516160}
 WORKLOAD = "medium"
 LM_ITERS = 30
 E2E_RUNS = 3
@@ -479,9 +482,8 @@ def main():
         bound, peak, unit, psrc = "hbm", hbm, "GB/s", peak_kind + " (burst copy)"
     roof_pcg = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "peak_source": psrc,
-                # the ncu counters were taken on the default workload only
-                "traffic": NCU_TRAFFIC.get("k_spcg" if prob.explicit_solver else "k_pcg")
-                if kind != ba.BA_SOLVER_DENSE and args.workload == WORKLOAD else None,
+                "traffic": NCU_TRAFFIC.get((args.workload, "k_spcg" if prob.explicit_solver else "k_pcg"))
+                if kind != ba.BA_SOLVER_DENSE and args.precision == "fp32" else None,
                 "algorithmic_per_launch": per_launch,
                 "formula": unit_txt, "launch_ms_mean": kern_ms,
                 "mean_pcg_iters": mean_it, "us_per_pcg_iter": (kern_ms * 1e3 / mean_it) if mean_it else None,
@@ -506,7 +508,7 @@ def main():
                      "bound": "alu", "achieved": flops / (form_ms * 1e-3) / 1e12, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": flops / (form_ms * 1e-3) / 1e12 / fp32_peak,
                      "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x 2032 MHz",
-                     "traffic": NCU_TRAFFIC.get(fname) if args.workload == WORKLOAD else None,
+                     "traffic": NCU_TRAFFIC.get((args.workload, fname)) if args.precision == "fp32" else None,
                      "algorithmic_per_launch": flops,
                      "formula": "486 flops x co-visible pairs of free cameras", "pairs": npairs,
                      "hbm_bytes_algorithmic": 8 * npairs + 108 * N + 4 * n * n,
