@@ -264,7 +264,7 @@ __host__ __device__ inline int spcg_row_stride(int n) {
 template <typename T>
 __host__ __device__ size_t spcg_vec_elems(int n, int Cf);
 template <typename T>
-const void* spcg_kernel_ptr(bool rows_in_smem, bool sparse = false);
+const void* spcg_kernel_ptr(bool rows_in_smem);
 template <typename T>
 cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
 // partitioned PCG on the block-sparse system (each block owns a slice of cameras)

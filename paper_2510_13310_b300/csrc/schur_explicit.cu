@@ -772,17 +772,14 @@ cudaError_t launch_spcg_precond(int Cf, const T* Dinv, const double* dscale, T* 
 // t handles the vector entries of cameras t, t + 512, ...
 // kRows: the block's rows of S^ sit in shared memory (else streamed from device
 // memory by every matvec); one instance per placement keeps registers in check
-// kSparse: the block-sparse system; block b owns whole cameras (ranks
-// [Cf b / G, Cf (b+1) / G)) and forms their rows of q from the stored blocks.
-template <typename T, bool kRows, bool kSparse>
+template <typename T, bool kRows>
 __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int W = spcg_words<T>();
   const int G = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int n = a.n, ns = spcg_row_stride<T>(n), Cf = a.Cf;
-  const int r0 = kSparse ? 9 * (int)(((long long)Cf * bid) / G) : (int)(((long long)n * bid) / G);
-  const int r1 = kSparse ? 9 * (int)(((long long)Cf * (bid + 1)) / G) : (int)(((long long)n * (bid + 1)) / G);
+  const int r0 = (int)(((long long)n * bid) / G), r1 = (int)(((long long)n * (bid + 1)) / G);
   const int nr = r1 - r0;
   unsigned char* sp = smem_raw;
   T* red = reinterpret_cast<T*>(sp);
@@ -863,36 +860,6 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
     const size_t set_words = (size_t)n * W;
     unsigned long long* set = words + (size_t)(it & 1) * kSpcgReplicas * set_words;
     // q = S^_rows p for the owned rows, published as tagged words
-    if constexpr (kSparse) {
-      // one warp per owned camera; three groups of nine lanes take every third
-      // block of the row, lane a of a group row a of the block; the groups' sums
-      // are added in a fixed order and lanes 0-8 publish the camera's 9 entries
-      const int grp = lane / 9, ra = lane - 9 * grp;
-      for (int f = r0 / 9 + warp; f < r1 / 9; f += nwarps) {
-        const int c = a.cam_map[f];
-        const int e0 = a.brp[c], e1 = a.brp[c + 1];
-        T acc = T(0);
-        if (lane < 27) {
-          for (int e = e0 + grp; e < e1; e += 3) {
-            const int2 ent = a.bent[e];  // (column camera, block slot)
-            const int cf = a.crank[ent.x];
-            if (cf < 0) continue;
-            const T* row = a.Bs + (size_t)kBlkStride * ent.y + 9 * ra;
-            const T* pj = pv + 9 * cf;
-#pragma unroll
-            for (int t = 0; t < 9; ++t) acc = fma(__ldg(row + t), pj[t], acc);
-          }
-        }
-        const T v1 = __shfl_down_sync(0xffffffffu, acc, 9);
-        const T v2 = __shfl_down_sync(0xffffffffu, acc, 18);
-        if (lane < 9) {
-          const T q = (acc + v1) + v2;
-#pragma unroll
-          for (int rep = 0; rep < kSpcgReplicas; ++rep)
-            spcg_publish<T>(set + rep * set_words + (size_t)(9 * f + lane) * W, q, tag);
-        }
-      }
-    } else {
     if constexpr (sizeof(T) == 4) {
       if constexpr (kRows) {
         // column split: warp w takes a slice of the float4 columns of every owned
@@ -987,7 +954,6 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
         if (lane < kSpcgReplicas) spcg_publish<T>(set + lane * set_words + (size_t)(r0 + r) * W, acc, tag);
       }
     }
-    }  // dense
     if constexpr (kFused) x_pending = false;  // the matvec pass applied a_prev p
     // gather q from this block's copy, coalesced (thread t: entries t, t + 512, ...,
     // up to four in flight), and (p, q)
@@ -1128,16 +1094,15 @@ __global__ void __launch_bounds__(kSpcgThreads, 1) k_spcg(SpcgArgs<T> a) {
 }
 
 template <typename T>
-const void* spcg_kernel_ptr(bool rows_in_smem, bool sparse) {
-  if (sparse) return reinterpret_cast<const void*>(&k_spcg<T, false, true>);
-  return rows_in_smem ? reinterpret_cast<const void*>(&k_spcg<T, true, false>)
-                      : reinterpret_cast<const void*>(&k_spcg<T, false, false>);
+const void* spcg_kernel_ptr(bool rows_in_smem) {
+  return rows_in_smem ? reinterpret_cast<const void*>(&k_spcg<T, true>)
+                      : reinterpret_cast<const void*>(&k_spcg<T, false>);
 }
 
 template <typename T>
 cudaError_t launch_spcg(const SpcgArgs<T>& a, int grid, size_t smem, cudaStream_t s) {
   void* args[] = {const_cast<SpcgArgs<T>*>(&a)};
-  return cudaLaunchCooperativeKernel(spcg_kernel_ptr<T>(a.rows_in_smem != 0, a.Bs != nullptr), dim3(grid),
+  return cudaLaunchCooperativeKernel(spcg_kernel_ptr<T>(a.rows_in_smem != 0), dim3(grid),
                                      dim3(kSpcgThreads), args, smem, s);
 }
 
@@ -1537,7 +1502,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
   template cudaError_t launch_dscale<T>(int, const int*, const T*, double, double*, cudaStream_t);       \
   template size_t spcg_smem_bytes<T>(int, int, int, int, int);                                         \
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \
-  template const void* spcg_kernel_ptr<T>(bool, bool);                                                   \
+  template const void* spcg_kernel_ptr<T>(bool);                                                         \
   template cudaError_t launch_spcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                  \
   template cudaError_t launch_bspcg<T>(const SpcgArgs<T>&, int, size_t, cudaStream_t);                 \
   template size_t bspcg_smem_bytes<T>(int, int);                                                       \
