@@ -389,7 +389,7 @@ ba_status run_extraction(ba_problem* pb, bool drop, int* rounds_out) {
   ST(finalize());
   if (p->h_sc->changed) {
     // the speculative pass already compared against the previous masks: keep
-    // its verdict (a spurious "changed" only costs a recomputation)
+    // its outcome (a spurious "changed" only costs a recomputation)
     const int spec_mask_changed = p->h_sc->mask_changed;
     for (;;) {
       ST(peel_round());
