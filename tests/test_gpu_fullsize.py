@@ -145,3 +145,36 @@ def test_large_workload_configured_schedule():
     print(f"after 11 iterations: kept outliers {om[sc.is_outlier].mean():.4f}, "
           f"inliers {om[~sc.is_outlier].mean():.4f}")
     gpu.close()
+
+
+def test_extraction_ablation_on_injected_frustum_exits():
+    """The ablation idea of Sec. 4.2 (per-iteration extraction against one-shot
+    pruning) re-run on the 1M-observation geometry with injected frustum exits
+    (30% of the wide points start above the image of their nearer cameras):
+    30 FP32 LM iterations in each mode from the same start.  One-shot keeps the
+    first active set; dynamic extraction re-admits the observations as the points
+    come back into view and ends with more active observations (996,846 against
+    908,556) and a slightly smaller error on the lifted points (1.56e-2 against
+    1.58e-2, measured; the runs are deterministic).  The table is printed."""
+    sc = scenes.make_scene("medium", frustum_exit_frac=0.3)
+    lifted = np.flatnonzero(np.abs(sc.pts0[:, 2] - sc.pts_gt[:, 2]) > 0.5)
+    res = {}
+    for name, mode in (("one-shot", ba.BA_EXTRACT_ONCE), ("dynamic", ba.BA_EXTRACT_DYNAMIC)):
+        gpu = ba.Problem.from_scene(sc, ba.Options(precision=ba.BA_FP32, extract_mode=mode))
+        log = gpu.solve(30)
+        c, p = gpu.get_params()
+        gpu.close()
+        err = np.linalg.norm(p - sc.pts_gt, axis=1)
+        res[name] = dict(act0=log[0]["n_obs_act"], act=log[-1]["n_obs_act"], rmse=log[-1]["rmse_px"],
+                         rot=pose_diff(c, sc.cams_gt)["rot_deg"], lifted=np.median(err[lifted]),
+                         allp=np.median(err))
+    print(f"{len(lifted)} lifted points of {sc.spec.n_pts}")
+    print("mode | active obs (first, last) | final RMSE px | max rotation error deg | "
+          "median point error: lifted, all")
+    for k, r in res.items():
+        print(f"{k} | {r['act0']}, {r['act']} | {r['rmse']:.3f} | {r['rot']:.4f} | {r['lifted']:.3e}, "
+              f"{r['allp']:.3e}")
+    once, dyn = res["one-shot"], res["dynamic"]
+    assert once["act"] == once["act0"] == dyn["act0"]
+    assert dyn["act"] > once["act"]
+    assert dyn["lifted"] < once["lifted"]
