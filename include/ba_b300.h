@@ -102,8 +102,8 @@ typedef struct {
                                   P = Exp(w) (X - c); k1, k2 are ignored and left unchanged (the
                                   paper stores the rotation as a quaternion; the axis-angle slots
                                   hold the same rotation, and the update is the same left
-                                  increment).  With BA_FP32 the centre model needs an explicit
-                                  solver; ba_backward needs BA_CAMERA_RADIAL. */
+                                  increment).  Every solver supports both models;
+                                  ba_backward needs BA_CAMERA_RADIAL. */
 } ba_options;
 
 enum { BA_SOLVER_AUTO = 0, BA_SOLVER_IMPLICIT = 1, BA_SOLVER_EXPLICIT = 2, BA_SOLVER_DENSE = 3,

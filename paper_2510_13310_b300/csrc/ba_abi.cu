@@ -1144,13 +1144,6 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       set_error("BA_SOLVER_DENSE needs BA_FP32 (the factorisation runs on TF32 tensor cores)");
       return BA_ERR_INVALID_ARG;
     }
-    // the FP32 implicit PCG recomputes the radial model's Jacobian blocks itself;
-    // the centre model runs on the stored blocks of the other solvers
-    const bool no_implicit = !pb->fp64 && opts->camera_model == BA_CAMERA_CENTRE;
-    if (so == BA_SOLVER_IMPLICIT && no_implicit) {
-      set_error("BA_CAMERA_CENTRE with BA_FP32 needs an explicit solver (EXPLICIT, SPARSE or DENSE)");
-      return BA_ERR_INVALID_ARG;
-    }
     // The dense tensor-core solve is opt-in: on the 12M-observation dense
     // workload (2,000 cameras) forming S from 174M co-visible pairs alone costs
     // about as much as the whole implicit block-Jacobi PCG, which converges in
@@ -1177,7 +1170,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
         const double n = 9.0 * C, it = 40.0;
         const double t_exp = pairs * 0.1e-9 + 3.0 * 4.0 * n * n / 6.5e12 + N * 50e-12 +
                              it * (4.0 * n * n / 4.9e12 + 10e-6);
-        const double t_imp = no_implicit ? 1e300 : it * (N * 66e-12 + P * 245e-12);
+        const double t_imp = it * (N * 66e-12 + P * 245e-12);
         // and only within the explicit system's memory bound below
         const bool exp_fits = (size_t)81 * C * C * (R + 8) <= ((size_t)8 << 30);
         auto_explicit = t_exp < t_imp && exp_fits;

@@ -207,6 +207,7 @@ struct WOp {
   T D00, D01, D02, D10, D11, D12, D22;     // dr/dP
   T ju0, ju1, ju2, jv0, jv1, jv2;          // intrinsic partials of u, v
   T rw;                                    // rho'
+  bool ctr;                                // centre model: a = R (X - c), slots 3-5 the centre
 
   __device__ __forceinline__ void wt_x(const T* __restrict__ x, bool rec, T& o0, T& o1, T& o2) const {
     if (!rec) {
@@ -220,10 +221,18 @@ struct WOp {
       }
       return;
     }
-    // t = Jc x = D (x_w x RX + x_t) + J_intr x_intr
-    T m0 = x[1] * a2 - x[2] * a1 + x[3];
-    T m1 = x[2] * a0 - x[0] * a2 + x[4];
-    T m2 = x[0] * a1 - x[1] * a0 + x[5];
+    // t = Jc x = D (x_w x a + x_t) + J_intr x_intr (radial: a = RX); centre
+    // model: D (x_w x a - R x_c) with a = R (X - c)
+    T m0 = x[1] * a2 - x[2] * a1, m1 = x[2] * a0 - x[0] * a2, m2 = x[0] * a1 - x[1] * a0;
+    if (ctr) {
+      m0 -= R[0] * x[3] + R[1] * x[4] + R[2] * x[5];
+      m1 -= R[3] * x[3] + R[4] * x[4] + R[5] * x[5];
+      m2 -= R[6] * x[3] + R[7] * x[4] + R[8] * x[5];
+    } else {
+      m0 += x[3];
+      m1 += x[4];
+      m2 += x[5];
+    }
     T tu = D00 * m0 + D01 * m1 + D02 * m2 + ju0 * x[6] + ju1 * x[7] + ju2 * x[8];
     T tv = D10 * m0 + D11 * m1 + D12 * m2 + jv0 * x[6] + jv1 * x[7] + jv2 * x[8];
     T td = D22 * m2;
@@ -251,9 +260,15 @@ struct WOp {
     o[0] = rw * (a1 * g2 - a2 * g1);
     o[1] = rw * (a2 * g0 - a0 * g2);
     o[2] = rw * (a0 * g1 - a1 * g0);
-    o[3] = rw * g0;
-    o[4] = rw * g1;
-    o[5] = rw * g2;
+    if (ctr) {  // centre columns -D R: -(R^T g)
+      o[3] = -rw * (R[0] * g0 + R[3] * g1 + R[6] * g2);
+      o[4] = -rw * (R[1] * g0 + R[4] * g1 + R[7] * g2);
+      o[5] = -rw * (R[2] * g0 + R[5] * g1 + R[8] * g2);
+    } else {
+      o[3] = rw * g0;
+      o[4] = rw * g1;
+      o[5] = rw * g2;
+    }
     o[6] = rw * (ju0 * eu + jv0 * ev);
     o[7] = rw * (ju1 * eu + jv1 * ev);
     o[8] = rw * (ju2 * eu + jv2 * ev);
@@ -319,6 +334,12 @@ __device__ __forceinline__ void make_op(const PcgArgs<T>& a, const PcgSmem<T>& s
   op.jv1 = f * yn * rr;
   op.jv2 = f * yn * rr * rr;
   op.rw = ws < T(0) ? -ws : ws;
+  op.ctr = cw[15] != T(0);
+  if (op.ctr) {
+    // centre model: the rotation increment acts on P = R (X - c); no distortion columns
+    op.a0 = px, op.a1 = py, op.a2 = pz;
+    op.ju1 = op.ju2 = op.jv1 = op.jv2 = T(0);
+  }
 }
 
 template <typename T>

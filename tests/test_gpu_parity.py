@@ -617,9 +617,13 @@ def test_centre_model_blocks_match_oracle(precision, tol):
 
 @pytest.mark.parametrize("precision,solver", [(ba.BA_FP64, ba.BA_SOLVER_IMPLICIT),
                                               (ba.BA_FP64, ba.BA_SOLVER_EXPLICIT),
+                                              (ba.BA_FP32, ba.BA_SOLVER_IMPLICIT),
                                               (ba.BA_FP32, ba.BA_SOLVER_EXPLICIT),
                                               (ba.BA_FP32, ba.BA_SOLVER_SPARSE)])
 def test_centre_model_damped_step_matches_oracle(precision, solver):
+    """The damped step under every solver; the FP32 implicit PCG recomputes the
+    centre model's blocks inside its matvec (rotation columns on R (X - c), centre
+    columns -D R, no distortion columns)."""
     sc = geometric(12, 3000, 2, 12, 5.0, seed=41, camera_model="centre")
     gpu, orc = pair(sc, precision, camera_model=ba.BA_CAMERA_CENTRE, solver=solver,
                     pcg_rel_tol=1e-10 if precision == ba.BA_FP64 else 1e-6)
@@ -634,10 +638,10 @@ def test_centre_model_damped_step_matches_oracle(precision, solver):
 
 
 def test_centre_model_trajectory_and_restrictions():
-    """FP32 LM with the centre model follows the oracle per iteration; the FP32
-    implicit solver (which recomputes the radial model's blocks) is refused, as is
-    the adjoint (no k1, k2 columns: the undamped system is singular); the
-    allocation-free cost follows the model too."""
+    """FP32 LM with the centre model follows the oracle per iteration, with the
+    explicit and with the implicit solver; the adjoint is refused (no k1, k2
+    columns: the undamped system is singular); the allocation-free cost follows
+    the model too."""
     sc = geometric(40, 20000, 3, 20, 10.0, seed=1001, camera_model="centre")
     gpu, orc = pair(sc, ba.BA_FP32, camera_model=ba.BA_CAMERA_CENTRE)
     assert gpu.solver_kind == ba.BA_SOLVER_EXPLICIT
@@ -649,8 +653,12 @@ def test_centre_model_trajectory_and_restrictions():
         assert a["accepted"] == b["accepted"], i
     c_g, _ = gpu.get_params()
     np.testing.assert_array_equal(c_g[:, 7:], sc.cams0[:, 7:])  # k1, k2 untouched
-    with pytest.raises(ba.BAError):
-        ba.Problem.from_scene(sc, ba.Options(camera_model=ba.BA_CAMERA_CENTRE, solver=ba.BA_SOLVER_IMPLICIT))
+    imp = ba.Problem.from_scene(sc, ba.Options(precision=ba.BA_FP32, camera_model=ba.BA_CAMERA_CENTRE,
+                                               solver=ba.BA_SOLVER_IMPLICIT))
+    for i, (a, b) in enumerate(zip(imp.solve(8), log_o)):
+        assert a["cost"] == pytest.approx(b["cost"], rel=1e-5), i
+        assert a["accepted"] == b["accepted"], i
+    imp.close()
     with pytest.raises(ba.BAError):
         gpu.backward(np.zeros_like(sc.cams0), np.zeros_like(sc.pts0))
     dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
