@@ -102,8 +102,9 @@ typedef struct {
                                   P = Exp(w) (X - c); k1, k2 are ignored and left unchanged (the
                                   paper stores the rotation as a quaternion; the axis-angle slots
                                   hold the same rotation, and the update is the same left
-                                  increment).  Every solver supports both models;
-                                  ba_backward needs BA_CAMERA_RADIAL. */
+                                  increment).  Every solver and ba_backward support both
+                                  models; under BA_CAMERA_CENTRE the solve holds the k1, k2
+                                  unknowns with a unit diagonal (they stay zero). */
 } ba_options;
 
 enum { BA_SOLVER_AUTO = 0, BA_SOLVER_IMPLICIT = 1, BA_SOLVER_EXPLICIT = 2, BA_SOLVER_DENSE = 3,

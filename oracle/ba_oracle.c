@@ -824,6 +824,24 @@ int oracle_solve_step(const oracle_problem* pb, const oracle_opts* o, const doub
   double* b = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
   int status = 0;
   double relres = 0.0;
+  /* Camera model of Sec. 3.2 (centre, rotation, focal): slots 7 and 8 are not
+   * parameters.  Their Jacobian columns and gradient entries are zero; the solve
+   * holds them with a unit diagonal in U (before damping), which decouples them
+   * exactly (their unknowns come out zero) and keeps the undamped system of the
+   * adjoint nonsingular.  The other unknowns are those of the system without the
+   * two slots. */
+  double* Uk = NULL;
+  if (o->camera_model == 1 && C > 0) {
+    Uk = (double*)malloc(sizeof(double) * 81 * (size_t)C);
+    memcpy(Uk, U, sizeof(double) * 81 * (size_t)C);
+    for (int64_t c = 0; c < C; ++c)
+      for (int i = 7; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+          Uk[81 * c + 9 * i + j] = i == j ? 1.0 : 0.0;
+          Uk[81 * c + 9 * j + i] = i == j ? 1.0 : 0.0;
+        }
+    U = Uk;
+  }
   if (damped_point_inverses(P, V, pt_rank, lambda, Vinv)) status = -1;
   csr_t byc = build_csr(C, N, pb->obs_cam);
   csr_t byp = build_csr(P, N, pb->obs_pt);
@@ -909,6 +927,7 @@ int oracle_solve_step(const oracle_problem* pb, const oracle_opts* o, const doub
   free(Vinv);
   free(xc);
   free(b);
+  free(Uk);
   return status;
 }
 
@@ -1125,6 +1144,7 @@ int oracle_backward(const oracle_problem* pb, const oracle_opts* o, const double
       ac[9 * c + i] = -acc;
     }
     for (int i = 3; i < 9; ++i) ac[9 * c + i] = -dL_dcams[9 * c + i];
+    if (o->camera_model == 1) ac[9 * c + 7] = ac[9 * c + 8] = 0.0;  /* not parameters */
   }
   for (int64_t i = 0; i < 3 * P; ++i) ap[i] = -dL_dpts[i];
   oracle_opts od = *o;

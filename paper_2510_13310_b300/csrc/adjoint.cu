@@ -46,7 +46,7 @@ template <typename T>
 __global__ void k_adjoint_rhs(int C, int P, const double* __restrict__ cams64, const int* __restrict__ crank,
                               const uint8_t* __restrict__ pt_act, const double* __restrict__ dL_dc,
                               const double* __restrict__ dL_dp, T* __restrict__ Ug, T* __restrict__ gp,
-                              double* __restrict__ a_c, double* __restrict__ a_p) {
+                              double* __restrict__ a_c, double* __restrict__ a_p, int kfix) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < C) {
     const int c = (int)i;
@@ -57,6 +57,7 @@ __global__ void k_adjoint_rhs(int C, int P, const double* __restrict__ cams64, c
       so3_jl_inv_T_apply(cams64 + 9 * (size_t)c, d, a);
 #pragma unroll
       for (int j = 3; j < 9; ++j) a[j] = d[j];
+      if (kfix) a[7] = a[8] = 0.0;  // not parameters under the camera model of Sec. 3.2
     }
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
@@ -75,11 +76,11 @@ __global__ void k_adjoint_rhs(int C, int P, const double* __restrict__ cams64, c
 template <typename T>
 cudaError_t launch_adjoint_rhs(int C, int P, const double* cams64, const int* crank, const uint8_t* pt_act,
                                const double* dL_dc, const double* dL_dp, T* Ug, T* gp, cudaStream_t s,
-                               double* a_c, double* a_p) {
+                               double* a_c, double* a_p, int kfix) {
   const long long n = std::max((long long)C, 3LL * P);
   if (n > 0)
     k_adjoint_rhs<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C, P, cams64, crank, pt_act, dL_dc, dL_dp, Ug, gp,
-                                                                  a_c, a_p);
+                                                                  a_c, a_p, kfix);
   return cudaGetLastError();
 }
 
@@ -348,7 +349,7 @@ cudaError_t launch_adjoint_obs(const Layout& L, const ModelParams& mp, const T* 
 #define BAB_INST_ADJ(T)                                                                                   \
   template cudaError_t launch_adjoint_rhs<T>(int, int, const double*, const int*, const uint8_t*,      \
                                              const double*, const double*, T*, T*, cudaStream_t,         \
-                                             double*, double*);                                          \
+                                             double*, double*, int);                                     \
   template cudaError_t launch_adj_residual<T>(int, int, const int*, const int*, const uint8_t*,         \
                                               const double*, const double*, const double*, const double*, \
                                               T*, T*, cudaStream_t);                                     \

@@ -462,7 +462,8 @@ ba_status schur_t(ba_problem* pb, double lambda) {
     CU(cudaStreamWaitEvent(pb->side, pb->fork, 0));
     cs = pb->side;
     // the Jacobi scaling the formation needs now (it depends on U* only)
-    LAUNCH(1, launch_dscale<T>(pb->n_cam_free, pb->cam_map, (const T*)pb->Ug, lambda, pb->dscale, pb->stream));
+    LAUNCH(1, launch_dscale<T>(pb->n_cam_free, pb->cam_map, (const T*)pb->Ug, lambda, pb->dscale, pb->stream,
+                               pb->mp.cam_model == BA_CAMERA_CENTRE));
   }
   LAUNCH(1, launch_cam_accum<T>(pb->L, pb->mp, 1, (const T*)pb->camw[s], (const T*)pb->ptsw[s],
                                 pb->obs_act_co, pb->cam_act, pb->crank, (const T*)pb->Vinv,
@@ -471,7 +472,7 @@ ba_status schur_t(ba_problem* pb, double lambda) {
   LAUNCH(1, launch_schur_diag<T>(pb->n_cam_free, pb->cam_map, (const T*)pb->Ug, (const T*)pb->Sg, lambda,
                                  (T*)pb->Ud, (T*)pb->Dinv, (T*)pb->bvec, (T*)pb->dampc,
                                  pb->explicit_S ? (T*)pb->Dblk : nullptr,
-                                 pb->explicit_S && !pb->side ? pb->dscale : nullptr, pb->err, cs));
+                                 pb->explicit_S && !pb->side ? pb->dscale : nullptr, pb->err, cs, pb->mp.cam_model == BA_CAMERA_CENTRE));
   if (cs != pb->stream) {
     CU(cudaEventRecord(pb->join, cs));
     pb->join_pending = true;
@@ -729,7 +730,7 @@ ba_status backward_t(ba_problem* pb, const double* dc, const double* dpts, doubl
   }
   LAUNCH(1, launch_adjoint_rhs<T>(C, P, pb->cams64[pb->cur], pb->crank, pb->pt_act, dc, dpts, (T*)pb->Ug,
                                   (T*)pb->gp, pb->stream, refine ? pb->adj_ac : nullptr,
-                                  refine ? pb->adj_ap : nullptr));
+                                  refine ? pb->adj_ap : nullptr, pb->mp.cam_model == BA_CAMERA_CENTRE));
   pb->linearized = false;  // the gradient slots now hold the adjoint right-hand side
   ST(schur_t<T>(pb, 0.0));
   ST(pcg_t<T>(pb, 0.0));
@@ -1942,11 +1943,6 @@ ba_status ba_backward(ba_problem* pb, const double* dL_dcams, const double* dL_d
                       double* dL_duv, double* dL_ddepth) {
   if (!pb || !dL_dcams || !dL_dpts || !dL_duv || !dL_ddepth) {
     set_error("ba_backward: NULL argument");
-    return BA_ERR_INVALID_ARG;
-  }
-  if (pb->mp.cam_model != BA_CAMERA_RADIAL) {
-    // the undamped system has no k1, k2 columns under the centre model: singular
-    set_error("ba_backward: the implicit adjoint is defined for BA_CAMERA_RADIAL");
     return BA_ERR_INVALID_ARG;
   }
   ST(ensure_linearized(pb));

@@ -226,7 +226,8 @@ cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_ac
 template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
                               T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, double* dscale, int* err,
-                              cudaStream_t s);  // dscale (nullable): D and 1/D of the explicit system
+                              cudaStream_t s,
+                              int kfix = 0);  // dscale (nullable): D and 1/D of the explicit system
 // Camera-owned formation of the explicit system (FP32): every co-visibility run
 // (i, j) is summed by its owner camera (run_owner_first), whose Y^ rows, stored in
 // camera order, are staged in shared memory chunk by chunk; pairs hold (owner's
@@ -253,7 +254,7 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
                           bool sparse = false,
                           const CamForm* cf = nullptr);       // FP32: camera-owned formation
 template <typename T>
-cudaError_t launch_dscale(int Cf, const int* cam_map, const T* Ug, double lambda, double* dscale, cudaStream_t s);
+cudaError_t launch_dscale(int Cf, const int* cam_map, const T* Ug, double lambda, double* dscale, cudaStream_t s, int kfix = 0);
 template <typename T>
 size_t spcg_smem_bytes(int n, int rows, int rows_in_smem, int vecs_in_smem, int Cf);
 // row stride of S^: FP32 rows padded to a multiple of 4 entries (zeros)
@@ -311,7 +312,7 @@ cudaError_t launch_scatter_cams(int C, const int* crank, const T* x, double* dc,
 template <typename T>
 cudaError_t launch_adjoint_rhs(int C, int P, const double* cams64, const int* crank, const uint8_t* pt_act,
                                const double* dL_dc, const double* dL_dp, T* Ug, T* gp, cudaStream_t s,
-                               double* a_c = nullptr, double* a_p = nullptr);
+                               double* a_c = nullptr, double* a_p = nullptr, int kfix = 0);
 // FP64-residual refinement of the adjoint solve (adjoint.cu): H mu in FP64 from the
 // FP64 state (u_obs [3N] point order, hmu_p [3P], part [9 n_chunks]), the residual
 // a - H mu into the gradient slots, mu accumulation, and the outputs from mu

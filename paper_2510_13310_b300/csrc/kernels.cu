@@ -1051,7 +1051,10 @@ template <typename T>
 __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* __restrict__ Ug,
                              const T* __restrict__ Sg, double lambda, T* __restrict__ Ud,
                              T* __restrict__ Dinv, T* __restrict__ b, T* __restrict__ dampc,
-                             T* __restrict__ Dblk, double* __restrict__ dscale, int* err) {
+                             T* __restrict__ Dblk, double* __restrict__ dscale, int* err, int kfix) {
+  // kfix (camera model of Sec. 3.2): slots 7 and 8 are not parameters; U holds
+  // them with a unit diagonal (zero Jacobian columns and gradient entries), which
+  // decouples them and keeps the undamped adjoint system nonsingular.
   // D = U* - W V*^-1 W^T, its Cholesky factor and its inverse in FP64 (the two
   // terms can nearly cancel; an FP32 factorisation measurably weakens the
   // preconditioner of the undamped adjoint system)
@@ -1068,7 +1071,7 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
   A* D = Ds[w];
   for (int q = lane; q < 81; q += 32) {
     int i = q / 9, j = q - 9 * i;
-    double uij = u[sym9(i, j)];
+    double uij = (kfix && (i >= 7 || j >= 7)) ? (i == j ? 1.0 : 0.0) : (double)u[sym9(i, j)];
     if (i == j) {
       double dc = clamp_diag(uij);
       dampc[9 * (size_t)f + i] = (T)dc;
@@ -1152,11 +1155,12 @@ __global__ void k_schur_diag(int Cf, const int* __restrict__ cam_map, const T* _
 
 template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
-                              T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, double* dscale, int* err, cudaStream_t s) {
+                              T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, double* dscale, int* err, cudaStream_t s,
+                              int kfix) {
   if (Cf > 0)
     k_schur_diag<T><<<(Cf + kDiagWarps - 1) / kDiagWarps, 32 * kDiagWarps, 0, s>>>(Cf, cam_map, Ug, Sg, lambda, Ud,
                                                                                     Dinv, b, dampc, Dblk, dscale,
-                                                                                    err);
+                                                                                    err, kfix);
   return cudaGetLastError();
 }
 
@@ -1349,7 +1353,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
   template cudaError_t launch_damp_pts<T>(int, const T*, const T*, const uint8_t*, double, T*, T*,  \
                                           int*, cudaStream_t);                                      \
   template cudaError_t launch_schur_diag<T>(int, const int*, const T*, const T*, double, T*, T*,    \
-                                            T*, T*, T*, double*, int*, cudaStream_t);               \
+                                            T*, T*, T*, double*, int*, cudaStream_t, int);          \
   template cudaError_t launch_pred_cams<T>(int, const int*, const T*, const T*, const T*, double,   \
                                            double*, int, cudaStream_t);                             \
   template cudaError_t launch_candidate<T>(int, int, const int*, const T*, const T*, const double*, \

@@ -437,11 +437,12 @@ __global__ void k_S_finalize(int Cf, const T* __restrict__ Dblk, const double* _
 // kernel stores it
 template <typename T>
 __global__ void k_dscale(int Cf, const int* __restrict__ cam_map, const T* __restrict__ Ug, double lambda,
-                         double* __restrict__ dscale) {
+                         double* __restrict__ dscale, int kfix) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= 9 * Cf) return;
   const int f = e / 9, i = e - 9 * f;
-  double u = (double)Ug[54 * (size_t)cam_map[f] + sym9(i, i)];
+  // kfix: slots 7 and 8 held by a unit diagonal (as in the Schur-diagonal kernel)
+  double u = kfix && i >= 7 ? 1.0 : (double)Ug[54 * (size_t)cam_map[f] + sym9(i, i)];
   u += lambda * fmin(fmax(u, 1e-6), 1e32);
   const double d = (double)(T)u;
   const double sd = sqrt(d > 0.0 ? d : 1e-30);
@@ -450,8 +451,9 @@ __global__ void k_dscale(int Cf, const int* __restrict__ cam_map, const T* __res
 }
 
 template <typename T>
-cudaError_t launch_dscale(int Cf, const int* cam_map, const T* Ug, double lambda, double* dscale, cudaStream_t s) {
-  if (Cf > 0) k_dscale<T><<<(9 * Cf + 255) / 256, 256, 0, s>>>(Cf, cam_map, Ug, lambda, dscale);
+cudaError_t launch_dscale(int Cf, const int* cam_map, const T* Ug, double lambda, double* dscale, cudaStream_t s,
+                          int kfix) {
+  if (Cf > 0) k_dscale<T><<<(9 * Cf + 255) / 256, 256, 0, s>>>(Cf, cam_map, Ug, lambda, dscale, kfix);
   return cudaGetLastError();
 }
 
@@ -1499,7 +1501,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
                                         const T*, const int*, const T*, const T*, double*, int, T*, T*, \
                                         bool, int, cudaEvent_t, cudaEvent_t, cudaEvent_t, cudaStream_t, \
                                         const int*, bool, const CamForm*);                              \
-  template cudaError_t launch_dscale<T>(int, const int*, const T*, double, double*, cudaStream_t);       \
+  template cudaError_t launch_dscale<T>(int, const int*, const T*, double, double*, cudaStream_t, int);  \
   template size_t spcg_smem_bytes<T>(int, int, int, int, int);                                         \
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \
   template const void* spcg_kernel_ptr<T>(bool);                                                         \
