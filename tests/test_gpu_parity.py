@@ -354,28 +354,44 @@ def test_track_length_limit():
                 ba.Problem(cams, np.zeros((1, 3)), oc, op, uv, np.zeros(n))
 
 
-def test_degenerate_problems():
+@pytest.mark.parametrize("precision,solver", [(ba.BA_FP64, ba.BA_SOLVER_AUTO), (ba.BA_FP64, ba.BA_SOLVER_IMPLICIT),
+                                              (ba.BA_FP32, ba.BA_SOLVER_IMPLICIT), (ba.BA_FP32, ba.BA_SOLVER_EXPLICIT),
+                                              (ba.BA_FP32, ba.BA_SOLVER_SPARSE), (ba.BA_FP32, ba.BA_SOLVER_DENSE)])
+def test_degenerate_problems(precision, solver):
+    """Under every solver: only the gauge camera (no camera unknowns), cameras and
+    points without observations (LM steps and the adjoint), no observations at
+    all; what has no observation stays unchanged."""
+    o = ba.Options(precision=precision, solver=solver)
     # only the gauge camera: nothing to solve for cameras, points still move
     sc = tiny(n_cams=4, n_pts=50, track=3, seed=2)
     keep = sc.obs_cam == 0
     p = ba.Problem(sc.cams0[:1], sc.pts0, sc.obs_cam[keep], sc.obs_pt[keep], sc.obs_uv[keep],
-                   sc.depth[keep], ba.Options(precision=ba.BA_FP64))
+                   sc.depth[keep], o)
     info = p.lm_step()
     assert info["pcg_iters"] == 0
+    p.close()
     # points and cameras without any observation
-    C, P = sc.spec.n_cams + 2, sc.spec.n_pts + 5
     cams = np.concatenate([sc.cams0, sc.cams0[:2]])
     pts = np.concatenate([sc.pts0, np.zeros((5, 3))])
-    p = ba.Problem(cams, pts, sc.obs_cam, sc.obs_pt, sc.obs_uv, sc.depth)
-    p.lm_step()
+    p = ba.Problem(cams, pts, sc.obs_cam, sc.obs_pt, sc.obs_uv, sc.depth, o)
+    p.solve(2)
     act = p.get_active()
     assert not act["cam_mask"][-2:].any() and not act["pt_mask"][-5:].any()
     assert (act["pt_rank"][-5:] == -1).all()
+    c, q = p.get_params()
+    np.testing.assert_array_equal(c[-2:], cams[-2:])
+    np.testing.assert_array_equal(q[-5:], pts[-5:])
+    duv, dd = p.backward(c - np.concatenate([sc.cams_gt, sc.cams_gt[:2]]), np.zeros_like(q))
+    assert np.all(np.isfinite(duv)) and np.all(np.isfinite(dd))
+    p.close()
     # no observations at all
     p = ba.Problem(sc.cams0, sc.pts0, np.zeros(0, np.int32), np.zeros(0, np.int32),
-                   np.zeros((0, 2)), np.zeros(0))
+                   np.zeros((0, 2)), np.zeros(0), o)
     info = p.lm_step()
     assert info["n_obs_act"] == 0
+    duv, dd = p.backward(np.ones_like(sc.cams0), np.ones_like(sc.pts0))
+    assert duv.shape == (0, 2) and dd.shape == (0,)
+    p.close()
 
 
 def test_device_and_host_buffers_agree():
