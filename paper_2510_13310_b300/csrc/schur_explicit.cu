@@ -9,9 +9,11 @@
 // S is formed Jacobi-scaled, S^ = D^-1 S D^-1 with D = sqrt(diag U*), so every
 // entry is of order one.  Off-diagonal blocks S_ij (i < j) are sums over the
 // points both cameras see; those pairs of observations are listed once at set-up
-// (the co-visibility runs), so each block is summed by one warp in registers in
-// a fixed order: no atomics, bit-reproducible.  The diagonal blocks come from the
-// block-Jacobi pass (U* - sum W V*^-1 W^T) and the lower triangle is mirrored.
+// (the co-visibility runs), so each block is summed by one warp (or, with very
+// many short runs, one lane) in registers in a fixed order: no atomics,
+// bit-reproducible.  The diagonal blocks come from the block-Jacobi pass
+// (U* - sum W V*^-1 W^T) and the lower triangle is mirrored.  The same blocks feed
+// the block-sparse storage and its partitioned PCG further down.
 #include <cuda/atomic>
 #include <type_traits>
 
@@ -518,7 +520,7 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
 
 // ---------------------------------------------------------------------------
 // PCG on the scaled explicit system S^ x^ = b^ (b^ = D^-1 b, x = D^-1 x^) with the
-// block-Jacobi preconditioner of S^ (Sec. 4.3).
+// block-Jacobi preconditioner of S^ (Sec. 4.2 step 3).
 //
 // The vectors are short (n = 9 Cf <= 4608), so every block keeps all of them
 // (p, r, z, q, x) and updates them redundantly; the only distributed work is
