@@ -469,9 +469,29 @@ cudaError_t dense_cholesky_tc(float* A, long long lda, int np, float* Linv, int*
   }
   const int T = np / kPt;
   long long nl = 0;
-  cudaError_t e = cudaSuccess;
+  // Look-ahead of depth one: after panel p is factored (A_p), the trailing update
+  // is split into the next panel's columns (B_p, right behind A_p, so that panel
+  // p + 1 is factored next) and the columns beyond (C_p), which runs while panel
+  // p + 1 is factored.  A and B run on a high-priority stream, C on a low-priority
+  // one, so the block scheduler gives the factorisation's small launches the SMs
+  // that C's tiles free.  B_{p+1} touches columns C_p also updates and waits for
+  // it; C_{p+1} follows C_p and waits for A_{p+1}.  Both streams fork from and
+  // join the caller's stream s.
+  const cudaStream_t s_in = s;
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_c = nullptr;
+  int prio_lo = 0, prio_hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, prio_lo);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_a, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_c, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_a, s_in);  // fork: the inputs are ready on s_in
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_a, 0);
+  bool c_pending = false;  // a C update was enqueued on s2 since s last waited for it
   for (int p0 = 0; p0 < T && e == cudaSuccess; p0 += kPanelTiles) {
     const int p1 = min(T, p0 + kPanelTiles);
+    // A_p: the panel's diagonal tiles, the tiles below them, the in-panel updates
     for (int j = p0; j < p1 && e == cudaSuccess; ++j) {
       float* Ajj = A + (size_t)j * kPt * lda + (size_t)j * kPt;
       float* Lj = Linv + (size_t)j * kPt * kPt;
@@ -491,13 +511,41 @@ cudaError_t dense_cholesky_tc(float* A, long long lda, int np, float* Linv, int*
       }
     }
     const int rest = T - p1;
-    if (e == cudaSuccess && rest > 0) {
-      const float* Lp = A + (size_t)p1 * kPt * lda + (size_t)p0 * kPt;
-      float* Cq = A + (size_t)p1 * kPt * lda + (size_t)p1 * kPt;
-      e = tc_gemm_nt(Lp, lda, Lp, lda, Cq, lda, rest * kPt, rest * kPt, (p1 - p0) * kPt, -1.f, 1.f, true, err, s);
+    if (e != cudaSuccess || rest <= 0) continue;
+    const int p2 = min(T, p1 + kPanelTiles);
+    const float* Lp = A + (size_t)p1 * kPt * lda + (size_t)p0 * kPt;  // rows p1.., panel p's columns
+    const int K = (p1 - p0) * kPt;
+    // C_p: columns p2.. (rows p2..), on s2 once A_p is done
+    if (p2 < T) {
+      e = cudaEventRecord(ev_a, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev_a, 0);
+      const float* Lq = Lp + (size_t)(p2 - p1) * kPt * lda;
+      float* Cq = A + (size_t)p2 * kPt * lda + (size_t)p2 * kPt;
+      if (e == cudaSuccess)
+        e = tc_gemm_nt(Lq, lda, Lq, lda, Cq, lda, (T - p2) * kPt, (T - p2) * kPt, K, -1.f, 1.f, true, err, s2);
       ++nl;
     }
+    // B_p: columns p1..p2 (rows p1..), on s, after the previous C (same columns)
+    if (e == cudaSuccess && c_pending) e = cudaStreamWaitEvent(s, ev_c, 0);
+    c_pending = false;
+    if (e == cudaSuccess) {
+      float* Cb = A + (size_t)p1 * kPt * lda + (size_t)p1 * kPt;
+      e = tc_gemm_nt(Lp, lda, Lp, lda, Cb, lda, rest * kPt, (p2 - p1) * kPt, K, -1.f, 1.f, true, err, s);
+      ++nl;
+    }
+    if (e == cudaSuccess && p2 < T) {
+      e = cudaEventRecord(ev_c, s2);
+      c_pending = true;
+    }
   }
+  // join: the caller's stream waits for the last C update and for the factorisation
+  if (e == cudaSuccess && c_pending) e = cudaStreamWaitEvent(s, ev_c, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_a, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev_a, 0);
+  if (ev_a) cudaEventDestroy(ev_a);
+  if (ev_c) cudaEventDestroy(ev_c);
+  if (s2) cudaStreamDestroy(s2);  // released once its work completes
+  if (s != s_in) cudaStreamDestroy(s);
   if (launches) *launches += nl;
   return e;
 }
