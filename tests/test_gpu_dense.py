@@ -45,8 +45,10 @@ def spd(n, cond, seed):
     return A / d[:, None] / d[None, :]  # Jacobi-scaled like S^
 
 
-@pytest.mark.parametrize("n", [100, 128, 300, 1000, 1791, 2100])
+@pytest.mark.parametrize("n", [100, 128, 300, 1000, 1791, 2100, 4000])
 def test_dense_cholesky_reconstructs(n):
+    """Orders from one tile to 32 tiles (four panels of eight: the look-ahead's split
+    trailing updates, the rest on the low-priority stream, run for three of them)."""
     A = spd(n, 1e3, seed=n)
     L, flags = ba.dense_cholesky(A.astype(np.float32))
     assert flags == 0
