@@ -256,11 +256,13 @@ __device__ __forceinline__ void chol32_step(float (&R)[32], int lane, bool& bad,
   const float lik = lane == K ? dkk * rs : (lane > K ? R[K] * rs : 0.f);
   if (lane == 0) dinv[K] = rs;
   R[K] = lik;
+  // every L_jK first (independent shuffles issued back to back), then the updates
+  float lj[32];
 #pragma unroll
-  for (int j = K + 1; j < 32; ++j) {
-    const float ljk = __shfl_sync(0xffffffffu, lik, j);
-    if (lane >= j) R[j] -= lik * ljk;
-  }
+  for (int j = K + 1; j < 32; ++j) lj[j] = __shfl_sync(0xffffffffu, lik, j);
+#pragma unroll
+  for (int j = K + 1; j < 32; ++j)
+    if (lane >= j) R[j] -= lik * lj[j];
   if constexpr (K + 1 < 32) chol32_step<K + 1>(R, lane, bad, dinv);
 }
 
