@@ -213,6 +213,46 @@ def test_explicit_step_with_many_short_runs_matches_oracle(precision, solver):
     check_step(g, o, *STEP_TOL[precision])
 
 
+@pytest.mark.parametrize("solver", [ba.BA_SOLVER_IMPLICIT, ba.BA_SOLVER_EXPLICIT, ba.BA_SOLVER_SPARSE,
+                                    ba.BA_SOLVER_DENSE])
+def test_two_problems_interleaved_on_two_streams(solver):
+    """Two problems alive at once, their LM steps and adjoints interleaved on two
+    streams, give the same bits as each run alone: no problem reads another's
+    state (exchange words, scratch, cached buffers)."""
+    a_sc = geometric(30, 4000, 4, 12, 7.0, seed=61)
+    b_sc = geometric(45, 6000, 4, 10, 6.0, seed=62)
+    o = ba.Options(precision=ba.BA_FP32, solver=solver)
+
+    def alone(sc):
+        p = ba.Problem.from_scene(sc, o)
+        log = [p.lm_step()["cost"] for _ in range(5)]
+        c, q = p.get_params()
+        g = p.backward(c - sc.cams_gt, q - sc.pts_gt)
+        p.close()
+        return log, c, q, g
+
+    ref_a, ref_b = alone(a_sc), alone(b_sc)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    pa = ba.Problem.from_scene(a_sc, o, stream=sa.cuda_stream)
+    pb = ba.Problem.from_scene(b_sc, o, stream=sb.cuda_stream)
+    la, lb = [], []
+    for _ in range(5):
+        la.append(pa.lm_step()["cost"])
+        lb.append(pb.lm_step()["cost"])
+    ca, qa = pa.get_params()
+    cb, qb = pb.get_params()
+    ga = pa.backward(ca - a_sc.cams_gt, qa - a_sc.pts_gt)
+    gb = pb.backward(cb - b_sc.cams_gt, qb - b_sc.pts_gt)
+    for got, ref in (((la, ca, qa, ga), ref_a), ((lb, cb, qb, gb), ref_b)):
+        assert got[0] == ref[0]
+        np.testing.assert_array_equal(got[1], ref[1])
+        np.testing.assert_array_equal(got[2], ref[2])
+        np.testing.assert_array_equal(got[3][0], ref[3][0])
+        np.testing.assert_array_equal(got[3][1], ref[3][1])
+    pa.close()
+    pb.close()
+
+
 @pytest.mark.parametrize("solver", [ba.BA_SOLVER_EXPLICIT, ba.BA_SOLVER_IMPLICIT])
 def test_reused_device_buffers_give_identical_runs(solver):
     """ba_destroy hands a problem's buffers to the process cache and the next
