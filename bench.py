@@ -39,10 +39,10 @@ METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 
 
 # DRAM bytes (read + write) of one launch of a roofline kernel on a workload, from
 # ncu captures (profiles/k_spcg_medium_1M_obs.md,
-# profiles/top_kernels_traffic_medium_1M_obs.md,
+# profiles/k_form_S_runs_medium_1M_obs.md,
 # profiles/k_form_S_cam_dense_mid_1M_obs.md); absent once the kernel has changed
 # since the counters were taken, or for workloads not captured.
-NCU_TRAFFIC = {("medium", "k_spcg"): 13154816 + 26368, ("medium", "k_form_S_runs"): 303936768 + 7791360,
+NCU_TRAFFIC = {("medium", "k_spcg"): 13154816 + 26368, ("medium", "k_form_S_runs"): 302387200 + 8206336,
                ("dense_mid", "k_form_S_cam"): 367535616 + 51516160}
 WORKLOAD = "medium"
 LM_ITERS = 30
