@@ -143,7 +143,7 @@ void ba_default_options(ba_options* o);
  * a prior is given): the parameter vector x = [c; p] and the observation set
  * from which Sec. 4.2 step 1 builds O_valid at every iteration.
  * Checks index ranges, finiteness and duplicate (camera, point) pairs on the
- * host (BA_ERR_INVALID_ARG).  Limits: N < 2^31, at most 256 observations per
+ * host (BA_ERR_INVALID_ARG).  Limits: N < 2^30, at most 256 observations per
  * point.  stream: a cudaStream_t (NULL = legacy default stream).  The problem
  * lives on the device current at the call.  Input arrays may be host or device
  * memory (host arrays are read in place); the call returns with the device idle.
@@ -309,9 +309,9 @@ void ba_gp_default_options(ba_gp_options* o);
  * rays [N][3], depth [N] (metric distance along the ray; <= 0 or NaN: none, the
  * scale is free), scales0 [N] initial scales of the free observations (NULL: 1;
  * entries of pinned observations are ignored).  Host or device pointers; the
- * library copies them.  Errors: BA_ERR_INVALID_ARG for bad sizes, indices,
- * duplicate (camera, point) pairs, more than 256 observations per point or
- * non-finite centres, points, rays or scales. */
+ * library copies them.  Errors: BA_ERR_INVALID_ARG for bad sizes (N < 2^30),
+ * indices, duplicate (camera, point) pairs, more than 256 observations per point
+ * or non-finite centres, points, rays or scales. */
 ba_status ba_gp_create(const ba_gp_options* opts, void* stream, int64_t n_cams, const double* centres,
                        int64_t n_pts, const double* pts, int64_t n_obs, const int32_t* obs_cam,
                        const int32_t* obs_pt, const double* rays, const double* depth, const double* scales0,

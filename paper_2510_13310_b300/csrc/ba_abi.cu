@@ -898,8 +898,9 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     set_error("invalid options");
     return BA_ERR_INVALID_ARG;
   }
+  // N < 2^30 keeps every 32-bit index of the kernels plus its grid stride below 2^31
   if (n_cams < 0 || n_pts < 0 || n_obs < 0 || n_cams >= (1LL << 24) || n_pts >= (1LL << 30) ||
-      n_obs >= (1LL << 31) - 1024) {
+      n_obs >= (1LL << 30)) {
     set_error("sizes out of range");
     return BA_ERR_INVALID_ARG;
   }
@@ -1765,7 +1766,7 @@ ba_status ba_selftest_layout(int64_t n_cams, const double* cams, int64_t n_pts, 
                              const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv, int with_covis,
                              int* mismatch) {
   if (!mismatch || n_cams < 0 || n_pts < 0 || n_obs < 0 || n_cams >= (1LL << 24) || n_pts >= (1LL << 30) ||
-      n_obs >= (1LL << 31) - 1024 || (n_cams && !cams) || (n_pts && !pts) ||
+      n_obs >= (1LL << 30) || (n_cams && !cams) || (n_pts && !pts) ||
       (n_obs && (!obs_cam || !obs_pt || !obs_uv))) {
     set_error("ba_selftest_layout: invalid arguments");
     return BA_ERR_INVALID_ARG;

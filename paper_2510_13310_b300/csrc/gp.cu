@@ -740,7 +740,7 @@ ba_status gp_create_impl(const ba_gp_options* opts, void* stream, int64_t n_cams
     return BA_ERR_INVALID_ARG;
   }
   if (n_cams < 0 || n_pts < 0 || n_obs < 0 || n_cams >= (1LL << 24) || n_pts >= (1LL << 30) ||
-      n_obs >= (1LL << 31) - 1024) {
+      n_obs >= (1LL << 30)) {
     gp_error("sizes out of range");
     return BA_ERR_INVALID_ARG;
   }

@@ -667,7 +667,7 @@ int build_covis_runs_dev(const DevLayout& L, int C, int N, const DevAlloc& alloc
         total64 += t * (t - 1) / 2;
       }
     }
-    if (total64 >= (1LL << 31) - 1)
+    if (total64 >= (1LL << 30))  // pair indices plus a loop stride stay below 2^31
       return fail(err, 1, "too many co-visible observation pairs (%lld) for the explicit system", total64);
     DCU(dev_exclusive_scan(cnt, N, d_total, sc, s));
     total = (int)total64;

@@ -62,6 +62,11 @@ def test_invalid_options_rejected_before_any_device_work():
     o.pcg_rel_tol = 1e-6
     st = L.ba_create(ct.byref(o), None, -1, None, 0, None, 0, None, None, None, None, ct.byref(h))
     assert st == ba.BA_ERR_INVALID_ARG
+    # 2^30 observations and more: refused before any array is read (32-bit kernel
+    # indices plus their grid stride stay below 2^31 under the limit)
+    st = L.ba_create(ct.byref(o), None, 0, None, 0, None, 1 << 30, None, None, None, None, ct.byref(h))
+    assert st == ba.BA_ERR_INVALID_ARG and not h.value
+    assert "sizes out of range" in L.ba_last_error().decode()
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
