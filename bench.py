@@ -210,7 +210,25 @@ def run_dense_kernels():
     return 0
 
 
-def run_gp_measure(torch, ba, dev, stream, steps=8, warmup=3):
+def gp_oracle_cpu_baseline(sc, max_seconds=10.0, max_iters=8):
+    """The FP64 CPU oracle of global positioning (test infrastructure) on a bounded
+    sample of the same scene: LM iterations until max_seconds of work or max_iters
+    (at least one), one iteration per call with the state carried over."""
+    import oracle
+    ob = oracle.OracleGP.from_scene(sc)
+    t, X, s = sc.centres0.copy(), sc.pts0.copy(), sc.scales0.copy()
+    done, t_tot = 0, 0.0
+    while done < max_iters and t_tot < max_seconds:
+        t0 = time.perf_counter()
+        t, X, s, _ = ob.lm(t, X, s, 1)
+        t_tot += time.perf_counter() - t0
+        done += 1
+    return {"value": done / t_tot, "unit": "LM iters/s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{done} LM iteration(s) of the global-positioning scene (FP64, dense Cholesky of the "
+                      f"centre system), {t_tot:.1f} s"}
+
+
+def run_gp_measure(torch, ba, dev, stream, steps=8, warmup=3, cpu=True):
     """Depth-constrained global positioning on the same geometry (200 cameras, 100k
     points, ~1M observations, rays with 0.5 px angular noise, 2% outliers, metric
     range priors on 50%): LM iterations/s over `steps` timed iterations (CUDA
@@ -249,6 +267,8 @@ def run_gp_measure(torch, ba, dev, stream, steps=8, warmup=3):
                                   "peak_source": kind + " (burst copy)",
                                   "formula": "164 B x obs + 80 B x points"}}
     prob.close()
+    if cpu:
+        out["cpu_baseline"] = gp_oracle_cpu_baseline(sc)
     return out
 
 
@@ -354,7 +374,7 @@ def main():
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         print(json.dumps(run_gp_measure(torch, ba, dev, torch.cuda.current_stream(dev), steps=args.steps,
-                                        warmup=args.warmup)), flush=True)
+                                        warmup=args.warmup, cpu=not args.no_cpu_baseline)), flush=True)
         return 0
 
     import torch
@@ -602,7 +622,7 @@ def main():
 
     gp = None
     if not args.no_gp and args.workload == WORKLOAD:
-        gp = run_gp_measure(torch, ba, dev, stream)
+        gp = run_gp_measure(torch, ba, dev, stream, cpu=rank == 0 and not args.no_cpu_baseline)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
