@@ -190,23 +190,39 @@ class Options:
 
 
 class _Arr:
-    """Keeps a host/device buffer alive and exposes its address."""
+    """Keeps a host/device buffer alive and exposes its address.
 
-    def __init__(self, a, dtype):
+    size: the element count the library will read or write (ValueError otherwise:
+    the C ABI takes bare pointers and cannot check).  out: the library writes into
+    the buffer, so it must be used in place: the exact dtype, contiguous (a NumPy
+    array also writeable); anything that would need a converted copy is refused
+    instead of silently receiving the results in a temporary."""
+
+    def __init__(self, a, dtype, size=None, what="array", out=False):
         self.obj = a
         if hasattr(a, "data_ptr"):  # torch tensor
             import torch
             tdt = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8,
                    np.float32: torch.float32}[dtype]
+            if out and (a.dtype != tdt or not a.is_contiguous()):
+                raise ValueError(f"{what}: output tensor must be contiguous {tdt}")
             t = a.contiguous()
             if t.dtype != tdt:
                 t = t.to(tdt)
             self.obj = t
             self.ptr = t.data_ptr()
+            n = t.numel()
         else:
+            if out and not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous
+                            and a.flags.writeable):
+                raise ValueError(f"{what}: output array must be a writeable C-contiguous {np.dtype(dtype)} array")
             arr = np.ascontiguousarray(a, dtype=dtype)
             self.obj = arr
             self.ptr = arr.ctypes.data
+            n = arr.size
+        if size is not None and n != size:
+            raise ValueError(f"{what}: {n} elements, expected {size}")
+        self.n = n
 
     @property
     def p(self):
@@ -222,14 +238,29 @@ def selftest_layout(cams, pts, obs_cam, obs_pt, obs_uv, with_covis=True):
     """ba_selftest_layout on host arrays: the mismatch bitmask (0 = the device
     layout equals the host reference layout bit for bit)."""
     L = lib()
-    arrs = [_Arr(cams, np.float64), _Arr(pts, np.float64), _Arr(obs_cam, np.int32), _Arr(obs_pt, np.int32),
-            _Arr(obs_uv, np.float64)]
+    arrs = _problem_arrays(cams, pts, obs_cam, obs_pt, obs_uv, None)
     mm = ct.c_int(-1)
-    _check(L.ba_selftest_layout(int(np.prod(arrs[0].obj.shape)) // 9, arrs[0].p,
-                                int(np.prod(arrs[1].obj.shape)) // 3, arrs[1].p, int(np.prod(arrs[2].obj.shape)),
+    _check(L.ba_selftest_layout(arrs[0].n // 9, arrs[0].p, arrs[1].n // 3, arrs[1].p, arrs[2].n,
                                 arrs[2].p, arrs[3].p, arrs[4].p, int(bool(with_covis)), ct.byref(mm)),
            "ba_selftest_layout")
     return mm.value
+
+
+def _problem_arrays(cams, pts, obs_cam, obs_pt, obs_uv, depth, cam_width=9, uv_width=2, what="ba_create"):
+    """The input arrays of a problem, sizes checked against each other: cams
+    [C][cam_width], pts [P][3], obs_cam, obs_pt [N], obs_uv [N][uv_width], depth [N]."""
+    c = _Arr(cams, np.float64, what=f"{what}: cameras")
+    p = _Arr(pts, np.float64, what=f"{what}: points")
+    if c.n % cam_width or p.n % 3:
+        raise ValueError(f"{what}: camera array of {c.n} values is not [C][{cam_width}] "
+                         f"or point array of {p.n} values is not [P][3]")
+    oc = _Arr(obs_cam, np.int32, what=f"{what}: obs_cam")
+    N = oc.n
+    arrs = [c, p, oc, _Arr(obs_pt, np.int32, N, f"{what}: obs_pt"),
+            _Arr(obs_uv, np.float64, uv_width * N, f"{what}: observations")]
+    if depth is not None:
+        arrs.append(_Arr(depth, np.float64, N, f"{what}: depth"))
+    return arrs
 
 
 def _stream_handle(stream):
@@ -253,11 +284,10 @@ class Problem:
         self.options = options or Options()
         o = self.options
         copt, self._fixed = _c_options(o)
-        arrs = [_Arr(cams, np.float64), _Arr(pts, np.float64), _Arr(obs_cam, np.int32),
-                _Arr(obs_pt, np.int32), _Arr(obs_uv, np.float64), _Arr(depth, np.float64)]
-        self.n_cams = int(np.prod(arrs[0].obj.shape)) // 9
-        self.n_pts = int(np.prod(arrs[1].obj.shape)) // 3
-        self.n_obs = int(np.prod(arrs[2].obj.shape))
+        arrs = _problem_arrays(cams, pts, obs_cam, obs_pt, obs_uv, depth)
+        self.n_cams = arrs[0].n // 9
+        self.n_pts = arrs[1].n // 3
+        self.n_obs = arrs[2].n
         h = ct.c_void_p()
         st = self.L.ba_create(ct.byref(copt), _stream_handle(stream), self.n_cams, arrs[0].p,
                               self.n_pts, arrs[1].p, self.n_obs, arrs[2].p, arrs[3].p, arrs[4].p,
@@ -301,12 +331,14 @@ class Problem:
         """Copies into the given buffers (NumPy or torch); allocates NumPy arrays if omitted."""
         c = cams if cams is not None else np.zeros((self.n_cams, 9))
         p = pts if pts is not None else np.zeros((self.n_pts, 3))
-        ca, pa = _Arr(c, np.float64), _Arr(p, np.float64)
+        ca = _Arr(c, np.float64, 9 * self.n_cams, "get_params: cameras", out=True)
+        pa = _Arr(p, np.float64, 3 * self.n_pts, "get_params: points", out=True)
         _check(self.L.ba_get_params(self.h, ca.p, pa.p), "ba_get_params")
         return ca.obj, pa.obj
 
     def set_params(self, cams, pts):
-        ca, pa = _Arr(cams, np.float64), _Arr(pts, np.float64)
+        ca = _Arr(cams, np.float64, 9 * self.n_cams, "set_params: cameras")
+        pa = _Arr(pts, np.float64, 3 * self.n_pts, "set_params: points")
         _check(self.L.ba_set_params(self.h, ca.p, pa.p), "ba_set_params")
 
     def extract(self, drop=False):
@@ -344,8 +376,8 @@ class Problem:
 
     def eval_cost(self, cams=None, pts=None):
         F, r = ct.c_double(0), ct.c_double(0)
-        ca = _Arr(cams, np.float64) if cams is not None else None
-        pa = _Arr(pts, np.float64) if pts is not None else None
+        ca = _Arr(cams, np.float64, 9 * self.n_cams, "eval_cost: cameras") if cams is not None else None
+        pa = _Arr(pts, np.float64, 3 * self.n_pts, "eval_cost: points") if pts is not None else None
         _check(self.L.ba_eval_cost(self.h, ca.p if ca else None, pa.p if pa else None,
                                    ct.byref(F), ct.byref(r)), "ba_eval_cost")
         return F.value, r.value
@@ -353,8 +385,10 @@ class Problem:
     def backward(self, dL_dcams, dL_dpts, dL_duv=None, dL_ddepth=None):
         duv = dL_duv if dL_duv is not None else np.zeros((self.n_obs, 2))
         dd = dL_ddepth if dL_ddepth is not None else np.zeros(self.n_obs)
-        a, b = _Arr(dL_dcams, np.float64), _Arr(dL_dpts, np.float64)
-        ua, da = _Arr(duv, np.float64), _Arr(dd, np.float64)
+        a = _Arr(dL_dcams, np.float64, 9 * self.n_cams, "backward: dL/dcams")
+        b = _Arr(dL_dpts, np.float64, 3 * self.n_pts, "backward: dL/dpts")
+        ua = _Arr(duv, np.float64, 2 * self.n_obs, "backward: dL/duv", out=True)
+        da = _Arr(dd, np.float64, self.n_obs, "backward: dL/ddepth", out=True)
         _check(self.L.ba_backward(self.h, a.p, b.p, ua.p, da.p), "ba_backward",
                allow=(BA_OK, BA_ERR_NOT_CONVERGED))
         return ua.obj, da.obj
@@ -505,12 +539,12 @@ class GPProblem:
         self._fixed = np.ascontiguousarray(np.asarray(o.fixed_cams, dtype=np.int32))
         copt = _GPOptions(o.huber_delta, o.lambda0, o.pcg_rel_tol, o.pcg_max_iters,
                           self._fixed.ctypes.data_as(ct.POINTER(ct.c_int32)), len(self._fixed), o.solver)
-        arrs = [_Arr(centres, np.float64), _Arr(pts, np.float64), _Arr(obs_cam, np.int32),
-                _Arr(obs_pt, np.int32), _Arr(rays, np.float64), _Arr(depth, np.float64)]
-        s0 = None if scales0 is None else _Arr(scales0, np.float64)
-        self.n_cams = int(np.prod(arrs[0].obj.shape)) // 3
-        self.n_pts = int(np.prod(arrs[1].obj.shape)) // 3
-        self.n_obs = int(np.prod(arrs[2].obj.shape))
+        arrs = _problem_arrays(centres, pts, obs_cam, obs_pt, rays, depth, cam_width=3, uv_width=3,
+                               what="ba_gp_create")
+        self.n_cams = arrs[0].n // 3
+        self.n_pts = arrs[1].n // 3
+        self.n_obs = arrs[2].n
+        s0 = None if scales0 is None else _Arr(scales0, np.float64, self.n_obs, "ba_gp_create: scales0")
         h = ct.c_void_p()
         _check(self.L.ba_gp_create(ct.byref(copt), _stream_handle(stream), self.n_cams, arrs[0].p, self.n_pts,
                                    arrs[1].p, self.n_obs, arrs[2].p, arrs[3].p, arrs[4].p, arrs[5].p,

@@ -4,6 +4,7 @@ import ctypes as ct
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2510_13310_b300 import ba, build
@@ -111,3 +112,41 @@ def test_noalloc_binding_rejects_bad_tensors(change, match):
     with pytest.raises(ValueError, match=match):
         ba.eval_cost_noalloc(a["cams"], a["pts"], a["obs_cam"], a["obs_pt"], a["obs_uv"],
                              a["depth"], a["out"], obs_mask=a["obs_mask"])
+
+
+def _problem_args(C=3, P=4, N=5):
+    rng = np.random.default_rng(0)
+    return dict(cams=np.zeros((C, 9)), pts=np.zeros((P, 3)), obs_cam=rng.integers(0, C, N).astype(np.int32),
+                obs_pt=rng.integers(0, P, N).astype(np.int32), obs_uv=np.zeros((N, 2)), depth=np.zeros(N))
+
+
+@pytest.mark.parametrize("change,match", [
+    (lambda a: a.update(cams=np.zeros((3, 8))), r"not \[C\]\[9\]"),
+    (lambda a: a.update(pts=np.zeros(10)), r"not \[P\]\[3\]"),
+    (lambda a: a.update(obs_pt=np.zeros(4, np.int32)), "obs_pt: 4 elements, expected 5"),
+    (lambda a: a.update(obs_uv=np.zeros((4, 2))), "observations: 8 elements, expected 10"),
+    (lambda a: a.update(depth=np.zeros(6)), "depth: 6 elements, expected 5"),
+])
+def test_problem_binding_checks_sizes_before_the_library_reads(change, match):
+    """The C ABI takes bare pointers: a short observation array would be read past
+    its end, so the binding checks every size against N before ba_create."""
+    a = _problem_args()
+    change(a)
+    with pytest.raises(ValueError, match=match):
+        ba.Problem(a["cams"], a["pts"], a["obs_cam"], a["obs_pt"], a["obs_uv"], a["depth"])
+
+
+def test_output_buffers_are_used_in_place_or_refused():
+    """An output buffer the library writes must be the exact dtype and contiguous:
+    a converted copy would receive the results instead of the caller's buffer."""
+    torch = pytest.importorskip("torch")
+    for bad in (np.zeros(6, np.float32), np.zeros((3, 4))[:, ::2], torch.zeros(6, dtype=torch.float32),
+                torch.zeros(3, 4, dtype=torch.float64)[:, ::2]):
+        with pytest.raises(ValueError, match="output"):
+            ba._Arr(bad, np.float64, 6, "out", out=True)
+    good = np.zeros(6)
+    assert ba._Arr(good, np.float64, 6, "out", out=True).obj is good
+    t = torch.zeros(6, dtype=torch.float64)
+    assert ba._Arr(t, np.float64, 6, "out", out=True).ptr == t.data_ptr()
+    with pytest.raises(ValueError, match="7 elements, expected 6"):
+        ba._Arr(np.zeros(7), np.float64, 6, "out", out=True)
