@@ -44,6 +44,14 @@ METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 
 # since the counters were taken, or for workloads not captured.
 NCU_TRAFFIC = {("medium", "k_spcg"): 13154816 + 26368, ("medium", "k_form_S_runs"): 302387200 + 8206336,
                ("dense_mid", "k_form_S_cam"): 367535616 + 51516160}
+# the measured limiter of a kernel whose roofline bound (ALU) is not what stops it:
+# ncu counters of one launch on the workload (profiles/<kernel>_<workload>...md)
+NCU_LIMITER = {("medium", "k_form_S_runs"): {
+    "counter": "l1tex__throughput.avg.pct_of_peak_sustained_active", "value_pct": 93.9,
+    "long_scoreboard_cycles_per_issue": 8.0, "warp_cycles_per_issue": 9.92,
+    "reading": "the L1TEX pipe moving the scattered 112-byte Y^ row gathers (two per co-visible pair) is "
+               "the limiter, not the FP32 pipe",
+    "source": "profiles/k_form_S_runs_medium_1M_obs.md"}}
 WORKLOAD = "medium"
 LM_ITERS = 30
 E2E_RUNS = 3
@@ -538,6 +546,7 @@ def main():
                      "unit": "TFLOP/s", "frac": flops / (form_ms * 1e-3) / 1e12 / fp32_peak,
                      "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x 2032 MHz",
                      "traffic": NCU_TRAFFIC.get((args.workload, fname)) if args.precision == "fp32" else None,
+                     "measured_limiter": NCU_LIMITER.get((args.workload, fname)) if args.precision == "fp32" else None,
                      "algorithmic_per_launch": flops,
                      "formula": "486 flops x co-visible pairs of free cameras", "pairs": npairs,
                      "hbm_bytes_algorithmic": 8 * npairs + 108 * N + 4 * n * n,
