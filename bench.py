@@ -459,7 +459,8 @@ def main():
     ext_roof = {"bytes_algorithmic": ext_bytes, "ms": ext_ms,
                 "achieved_gbs": ext_bytes / (ext_ms * 1e-3) / 1e9,
                 "frac_of_hbm": ext_bytes / (ext_ms * 1e-3) / 1e9 / _peaks()[0],
-                "note": "~10 launches and one blocking readback of the counts: latency-bound"}
+                "note": "one CUDA graph replay (the first pass: ~16 kernels and 7 memsets) and one blocking "
+                        "readback of the counts: latency-bound"}
 
     # roofline of the dominant kernel: of the PCG launch (ms[4]) and the co-visibility
     # product that forms the explicit system (ms[7]), the one with the larger mean

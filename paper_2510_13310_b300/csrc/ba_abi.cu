@@ -184,6 +184,15 @@ struct ba_problem {
   bool cand_cams_done = false;  // launched early for this step; `cand_join` marks its end
   cudaEvent_t cand_fork = nullptr, cand_join = nullptr;  // around the co-visibility product kernel of the latest formation
   bool evf_valid = false;
+  // step (c): the first pass of an extraction (begin, one peel round, the
+  // finalisation, the scalars back to the host) is a fixed sequence of ~20
+  // operations per (drop, state slot); it is captured once into a CUDA graph on
+  // `cap` and replayed on `stream` (the same kernels in the same order: the same
+  // bits, without a launch gap between them)
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t ext_graph[2][2] = {};
+  long long ext_graph_launches[2][2] = {};
+  bool ext_graph_off = false;  // capture failed once: launch the operations one by one
 };
 
 namespace {
@@ -354,10 +363,6 @@ ba_status run_extraction(ba_problem* pb, bool drop, int* rounds_out) {
   ba_problem* p = pb;
   int slot = p->cur;
   if (!p->bits_valid[slot]) ST(eval_state(p, slot, true, false));
-  LAUNCH(1, launch_extract_begin(p->L, p->alive, p->bits[slot], p->valid, drop ? 1 : 0, p->stream));
-  LAUNCH(1, launch_fill_u8(p->cam_act, 1, p->C, p->stream));
-  LAUNCH(1, launch_fill_u8(p->pt_act, 1, p->P, p->stream));
-  CU(cudaMemsetAsync(p->cam_cnt, 0, sizeof(int) * std::max(1, p->C), p->stream));
   int rounds = 0;
   const int max_rounds = p->C + p->P + 2;
   // One peel round, then the finalisation launched speculatively: a single
@@ -371,7 +376,7 @@ ba_status run_extraction(ba_problem* pb, bool drop, int* rounds_out) {
     LAUNCH(1, launch_peel_cams(p->L, p->cam_act, p->cam_cnt, p->opt.min_cam_obs, p->sc, p->stream));
     return BA_OK;
   };
-  auto finalize = [&]() -> ba_status {
+  auto finalize_enqueue = [&]() -> ba_status {
     CU(cudaMemsetAsync(&p->sc->mask_changed, 0, sizeof(int), p->stream));
     CU(cudaMemsetAsync(&p->sc->n_obs_act, 0, sizeof(int), p->stream));
     CU(cudaMemsetAsync(&p->sc->n_cam_act, 0, sizeof(int), p->stream));
@@ -383,10 +388,55 @@ ba_status run_extraction(ba_problem* pb, bool drop, int* rounds_out) {
     LAUNCH(3, launch_rank(p->pt_act, p->P, p->pt_rank, p->pt_map, &p->sc->n_pt_act, p->rank_tmp,
                           p->n_rank_tmp, p->stream));
     CU(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->stream));
+    return BA_OK;
+  };
+  auto finalize = [&]() -> ba_status {
+    ST(finalize_enqueue());
     return sync(p);
   };
-  ST(peel_round());
-  ST(finalize());
+  // the first pass: begin, one peel round, the finalisation launched speculatively
+  auto first_pass = [&]() -> ba_status {
+    LAUNCH(1, launch_extract_begin(p->L, p->alive, p->bits[slot], p->valid, drop ? 1 : 0, p->stream));
+    LAUNCH(1, launch_fill_u8(p->cam_act, 1, p->C, p->stream));
+    LAUNCH(1, launch_fill_u8(p->pt_act, 1, p->P, p->stream));
+    CU(cudaMemsetAsync(p->cam_cnt, 0, sizeof(int) * std::max(1, p->C), p->stream));
+    ST(peel_round());
+    return finalize_enqueue();
+  };
+  cudaGraphExec_t& ge = p->ext_graph[drop ? 1 : 0][slot];
+  if (!ge && !p->ext_graph_off) {
+    // capture the first pass once (thread-local capture: other threads' CUDA calls
+    // are unaffected); on any failure the operations are launched one by one
+    if (!p->cap) CU(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    cudaStream_t main_stream = p->stream;
+    const long long l0 = p->launches;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      p->stream = p->cap;
+      const ba_status st = first_pass();
+      p->stream = main_stream;
+      ok = cudaStreamEndCapture(p->cap, &graph) == cudaSuccess && st == BA_OK && graph;
+    }
+    if (ok) ok = cudaGraphInstantiate(&ge, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    p->ext_graph_launches[drop ? 1 : 0][slot] = p->launches - l0;
+    p->launches = l0;
+    if (!ok) {
+      ge = nullptr;
+      p->ext_graph_off = true;
+      (void)cudaGetLastError();  // the capture's error is not the caller's
+    }
+  }
+  if (ge) {
+    p->launches += p->ext_graph_launches[drop ? 1 : 0][slot];
+    rounds = 1;
+    CU(cudaGraphLaunch(ge, p->stream));
+    ST(sync(p));
+  } else {
+    ST(first_pass());
+    ST(sync(p));
+  }
   if (p->h_sc->changed) {
     // the speculative pass already compared against the previous masks: keep
     // its outcome (a spurious "changed" only costs a recomputation)
@@ -1465,6 +1515,10 @@ void free_problem(ba_problem* pb) {
     cudaStreamSynchronize(pb->side);
     cudaStreamDestroy(pb->side);
   }
+  for (auto& row : pb->ext_graph)
+    for (cudaGraphExec_t& g : row)
+      if (g) cudaGraphExecDestroy(g);
+  if (pb->cap) cudaStreamDestroy(pb->cap);
   if (pb->fork) cudaEventDestroy(pb->fork);
   if (pb->join) cudaEventDestroy(pb->join);
   if (pb->cand_fork) cudaEventDestroy(pb->cand_fork);
