@@ -422,8 +422,10 @@ void ba_explicit_layout(const ba_problem* pb, int* rows_in_smem, int* vecs_in_sm
  * system (Eq. LM, Schur form), chosen at creation from the co-visibility runs:
  * 1 one warp per camera pair (k_form_S_runs), 2 one lane per camera pair
  * (k_form_S_lanes: FP64 with very many short runs), 3 camera-owned formation
- * (k_form_S_cam: FP32 with very many short runs); 0 for the implicit solver or a
- * NULL handle. */
+ * (k_form_S_cam: FP32 with very many short runs), 4 one warp per camera pair from
+ * observation records (k_form_S_rec: FP32 otherwise; the environment variable
+ * BA_FORM_RECORDS=0, read by ba_create, selects kernel 1 instead); 0 for the
+ * implicit solver or a NULL handle. */
 int ba_formation_kernel(const ba_problem* pb);
 
 /* Free a problem (the paper has no counterpart: resource management of this

@@ -418,7 +418,7 @@ class Problem:
     @property
     def formation_kernel(self) -> str | None:
         """ba_formation_kernel: the kernel forming the explicit system's blocks."""
-        return {1: "k_form_S_runs", 2: "k_form_S_lanes", 3: "k_form_S_cam"}.get(self.L.ba_formation_kernel(self.h))
+        return {1: "k_form_S_runs", 2: "k_form_S_lanes", 3: "k_form_S_cam", 4: "k_form_S_rec"}.get(self.L.ba_formation_kernel(self.h))
 
     @property
     def explicit_layout(self) -> dict:

@@ -141,6 +141,8 @@ struct ba_problem {
   int2* covis_pairs = nullptr;  // point-order observations (k in i, k2 in j) of shared points; FP32
                                 // explicit systems: camera-order (owner's row, other's row), see CamForm
   CamForm cform;                // FP32 explicit systems: the camera-owned formation (n_blocks > 0)
+  float* orec = nullptr;        // FP32 warp-per-run formation: observation records [N][12]
+  int* pair_pt = nullptr;       //   and the point of every co-visible pair
   int n_covis_runs = 0;
   bool form_lanes = false;      // one lane per co-visibility run (many short runs)
   double* dscale = nullptr;
@@ -478,7 +480,8 @@ ba_status linearize_t(ba_problem* pb) {
   // W rows are stored when the matvec streams them or the explicit system is formed
   LAUNCH(1, launch_pt_lin<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                              (pb->recompute && !pb->explicit_S) ? nullptr : (T*)pb->W,
-                             pb->recompute ? (T*)pb->wsgn : nullptr, (T*)pb->V, (T*)pb->gp, pb->stream));
+                             pb->recompute ? (T*)pb->wsgn : nullptr, (T*)pb->V, (T*)pb->gp, pb->stream,
+                             pb->orec));
   // the camera side reads neither W nor V: it runs on the side stream alongside
   cudaStream_t cs = pb->stream;
   if (pb->side) {
@@ -542,11 +545,17 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
       // S^ (and the dense factor) of the previous solve at the same state and damping
       if (pb->join_pending) CU(cudaStreamWaitEvent(pb->stream, pb->join, 0));
     } else {
+      FormRec frec;
+      frec.rec = pb->orec;
+      frec.pair_pt = pb->pair_pt;
+      frec.camw = pb->camw[s];
+      frec.centre = pb->mp.cam_model == BA_CAMERA_CENTRE;
       LAUNCH(3, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
                                  (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
                                  Cf, (T*)pb->Yhat, pb->sparse ? (T*)pb->Bs : (T*)pb->Shat, pb->form_lanes,
                                  pb->num_sms, pb->evf[0], pb->evf[1], pb->join_pending ? pb->join : nullptr,
-                                 pb->stream, pb->cam_map, pb->sparse, pb->cform.n_blocks ? &pb->cform : nullptr));
+                                 pb->stream, pb->cam_map, pb->sparse, pb->cform.n_blocks ? &pb->cform : nullptr,
+                                 pb->orec ? &frec : nullptr));
       pb->evf_valid = true;
     }
     pb->join_pending = false;  // the main stream waits for the chain
@@ -1339,6 +1348,15 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     // per camera its blocks would hold few live lanes, each walking its run's pairs
     // one dependent gather at a time; the warp-per-run kernel is faster there
     // (0.23 against 0.50 ms on the 200-camera bench workload).
+    // FP32 with fewer, longer runs (the warp-per-run kernel): the blocks are formed
+    // from observation records (k_form_S_rec) unless BA_FORM_RECORDS=0 keeps the Y^ rows
+    const char* frv = std::getenv("BA_FORM_RECORDS");
+    if (!pb->fp64 && !pb->form_lanes && cv.n_runs > 0 && !(frv && frv[0] == '0')) {
+      ST(dalloc(pb, &pb->orec, (size_t)12 * std::max(N, 1)));
+      CU(cudaMemset(pb->orec, 0, sizeof(float) * 12 * (size_t)std::max(N, 1)));
+      ST(dalloc(pb, &pb->pair_pt, std::max<size_t>(cv.npairs, 1)));
+      LAUNCH(1, launch_pair_pt(cv.npairs, cv.pairs, dl.po_pt, pb->pair_pt, pb->stream));
+    }
     if (!pb->fp64 && pb->form_lanes) {
       // runs grouped by owner camera, blocks of up to 128 runs
       int* po_co = nullptr;
@@ -1408,7 +1426,7 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
   if (pb->explicit_S && n_max > 0) {
     if (!pb->sparse)
       ST(dalloc_bytes(pb, &pb->Shat, R * (size_t)n_max * (pb->fp64 ? spcg_row_stride<double>(n_max) : spcg_row_stride<float>(n_max))));
-    ST(dalloc_bytes(pb, &pb->Yhat, R * (size_t)kWStride * ((size_t)N + 1)));
+    if (!pb->orec) ST(dalloc_bytes(pb, &pb->Yhat, R * (size_t)kWStride * ((size_t)N + 1)));
     ST(dalloc_bytes(pb, &pb->bs_wx, R * 3 * std::max<size_t>(N, 1)));  // W_k^T dc per observation
     ST(dalloc(pb, &pb->dscale, (size_t)2 * n_max));  // D, then 1/D in the working precision
     ST(dalloc_bytes(pb, &pb->Dblk, R * 45 * (size_t)C));
@@ -2051,7 +2069,7 @@ int64_t ba_kernel_launches(const ba_problem* pb) { return pb ? pb->launches : 0;
 
 int ba_formation_kernel(const ba_problem* pb) {
   if (!pb || !pb->explicit_S || pb->n_covis_runs == 0) return 0;
-  return pb->cform.n_blocks ? 3 : pb->form_lanes ? 2 : 1;
+  return pb->cform.n_blocks ? 3 : pb->form_lanes ? 2 : pb->orec ? 4 : 1;
 }
 
 ba_status ba_debug_bounds(int reset, int64_t* site, int64_t* index) {

@@ -212,7 +212,8 @@ int rank_blocks(int n);
 
 template <typename T>
 cudaError_t launch_pt_lin(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
-                          const uint8_t* obs_act, T* W, T* wsgn, T* V, T* gp, cudaStream_t s);
+                          const uint8_t* obs_act, T* W, T* wsgn, T* V, T* gp, cudaStream_t s,
+                          float* orec = nullptr);  // FP32 explicit systems: observation records [N][12]
 template <typename T>
 cudaError_t launch_cam_accum(const Layout& L, const ModelParams& mp, int mode, const T* camw,
                              const T* ptsw, const uint8_t* act_co, const uint8_t* cam_act,
@@ -244,6 +245,16 @@ __host__ __device__ constexpr bool run_owner_first(int i, int j) { return ((i + 
 cudaError_t launch_owner_pairs(int N, const int* co_po, int* po_co, int n_runs, const int4* runs, int2* pairs,
                                cudaStream_t s);
 
+// FP32 warp-per-run formation from observation records (k_form_S_rec): the
+// records written by the point-side linearisation, the point of every pair, the
+// working camera records
+struct FormRec {
+  const float* rec = nullptr;      // [N][12]
+  const int* pair_pt = nullptr;    // [npairs]
+  const void* camw = nullptr;      // working cameras [C][kCamStride] (FP32)
+  bool centre = false;             // the camera model of Sec. 3.2 (centre, rotation, focal)
+};
+cudaError_t launch_pair_pt(size_t npairs, const int2* pairs, const int* po_pt, int* pair_pt, cudaStream_t s);
 template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
@@ -252,7 +263,8 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
                                                               // diagonal blocks are written
                           const int* cam_map = nullptr,       // sparse: Shat is the block storage
                           bool sparse = false,
-                          const CamForm* cf = nullptr);       // FP32: camera-owned formation
+                          const CamForm* cf = nullptr,        // FP32: camera-owned formation
+                          const FormRec* fr = nullptr);       // FP32: formation from observation records
 template <typename T>
 cudaError_t launch_dscale(int Cf, const int* cam_map, const T* Ug, double lambda, double* dscale, cudaStream_t s, int kfix = 0);
 template <typename T>

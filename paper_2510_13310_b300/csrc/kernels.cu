@@ -676,12 +676,14 @@ __device__ __forceinline__ void load_pt(const T* __restrict__ ptsw, int p, T& x,
 // W: stored W rows (nullptr when the matvec recomputes the Jacobian); wsgn: per
 // observation IRLS weight rho', negated when the observation has no depth prior
 // (0 for inactive observations), in the padded per-tile layout (nullptr if unused).
+// orec (nullable, FP32): the observation's record [12] for the explicit system's
+// formation (D00 D01 D02 D11 D12 D22 a0 a1 a2 xn yn w; zeros when inactive)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, const T* __restrict__ camw,
                                                    const T* __restrict__ ptsw,
                                                    const uint8_t* __restrict__ obs_act, T* __restrict__ W,
                                                    T* __restrict__ wsgn, T* __restrict__ V,
-                                                   T* __restrict__ gp) {
+                                                   T* __restrict__ gp, float* __restrict__ orec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ws = reinterpret_cast<T*>(smem_raw);  // [kTileObs][kWStride]
   T* Vs = Ws + kTileObs * kWStride;        // [kTileObs][9]
@@ -700,6 +702,10 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
 #pragma unroll
       for (int j = 0; j < 9; ++j) vrow[j] = T(0);
       if (wsgn) wsgn[(size_t)d.g_row + i] = T(0);
+      if (orec) {
+        float4* r4 = reinterpret_cast<float4*>(orec) + 3 * (size_t)k;
+        r4[0] = r4[1] = r4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       continue;
     }
     T cw[kCamStride];
@@ -713,6 +719,12 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
                      (T)mp.cy, (T)mp.huber, o);
     T w = o.wrob;
     if (wsgn) wsgn[(size_t)d.g_row + i] = tau > T(0) ? w : -w;
+    if (orec) {
+      float4* r4 = reinterpret_cast<float4*>(orec) + 3 * (size_t)k;
+      r4[0] = make_float4((float)o.D00, (float)o.D01, (float)o.D02, (float)o.D11);
+      r4[1] = make_float4((float)o.D12, (float)o.D22, (float)o.a0, (float)o.a1);
+      r4[2] = make_float4((float)o.a2, (float)o.xn, (float)o.yn, (float)w);
+    }
     if (W) {
       // the row in registers, then stored as 16-byte words (the 28-word row
       // stride puts the 8 lanes of a quarter-warp on distinct bank groups)
@@ -764,7 +776,7 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
 
 template <typename T>
 cudaError_t launch_pt_lin(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
-                          const uint8_t* obs_act, T* W, T* wsgn, T* V, T* gp, cudaStream_t s) {
+                          const uint8_t* obs_act, T* W, T* wsgn, T* V, T* gp, cudaStream_t s, float* orec) {
   if (L.n_tiles == 0) return cudaSuccess;
   size_t smem = sizeof(T) * kTileObs * (kWStride + 9);
   static bool attr = false;
@@ -772,7 +784,7 @@ cudaError_t launch_pt_lin(const Layout& L, const ModelParams& mp, const T* camw,
     cudaFuncSetAttribute(k_pt_lin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_pt_lin<T><<<L.n_tiles, kBlock, smem, s>>>(L, mp, camw, ptsw, obs_act, W, wsgn, V, gp);
+  k_pt_lin<T><<<L.n_tiles, kBlock, smem, s>>>(L, mp, camw, ptsw, obs_act, W, wsgn, V, gp, orec);
   return cudaGetLastError();
 }
 
@@ -1345,7 +1357,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
                                             const int*, const int*, int*, double*, double*, T*, T*,    \
                                             int*, T*, T*, cudaStream_t);                               \
   template cudaError_t launch_pt_lin<T>(const Layout&, const ModelParams&, const T*, const T*,      \
-                                        const uint8_t*, T*, T*, T*, T*, cudaStream_t);              \
+                                        const uint8_t*, T*, T*, T*, T*, cudaStream_t, float*);      \
   template cudaError_t launch_cam_accum<T>(const Layout&, const ModelParams&, int, const T*,        \
                                            const T*, const uint8_t*, const uint8_t*, const int*,    \
                                            const T*, const T*, T*, cudaStream_t);                   \

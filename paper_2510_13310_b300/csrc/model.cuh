@@ -24,6 +24,10 @@ struct ObsLin {
   T Jc[3][9];
   T Jp[3][3];
   T wrob;   // IRLS weight rho'(|r|^2) of the Huber loss
+  // what both blocks are built from (the observation record of the explicit
+  // system's formation): D = d r / d P (D10 = D01, D20 = D21 = 0), the point a the
+  // rotation increment acts on, the normalised image point
+  T D00, D01, D02, D11, D12, D22, a0, a1, a2, xn, yn;
 };
 
 // Huber weight on the squared norm s: 1 inside, delta / sqrt(s) outside.
@@ -113,6 +117,8 @@ __device__ __forceinline__ void linearize_obs(const T* __restrict__ cw, T X0, T 
 
   // model 1: the rotation increment acts on R (X - c) = P
   if (cw[15] != T(0)) a0 = px, a1 = py, a2 = pz;
+  o.D00 = D00, o.D01 = D01, o.D02 = D02, o.D11 = D11, o.D12 = D12, o.D22 = D22;
+  o.a0 = a0, o.a1 = a1, o.a2 = a2, o.xn = xn, o.yn = yn;
   // rotation columns: D * (-[a]x) with -[a]x = [[0,a2,-a1],[-a2,0,a0],[a1,-a0,0]]
   o.Jc[0][0] = -D01 * a2 + D02 * a1;
   o.Jc[0][1] = D00 * a2 - D02 * a0;

@@ -224,6 +224,176 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same blocks from observation records (FP32, warp per run).  The pair term
+// W_k V*_p^-1 W_k2^T with W = w Jc^T Jp and Jp = D R is
+//   Jc_k^T K Jc_k2,   K = w w2 (D R_i) V*_p^-1 (D2 R_j)^T   (3 x 3),
+// so a pair needs the two observations' records (D, the point the rotation
+// increment acts on, the normalised image point, the IRLS weight: 48 B each,
+// written by the point-side linearisation and independent of the damping), the
+// point's V*^-1 (24 B) and the two cameras' constants (R, f, k1, k2), against two
+// 112-byte rows of Y^ = D^-1 W M_p before, and no Y^ pass.  The Jacobi scaling
+// is applied to the summed block.  Each lane sums its pairs in order and the
+// lanes are reduced in a fixed butterfly (deterministic).
+// ---------------------------------------------------------------------------
+struct ObsRec {
+  float d00, d01, d02, d11, d12, d22, a0, a1, a2, xn, yn, w;
+};
+__device__ __forceinline__ ObsRec load_rec(const float4* __restrict__ R4, int k) {
+  const float4 u = R4[3 * (size_t)k], v = R4[3 * (size_t)k + 1], t = R4[3 * (size_t)k + 2];
+  return ObsRec{u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, t.x, t.y, t.z, t.w};
+}
+// column c of the 3 x 9 camera Jacobian (rows u, v, depth; model.cuh) from the
+// record, the camera constants cam = (R[9], f, k1, k2) and A = D R (the centre
+// model's centre columns are -A and it has no k1, k2 columns)
+__device__ __forceinline__ void rec_jc_col(const ObsRec& r, const float* cam, const float (&A)[3][3], bool centre,
+                                           int c, float& j0, float& j1, float& j2) {
+  const float f = cam[9], k1 = cam[10], k2 = cam[11];
+  const float rr = r.xn * r.xn + r.yn * r.yn;
+  switch (c) {
+    case 0: j0 = -r.d01 * r.a2 + r.d02 * r.a1; j1 = -r.d11 * r.a2 + r.d12 * r.a1; j2 = r.d22 * r.a1; break;
+    case 1: j0 = r.d00 * r.a2 - r.d02 * r.a0; j1 = r.d01 * r.a2 - r.d12 * r.a0; j2 = -r.d22 * r.a0; break;
+    case 2: j0 = -r.d00 * r.a1 + r.d01 * r.a0; j1 = -r.d01 * r.a1 + r.d11 * r.a0; j2 = 0.f; break;
+    case 3: j0 = centre ? -A[0][0] : r.d00; j1 = centre ? -A[1][0] : r.d01; j2 = centre ? -A[2][0] : 0.f; break;
+    case 4: j0 = centre ? -A[0][1] : r.d01; j1 = centre ? -A[1][1] : r.d11; j2 = centre ? -A[2][1] : 0.f; break;
+    case 5: j0 = centre ? -A[0][2] : r.d02; j1 = centre ? -A[1][2] : r.d12; j2 = centre ? -A[2][2] : r.d22; break;
+    case 6: {
+      const float dist = 1.f + rr * (k1 + k2 * rr);
+      j0 = dist * r.xn; j1 = dist * r.yn; j2 = 0.f;
+    } break;
+    case 7: j0 = centre ? 0.f : f * r.xn * rr; j1 = centre ? 0.f : f * r.yn * rr; j2 = 0.f; break;
+    default: j0 = centre ? 0.f : f * r.xn * rr * rr; j1 = centre ? 0.f : f * r.yn * rr * rr; j2 = 0.f; break;
+  }
+}
+// A = D R for a record (D10 = D01, D20 = D21 = 0)
+__device__ __forceinline__ void rec_dr(const ObsRec& r, const float* R, float (&A)[3][3]) {
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    A[0][t] = r.d00 * R[t] + r.d01 * R[3 + t] + r.d02 * R[6 + t];
+    A[1][t] = r.d01 * R[t] + r.d11 * R[3 + t] + r.d12 * R[6 + t];
+    A[2][t] = r.d22 * R[6 + t];
+  }
+}
+
+template <bool kSparse, bool kCentre>
+__global__ void __launch_bounds__(128, 3)
+    k_form_S_rec(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
+                 const int* __restrict__ pair_pt, const float* __restrict__ orec, const float* __restrict__ Vinv,
+                 const float* __restrict__ camw, const double* __restrict__ dscale, const int* __restrict__ crank,
+                 int Cf, float* __restrict__ Shat, int C, int N, int P) {
+  __shared__ float cam_s[4][24];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int ld = spcg_row_stride<float>(9 * Cf);
+  const float4* R4 = reinterpret_cast<const float4*>(orec);
+  const float2* V2 = reinterpret_cast<const float2*>(Vinv);
+  const float* dinv = reinterpret_cast<const float*>(dscale + 9 * (size_t)Cf);
+  for (int ri = gw; ri < n_runs; ri += nw) {
+    const int4 rn = runs[ri];  // (camera i, camera j, first pair, pair count)
+    const int ci_ = bidx(rn.x, C, 39), cj_ = bidx(rn.y, C, 39);
+    const int a = crank[ci_], b = crank[cj_];
+    if (a < 0 || b < 0) continue;
+    // the two cameras' R, f, k1, k2 (working records: R t f k1 k2 model)
+    __syncwarp();
+    if (lane < 9) cam_s[wib][lane] = camw[kCamStride * (size_t)ci_ + lane];
+    else if (lane < 12) cam_s[wib][lane] = camw[kCamStride * (size_t)ci_ + lane + 3];
+    else if (lane < 21) cam_s[wib][lane] = camw[kCamStride * (size_t)cj_ + lane - 12];
+    else if (lane < 24) cam_s[wib][lane] = camw[kCamStride * (size_t)cj_ + lane - 9];
+    constexpr bool centre = kCentre;  // the camera model (flag of the working records)
+    __syncwarp();
+    const float* ci = cam_s[wib];
+    const float* cj = cam_s[wib] + 12;
+    float acc[81];
+#pragma unroll
+    for (int q = 0; q < 81; ++q) acc[q] = 0.f;
+    const int qe = rn.z + rn.w;
+    int q = rn.z + lane;
+    int2 nxt = q < qe ? pairs[q] : make_int2(0, 0);
+    int npt = q < qe ? pair_pt[q] : 0;
+    for (; q < qe; q += 32) {
+      const int2 pr = nxt;
+      const int p = bidx(npt, P, 40);
+      if (q + 32 < qe) nxt = pairs[q + 32], npt = pair_pt[q + 32];  // next pair's indices in flight
+      const ObsRec r1 = load_rec(R4, bidx(pr.x, N, 41)), r2 = load_rec(R4, bidx(pr.y, N, 41));
+      const float2 v0 = V2[3 * (size_t)p], v1 = V2[3 * (size_t)p + 1], v2 = V2[3 * (size_t)p + 2];
+      const float v00 = v0.x, v01 = v0.y, v02 = v1.x, v11 = v1.y, v12 = v2.x, v22 = v2.y;
+      float A2[3][3], A1[3][3];
+      rec_dr(r2, cj, A2);
+      rec_dr(r1, ci, A1);
+      // B = V*^-1 A2^T, K = w w2 A1 B
+      float B[3][3];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        B[0][t] = v00 * A2[t][0] + v01 * A2[t][1] + v02 * A2[t][2];
+        B[1][t] = v01 * A2[t][0] + v11 * A2[t][1] + v12 * A2[t][2];
+        B[2][t] = v02 * A2[t][0] + v12 * A2[t][1] + v22 * A2[t][2];
+      }
+      const float ww = r1.w * r2.w;
+      float K[3][3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) K[r][t] = ww * (A1[r][0] * B[0][t] + A1[r][1] * B[1][t] + A1[r][2] * B[2][t]);
+      // T = K Jc2 (3 x 9), then acc += Jc1^T T; a Jacobian's depth row is zero
+      // outside the rotation, centre/translation columns
+      float T[3][9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        float j0, j1, j2;
+        rec_jc_col(r2, cj, A2, centre, c, j0, j1, j2);
+        const bool dz = c < 2 || (c >= 3 && c <= 5);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) T[r][c] = dz ? K[r][0] * j0 + K[r][1] * j1 + K[r][2] * j2 : K[r][0] * j0 + K[r][1] * j1;
+      }
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        float j0, j1, j2;
+        rec_jc_col(r1, ci, A1, centre, c, j0, j1, j2);
+        const bool dz = c < 2 || (c >= 3 && c <= 5);
+#pragma unroll
+        for (int s2 = 0; s2 < 9; ++s2)
+          acc[9 * c + s2] += dz ? j0 * T[0][s2] + j1 * T[1][s2] + j2 * T[2][s2] : j0 * T[0][s2] + j1 * T[1][s2];
+      }
+    }
+    // warp reduce-scatter of the 81 sums (padded to 96), then the Jacobi scaling
+    float v[96];
+#pragma unroll
+    for (int t = 0; t < 96; ++t) v[t] = t < 81 ? acc[t] : 0.f;
+    rs_round<float, 96>(v, lane, 0);
+    rs_round<float, 48>(v, lane, 1);
+    rs_round<float, 24>(v, lane, 2);
+    rs_round<float, 12>(v, lane, 3);
+    rs_round<float, 6>(v, lane, 4);
+    const int base = 48 * (lane & 1) + 24 * ((lane >> 1) & 1) + 12 * ((lane >> 2) & 1) + 6 * ((lane >> 3) & 1) +
+                     3 * ((lane >> 4) & 1);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int t = base + j;
+      if (t < 81) {
+        const int r = t / 9, s2 = t - 9 * r;
+        const float val = -(v[j] * dinv[9 * a + r]) * dinv[9 * b + s2];
+        if constexpr (kSparse) {
+          Shat[(size_t)kBlkStride * (2 * (size_t)ri) + 9 * r + s2] = val;
+          Shat[(size_t)kBlkStride * (2 * (size_t)ri + 1) + 9 * s2 + r] = val;
+        } else {
+          Shat[(size_t)(9 * a + r) * ld + 9 * b + s2] = val;
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_pair_pt(size_t npairs, const int2* __restrict__ pairs, const int* __restrict__ po_pt,
+                          int* __restrict__ pair_pt) {
+  const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (q < npairs) pair_pt[q] = po_pt[pairs[q].x];
+}
+
+cudaError_t launch_pair_pt(size_t npairs, const int2* pairs, const int* po_pt, int* pair_pt, cudaStream_t s) {
+  if (npairs) k_pair_pt<<<(unsigned)((npairs + 255) / 256), 256, 0, s>>>(npairs, pairs, po_pt, pair_pt);
+  return cudaGetLastError();
+}
+
 // The same blocks with one lane per run, for scenes with very many short runs
 // (every camera pair sharing a few dozen points): each lane accumulates its run
 // in registers and writes the 81 entries itself, so no cross-lane reduction is
@@ -463,12 +633,14 @@ template <typename T>
 cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const int2* pairs, const T* W,
                           const T* Vinv, const int* crank, const T* Ud, const T* Dblk, double* dscale,
                           int Cf, T* Y, T* Shat, bool lanes, int num_sms, cudaEvent_t ev0, cudaEvent_t ev1,
-                          cudaEvent_t join, cudaStream_t s, const int* cam_map, bool sparse, const CamForm* cf) {
-  if (sizeof(T) != 4) cf = nullptr;  // FP64 keeps point-order rows and the pair kernels
+                          cudaEvent_t join, cudaStream_t s, const int* cam_map, bool sparse, const CamForm* cf,
+                          const FormRec* fr) {
+  if (sizeof(T) != 4) cf = nullptr, fr = nullptr;  // FP64 keeps point-order rows and the pair kernels
+  if (cf || lanes) fr = nullptr;  // records serve the warp-per-run kernel
   if (Cf <= 0) return cudaSuccess;
   const int n = 9 * Cf;
   // dscale (D and 1/D) was written by the Schur-diagonal kernel
-  if (L.N > 0)
+  if (L.N > 0 && !fr)
     k_form_Y<T><<<(L.N + kYRows - 1) / kYRows, kYRows, 0, s>>>(L.N, L.C, L.P, L.po_cam, L.po_pt, W, Vinv, crank,
                                                                dscale, Cf, Y, cf ? cf->po_co : nullptr);
   cudaError_t e = cudaSuccess;
@@ -502,8 +674,20 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
       int grid = (n_runs + wpb - 1) / wpb;
       const int resident = (sizeof(T) == 4 ? 3 : 1) * num_sms;
       if (grid > resident) grid = resident;
-      if (sparse) k_form_S_runs<T, true><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat, L.C, L.N);
-      else k_form_S_runs<T, false><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat, L.C, L.N);
+      if constexpr (sizeof(T) == 4) {
+        if (fr) {
+          const float* Vf = reinterpret_cast<const float*>(Vinv);
+          const float* Cw = reinterpret_cast<const float*>(fr->camw);
+          auto* kern = sparse ? (fr->centre ? k_form_S_rec<true, true> : k_form_S_rec<true, false>)
+                              : (fr->centre ? k_form_S_rec<false, true> : k_form_S_rec<false, false>);
+          kern<<<grid, 128, 0, s>>>(n_runs, runs, pairs, fr->pair_pt, fr->rec, Vf, Cw, dscale, crank, Cf,
+                                    (float*)Shat, L.C, L.N, L.P);
+        }
+      }
+      if (!fr) {
+        if (sparse) k_form_S_runs<T, true><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat, L.C, L.N);
+        else k_form_S_runs<T, false><<<grid, 128, 0, s>>>(n_runs, runs, pairs, Y, crank, Cf, Shat, L.C, L.N);
+      }
     }
   }
   if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
@@ -1502,7 +1686,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
   template cudaError_t launch_form_S<T>(const Layout&, int, const int4*, const int2*, const T*,        \
                                         const T*, const int*, const T*, const T*, double*, int, T*, T*, \
                                         bool, int, cudaEvent_t, cudaEvent_t, cudaEvent_t, cudaStream_t, \
-                                        const int*, bool, const CamForm*);                              \
+                                        const int*, bool, const CamForm*, const FormRec*);              \
   template cudaError_t launch_dscale<T>(int, const int*, const T*, double, double*, cudaStream_t, int);  \
   template size_t spcg_smem_bytes<T>(int, int, int, int, int);                                         \
   template __host__ __device__ size_t spcg_vec_elems<T>(int, int);                                     \

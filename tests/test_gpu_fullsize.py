@@ -147,6 +147,24 @@ def test_large_workload_configured_schedule():
     gpu.close()
 
 
+def similarity_aligned_errors(p, p_gt):
+    """Point errors after the least-squares similarity s R p + t that maps p onto
+    p_gt (Umeyama 1991): the error left once the gauge (rotation, translation,
+    scale) is taken out, which the depth priors fix only weakly.  The similarity is
+    fitted on the points whose raw error is within three times the median (points
+    that never rejoin the active set keep gross errors) and applied to all."""
+    raw = np.linalg.norm(p - p_gt, axis=1)
+    fit = raw <= 3.0 * np.median(raw)
+    mu, mu_gt = p[fit].mean(0), p_gt[fit].mean(0)
+    a, b = p[fit] - mu, p_gt[fit] - mu_gt
+    U, S, Vt = np.linalg.svd(b.T @ a / len(a))
+    d = np.ones(3)
+    d[2] = np.sign(np.linalg.det(U @ Vt))
+    R = U @ np.diag(d) @ Vt
+    s = (S * d).sum() / (a * a).sum(1).mean()
+    return np.linalg.norm(s * (p - mu) @ R.T + mu_gt - p_gt, axis=1)
+
+
 def test_extraction_ablation_on_injected_frustum_exits():
     """The ablation idea of Sec. 4.2 (per-iteration extraction against one-shot
     pruning) re-run on the 1M-observation geometry with injected frustum exits
@@ -154,8 +172,13 @@ def test_extraction_ablation_on_injected_frustum_exits():
     30 FP32 LM iterations in each mode from the same start.  One-shot keeps the
     first active set; dynamic extraction re-admits the observations as the points
     come back into view and ends with more active observations (996,846 against
-    908,556) and a slightly smaller error on the lifted points (1.56e-2 against
-    1.58e-2, measured; the runs are deterministic).  The table is printed."""
+    908,556).  Point errors are compared after a similarity alignment to the
+    ground truth: the raw errors are dominated by drift along the weakly fixed
+    gauge, which moves with the rounding of the solves (two formation kernels
+    summing in different orders end 30% apart raw and within 0.1% aligned).
+    Aligned, dynamic extraction ends with a lower median error on the lifted
+    points (measured 2.62e-3 against 3.50e-3) and a slightly higher one over all
+    points (2.55e-3 against 2.24e-3).  The table is printed."""
     sc = scenes.make_scene("medium", frustum_exit_frac=0.3)
     lifted = np.flatnonzero(np.abs(sc.pts0[:, 2] - sc.pts_gt[:, 2]) > 0.5)
     res = {}
@@ -165,16 +188,19 @@ def test_extraction_ablation_on_injected_frustum_exits():
         c, p = gpu.get_params()
         gpu.close()
         err = np.linalg.norm(p - sc.pts_gt, axis=1)
+        al = similarity_aligned_errors(p, sc.pts_gt)
         res[name] = dict(act0=log[0]["n_obs_act"], act=log[-1]["n_obs_act"], rmse=log[-1]["rmse_px"],
                          rot=pose_diff(c, sc.cams_gt)["rot_deg"], lifted=np.median(err[lifted]),
-                         allp=np.median(err))
+                         allp=np.median(err), lifted_al=np.median(al[lifted]), allp_al=np.median(al))
     print(f"{len(lifted)} lifted points of {sc.spec.n_pts}")
     print("mode | active obs (first, last) | final RMSE px | max rotation error deg | "
-          "median point error: lifted, all")
+          "median point error: lifted, all | after similarity alignment: lifted, all")
     for k, r in res.items():
         print(f"{k} | {r['act0']}, {r['act']} | {r['rmse']:.3f} | {r['rot']:.4f} | {r['lifted']:.3e}, "
-              f"{r['allp']:.3e}")
+              f"{r['allp']:.3e} | {r['lifted_al']:.3e}, {r['allp_al']:.3e}")
     once, dyn = res["one-shot"], res["dynamic"]
     assert once["act"] == once["act0"] == dyn["act0"]
     assert dyn["act"] > once["act"]
-    assert dyn["lifted"] < once["lifted"]
+    for r in res.values():
+        assert np.isfinite(r["rmse"]) and r["allp_al"] < 1e-2
+    assert dyn["lifted_al"] < 0.9 * once["lifted_al"]

@@ -526,6 +526,38 @@ def test_explicit_solver_with_many_short_runs_matches_oracle():
     check_step(g, o, *STEP_TOL[ba.BA_FP32])
 
 
+@pytest.mark.parametrize("solver", [ba.BA_SOLVER_EXPLICIT, ba.BA_SOLVER_SPARSE])
+@pytest.mark.parametrize("model", [ba.BA_CAMERA_RADIAL, ba.BA_CAMERA_CENTRE])
+def test_formation_from_records_and_from_rows_match_oracle(monkeypatch, solver, model):
+    """FP32 explicit systems with a few hundred pairs per camera pair: the blocks
+    formed from the observation records (k_form_S_rec: D, the rotated point, the
+    normalised point, the weight; V*^-1 per point) and from the Y^ rows
+    (k_form_S_runs, selected by BA_FORM_RECORDS=0) both give the oracle's damped
+    step, under both camera models and both storages, and each is deterministic."""
+    sc = geometric(30, 8000, 3, 14, 8.0, seed=91, camera_model="centre" if model == ba.BA_CAMERA_CENTRE else "radial")
+    lam = 1e-3
+    steps = {}
+    for env in ("1", "0"):
+        monkeypatch.setenv("BA_FORM_RECORDS", env)
+        gpu, orc = pair(sc, ba.BA_FP32, solver=solver, camera_model=model)
+        steps[gpu.formation_kernel] = gpu.solve_damped(lam)
+        again = ba.Problem.from_scene(sc, ba.Options(precision=ba.BA_FP32, solver=solver, camera_model=model))
+        g2 = again.solve_damped(lam)
+        assert np.array_equal(g2["dc"], steps[gpu.formation_kernel]["dc"])
+        gpu.close(); again.close()
+    assert set(steps) == {"k_form_S_rec", "k_form_S_runs"}
+    o = _oracle_step_model(sc, orc, lam)
+    for g in steps.values():
+        check_step(g, o, *STEP_TOL[ba.BA_FP32])
+
+
+def _oracle_step_model(sc, orc, lam):
+    geom, _ = orc.predicate(sc.cams0, sc.pts0)
+    ext = orc.extract(geom)
+    ne = orc.normal_equations(sc.cams0, sc.pts0, ext["obs_mask"])
+    return orc.solve_step(ne, ext, lam)
+
+
 # ---------------------------------------------------------------------------
 # checkpoint / resume
 # ---------------------------------------------------------------------------
