@@ -479,7 +479,7 @@ ba_status linearize_t(ba_problem* pb) {
   if (pb->side) CU(cudaEventRecord(pb->fork, pb->stream));
   // W rows are stored when the matvec streams them or the explicit system is formed
   LAUNCH(1, launch_pt_lin<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
-                             (pb->recompute && !pb->explicit_S) ? nullptr : (T*)pb->W,
+                             (pb->recompute && (!pb->explicit_S || pb->orec)) ? nullptr : (T*)pb->W,
                              pb->recompute ? (T*)pb->wsgn : nullptr, (T*)pb->V, (T*)pb->gp, pb->stream,
                              pb->orec));
   // the camera side reads neither W nor V: it runs on the side stream alongside
@@ -657,9 +657,10 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
   }
   LAUNCH(2, launch_backsub_pts<T>(pb->L, pb->mp, (const T*)pb->camw[s], (const T*)pb->ptsw[s], pb->obs_act,
                                   pb->pt_act, pb->crank, (const T*)pb->x, (const T*)pb->Vinv, (const T*)pb->V,
-                                  (const T*)pb->gp, (const T*)pb->W, lambda, (T*)pb->dp, (T*)pb->bs_wx, Cf,
+                                  (const T*)pb->gp, pb->orec ? nullptr : (const T*)pb->W, lambda, (T*)pb->dp,
+                                  (T*)pb->bs_wx, Cf,
                                   pb->cam_map, (const T*)pb->Ug, (const T*)pb->dampc, pb->pred_parts, pb->sc,
-                                  pb->bs_grid, pb->stream));
+                                  pb->bs_grid, pb->stream, pb->orec));
   return BA_OK;
 }
 
@@ -1588,7 +1589,7 @@ ba_status copy_out_linearization(ba_problem* pb, double* U, double* V, double* W
   if (W && N) {
     // in recompute mode the W blocks are never stored: form them into a scratch
     // buffer with the same linearization kernel (inspection only)
-    T* wsrc = (T*)pb->W;
+    T* wsrc = pb->orec ? nullptr : (T*)pb->W;  // W rows are not stored when records are
     T* wtmp = nullptr;
     T* scratch_v = nullptr;
     cudaError_t e = cudaSuccess;

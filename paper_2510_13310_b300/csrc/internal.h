@@ -298,7 +298,8 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
                                const uint8_t* act_po, const uint8_t* pt_act, const int* crank, const T* x,
                                const T* Vinv, const T* V, const T* gp, const T* Wst, double lambda, T* dp,
                                T* wx, int Cf, const int* cam_map, const T* Ug, const T* dampc, double* pred_parts,
-                               Scalars* sc, int grid, cudaStream_t s);  // also sc->pred (points and cameras)
+                               Scalars* sc, int grid, cudaStream_t s,  // also sc->pred (points and cameras)
+                               const float* orec = nullptr);  // FP32: W^T x from the observation records
 template <typename T>
 cudaError_t launch_pcg(const PcgArgs<T>& a, int grid, size_t smem, cudaStream_t s);
 template <typename T>

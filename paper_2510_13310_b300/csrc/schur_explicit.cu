@@ -676,6 +676,10 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
       if (grid > resident) grid = resident;
       if constexpr (sizeof(T) == 4) {
         if (fr) {
+          // one block per four runs (no resident-only grid): blocks retire as they
+          // finish, so the side stream's Schur-diagonal chain, which the diagonal
+          // blocks wait for, is scheduled alongside instead of after the formation
+          grid = (n_runs + wpb - 1) / wpb;
           const float* Vf = reinterpret_cast<const float*>(Vinv);
           const float* Cw = reinterpret_cast<const float*>(fr->camw);
           auto* kern = sparse ? (fr->centre ? k_form_S_rec<true, true> : k_form_S_rec<true, false>)
@@ -1579,16 +1583,46 @@ int spcg_words_per_value(bool fp64) { return kSpcgReplicas * (fp64 ? spcg_words<
 // recomputed; coalesced over point order), then one thread per point sums its
 // observations' terms in point order.
 // ---------------------------------------------------------------------------
+// orec (FP32, nullable): W_k^T x = w Jp^T (Jc x) from the observation record
+// (Jp = D R; the same record the explicit system was formed from), no W row
 template <typename T>
 __global__ void k_backsub_obs(Layout L, ModelParams mp, const T* __restrict__ camw, const T* __restrict__ ptsw,
                               const uint8_t* __restrict__ act_po, const int* __restrict__ crank,
-                              const T* __restrict__ x, const T* __restrict__ Wst, T* __restrict__ wx) {
+                              const T* __restrict__ x, const T* __restrict__ Wst, T* __restrict__ wx,
+                              const float* __restrict__ orec) {
   const T* po_uv = reinterpret_cast<const T*>(L.po_uvw);
   const T* po_tau = reinterpret_cast<const T*>(L.po_tauw);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += gridDim.x * blockDim.x) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
     const int cr = act_po[k] ? crank[bidx(L.po_cam[k], L.C, 16)] : -1;
-    if (cr >= 0) {
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (cr >= 0 && orec) {
+        const ObsRec r = load_rec(reinterpret_cast<const float4*>(orec), k);
+        const float* cwp = reinterpret_cast<const float*>(camw) + kCamStride * (size_t)bidx(L.po_cam[k], L.C, 16);
+        float cam[12];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) cam[q] = cwp[q];
+        cam[9] = cwp[12], cam[10] = cwp[13], cam[11] = cwp[14];
+        const bool centre = cwp[15] != 0.f;
+        float A[3][3];
+        rec_dr(r, cam, A);
+        const float* xv = reinterpret_cast<const float*>(x) + 9 * (size_t)cr;
+        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          float j0, j1, j2;
+          rec_jc_col(r, cam, A, centre, c, j0, j1, j2);
+          const float xc = xv[c];
+          u0 += j0 * xc, u1 += j1 * xc, u2 += j2 * xc;
+        }
+        s0 = r.w * (A[0][0] * u0 + A[1][0] * u1 + A[2][0] * u2);
+        s1 = r.w * (A[0][1] * u0 + A[1][1] * u1 + A[2][1] * u2);
+        s2 = r.w * (A[0][2] * u0 + A[1][2] * u1 + A[2][2] * u2);
+        done = true;
+      }
+    }
+    if (cr >= 0 && !done) {
       T W[27];
       if (Wst) {
         load_row27<T>(Wst + kWStride * (size_t)k, W);
@@ -1672,10 +1706,11 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
                                const uint8_t* act_po, const uint8_t* pt_act, const int* crank, const T* x,
                                const T* Vinv, const T* V, const T* gp, const T* Wst, double lambda, T* dp,
                                T* wx, int Cf, const int* cam_map, const T* Ug, const T* dampc, double* pred_parts,
-                               Scalars* sc, int grid, cudaStream_t s) {
+                               Scalars* sc, int grid, cudaStream_t s, const float* orec) {
   if (L.N > 0) {
     const int g = (int)std::min<long long>(((long long)L.N + 255) / 256, 65535);
-    k_backsub_obs<T><<<g, 256, 0, s>>>(L, mp, camw, ptsw, act_po, crank, x, Wst, wx);
+    k_backsub_obs<T><<<g, 256, 0, s>>>(L, mp, camw, ptsw, act_po, crank, x, Wst, wx,
+                                       sizeof(T) == 4 ? orec : nullptr);
   }
   k_backsub_pts<T><<<grid, 256, 0, s>>>(L, pt_act, wx, Vinv, V, gp, lambda, dp, Cf, cam_map, x, Ug, dampc,
                                         pred_parts, sc);
@@ -1700,7 +1735,7 @@ cudaError_t launch_backsub_pts(const Layout& L, const ModelParams& mp, const T* 
                                              const uint8_t*, const uint8_t*, const int*, const T*,     \
                                              const T*, const T*, const T*, const T*, double, T*, T*,   \
                                              int, const int*, const T*, const T*, double*, Scalars*, int, \
-                                             cudaStream_t);
+                                             cudaStream_t, const float*);
 BAB_SINST(float)
 BAB_SINST(double)
 
