@@ -43,6 +43,7 @@ METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 
 # profiles/k_form_S_cam_dense_mid_1M_obs.md); absent once the kernel has changed
 # since the counters were taken, or for workloads not captured.
 NCU_TRAFFIC = {("medium", "k_spcg"): 13154816 + 26368, ("medium", "k_form_S_runs"): 302387200 + 8206336,
+               ("medium", "k_form_S_rec"): 130734592 + 7529728,
                ("dense_mid", "k_form_S_cam"): 367535616 + 51516160}
 # the measured limiter of a kernel whose roofline bound (ALU) is not what stops it:
 # ncu counters of one launch on the workload (profiles/<kernel>_<workload>...md)
@@ -51,7 +52,13 @@ NCU_LIMITER = {("medium", "k_form_S_runs"): {
     "long_scoreboard_cycles_per_issue": 8.0, "warp_cycles_per_issue": 9.92,
     "reading": "the L1TEX pipe moving the scattered 112-byte Y^ row gathers (two per co-visible pair) is "
                "the limiter, not the FP32 pipe",
-    "source": "profiles/k_form_S_runs_medium_1M_obs.md"}}
+    "source": "profiles/k_form_S_runs_medium_1M_obs.md"},
+    ("medium", "k_form_S_rec"): {
+    "counter": "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active", "value_pct": 48.6,
+    "issue_active_pct": 55.5, "l1tex_throughput_pct": 73.4, "long_scoreboard_cycles_per_issue": 2.39,
+    "reading": "the FP32 pipe rebuilding each pair's Jacobians and the 3 x 3 coupling (about 1.5 x the "
+               "486 algorithmic flops per pair) shares the limit with the record gathers",
+    "source": "profiles/k_form_S_rec_medium_1M_obs.md"}}
 WORKLOAD = "medium"
 LM_ITERS = 30
 E2E_RUNS = 3
@@ -541,6 +548,14 @@ def main():
         fp32_peak = sms * 128 * 2 * 2032e6 / 1e12
         # the kernel the library picked at creation
         fname = form_kernel or "k_form_S_runs"
+        if fname == "k_form_S_rec":
+            # pair list (8 B) and its point (4 B); one 48-byte record per observation,
+            # V*^-1 per point (24 B); the dense S^ written once
+            form_bytes = 12 * npairs + 48 * N + 24 * P + 4 * n * n
+            form_bytes_txt = "12 B x pairs + 48 B x observations + 24 B x points + 4 n^2"
+        else:
+            form_bytes = 8 * npairs + 108 * N + 4 * n * n
+            form_bytes_txt = "8 B x pairs + 108 B x observations + 4 n^2"
         roof_form = {"kernel": fname
                      + " (co-visibility block products forming the explicit system)",
                      "bound": "alu", "achieved": flops / (form_ms * 1e-3) / 1e12, "peak": fp32_peak,
@@ -550,8 +565,9 @@ def main():
                      "measured_limiter": NCU_LIMITER.get((args.workload, fname)) if args.precision == "fp32" else None,
                      "algorithmic_per_launch": flops,
                      "formula": "486 flops x co-visible pairs of free cameras", "pairs": npairs,
-                     "hbm_bytes_algorithmic": 8 * npairs + 108 * N + 4 * n * n,
-                     "hbm_frac_of_measured": (8 * npairs + 108 * N + 4 * n * n) / (form_ms * 1e-3) / 1e9 / hbm,
+                     "hbm_bytes_algorithmic": form_bytes,
+                     "hbm_bytes_formula": form_bytes_txt,
+                     "hbm_frac_of_measured": form_bytes / (form_ms * 1e-3) / 1e9 / hbm,
                      "launch_ms_mean": form_ms}
     if roof_form is not None and roof_form["launch_ms_mean"] > (kern_ms or 0.0):
         roofline, roofline_next = roof_form, roof_pcg

@@ -1255,10 +1255,6 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     ST(dalloc_bytes(pb, &pb->wsgn, R * ((size_t)pb->g_rows + 4)));
     CU(cudaMemset(pb->wsgn, 0, R * ((size_t)pb->g_rows + 4)));
   }
-  if (!pb->recompute || pb->explicit_S) {
-    ST(dalloc_bytes(pb, &pb->W, R * kWStride * ((size_t)pb->w_rows + 1)));
-    CU(cudaMemset(pb->W, 0, R * kWStride * ((size_t)pb->w_rows + 1)));
-  }
   ST(dalloc_bytes(pb, &pb->V, R * 6 * (size_t)P));
   ST(dalloc_bytes(pb, &pb->gp, R * 3 * (size_t)P));
   ST(dalloc_bytes(pb, &pb->Vinv, R * 6 * ((size_t)P + 2)));
@@ -1422,6 +1418,12 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
       if (!ent.empty()) CU(cudaMemcpy(pb->bent, ent.data(), sizeof(int2) * ent.size(), cudaMemcpyHostToDevice));
       ST(dalloc_bytes(pb, &pb->Bs, R * kBlkStride * (2 * (size_t)cv.n_runs + C)));
     }
+  }
+  // W rows: streamed by the FP64 matvec, read by the Y^ pass and the
+  // back-substitution of explicit systems formed from Y^ (not with records)
+  if (!pb->recompute || (pb->explicit_S && !pb->orec)) {
+    ST(dalloc_bytes(pb, &pb->W, R * kWStride * ((size_t)pb->w_rows + 1)));
+    CU(cudaMemset(pb->W, 0, R * kWStride * ((size_t)pb->w_rows + 1)));
   }
   // explicit reduced camera system (solver option; automatic for up to 512 cameras)
   if (pb->explicit_S && n_max > 0) {
