@@ -43,7 +43,7 @@ METRIC = "BA LM iters/s & Jacobian+Schur Gobs/s at 1M obs; time-to-RMSE vs FP64 
 # profiles/k_form_S_cam_dense_mid_1M_obs.md); absent once the kernel has changed
 # since the counters were taken, or for workloads not captured.
 NCU_TRAFFIC = {("medium", "k_spcg"): 13154816 + 26368, ("medium", "k_form_S_runs"): 302387200 + 8206336,
-               ("medium", "k_form_S_rec"): 130734592 + 7529728,
+               ("medium", "k_form_S_rec"): 170977024 + 7290112,
                ("dense_mid", "k_form_S_cam"): 367535616 + 51516160}
 # the measured limiter of a kernel whose roofline bound (ALU) is not what stops it:
 # ncu counters of one launch on the workload (profiles/<kernel>_<workload>...md)
@@ -54,10 +54,11 @@ NCU_LIMITER = {("medium", "k_form_S_runs"): {
                "the limiter, not the FP32 pipe",
     "source": "profiles/k_form_S_runs_medium_1M_obs.md"},
     ("medium", "k_form_S_rec"): {
-    "counter": "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active", "value_pct": 48.6,
-    "issue_active_pct": 55.5, "l1tex_throughput_pct": 73.4, "long_scoreboard_cycles_per_issue": 2.39,
-    "reading": "the FP32 pipe rebuilding each pair's Jacobians and the 3 x 3 coupling (about 1.5 x the "
-               "486 algorithmic flops per pair) shares the limit with the record gathers",
+    "counter": "smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio", "value": 5.44,
+    "warp_cycles_per_issue": 7.74, "issue_active_pct": 37.4, "fma_pipe_pct": 31.0, "l1tex_throughput_pct": 67.6,
+    "reading": "the warps wait on the scattered record gathers (three 32-byte-aligned records per pair, 12 "
+               "resident warps per SM at 168 registers); the FP32 pipe is a third busy. Staging the gathers "
+               "through shared memory (cp.async or per-record cp.async.bulk rings) measured slower",
     "source": "profiles/k_form_S_rec_medium_1M_obs.md"}}
 WORKLOAD = "medium"
 LM_ITERS = 30
@@ -444,9 +445,11 @@ def main():
     ab_ms = statistics.median([i["ms"][1] + i["ms"][2] for i in lin]) if lin else None
     schur_ms = statistics.median([i["ms"][2] for i in infos])
     gobs = N / (ab_ms * 1e-3) / 1e9 if ab_ms else None
-    # (a)+(b) against HBM: 124 B per observation (uv 8, prior 4, point index 4, W row
-    # write 108) plus 12 B read and 36 B written per point
-    ab_bytes = 124 * N + 48 * scene.spec.n_pts
+    # (a)+(b) against HBM: per observation 16 B in (uv 8, prior 4, point index 4) and
+    # the W row (108 B) or, for the formation from records, the 64-byte record
+    # written; per point 12 B read and 36 B written
+    rec_out = 64 if prob.formation_kernel == "k_form_S_rec" else 108
+    ab_bytes = (16 + rec_out) * N + 48 * scene.spec.n_pts
     ab_roof = {"bytes_algorithmic": ab_bytes, "ms": ab_ms,
                "achieved_gbs": ab_bytes / (ab_ms * 1e-3) / 1e9 if ab_ms else None,
                "frac_of_hbm": ab_bytes / (ab_ms * 1e-3) / 1e9 / _peaks()[0] if ab_ms else None}
@@ -549,10 +552,10 @@ def main():
         # the kernel the library picked at creation
         fname = form_kernel or "k_form_S_runs"
         if fname == "k_form_S_rec":
-            # pair list (8 B) and its point (4 B); one 48-byte record per observation,
-            # V*^-1 per point (24 B); the dense S^ written once
-            form_bytes = 12 * npairs + 48 * N + 24 * P + 4 * n * n
-            form_bytes_txt = "12 B x pairs + 48 B x observations + 24 B x points + 4 n^2"
+            # pair list (8 B) and its point (4 B); one 64-byte record per observation,
+            # one 32-byte record (V*^-1) per point; the dense S^ written once
+            form_bytes = 12 * npairs + 64 * N + 32 * P + 4 * n * n
+            form_bytes_txt = "12 B x pairs + 64 B x observations + 32 B x points + 4 n^2"
         else:
             form_bytes = 8 * npairs + 108 * N + 4 * n * n
             form_bytes_txt = "8 B x pairs + 108 B x observations + 4 n^2"

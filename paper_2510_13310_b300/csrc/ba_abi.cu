@@ -141,7 +141,8 @@ struct ba_problem {
   int2* covis_pairs = nullptr;  // point-order observations (k in i, k2 in j) of shared points; FP32
                                 // explicit systems: camera-order (owner's row, other's row), see CamForm
   CamForm cform;                // FP32 explicit systems: the camera-owned formation (n_blocks > 0)
-  float* orec = nullptr;        // FP32 warp-per-run formation: observation records [N][12]
+  float* orec = nullptr;        // FP32 warp-per-run formation: observation records [N][16]
+  float* prec = nullptr;        //   point records [P][8] (V*^-1)
   int* pair_pt = nullptr;       //   and the point of every co-visible pair
   int n_covis_runs = 0;
   bool form_lanes = false;      // one lane per co-visibility run (many short runs)
@@ -508,7 +509,7 @@ ba_status schur_t(ba_problem* pb, double lambda) {
     pb->join_pending = false;
   }
   LAUNCH(1, launch_damp_pts<T>(pb->P, (const T*)pb->V, (const T*)pb->gp, pb->pt_act, lambda, (T*)pb->Vinv,
-                               (T*)pb->z0, pb->err, pb->stream));
+                               (T*)pb->z0, pb->err, pb->stream, pb->prec));
   cudaStream_t cs = pb->stream;
   if (pb->explicit_S && pb->side) {
     CU(cudaEventRecord(pb->fork, pb->stream));  // after the point damping
@@ -549,6 +550,7 @@ ba_status spcg_t(ba_problem* pb, double lambda) {
       frec.rec = pb->orec;
       frec.pair_pt = pb->pair_pt;
       frec.camw = pb->camw[s];
+      frec.prec = pb->prec;
       frec.centre = pb->mp.cam_model == BA_CAMERA_CENTRE;
       LAUNCH(3, launch_form_S<T>(pb->L, pb->n_covis_runs, pb->covis_runs, pb->covis_pairs, (const T*)pb->W,
                                  (const T*)pb->Vinv, pb->crank, (const T*)pb->Ud, (const T*)pb->Dblk, pb->dscale,
@@ -1349,9 +1351,11 @@ ba_status create_impl(const ba_options* opts, void* stream, int64_t n_cams, cons
     // from observation records (k_form_S_rec) unless BA_FORM_RECORDS=0 keeps the Y^ rows
     const char* frv = std::getenv("BA_FORM_RECORDS");
     if (!pb->fp64 && !pb->form_lanes && cv.n_runs > 0 && !(frv && frv[0] == '0')) {
-      ST(dalloc(pb, &pb->orec, (size_t)12 * std::max(N, 1)));
-      CU(cudaMemset(pb->orec, 0, sizeof(float) * 12 * (size_t)std::max(N, 1)));
+      ST(dalloc(pb, &pb->orec, (size_t)16 * std::max(N, 1)));
+      CU(cudaMemset(pb->orec, 0, sizeof(float) * 16 * (size_t)std::max(N, 1)));
       ST(dalloc(pb, &pb->pair_pt, std::max<size_t>(cv.npairs, 1)));
+      ST(dalloc(pb, &pb->prec, (size_t)8 * std::max(P, 1)));
+      CU(cudaMemset(pb->prec, 0, sizeof(float) * 8 * (size_t)std::max(P, 1)));
       LAUNCH(1, launch_pair_pt(cv.npairs, cv.pairs, dl.po_pt, pb->pair_pt, pb->stream));
     }
     if (!pb->fp64 && pb->form_lanes) {

@@ -213,7 +213,7 @@ int rank_blocks(int n);
 template <typename T>
 cudaError_t launch_pt_lin(const Layout& L, const ModelParams& mp, const T* camw, const T* ptsw,
                           const uint8_t* obs_act, T* W, T* wsgn, T* V, T* gp, cudaStream_t s,
-                          float* orec = nullptr);  // FP32 explicit systems: observation records [N][12]
+                          float* orec = nullptr);  // FP32 explicit systems: observation records [N][16]
 template <typename T>
 cudaError_t launch_cam_accum(const Layout& L, const ModelParams& mp, int mode, const T* camw,
                              const T* ptsw, const uint8_t* act_co, const uint8_t* cam_act,
@@ -223,7 +223,8 @@ template <typename T>
 cudaError_t launch_cam_reduce(const Layout& L, const T* partials, T* out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_act, double lambda,
-                            T* Vinv, T* z0, int* err, cudaStream_t s);
+                            T* Vinv, T* z0, int* err, cudaStream_t s,
+                            float* prec = nullptr);      // FP32: point records [P][8] (V*^-1, 0, 0)
 template <typename T>
 cudaError_t launch_schur_diag(int Cf, const int* cam_map, const T* Ug, const T* Sg, double lambda,
                               T* Ud, T* Dinv, T* b, T* dampc, T* Dblk, double* dscale, int* err,
@@ -249,9 +250,10 @@ cudaError_t launch_owner_pairs(int N, const int* co_po, int* po_co, int n_runs, 
 // records written by the point-side linearisation, the point of every pair, the
 // working camera records
 struct FormRec {
-  const float* rec = nullptr;      // [N][12]
+  const float* rec = nullptr;      // [N][16] observation records
   const int* pair_pt = nullptr;    // [npairs]
   const void* camw = nullptr;      // working cameras [C][kCamStride] (FP32)
+  const float* prec = nullptr;     // [P][8] point records: V*^-1 (6), 0, 0
   bool centre = false;             // the camera model of Sec. 3.2 (centre, rotation, focal)
 };
 cudaError_t launch_pair_pt(size_t npairs, const int2* pairs, const int* po_pt, int* pair_pt, cudaStream_t s);

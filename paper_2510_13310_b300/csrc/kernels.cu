@@ -676,8 +676,12 @@ __device__ __forceinline__ void load_pt(const T* __restrict__ ptsw, int p, T& x,
 // W: stored W rows (nullptr when the matvec recomputes the Jacobian); wsgn: per
 // observation IRLS weight rho', negated when the observation has no depth prior
 // (0 for inactive observations), in the padded per-tile layout (nullptr if unused).
-// orec (nullable, FP32): the observation's record [12] for the explicit system's
-// formation (D00 D01 D02 D11 D12 D22 a0 a1 a2 xn yn w; zeros when inactive)
+// orec (nullable, FP32): the observation's record [16] for the explicit system's
+// formation and back-substitution: w D^T D (G00 G01 G02 G11 G12 G22), w D^T e
+// (u0 u1 u2) with e = (xn, yn, 0), the intrinsic factor g = (dist, f rr, f rr^2)
+// ((dist, 0, 0) for the centre model), the point the rotation increment acts on
+// (a0 a1 a2), one zero; all zero when inactive (D = d r / d P, w the IRLS weight,
+// rr = xn^2 + yn^2; model.cuh)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, const T* __restrict__ camw,
                                                    const T* __restrict__ ptsw,
@@ -703,8 +707,8 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
       for (int j = 0; j < 9; ++j) vrow[j] = T(0);
       if (wsgn) wsgn[(size_t)d.g_row + i] = T(0);
       if (orec) {
-        float4* r4 = reinterpret_cast<float4*>(orec) + 3 * (size_t)k;
-        r4[0] = r4[1] = r4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4* r4 = reinterpret_cast<float4*>(orec) + 4 * (size_t)k;
+        r4[0] = r4[1] = r4[2] = r4[3] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       continue;
     }
@@ -720,10 +724,19 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
     T w = o.wrob;
     if (wsgn) wsgn[(size_t)d.g_row + i] = tau > T(0) ? w : -w;
     if (orec) {
-      float4* r4 = reinterpret_cast<float4*>(orec) + 3 * (size_t)k;
-      r4[0] = make_float4((float)o.D00, (float)o.D01, (float)o.D02, (float)o.D11);
-      r4[1] = make_float4((float)o.D12, (float)o.D22, (float)o.a0, (float)o.a1);
-      r4[2] = make_float4((float)o.a2, (float)o.xn, (float)o.yn, (float)w);
+      // columns of D: (D00, D01, 0), (D01, D11, 0), (D02, D12, D22)
+      const float d00 = (float)o.D00, d01 = (float)o.D01, d02 = (float)o.D02, d11 = (float)o.D11,
+                  d12 = (float)o.D12, d22 = (float)o.D22, xn = (float)o.xn, yn = (float)o.yn, wf = (float)w;
+      const float rr = xn * xn + yn * yn, f = (float)cw[12];
+      const float dist = 1.f + rr * ((float)cw[13] + (float)cw[14] * rr);
+      const bool centre = cw[15] != T(0);
+      float4* r4 = reinterpret_cast<float4*>(orec) + 4 * (size_t)k;
+      r4[0] = make_float4(wf * (d00 * d00 + d01 * d01), wf * (d00 * d01 + d01 * d11), wf * (d00 * d02 + d01 * d12),
+                          wf * (d01 * d01 + d11 * d11));
+      r4[1] = make_float4(wf * (d01 * d02 + d11 * d12), wf * (d02 * d02 + d12 * d12 + d22 * d22),
+                          wf * (d00 * xn + d01 * yn), wf * (d01 * xn + d11 * yn));
+      r4[2] = make_float4(wf * (d02 * xn + d12 * yn), dist, centre ? 0.f : f * rr, centre ? 0.f : f * rr * rr);
+      r4[3] = make_float4((float)o.a0, (float)o.a1, (float)o.a2, 0.f);
     }
     if (W) {
       // the row in registers, then stored as 16-byte words (the 28-word row
@@ -1000,16 +1013,25 @@ __global__ void k_damp_pts(int P, const T* __restrict__ V, const T* __restrict__
 __device__ __forceinline__ F2 f2_of(float x) { return F2{x, 0.f}; }
 __device__ __forceinline__ float f2_round(F2 a) { return __fadd_rn(a.h, a.l); }
 
+// prec (nullable): the point record [8] of the explicit system's formation from
+// observation records: V*^-1 (6, as in Vinv), two zeros
 __global__ void k_damp_pts_df(int P, const float* __restrict__ V, const float* __restrict__ gp,
                               const uint8_t* __restrict__ pt_act, F2 lambda, float* __restrict__ Vinv,
-                              float* __restrict__ z0, int* err) {
+                              float* __restrict__ z0, int* err, float* __restrict__ prec) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   float* vo = Vinv + 6 * (size_t)p;
   float* zo = z0 + 3 * (size_t)p;
+  auto point_record = [&]() {
+    if (!prec) return;
+    float4* r4 = reinterpret_cast<float4*>(prec) + 2 * (size_t)p;
+    r4[0] = make_float4(vo[0], vo[1], vo[2], vo[3]);
+    r4[1] = make_float4(vo[4], vo[5], 0.f, 0.f);
+  };
   if (!pt_act[p]) {
     for (int j = 0; j < 6; ++j) vo[j] = 0.f;
     for (int j = 0; j < 3; ++j) zo[j] = 0.f;
+    point_record();
     return;
   }
   const float* v = V + 6 * (size_t)p;
@@ -1025,6 +1047,7 @@ __global__ void k_damp_pts_df(int P, const float* __restrict__ V, const float* _
     atomicOr(err, 4);
     for (int j = 0; j < 6; ++j) vo[j] = 0.f;
     for (int j = 0; j < 3; ++j) zo[j] = 0.f;
+    point_record();
     return;
   }
   const F2 id = f2_recip(det);
@@ -1038,16 +1061,17 @@ __global__ void k_damp_pts_df(int P, const float* __restrict__ V, const float* _
   zo[0] = f2_round(f2_add(f2_add(f2_mul(i00, g0), f2_mul(i01, g1)), f2_mul(i02, g2)));
   zo[1] = f2_round(f2_add(f2_add(f2_mul(i01, g0), f2_mul(i11, g1)), f2_mul(i12, g2)));
   zo[2] = f2_round(f2_add(f2_add(f2_mul(i02, g0), f2_mul(i12, g1)), f2_mul(i22, g2)));
+  point_record();
 }
 
 template <typename T>
 cudaError_t launch_damp_pts(int P, const T* V, const T* gp, const uint8_t* pt_act, double lambda,
-                            T* Vinv, T* z0, int* err, cudaStream_t s) {
+                            T* Vinv, T* z0, int* err, cudaStream_t s, float* prec) {
   if (P <= 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
     const float lh = (float)lambda;
     const F2 lam{lh, (float)(lambda - (double)lh)};
-    k_damp_pts_df<<<(P + 255) / 256, 256, 0, s>>>(P, V, gp, pt_act, lam, Vinv, z0, err);
+    k_damp_pts_df<<<(P + 255) / 256, 256, 0, s>>>(P, V, gp, pt_act, lam, Vinv, z0, err, prec);
   } else
     k_damp_pts<T><<<(P + 255) / 256, 256, 0, s>>>(P, V, gp, pt_act, lambda, Vinv, z0, err);
   return cudaGetLastError();
@@ -1363,7 +1387,7 @@ cudaError_t launch_permute_rows(const int* orig, const int* row, const T* src, i
                                            const T*, const T*, T*, cudaStream_t);                   \
   template cudaError_t launch_cam_reduce<T>(const Layout&, const T*, T*, cudaStream_t);             \
   template cudaError_t launch_damp_pts<T>(int, const T*, const T*, const uint8_t*, double, T*, T*,  \
-                                          int*, cudaStream_t);                                      \
+                                          int*, cudaStream_t, float*);                              \
   template cudaError_t launch_schur_diag<T>(int, const int*, const T*, const T*, double, T*, T*,    \
                                             T*, T*, T*, double*, int*, cudaStream_t, int);          \
   template cudaError_t launch_pred_cams<T>(int, const int*, const T*, const T*, const T*, double,   \

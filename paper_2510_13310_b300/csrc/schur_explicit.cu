@@ -225,84 +225,101 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
 }
 
 // ---------------------------------------------------------------------------
-// The same blocks from observation records (FP32, warp per run).  The pair term
-// W_k V*_p^-1 W_k2^T with W = w Jc^T Jp and Jp = D R is
-//   Jc_k^T K Jc_k2,   K = w w2 (D R_i) V*_p^-1 (D2 R_j)^T   (3 x 3),
-// so a pair needs the two observations' records (D, the point the rotation
-// increment acts on, the normalised image point, the IRLS weight: 48 B each,
-// written by the point-side linearisation and independent of the damping), the
-// point's V*^-1 (24 B) and the two cameras' constants (R, f, k1, k2), against two
-// 112-byte rows of Y^ = D^-1 W M_p before, and no Y^ pass.  The Jacobi scaling
-// is applied to the summed block.  Each lane sums its pairs in order and the
-// lanes are reduced in a fixed butterfly (deterministic).
+// The same blocks from observation records (FP32, warp per run).  With D the
+// derivative of the residual in the camera frame (model.cuh), the camera Jacobian
+// factors as Jc = [D N | D T | e g^T]: N = -[a]x (a = R X, or R X + t for the
+// centre model), T = I (or -R for the centre model's centre columns), e = (xn, yn,
+// 0) and g = (dist, f rr, f rr^2) (or (dist, 0, 0) for the centre model, whose
+// dist is 1); the point Jacobian is Jp = D R and W = w Jc^T Jp.  The pair term
+// W_k V*_p^-1 W_k2^T then needs, per observation, G = w D^T D, u = w D^T e, g and a
+// (the record, 64 B, written by the point-side linearisation and independent of
+// the damping) and, per pair,
+//   M = R_i V*_p^-1 R_j^T,  L = G M G2,  h = G M u2,  h2 = G2 M^T u,  c = u . M u2:
+//   rot-rot [a]x L N2, rot-trans [a]x L T2, trans-rot T^T L N2, trans-trans T^T L T2,
+//   rot-intr ([a]x h) g2^T, trans-intr (T^T h) g2^T, intr-rot g (a2 x h2)^T,
+//   intr-trans g (T2^T h2)^T, intr-intr c g g2^T.
+// A pair reads two observation records and the point's record (V*^-1, 32 B,
+// written with V*^-1 by the point damping): 160 B in five 32-byte loads, against
+// two 112-byte rows of Y^ = D^-1 W M_p, and no Y^ pass runs.  The gathers are
+// what limits this kernel (one L1 wavefront per lane and load, the lanes' records
+// being scattered), hence the 32-byte loads and the stored a and g.  The Jacobi
+// scaling is applied to the summed block.  Each lane sums its pairs in order and
+// the lanes are reduced in a fixed butterfly (deterministic).
 // ---------------------------------------------------------------------------
+// one 32-byte read-only load (32-byte aligned address)
+__device__ __forceinline__ void ld_nc_v8(const float* __restrict__ p, float (&v)[8]) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+      : "l"(p));
+}
+// observation record [16]: G00 G01 G02 G11 G12 G22 u0 u1 | u2 g0 g1 g2 a0 a1 a2 0
 struct ObsRec {
-  float d00, d01, d02, d11, d12, d22, a0, a1, a2, xn, yn, w;
+  float g00, g01, g02, g11, g12, g22, u0, u1, u2, gi0, gi1, gi2, a0, a1, a2;
 };
-__device__ __forceinline__ ObsRec load_rec(const float4* __restrict__ R4, int k) {
-  const float4 u = R4[3 * (size_t)k], v = R4[3 * (size_t)k + 1], t = R4[3 * (size_t)k + 2];
-  return ObsRec{u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, t.x, t.y, t.z, t.w};
+__device__ __forceinline__ ObsRec load_rec(const float* __restrict__ rec, int k) {
+  float x[8], y[8];
+  ld_nc_v8(rec + 16 * (size_t)k, x);
+  ld_nc_v8(rec + 16 * (size_t)k + 8, y);
+  return ObsRec{x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], y[0], y[1], y[2], y[3], y[4], y[5], y[6]};
 }
-// column c of the 3 x 9 camera Jacobian (rows u, v, depth; model.cuh) from the
-// record, the camera constants cam = (R[9], f, k1, k2) and A = D R (the centre
-// model's centre columns are -A and it has no k1, k2 columns)
-__device__ __forceinline__ void rec_jc_col(const ObsRec& r, const float* cam, const float (&A)[3][3], bool centre,
-                                           int c, float& j0, float& j1, float& j2) {
-  const float f = cam[9], k1 = cam[10], k2 = cam[11];
-  const float rr = r.xn * r.xn + r.yn * r.yn;
-  switch (c) {
-    case 0: j0 = -r.d01 * r.a2 + r.d02 * r.a1; j1 = -r.d11 * r.a2 + r.d12 * r.a1; j2 = r.d22 * r.a1; break;
-    case 1: j0 = r.d00 * r.a2 - r.d02 * r.a0; j1 = r.d01 * r.a2 - r.d12 * r.a0; j2 = -r.d22 * r.a0; break;
-    case 2: j0 = -r.d00 * r.a1 + r.d01 * r.a0; j1 = -r.d01 * r.a1 + r.d11 * r.a0; j2 = 0.f; break;
-    case 3: j0 = centre ? -A[0][0] : r.d00; j1 = centre ? -A[1][0] : r.d01; j2 = centre ? -A[2][0] : 0.f; break;
-    case 4: j0 = centre ? -A[0][1] : r.d01; j1 = centre ? -A[1][1] : r.d11; j2 = centre ? -A[2][1] : 0.f; break;
-    case 5: j0 = centre ? -A[0][2] : r.d02; j1 = centre ? -A[1][2] : r.d12; j2 = centre ? -A[2][2] : r.d22; break;
-    case 6: {
-      const float dist = 1.f + rr * (k1 + k2 * rr);
-      j0 = dist * r.xn; j1 = dist * r.yn; j2 = 0.f;
-    } break;
-    case 7: j0 = centre ? 0.f : f * r.xn * rr; j1 = centre ? 0.f : f * r.yn * rr; j2 = 0.f; break;
-    default: j0 = centre ? 0.f : f * r.xn * rr * rr; j1 = centre ? 0.f : f * r.yn * rr * rr; j2 = 0.f; break;
-  }
-}
-// A = D R for a record (D10 = D01, D20 = D21 = 0)
-__device__ __forceinline__ void rec_dr(const ObsRec& r, const float* R, float (&A)[3][3]) {
+// symmetric 3 x 3 G of a record times a general 3 x 3 B (rows r of G B)
+__device__ __forceinline__ void rec_gmul(const ObsRec& r, const float (&B)[3][3], float (&out)[3][3]) {
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
-    A[0][t] = r.d00 * R[t] + r.d01 * R[3 + t] + r.d02 * R[6 + t];
-    A[1][t] = r.d01 * R[t] + r.d11 * R[3 + t] + r.d12 * R[6 + t];
-    A[2][t] = r.d22 * R[6 + t];
+    out[0][t] = r.g00 * B[0][t] + r.g01 * B[1][t] + r.g02 * B[2][t];
+    out[1][t] = r.g01 * B[0][t] + r.g11 * B[1][t] + r.g12 * B[2][t];
+    out[2][t] = r.g02 * B[0][t] + r.g12 * B[1][t] + r.g22 * B[2][t];
   }
+}
+__device__ __forceinline__ void rec_gvec(const ObsRec& r, const float (&v)[3], float (&out)[3]) {
+  out[0] = r.g00 * v[0] + r.g01 * v[1] + r.g02 * v[2];
+  out[1] = r.g01 * v[0] + r.g11 * v[1] + r.g12 * v[2];
+  out[2] = r.g02 * v[0] + r.g12 * v[1] + r.g22 * v[2];
+}
+
+// Z N2 added into rows r0.. of acc at column 0 (N2 = -[a2]x)
+__device__ __forceinline__ void acc_times_n(float (&acc)[81], int row0, const float (&Z)[3][3], const float (&a2)[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    acc[9 * (row0 + r) + 0] += -Z[r][1] * a2[2] + Z[r][2] * a2[1];
+    acc[9 * (row0 + r) + 1] += Z[r][0] * a2[2] - Z[r][2] * a2[0];
+    acc[9 * (row0 + r) + 2] += -Z[r][0] * a2[1] + Z[r][1] * a2[0];
+  }
+}
+// Z T2 added into rows row0.. at columns 3-5 (T2 = I, or -R_j for the centre model)
+template <bool kCentre>
+__device__ __forceinline__ void acc_times_t(float (&acc)[81], int row0, const float (&Z)[3][3], const float* Rj) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+      acc[9 * (row0 + r) + 3 + t] +=
+          kCentre ? -(Z[r][0] * Rj[t] + Z[r][1] * Rj[3 + t] + Z[r][2] * Rj[6 + t]) : Z[r][t];
 }
 
 template <bool kSparse, bool kCentre>
 __global__ void __launch_bounds__(128, 3)
     k_form_S_rec(int n_runs, const int4* __restrict__ runs, const int2* __restrict__ pairs,
-                 const int* __restrict__ pair_pt, const float* __restrict__ orec, const float* __restrict__ Vinv,
-                 const float* __restrict__ camw, const double* __restrict__ dscale, const int* __restrict__ crank,
-                 int Cf, float* __restrict__ Shat, int C, int N, int P) {
-  __shared__ float cam_s[4][24];
+                 const int* __restrict__ pair_pt, const float* __restrict__ orec, const float* __restrict__ prec,
+                 const float* __restrict__ camw, const double* __restrict__ dscale,
+                 const int* __restrict__ crank, int Cf, float* __restrict__ Shat, int C, int N, int P) {
+  __shared__ float cam_s[4][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int ld = spcg_row_stride<float>(9 * Cf);
-  const float4* R4 = reinterpret_cast<const float4*>(orec);
-  const float2* V2 = reinterpret_cast<const float2*>(Vinv);
   const float* dinv = reinterpret_cast<const float*>(dscale + 9 * (size_t)Cf);
   for (int ri = gw; ri < n_runs; ri += nw) {
     const int4 rn = runs[ri];  // (camera i, camera j, first pair, pair count)
     const int ci_ = bidx(rn.x, C, 39), cj_ = bidx(rn.y, C, 39);
     const int a = crank[ci_], b = crank[cj_];
     if (a < 0 || b < 0) continue;
-    // the two cameras' R, f, k1, k2 (working records: R t f k1 k2 model)
+    // the two cameras' rotations (the first 9 entries of the working records)
     __syncwarp();
     if (lane < 9) cam_s[wib][lane] = camw[kCamStride * (size_t)ci_ + lane];
-    else if (lane < 12) cam_s[wib][lane] = camw[kCamStride * (size_t)ci_ + lane + 3];
-    else if (lane < 21) cam_s[wib][lane] = camw[kCamStride * (size_t)cj_ + lane - 12];
-    else if (lane < 24) cam_s[wib][lane] = camw[kCamStride * (size_t)cj_ + lane - 9];
-    constexpr bool centre = kCentre;  // the camera model (flag of the working records)
+    else if (lane >= 16 && lane < 25) cam_s[wib][lane] = camw[kCamStride * (size_t)cj_ + lane - 16];
     __syncwarp();
     const float* ci = cam_s[wib];
-    const float* cj = cam_s[wib] + 12;
+    const float* cj = cam_s[wib] + 16;
     float acc[81];
 #pragma unroll
     for (int q = 0; q < 81; ++q) acc[q] = 0.f;
@@ -314,46 +331,83 @@ __global__ void __launch_bounds__(128, 3)
       const int2 pr = nxt;
       const int p = bidx(npt, P, 40);
       if (q + 32 < qe) nxt = pairs[q + 32], npt = pair_pt[q + 32];  // next pair's indices in flight
-      const ObsRec r1 = load_rec(R4, bidx(pr.x, N, 41)), r2 = load_rec(R4, bidx(pr.y, N, 41));
-      const float2 v0 = V2[3 * (size_t)p], v1 = V2[3 * (size_t)p + 1], v2 = V2[3 * (size_t)p + 2];
-      const float v00 = v0.x, v01 = v0.y, v02 = v1.x, v11 = v1.y, v12 = v2.x, v22 = v2.y;
-      float A2[3][3], A1[3][3];
-      rec_dr(r2, cj, A2);
-      rec_dr(r1, ci, A1);
-      // B = V*^-1 A2^T, K = w w2 A1 B
-      float B[3][3];
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        B[0][t] = v00 * A2[t][0] + v01 * A2[t][1] + v02 * A2[t][2];
-        B[1][t] = v01 * A2[t][0] + v11 * A2[t][1] + v12 * A2[t][2];
-        B[2][t] = v02 * A2[t][0] + v12 * A2[t][1] + v22 * A2[t][2];
-      }
-      const float ww = r1.w * r2.w;
-      float K[3][3];
+      const ObsRec r1 = load_rec(orec, bidx(pr.x, N, 41)), r2 = load_rec(orec, bidx(pr.y, N, 41));
+      float pv[8];  // the point record: V*^-1 (v00 v01 v02 v11 v12 v22), 0, 0
+      ld_nc_v8(prec + 8 * (size_t)p, pv);
+      const float V[3][3] = {{pv[0], pv[1], pv[2]}, {pv[1], pv[3], pv[4]}, {pv[2], pv[4], pv[5]}};
+      const float a1[3] = {r1.a0, r1.a1, r1.a2}, a2[3] = {r2.a0, r2.a1, r2.a2};
+      // M = R_i V R_j^T
+      float T0[3][3], M[3][3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int t = 0; t < 3; ++t) K[r][t] = ww * (A1[r][0] * B[0][t] + A1[r][1] * B[1][t] + A1[r][2] * B[2][t]);
-      // T = K Jc2 (3 x 9), then acc += Jc1^T T; a Jacobian's depth row is zero
-      // outside the rotation, centre/translation columns
-      float T[3][9];
+        for (int t = 0; t < 3; ++t) T0[r][t] = ci[3 * r] * V[0][t] + ci[3 * r + 1] * V[1][t] + ci[3 * r + 2] * V[2][t];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        float j0, j1, j2;
-        rec_jc_col(r2, cj, A2, centre, c, j0, j1, j2);
-        const bool dz = c < 2 || (c >= 3 && c <= 5);
+      for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int r = 0; r < 3; ++r) T[r][c] = dz ? K[r][0] * j0 + K[r][1] * j1 + K[r][2] * j2 : K[r][0] * j0 + K[r][1] * j1;
+        for (int t = 0; t < 3; ++t) M[r][t] = T0[r][0] * cj[3 * t] + T0[r][1] * cj[3 * t + 1] + T0[r][2] * cj[3 * t + 2];
+      // L = G M G2, h = G M u2, h2 = G2 M^T u, c = u . M u2
+      const float u1[3] = {r1.u0, r1.u1, r1.u2}, u2[3] = {r2.u0, r2.u1, r2.u2};
+      float Mu2[3], Mtu1[3], h1[3], h2[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        Mu2[r] = M[r][0] * u2[0] + M[r][1] * u2[1] + M[r][2] * u2[2];
+        Mtu1[r] = M[0][r] * u1[0] + M[1][r] * u1[1] + M[2][r] * u1[2];
+      }
+      rec_gvec(r1, Mu2, h1);
+      rec_gvec(r2, Mtu1, h2);
+      const float c = u1[0] * Mu2[0] + u1[1] * Mu2[1] + u1[2] * Mu2[2];
+      rec_gmul(r1, M, T0);  // T0 = G M
+      float L[3][3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        L[r][0] = T0[r][0] * r2.g00 + T0[r][1] * r2.g01 + T0[r][2] * r2.g02;
+        L[r][1] = T0[r][0] * r2.g01 + T0[r][1] * r2.g11 + T0[r][2] * r2.g12;
+        L[r][2] = T0[r][0] * r2.g02 + T0[r][1] * r2.g12 + T0[r][2] * r2.g22;
+      }
+      const float g1[3] = {r1.gi0, r1.gi1, r1.gi2}, g2[3] = {r2.gi0, r2.gi1, r2.gi2};
+      // rotation rows: [a1]x L (T0 reused), then times N2 and T2
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        T0[0][t] = a1[1] * L[2][t] - a1[2] * L[1][t];
+        T0[1][t] = a1[2] * L[0][t] - a1[0] * L[2][t];
+        T0[2][t] = a1[0] * L[1][t] - a1[1] * L[0][t];
+      }
+      acc_times_n(acc, 0, T0, a2);
+      acc_times_t<kCentre>(acc, 0, T0, cj);
+      // translation rows: T1^T L (L itself, or -R_i^T L), then times N2 and T2
+      if (kCentre) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int t = 0; t < 3; ++t) T0[r][t] = -(ci[r] * L[0][t] + ci[3 + r] * L[1][t] + ci[6 + r] * L[2][t]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int t = 0; t < 3; ++t) T0[r][t] = L[r][t];
+      }
+      acc_times_n(acc, 3, T0, a2);
+      acc_times_t<kCentre>(acc, 3, T0, cj);
+      // intrinsic rows and columns
+      float ah1[3], th1[3], ah2[3], th2[3];
+      ah1[0] = a1[1] * h1[2] - a1[2] * h1[1], ah1[1] = a1[2] * h1[0] - a1[0] * h1[2], ah1[2] = a1[0] * h1[1] - a1[1] * h1[0];
+      ah2[0] = a2[1] * h2[2] - a2[2] * h2[1], ah2[1] = a2[2] * h2[0] - a2[0] * h2[2], ah2[2] = a2[0] * h2[1] - a2[1] * h2[0];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        th1[r] = kCentre ? -(ci[r] * h1[0] + ci[3 + r] * h1[1] + ci[6 + r] * h1[2]) : h1[r];
+        th2[r] = kCentre ? -(cj[r] * h2[0] + cj[3 + r] * h2[1] + cj[6 + r] * h2[2]) : h2[r];
       }
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        float j0, j1, j2;
-        rec_jc_col(r1, ci, A1, centre, c, j0, j1, j2);
-        const bool dz = c < 2 || (c >= 3 && c <= 5);
+      for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int s2 = 0; s2 < 9; ++s2)
-          acc[9 * c + s2] += dz ? j0 * T[0][s2] + j1 * T[1][s2] + j2 * T[2][s2] : j0 * T[0][s2] + j1 * T[1][s2];
-      }
+        for (int t = 0; t < 3; ++t) {
+          acc[9 * r + 6 + t] += ah1[r] * g2[t];
+          acc[9 * (3 + r) + 6 + t] += th1[r] * g2[t];
+          acc[9 * (6 + t) + r] += g1[t] * ah2[r];
+          acc[9 * (6 + t) + 3 + r] += g1[t] * th2[r];
+          acc[9 * (6 + r) + 6 + t] += c * g1[r] * g2[t];
+        }
     }
     // warp reduce-scatter of the 81 sums (padded to 96), then the Jacobi scaling
     float v[96];
@@ -680,11 +734,10 @@ cudaError_t launch_form_S(const Layout& L, int n_runs, const int4* runs, const i
           // finish, so the side stream's Schur-diagonal chain, which the diagonal
           // blocks wait for, is scheduled alongside instead of after the formation
           grid = (n_runs + wpb - 1) / wpb;
-          const float* Vf = reinterpret_cast<const float*>(Vinv);
           const float* Cw = reinterpret_cast<const float*>(fr->camw);
           auto* kern = sparse ? (fr->centre ? k_form_S_rec<true, true> : k_form_S_rec<true, false>)
                               : (fr->centre ? k_form_S_rec<false, true> : k_form_S_rec<false, false>);
-          kern<<<grid, 128, 0, s>>>(n_runs, runs, pairs, fr->pair_pt, fr->rec, Vf, Cw, dscale, crank, Cf,
+          kern<<<grid, 128, 0, s>>>(n_runs, runs, pairs, fr->pair_pt, fr->rec, fr->prec, Cw, dscale, crank, Cf,
                                     (float*)Shat, L.C, L.N, L.P);
         }
       }
@@ -1583,8 +1636,9 @@ int spcg_words_per_value(bool fp64) { return kSpcgReplicas * (fp64 ? spcg_words<
 // recomputed; coalesced over point order), then one thread per point sums its
 // observations' terms in point order.
 // ---------------------------------------------------------------------------
-// orec (FP32, nullable): W_k^T x = w Jp^T (Jc x) from the observation record
-// (Jp = D R; the same record the explicit system was formed from), no W row
+// orec (FP32, nullable): W_k^T x = w Jp^T (Jc x) = R^T (G (N x_rot + T x_trans) +
+// u (g . x_intr)) from the observation record (the factors of Jc and Jp = D R of
+// the explicit system's formation), no W row
 template <typename T>
 __global__ void k_backsub_obs(Layout L, ModelParams mp, const T* __restrict__ camw, const T* __restrict__ ptsw,
                               const uint8_t* __restrict__ act_po, const int* __restrict__ crank,
@@ -1598,27 +1652,24 @@ __global__ void k_backsub_obs(Layout L, ModelParams mp, const T* __restrict__ ca
     bool done = false;
     if constexpr (sizeof(T) == 4) {
       if (cr >= 0 && orec) {
-        const ObsRec r = load_rec(reinterpret_cast<const float4*>(orec), k);
-        const float* cwp = reinterpret_cast<const float*>(camw) + kCamStride * (size_t)bidx(L.po_cam[k], L.C, 16);
-        float cam[12];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) cam[q] = cwp[q];
-        cam[9] = cwp[12], cam[10] = cwp[13], cam[11] = cwp[14];
-        const bool centre = cwp[15] != 0.f;
-        float A[3][3];
-        rec_dr(r, cam, A);
+        const ObsRec r = load_rec(orec, k);
+        const float* cam = reinterpret_cast<const float*>(camw) + kCamStride * (size_t)bidx(L.po_cam[k], L.C, 16);
+        const bool centre = cam[15] != 0.f;
+        const float a[3] = {r.a0, r.a1, r.a2}, g[3] = {r.gi0, r.gi1, r.gi2};
         const float* xv = reinterpret_cast<const float*>(x) + 9 * (size_t)cr;
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+        // y = N x_rot + T x_trans with N = -[a]x (x_rot x a), T = I or -R
+        float y[3] = {xv[1] * a[2] - xv[2] * a[1], xv[2] * a[0] - xv[0] * a[2], xv[0] * a[1] - xv[1] * a[0]};
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-          float j0, j1, j2;
-          rec_jc_col(r, cam, A, centre, c, j0, j1, j2);
-          const float xc = xv[c];
-          u0 += j0 * xc, u1 += j1 * xc, u2 += j2 * xc;
-        }
-        s0 = r.w * (A[0][0] * u0 + A[1][0] * u1 + A[2][0] * u2);
-        s1 = r.w * (A[0][1] * u0 + A[1][1] * u1 + A[2][1] * u2);
-        s2 = r.w * (A[0][2] * u0 + A[1][2] * u1 + A[2][2] * u2);
+        for (int t = 0; t < 3; ++t)
+          y[t] += centre ? -(cam[3 * t] * xv[3] + cam[3 * t + 1] * xv[4] + cam[3 * t + 2] * xv[5]) : xv[3 + t];
+        const float gx = g[0] * xv[6] + g[1] * xv[7] + g[2] * xv[8];
+        // W^T x = R^T (G y + u (g . x_intr))
+        float z[3];
+        rec_gvec(r, y, z);
+        z[0] += r.u0 * gx, z[1] += r.u1 * gx, z[2] += r.u2 * gx;
+        s0 = cam[0] * z[0] + cam[3] * z[1] + cam[6] * z[2];
+        s1 = cam[1] * z[0] + cam[4] * z[1] + cam[7] * z[2];
+        s2 = cam[2] * z[0] + cam[5] * z[1] + cam[8] * z[2];
         done = true;
       }
     }
