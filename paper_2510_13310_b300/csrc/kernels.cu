@@ -673,6 +673,14 @@ __device__ __forceinline__ void load_pt(const T* __restrict__ ptsw, int p, T& x,
   z = v.z;
 }
 
+// one 32-byte store (32-byte aligned address)
+__device__ __forceinline__ void st_v8(float* p, float a, float b, float c, float d, float e, float f, float g,
+                                      float h) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d), "f"(e), "f"(f), "f"(g), "f"(h)
+               : "memory");
+}
+
 // W: stored W rows (nullptr when the matvec recomputes the Jacobian); wsgn: per
 // observation IRLS weight rho', negated when the observation has no depth prior
 // (0 for inactive observations), in the padded per-tile layout (nullptr if unused).
@@ -683,7 +691,7 @@ __device__ __forceinline__ void load_pt(const T* __restrict__ ptsw, int p, T& x,
 // (a0 a1 a2), one zero; all zero when inactive (D = d r / d P, w the IRLS weight,
 // rr = xn^2 + yn^2; model.cuh)
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, const T* __restrict__ camw,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) k_pt_lin(Layout L, ModelParams mp, const T* __restrict__ camw,
                                                    const T* __restrict__ ptsw,
                                                    const uint8_t* __restrict__ obs_act, T* __restrict__ W,
                                                    T* __restrict__ wsgn, T* __restrict__ V,
@@ -706,9 +714,9 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
 #pragma unroll
       for (int j = 0; j < 9; ++j) vrow[j] = T(0);
       if (wsgn) wsgn[(size_t)d.g_row + i] = T(0);
-      if (orec) {
-        float4* r4 = reinterpret_cast<float4*>(orec) + 4 * (size_t)k;
-        r4[0] = r4[1] = r4[2] = r4[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (sizeof(T) == 4 && orec) {
+        st_v8(orec + 16 * (size_t)k, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+        st_v8(orec + 16 * (size_t)k + 8, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
       }
       continue;
     }
@@ -723,21 +731,6 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
                      (T)mp.cy, (T)mp.huber, o);
     T w = o.wrob;
     if (wsgn) wsgn[(size_t)d.g_row + i] = tau > T(0) ? w : -w;
-    if (orec) {
-      // columns of D: (D00, D01, 0), (D01, D11, 0), (D02, D12, D22)
-      const float d00 = (float)o.D00, d01 = (float)o.D01, d02 = (float)o.D02, d11 = (float)o.D11,
-                  d12 = (float)o.D12, d22 = (float)o.D22, xn = (float)o.xn, yn = (float)o.yn, wf = (float)w;
-      const float rr = xn * xn + yn * yn, f = (float)cw[12];
-      const float dist = 1.f + rr * ((float)cw[13] + (float)cw[14] * rr);
-      const bool centre = cw[15] != T(0);
-      float4* r4 = reinterpret_cast<float4*>(orec) + 4 * (size_t)k;
-      r4[0] = make_float4(wf * (d00 * d00 + d01 * d01), wf * (d00 * d01 + d01 * d11), wf * (d00 * d02 + d01 * d12),
-                          wf * (d01 * d01 + d11 * d11));
-      r4[1] = make_float4(wf * (d01 * d02 + d11 * d12), wf * (d02 * d02 + d12 * d12 + d22 * d22),
-                          wf * (d00 * xn + d01 * yn), wf * (d01 * xn + d11 * yn));
-      r4[2] = make_float4(wf * (d02 * xn + d12 * yn), dist, centre ? 0.f : f * rr, centre ? 0.f : f * rr * rr);
-      r4[3] = make_float4((float)o.a0, (float)o.a1, (float)o.a2, 0.f);
-    }
     if (W) {
       // the row in registers, then stored as 16-byte words (the 28-word row
       // stride puts the 8 lanes of a quarter-warp on distinct bank groups)
@@ -763,6 +756,20 @@ __global__ void __launch_bounds__(kBlock) k_pt_lin(Layout L, ModelParams mp, con
       for (int b = a; b < 3; ++b)
         vrow[sym3(a, b)] = w * (o.Jp[0][a] * o.Jp[0][b] + o.Jp[1][a] * o.Jp[1][b] + o.Jp[2][a] * o.Jp[2][b]);
       vrow[6 + a] = w * (o.Jp[0][a] * o.r[0] + o.Jp[1][a] * o.r[1] + o.Jp[2][a] * o.r[2]);
+    }
+    if (sizeof(T) == 4 && orec) {  // FP32 problems only
+      // columns of D: (D00, D01, 0), (D01, D11, 0), (D02, D12, D22)
+      const float d00 = (float)o.D00, d01 = (float)o.D01, d02 = (float)o.D02, d11 = (float)o.D11,
+                  d12 = (float)o.D12, d22 = (float)o.D22, xn = (float)o.xn, yn = (float)o.yn, wf = (float)w;
+      const float rr = xn * xn + yn * yn, f = (float)cw[12];
+      const float dist = 1.f + rr * ((float)cw[13] + (float)cw[14] * rr);
+      const bool centre = cw[15] != T(0);
+      float* rk = orec + 16 * (size_t)k;
+      st_v8(rk, wf * (d00 * d00 + d01 * d01), wf * (d00 * d01 + d01 * d11), wf * (d00 * d02 + d01 * d12),
+            wf * (d01 * d01 + d11 * d11), wf * (d01 * d02 + d11 * d12), wf * (d02 * d02 + d12 * d12 + d22 * d22),
+            wf * (d00 * xn + d01 * yn), wf * (d01 * xn + d11 * yn));
+      st_v8(rk + 8, wf * (d02 * xn + d12 * yn), dist, centre ? 0.f : f * rr, centre ? 0.f : f * rr * rr,
+            (float)o.a0, (float)o.a1, (float)o.a2, 0.f);
     }
   }
   __syncthreads();
