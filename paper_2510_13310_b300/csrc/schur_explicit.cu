@@ -243,8 +243,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
 // two 112-byte rows of Y^ = D^-1 W M_p, and no Y^ pass runs.  The gathers are
 // what limits this kernel (one L1 wavefront per lane and load, the lanes' records
 // being scattered), hence the 32-byte loads and the stored a and g.  The Jacobi
-// scaling is applied to the summed block.  Each lane sums its pairs in order and
-// the lanes are reduced in a fixed butterfly (deterministic).
+// scaling is applied to the summed block.  Each lane sums its pairs in order (the
+// intrinsic rows' 27 sums in shared memory, the other 54 in registers) and the
+// lanes are reduced in a fixed butterfly (deterministic).
 // ---------------------------------------------------------------------------
 // one 32-byte read-only load (32-byte aligned address)
 __device__ __forceinline__ void ld_nc_v8(const float* __restrict__ p, float (&v)[8]) {
@@ -278,7 +279,8 @@ __device__ __forceinline__ void rec_gvec(const ObsRec& r, const float (&v)[3], f
 }
 
 // Z N2 added into rows r0.. of acc at column 0 (N2 = -[a2]x)
-__device__ __forceinline__ void acc_times_n(float (&acc)[81], int row0, const float (&Z)[3][3], const float (&a2)[3]) {
+template <int K>
+__device__ __forceinline__ void acc_times_n(float (&acc)[K], int row0, const float (&Z)[3][3], const float (&a2)[3]) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     acc[9 * (row0 + r) + 0] += -Z[r][1] * a2[2] + Z[r][2] * a2[1];
@@ -287,8 +289,8 @@ __device__ __forceinline__ void acc_times_n(float (&acc)[81], int row0, const fl
   }
 }
 // Z T2 added into rows row0.. at columns 3-5 (T2 = I, or -R_j for the centre model)
-template <bool kCentre>
-__device__ __forceinline__ void acc_times_t(float (&acc)[81], int row0, const float (&Z)[3][3], const float* Rj) {
+template <bool kCentre, int K>
+__device__ __forceinline__ void acc_times_t(float (&acc)[K], int row0, const float (&Z)[3][3], const float* Rj) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -304,7 +306,9 @@ __global__ void __launch_bounds__(128, 3)
                  const float* __restrict__ camw, const double* __restrict__ dscale,
                  const int* __restrict__ crank, int Cf, float* __restrict__ Shat, int C, int N, int P) {
   __shared__ float cam_s[4][32];
+  __shared__ float sacc_s[4][27 * 32];  // the intrinsic rows' sums, entry t of lane l at 32 t + l
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* sacc = sacc_s[wib] + lane;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int ld = spcg_row_stride<float>(9 * Cf);
   const float* dinv = reinterpret_cast<const float*>(dscale + 9 * (size_t)Cf);
@@ -320,9 +324,11 @@ __global__ void __launch_bounds__(128, 3)
     __syncwarp();
     const float* ci = cam_s[wib];
     const float* cj = cam_s[wib] + 16;
-    float acc[81];
+    float acc[54];  // rows 0-5 (rotation, translation); rows 6-8 in sacc
 #pragma unroll
-    for (int q = 0; q < 81; ++q) acc[q] = 0.f;
+    for (int q = 0; q < 54; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int t = 0; t < 27; ++t) sacc[32 * t] = 0.f;
     const int qe = rn.z + rn.w;
     int q = rn.z + lane;
     int2 nxt = q < qe ? pairs[q] : make_int2(0, 0);
@@ -357,6 +363,22 @@ __global__ void __launch_bounds__(128, 3)
       rec_gvec(r1, Mu2, h1);
       rec_gvec(r2, Mtu1, h2);
       const float c = u1[0] * Mu2[0] + u1[1] * Mu2[1] + u1[2] * Mu2[2];
+      const float g1[3] = {r1.gi0, r1.gi1, r1.gi2}, g2[3] = {r2.gi0, r2.gi1, r2.gi2};
+      // intrinsic rows first (shared memory): g (a2 x h2)^T, g (T2^T h2)^T, c g g2^T
+      {
+        float ah2[3], th2[3];
+        ah2[0] = a2[1] * h2[2] - a2[2] * h2[1], ah2[1] = a2[2] * h2[0] - a2[0] * h2[2], ah2[2] = a2[0] * h2[1] - a2[1] * h2[0];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) th2[r] = kCentre ? -(cj[r] * h2[0] + cj[3 + r] * h2[1] + cj[6 + r] * h2[2]) : h2[r];
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            sacc[32 * (9 * t + r)] += g1[t] * ah2[r];
+            sacc[32 * (9 * t + 3 + r)] += g1[t] * th2[r];
+            sacc[32 * (9 * t + 6 + r)] += c * g1[t] * g2[r];
+          }
+      }
       rec_gmul(r1, M, T0);  // T0 = G M
       float L[3][3];
 #pragma unroll
@@ -365,7 +387,6 @@ __global__ void __launch_bounds__(128, 3)
         L[r][1] = T0[r][0] * r2.g01 + T0[r][1] * r2.g11 + T0[r][2] * r2.g12;
         L[r][2] = T0[r][0] * r2.g02 + T0[r][1] * r2.g12 + T0[r][2] * r2.g22;
       }
-      const float g1[3] = {r1.gi0, r1.gi1, r1.gi2}, g2[3] = {r2.gi0, r2.gi1, r2.gi2};
       // rotation rows: [a1]x L (T0 reused), then times N2 and T2
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
@@ -389,30 +410,23 @@ __global__ void __launch_bounds__(128, 3)
       }
       acc_times_n(acc, 3, T0, a2);
       acc_times_t<kCentre>(acc, 3, T0, cj);
-      // intrinsic rows and columns
-      float ah1[3], th1[3], ah2[3], th2[3];
+      // the intrinsic columns of rows 0-5: ([a1]x h) g2^T, (T1^T h) g2^T
+      float ah1[3], th1[3];
       ah1[0] = a1[1] * h1[2] - a1[2] * h1[1], ah1[1] = a1[2] * h1[0] - a1[0] * h1[2], ah1[2] = a1[0] * h1[1] - a1[1] * h1[0];
-      ah2[0] = a2[1] * h2[2] - a2[2] * h2[1], ah2[1] = a2[2] * h2[0] - a2[0] * h2[2], ah2[2] = a2[0] * h2[1] - a2[1] * h2[0];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        th1[r] = kCentre ? -(ci[r] * h1[0] + ci[3 + r] * h1[1] + ci[6 + r] * h1[2]) : h1[r];
-        th2[r] = kCentre ? -(cj[r] * h2[0] + cj[3 + r] * h2[1] + cj[6 + r] * h2[2]) : h2[r];
-      }
+      for (int r = 0; r < 3; ++r) th1[r] = kCentre ? -(ci[r] * h1[0] + ci[3 + r] * h1[1] + ci[6 + r] * h1[2]) : h1[r];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
           acc[9 * r + 6 + t] += ah1[r] * g2[t];
           acc[9 * (3 + r) + 6 + t] += th1[r] * g2[t];
-          acc[9 * (6 + t) + r] += g1[t] * ah2[r];
-          acc[9 * (6 + t) + 3 + r] += g1[t] * th2[r];
-          acc[9 * (6 + r) + 6 + t] += c * g1[r] * g2[t];
         }
     }
     // warp reduce-scatter of the 81 sums (padded to 96), then the Jacobi scaling
     float v[96];
 #pragma unroll
-    for (int t = 0; t < 96; ++t) v[t] = t < 81 ? acc[t] : 0.f;
+    for (int t = 0; t < 96; ++t) v[t] = t < 54 ? acc[t] : t < 81 ? sacc[32 * (t - 54)] : 0.f;
     rs_round<float, 96>(v, lane, 0);
     rs_round<float, 48>(v, lane, 1);
     rs_round<float, 24>(v, lane, 2);

@@ -70,3 +70,40 @@ def test_noalloc_rejects_oversize_and_unmapped_host_memory():
                                 z_i.data_ptr(), z_i.data_ptr(), z_d.data_ptr(), z_d.data_ptr(),
                                 None, out.data_ptr())
     assert st == ba.BA_ERR_INVALID_ARG
+
+
+def test_noalloc_call_captured_in_a_cuda_graph_replays_for_new_states():
+    """The entry point exists for code captured into CUDA graphs: one call captured
+    (after a warm-up call outside capture), then replayed with the cameras and
+    points rewritten in place, must give ba_eval_cost's numbers each time."""
+    sc = scenes.make_scene("small")
+    opts = ba.Options(invalid_depth_weight=1e-3)
+    prob = ba.Problem.from_scene(sc, opts)
+    prob.extract()
+    mask = prob.get_active()["obs_mask"]
+    cams_d, pts_d = _dev(sc.cams0, torch.float64), _dev(sc.pts0, torch.float64)
+    obs = [_dev(sc.obs_cam, torch.int32), _dev(sc.obs_pt, torch.int32),
+           _dev(sc.obs_uv, torch.float64), _dev(sc.depth, torch.float64)]
+    m = _dev(mask, torch.uint8)
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ba.eval_cost_noalloc(cams_d, pts_d, *obs, out, obs_mask=m, options=opts, stream=side.cuda_stream)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ba.eval_cost_noalloc(cams_d, pts_d, *obs, out, obs_mask=m, options=opts,
+                             stream=torch.cuda.current_stream().cuda_stream)
+    for cams, pts in ((sc.cams_gt, sc.pts_gt), (sc.cams0, sc.pts0)):
+        cams_d.copy_(torch.as_tensor(np.ascontiguousarray(cams)))
+        pts_d.copy_(torch.as_tensor(np.ascontiguousarray(pts)))
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        F_ref, rmse_ref = prob.eval_cost(cams, pts)
+        F, rmse, n = out.tolist()
+        assert F == pytest.approx(F_ref, rel=1e-12)
+        assert rmse == pytest.approx(rmse_ref, rel=1e-12)
+        assert n == int(mask.sum())
