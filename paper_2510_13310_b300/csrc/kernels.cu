@@ -780,17 +780,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) k_pt_lin(Layou
     const V4* Wsrc = reinterpret_cast<const V4*>(Ws);
     for (int j = threadIdx.x; j < (kWStride / 4) * n; j += blockDim.x) Wdst[j] = Wsrc[j];
   }
-  for (int p = pb + threadIdx.x; p < pe; p += blockDim.x) {
-    T acc[9];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) acc[j] = T(0);
-    for (int k = L.pt_off[p]; k < L.pt_off[p + 1]; ++k)
-#pragma unroll
-      for (int j = 0; j < 9; ++j) acc[j] += Vs[9 * (k - ob) + j];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) V[6 * (size_t)p + j] = acc[j];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) gp[3 * (size_t)p + j] = acc[6 + j];
+  // nine threads per point, one per entry of (V, g_p), each summing the point's
+  // observations in order
+  for (int t = threadIdx.x; t < 9 * (pe - pb); t += blockDim.x) {
+    const int p = pb + t / 9, j = t - 9 * (t / 9);
+    T acc = T(0);
+    for (int k = L.pt_off[p]; k < L.pt_off[p + 1]; ++k) acc += Vs[9 * (k - ob) + j];
+    if (j < 6) V[6 * (size_t)p + j] = acc;
+    else gp[3 * (size_t)p + j - 6] = acc;
   }
 }
 
