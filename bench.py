@@ -47,7 +47,14 @@ NCU_TRAFFIC = {("medium", "k_spcg"): 13154816 + 26368, ("medium", "k_form_S_runs
                ("dense_mid", "k_form_S_cam"): 367535616 + 51516160}
 # the measured limiter of a kernel whose roofline bound (ALU) is not what stops it:
 # ncu counters of one launch on the workload (profiles/<kernel>_<workload>...md)
-NCU_LIMITER = {("medium", "k_form_S_runs"): {
+NCU_LIMITER = {("medium", "k_spcg"): {
+    "counter": "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed", "value_pct": 0.72,
+    "issue_active_pct": 40.4, "l1tex_throughput_pct": 39.3, "warps_active_pct": 25.1,
+    "reading": "latency-bound: S^ is read from HBM once per launch and then from shared memory; each PCG "
+               "iteration is a shared-memory matvec of 12-13 rows per block and one all-gather of q through "
+               "tagged words in L2 (about a third of the iteration waiting for the slowest block's words)",
+    "source": "profiles/k_spcg_medium_1M_obs.md"},
+    ("medium", "k_form_S_runs"): {
     "counter": "l1tex__throughput.avg.pct_of_peak_sustained_active", "value_pct": 93.9,
     "long_scoreboard_cycles_per_issue": 8.0, "warp_cycles_per_issue": 9.92,
     "reading": "the L1TEX pipe moving the scattered 112-byte Y^ row gathers (two per co-visible pair) is "
@@ -535,7 +542,9 @@ def main():
                 "algorithmic_per_launch": per_launch,
                 "formula": unit_txt, "launch_ms_mean": kern_ms,
                 "mean_pcg_iters": mean_it, "us_per_pcg_iter": (kern_ms * 1e3 / mean_it) if mean_it else None,
-                "solver": solver_name}
+                "solver": solver_name,
+                "measured_limiter": NCU_LIMITER.get((args.workload, "k_spcg"))
+                if kind == ba.BA_SOLVER_EXPLICIT and args.precision == "fp32" else None}
     roof_form = None
     form = [i["ms"][7] for i in infos if i["ms"][7] > 0]
     if form:
