@@ -240,9 +240,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
 //   intr-trans g (T2^T h2)^T, intr-intr c g g2^T.
 // A pair reads two observation records and the point's record (V*^-1, 32 B,
 // written with V*^-1 by the point damping): 160 B in five 32-byte loads, against
-// two 112-byte rows of Y^ = D^-1 W M_p, and no Y^ pass runs.  The gathers are
-// what limits this kernel (one L1 wavefront per lane and load, the lanes' records
-// being scattered), hence the 32-byte loads and the stored a and g.  The Jacobi
+// two 112-byte rows of Y^ = D^-1 W M_p, and no Y^ pass runs.  The latency of these
+// scattered gathers is what limits this kernel (12 resident warps per SM at 168
+// registers); the 32-byte loads and the stored a and g keep the loads and the
+// per-pair arithmetic few.  The Jacobi
 // scaling is applied to the summed block.  Each lane sums its pairs in order (the
 // intrinsic rows' 27 sums in shared memory, the other 54 in registers) and the
 // lanes are reduced in a fixed butterfly (deterministic).
